@@ -1,0 +1,185 @@
+"""Pins of the oracle's scheme layer: what decrypts must equal the plaintext-side
+computation the paper states (rotation = slot roll, conj, products, BSGS = matrix
+product, conv = FP64 conv2d, EvalMod = sine), plus the Table 1 operation counts."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import boot as BT
+from oracle import encoding as E
+from oracle import params as PP
+from oracle.scheme import Oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(11)
+
+
+@pytest.fixture(scope="module")
+def small():
+    P = PP.Params(9, 6, 3, 60, 40, 60, h=32)
+    o = Oracle(P, 42)
+    o.gen_relin_key()
+    o.gen_conj_key()
+    o.gen_rotation_keys([1, 3, 7, 100])
+    return o
+
+
+def slots(o, ct):
+    return o.decode_slots(o.decrypt(ct))
+
+
+def cvec(n):
+    return rng.normal(size=n) + 1j * rng.normal(size=n)
+
+
+def test_encrypt_decrypt(small):
+    o = small
+    m = o.P.n // 2
+    z = cvec(m)
+    for lev in (o.P.L, 2, 0):
+        pt = o.encode_pt(z, lev, o.P.delta[lev])
+        assert np.abs(slots(o, o.encrypt(pt, 1)) - z).max() < 1e-6
+        assert np.abs(slots(o, o.encrypt_sk(pt, 2)) - z).max() < 1e-6
+        # decode(encode) without encryption is exact to the rounding of the encoding
+        assert np.abs(o.decode_slots(pt) - z).max() < 1e-9
+
+
+def test_rotation_conjugation_product(small):
+    o = small
+    m = o.P.n // 2
+    z = cvec(m)
+    L = o.P.L
+    ct = o.encrypt(o.encode_pt(z, L, o.P.delta[L]), 3)
+    outs = o.rotate_hoisted(ct, [0, 1, 3, 7, 100])
+    for r, c in zip([0, 1, 3, 7, 100], outs):
+        assert np.abs(slots(o, c) - np.roll(z, -r)).max() < 1e-6       # HRot: slot j <- j + r
+    assert np.abs(slots(o, o.conjugate(ct)) - np.conj(z)).max() < 1e-6
+    sq = o.rescale(o.mul_relin(ct, ct))
+    assert sq.scale == o.P.delta[L - 1]                                 # canonical ladder
+    assert np.abs(slots(o, sq) - z * z).max() < 1e-5
+    im = o.imult(ct)
+    assert np.abs(slots(o, im) - 1j * z).max() < 1e-6
+    down = o.level_down(ct, 1)
+    assert down.level == 1 and abs(down.scale - o.P.delta[1]) < 1e-9 * down.scale
+    assert np.abs(slots(o, down) - z).max() < 1e-5
+    c = o.add_const(ct, 0.75)
+    assert np.abs(slots(o, c) - (z + 0.75)).max() < 1e-6
+
+
+def test_mod_raise_overflow_is_small_multiple_of_q0(small):
+    o = small
+    m = o.P.n // 2
+    ct = o.encrypt(o.encode_pt(cvec(m) * 0.1, 0, 2.0 ** 30), 4)
+    t0 = o.centred_coeffs(o.decrypt(ct))
+    raised = o.mod_raise(ct)
+    t = o.centred_coeffs(o.decrypt(raised))
+    I = (t - t0) / float(o.P.q[0])
+    assert np.allclose(I, np.round(I))
+    assert np.abs(I).max() <= (o.P.h + 1) / 2
+
+
+def test_bsgs_equals_matrix_product(small):
+    """Eq. 3 with the BSGS split (Sec. 2.5) on a sparse matrix with AP diagonals"""
+    o = small
+    m = o.P.n // 2
+    L = o.P.L
+    a0, step, count = m - 6, 3, 5
+    diags = {(a0 + step * i) % m: cvec(m) * 0.3 for i in range(count)}
+    o.gen_rotation_keys([step * b for b in range(1, 4)] + [(a0 + step * 2 * g) % m for g in range(3)]
+                        + [(a0 + step * 4 * g) % m for g in range(2)])
+    z = cvec(m)
+    ct = o.encrypt(o.encode_pt(z, L, o.P.delta[L]), 5)
+    want = E.diag_apply(diags, z)
+    for B in (1, 2, 4):
+        o.gen_rotation_keys([(a0 + step * B * g) % m for g in range(-(-count // B))])
+        plan = o.make_plan(diags, a0, step, count, L, float(o.P.q[L]), B)
+        out = o.rescale(o.bsgs(ct, plan))
+        assert np.abs(slots(o, out) - want).max() < 1e-5
+
+
+def test_cfg1_conv_matches_fp64_and_table1():
+    """config-1 shape: fused CinS conv == FP64 conv2d; op counts = Table 1 (C PMult,
+    2 sqrt(C) - 2 HRot, one rescale)"""
+    gold = json.load(open(os.path.join(GOLD, "table1_op_counts.json")))
+    assert gold["conv2d"]["pmult"] == "C" and gold["conv2d"]["hrot"] == "2*sqrt(C)-2"
+    P = PP.cfg1_params()
+    o = Oracle(P, 1)
+    x = rng.random((1, 16, 16))
+    W = rng.uniform(-1, 1, (1, 1, 3, 3))
+    w = E.pad_width(16, 3)
+    C = P.n // (w * w)
+    z = E.cins_input_slots(x, w, P.n)
+    for lev in (P.L, 1):
+        ct = o.encrypt(o.encode_pt(z, lev, P.delta[lev]), 3)
+        plan = o.conv_plan(W, 1, 1, 3, w, lev, (P.delta[lev - 1] * float(P.q[lev])) / ct.scale)
+        o.gen_rotation_keys(plan.rotations(P.n // 2))
+        o.ops = {k: 0 for k in o.ops}
+        out = o.conv2d_cins(ct, plan)
+        assert o.ops["pmult"] == C and o.ops["hrot"] == 2 * math.isqrt(C) - 2
+        assert out.level == lev - 1 and o.ops["rescale"] == 1
+        got = E.conv_output_from_coeffs(o.decode_coeffs(o.decrypt(out)), C, w * w, 1, w, 16)
+        assert np.abs(got - E.conv2d_same(x, W)).max() < 1e-6
+
+
+def test_full_channel_conv_op_counts():
+    """C = C_in = C_out = 16 channels per ciphertext: 16 PMult and 6 HRot (Table 1)"""
+    P = PP.Params(10, 3, 1, 60, 42, 60)
+    o = Oracle(P, 2)
+    w0, w = 4, 8
+    C = P.n // (w * w)
+    x = rng.random((C, w0, w0))
+    W = rng.normal(0, 0.1, (C, C, 3, 3))
+    ct = o.encrypt(o.encode_pt(E.cins_input_slots(x, w, P.n), 1, P.delta[1]), 1)
+    plan = o.conv_plan(W, C, C, 3, w, 1, (P.delta[0] * float(P.q[1])) / ct.scale)
+    o.gen_rotation_keys(plan.rotations(P.n // 2))
+    o.ops = {k: 0 for k in o.ops}
+    out = o.conv2d_cins(ct, plan)
+    assert o.ops["pmult"] == 16 and o.ops["hrot"] == 6
+    got = E.conv_output_from_coeffs(o.decode_coeffs(o.decrypt(out)), C, w * w, C, w, w0)
+    assert np.abs(got - E.conv2d_same(x, W)).max() < 1e-6
+
+
+def test_chebyshev_and_evalmod(small):
+    o = small
+    P = o.P
+    m = P.n // 2
+    y = rng.uniform(-1, 1, m)
+    L = P.L
+    ct = o.encrypt(o.encode_pt(y, L, P.delta[L]), 6)
+    coeffs = np.polynomial.chebyshev.chebinterpolate(lambda t: np.sin(3 * t) + 0.5 * t * t, 5)
+    out = o.cheb_eval(ct, list(coeffs))
+    assert out.level == L - math.ceil(math.log2(5)) - 1
+    assert np.abs(slots(o, out).real - np.polynomial.chebyshev.chebval(y, coeffs)).max() < 1e-5
+
+
+@pytest.mark.slow
+def test_block_matches_fp64_conv():
+    """Alg. 1 block (no activation) at N = 2^10 with the config-2 prime chain: decoded output
+    is the masked conv output within 2^-12 (spec accuracy bar)"""
+    P = PP.Params(10, 24, 3, 60, 42, 60, h=192, n_p=7, boot_bits=48, n_boot=14)
+    o = Oracle(P, 5)
+    w0, w, f = 4, 8, 3
+    n = P.n
+    C = n // (w * w)
+    cin = cout = 4
+    x = rng.random((cin, w0, w0))
+    W = rng.normal(0, 0.1, (cout, cin, f, f))
+    ct = o.encrypt(o.encode_pt(E.cins_input_slots(x, w, n), 1, P.delta[1]), 3)
+    cfg = BT.BootConfig(o, w, w0, cout)
+    plan = o.conv_plan(W, cin, cout, f, w, 1, (cfg.delta0 * float(P.q[1])) / ct.scale)
+    o.gen_rotation_keys(BT.block_rotations(o, plan, cfg))
+    o.gen_conj_key()
+    o.gen_relin_key()
+    out = BT.block(o, ct, plan, cfg)
+    assert out.level == cfg.l_out
+    got = slots(o, out)
+    ell = w * w // 2
+    pix = np.stack([E.encode(got[i * ell:(i + 1) * ell], w * w) for i in range(C)])
+    ref = np.zeros((C, w * w))
+    conv = E.conv2d_same(x, W)
+    for i in range(cout):
+        ref[i] = E.flatten_padded(conv[i], w)
+    assert np.abs(pix - ref).max() < 2.0 ** -12
