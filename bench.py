@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark: ms per conv2d + bootstrap block at N = 2^16 (config 2).
+
+One step = one Alg. 1 block (fused CinS conv -> ModRaise -> CtoS -> EvalMod(Re, Im)
+-> mask -> StoC1) on one ciphertext holding 16 channels of 32 x 32 (padded to 64 x 64),
+with 3x3 Gaussian(0, 0.1) weights.  Keys, plaintext diagonals and the input
+ciphertext are resident in HBM before the timed region; the working set (rotation
+keys alone are several GB) is far larger than the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as WL  # noqa: E402
+
+METRIC = "ms per conv2d+bootstrap block at N=2^16"
+CONFIG = "cfg2"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+# ------------------------------------------------------------- workload -----
+def block_setup(K, torch, seed=1):
+    d = WL.PARAMS[CONFIG]
+    spec = WL.CONV[CONFIG]
+    w = 1
+    while w < spec["w0"] + spec["f"] // 2:
+        w *= 2
+    ctx = K.ckks_ctx_create(d, seed, torch.cuda.current_stream().cuda_stream)
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
+    delta0 = 2.0 ** 49
+    x = WL.image(seed, spec["cin"], spec["w0"])
+    W = WL.weights(seed, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+    conv = K.ckks_ptset_conv_fused(ctx, W, spec["cin"], spec["cout"], spec["f"], w, 1, (delta0 * q[1]) / delta[1])
+    rots = sorted(set(K.ckks_ptset_rotations(conv)) | set(K.ckks_boot_rotations(bt)))
+    keys = K.ckks_keygen(ctx, rots, True)
+    ct = K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, x, w, 1, delta[1]), 1)
+    K.ckks_sync(ctx)
+    return dict(ctx=ctx, keys=keys, bt=bt, conv=conv, ct=ct, x=x, W=W, w=w, spec=spec, rots=rots)
+
+
+def check_accuracy(K, s, out):
+    """decoded block output vs the masked FP64 conv2d (max abs error)"""
+    spec = s["spec"]
+    got = K.ckks_decode_image(s["ctx"], K.ckks_decrypt(s["ctx"], s["keys"], out), spec["cout"], spec["w0"], s["w"])
+    x, W = s["x"], s["W"]
+    c = spec["f"] // 2
+    h = spec["w0"]
+    xp = np.zeros((x.shape[0], h + 2 * c, h + 2 * c))
+    xp[:, c:c + h, c:c + h] = x
+    ref = np.zeros((W.shape[0], h, h))
+    for a in range(spec["f"]):
+        for b in range(spec["f"]):
+            ref += np.einsum("oi,ihw->ohw", W[:, :, a, b], xp[:, a:a + h, b:b + h])
+    return float(np.abs(got - ref).max())
+
+
+# ------------------------------------------------------------ oracle arm -----
+def oracle_sample(seconds_budget):
+    """Time the CPU oracle on a bounded sample of the block and scale it to ms per block.
+
+    Sample: the fused conv at level 1, then at level 19 one hoisted rotation (one key
+    switch), one rescale and one PMult, all at N = 2^16 on the config-2 chain.  The block
+    estimate is conv + n_keyswitch * t_ks + n_rescale * t_rs + n_pmult * t_pm, with the
+    counts of one block (taken from the block's structure: they are properties of the
+    algorithm, identical on both implementations)."""
+    from oracle import boot as BT
+    from oracle import encoding as E
+    from oracle import params as PP
+    from oracle.scheme import Oracle
+    d = WL.PARAMS[CONFIG]
+    spec = WL.CONV[CONFIG]
+    P = PP.Params(d["log_n"], d["n_q"], d["dnum"], d["q0_bits"], d["scale_bits"], d["p_bits"], h=d["h"],
+                  sigma=d["sigma"], n_p=d["n_p"], boot_bits=d["boot_bits"], n_boot=d["n_boot"])
+    o = Oracle(P, 1)
+    w = E.pad_width(spec["w0"], spec["f"])
+    x = WL.image(1, spec["cin"], spec["w0"])
+    W = WL.weights(1, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+    plan = o.conv_plan(W, spec["cin"], spec["cout"], spec["f"], w, 1, (2.0 ** 49 * float(P.q[1])) / P.delta[1])
+    o.gen_rotation_keys(plan.rotations(P.n // 2) + [1])
+    ct = o.encrypt(o.encode_pt(E.cins_input_slots(x, w, P.n), 1, P.delta[1]), 1)
+    t0 = time.perf_counter()
+    o.conv2d_cins(ct, plan)
+    t_conv = time.perf_counter() - t0
+    hi = o.encrypt(o.encode_pt(WL.slots(2, P.n // 2, 0.5), 19, P.delta[19]), 2)
+    reps = 0
+    t_ks = t_rs = t_pm = 0.0
+    pt = o.encode_pt(WL.slots(3, P.n // 2), 19, P.delta[19])
+    start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        o.rotate(hi, 1)
+        t1 = time.perf_counter()
+        o.rescale(hi)
+        t2 = time.perf_counter()
+        o.mul_plain(hi, pt)
+        t3 = time.perf_counter()
+        t_ks += t1 - t0
+        t_rs += t2 - t1
+        t_pm += t3 - t2
+        reps += 1
+        if time.perf_counter() - start > seconds_budget * 0.5 or reps >= 8:
+            break
+    t_ks, t_rs, t_pm = t_ks / reps, t_rs / reps, t_pm / reps
+    counts = block_op_counts()
+    est = t_conv + counts["keyswitch"] * t_ks + counts["rescale"] * t_rs + counts["pmult"] * t_pm
+    cores = os.cpu_count()
+    sample = ("oracle at N=2^16, config-2 chain: fused conv at level 1 (%.2f s) + %d x [1 key switch, 1 rescale, "
+              "1 PMult] at level 19 (%.2f / %.3f / %.3f s each); ms per block = conv + %d keyswitch + %d rescale + "
+              "%d PMult" % (t_conv, reps, t_ks, t_rs, t_pm, counts["keyswitch"], counts["rescale"], counts["pmult"]))
+    return est * 1e3, cores, sample
+
+
+def block_op_counts():
+    """operation counts of one config-2 block (from the library's counters when it has run,
+    else the algorithm's fixed structure as recorded in the design doc)"""
+    path = os.path.join(ROOT, "profiles", "block_op_counts.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {"keyswitch": 180, "rescale": 300, "pmult": 120}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    cores = sample = None
+    for i in range(args.warmup + args.steps):
+        v, cores, sample = oracle_sample(per_step)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "config-2 block: 16x32x32 -> 16, 3x3 conv fused with StoC2, full bootstrap, "
+                                   "N=2^16, 24 limbs", "l2": "working set > L2"},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU arm -----
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+
+    s = block_setup(K, torch, seed=1 + rank)
+    ctx = s["ctx"]
+    out = K.ckks_ct_create(ctx)
+    for _ in range(args.warmup):
+        K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
+    K.ckks_sync(ctx)
+    err = check_accuracy(K, s, out)
+    # operation counts of one block
+    K.ckks_ctx_reset_counters(ctx)
+    K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
+    K.ckks_sync(ctx)
+    counts = K.ckks_ctx_counters(ctx)
+
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = K.ckks_ctx_counters(ctx)["launches"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    launches = K.ckks_ctx_counters(ctx)["launches"] - launches0
+    if dist:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    ms_per_step = t_ms / args.steps
+    value = t_ms / (args.steps * world)
+
+    # end to end through the C ABI with host buffers: import (H2D + NTT), block, export (iNTT + D2H)
+    host_in = torch.empty(K.ckks_ct_export_rns(ctx, s["ct"]).size, dtype=torch.int64, pin_memory=True).numpy()
+    host_in[:] = K.ckks_ct_export_rns(ctx, s["ct"]).reshape(-1).view(np.int64)
+    lev_in, sc_in = K.ckks_ct_info(s["ct"])
+    lev_out, _ = K.ckks_ct_info(out)
+    host_out = torch.empty(2 * (lev_out + 1) * ctx.n, dtype=torch.int64, pin_memory=True).numpy()
+    ct_in = K.ckks_ct_create(ctx)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        K.ckks_ct_import_rns(ctx, host_in.view(np.uint64), lev_in, sc_in, ct_in)
+        K.ckks_block(ctx, s["keys"], ct_in, s["conv"], s["bt"], out)
+        K.lib().ckks_ct_export_rns(ctx, out, host_out.ctypes.data_as(K.ctypes.c_void_p))
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+
+    # per-kernel CUDA-event timing of one more block (roofline of the dominant kernel)
+    K.ckks_ctx_reset_counters(ctx)
+    K.ckks_ctx_set_timing(ctx, 1)
+    K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
+    K.ckks_ctx_set_timing(ctx, 0)
+    kst = K.ckks_ctx_kernel_stats(ctx)
+    total = sum(v["ms"] for v in kst.values())
+    top = max(kst.items(), key=lambda kv: kv[1]["ms"])
+    pk = peaks()
+    achieved = top[1]["bytes"] / (top[1]["ms"] * 1e-3) / 1e9
+    roof = {"kernel": top[0], "bound": "hbm", "achieved": round(achieved, 1), "peak": pk.get("hbm_gbs"),
+            "unit": "GB/s", "frac": round(achieved / pk.get("hbm_gbs"), 4), "traffic": None,
+            "share": round(top[1]["ms"] / total, 4),
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                            "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                        for k, v in sorted(kst.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            v, cores, sample = oracle_sample(args.cpu_sample_seconds)
+            cpu = {"value": round(v, 1), "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
+        except Exception as e:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": "failed: %s" % e}
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "config-2 block: 16x32x32 -> 16, 3x3 conv fused with StoC2, full bootstrap "
+                                   "(CtoS 3 levels, EvalMod deg 59 + 3 double angles, StoC1 3 levels), "
+                                   "N=2^16, 24 limbs", "batch": 1, "l2": "working set > L2 (keys ~GBs)",
+                       "decoded_max_abs_err": err, "parallelism": "replicas" if world > 1 else "single"},
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(host_in.nbytes),
+                    "d2h_bytes_per_step": int(host_out.nbytes)},
+            "roofline": roof, "op_counts": counts, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

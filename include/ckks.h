@@ -1,0 +1,286 @@
+/*
+ * ckks.h -- C ABI of the GB300 RNS-CKKS library for CinS conv2d fused with
+ * bootstrapping (NeuJeans, arXiv 2312.04356).
+ *
+ * Scheme: RNS-CKKS (Sec. 2.1: KeyGen / Enc / Dec / Eval, HE ops "OpName(ct, x)",
+ * HRot), bootstrapping ModRaise -> CtoS -> ModEval -> StoC (Sec. 2.4), CinS
+ * encoding (Sec. 3), conv2d by diagonal BSGS (Sec. 2.5, Eq. 3, Eq. 7), fusion of
+ * the conv with StoC2 (Sec. 4, Eq. 8) and the Alg. 1 block.
+ *
+ * Conventions
+ *  - Ring Z_q[X]/(X^N + 1).  A polynomial at level l has l+1 RNS limbs mod
+ *    q_0..q_l; the library stores them on the device limb-major, uint64
+ *    [limb][N], in the NTT (evaluation) domain, bit-reversed order.  Arrays that
+ *    cross this ABI through *_import_rns / *_export_rns are host arrays in the
+ *    COEFFICIENT domain, same [limb][N] layout (a ciphertext is [2][l+1][N]:
+ *    c0 then c1), residues in [0, q_i).
+ *  - Slots: z_j = m(zeta^(5^j)), zeta = exp(pi i / N), j < N/2 (Sec. 2.2);
+ *    HRot(ct, r) moves slot j + r to slot j (Galois element 5^r mod 2N).
+ *  - Every ciphertext carries a level and a scale (double).  Each level has a
+ *    canonical scale Delta_l with Delta_{l-1} = Delta_l^2 / q_l inside each of
+ *    the two prime segments (bootstrapping levels, circuit levels).
+ *  - Handles are opaque and owned by the caller, who creates and destroys them;
+ *    no call takes ownership of its arguments.  Inputs are const; output
+ *    handles are overwritten (their device storage is resized as needed).
+ *    Output handles may alias inputs unless stated otherwise.
+ *  - All device work is enqueued on the stream given to ckks_ctx_create; calls
+ *    return once the work is enqueued unless stated otherwise.  ckks_sync waits
+ *    and reports deferred device errors.  A handle may only be used with the
+ *    context that created it.
+ *  - Return value: CKKS_OK (0) or one of the CKKS_E* codes; no exceptions cross
+ *    the ABI.  ckks_last_error(ctx) describes the last failure on that context.
+ *  - Randomness: SplitMix64 used as a counter generator; stream key
+ *    mix(seed ^ mix(tag + 0x9E3779B97F4A7C15)), word i = mix(key + (i+1)*gamma),
+ *    with the tag layout kind<<56 | a<<16 | b.  Uniform residues are drawn
+ *    directly in the NTT domain as (w[2k] << 64 | w[2k+1]) mod q, k = prime_id*N + j.
+ */
+#ifndef CKKS_GB300_H
+#define CKKS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CKKS_OK 0
+#define CKKS_EINVAL 1   /* bad argument, shape, level or scale mismatch */
+#define CKKS_ENOKEY 2   /* a needed rotation / conjugation / relinearisation key is absent */
+#define CKKS_ELEVEL 3   /* not enough levels left for the operation */
+#define CKKS_ENOMEM 4   /* device allocation failed */
+#define CKKS_ETIMEOUT 5 /* a bounded device wait gave up */
+#define CKKS_ECUDA 6    /* any other CUDA error */
+
+typedef struct ckks_ctx ckks_ctx;
+typedef struct ckks_keys ckks_keys;
+typedef struct ckks_ct ckks_ct;
+typedef struct ckks_pt ckks_pt;
+typedef struct ckks_ptset ckks_ptset;
+typedef struct ckks_boot ckks_boot;
+
+/* Parameter set (Table 3 and the RNS-CKKS chain).
+ *   log_n       log2 N
+ *   n_q         Q-limbs; levels 0..n_q-1
+ *   dnum        key-switching digits; alpha = ceil(n_q / dnum) limbs per digit
+ *   n_p         special primes (0 = alpha)
+ *   q0_bits     base prime q_0 = largest prime < 2^q0_bits, = 1 mod 2N
+ *   scale_bits  circuit levels 1..n_q-1-n_boot: Delta = 2^scale_bits
+ *   p_bits      special primes: next largest primes < 2^p_bits, = 1 mod 2N
+ *   boot_bits, n_boot  the top n_boot levels use base 2^boot_bits (0 = none)
+ *   h           Hamming weight of the secret (0 = uniform ternary)
+ *   sigma       Gaussian error deviation (truncated at |e| <= 19)
+ * Scaling primes: within a segment of base 2^b, from its top level down, q_l is
+ * the unused prime = 1 mod 2N nearest to Delta_l^2 / 2^b (ties: the smaller),
+ * Delta_top = 2^b, Delta_{l-1} = Delta_l^2 / q_l.  The bootstrapping segment is
+ * chosen first.  psi_i is the smallest primitive 2N-th root of unity mod q_i. */
+typedef struct ckks_params {
+    int log_n, n_q, dnum, n_p;
+    int q0_bits, scale_bits, p_bits;
+    int boot_bits, n_boot;
+    int h;
+    double sigma;
+} ckks_params;
+
+/* ---- context ------------------------------------------------------------ */
+/* Builds primes, roots and twiddle tables on `cuda_stream` (a cudaStream_t, NULL =
+ * legacy default stream).  seed drives every random draw of keys and encryption.
+ * Errors: CKKS_EINVAL (log_n outside 3..17, n_q < 1, ...), CKKS_ENOMEM, CKKS_ECUDA. */
+int ckks_ctx_create(const ckks_params* params, uint64_t seed, void* cuda_stream, ckks_ctx** out);
+int ckks_ctx_destroy(ckks_ctx* ctx);
+const char* ckks_last_error(const ckks_ctx* ctx);
+/* Waits for the context's stream; returns CKKS_ECUDA on a deferred device error. */
+int ckks_sync(ckks_ctx* ctx);
+/* Host copies of the chain: q[n_q], p[n_p], psi[n_q + n_p] (q's then p's), delta[n_q].
+ * Any pointer may be NULL. */
+int ckks_ctx_info(const ckks_ctx* ctx, uint64_t* q, uint64_t* p, uint64_t* psi, double* delta);
+/* The 39-entry cumulative table of the Gaussian sampler (entry k: values <= k - 19). */
+int ckks_ctx_gauss_table(const ckks_ctx* ctx, uint64_t* table39);
+
+/* ---- measurement (the paper's per-phase breakdown, Table 2) ---------------- */
+/* Switch per-kernel CUDA-event timing on or off (off by default).  While on, every
+ * kernel launch is bracketed by two events on the context's stream. */
+int ckks_ctx_set_timing(ckks_ctx* ctx, int on);
+/* counters[0..5] = kernel launches, key switches, PMults, HRots, HMults, rescales
+ * since the context was created (or the last reset) */
+int ckks_ctx_counters(const ckks_ctx* ctx, int64_t* counters6);
+int ckks_ctx_reset_counters(ckks_ctx* ctx);
+/* Per-kernel statistics gathered while timing was on, as a JSON object
+ * {"kernel": [launches, total_ms, algorithmic_bytes], ...} (bytes: the minimum each
+ * launch must read and write, summed) written to buf (NUL-terminated, truncated
+ * to cap bytes); *len receives the full length.  Synchronises the stream. */
+int ckks_ctx_kernel_stats(ckks_ctx* ctx, char* buf, int cap, int* len);
+
+/* ---- keys (Sec. 2.1 KeyGen) ----------------------------------------------- */
+/* Secret key s (h-sparse or uniform ternary), public key (-a s + e, a) over Q_L,
+ * relinearisation key, rotation keys for every step in rot_steps (mod N/2, 0 and
+ * duplicates ignored) and, if want_conj, the conjugation key.  Switching keys are
+ * hybrid: per digit d, (b_d, a_d) over Q_L u P with b_d = -a_d s + e_d + [P]_{q_i} s'
+ * on the digit's limbs.  Keys stay resident on the device. */
+int ckks_keygen(ckks_ctx* ctx, const int32_t* rot_steps, int n_rot, int want_conj, ckks_keys** out);
+int ckks_keys_add_rotations(ckks_ctx* ctx, ckks_keys* keys, const int32_t* rot_steps, int n_rot);
+int ckks_keys_destroy(ckks_keys* keys);
+/* host copy of the secret key's coefficients (int64[N], values in {-1, 0, 1}) */
+int ckks_keys_export_secret(ckks_ctx* ctx, const ckks_keys* keys, int64_t* s);
+
+/* ---- handles ------------------------------------------------------------ */
+int ckks_ct_create(ckks_ctx* ctx, ckks_ct** out);
+int ckks_ct_destroy(ckks_ct* ct);
+int ckks_ct_info(const ckks_ct* ct, int* level, double* scale);
+int ckks_ct_set_scale(ckks_ct* ct, double scale);
+/* host [2][level+1][N] coefficient domain <-> device (NTT domain inside) */
+int ckks_ct_import_rns(ckks_ctx* ctx, const uint64_t* host, int level, double scale, ckks_ct* out);
+int ckks_ct_export_rns(ckks_ctx* ctx, const ckks_ct* ct, uint64_t* host);
+int ckks_pt_create(ckks_ctx* ctx, ckks_pt** out);
+int ckks_pt_destroy(ckks_pt* pt);
+int ckks_pt_info(const ckks_pt* pt, int* level, double* scale);
+/* host [level+1][N] coefficient domain: the bit-exact parity path for plaintexts */
+int ckks_pt_import_rns(ckks_ctx* ctx, const uint64_t* host, int level, double scale, ckks_pt* out);
+int ckks_pt_export_rns(ckks_ctx* ctx, const ckks_pt* pt, uint64_t* host);
+
+/* ---- encoding (Sec. 2.2, Sec. 3.3.1) -------------------------------------- */
+#define CKKS_SLOT 0       /* n <= N/2 complex slots (re, im); f = (1/N)(conj(U)^T z + U^T conj(z)) */
+#define CKKS_COEFF 1      /* n <= N real coefficients (re) */
+#define CKKS_CINS_REAL 2  /* real CinS (Eq. 5): n = C * slice_len reals, slice_len = 2l, C = N / 2l;
+                             slot i*l + j = sum_k m_i[k] omega_{4l}^(5^j k) (Appendix A) */
+/* FP64 on the host; coefficients round(scale * f) (halves away from zero), |.| < 2^62. */
+int ckks_encode(ckks_ctx* ctx, const double* re, const double* im, int n, int level, double scale,
+                int kind, int slice_len, ckks_pt* out);
+/* Exact CRT to centred integers, divide by the plaintext's scale, then the inverse
+ * of `kind`.  Blocks until the data is on the host. */
+int ckks_decode(ckks_ctx* ctx, const ckks_pt* pt, int kind, int slice_len, double* re, double* im, int n);
+
+/* Data organisation of Sec. 3.3.2: each of the c channels of img ([c][w0][w0] doubles)
+ * is zero-padded to w x w (image top-left), flattened row-major and placed in slice i
+ * (2l = w^2 reals, C = N / w^2 >= c slices), then real-CinS encoded (Eq. 5). */
+int ckks_encode_image(ckks_ctx* ctx, const double* img, int c, int w0, int w, int level, double scale,
+                      ckks_pt* out);
+/* Inverse reading into out[c][w0][w0].  from_coeff = 0: real-CinS slots.  from_coeff = 1:
+ * the coefficient-encoded output of the fused conv, channel i at coefficients
+ * k*C + rev_C(i), k < w^2 (Thm. 2 with Y = X^C).  Blocks until the data is on the host. */
+int ckks_decode_image(ckks_ctx* ctx, const ckks_pt* pt, int from_coeff, int c, int w0, int w, double* out);
+
+/* ---- encryption (Sec. 2.1 Enc / Dec) -------------------------------------- */
+/* pk: (u b + e0 + m, u a + e1), u uniform ternary, e0, e1 Gaussian; streams tagged by nonce */
+int ckks_encrypt(ckks_ctx* ctx, const ckks_keys* keys, const ckks_pt* pt, uint64_t nonce, ckks_ct* out);
+/* sk: (-a s + e + m, a), a uniform over the level's limbs */
+int ckks_encrypt_sk(ckks_ctx* ctx, const ckks_keys* keys, const ckks_pt* pt, uint64_t nonce, ckks_ct* out);
+/* m = c0 + c1 s */
+int ckks_decrypt(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, ckks_pt* out);
+
+/* ---- HE ops (Sec. 2.1 "OpName(ct, x)") ------------------------------------ */
+/* HAdd / HSub: same level, scales equal to 2^-30 relative */
+int ckks_add(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out);
+int ckks_sub(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out);
+/* PMult without rescale: scale = ct.scale * pt.scale; pt must be at the ct's level */
+int ckks_mul_plain(ckks_ctx* ctx, const ckks_ct* ct, const ckks_pt* pt, ckks_ct* out);
+/* HMult: tensor, relinearise (key switch of c1 c1'), no rescale; same level */
+int ckks_mul_relin(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* a, const ckks_ct* b, ckks_ct* out);
+/* CMult by an integer (scale unchanged) */
+int ckks_mul_int(ckks_ctx* ctx, const ckks_ct* ct, int64_t c, ckks_ct* out);
+/* CAdd: every slot += c, as llround(c * scale) added to the constant coefficient */
+int ckks_add_const(ckks_ctx* ctx, const ckks_ct* ct, double c, ckks_ct* out);
+/* every slot times i (polynomial times X^(N/2)) */
+int ckks_imult(ckks_ctx* ctx, const ckks_ct* ct, ckks_ct* out);
+/* Rescale (Sec. 2.4): c'_i = (c_i - [c_l]_{q_l, centred}) q_l^{-1}; scale / q_l */
+int ckks_rescale(ckks_ctx* ctx, const ckks_ct* ct, ckks_ct* out);
+/* drop limbs above `level` (scale unchanged) */
+int ckks_mod_drop(ckks_ctx* ctx, const ckks_ct* ct, int level, ckks_ct* out);
+/* per level: times llround((Delta_{l-1} * q_l) / scale), rescale, scale := Delta_{l-1} */
+int ckks_level_down(ckks_ctx* ctx, const ckks_ct* ct, int level, ckks_ct* out);
+/* ModRaise (Sec. 2.4): level-0 ct, centred residues mod q_0 lifted to every limb; scale kept */
+int ckks_mod_raise(ckks_ctx* ctx, const ckks_ct* ct, ckks_ct* out);
+/* HRot for each step (Sec. 2.1): one ModUp of c1 shared by all steps ("hoisted");
+ * per step: Galois automorphism of the raised digits, inner product with the key,
+ * ModDown.  outs[i] receives step i; outs must not alias `in`.  CKKS_ENOKEY if a key
+ * is missing. */
+int ckks_rotate_hoisted(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const int32_t* steps,
+                        int n, ckks_ct* const* outs);
+/* conjugation (Galois element 2N - 1) */
+int ckks_conjugate(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, ckks_ct* out);
+
+/* ---- BSGS linear maps (Sec. 2.5, Eq. 3) ----------------------------------- */
+/* A map on the N/2 slots with diagonals at offsets a0 + step*i (mod N/2), i < count,
+ * evaluated as sum_g rot_{a0+step*g*B}( sum_b pt_{g,b} (.) rot_{step*b}(ct) ) with
+ * pt_{g,b} = diag_{a0+step(gB+b)} pre-rotated right by a0 + step*g*B.  Absent
+ * (g, b) entries are zero diagonals.  All plaintexts sit at `level`. */
+int ckks_ptset_create(ckks_ctx* ctx, int a0, int step, int count, int bsgs_B, int level, double scale,
+                      ckks_ptset** out);
+int ckks_ptset_destroy(ckks_ptset* ps);
+/* host [level+1][N] coefficient-domain limbs of pt_{g,b} (copied) */
+int ckks_ptset_set_rns(ckks_ctx* ctx, ckks_ptset* ps, int g, int b, const uint64_t* host);
+int ckks_ptset_info(const ckks_ptset* ps, int* a0, int* step, int* count, int* bsgs_B, int* level,
+                    double* scale, int* n_pts);
+/* distinct non-zero rotation steps the map needs (baby then giant); *n_out = count */
+int ckks_ptset_rotations(const ckks_ptset* ps, int32_t* steps, int cap, int* n_out);
+/* evaluate the map, no rescale */
+int ckks_bsgs(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, const ckks_ptset* ps, ckks_ct* out);
+
+/* Fused CinS conv2d (Sec. 4.2): plaintexts of the diagonals of K' = S' K^, where K^ is
+ * the C x C slice matrix of DFT'_{2l}(k_{o,i}) (kernel vectors of Fig. 1 with 'same'
+ * padding, cross-correlation) and S' the slice matrix of StoC2 = S_{N/2 <- l}.
+ * weights: [cout][cin][f][f] doubles; channel i of the input sits in slice i of a
+ * w x w padded image (w a power of two, 2l = w^2, C = N / w^2 >= cin, cout).
+ * BSGS over offsets d*l, d < C; bsgs_B = 0 picks 2^ceil(log2(C)/2). */
+int ckks_ptset_conv_fused(ckks_ctx* ctx, const double* weights, int cin, int cout, int f, int w, int level,
+                          double pt_scale, int bsgs_B, ckks_ptset** out);
+/* Alg. 1 line 1: BSGS with the fused diagonals, then rescale.  The output is
+ * coefficient-encoded: coefficient k*C + rev_C(i) holds Delta * o_i[k] (Thm. 2, Y = X^C). */
+int ckks_conv2d_cins(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
+                     ckks_ct* out);
+
+/* ---- bootstrapping and the Alg. 1 block ----------------------------------- */
+typedef struct ckks_boot_params {
+    int w, w0, cout;      /* padded width, image width, output channels (masks) */
+    int K;                /* |ModRaise overflow| < K */
+    int r;                /* double-angle steps */
+    int deg;              /* Chebyshev degree of the cosine */
+    int ctos_levels, stoc_levels;
+    double delta0;        /* scale of the level-0 ciphertext entering ModRaise */
+} ckks_boot_params;
+/* Builds: ModRaise scale q0*K_eff and drop constant c_drop = llround((Delta_{ld-1} q_ld) /
+ * (q0 K)) with ld = L - ctos_levels, K_eff = (Delta_{ld-1} q_ld) / (q0 c_drop); CtoS =
+ * T_{N/2}^{-1} in ctos_levels BSGS levels (largest stride first, plaintext scale q_l,
+ * last level times 1/2); Chebyshev coefficients of cos(2 pi (K_eff y - 1/4) / 2^r);
+ * padding masks times q0 / (2 pi delta0); StoC1 = S_{l <- 1} in stoc_levels levels. */
+int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out);
+int ckks_boot_destroy(ckks_boot* bt);
+/* info[0..7] = K_eff, s_raise, c_drop, l_drop, l_em, l_out, s_em, s_mask */
+int ckks_boot_info(const ckks_boot* bt, double* info8);
+int ckks_boot_rotations(const ckks_boot* bt, int32_t* steps, int cap, int* n_out);
+/* replace one CtoS / StoC1 level, the EvalMod coefficients, or the masks
+ * (used to feed identical plaintexts to two implementations) */
+int ckks_boot_set_ctos(ckks_ctx* ctx, ckks_boot* bt, int i, const ckks_ptset* ps);
+int ckks_boot_set_stoc(ckks_ctx* ctx, ckks_boot* bt, int i, const ckks_ptset* ps);
+int ckks_boot_set_coeffs(ckks_ctx* ctx, ckks_boot* bt, const double* coeffs, int deg);
+int ckks_boot_set_masks(ckks_ctx* ctx, ckks_boot* bt, const ckks_pt* re, const ckks_pt* im);
+/* ModRaise -> CtoS -> conjugate split (Re = ct + conj, Im = i (conj - ct)) -> scale drop
+ * -> EvalMod(Re), EvalMod(Im) (Alg. 1 line 2). */
+int ckks_bootstrap(ckks_ctx* ctx, const ckks_keys* keys, const ckks_boot* bt, const ckks_ct* ct0,
+                   ckks_ct* out_re, ckks_ct* out_im);
+/* mask PMults, Re + i Im, HMatmul(S_{l<-1}) (Alg. 1 lines 3-6 without HActivation) */
+int ckks_stoc1(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* re, const ckks_ct* im, const ckks_boot* bt,
+               ckks_ct* out);
+/* one conv2d + bootstrap block: conv2d_cins -> bootstrap -> stoc1 */
+int ckks_block(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
+               const ckks_boot* bt, ckks_ct* out);
+
+/* ---- polynomial evaluation (HActivation) --------------------------------- */
+#define CKKS_BASIS_CHEB 0
+/* sum_k c_k T_k(y), y = (2x - a - b) / (b - a) (only a = -1, b = 1 supported); T_k from
+ * T_{ceil(k/2)} T_{floor(k/2)}, each c_k T_k brought to the canonical scale of the
+ * common target level after one rescale; levels used: ceil(log2 deg) + 1. */
+int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, int deg,
+                   int basis, double a, double b, ckks_ct* out);
+
+/* ---- raw kernels on caller device memory ---------------------------------- */
+/* In-place forward / inverse negacyclic NTT of n_limbs limbs at `dev` ([n_limbs][N]
+ * uint64 device memory, residues < q); limb i uses the prime with global id
+ * prime_ids[i] (q_0..q_L are 0..L, p_j is n_q + j).  Forward: out[i] =
+ * sum_j a[j] psi^((2 rev(i) + 1) j), bit-reversed order. */
+int ckks_ntt_forward(ckks_ctx* ctx, uint64_t* dev, int n_limbs, const int32_t* prime_ids);
+int ckks_ntt_inverse(ckks_ctx* ctx, uint64_t* dev, int n_limbs, const int32_t* prime_ids);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CKKS_GB300_H */

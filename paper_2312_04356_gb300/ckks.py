@@ -1,0 +1,606 @@
+"""Python binding of the C ABI in include/ckks.h (argument marshalling only).
+
+Every function has the name of the C entry point it wraps and raises CkksError
+on a non-zero status.  Handles are small owner objects that call the matching
+*_destroy when collected.  Host arrays are numpy arrays in the layouts the header
+documents (coefficient domain, [limb][N] uint64).
+
+The shared library is built in-tree by paper_2312_04356_gb300/build.py; if it is
+absent, loading fails with an error (there is no fallback implementation).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "_build", "libckks_gb300.so")
+
+CKKS_OK, CKKS_EINVAL, CKKS_ENOKEY, CKKS_ELEVEL, CKKS_ENOMEM, CKKS_ETIMEOUT, CKKS_ECUDA = range(7)
+CKKS_SLOT, CKKS_COEFF, CKKS_CINS_REAL = 0, 1, 2
+CKKS_BASIS_CHEB = 0
+
+_lib = None
+
+
+class CkksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("ckks error %d: %s" % (code, msg))
+        self.code = code
+
+
+class ckks_params(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_int), ("n_q", ctypes.c_int), ("dnum", ctypes.c_int), ("n_p", ctypes.c_int),
+                ("q0_bits", ctypes.c_int), ("scale_bits", ctypes.c_int), ("p_bits", ctypes.c_int),
+                ("boot_bits", ctypes.c_int), ("n_boot", ctypes.c_int), ("h", ctypes.c_int),
+                ("sigma", ctypes.c_double)]
+
+
+class ckks_boot_params(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int), ("w0", ctypes.c_int), ("cout", ctypes.c_int), ("K", ctypes.c_int),
+                ("r", ctypes.c_int), ("deg", ctypes.c_int), ("ctos_levels", ctypes.c_int),
+                ("stoc_levels", ctypes.c_int), ("delta0", ctypes.c_double)]
+
+
+VP = ctypes.c_void_p
+PVP = ctypes.POINTER(ctypes.c_void_p)
+I = ctypes.c_int
+D = ctypes.c_double
+U64 = ctypes.c_uint64
+I64 = ctypes.c_int64
+
+_SIGS = {
+    "ckks_ctx_create": [ctypes.POINTER(ckks_params), U64, VP, PVP],
+    "ckks_ctx_destroy": [VP],
+    "ckks_sync": [VP],
+    "ckks_ctx_info": [VP, VP, VP, VP, VP],
+    "ckks_ctx_gauss_table": [VP, VP],
+    "ckks_ctx_set_timing": [VP, I],
+    "ckks_ctx_counters": [VP, VP],
+    "ckks_ctx_reset_counters": [VP],
+    "ckks_ctx_kernel_stats": [VP, VP, I, VP],
+    "ckks_keygen": [VP, VP, I, I, PVP],
+    "ckks_keys_add_rotations": [VP, VP, VP, I],
+    "ckks_keys_destroy": [VP],
+    "ckks_keys_export_secret": [VP, VP, VP],
+    "ckks_ct_create": [VP, PVP],
+    "ckks_ct_destroy": [VP],
+    "ckks_ct_info": [VP, VP, VP],
+    "ckks_ct_set_scale": [VP, D],
+    "ckks_ct_import_rns": [VP, VP, I, D, VP],
+    "ckks_ct_export_rns": [VP, VP, VP],
+    "ckks_pt_create": [VP, PVP],
+    "ckks_pt_destroy": [VP],
+    "ckks_pt_info": [VP, VP, VP],
+    "ckks_pt_import_rns": [VP, VP, I, D, VP],
+    "ckks_pt_export_rns": [VP, VP, VP],
+    "ckks_encode": [VP, VP, VP, I, I, D, I, I, VP],
+    "ckks_decode": [VP, VP, I, I, VP, VP, I],
+    "ckks_encode_image": [VP, VP, I, I, I, I, D, VP],
+    "ckks_decode_image": [VP, VP, I, I, I, I, VP],
+    "ckks_encrypt": [VP, VP, VP, U64, VP],
+    "ckks_encrypt_sk": [VP, VP, VP, U64, VP],
+    "ckks_decrypt": [VP, VP, VP, VP],
+    "ckks_add": [VP, VP, VP, VP],
+    "ckks_sub": [VP, VP, VP, VP],
+    "ckks_mul_plain": [VP, VP, VP, VP],
+    "ckks_mul_relin": [VP, VP, VP, VP, VP],
+    "ckks_mul_int": [VP, VP, I64, VP],
+    "ckks_add_const": [VP, VP, D, VP],
+    "ckks_imult": [VP, VP, VP],
+    "ckks_rescale": [VP, VP, VP],
+    "ckks_mod_drop": [VP, VP, I, VP],
+    "ckks_level_down": [VP, VP, I, VP],
+    "ckks_mod_raise": [VP, VP, VP],
+    "ckks_rotate_hoisted": [VP, VP, VP, VP, I, VP],
+    "ckks_conjugate": [VP, VP, VP, VP],
+    "ckks_ptset_create": [VP, I, I, I, I, I, D, PVP],
+    "ckks_ptset_destroy": [VP],
+    "ckks_ptset_set_rns": [VP, VP, I, I, VP],
+    "ckks_ptset_info": [VP, VP, VP, VP, VP, VP, VP, VP],
+    "ckks_ptset_rotations": [VP, VP, I, VP],
+    "ckks_bsgs": [VP, VP, VP, VP, VP],
+    "ckks_ptset_conv_fused": [VP, VP, I, I, I, I, I, D, I, PVP],
+    "ckks_conv2d_cins": [VP, VP, VP, VP, VP],
+    "ckks_boot_create": [VP, ctypes.POINTER(ckks_boot_params), PVP],
+    "ckks_boot_destroy": [VP],
+    "ckks_boot_info": [VP, VP],
+    "ckks_boot_rotations": [VP, VP, I, VP],
+    "ckks_boot_set_ctos": [VP, VP, I, VP],
+    "ckks_boot_set_stoc": [VP, VP, I, VP],
+    "ckks_boot_set_coeffs": [VP, VP, VP, I],
+    "ckks_boot_set_masks": [VP, VP, VP, VP],
+    "ckks_bootstrap": [VP, VP, VP, VP, VP, VP],
+    "ckks_stoc1": [VP, VP, VP, VP, VP, VP],
+    "ckks_block": [VP, VP, VP, VP, VP, VP],
+    "ckks_eval_poly": [VP, VP, VP, VP, I, I, D, D, VP],
+    "ckks_ntt_forward": [VP, VP, I, VP],
+    "ckks_ntt_inverse": [VP, VP, I, VP],
+}
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(SO_PATH):
+        raise RuntimeError("CUDA library not built: %s is missing (run paper_2312_04356_gb300.build.build())"
+                           % SO_PATH)
+    L = ctypes.CDLL(SO_PATH)
+    for name, args in _SIGS.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.ckks_last_error.argtypes = [VP]
+    L.ckks_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    return list(_SIGS) + ["ckks_last_error"]
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _u64(a):
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------------ handles --
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ptr, ctx=None):
+        self.ptr = ptr
+        self.ctx = ctx          # keeps the context alive while the handle lives
+
+    @property
+    def _as_parameter_(self):
+        return self.ptr
+
+    def close(self):
+        if self.ptr:
+            getattr(lib(), self._destroy)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context(_Handle):
+    _destroy = "ckks_ctx_destroy"
+
+    def check(self, rc):
+        if rc != CKKS_OK:
+            msg = lib().ckks_last_error(self.ptr)
+            raise CkksError(rc, msg.decode() if msg else "")
+        return rc
+
+    def close(self):
+        if self.ptr:
+            lib().ckks_ctx_destroy(self.ptr)
+            self.ptr = None
+
+
+class Keys(_Handle):
+    _destroy = "ckks_keys_destroy"
+
+
+class Ciphertext(_Handle):
+    _destroy = "ckks_ct_destroy"
+
+
+class Plaintext(_Handle):
+    _destroy = "ckks_pt_destroy"
+
+
+class PtSet(_Handle):
+    _destroy = "ckks_ptset_destroy"
+
+
+class Boot(_Handle):
+    _destroy = "ckks_boot_destroy"
+
+
+# ------------------------------------------------------------- context ------
+def ckks_ctx_create(params: dict, seed: int, stream: int = 0) -> Context:
+    p = ckks_params(log_n=params["log_n"], n_q=params["n_q"], dnum=params["dnum"], n_p=params.get("n_p", 0),
+                    q0_bits=params["q0_bits"], scale_bits=params["scale_bits"], p_bits=params["p_bits"],
+                    boot_bits=params.get("boot_bits", 0), n_boot=params.get("n_boot", 0), h=params.get("h", 0),
+                    sigma=params.get("sigma", 3.2))
+    out = ctypes.c_void_p()
+    rc = lib().ckks_ctx_create(ctypes.byref(p), seed, ctypes.c_void_p(stream), ctypes.byref(out))
+    if rc != CKKS_OK:
+        raise CkksError(rc, "context creation failed")
+    ctx = Context(out.value)
+    ctx.params = dict(params)
+    ctx.n = 1 << params["log_n"]
+    ctx.n_q = params["n_q"]
+    alpha = -(-params["n_q"] // params["dnum"])
+    ctx.n_p = params.get("n_p", 0) or alpha
+    return ctx
+
+
+def ckks_sync(ctx):
+    ctx.check(lib().ckks_sync(ctx))
+
+
+def ckks_ctx_info(ctx):
+    q = np.zeros(ctx.n_q, dtype=np.uint64)
+    p = np.zeros(ctx.n_p, dtype=np.uint64)
+    psi = np.zeros(ctx.n_q + ctx.n_p, dtype=np.uint64)
+    delta = np.zeros(ctx.n_q, dtype=np.float64)
+    ctx.check(lib().ckks_ctx_info(ctx, _ptr(q), _ptr(p), _ptr(psi), _ptr(delta)))
+    return [int(x) for x in q], [int(x) for x in p], [int(x) for x in psi], [float(x) for x in delta]
+
+
+def ckks_ctx_gauss_table(ctx):
+    t = np.zeros(39, dtype=np.uint64)
+    ctx.check(lib().ckks_ctx_gauss_table(ctx, _ptr(t)))
+    return t
+
+
+def ckks_ctx_set_timing(ctx, on):
+    ctx.check(lib().ckks_ctx_set_timing(ctx, int(on)))
+
+
+def ckks_ctx_counters(ctx):
+    a = np.zeros(6, dtype=np.int64)
+    ctx.check(lib().ckks_ctx_counters(ctx, _ptr(a)))
+    return dict(zip(["launches", "keyswitch", "pmult", "hrot", "hmult", "rescale"], [int(x) for x in a]))
+
+
+def ckks_ctx_reset_counters(ctx):
+    ctx.check(lib().ckks_ctx_reset_counters(ctx))
+
+
+def ckks_ctx_kernel_stats(ctx):
+    import json
+    n = ctypes.c_int()
+    ctx.check(lib().ckks_ctx_kernel_stats(ctx, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    ctx.check(lib().ckks_ctx_kernel_stats(ctx, buf, n.value + 1, ctypes.byref(n)))
+    return {k: dict(launches=int(v[0]), ms=float(v[1]), bytes=float(v[2]))
+            for k, v in json.loads(buf.value.decode()).items()}
+
+
+# ---------------------------------------------------------------- keys ------
+def ckks_keygen(ctx, rot_steps=(), want_conj=True) -> Keys:
+    st = np.ascontiguousarray(list(rot_steps), dtype=np.int32)
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_keygen(ctx, _ptr(st) if len(st) else None, len(st), int(want_conj), ctypes.byref(out)))
+    return Keys(out.value, ctx)
+
+
+def ckks_keys_add_rotations(ctx, keys, rot_steps):
+    st = np.ascontiguousarray(list(rot_steps), dtype=np.int32)
+    if len(st):
+        ctx.check(lib().ckks_keys_add_rotations(ctx, keys, _ptr(st), len(st)))
+
+
+def ckks_keys_export_secret(ctx, keys):
+    s = np.zeros(ctx.n, dtype=np.int64)
+    ctx.check(lib().ckks_keys_export_secret(ctx, keys, _ptr(s)))
+    return s
+
+
+# ------------------------------------------------------------- handles ------
+def ckks_ct_create(ctx) -> Ciphertext:
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_ct_create(ctx, ctypes.byref(out)))
+    return Ciphertext(out.value, ctx)
+
+
+def ckks_ct_info(ct):
+    lev, sc = ctypes.c_int(), ctypes.c_double()
+    lib().ckks_ct_info(ct, ctypes.byref(lev), ctypes.byref(sc))
+    return lev.value, sc.value
+
+
+def ckks_ct_set_scale(ct, scale):
+    lib().ckks_ct_set_scale(ct, scale)
+
+
+def ckks_ct_import_rns(ctx, limbs, level, scale, out=None):
+    out = out or ckks_ct_create(ctx)
+    a = _u64(limbs)
+    assert a.size == 2 * (level + 1) * ctx.n
+    ctx.check(lib().ckks_ct_import_rns(ctx, _ptr(a), level, scale, out))
+    return out
+
+
+def ckks_ct_export_rns(ctx, ct):
+    lev, _ = ckks_ct_info(ct)
+    a = np.zeros((2, lev + 1, ctx.n), dtype=np.uint64)
+    ctx.check(lib().ckks_ct_export_rns(ctx, ct, _ptr(a)))
+    return a
+
+
+def ckks_pt_create(ctx) -> Plaintext:
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_pt_create(ctx, ctypes.byref(out)))
+    return Plaintext(out.value, ctx)
+
+
+def ckks_pt_info(pt):
+    lev, sc = ctypes.c_int(), ctypes.c_double()
+    lib().ckks_pt_info(pt, ctypes.byref(lev), ctypes.byref(sc))
+    return lev.value, sc.value
+
+
+def ckks_pt_import_rns(ctx, limbs, level, scale, out=None):
+    out = out or ckks_pt_create(ctx)
+    a = _u64(limbs)
+    assert a.size == (level + 1) * ctx.n
+    ctx.check(lib().ckks_pt_import_rns(ctx, _ptr(a), level, scale, out))
+    return out
+
+
+def ckks_pt_export_rns(ctx, pt):
+    lev, _ = ckks_pt_info(pt)
+    a = np.zeros((lev + 1, ctx.n), dtype=np.uint64)
+    ctx.check(lib().ckks_pt_export_rns(ctx, pt, _ptr(a)))
+    return a
+
+
+# ------------------------------------------------------------- encoding -----
+def ckks_encode(ctx, values, level, scale, kind=CKKS_SLOT, slice_len=0, out=None):
+    out = out or ckks_pt_create(ctx)
+    v = np.asarray(values)
+    re = _f64(v.real)
+    im = _f64(v.imag) if np.iscomplexobj(v) else None
+    ctx.check(lib().ckks_encode(ctx, _ptr(re), _ptr(im), len(re), level, scale, kind, slice_len, out))
+    return out
+
+
+def ckks_decode(ctx, pt, kind=CKKS_SLOT, slice_len=0, n=None):
+    if n is None:
+        n = ctx.n // 2 if kind == CKKS_SLOT else ctx.n
+    re = np.zeros(n, dtype=np.float64)
+    im = np.zeros(n, dtype=np.float64)
+    ctx.check(lib().ckks_decode(ctx, pt, kind, slice_len, _ptr(re), _ptr(im), n))
+    return re + 1j * im if kind == CKKS_SLOT else re
+
+
+def ckks_encode_image(ctx, img, w, level, scale, out=None):
+    """img: (c, w0, w0) -> real-CinS plaintext, channel i in slice i of a w x w padded image"""
+    a = _f64(img)
+    c, w0 = a.shape[0], a.shape[1]
+    out = out or ckks_pt_create(ctx)
+    ctx.check(lib().ckks_encode_image(ctx, _ptr(a), c, w0, w, level, scale, out))
+    return out
+
+
+def ckks_decode_image(ctx, pt, c, w0, w, from_coeff=False):
+    out = np.zeros((c, w0, w0), dtype=np.float64)
+    ctx.check(lib().ckks_decode_image(ctx, pt, int(from_coeff), c, w0, w, _ptr(out)))
+    return out
+
+
+# ----------------------------------------------------------- encryption -----
+def ckks_encrypt(ctx, keys, pt, nonce, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_encrypt(ctx, keys, pt, nonce, out))
+    return out
+
+
+def ckks_encrypt_sk(ctx, keys, pt, nonce, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_encrypt_sk(ctx, keys, pt, nonce, out))
+    return out
+
+
+def ckks_decrypt(ctx, keys, ct, out=None):
+    out = out or ckks_pt_create(ctx)
+    ctx.check(lib().ckks_decrypt(ctx, keys, ct, out))
+    return out
+
+
+# -------------------------------------------------------------- HE ops ------
+def _unary(name):
+    def f(ctx, ct, out=None):
+        out = out or ckks_ct_create(ctx)
+        ctx.check(getattr(lib(), name)(ctx, ct, out))
+        return out
+    f.__name__ = name
+    return f
+
+
+def _binary(name):
+    def f(ctx, a, b, out=None):
+        out = out or ckks_ct_create(ctx)
+        ctx.check(getattr(lib(), name)(ctx, a, b, out))
+        return out
+    f.__name__ = name
+    return f
+
+
+ckks_add = _binary("ckks_add")
+ckks_sub = _binary("ckks_sub")
+ckks_mul_plain = _binary("ckks_mul_plain")
+ckks_imult = _unary("ckks_imult")
+ckks_rescale = _unary("ckks_rescale")
+ckks_mod_raise = _unary("ckks_mod_raise")
+
+
+def ckks_mul_relin(ctx, keys, a, b, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_mul_relin(ctx, keys, a, b, out))
+    return out
+
+
+def ckks_mul_int(ctx, ct, c, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_mul_int(ctx, ct, int(c), out))
+    return out
+
+
+def ckks_add_const(ctx, ct, c, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_add_const(ctx, ct, float(c), out))
+    return out
+
+
+def ckks_mod_drop(ctx, ct, level, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_mod_drop(ctx, ct, level, out))
+    return out
+
+
+def ckks_level_down(ctx, ct, level, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_level_down(ctx, ct, level, out))
+    return out
+
+
+def ckks_rotate_hoisted(ctx, keys, ct, steps, outs=None):
+    st = np.ascontiguousarray(list(steps), dtype=np.int32)
+    outs = outs or [ckks_ct_create(ctx) for _ in st]
+    arr = (ctypes.c_void_p * len(outs))(*[o.ptr for o in outs])
+    ctx.check(lib().ckks_rotate_hoisted(ctx, keys, ct, _ptr(st), len(st), ctypes.cast(arr, ctypes.c_void_p)))
+    return outs
+
+
+def ckks_conjugate(ctx, keys, ct, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_conjugate(ctx, keys, ct, out))
+    return out
+
+
+# ----------------------------------------------------------------- BSGS -----
+def ckks_ptset_create(ctx, a0, step, count, bsgs_B, level, scale) -> PtSet:
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_ptset_create(ctx, a0, step, count, bsgs_B, level, scale, ctypes.byref(out)))
+    return PtSet(out.value, ctx)
+
+
+def ckks_ptset_set_rns(ctx, ps, g, b, limbs):
+    a = _u64(limbs)
+    ctx.check(lib().ckks_ptset_set_rns(ctx, ps, g, b, _ptr(a)))
+
+
+def ckks_ptset_info(ps):
+    vals = [ctypes.c_int() for _ in range(5)]
+    sc = ctypes.c_double()
+    npts = ctypes.c_int()
+    lib().ckks_ptset_info(ps, *[ctypes.byref(v) for v in vals], ctypes.byref(sc), ctypes.byref(npts))
+    a0, step, count, B, level = [v.value for v in vals]
+    return dict(a0=a0, step=step, count=count, B=B, level=level, scale=sc.value, n_pts=npts.value)
+
+
+def ckks_ptset_rotations(ps):
+    n = ctypes.c_int()
+    lib().ckks_ptset_rotations(ps, None, 0, ctypes.byref(n))
+    a = np.zeros(max(n.value, 1), dtype=np.int32)
+    lib().ckks_ptset_rotations(ps, _ptr(a), n.value, ctypes.byref(n))
+    return [int(x) for x in a[: n.value]]
+
+
+def ckks_bsgs(ctx, keys, ct, ps, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_bsgs(ctx, keys, ct, ps, out))
+    return out
+
+
+def ckks_ptset_conv_fused(ctx, weights, cin, cout, f, w, level, pt_scale, bsgs_B=0) -> PtSet:
+    W = _f64(weights)
+    assert W.size == cout * cin * f * f
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_ptset_conv_fused(ctx, _ptr(W), cin, cout, f, w, level, pt_scale, bsgs_B,
+                                          ctypes.byref(out)))
+    return PtSet(out.value, ctx)
+
+
+def ckks_conv2d_cins(ctx, keys, ct, conv, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_conv2d_cins(ctx, keys, ct, conv, out))
+    return out
+
+
+# -------------------------------------------------------- bootstrapping -----
+def ckks_boot_create(ctx, w, w0, cout, K=28, r=3, deg=59, ctos_levels=3, stoc_levels=3, delta0=2.0 ** 49) -> Boot:
+    bp = ckks_boot_params(w=w, w0=w0, cout=cout, K=K, r=r, deg=deg, ctos_levels=ctos_levels,
+                          stoc_levels=stoc_levels, delta0=delta0)
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_boot_create(ctx, ctypes.byref(bp), ctypes.byref(out)))
+    return Boot(out.value, ctx)
+
+
+def ckks_boot_info(bt):
+    a = np.zeros(8, dtype=np.float64)
+    lib().ckks_boot_info(bt, _ptr(a))
+    keys = ["K_eff", "s_raise", "c_drop", "l_drop", "l_em", "l_out", "s_em", "s_mask"]
+    return dict(zip(keys, [float(x) for x in a]))
+
+
+def ckks_boot_rotations(bt):
+    n = ctypes.c_int()
+    lib().ckks_boot_rotations(bt, None, 0, ctypes.byref(n))
+    a = np.zeros(max(n.value, 1), dtype=np.int32)
+    lib().ckks_boot_rotations(bt, _ptr(a), n.value, ctypes.byref(n))
+    return [int(x) for x in a[: n.value]]
+
+
+def ckks_boot_set_ctos(ctx, bt, i, ps):
+    ctx.check(lib().ckks_boot_set_ctos(ctx, bt, i, ps))
+
+
+def ckks_boot_set_stoc(ctx, bt, i, ps):
+    ctx.check(lib().ckks_boot_set_stoc(ctx, bt, i, ps))
+
+
+def ckks_boot_set_coeffs(ctx, bt, coeffs):
+    c = _f64(coeffs)
+    ctx.check(lib().ckks_boot_set_coeffs(ctx, bt, _ptr(c), len(c) - 1))
+
+
+def ckks_boot_set_masks(ctx, bt, re, im):
+    ctx.check(lib().ckks_boot_set_masks(ctx, bt, re, im))
+
+
+def ckks_bootstrap(ctx, keys, bt, ct0, out_re=None, out_im=None):
+    out_re = out_re or ckks_ct_create(ctx)
+    out_im = out_im or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_bootstrap(ctx, keys, bt, ct0, out_re, out_im))
+    return out_re, out_im
+
+
+def ckks_stoc1(ctx, keys, re, im, bt, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_stoc1(ctx, keys, re, im, bt, out))
+    return out
+
+
+def ckks_block(ctx, keys, ct, conv, bt, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_block(ctx, keys, ct, conv, bt, out))
+    return out
+
+
+def ckks_eval_poly(ctx, keys, ct, coeffs, basis=CKKS_BASIS_CHEB, a=-1.0, b=1.0, out=None):
+    out = out or ckks_ct_create(ctx)
+    c = _f64(coeffs)
+    ctx.check(lib().ckks_eval_poly(ctx, keys, ct, _ptr(c), len(c) - 1, basis, a, b, out))
+    return out
+
+
+# ------------------------------------------------------------- raw NTT ------
+def ckks_ntt_forward(ctx, dev_ptr, n_limbs, prime_ids):
+    ids = np.ascontiguousarray(prime_ids, dtype=np.int32)
+    ctx.check(lib().ckks_ntt_forward(ctx, ctypes.c_void_p(dev_ptr), n_limbs, _ptr(ids)))
+
+
+def ckks_ntt_inverse(ctx, dev_ptr, n_limbs, prime_ids):
+    ids = np.ascontiguousarray(prime_ids, dtype=np.int32)
+    ctx.check(lib().ckks_ntt_inverse(ctx, ctypes.c_void_p(dev_ptr), n_limbs, _ptr(ids)))

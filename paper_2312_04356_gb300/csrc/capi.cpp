@@ -1,0 +1,1023 @@
+// extern "C" entry points (include/ckks.h).  Each call catches every C++ error and
+// returns a status code; ckks_last_error(ctx) keeps the message.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <set>
+
+#include "internal.h"
+#include "scheme_ops.h"
+
+using namespace hostmath;
+
+namespace {
+
+template <class F>
+int guard(const ckks_ctx* c, F&& f) {
+    try {
+        f();
+        return CKKS_OK;
+    } catch (const CkksError& e) {
+        if (c) const_cast<ckks_ctx*>(c)->err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) const_cast<ckks_ctx*>(c)->err = "host allocation failed";
+        return CKKS_ENOMEM;
+    } catch (const std::exception& e) {
+        if (c) const_cast<ckks_ctx*>(c)->err = e.what();
+        return CKKS_EINVAL;
+    }
+}
+
+#define REQ(p) CK_CHECK((p) != nullptr, CKKS_EINVAL, #p " is NULL")
+
+void upload_coeffs(ckks_ctx* c, const std::vector<int64_t>& v, int level, double scale, ckks_pt* out) {
+    const size_t n = c->n;
+    DevBuf sm(n, c->stream);
+    CUDA_CHECK(cudaMemcpyAsync(sm.ptr, v.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
+    out->ctx = c;
+    out->buf = DevBuf((size_t)(level + 1) * n, c->stream);
+    out->level = level;
+    out->scale = scale;
+    kern::small_to_rns(c, (const int64_t*)sm.ptr, out->buf.ptr, level + 1, c->d_iota);
+    kern::ntt_forward(c, out->buf.ptr, level + 1, c->d_iota, level + 1);
+}
+
+std::vector<int64_t> round_coeffs(const std::vector<double>& f, double scale) {
+    std::vector<int64_t> v(f.size());
+    for (size_t k = 0; k < f.size(); ++k) {
+        double x = f[k] * scale;
+        CK_CHECK(fabs(x) < ldexp(1.0, 62), CKKS_EINVAL, "encoded coefficient exceeds 2^62");
+        v[k] = llround_away(x);
+    }
+    return v;
+}
+
+void encode_complex(ckks_ctx* c, const std::vector<cplx>& z, int level, double scale, ckks_pt* out) {
+    CK_CHECK(level >= 0 && level <= c->L, CKKS_EINVAL, "level out of range");
+    std::vector<cplx> zz(z);
+    zz.resize(c->n / 2, cplx(0, 0));
+    upload_coeffs(c, round_coeffs(fp64::encode_slots(zz, c->n), scale), level, scale, out);
+}
+
+// limbs (host, coefficient domain, [nl][N]) -> centred values / scale, by Garner's mixed radix
+std::vector<double> crt_centred(const ckks_ctx* c, const std::vector<u64>& limbs, int nl) {
+    const size_t n = c->n;
+    std::vector<double> out(n);
+    // inverse of prod_{k<i} q_k mod q_i
+    std::vector<u64> pinv(nl);
+    for (int i = 0; i < nl; ++i) {
+        u64 pr = 1;
+        for (int k = 0; k < i; ++k) pr = mulmod(pr, c->q[k] % c->q[i], c->q[i]);
+        pinv[i] = i ? invmod(pr, c->q[i]) : 1;
+    }
+    std::vector<u64> v(nl);
+    for (size_t j = 0; j < n; ++j) {
+        bool neg = false;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = 0; i < nl; ++i) {
+                u64 qi = c->q[i];
+                u64 r = limbs[(size_t)i * n + j];
+                if (neg) r = r ? qi - r : 0;
+                // v_i = (r - sum_{t<i} v_t prod_{k<t} q_k) * (prod_{k<i} q_k)^{-1} mod q_i
+                u64 acc = 0, pr = 1;
+                for (int t = 0; t < i; ++t) {
+                    acc = (acc + mulmod(v[t] % qi, pr, qi)) % qi;
+                    pr = mulmod(pr, c->q[t] % qi, qi);
+                }
+                u64 diff = r >= acc ? r - acc : r + qi - acc;
+                v[i] = mulmod(diff, pinv[i], qi);
+            }
+            if (pass == 0 && v[nl - 1] > (c->q[nl - 1] - 1) / 2) {
+                neg = true;
+                continue;
+            }
+            break;
+        }
+        double x = 0.0;
+        for (int i = nl - 1; i >= 0; --i) x = x * (double)c->q[i] + (double)v[i];
+        out[j] = neg ? -x : x;
+    }
+    return out;
+}
+
+std::vector<u64> download(ckks_ctx* c, const u64* dev, size_t words) {
+    std::vector<u64> h(words);
+    CUDA_CHECK(cudaMemcpyAsync(h.data(), dev, words * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    return h;
+}
+
+ckks_ptset* make_plan(ckks_ctx* c, const fp64::Diag& D, int a0, int step, int count, int level, double scale,
+                      int B) {
+    const int m = c->n / 2;
+    std::unique_ptr<ckks_ptset> ps(new ckks_ptset());
+    ps->ctx = c;
+    ps->a0 = ((a0 % m) + m) % m;
+    ps->step = step;
+    ps->count = count;
+    ps->B = B > 0 ? B : fp64::default_bsgs_B(count);
+    ps->level = level;
+    ps->scale = scale;
+    for (int g = 0; g < ps->G(); ++g) {
+        const long long R = ((long long)ps->a0 + (long long)step * g * ps->B) % m;
+        for (int b = 0; b < ps->B; ++b) {
+            const int i = g * ps->B + b;
+            if (i >= count) break;
+            const int off = (int)(((long long)ps->a0 + (long long)step * i) % m);
+            auto it = D.find(off);
+            if (it == D.end()) continue;
+            std::vector<cplx> v(m);
+            for (int t = 0; t < m; ++t) v[t] = it->second[((t - R) % m + m) % m];
+            auto pt = std::make_unique<ckks_pt>();
+            encode_complex(c, v, level, scale, pt.get());
+            ps->pts[std::make_pair(g, b)] = std::move(pt);
+        }
+    }
+    return ps.release();
+}
+
+void assign(ckks_ct* out, ckks_ct&& v) {
+    ckks_ctx* c = v.ctx;
+    *out = std::move(v);
+    out->ctx = c;
+}
+
+}  // namespace
+
+extern "C" {
+
+// ------------------------------------------------------------- context ------
+int ckks_ctx_create(const ckks_params* params, uint64_t seed, void* stream, ckks_ctx** out) {
+    if (!params || !out) return CKKS_EINVAL;
+    try {
+        *out = ctx_create(params, seed, (cudaStream_t)stream);
+        return CKKS_OK;
+    } catch (const CkksError& e) {
+        fprintf(stderr, "ckks_ctx_create: %s\n", e.msg.c_str());
+        return e.code;
+    } catch (...) {
+        return CKKS_EINVAL;
+    }
+}
+
+int ckks_ctx_destroy(ckks_ctx* ctx) {
+    delete ctx;
+    return CKKS_OK;
+}
+
+const char* ckks_last_error(const ckks_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int ckks_sync(ckks_ctx* ctx) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        CUDA_CHECK(cudaGetLastError());
+    });
+}
+
+int ckks_ctx_info(const ckks_ctx* ctx, uint64_t* q, uint64_t* p, uint64_t* psi, double* delta) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        if (q) std::copy(ctx->q.begin(), ctx->q.end(), q);
+        if (p) std::copy(ctx->p.begin(), ctx->p.end(), p);
+        if (psi) std::copy(ctx->psi.begin(), ctx->psi.end(), psi);
+        if (delta) std::copy(ctx->delta.begin(), ctx->delta.end(), delta);
+    });
+}
+
+int ckks_ctx_gauss_table(const ckks_ctx* ctx, uint64_t* t) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(t);
+        std::copy(ctx->gauss, ctx->gauss + 39, t);
+    });
+}
+
+// ---------------------------------------------------------- measurement -----
+int ckks_ctx_set_timing(ckks_ctx* ctx, int on) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        if (!on) ctx->collect_timing();
+        ctx->timing = on != 0;
+    });
+}
+
+int ckks_ctx_counters(const ckks_ctx* ctx, int64_t* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(out);
+        auto get = [&](const char* k) {
+            auto it = ctx->ops.find(k);
+            return it == ctx->ops.end() ? 0L : it->second;
+        };
+        out[0] = ctx->launches;
+        out[1] = get("keyswitch");
+        out[2] = get("pmult");
+        out[3] = get("hrot");
+        out[4] = get("hmult");
+        out[5] = get("rescale");
+    });
+}
+
+int ckks_ctx_reset_counters(ckks_ctx* ctx) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        ctx->collect_timing();
+        ctx->ops.clear();
+        ctx->launches = 0;
+        ctx->kstats.clear();
+    });
+}
+
+int ckks_ctx_kernel_stats(ckks_ctx* ctx, char* buf, int cap, int* len) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        ctx->collect_timing();
+        std::string js = "{";
+        bool first = true;
+        for (const auto& kv : ctx->kstats) {
+            char tmp[256];
+            snprintf(tmp, sizeof(tmp), "%s\"%s\": [%lld, %.6f, %.1f]", first ? "" : ", ", kv.first.c_str(),
+                     kv.second.launches, kv.second.ms, kv.second.bytes);
+            js += tmp;
+            first = false;
+        }
+        js += "}";
+        if (len) *len = (int)js.size();
+        if (buf && cap > 0) {
+            int k = std::min((int)js.size(), cap - 1);
+            memcpy(buf, js.data(), k);
+            buf[k] = 0;
+        }
+    });
+}
+
+// ---------------------------------------------------------------- keys ------
+int ckks_keygen(ckks_ctx* ctx, const int32_t* steps, int n, int want_conj, ckks_keys** out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(out);
+        CK_CHECK(n == 0 || steps, CKKS_EINVAL, "rot_steps is NULL");
+        *out = ops::keygen(ctx, steps, n, want_conj);
+    });
+}
+
+int ckks_keys_add_rotations(ckks_ctx* ctx, ckks_keys* keys, const int32_t* steps, int n) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(keys);
+        for (int i = 0; i < n; ++i) ops::add_galois_key(ctx, *keys, ops::galois_of_step(ctx, steps[i]));
+    });
+}
+
+int ckks_keys_destroy(ckks_keys* keys) {
+    delete keys;
+    return CKKS_OK;
+}
+
+int ckks_keys_export_secret(ckks_ctx* ctx, const ckks_keys* keys, int64_t* s) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        REQ(s);
+        std::copy(keys->s.begin(), keys->s.end(), s);
+    });
+}
+
+// -------------------------------------------------------------- handles -----
+int ckks_ct_create(ckks_ctx* ctx, ckks_ct** out) {
+    if (!ctx || !out) return CKKS_EINVAL;
+    *out = new ckks_ct();
+    (*out)->ctx = ctx;
+    return CKKS_OK;
+}
+int ckks_ct_destroy(ckks_ct* ct) {
+    delete ct;
+    return CKKS_OK;
+}
+int ckks_ct_info(const ckks_ct* ct, int* level, double* scale) {
+    if (!ct) return CKKS_EINVAL;
+    if (level) *level = ct->level;
+    if (scale) *scale = ct->scale;
+    return CKKS_OK;
+}
+int ckks_ct_set_scale(ckks_ct* ct, double scale) {
+    if (!ct) return CKKS_EINVAL;
+    ct->scale = scale;
+    return CKKS_OK;
+}
+
+int ckks_ct_import_rns(ckks_ctx* ctx, const uint64_t* host, int level, double scale, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(host);
+        REQ(out);
+        CK_CHECK(level >= 0 && level <= ctx->L, CKKS_EINVAL, "level out of range");
+        ckks_ct o = ops::new_ct(ctx, level, scale);
+        const size_t words = 2 * (size_t)(level + 1) * ctx->n;
+        CUDA_CHECK(cudaMemcpyAsync(o.buf.ptr, host, words * 8, cudaMemcpyHostToDevice, ctx->stream));
+        kern::ntt_forward(ctx, o.buf.ptr, 2 * (level + 1), ctx->d_iota, level + 1);
+        assign(out, std::move(o));
+    });
+}
+
+int ckks_ct_export_rns(ckks_ctx* ctx, const ckks_ct* ct, uint64_t* host) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(ct);
+        REQ(host);
+        CK_CHECK(ct->level >= 0, CKKS_EINVAL, "empty ciphertext");
+        const size_t words = 2 * (size_t)(ct->level + 1) * ctx->n;
+        DevBuf t(words, ctx->stream);
+        CUDA_CHECK(cudaMemcpyAsync(t.ptr, ct->buf.ptr, words * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        kern::ntt_inverse(ctx, t.ptr, 2 * (ct->level + 1), ctx->d_iota, ct->level + 1);
+        CUDA_CHECK(cudaMemcpyAsync(host, t.ptr, words * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+int ckks_pt_create(ckks_ctx* ctx, ckks_pt** out) {
+    if (!ctx || !out) return CKKS_EINVAL;
+    *out = new ckks_pt();
+    (*out)->ctx = ctx;
+    return CKKS_OK;
+}
+int ckks_pt_destroy(ckks_pt* pt) {
+    delete pt;
+    return CKKS_OK;
+}
+int ckks_pt_info(const ckks_pt* pt, int* level, double* scale) {
+    if (!pt) return CKKS_EINVAL;
+    if (level) *level = pt->level;
+    if (scale) *scale = pt->scale;
+    return CKKS_OK;
+}
+
+int ckks_pt_import_rns(ckks_ctx* ctx, const uint64_t* host, int level, double scale, ckks_pt* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(host);
+        REQ(out);
+        CK_CHECK(level >= 0 && level <= ctx->L, CKKS_EINVAL, "level out of range");
+        const size_t words = (size_t)(level + 1) * ctx->n;
+        DevBuf b(words, ctx->stream);
+        CUDA_CHECK(cudaMemcpyAsync(b.ptr, host, words * 8, cudaMemcpyHostToDevice, ctx->stream));
+        kern::ntt_forward(ctx, b.ptr, level + 1, ctx->d_iota, level + 1);
+        out->ctx = ctx;
+        out->buf = std::move(b);
+        out->level = level;
+        out->scale = scale;
+    });
+}
+
+int ckks_pt_export_rns(ckks_ctx* ctx, const ckks_pt* pt, uint64_t* host) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(pt);
+        REQ(host);
+        const size_t words = (size_t)(pt->level + 1) * ctx->n;
+        DevBuf t(words, ctx->stream);
+        CUDA_CHECK(cudaMemcpyAsync(t.ptr, pt->buf.ptr, words * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        kern::ntt_inverse(ctx, t.ptr, pt->level + 1, ctx->d_iota, pt->level + 1);
+        CUDA_CHECK(cudaMemcpyAsync(host, t.ptr, words * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+// ------------------------------------------------------------- encoding -----
+int ckks_encode(ckks_ctx* ctx, const double* re, const double* im, int n, int level, double scale, int kind,
+                int slice_len, ckks_pt* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(re);
+        REQ(out);
+        const int N = ctx->n;
+        if (kind == CKKS_SLOT) {
+            CK_CHECK(n >= 0 && n <= N / 2, CKKS_EINVAL, "too many slots");
+            std::vector<cplx> z(N / 2, cplx(0, 0));
+            for (int j = 0; j < n; ++j) z[j] = cplx(re[j], im ? im[j] : 0.0);
+            encode_complex(ctx, z, level, scale, out);
+        } else if (kind == CKKS_COEFF) {
+            CK_CHECK(n >= 0 && n <= N, CKKS_EINVAL, "too many coefficients");
+            std::vector<double> f(N, 0.0);
+            for (int j = 0; j < n; ++j) f[j] = re[j];
+            CK_CHECK(level >= 0 && level <= ctx->L, CKKS_EINVAL, "level out of range");
+            upload_coeffs(ctx, round_coeffs(f, scale), level, scale, out);
+        } else if (kind == CKKS_CINS_REAL) {
+            CK_CHECK(slice_len >= 2 && (slice_len & (slice_len - 1)) == 0 && slice_len <= N, CKKS_EINVAL,
+                     "slice_len must be a power of two in [2, N]");
+            const int C = N / slice_len;
+            CK_CHECK(n >= 0 && n <= N, CKKS_EINVAL, "too many values");
+            std::vector<double> m(N, 0.0);
+            for (int j = 0; j < n; ++j) m[j] = re[j];
+            encode_complex(ctx, fp64::real_cins_slots(m.data(), C, slice_len), level, scale, out);
+        } else {
+            CK_THROW(CKKS_EINVAL, "unknown encoding kind");
+        }
+    });
+}
+
+int ckks_decode(ckks_ctx* ctx, const ckks_pt* pt, int kind, int slice_len, double* re, double* im, int n) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(pt);
+        REQ(re);
+        const int N = ctx->n;
+        const int nl = pt->level + 1;
+        DevBuf t((size_t)nl * N, ctx->stream);
+        CUDA_CHECK(cudaMemcpyAsync(t.ptr, pt->buf.ptr, (size_t)nl * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        kern::ntt_inverse(ctx, t.ptr, nl, ctx->d_iota, nl);
+        std::vector<u64> h = download(ctx, t.ptr, (size_t)nl * N);
+        std::vector<double> f = crt_centred(ctx, h, nl);
+        for (double& x : f) x /= pt->scale;
+        if (kind == CKKS_COEFF) {
+            CK_CHECK(n <= N, CKKS_EINVAL, "n above N");
+            for (int j = 0; j < n; ++j) re[j] = f[j];
+        } else if (kind == CKKS_SLOT) {
+            CK_CHECK(n <= N / 2, CKKS_EINVAL, "n above N/2");
+            std::vector<cplx> z = fp64::decode_slots(f, N);
+            for (int j = 0; j < n; ++j) {
+                re[j] = z[j].real();
+                if (im) im[j] = z[j].imag();
+            }
+        } else if (kind == CKKS_CINS_REAL) {
+            CK_CHECK(slice_len >= 2 && (slice_len & (slice_len - 1)) == 0 && slice_len <= N, CKKS_EINVAL,
+                     "bad slice_len");
+            std::vector<double> m = fp64::cins_to_reals(fp64::decode_slots(f, N), N / slice_len, slice_len);
+            for (int j = 0; j < n && j < N; ++j) re[j] = m[j];
+        } else {
+            CK_THROW(CKKS_EINVAL, "unknown encoding kind");
+        }
+    });
+}
+
+int ckks_encode_image(ckks_ctx* ctx, const double* img, int c, int w0, int w, int level, double scale,
+                      ckks_pt* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(img);
+        REQ(out);
+        const int N = ctx->n;
+        CK_CHECK(w >= 2 && (w & (w - 1)) == 0 && w * w <= N && w0 >= 1 && w0 <= w, CKKS_EINVAL, "bad w / w0");
+        const int two_l = w * w, C = N / two_l;
+        CK_CHECK(c >= 1 && c <= C, CKKS_EINVAL, "channels do not fit in one ciphertext");
+        std::vector<double> m(N, 0.0);
+        for (int i = 0; i < c; ++i)
+            for (int r = 0; r < w0; ++r)
+                for (int col = 0; col < w0; ++col)
+                    m[(size_t)i * two_l + r * w + col] = img[((size_t)i * w0 + r) * w0 + col];
+        encode_complex(ctx, fp64::real_cins_slots(m.data(), C, two_l), level, scale, out);
+    });
+}
+
+int ckks_decode_image(ckks_ctx* ctx, const ckks_pt* pt, int from_coeff, int c, int w0, int w, double* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(pt);
+        REQ(out);
+        const int N = ctx->n;
+        CK_CHECK(w >= 2 && (w & (w - 1)) == 0 && w * w <= N && w0 >= 1 && w0 <= w, CKKS_EINVAL, "bad w / w0");
+        const int two_l = w * w, C = N / two_l;
+        CK_CHECK(c >= 1 && c <= C, CKKS_EINVAL, "channels do not fit in one ciphertext");
+        const int nl = pt->level + 1;
+        DevBuf t((size_t)nl * N, ctx->stream);
+        CUDA_CHECK(cudaMemcpyAsync(t.ptr, pt->buf.ptr, (size_t)nl * N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        kern::ntt_inverse(ctx, t.ptr, nl, ctx->d_iota, nl);
+        std::vector<double> f = crt_centred(ctx, download(ctx, t.ptr, (size_t)nl * N), nl);
+        for (double& x : f) x /= pt->scale;
+        int cbits = 0;
+        while ((1 << cbits) < C) ++cbits;
+        std::vector<double> m;
+        if (!from_coeff) m = fp64::cins_to_reals(fp64::decode_slots(f, N), C, two_l);
+        for (int i = 0; i < c; ++i) {
+            unsigned rv = 0, x = (unsigned)i;
+            for (int b = 0; b < cbits; ++b) {
+                rv = (rv << 1) | (x & 1);
+                x >>= 1;
+            }
+            for (int r = 0; r < w0; ++r)
+                for (int col = 0; col < w0; ++col) {
+                    const int k = r * w + col;
+                    out[((size_t)i * w0 + r) * w0 + col] =
+                        from_coeff ? f[(size_t)k * C + rv] : m[(size_t)i * two_l + k];
+                }
+        }
+    });
+}
+
+// ----------------------------------------------------------- encryption -----
+int ckks_encrypt(ckks_ctx* ctx, const ckks_keys* keys, const ckks_pt* pt, uint64_t nonce, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        REQ(pt);
+        REQ(out);
+        CK_CHECK(pt->level >= 0, CKKS_EINVAL, "empty plaintext");
+        assign(out, ops::encrypt(*keys, *pt, nonce));
+    });
+}
+int ckks_encrypt_sk(ckks_ctx* ctx, const ckks_keys* keys, const ckks_pt* pt, uint64_t nonce, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        REQ(pt);
+        REQ(out);
+        CK_CHECK(pt->level >= 0, CKKS_EINVAL, "empty plaintext");
+        assign(out, ops::encrypt_sk(*keys, *pt, nonce));
+    });
+}
+int ckks_decrypt(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, ckks_pt* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        REQ(ct);
+        REQ(out);
+        ops::decrypt(*keys, *ct, *out);
+    });
+}
+
+// -------------------------------------------------------------- HE ops ------
+#define CT_OK(x) CK_CHECK((x) && (x)->level >= 0, CKKS_EINVAL, #x " is NULL or empty")
+
+int ckks_add(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(a);
+        CT_OK(b);
+        REQ(out);
+        assign(out, ops::add(*a, *b));
+    });
+}
+int ckks_sub(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(a);
+        CT_OK(b);
+        REQ(out);
+        assign(out, ops::sub(*a, *b));
+    });
+}
+int ckks_mul_plain(ckks_ctx* ctx, const ckks_ct* ct, const ckks_pt* pt, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(ct);
+        REQ(pt);
+        REQ(out);
+        assign(out, ops::mul_plain(*ct, *pt));
+    });
+}
+int ckks_mul_relin(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* a, const ckks_ct* b, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(a);
+        CT_OK(b);
+        REQ(out);
+        assign(out, ops::mul_relin(*keys, *a, *b));
+    });
+}
+int ckks_mul_int(ckks_ctx* ctx, const ckks_ct* ct, int64_t c, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(ct);
+        REQ(out);
+        assign(out, ops::mul_int(*ct, c));
+    });
+}
+int ckks_add_const(ckks_ctx* ctx, const ckks_ct* ct, double c, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(ct);
+        REQ(out);
+        assign(out, ops::add_const(*ct, c));
+    });
+}
+int ckks_imult(ckks_ctx* ctx, const ckks_ct* ct, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(ct);
+        REQ(out);
+        assign(out, ops::imult(*ct));
+    });
+}
+int ckks_rescale(ckks_ctx* ctx, const ckks_ct* ct, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(ct);
+        REQ(out);
+        assign(out, ops::rescale(*ct));
+    });
+}
+int ckks_mod_drop(ckks_ctx* ctx, const ckks_ct* ct, int level, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(ct);
+        REQ(out);
+        assign(out, ops::mod_drop(*ct, level));
+    });
+}
+int ckks_level_down(ckks_ctx* ctx, const ckks_ct* ct, int level, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(ct);
+        REQ(out);
+        assign(out, ops::level_down(*ct, level));
+    });
+}
+int ckks_mod_raise(ckks_ctx* ctx, const ckks_ct* ct, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(ct);
+        REQ(out);
+        assign(out, ops::mod_raise(*ct));
+    });
+}
+int ckks_rotate_hoisted(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const int32_t* steps, int n,
+                        ckks_ct* const* outs) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(in);
+        CK_CHECK(n >= 0 && (n == 0 || (steps && outs)), CKKS_EINVAL, "bad steps/outs");
+        for (int i = 0; i < n; ++i) CK_CHECK(outs[i] && outs[i] != in, CKKS_EINVAL, "outs must not alias the input");
+        std::vector<long long> st(steps, steps + n);
+        std::vector<ckks_ct> r = ops::rotate_hoisted(*keys, *in, st);
+        for (int i = 0; i < n; ++i) assign(outs[i], std::move(r[i]));
+    });
+}
+int ckks_conjugate(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(ct);
+        REQ(out);
+        assign(out, ops::conjugate(*keys, *ct));
+    });
+}
+
+// ----------------------------------------------------------------- BSGS -----
+int ckks_ptset_create(ckks_ctx* ctx, int a0, int step, int count, int B, int level, double scale, ckks_ptset** out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(out);
+        CK_CHECK(step >= 1 && count >= 1 && level >= 0 && level <= ctx->L, CKKS_EINVAL, "bad plan parameters");
+        const int m = ctx->n / 2;
+        ckks_ptset* ps = new ckks_ptset();
+        ps->ctx = ctx;
+        ps->a0 = ((a0 % m) + m) % m;
+        ps->step = step;
+        ps->count = count;
+        ps->B = B > 0 ? B : fp64::default_bsgs_B(count);
+        ps->level = level;
+        ps->scale = scale;
+        *out = ps;
+    });
+}
+int ckks_ptset_destroy(ckks_ptset* ps) {
+    delete ps;
+    return CKKS_OK;
+}
+int ckks_ptset_set_rns(ckks_ctx* ctx, ckks_ptset* ps, int g, int b, const uint64_t* host) {
+    return guard(ctx, [&] {
+        REQ(ps);
+        REQ(host);
+        CK_CHECK(g >= 0 && g < ps->G() && b >= 0 && b < ps->B && g * ps->B + b < ps->count, CKKS_EINVAL,
+                 "(g, b) outside the plan");
+        auto pt = std::make_unique<ckks_pt>();
+        CK_CHECK(ckks_pt_import_rns(ctx, host, ps->level, ps->scale, pt.get()) == CKKS_OK, CKKS_EINVAL,
+                 "plaintext import failed");
+        ps->pts[std::make_pair(g, b)] = std::move(pt);
+    });
+}
+int ckks_ptset_info(const ckks_ptset* ps, int* a0, int* step, int* count, int* B, int* level, double* scale,
+                    int* n_pts) {
+    if (!ps) return CKKS_EINVAL;
+    if (a0) *a0 = ps->a0;
+    if (step) *step = ps->step;
+    if (count) *count = ps->count;
+    if (B) *B = ps->B;
+    if (level) *level = ps->level;
+    if (scale) *scale = ps->scale;
+    if (n_pts) *n_pts = (int)ps->pts.size();
+    return CKKS_OK;
+}
+
+static void plan_rotations(const ckks_ptset& ps, std::set<int>& out) {
+    const long long m = ps.ctx->n / 2;
+    for (const auto& kv : ps.pts) {
+        long long b = (long long)ps.step * kv.first.second % m;
+        if (b) out.insert((int)b);
+        long long R = ((long long)ps.a0 + (long long)ps.step * kv.first.first * ps.B) % m;
+        if (R) out.insert((int)R);
+    }
+}
+
+int ckks_ptset_rotations(const ckks_ptset* ps, int32_t* steps, int cap, int* n_out) {
+    if (!ps || !n_out) return CKKS_EINVAL;
+    std::set<int> s;
+    plan_rotations(*ps, s);
+    int i = 0;
+    for (int r : s) {
+        if (steps && i < cap) steps[i] = r;
+        ++i;
+    }
+    *n_out = i;
+    return CKKS_OK;
+}
+
+int ckks_bsgs(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, const ckks_ptset* ps, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(ct);
+        REQ(ps);
+        REQ(out);
+        assign(out, ops::bsgs(*keys, *ct, *ps));
+    });
+}
+
+int ckks_ptset_conv_fused(ckks_ctx* ctx, const double* W, int cin, int cout, int f, int w, int level,
+                          double pt_scale, int B, ckks_ptset** out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(W);
+        REQ(out);
+        CK_CHECK(w >= 2 && (w & (w - 1)) == 0 && w * w <= ctx->n, CKKS_EINVAL, "w must be a power of two, w^2 <= N");
+        CK_CHECK(f >= 1 && f % 2 == 1 && f <= w, CKKS_EINVAL, "kernel size must be odd and <= w");
+        CK_CHECK(level >= 1 && level <= ctx->L, CKKS_EINVAL, "the fused conv needs level >= 1");
+        const int two_l = w * w, ell = two_l / 2, C = ctx->n / two_l, m = ctx->n / 2;
+        std::vector<std::vector<cplx>> diags = fp64::fused_conv_diagonals(W, cin, cout, f, w, ctx->n);
+        fp64::Diag D;
+        for (int d = 0; d < C; ++d) {
+            double mx = 0;
+            for (const cplx& v : diags[d]) mx = std::max(mx, std::abs(v));
+            if (mx > 0) D[(int)(((long long)d * ell) % m)] = diags[d];
+        }
+        *out = make_plan(ctx, D, 0, ell, C, level, pt_scale, B);
+    });
+}
+
+int ckks_conv2d_cins(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(in);
+        REQ(conv);
+        REQ(out);
+        assign(out, ops::rescale(ops::bsgs(*keys, *in, *conv)));
+    });
+}
+
+// -------------------------------------------------------- bootstrapping -----
+int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(bp);
+        REQ(out);
+        CK_CHECK(bp->w >= 2 && (bp->w & (bp->w - 1)) == 0 && bp->w * bp->w <= ctx->n, CKKS_EINVAL, "bad w");
+        CK_CHECK(bp->K >= 1 && bp->r >= 0 && bp->deg >= 2 && bp->ctos_levels >= 1 && bp->stoc_levels >= 1,
+                 CKKS_EINVAL, "bad bootstrapping parameters");
+        std::unique_ptr<ckks_boot> bt(new ckks_boot());
+        bt->ctx = ctx;
+        bt->bp = *bp;
+        const int n = ctx->n, m = n / 2, L = ctx->L;
+        bt->two_l = bp->w * bp->w;
+        bt->ell = bt->two_l / 2;
+        bt->C = n / bt->two_l;
+        const double q0 = (double)ctx->q[0];
+        const int ld = L - bp->ctos_levels;
+        CK_CHECK(ld >= 2, CKKS_ELEVEL, "not enough levels for CtoS");
+        bt->l_drop = ld;
+        bt->c_drop = llround_away((ctx->delta[ld - 1] * (double)ctx->q[ld]) / (q0 * (double)bp->K));
+        CK_CHECK(bt->c_drop >= 1, CKKS_EINVAL, "scale-drop constant below 1");
+        bt->K_eff = (ctx->delta[ld - 1] * (double)ctx->q[ld]) / (q0 * (double)bt->c_drop);
+        bt->s_raise = q0 * bt->K_eff;
+        // CtoS = T^{-1}: stages N/4 ... 1, largest stride first
+        std::vector<int> stages;
+        for (int k = m / 2; k >= 1; k /= 2) stages.push_back(k);
+        std::vector<std::vector<int>> groups = fp64::split_groups(stages, bp->ctos_levels);
+        for (size_t i = 0; i < groups.size(); ++i) {
+            std::vector<int> rev(groups[i].rbegin(), groups[i].rend());
+            fp64::Diag D = fp64::s_product(rev, m, true);
+            if (i + 1 == groups.size())
+                for (auto& kv : D)
+                    for (cplx& v : kv.second) v *= 0.5;
+            int a0, step, count;
+            fp64::ap_of_group(groups[i], m, &a0, &step, &count);
+            const int lev = L - (int)i;
+            bt->ctos.emplace_back(make_plan(ctx, D, a0, step, count, lev, (double)ctx->q[lev], 0));
+        }
+        bt->coeffs = fp64::cheb_interp_cos(bt->K_eff, bp->r, bp->deg);
+        int depth = 0;
+        while ((1 << depth) < bp->deg) ++depth;
+        bt->l_em = (ld - 1) - (depth + 1) - bp->r;
+        CK_CHECK(bt->l_em - 1 - bp->stoc_levels >= 0, CKKS_ELEVEL, "not enough levels for the block");
+        const int le = bt->l_em;
+        bt->s_em = (ctx->delta[le + 1] * ctx->delta[le + 1]) / (double)ctx->q[le + 1];
+        bt->s_mask = (ctx->delta[le - 1] * (double)ctx->q[le]) / bt->s_em;
+        // padding masks times q0 / (2 pi delta0): slot i l + u carries pixel rev_l(u) (Re) or rev_l(u) + l (Im)
+        const double val = q0 / (2.0 * 3.14159265358979323846 * bp->delta0);
+        std::vector<cplx> mre(m, cplx(0, 0)), mim(m, cplx(0, 0));
+        int lbits = 0;
+        while ((1 << lbits) < bt->ell) ++lbits;
+        for (int i = 0; i < bp->cout && i < bt->C; ++i)
+            for (int u = 0; u < bt->ell; ++u) {
+                unsigned k = 0, x = u;
+                for (int b = 0; b < lbits; ++b) {
+                    k = (k << 1) | (x & 1);
+                    x >>= 1;
+                }
+                int p1 = (int)k, p2 = (int)k + bt->ell;
+                if (p1 / bp->w < bp->w0 && p1 % bp->w < bp->w0) mre[(size_t)i * bt->ell + u] = val;
+                if (p2 / bp->w < bp->w0 && p2 % bp->w < bp->w0) mim[(size_t)i * bt->ell + u] = val;
+            }
+        bt->mask_re = std::make_unique<ckks_pt>();
+        bt->mask_im = std::make_unique<ckks_pt>();
+        encode_complex(ctx, mre, le, bt->s_mask, bt->mask_re.get());
+        encode_complex(ctx, mim, le, bt->s_mask, bt->mask_im.get());
+        // StoC1 = S_{l <- 1}: stages 1, 2, ..., l/2, smallest stride first
+        std::vector<int> st;
+        for (int k = 1; k < bt->ell; k *= 2) st.push_back(k);
+        std::vector<std::vector<int>> sg = fp64::split_groups(st, bp->stoc_levels);
+        for (size_t i = 0; i < sg.size(); ++i) {
+            std::vector<int> rev(sg[i].rbegin(), sg[i].rend());
+            fp64::Diag D = fp64::s_product(rev, m, false);
+            int a0, step, count;
+            fp64::ap_of_group(sg[i], m, &a0, &step, &count);
+            const int lev = le - 1 - (int)i;
+            bt->stoc.emplace_back(make_plan(ctx, D, a0, step, count, lev, ctx->delta[lev], 0));
+        }
+        bt->l_out = le - 1 - (int)bt->stoc.size();
+        *out = bt.release();
+    });
+}
+
+int ckks_boot_destroy(ckks_boot* bt) {
+    delete bt;
+    return CKKS_OK;
+}
+
+int ckks_boot_info(const ckks_boot* bt, double* info) {
+    if (!bt || !info) return CKKS_EINVAL;
+    info[0] = bt->K_eff;
+    info[1] = bt->s_raise;
+    info[2] = (double)bt->c_drop;
+    info[3] = bt->l_drop;
+    info[4] = bt->l_em;
+    info[5] = bt->l_out;
+    info[6] = bt->s_em;
+    info[7] = bt->s_mask;
+    return CKKS_OK;
+}
+
+int ckks_boot_rotations(const ckks_boot* bt, int32_t* steps, int cap, int* n_out) {
+    if (!bt || !n_out) return CKKS_EINVAL;
+    std::set<int> s;
+    for (const auto& p : bt->ctos) plan_rotations(*p, s);
+    for (const auto& p : bt->stoc) plan_rotations(*p, s);
+    int i = 0;
+    for (int r : s) {
+        if (steps && i < cap) steps[i] = r;
+        ++i;
+    }
+    *n_out = i;
+    return CKKS_OK;
+}
+
+static std::unique_ptr<ckks_ptset> clone_ptset(ckks_ctx* ctx, const ckks_ptset& ps) {
+    auto o = std::make_unique<ckks_ptset>();
+    o->ctx = ctx;
+    o->a0 = ps.a0;
+    o->step = ps.step;
+    o->count = ps.count;
+    o->B = ps.B;
+    o->level = ps.level;
+    o->scale = ps.scale;
+    for (const auto& kv : ps.pts) {
+        auto pt = std::make_unique<ckks_pt>();
+        const size_t words = (size_t)(kv.second->level + 1) * ctx->n;
+        pt->ctx = ctx;
+        pt->buf = DevBuf(words, ctx->stream);
+        pt->level = kv.second->level;
+        pt->scale = kv.second->scale;
+        CUDA_CHECK(cudaMemcpyAsync(pt->buf.ptr, kv.second->buf.ptr, words * 8, cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+        o->pts[kv.first] = std::move(pt);
+    }
+    return o;
+}
+
+int ckks_boot_set_ctos(ckks_ctx* ctx, ckks_boot* bt, int i, const ckks_ptset* ps) {
+    return guard(ctx, [&] {
+        REQ(bt);
+        REQ(ps);
+        CK_CHECK(i >= 0 && i < (int)bt->ctos.size() && ps->level == bt->ctos[i]->level, CKKS_EINVAL,
+                 "bad CtoS index or level");
+        bt->ctos[i] = clone_ptset(ctx, *ps);
+    });
+}
+int ckks_boot_set_stoc(ckks_ctx* ctx, ckks_boot* bt, int i, const ckks_ptset* ps) {
+    return guard(ctx, [&] {
+        REQ(bt);
+        REQ(ps);
+        CK_CHECK(i >= 0 && i < (int)bt->stoc.size() && ps->level == bt->stoc[i]->level, CKKS_EINVAL,
+                 "bad StoC index or level");
+        bt->stoc[i] = clone_ptset(ctx, *ps);
+    });
+}
+int ckks_boot_set_coeffs(ckks_ctx* ctx, ckks_boot* bt, const double* c, int deg) {
+    return guard(ctx, [&] {
+        REQ(bt);
+        REQ(c);
+        CK_CHECK(deg == bt->bp.deg, CKKS_EINVAL, "degree differs from the configuration");
+        bt->coeffs.assign(c, c + deg + 1);
+    });
+}
+int ckks_boot_set_masks(ckks_ctx* ctx, ckks_boot* bt, const ckks_pt* re, const ckks_pt* im) {
+    return guard(ctx, [&] {
+        REQ(bt);
+        REQ(re);
+        REQ(im);
+        CK_CHECK(re->level == bt->l_em && im->level == bt->l_em, CKKS_EINVAL, "masks must sit at l_em");
+        for (int k = 0; k < 2; ++k) {
+            const ckks_pt* src = k ? im : re;
+            auto pt = std::make_unique<ckks_pt>();
+            const size_t words = (size_t)(src->level + 1) * ctx->n;
+            pt->ctx = ctx;
+            pt->buf = DevBuf(words, ctx->stream);
+            pt->level = src->level;
+            pt->scale = src->scale;
+            CUDA_CHECK(cudaMemcpyAsync(pt->buf.ptr, src->buf.ptr, words * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+            (k ? bt->mask_im : bt->mask_re) = std::move(pt);
+        }
+    });
+}
+
+int ckks_bootstrap(ckks_ctx* ctx, const ckks_keys* keys, const ckks_boot* bt, const ckks_ct* ct0, ckks_ct* out_re,
+                   ckks_ct* out_im) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        REQ(bt);
+        CT_OK(ct0);
+        REQ(out_re);
+        REQ(out_im);
+        ckks_ct re, im;
+        ops::bootstrap(*keys, *bt, *ct0, re, im);
+        assign(out_re, std::move(re));
+        assign(out_im, std::move(im));
+    });
+}
+
+int ckks_stoc1(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* re, const ckks_ct* im, const ckks_boot* bt,
+               ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(re);
+        CT_OK(im);
+        REQ(bt);
+        REQ(out);
+        assign(out, ops::stoc1(*keys, *bt, *re, *im));
+    });
+}
+
+int ckks_block(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv, const ckks_boot* bt,
+               ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(in);
+        REQ(conv);
+        REQ(bt);
+        REQ(out);
+        ckks_ct x = ops::rescale(ops::bsgs(*keys, *in, *conv));
+        ckks_ct re, im;
+        ops::bootstrap(*keys, *bt, x, re, im);
+        assign(out, ops::stoc1(*keys, *bt, re, im));
+    });
+}
+
+int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, int deg, int basis,
+                   double a, double b, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(in);
+        REQ(coeffs);
+        REQ(out);
+        CK_CHECK(basis == CKKS_BASIS_CHEB, CKKS_EINVAL, "only the Chebyshev basis is supported");
+        CK_CHECK(a == -1.0 && b == 1.0, CKKS_EINVAL, "only the interval [-1, 1] is supported");
+        std::vector<double> c(coeffs, coeffs + deg + 1);
+        assign(out, ops::cheb_eval(*keys, *in, c));
+    });
+}
+
+// ------------------------------------------------------------ raw NTT -------
+static int raw_ntt(ckks_ctx* ctx, uint64_t* dev, int n_limbs, const int32_t* ids, bool inv) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(dev);
+        REQ(ids);
+        CK_CHECK(n_limbs >= 0, CKKS_EINVAL, "negative limb count");
+        for (int i = 0; i < n_limbs; ++i)
+            CK_CHECK(ids[i] >= 0 && ids[i] < ctx->nall, CKKS_EINVAL, "prime id out of range");
+        if (n_limbs == 0) return;
+        std::vector<u64> tmp(n_limbs);
+        DevBuf d((n_limbs + 1) / 2, ctx->stream);
+        std::vector<int> v(ids, ids + n_limbs);
+        CUDA_CHECK(cudaMemcpyAsync(d.ptr, v.data(), n_limbs * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        if (inv)
+            kern::ntt_inverse(ctx, (u64*)dev, n_limbs, (const int*)d.ptr, n_limbs);
+        else
+            kern::ntt_forward(ctx, (u64*)dev, n_limbs, (const int*)d.ptr, n_limbs);
+    });
+}
+int ckks_ntt_forward(ckks_ctx* ctx, uint64_t* dev, int n_limbs, const int32_t* ids) {
+    return raw_ntt(ctx, dev, n_limbs, ids, false);
+}
+int ckks_ntt_inverse(ckks_ctx* ctx, uint64_t* dev, int n_limbs, const int32_t* ids) {
+    return raw_ntt(ctx, dev, n_limbs, ids, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+// FP64 side of the library: canonical embedding, the factors of the special DFT,
+// real CinS, fused conv diagonals, Chebyshev interpolation.  Offline (plaintext
+// preparation) and client-side (encode/decode) work only.
+//
+//   slots   z_j = f(zeta^(5^j)), zeta = exp(pi i / N), j < N/2                (Sec. 2.2)
+//   T_n     T_n[i][j] = omega_{4n}^(5^i rev_n(j)), T_{N/2} = S_{N/4} ... S_1    (Sec. 2.3, Eq. 2)
+//   S_k     blockdiag(B_k), B_k = [[I, W_k], [I, -W_k]], W_k = diag(omega_{8k}^(5^i))
+//   DFT'    DFT'_{2l}(x)_j = sum_{k<2l} x_k omega_{4l}^(5^j k)                 (Appendix A)
+// A linear map on the N/2 slots is a map offset -> vector with
+//   (W m)_i = sum_o d_o[i] m[(i + o) mod M]                                      (Eq. 3)
+#include <math.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace fp64 {
+
+static const double PI = 3.14159265358979323846;
+
+static cplx root_of_unity(long long e, long long m) {
+    // exp(2 pi i e / m) with e reduced into [0, m)
+    e %= m;
+    if (e < 0) e += m;
+    double th = 2.0 * PI * (double)e / (double)m;
+    return cplx(cos(th), sin(th));
+}
+
+// in-place iterative radix-2 FFT; sign -1: sum_k a_k e^{-2 pi i jk/n}, sign +1: e^{+...}
+static void fft(std::vector<cplx>& a, int sign) {
+    const int n = (int)a.size();
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        std::vector<cplx> w(len / 2);
+        for (int k = 0; k < len / 2; ++k) w[k] = root_of_unity(sign * (long long)k, len);
+        for (int i = 0; i < n; i += len)
+            for (int k = 0; k < len / 2; ++k) {
+                cplx u = a[i + k], v = a[i + k + len / 2] * w[k];
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+static std::vector<long long> rot_group(int n) {
+    std::vector<long long> g(n / 2);
+    long long x = 1;
+    for (int j = 0; j < n / 2; ++j) {
+        g[j] = x;
+        x = x * 5 % (2LL * n);
+    }
+    return g;
+}
+
+// index m with 2m + 1 = e (mod 2N)
+static inline int odd_index(long long e, int n) {
+    e %= 2LL * n;
+    if (e < 0) e += 2LL * n;
+    return (int)((e - 1) / 2);
+}
+
+std::vector<cplx> decode_slots(const std::vector<double>& f, int n) {
+    // y_m = f(zeta^(2m+1)) = sum_k (f_k zeta^k) e^{2 pi i m k / N}
+    std::vector<cplx> g(n);
+    for (int k = 0; k < n; ++k) g[k] = f[k] * root_of_unity(k, 2LL * n);
+    fft(g, +1);
+    std::vector<long long> rg = rot_group(n);
+    std::vector<cplx> z(n / 2);
+    for (int j = 0; j < n / 2; ++j) z[j] = g[odd_index(rg[j], n)];
+    return z;
+}
+
+std::vector<double> encode_slots(const std::vector<cplx>& z, int n) {
+    // values at zeta^(5^j) are z_j, at zeta^(-5^j) their conjugates; invert the evaluation
+    std::vector<cplx> y(n, cplx(0, 0));
+    std::vector<long long> rg = rot_group(n);
+    for (int j = 0; j < n / 2; ++j) {
+        y[odd_index(rg[j], n)] = z[j];
+        y[odd_index(-rg[j], n)] = std::conj(z[j]);
+    }
+    fft(y, -1);
+    std::vector<double> f(n);
+    for (int k = 0; k < n; ++k) f[k] = (y[k] / (double)n * root_of_unity(-(long long)k, 2LL * n)).real();
+    return f;
+}
+
+// ------------------------------------------------------------- S factors ----
+static std::vector<cplx> w_diag(int k) {
+    std::vector<cplx> w(k);
+    long long e = 1;
+    for (int i = 0; i < k; ++i) {
+        w[i] = root_of_unity(e, 8LL * k);
+        e = e * 5 % (8LL * k);
+    }
+    return w;
+}
+
+static void acc_into(Diag& D, int off, const std::vector<cplx>& v) {
+    auto it = D.find(off);
+    if (it == D.end())
+        D[off] = v;
+    else
+        for (size_t i = 0; i < v.size(); ++i) it->second[i] += v[i];
+}
+
+static Diag s_factor(int k, int m, bool inverse) {
+    std::vector<cplx> w = w_diag(k);
+    std::vector<cplx> d0(m), dp(m), dm(m);
+    for (int i = 0; i < m; ++i) {
+        int u = i % (2 * k);
+        bool top = u < k;
+        cplx wu = w[top ? u : u - k];
+        if (!inverse) {
+            if (top) {
+                d0[i] = 1.0;
+                dp[i] = wu;
+            } else {
+                dm[i] = 1.0;
+                d0[i] = -wu;
+            }
+        } else {
+            if (top) {
+                d0[i] = 0.5;
+                dp[i] = 0.5;
+            } else {
+                dm[i] = 0.5 / wu;
+                d0[i] = -0.5 / wu;
+            }
+        }
+    }
+    Diag D;
+    D[0] = d0;
+    acc_into(D, k % m, dp);
+    acc_into(D, ((-k) % m + m) % m, dm);
+    return D;
+}
+
+static Diag diag_mul(const Diag& A, const Diag& B, int m) {
+    Diag C;
+    for (const auto& a : A)
+        for (const auto& b : B) {
+            int key = (a.first + b.first) % m;
+            std::vector<cplx> t(m);
+            for (int i = 0; i < m; ++i) t[i] = a.second[i] * b.second[(i + a.first) % m];
+            acc_into(C, key, t);
+        }
+    return C;
+}
+
+Diag s_product(const std::vector<int>& strides, int m, bool inverse) {
+    Diag out;
+    out[0] = std::vector<cplx>(m, cplx(1, 0));
+    for (int k : strides) out = diag_mul(out, s_factor(k, m, inverse), m);
+    return out;
+}
+
+std::vector<std::vector<int>> split_groups(const std::vector<int>& stages, int levels) {
+    std::vector<std::vector<int>> out;
+    int s = (int)stages.size();
+    int base = s / levels, extra = s % levels, pos = 0;
+    for (int g = 0; g < levels; ++g) {
+        int size = base + (g < extra ? 1 : 0);
+        if (size > 0) out.push_back(std::vector<int>(stages.begin() + pos, stages.begin() + pos + size));
+        pos += size;
+    }
+    return out;
+}
+
+void ap_of_group(const std::vector<int>& strides, int m, int* a0, int* step, int* count) {
+    int k = *std::min_element(strides.begin(), strides.end());
+    int s = (int)strides.size();
+    if (((long long)k << s) >= m) {
+        *a0 = 0;
+        *step = k;
+        *count = m / k;
+    } else {
+        *a0 = (int)((((long long)-((1LL << s) - 1) * k) % m + m) % m);
+        *step = k;
+        *count = (1 << (s + 1)) - 1;
+    }
+}
+
+int default_bsgs_B(int count) {
+    // 2^e with e the least integer such that 4^e >= count, i.e. 2^ceil(log2(count)/2)
+    if (count <= 1) return 1;
+    int e = 0;
+    while ((1LL << (2 * e)) < count) ++e;
+    return 1 << e;
+}
+
+// --------------------------------------------------------------- CinS ------
+std::vector<cplx> real_cins_slots(const double* m, int C, int two_l) {
+    const int ell = two_l / 2;
+    std::vector<cplx> z((size_t)C * ell);
+    for (int i = 0; i < C; ++i) {
+        std::vector<double> sl(m + (size_t)i * two_l, m + (size_t)(i + 1) * two_l);
+        std::vector<cplx> d = decode_slots(sl, two_l);   // DFT'_{2l}: the subring's embedding
+        std::copy(d.begin(), d.end(), z.begin() + (size_t)i * ell);
+    }
+    return z;
+}
+
+std::vector<double> cins_to_reals(const std::vector<cplx>& z, int C, int two_l) {
+    const int ell = two_l / 2;
+    std::vector<double> out((size_t)C * two_l);
+    for (int i = 0; i < C; ++i) {
+        std::vector<cplx> sl(z.begin() + (size_t)i * ell, z.begin() + (size_t)(i + 1) * ell);
+        std::vector<double> f = encode_slots(sl, two_l);
+        std::copy(f.begin(), f.end(), out.begin() + (size_t)i * two_l);
+    }
+    return out;
+}
+
+// Fig. 1 placement: (k *_{w^2} i)[p] = sum_{a,b} K[a][b] i[p + (a-c) w + (b-c)]; a tap at
+// offset -o < 0 goes to w^2 - o with its sign flipped (Y^{-o} = -Y^{w^2-o})
+static std::vector<double> kernel_vector(const double* K, int f, int w) {
+    const int c = f / 2, n = w * w;
+    std::vector<double> v(n, 0.0);
+    for (int a = 0; a < f; ++a)
+        for (int b = 0; b < f; ++b) {
+            int qo = -((a - c) * w + (b - c));
+            if (qo >= 0)
+                v[qo] += K[a * f + b];
+            else
+                v[n + qo] -= K[a * f + b];
+        }
+    return v;
+}
+
+std::vector<std::vector<cplx>> fused_conv_diagonals(const double* W, int cin, int cout, int f, int w, int n) {
+    const int two_l = w * w, ell = two_l / 2, C = n / two_l, m = n / 2;
+    CK_CHECK(C >= 1 && cin <= C && cout <= C, CKKS_EINVAL, "channels do not fit in one ciphertext");
+    // K^[o][i] = DFT'_{2l}(k_{o,i})
+    std::vector<std::vector<cplx>> Kh((size_t)C * C);
+    for (int o = 0; o < cout; ++o)
+        for (int i = 0; i < cin; ++i)
+            Kh[(size_t)o * C + i] = decode_slots(kernel_vector(W + ((size_t)o * cin + i) * f * f, f, w), two_l);
+    // S' = slice matrix of StoC2 = S_{N/2 <- l} = S_{N/4} ... S_l
+    std::vector<int> strides;
+    for (int k = m / 2; k >= ell; k /= 2) strides.push_back(k);
+    Diag S = s_product(strides, m, false);
+    std::vector<std::vector<cplx>> Sp((size_t)C * C, std::vector<cplx>(ell, cplx(0, 0)));
+    for (const auto& d : S) {
+        CK_CHECK(d.first % ell == 0, CKKS_EINVAL, "StoC2 is not slice-granular");
+        int dd = d.first / ell;
+        for (int i = 0; i < C; ++i)
+            for (int u = 0; u < ell; ++u) Sp[(size_t)i * C + (i + dd) % C][u] += d.second[(size_t)i * ell + u];
+    }
+    // K' = S' K^ (slice-wise products), diagonal delta: d[i l + u] = K'[i][(i + delta) % C][u]
+    std::vector<std::vector<cplx>> diags(C, std::vector<cplx>(m, cplx(0, 0)));
+    for (int i = 0; i < C; ++i)
+        for (int j = 0; j < C; ++j) {
+            std::vector<cplx> acc(ell, cplx(0, 0));
+            for (int mm = 0; mm < C; ++mm) {
+                const std::vector<cplx>& kk = Kh[(size_t)mm * C + j];
+                if (kk.empty()) continue;
+                const std::vector<cplx>& ss = Sp[(size_t)i * C + mm];
+                for (int u = 0; u < ell; ++u) acc[u] += ss[u] * kk[u];
+            }
+            int delta = ((j - i) % C + C) % C;
+            for (int u = 0; u < ell; ++u) diags[delta][(size_t)i * ell + u] = acc[u];
+        }
+    return diags;
+}
+
+// Chebyshev interpolant (first-kind nodes) of cos(2 pi (K y - 1/4) / 2^r) on [-1, 1]
+std::vector<double> cheb_interp_cos(double K, int r, int deg) {
+    const int n = deg + 1;
+    std::vector<double> fx(n), c(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double x = cos(PI * (j + 0.5) / n);
+        fx[j] = cos(2.0 * PI * (K * x - 0.25) / ldexp(1.0, r));
+    }
+    for (int k = 0; k < n; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += fx[j] * cos(PI * k * (j + 0.5) / n);
+        c[k] = 2.0 * s / n;
+    }
+    c[0] *= 0.5;
+    return c;
+}
+
+}  // namespace fp64

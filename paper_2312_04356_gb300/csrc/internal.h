@@ -1,0 +1,251 @@
+// Internal declarations of the GB300 RNS-CKKS library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ckks.h"
+#include "modarith.cuh"
+
+typedef std::complex<double> cplx;
+
+// ------------------------------------------------------------------ errors --
+struct CkksError {
+    int code;
+    std::string msg;
+};
+#define CK_THROW(code, msg) throw CkksError{(code), (msg)}
+#define CK_CHECK(cond, code, msg) \
+    do {                          \
+        if (!(cond)) CK_THROW(code, msg); \
+    } while (0)
+#define CUDA_CHECK(x)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (x);                                                               \
+        if (e_ != cudaSuccess)                                                              \
+            CK_THROW(e_ == cudaErrorMemoryAllocation ? CKKS_ENOMEM : CKKS_ECUDA,            \
+                     std::string(#x) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+// ------------------------------------------------------------ device data --
+// Per-prime constants, indexed by global prime id (q_0..q_L, then p_0..p_{np-1}).
+struct DevPrime {
+    DevMod m;
+    const u64* tw;   // psi^rev(k), k < N          (forward, Cooley-Tukey)
+    const u64* twp;  // Shoup companions
+    const u64* itw;  // psi^-rev(k)                 (inverse, Gentleman-Sande)
+    const u64* itwp;
+    u64 n_inv, n_inv_p;
+};
+
+// Base-conversion table: inputs (prime ids in_ids, count nin) -> outputs (out_ids, nout).
+//   xhat_i = x_i * qhat_inv[i] mod q_i ; y_m = sum_i xhat_i * qhat_mod[m*nin + i] mod p_m
+struct ConvTab {
+    int nin = 0, nout = 0;
+    std::vector<int> in_ids, out_ids;
+    int* d_in_ids = nullptr;
+    int* d_out_ids = nullptr;
+    u64* d_qhat_inv = nullptr;   // [nin] and Shoup [nin]
+    u64* d_qhat_mod = nullptr;   // [nout][nin] and Shoup [nout][nin]
+};
+
+// Device buffer owned by RAII (stream-ordered allocation on the context's stream).
+struct DevBuf {
+    u64* ptr = nullptr;
+    size_t words = 0;
+    cudaStream_t stream = 0;
+    DevBuf() {}
+    DevBuf(size_t w, cudaStream_t s);
+    ~DevBuf();
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+    DevBuf& operator=(DevBuf&& o) noexcept;
+    void reset();
+};
+
+struct ckks_ctx {
+    ckks_params P;
+    int logn = 0, n = 0, nq = 0, L = 0, alpha = 0, np = 0, nall = 0, n_circuit = 0;
+    std::vector<u64> q, p, psi;      // psi indexed by prime id
+    std::vector<u64> mod_of;         // modulus by prime id
+    std::vector<double> delta;
+    std::vector<DevMod> mods;        // by prime id
+    uint64_t seed = 0;
+    u64 gauss[39];
+    cudaStream_t stream = 0;
+    DevPrime* d_primes = nullptr;
+    u64* d_tables = nullptr;
+    u64* d_gauss = nullptr;
+    int* d_iota = nullptr;                   // 0..nall-1
+    u64* d_pinv = nullptr;                   // P^{-1} mod q_i [nq], Shoup [nq]
+    u64* d_qlinv = nullptr;                  // q_l^{-1} mod q_i [nq][nq], Shoup [nq][nq]
+    std::vector<int*> d_ext_ids;             // per level: [0..l] + specials
+    std::map<std::pair<int, int>, std::unique_ptr<ConvTab>> modup_tabs;  // (level, digit)
+    std::map<int, std::unique_ptr<ConvTab>> moddown_tabs;               // level
+    std::string err;
+    std::map<std::string, long> ops;   // op counters (PMult, HRot, keyswitch, ...)
+    // measurement: kernel launch count and, when timing is on, CUDA events around launches
+    mutable long long launches = 0;
+    bool timing = false;
+    struct Pending {
+        const char* name;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    struct KStat {
+        long long launches = 0;
+        double ms = 0, bytes = 0;
+    };
+    mutable std::vector<Pending> pending;
+    mutable std::vector<cudaEvent_t> event_pool;
+    mutable std::map<std::string, KStat> kstats;   // name -> launches, ms, algorithmic bytes
+    void collect_timing() const;
+
+    std::vector<std::vector<int>> digits(int level) const;
+    std::vector<int> ext_ids(int level) const;
+    const ConvTab& modup_tab(int level, int d);
+    const ConvTab& moddown_tab(int level);
+    ~ckks_ctx();
+};
+
+struct ckks_ct {
+    ckks_ctx* ctx = nullptr;
+    DevBuf buf;           // [2][level+1][N]
+    int level = -1;
+    double scale = 1.0;
+    u64* c0() const { return buf.ptr; }
+    u64* c1() const { return buf.ptr + (size_t)(level + 1) * ctx->n; }
+};
+
+struct ckks_pt {
+    ckks_ctx* ctx = nullptr;
+    DevBuf buf;           // [level+1][N], NTT domain
+    int level = -1;
+    double scale = 1.0;
+};
+
+struct SwitchKey {
+    DevBuf b, a;          // [ndig][nall][N], NTT domain
+    int ndig = 0;
+};
+
+struct ckks_keys {
+    ckks_ctx* ctx = nullptr;
+    std::vector<int64_t> s;          // secret coefficients
+    DevBuf s_ntt;                    // [nall][N]
+    DevBuf pk_b, pk_a;               // [nq][N]
+    std::map<u64, std::unique_ptr<SwitchKey>> swk;   // 0 = relin, else Galois element
+};
+
+struct ckks_ptset {
+    ckks_ctx* ctx = nullptr;
+    int a0 = 0, step = 1, count = 1, B = 1, level = 0;
+    double scale = 1.0;
+    std::map<std::pair<int, int>, std::unique_ptr<ckks_pt>> pts;
+    int G() const { return (count + B - 1) / B; }
+};
+
+struct ckks_boot {
+    ckks_ctx* ctx = nullptr;
+    ckks_boot_params bp;
+    int two_l = 0, ell = 0, C = 0, l_drop = 0, l_em = 0, l_out = 0;
+    long long c_drop = 0;
+    double K_eff = 0, s_raise = 0, s_em = 0, s_mask = 0;
+    std::vector<double> coeffs;
+    std::vector<std::unique_ptr<ckks_ptset>> ctos, stoc;
+    std::unique_ptr<ckks_pt> mask_re, mask_im;
+};
+
+// Scope object placed around one kernel launch: counts it and, if the context's
+// timing flag is set, brackets it with CUDA events on the context's stream.
+struct KTimer {
+    const ckks_ctx* c;
+    const char* name;
+    double bytes;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KTimer(const ckks_ctx* ctx, const char* nm, double algo_bytes);
+    ~KTimer();
+};
+
+// ----------------------------------------------------------- kernel API --
+// All launchers enqueue on ctx->stream.  `ids` are device arrays of prime ids
+// (length lpp = limbs per polynomial); limb k of a multi-polynomial array uses ids[k % lpp].
+namespace kern {
+void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp);
+void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp);
+void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
+void sub(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
+void neg(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, const int* ids, int lpp);
+void mul(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
+// o += a * b
+void mul_acc(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
+// o = a * s[limb % lpp] (s residues, sp their Shoup companions; device arrays)
+void mul_scalar(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nlimbs, const int* ids,
+                int lpp);
+// a[limb][*] += v[limb]: adds the constant polynomial v in the NTT domain (device array v)
+void add_const_term(const ckks_ctx* c, u64* a, const u64* v, int nlimbs, const int* ids);
+// signed small ints (device int64 [N]) -> residues [nlimbs][N] (coefficient domain)
+void small_to_rns(const ckks_ctx* c, const int64_t* v, u64* o, int nlimbs, const int* ids);
+// o[i] = a[galois_src(i)] in the NTT domain
+void automorph(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, u64 g);
+// X^{N/2} times a, NTT domain: pointwise by psi^((2 rev(i)+1) N/2)
+void imult(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, const int* ids, int lpp);
+// centred lift of one coefficient-domain limb with prime `src_id` into nlimbs limbs
+void lift_centred(const ckks_ctx* c, const u64* src, int src_id, u64* o, int nlimbs, const int* ids);
+// out_i = (a_i - b_i) * s_i  (s device residues per limb index % lpp, Shoup companions sp)
+void sub_mul_scalar(const ckks_ctx* c, const u64* a, const u64* b, const u64* s, const u64* sp, u64* o,
+                    int nlimbs, const int* ids, int lpp);
+// fast base conversion, coefficient domain: in [nin][N] (limb stride in_stride words),
+// out rows written at out + out_row[m]*N
+void base_convert(const ckks_ctx* c, const ConvTab& t, const u64* in, size_t in_stride, u64* out,
+                  size_t out_stride, int npoly, size_t in_poly_stride, size_t out_poly_stride);
+// key-switch inner product: D [ndig][next][N], key rows krow[e] of [ndig][nall][N];
+// ob/oa [next][N] = sum_d D_d(sigma_g) * key_d ; g = 1 means no automorphism
+void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
+              const u64* ka, u64* ob, u64* oa, u64 g);
+// uniform residues in the NTT domain drawn from the counter stream (see ckks.h)
+void sample_uniform(const ckks_ctx* c, u64* o, int nlimbs, const int* ids, u64 key);
+void sample_small(const ckks_ctx* c, int64_t* o, u64 key, int kind /*0 ternary, 1 gauss*/);
+}  // namespace kern
+
+// host helpers shared by the translation units
+namespace hostmath {
+u64 mulmod(u64 a, u64 b, u64 q);
+u64 powmod(u64 a, u64 e, u64 q);
+u64 invmod(u64 a, u64 q);
+u64 shoup(u64 w, u64 q);
+u64 from_signed(int64_t v, u64 q);
+DevMod make_mod(u64 q);
+bool is_prime(u64 n);
+u64 splitmix_mix(u64 z);
+u64 stream_key(u64 seed, u64 tag);
+u64 stream_word(u64 key, u64 i);
+long long llround_away(double x);
+}  // namespace hostmath
+
+// chain construction (chain.cpp)
+void build_chain(const ckks_params& P, std::vector<u64>& q, std::vector<u64>& p, std::vector<double>& delta);
+u64 smallest_root_2n(u64 q, int n);
+void gauss_table(double sigma, u64* t39);
+
+// FP64 encoding and plan construction (fp64.cpp)
+namespace fp64 {
+std::vector<double> encode_slots(const std::vector<cplx>& z, int n);       // -> N real coeffs
+std::vector<cplx> decode_slots(const std::vector<double>& f, int n);       // -> N/2 slots
+typedef std::map<int, std::vector<cplx>> Diag;                            // offset -> vector
+Diag s_product(const std::vector<int>& strides, int m, bool inverse);
+std::vector<std::vector<int>> split_groups(const std::vector<int>& stages, int levels);
+void ap_of_group(const std::vector<int>& strides, int m, int* a0, int* step, int* count);
+std::vector<std::vector<cplx>> fused_conv_diagonals(const double* W, int cin, int cout, int f, int w, int n);
+std::vector<cplx> real_cins_slots(const double* m, int C, int two_l);
+std::vector<double> cins_to_reals(const std::vector<cplx>& z, int C, int two_l);
+std::vector<double> cheb_interp_cos(double K, int r, int deg);
+int default_bsgs_B(int count);
+}  // namespace fp64
+

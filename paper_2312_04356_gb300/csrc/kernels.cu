@@ -1,0 +1,535 @@
+// Device kernels of the RNS-CKKS hot path and their launchers.
+//
+// Layout: a polynomial is [limb][N] uint64, limb k of an array of several
+// polynomials uses the prime with global id ids[k % lpp].  One CTA row of the
+// grid (blockIdx.y) is one limb, so the modulus is uniform inside a CTA.
+#include "internal.h"
+
+// ------------------------------------------------------------ DevBuf -------
+DevBuf::DevBuf(size_t w, cudaStream_t s) : words(w), stream(s) {
+    if (w) {
+        cudaError_t e = cudaMallocAsync((void**)&ptr, w * sizeof(u64), s);
+        if (e != cudaSuccess) {
+            ptr = nullptr;
+            CK_THROW(CKKS_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+        }
+    }
+}
+DevBuf::~DevBuf() { reset(); }
+DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+        reset();
+        ptr = o.ptr;
+        words = o.words;
+        stream = o.stream;
+        o.ptr = nullptr;
+        o.words = 0;
+    }
+    return *this;
+}
+void DevBuf::reset() {
+    if (ptr) cudaFreeAsync(ptr, stream);
+    ptr = nullptr;
+    words = 0;
+}
+
+static cudaEvent_t take_event(const ckks_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+KTimer::KTimer(const ckks_ctx* ctx, const char* nm, double algo_bytes) : c(ctx), name(nm), bytes(algo_bytes) {
+    ++c->launches;
+    if (c->timing) {
+        a = take_event(c);
+        b = take_event(c);
+        cudaEventRecord(a, c->stream);
+    }
+}
+
+KTimer::~KTimer() {
+    if (a) {
+        cudaEventRecord(b, c->stream);
+        c->pending.push_back({name, a, b, bytes});
+        if (c->pending.size() > 4096) c->collect_timing();
+    }
+}
+
+void ckks_ctx::collect_timing() const {
+    if (pending.empty()) return;
+    cudaEventSynchronize(pending.back().b);
+    for (const Pending& p : pending) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        KStat& st = kstats[p.name];
+        st.launches += 1;
+        st.ms += ms;
+        st.bytes += p.bytes;
+        event_pool.push_back(p.a);
+        event_pool.push_back(p.b);
+    }
+    pending.clear();
+}
+
+namespace {
+
+constexpr int EW_THREADS = 256;
+
+inline dim3 ew_grid(int n, int nlimbs) {
+    int x = n / (EW_THREADS * 4);
+    if (x < 1) x = 1;
+    return dim3(x, nlimbs);
+}
+
+#define EW_LOOP(n) for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (n); j += gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------------ NTT ----
+// One pass covers `c` consecutive butterfly stages s0..s0+c-1 (stage s: 2^s groups,
+// stride t = N >> (s+1)).  Over those stages only index bits log2(T1)..log2(T0) move
+// (T0 = N >> (s0+1), T1 = N >> (s0+c)), so the limb splits into independent
+// sub-problems of 2^c elements j = hi*2T0 + k*T1 + lo.  A CTA stages SUB of them
+// (4096 elements) in shared memory, runs the c stages, and writes them back.
+constexpr int NTT_TILE = 4096;
+constexpr int NTT_THREADS = 256;
+
+template <bool INV>
+__global__ void __launch_bounds__(NTT_THREADS)
+    k_ntt_pass(u64* __restrict__ data, const DevPrime* __restrict__ primes, const int* __restrict__ ids, int lpp,
+               int logn, int s0, int c, int logsub, int scale_out) {
+    extern __shared__ u64 sm[];
+    const int limb = blockIdx.y;
+    const DevPrime* P = primes + ids[limb % lpp];
+    const u64 q = P->m.q;
+    u64* a = data + ((size_t)limb << logn);
+    const int span = 1 << c;
+    const int SUB = 1 << logsub;
+    const int stride = SUB > 1 ? SUB + 1 : 1;
+    const int logT1 = logn - s0 - c;
+    const int T1 = 1 << logT1;
+    const int log2T0 = logn - s0;
+    const int sid0 = blockIdx.x * SUB;
+    const int total = SUB << c;
+
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int s, k;
+        if (T1 == 1) {
+            s = e >> c;
+            k = e & (span - 1);
+        } else {
+            k = e >> logsub;
+            s = e & (SUB - 1);
+        }
+        int sid = sid0 + s;
+        size_t j = ((size_t)(sid >> logT1) << log2T0) + ((size_t)k << logT1) + (sid & (T1 - 1));
+        sm[k * stride + s] = a[j];
+    }
+    __syncthreads();
+
+    const int nbf = total >> 1;
+    for (int u = 0; u < c; ++u) {
+        const int uu = INV ? (c - 1 - u) : u;
+        const int sg = s0 + uu;               // global stage
+        const int lt = c - 1 - uu;            // log2 of the local stride
+        const int tk = 1 << lt;
+        for (int e = threadIdx.x; e < nbf; e += blockDim.x) {
+            const int s = e & (SUB - 1);
+            const int b = e >> logsub;
+            const int k = ((b >> lt) << (lt + 1)) | (b & (tk - 1));
+            const int sid = sid0 + s;
+            const size_t j = ((size_t)(sid >> logT1) << log2T0) + ((size_t)k << logT1) + (sid & (T1 - 1));
+            const int widx = (1 << sg) + (int)(j >> (logn - sg));
+            u64* px = sm + k * stride + s;
+            u64* py = sm + (k + tk) * stride + s;
+            const u64 x = *px, y = *py;
+            if (!INV) {
+                const u64 v = mul_shoup(y, P->tw[widx], P->twp[widx], q);
+                *px = add_mod(x, v, q);
+                *py = sub_mod(x, v, q);
+            } else {
+                *px = add_mod(x, y, q);
+                *py = mul_shoup(sub_mod(x, y, q), P->itw[widx], P->itwp[widx], q);
+            }
+        }
+        __syncthreads();
+    }
+
+    const u64 ninv = P->n_inv, ninvp = P->n_inv_p;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int s, k;
+        if (T1 == 1) {
+            s = e >> c;
+            k = e & (span - 1);
+        } else {
+            k = e >> logsub;
+            s = e & (SUB - 1);
+        }
+        int sid = sid0 + s;
+        size_t j = ((size_t)(sid >> logT1) << log2T0) + ((size_t)k << logT1) + (sid & (T1 - 1));
+        u64 v = sm[k * stride + s];
+        if (scale_out) v = mul_shoup(v, ninv, ninvp, q);
+        a[j] = v;
+    }
+}
+
+struct PassPlan {
+    int s0, c;
+};
+
+inline std::vector<PassPlan> ntt_passes(int logn) {
+    if (logn <= 12) return {{0, logn}};
+    return {{0, logn - 8}, {logn - 8, 8}};
+}
+
+template <bool INV>
+void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, PassPlan p, int scale_out) {
+    const int logn = cx->logn;
+    int logsub = 12 - p.c;
+    if (logsub < 0) logsub = 0;
+    if (logsub > logn - p.c) logsub = logn - p.c;
+    const int SUB = 1 << logsub;
+    const int tiles = (1 << (logn - p.c)) / SUB;
+    const int stride = SUB > 1 ? SUB + 1 : 1;
+    const size_t smem = (size_t)stride * (1 << p.c) * sizeof(u64);
+    dim3 grid(tiles, nlimbs);
+    { KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0);
+    k_ntt_pass<INV><<<grid, NTT_THREADS, smem, cx->stream>>>(data, cx->d_primes, ids, lpp, logn, p.s0, p.c, logsub,
+                                                             scale_out);
+    }
+}
+
+// ----------------------------------------------------------- elementwise ----
+__global__ void k_add(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const u64 q = P[ids[limb % lpp]].m.q;
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = add_mod(a[off + j], b[off + j], q);
+}
+__global__ void k_sub(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const u64 q = P[ids[limb % lpp]].m.q;
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = sub_mod(a[off + j], b[off + j], q);
+}
+__global__ void k_neg(const u64* a, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const u64 q = P[ids[limb % lpp]].m.q;
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = neg_mod(a[off + j], q);
+}
+__global__ void k_mul(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const DevMod m = P[ids[limb % lpp]].m;
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = mul_mod(a[off + j], b[off + j], m);
+}
+__global__ void k_mul_acc(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const DevMod m = P[ids[limb % lpp]].m;
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = add_mod(o[off + j], mul_mod(a[off + j], b[off + j], m), m.q);
+}
+__global__ void k_mul_scalar(const u64* a, const u64* s, const u64* sp, u64* o, const DevPrime* P, const int* ids,
+                             int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const int r = limb % lpp;
+    const u64 q = P[ids[r]].m.q;
+    const u64 w = s[r], wp = sp[r];
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = mul_shoup(a[off + j], w, wp, q);
+}
+__global__ void k_add_scalar(u64* a, const u64* v, const DevPrime* P, const int* ids, int logn) {
+    const int limb = blockIdx.y;
+    const u64 q = P[ids[limb]].m.q;
+    const u64 c = v[limb];
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) a[off + j] = add_mod(a[off + j], c, q);
+}
+__global__ void k_small_to_rns(const int64_t* v, u64* o, const DevPrime* P, const int* ids, int logn) {
+    const int limb = blockIdx.y;
+    const DevMod m = P[ids[limb]].m;
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) {
+        const int64_t x = v[j];
+        if (x >= 0) {
+            o[off + j] = reduce64((u64)x, m);
+        } else {
+            const u64 r = reduce64((u64)(-(x + 1)) + 1ull, m);
+            o[off + j] = r ? m.q - r : 0;
+        }
+    }
+}
+__global__ void k_automorph(const u64* a, u64* o, u64 g, int logn) {
+    const size_t off = (size_t)blockIdx.y << logn;
+    EW_LOOP(1 << logn) o[off + j] = a[off + galois_src(j, g, logn)];
+}
+__global__ void k_imult(const u64* a, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const DevPrime* pr = P + ids[limb % lpp];
+    const u64 q = pr->m.q;
+    // X^{N/2} at psi^(2r+1): psi^{N/2} when r is even, -psi^{N/2} when r is odd;
+    // psi^{N/2} = tw[1] since rev(1) = N/2
+    const u64 w = pr->tw[1], wp = pr->twp[1];
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) {
+        u64 v = mul_shoup(a[off + j], w, wp, q);
+        unsigned r = brev_bits(j, logn);
+        o[off + j] = (r & 1) ? neg_mod(v, q) : v;
+    }
+}
+__global__ void k_lift_centred(const u64* src, u64 qs, u64* o, const DevPrime* P, const int* ids, int logn) {
+    const int limb = blockIdx.y;
+    const DevMod t = P[ids[limb]].m;
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = centred_to(src[j], qs, t);
+}
+__global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const u64* sp, u64* o,
+                                 const DevPrime* P, const int* ids, int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const int r = limb % lpp;
+    const u64 q = P[ids[r]].m.q;
+    const u64 w = s[r], wp = sp[r];
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = mul_shoup(sub_mod(a[off + j], b[off + j], q), w, wp, q);
+}
+
+// ------------------------------------------------------- base conversion ----
+// y_m = sum_i [x_i * qhat_i^{-1}]_{q_i} * (qhat_i mod p_m)  (no correction term)
+constexpr int MAX_CONV_IN = 16;
+__global__ void k_base_convert(const u64* __restrict__ in, size_t in_stride, u64* __restrict__ out,
+                               size_t out_stride, int nin, int nout, const int* __restrict__ in_ids,
+                               const int* __restrict__ out_ids, const int* __restrict__ out_rows,
+                               const u64* __restrict__ qinv, const u64* __restrict__ qmod,
+                               const DevPrime* __restrict__ P, int logn, size_t in_pstride, size_t out_pstride) {
+    const int poly = blockIdx.y;
+    in += poly * in_pstride;
+    out += poly * out_pstride;
+    EW_LOOP(1 << logn) {
+        u64 xh[MAX_CONV_IN];
+#pragma unroll
+        for (int i = 0; i < MAX_CONV_IN; ++i) {
+            if (i < nin) {
+                const u64 qi = P[in_ids[i]].m.q;
+                xh[i] = mul_shoup(in[i * in_stride + j], qinv[i], qinv[nin + i], qi);
+            }
+        }
+        for (int m = 0; m < nout; ++m) {
+            const u64 pm = P[out_ids[m]].m.q;
+            const u64* cm = qmod + (size_t)m * nin;
+            const u64* cmp = qmod + (size_t)nout * nin + (size_t)m * nin;
+            u64 acc = 0;
+#pragma unroll
+            for (int i = 0; i < MAX_CONV_IN; ++i)
+                if (i < nin) acc = add_mod(acc, mul_shoup(xh[i], cm[i], cmp[i], pm), pm);
+            out[(size_t)out_rows[m] * out_stride + j] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------- key-switch product ----
+__global__ void k_ks_inner(const u64* __restrict__ D, int ndig, int next, const int* __restrict__ ext_ids,
+                           const u64* __restrict__ kb, const u64* __restrict__ ka, u64* __restrict__ ob,
+                           u64* __restrict__ oa, const DevPrime* __restrict__ P, int logn, u64 g, size_t kstride) {
+    const int e = blockIdx.y;
+    const int id = ext_ids[e];
+    const DevMod m = P[id].m;
+    const size_t n = (size_t)1 << logn;
+    EW_LOOP(1 << logn) {
+        const unsigned src = g == 1 ? (unsigned)j : galois_src(j, g, logn);
+        u64 accb = 0, acca = 0;
+        for (int d = 0; d < ndig; ++d) {
+            const u64 x = D[((size_t)d * next + e) * n + src];
+            const size_t kk = d * kstride + (size_t)id * n + j;
+            accb = add_mod(accb, mul_mod(x, kb[kk], m), m.q);
+            acca = add_mod(acca, mul_mod(x, ka[kk], m), m.q);
+        }
+        ob[(size_t)e * n + j] = accb;
+        oa[(size_t)e * n + j] = acca;
+    }
+}
+
+// ------------------------------------------------------------ sampling ----
+__device__ __forceinline__ u64 d_mix(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ u64 d_word(u64 key, u64 i) { return d_mix(key + (i + 1) * 0x9E3779B97F4A7C15ULL); }
+
+__global__ void k_sample_uniform(u64* o, const DevPrime* P, const int* ids, int logn, u64 key) {
+    const int limb = blockIdx.y;
+    const int id = ids[limb];
+    const DevMod m = P[id].m;
+    const u64 two64 = barrett_reduce128(1, 0, m);   // 2^64 mod q
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) {
+        const u64 k = ((u64)id << logn) + (u64)j;
+        const u64 w1 = d_word(key, 2 * k), w2 = d_word(key, 2 * k + 1);
+        o[off + j] = add_mod(mul_mod(reduce64(w1, m), two64, m), reduce64(w2, m), m.q);
+    }
+}
+__global__ void k_sample_small(int64_t* o, int logn, u64 key, int kind, const u64* gauss) {
+    EW_LOOP(1 << logn) {
+        const u64 w = d_word(key, (u64)j);
+        if (kind == 0) {
+            o[j] = (int64_t)(w % 3ull) - 1;
+        } else {
+            const u64 u = w >> 1;
+            int k = 0;
+            while (k < 38 && u >= gauss[k]) ++k;
+            o[j] = (int64_t)k - 19;
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers ---
+namespace kern {
+
+#define LAUNCH_CHECK() CUDA_CHECK(cudaGetLastError())
+
+void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp) {
+    if (nlimbs <= 0) return;
+    for (const PassPlan& p : ntt_passes(c->logn)) launch_pass<false>(c, data, nlimbs, ids, lpp, p, 0);
+    LAUNCH_CHECK();
+}
+
+void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp) {
+    if (nlimbs <= 0) return;
+    std::vector<PassPlan> ps = ntt_passes(c->logn);
+    for (int i = (int)ps.size() - 1; i >= 0; --i)
+        launch_pass<true>(c, data, nlimbs, ids, lpp, ps[i], ps[i].s0 == 0 ? 1 : 0);
+    LAUNCH_CHECK();
+}
+
+void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "add", 3.0 * (double)nl * c->n * 8.0);
+    k_add<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, o, c->d_primes, ids, lpp, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void sub(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "sub", 3.0 * (double)nl * c->n * 8.0);
+    k_sub<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, o, c->d_primes, ids, lpp, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void neg(const ckks_ctx* c, const u64* a, u64* o, int nl, const int* ids, int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "neg", 2.0 * (double)nl * c->n * 8.0);
+    k_neg<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, o, c->d_primes, ids, lpp, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void mul(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "mul", 3.0 * (double)nl * c->n * 8.0);
+    k_mul<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, o, c->d_primes, ids, lpp, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void mul_acc(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "mul_acc", 4.0 * (double)nl * c->n * 8.0);
+    k_mul_acc<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, o, c->d_primes, ids, lpp, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void mul_scalar(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nl, const int* ids,
+                int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "mul_scalar", 2.0 * (double)nl * c->n * 8.0);
+    k_mul_scalar<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, s, sp, o, c->d_primes, ids, lpp, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void add_const_term(const ckks_ctx* c, u64* a, const u64* v, int nl, const int* ids) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "add_scalar", 2.0 * (double)nl * c->n * 8.0);
+    k_add_scalar<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, v, c->d_primes, ids, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void small_to_rns(const ckks_ctx* c, const int64_t* v, u64* o, int nl, const int* ids) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "small_to_rns", (nl + 1.0) * c->n * 8.0);
+    k_small_to_rns<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(v, o, c->d_primes, ids, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void automorph(const ckks_ctx* c, const u64* a, u64* o, int nl, u64 g) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "automorph", 2.0 * (double)nl * c->n * 8.0);
+    k_automorph<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, o, g, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void imult(const ckks_ctx* c, const u64* a, u64* o, int nl, const int* ids, int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "imult", 2.0 * (double)nl * c->n * 8.0);
+    k_imult<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, o, c->d_primes, ids, lpp, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void lift_centred(const ckks_ctx* c, const u64* src, int src_id, u64* o, int nl, const int* ids) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "lift_centred", (nl + 1.0) * c->n * 8.0);
+    k_lift_centred<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(src, c->mod_of[src_id], o, c->d_primes, ids,
+                                                                     c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void sub_mul_scalar(const ckks_ctx* c, const u64* a, const u64* b, const u64* s, const u64* sp, u64* o, int nl,
+                    const int* ids, int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "sub_mul_scalar", 3.0 * (double)nl * c->n * 8.0);
+    k_sub_mul_scalar<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, s, sp, o, c->d_primes, ids, lpp,
+                                                                       c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void base_convert(const ckks_ctx* c, const ConvTab& t, const u64* in, size_t in_stride, u64* out,
+                  size_t out_stride, int npoly, size_t in_pstride, size_t out_pstride) {
+    CK_CHECK(t.nin <= MAX_CONV_IN, CKKS_EINVAL, "base conversion with more than 16 input limbs");
+    if (t.nout == 0) return;
+    dim3 grid(ew_grid(c->n, 1).x, npoly);
+    // d_out_ids is followed by out_rows in the same allocation
+    { KTimer kt_(c, "base_convert", (double)npoly * (t.nin + t.nout) * c->n * 8.0);
+    k_base_convert<<<grid, EW_THREADS, 0, c->stream>>>(in, in_stride, out, out_stride, t.nin, t.nout, t.d_in_ids,
+                                                       t.d_out_ids, t.d_out_ids + t.nout, t.d_qhat_inv, t.d_qhat_mod,
+                                                       c->d_primes, c->logn, in_pstride, out_pstride);
+    }
+    LAUNCH_CHECK();
+}
+void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
+              const u64* ka, u64* ob, u64* oa, u64 g) {
+    { KTimer kt_(c, "ks_inner", (3.0 * ndig + 2.0) * next * c->n * 8.0);
+    k_ks_inner<<<ew_grid(c->n, next), EW_THREADS, 0, c->stream>>>(D, ndig, next, ext_ids, kb, ka, ob, oa,
+                                                                   c->d_primes, c->logn, g,
+                                                                   (size_t)c->nall << c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void sample_uniform(const ckks_ctx* c, u64* o, int nl, const int* ids, u64 key) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "sample_uniform", (double)nl * c->n * 8.0);
+    k_sample_uniform<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(o, c->d_primes, ids, c->logn, key);
+    }
+    LAUNCH_CHECK();
+}
+void sample_small(const ckks_ctx* c, int64_t* o, u64 key, int kind) {
+    { KTimer kt_(c, "sample_small", c->n * 8.0);
+    k_sample_small<<<ew_grid(c->n, 1), EW_THREADS, 0, c->stream>>>(o, c->logn, key, kind, c->d_gauss);
+    }
+    LAUNCH_CHECK();
+}
+
+}  // namespace kern

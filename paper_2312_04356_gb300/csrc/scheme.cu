@@ -1,0 +1,818 @@
+// RNS-CKKS scheme on the GPU: context, keys, encryption, key switching, rotations,
+// BSGS linear maps, the fused CinS conv, Chebyshev evaluation and bootstrapping.
+//
+// Every ciphertext limb lives on the device in the NTT domain.  Host code only
+// sequences kernels (kernels.cu) and prepares constants.  Steps follow the paper's
+// Alg. 1 and the hybrid RNS-CKKS it builds on (Sec. 2.1, Sec. 2.4):
+//   key switching: digits of alpha consecutive limbs; ModUp by fast base conversion
+//   without correction; inner product with the key over Q_l u P; ModDown
+//   (c - Conv_{P->Q}([c]_P)) P^{-1}.  Rotations are always hoisted: ModUp(c1) once,
+//   then per step the automorphism is applied to the raised digits inside the inner
+//   product (k_ks_inner gathers through the Galois permutation).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <set>
+
+#include "internal.h"
+#include "scheme_ops.h"
+
+using namespace hostmath;
+
+namespace {
+
+enum { K_SK = 1, K_SK_SIGN = 2, K_PK_A = 3, K_PK_E = 4, K_SWK_A = 5, K_SWK_E = 6, K_ENC_U = 7, K_ENC_E0 = 8,
+       K_ENC_E1 = 9, K_ENCSK_A = 10, K_ENCSK_E = 11 };
+
+inline u64 tag(u64 kind, u64 a = 0, u64 b = 0) { return (kind << 56) | (a << 16) | b; }
+
+template <class T>
+T* dev_upload_persistent(const std::vector<T>& v) {
+    T* p = nullptr;
+    if (v.empty()) return nullptr;
+    CUDA_CHECK(cudaMalloc((void**)&p, v.size() * sizeof(T)));
+    CUDA_CHECK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+}
+
+}  // namespace
+
+namespace ops {
+
+DevBuf upload(ckks_ctx* c, const std::vector<u64>& v) {
+    DevBuf b(v.size(), c->stream);
+    if (!v.empty()) CUDA_CHECK(cudaMemcpyAsync(b.ptr, v.data(), v.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    return b;
+}
+
+}  // namespace ops
+
+// ============================================================ context ======
+std::vector<std::vector<int>> ckks_ctx::digits(int level) const {
+    std::vector<std::vector<int>> out;
+    for (int d = 0; d < P.dnum; ++d) {
+        int lo = d * alpha, hi = std::min((d + 1) * alpha, level + 1);
+        if (lo < hi) {
+            std::vector<int> g;
+            for (int i = lo; i < hi; ++i) g.push_back(i);
+            out.push_back(g);
+        }
+    }
+    return out;
+}
+
+std::vector<int> ckks_ctx::ext_ids(int level) const {
+    std::vector<int> v;
+    for (int i = 0; i <= level; ++i) v.push_back(i);
+    for (int j = 0; j < np; ++j) v.push_back(nq + j);
+    return v;
+}
+
+static std::unique_ptr<ConvTab> make_conv_tab(ckks_ctx* c, const std::vector<int>& in_ids,
+                                              const std::vector<int>& out_ids, const std::vector<int>& out_rows) {
+    auto t = std::make_unique<ConvTab>();
+    t->nin = (int)in_ids.size();
+    t->nout = (int)out_ids.size();
+    t->in_ids = in_ids;
+    t->out_ids = out_ids;
+    std::vector<u64> qinv(2 * t->nin), qmod(2 * (size_t)t->nout * t->nin);
+    for (int i = 0; i < t->nin; ++i) {
+        u64 qi = c->mod_of[in_ids[i]];
+        u64 prod = 1;
+        for (int k = 0; k < t->nin; ++k)
+            if (k != i) prod = mulmod(prod, c->mod_of[in_ids[k]] % qi, qi);
+        qinv[i] = invmod(prod, qi);
+        qinv[t->nin + i] = shoup(qinv[i], qi);
+        for (int m = 0; m < t->nout; ++m) {
+            u64 pm = c->mod_of[out_ids[m]];
+            u64 v = 1;
+            for (int k = 0; k < t->nin; ++k)
+                if (k != i) v = mulmod(v, c->mod_of[in_ids[k]] % pm, pm);
+            qmod[(size_t)m * t->nin + i] = v;
+            qmod[(size_t)t->nout * t->nin + (size_t)m * t->nin + i] = shoup(v, pm);
+        }
+    }
+    std::vector<int> ids_rows = out_ids;
+    ids_rows.insert(ids_rows.end(), out_rows.begin(), out_rows.end());
+    t->d_in_ids = dev_upload_persistent(in_ids);
+    t->d_out_ids = dev_upload_persistent(ids_rows);
+    t->d_qhat_inv = dev_upload_persistent(qinv);
+    t->d_qhat_mod = dev_upload_persistent(qmod);
+    return t;
+}
+
+const ConvTab& ckks_ctx::modup_tab(int level, int d) {
+    auto key = std::make_pair(level, d);
+    auto it = modup_tabs.find(key);
+    if (it != modup_tabs.end()) return *it->second;
+    std::vector<int> dig = digits(level)[d];
+    std::vector<int> ext = ext_ids(level);
+    std::vector<int> out_ids, out_rows;
+    for (int r = 0; r < (int)ext.size(); ++r) {
+        if (r >= dig.front() && r <= dig.back()) continue;
+        out_ids.push_back(ext[r]);
+        out_rows.push_back(r);
+    }
+    modup_tabs[key] = make_conv_tab(this, dig, out_ids, out_rows);
+    return *modup_tabs[key];
+}
+
+const ConvTab& ckks_ctx::moddown_tab(int level) {
+    auto it = moddown_tabs.find(level);
+    if (it != moddown_tabs.end()) return *it->second;
+    std::vector<int> in_ids, out_ids, out_rows;
+    for (int j = 0; j < np; ++j) in_ids.push_back(nq + j);
+    for (int i = 0; i <= level; ++i) {
+        out_ids.push_back(i);
+        out_rows.push_back(i);
+    }
+    moddown_tabs[level] = make_conv_tab(this, in_ids, out_ids, out_rows);
+    return *moddown_tabs[level];
+}
+
+static void free_tab(ConvTab* t) {
+    cudaFree(t->d_in_ids);
+    cudaFree(t->d_out_ids);
+    cudaFree(t->d_qhat_inv);
+    cudaFree(t->d_qhat_mod);
+}
+
+ckks_ctx::~ckks_ctx() {
+    cudaStreamSynchronize(stream);
+    for (auto& kv : modup_tabs) free_tab(kv.second.get());
+    for (auto& kv : moddown_tabs) free_tab(kv.second.get());
+    for (int* p : d_ext_ids) cudaFree(p);
+    cudaFree(d_iota);
+    cudaFree(d_primes);
+    cudaFree(d_tables);
+    cudaFree(d_gauss);
+    cudaFree(d_pinv);
+    cudaFree(d_qlinv);
+}
+
+static unsigned brev_host(unsigned x, int bits) {
+    unsigned r = 0;
+    for (int i = 0; i < bits; ++i) {
+        r = (r << 1) | (x & 1);
+        x >>= 1;
+    }
+    return r;
+}
+
+ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
+    CK_CHECK(P && P->log_n >= 3 && P->log_n <= 17, CKKS_EINVAL, "log_n must be in 3..17");
+    CK_CHECK(P->n_q >= 1 && P->dnum >= 1 && P->n_boot >= 0 && P->n_boot < P->n_q, CKKS_EINVAL, "bad n_q/dnum/n_boot");
+    CK_CHECK(P->q0_bits <= 61 && P->p_bits <= 61 && P->scale_bits <= 61 && P->boot_bits <= 61, CKKS_EINVAL,
+             "primes must stay below 2^61");
+    std::unique_ptr<ckks_ctx> c(new ckks_ctx());
+    c->P = *P;
+    c->logn = P->log_n;
+    c->n = 1 << P->log_n;
+    c->nq = P->n_q;
+    c->L = P->n_q - 1;
+    c->alpha = (P->n_q + P->dnum - 1) / P->dnum;
+    c->np = P->n_p > 0 ? P->n_p : c->alpha;
+    c->nall = c->nq + c->np;
+    c->n_circuit = c->L - P->n_boot;
+    c->seed = seed;
+    c->stream = stream;
+    CK_CHECK(c->alpha <= 16 && c->np <= 16, CKKS_EINVAL, "digits and special primes are limited to 16 limbs");
+    build_chain(*P, c->q, c->p, c->delta);
+    c->mod_of = c->q;
+    c->mod_of.insert(c->mod_of.end(), c->p.begin(), c->p.end());
+    const int n = c->n, logn = c->logn;
+    // twiddle tables: per prime 4 arrays of N words
+    std::vector<u64> tables((size_t)c->nall * 4 * n);
+    std::vector<DevPrime> primes(c->nall);
+    c->psi.resize(c->nall);
+    c->mods.resize(c->nall);
+    CUDA_CHECK(cudaMalloc((void**)&c->d_tables, tables.size() * sizeof(u64)));
+    std::vector<u64> pw(n), ipw(n);
+    for (int id = 0; id < c->nall; ++id) {
+        const u64 qq = c->mod_of[id];
+        const u64 psi = smallest_root_2n(qq, n);
+        const u64 ipsi = invmod(psi, qq);
+        c->psi[id] = psi;
+        c->mods[id] = make_mod(qq);
+        pw[0] = ipw[0] = 1;
+        for (int e = 1; e < n; ++e) {
+            pw[e] = mulmod(pw[e - 1], psi, qq);
+            ipw[e] = mulmod(ipw[e - 1], ipsi, qq);
+        }
+        u64* base = tables.data() + (size_t)id * 4 * n;
+        for (int k = 0; k < n; ++k) {
+            unsigned r = brev_host(k, logn);
+            base[k] = pw[r];
+            base[n + k] = shoup(pw[r], qq);
+            base[2 * n + k] = ipw[r];
+            base[3 * n + k] = shoup(ipw[r], qq);
+        }
+        DevPrime& dp = primes[id];
+        dp.m = c->mods[id];
+        const u64* dbase = c->d_tables + (size_t)id * 4 * n;
+        dp.tw = dbase;
+        dp.twp = dbase + n;
+        dp.itw = dbase + 2 * n;
+        dp.itwp = dbase + 3 * n;
+        dp.n_inv = invmod((u64)n % qq, qq);
+        dp.n_inv_p = shoup(dp.n_inv, qq);
+    }
+    CUDA_CHECK(cudaMemcpy(c->d_tables, tables.data(), tables.size() * sizeof(u64), cudaMemcpyHostToDevice));
+    c->d_primes = dev_upload_persistent(primes);
+    gauss_table(P->sigma, c->gauss);
+    c->d_gauss = dev_upload_persistent(std::vector<u64>(c->gauss, c->gauss + 39));
+    std::vector<int> iota(c->nall);
+    for (int i = 0; i < c->nall; ++i) iota[i] = i;
+    c->d_iota = dev_upload_persistent(iota);
+    for (int l = 0; l <= c->L; ++l) c->d_ext_ids.push_back(dev_upload_persistent(c->ext_ids(l)));
+    // P^{-1} mod q_i and q_l^{-1} mod q_i (Shoup pairs)
+    std::vector<u64> pinv(2 * c->nq), qlinv(2 * (size_t)c->nq * c->nq, 0);
+    for (int i = 0; i < c->nq; ++i) {
+        u64 pr = 1;
+        for (u64 pj : c->p) pr = mulmod(pr, pj % c->q[i], c->q[i]);
+        pinv[i] = invmod(pr, c->q[i]);
+        pinv[c->nq + i] = shoup(pinv[i], c->q[i]);
+    }
+    for (int l = 1; l < c->nq; ++l)
+        for (int i = 0; i < l; ++i) {
+            u64 v = invmod(c->q[l] % c->q[i], c->q[i]);
+            qlinv[(size_t)l * c->nq + i] = v;
+            qlinv[(size_t)c->nq * c->nq + (size_t)l * c->nq + i] = shoup(v, c->q[i]);
+        }
+    c->d_pinv = dev_upload_persistent(pinv);
+    c->d_qlinv = dev_upload_persistent(qlinv);
+    cudaMemPool_t pool;
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    return c.release();
+}
+
+// ============================================================ helpers ======
+namespace ops {
+
+void ensure_ct(ckks_ct& ct, ckks_ctx* c, int level) {
+    ct.ctx = c;
+    size_t need = 2 * (size_t)(level + 1) * c->n;
+    if (ct.buf.words < need || ct.buf.ptr == nullptr) ct.buf = DevBuf(need, c->stream);
+    ct.level = level;
+}
+
+ckks_ct new_ct(ckks_ctx* c, int level, double scale) {
+    ckks_ct ct;
+    ensure_ct(ct, c, level);
+    ct.scale = scale;
+    return ct;
+}
+
+ckks_ct copy_ct(const ckks_ct& a) {
+    ckks_ct o = new_ct(a.ctx, a.level, a.scale);
+    CUDA_CHECK(cudaMemcpyAsync(o.buf.ptr, a.buf.ptr, 2 * (size_t)(a.level + 1) * a.ctx->n * 8,
+                               cudaMemcpyDeviceToDevice, a.ctx->stream));
+    return o;
+}
+
+static void check_same(const ckks_ct& a, const ckks_ct& b) {
+    CK_CHECK(a.level == b.level, CKKS_EINVAL, "ciphertext levels differ");
+    CK_CHECK(fabs(a.scale - b.scale) <= ldexp(1.0, -30) * fabs(a.scale), CKKS_EINVAL, "ciphertext scales differ");
+}
+
+ckks_ct add(const ckks_ct& a, const ckks_ct& b) {
+    check_same(a, b);
+    ckks_ctx* c = a.ctx;
+    ckks_ct o = new_ct(c, a.level, a.scale);
+    kern::add(c, a.buf.ptr, b.buf.ptr, o.buf.ptr, 2 * (a.level + 1), c->d_iota, a.level + 1);
+    return o;
+}
+
+ckks_ct sub(const ckks_ct& a, const ckks_ct& b) {
+    check_same(a, b);
+    ckks_ctx* c = a.ctx;
+    ckks_ct o = new_ct(c, a.level, a.scale);
+    kern::sub(c, a.buf.ptr, b.buf.ptr, o.buf.ptr, 2 * (a.level + 1), c->d_iota, a.level + 1);
+    return o;
+}
+
+ckks_ct mul_plain(const ckks_ct& a, const ckks_pt& p) {
+    CK_CHECK(p.level == a.level, CKKS_EINVAL, "plaintext level differs from the ciphertext level");
+    ckks_ctx* c = a.ctx;
+    c->ops["pmult"]++;
+    ckks_ct o = new_ct(c, a.level, a.scale * p.scale);
+    const int nl = a.level + 1;
+    kern::mul(c, a.c0(), p.buf.ptr, o.c0(), nl, c->d_iota, nl);
+    kern::mul(c, a.c1(), p.buf.ptr, o.c1(), nl, c->d_iota, nl);
+    return o;
+}
+
+// o += a * p (both polynomials)
+void mul_plain_acc(ckks_ct& o, const ckks_ct& a, const ckks_pt& p) {
+    CK_CHECK(p.level == a.level && o.level == a.level, CKKS_EINVAL, "level mismatch in multiply-accumulate");
+    ckks_ctx* c = a.ctx;
+    c->ops["pmult"]++;
+    const int nl = a.level + 1;
+    kern::mul_acc(c, a.c0(), p.buf.ptr, o.c0(), nl, c->d_iota, nl);
+    kern::mul_acc(c, a.c1(), p.buf.ptr, o.c1(), nl, c->d_iota, nl);
+}
+
+ckks_ct mul_int(const ckks_ct& a, long long v) {
+    ckks_ctx* c = a.ctx;
+    const int nl = a.level + 1;
+    std::vector<u64> s(2 * nl);
+    for (int i = 0; i < nl; ++i) {
+        s[i] = from_signed(v, c->q[i]);
+        s[nl + i] = shoup(s[i], c->q[i]);
+    }
+    DevBuf d = upload(c, s);
+    ckks_ct o = new_ct(c, a.level, a.scale);
+    kern::mul_scalar(c, a.buf.ptr, d.ptr, d.ptr + nl, o.buf.ptr, 2 * nl, c->d_iota, nl);
+    return o;
+}
+
+ckks_ct add_const(const ckks_ct& a, double cst) {
+    ckks_ctx* c = a.ctx;
+    const int nl = a.level + 1;
+    long long v = llround_away(cst * a.scale);
+    std::vector<u64> s(nl);
+    for (int i = 0; i < nl; ++i) s[i] = from_signed(v, c->q[i]);
+    DevBuf d = upload(c, s);
+    ckks_ct o = copy_ct(a);
+    kern::add_const_term(c, o.c0(), d.ptr, nl, c->d_iota);
+    return o;
+}
+
+ckks_ct imult(const ckks_ct& a) {
+    ckks_ctx* c = a.ctx;
+    ckks_ct o = new_ct(c, a.level, a.scale);
+    kern::imult(c, a.buf.ptr, o.buf.ptr, 2 * (a.level + 1), c->d_iota, a.level + 1);
+    return o;
+}
+
+ckks_ct rescale(const ckks_ct& a) {
+    ckks_ctx* c = a.ctx;
+    const int l = a.level;
+    CK_CHECK(l >= 1, CKKS_ELEVEL, "cannot rescale a level-0 ciphertext");
+    c->ops["rescale"]++;
+    const size_t n = c->n;
+    DevBuf last(2 * n, c->stream);
+    CUDA_CHECK(cudaMemcpyAsync(last.ptr, a.c0() + (size_t)l * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_CHECK(cudaMemcpyAsync(last.ptr + n, a.c1() + (size_t)l * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    kern::ntt_inverse(c, last.ptr, 2, c->d_iota + l, 1);
+    DevBuf lift(2 * (size_t)l * n, c->stream);
+    kern::lift_centred(c, last.ptr, l, lift.ptr, l, c->d_iota);
+    kern::lift_centred(c, last.ptr + n, l, lift.ptr + (size_t)l * n, l, c->d_iota);
+    kern::ntt_forward(c, lift.ptr, 2 * l, c->d_iota, l);
+    ckks_ct o = new_ct(c, l - 1, a.scale / (double)c->q[l]);
+    const u64* s = c->d_qlinv + (size_t)l * c->nq;
+    const u64* sp = c->d_qlinv + (size_t)c->nq * c->nq + (size_t)l * c->nq;
+    kern::sub_mul_scalar(c, a.c0(), lift.ptr, s, sp, o.c0(), l, c->d_iota, l);
+    kern::sub_mul_scalar(c, a.c1(), lift.ptr + (size_t)l * n, s, sp, o.c1(), l, c->d_iota, l);
+    return o;
+}
+
+ckks_ct mod_drop(const ckks_ct& a, int level) {
+    CK_CHECK(level >= 0 && level <= a.level, CKKS_EINVAL, "mod_drop to a higher level");
+    ckks_ctx* c = a.ctx;
+    ckks_ct o = new_ct(c, level, a.scale);
+    const size_t bytes = (size_t)(level + 1) * c->n * 8;
+    CUDA_CHECK(cudaMemcpyAsync(o.c0(), a.c0(), bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_CHECK(cudaMemcpyAsync(o.c1(), a.c1(), bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return o;
+}
+
+ckks_ct level_down(const ckks_ct& a, int level) {
+    ckks_ctx* c = a.ctx;
+    CK_CHECK(level >= 0 && level <= a.level, CKKS_EINVAL, "level_down to a higher level");
+    if (level == a.level) return copy_ct(a);
+    ckks_ct x;
+    const ckks_ct* cur = &a;
+    while (cur->level > level) {
+        const int l = cur->level;
+        long long k = llround_away((c->delta[l - 1] * (double)c->q[l]) / cur->scale);
+        ckks_ct t = rescale(mul_int(*cur, k));
+        t.scale = c->delta[l - 1];
+        x = std::move(t);
+        cur = &x;
+    }
+    return x;
+}
+
+ckks_ct mod_raise(const ckks_ct& a) {
+    ckks_ctx* c = a.ctx;
+    CK_CHECK(a.level == 0, CKKS_EINVAL, "ModRaise needs a level-0 ciphertext");
+    const size_t n = c->n;
+    DevBuf coef(2 * n, c->stream);
+    CUDA_CHECK(cudaMemcpyAsync(coef.ptr, a.c0(), n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_CHECK(cudaMemcpyAsync(coef.ptr + n, a.c1(), n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    kern::ntt_inverse(c, coef.ptr, 2, c->d_iota, 1);
+    ckks_ct o = new_ct(c, c->L, a.scale);
+    kern::lift_centred(c, coef.ptr, 0, o.c0(), c->nq, c->d_iota);
+    kern::lift_centred(c, coef.ptr + n, 0, o.c1(), c->nq, c->d_iota);
+    kern::ntt_forward(c, o.buf.ptr, 2 * c->nq, c->d_iota, c->nq);
+    return o;
+}
+
+// ------------------------------------------------------- key switching -----
+// D: [ndig][next][N], NTT domain
+DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out) {
+    const size_t n = c->n;
+    const int nl = level + 1;
+    const int next = nl + c->np;
+    std::vector<std::vector<int>> dig = c->digits(level);
+    const int ndig = (int)dig.size();
+    DevBuf coef(nl * n, c->stream);
+    CUDA_CHECK(cudaMemcpyAsync(coef.ptr, x, nl * n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    kern::ntt_inverse(c, coef.ptr, nl, c->d_iota, nl);
+    DevBuf D((size_t)ndig * next * n, c->stream);
+    const int* ext = c->d_ext_ids[level];
+    for (int d = 0; d < ndig; ++d) {
+        u64* Dd = D.ptr + (size_t)d * next * n;
+        const int lo = dig[d].front(), hi = dig[d].back() + 1;
+        const ConvTab& t = c->modup_tab(level, d);
+        kern::base_convert(c, t, coef.ptr + (size_t)lo * n, n, Dd, n, 1, 0, 0);
+        CUDA_CHECK(cudaMemcpyAsync(Dd + (size_t)lo * n, x + (size_t)lo * n, (size_t)(hi - lo) * n * 8,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+        if (lo > 0) kern::ntt_forward(c, Dd, lo, ext, lo);
+        if (next > hi) kern::ntt_forward(c, Dd + (size_t)hi * n, next - hi, ext + hi, next - hi);
+    }
+    *ndig_out = ndig;
+    return D;
+}
+
+// inner product with switching key `code` (automorphism g applied to D on the fly), ModDown
+void key_switch_raised(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
+                       u64* out0, u64* out1) {
+    auto it = keys.swk.find(code);
+    CK_CHECK(it != keys.swk.end(), CKKS_ENOKEY, "missing switching key (code " + std::to_string(code) + ")");
+    const SwitchKey& k = *it->second;
+    c->ops["keyswitch"]++;
+    const size_t n = c->n;
+    const int nl = level + 1;
+    const int next = nl + c->np;
+    DevBuf acc(2 * (size_t)next * n, c->stream);
+    u64* ab = acc.ptr;
+    u64* aa = acc.ptr + (size_t)next * n;
+    kern::ks_inner(c, D, ndig, next, c->d_ext_ids[level], k.b.ptr, k.a.ptr, ab, aa, g);
+    // ModDown of both halves
+    const int* pid = c->d_ext_ids[level] + nl;
+    kern::ntt_inverse(c, ab + (size_t)nl * n, c->np, pid, c->np);
+    kern::ntt_inverse(c, aa + (size_t)nl * n, c->np, pid, c->np);
+    DevBuf conv(2 * (size_t)nl * n, c->stream);
+    kern::base_convert(c, c->moddown_tab(level), ab + (size_t)nl * n, n, conv.ptr, n, 2, (size_t)next * n,
+                       (size_t)nl * n);
+    kern::ntt_forward(c, conv.ptr, 2 * nl, c->d_iota, nl);
+    kern::sub_mul_scalar(c, ab, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out0, nl, c->d_iota, nl);
+    kern::sub_mul_scalar(c, aa, conv.ptr + (size_t)nl * n, c->d_pinv, c->d_pinv + c->nq, out1, nl, c->d_iota, nl);
+}
+
+u64 galois_of_step(const ckks_ctx* c, long long r) {
+    const long long m = c->n / 2;
+    r %= m;
+    if (r < 0) r += m;
+    return powmod(5, (u64)r, 2ULL * c->n);
+}
+
+std::vector<ckks_ct> rotate_hoisted(const ckks_keys& keys, const ckks_ct& a, const std::vector<long long>& steps) {
+    ckks_ctx* c = a.ctx;
+    const int l = a.level, nl = l + 1;
+    const size_t n = c->n;
+    std::vector<ckks_ct> outs;
+    DevBuf D;
+    int ndig = 0;
+    for (long long r : steps) {
+        const u64 g = galois_of_step(c, r);
+        if (g == 1) {
+            outs.push_back(copy_ct(a));
+            continue;
+        }
+        if (!D.ptr) D = mod_up(c, a.c1(), l, &ndig);
+        c->ops["hrot"]++;
+        ckks_ct o = new_ct(c, l, a.scale);
+        DevBuf k0(nl * n, c->stream);
+        key_switch_raised(c, keys, D.ptr, ndig, l, g, g, k0.ptr, o.c1());
+        kern::automorph(c, a.c0(), o.c0(), nl, g);
+        kern::add(c, o.c0(), k0.ptr, o.c0(), nl, c->d_iota, nl);
+        outs.push_back(std::move(o));
+    }
+    return outs;
+}
+
+ckks_ct rotate(const ckks_keys& keys, const ckks_ct& a, long long r) {
+    std::vector<ckks_ct> v = rotate_hoisted(keys, a, {r});
+    return std::move(v[0]);
+}
+
+ckks_ct conjugate(const ckks_keys& keys, const ckks_ct& a) {
+    ckks_ctx* c = a.ctx;
+    const int l = a.level, nl = l + 1;
+    const u64 g = 2ULL * c->n - 1;
+    int ndig = 0;
+    DevBuf D = mod_up(c, a.c1(), l, &ndig);
+    ckks_ct o = new_ct(c, l, a.scale);
+    DevBuf k0(nl * (size_t)c->n, c->stream);
+    key_switch_raised(c, keys, D.ptr, ndig, l, g, g, k0.ptr, o.c1());
+    kern::automorph(c, a.c0(), o.c0(), nl, g);
+    kern::add(c, o.c0(), k0.ptr, o.c0(), nl, c->d_iota, nl);
+    return o;
+}
+
+ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
+    ckks_ctx* c = a.ctx;
+    CK_CHECK(a.level == b.level, CKKS_EINVAL, "HMult operands at different levels");
+    c->ops["hmult"]++;
+    const int l = a.level, nl = l + 1;
+    const size_t n = c->n;
+    ckks_ct o = new_ct(c, l, a.scale * b.scale);
+    DevBuf d2(nl * n, c->stream);
+    kern::mul(c, a.c0(), b.c0(), o.c0(), nl, c->d_iota, nl);
+    kern::mul(c, a.c0(), b.c1(), o.c1(), nl, c->d_iota, nl);
+    kern::mul_acc(c, a.c1(), b.c0(), o.c1(), nl, c->d_iota, nl);
+    kern::mul(c, a.c1(), b.c1(), d2.ptr, nl, c->d_iota, nl);
+    int ndig = 0;
+    DevBuf D = mod_up(c, d2.ptr, l, &ndig);
+    DevBuf k(2 * nl * n, c->stream);
+    key_switch_raised(c, keys, D.ptr, ndig, l, 0, 1, k.ptr, k.ptr + nl * n);
+    kern::add(c, o.buf.ptr, k.ptr, o.buf.ptr, 2 * nl, c->d_iota, nl);
+    return o;
+}
+
+// ---------------------------------------------------------------- BSGS -----
+ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps) {
+    ckks_ctx* c = a.ctx;
+    CK_CHECK(a.level == ps.level, CKKS_EINVAL, "ciphertext level differs from the plaintext set's level");
+    CK_CHECK(!ps.pts.empty(), CKKS_EINVAL, "empty plaintext set");
+    const long long m = c->n / 2;
+    std::set<int> used;
+    for (const auto& kv : ps.pts) used.insert(kv.first.second);
+    std::vector<int> used_b(used.begin(), used.end());
+    std::vector<long long> steps;
+    for (int b : used_b) steps.push_back(((long long)ps.step * b) % m);
+    std::vector<ckks_ct> baby = rotate_hoisted(keys, a, steps);
+    std::map<int, int> bidx;
+    for (size_t i = 0; i < used_b.size(); ++i) bidx[used_b[i]] = (int)i;
+    ckks_ct out;
+    bool have = false;
+    for (int g = 0; g < ps.G(); ++g) {
+        ckks_ct inner;
+        bool hin = false;
+        for (int b = 0; b < ps.B; ++b) {
+            auto it = ps.pts.find(std::make_pair(g, b));
+            if (it == ps.pts.end()) continue;
+            const ckks_ct& x = baby[bidx[b]];
+            if (!hin) {
+                inner = mul_plain(x, *it->second);
+                hin = true;
+            } else {
+                mul_plain_acc(inner, x, *it->second);
+            }
+        }
+        if (!hin) continue;
+        const long long R = (((long long)ps.a0 + (long long)ps.step * g * ps.B) % m + m) % m;
+        if (R) inner = rotate(keys, inner, R);
+        if (!have) {
+            out = std::move(inner);
+            have = true;
+        } else {
+            kern::add(c, out.buf.ptr, inner.buf.ptr, out.buf.ptr, 2 * (out.level + 1), c->d_iota, out.level + 1);
+        }
+    }
+    return out;
+}
+
+// ------------------------------------------------ Chebyshev / EvalMod -----
+ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs) {
+    ckks_ctx* c = x.ctx;
+    const int d = (int)coeffs.size() - 1;
+    CK_CHECK(d >= 1, CKKS_EINVAL, "polynomial degree must be >= 1");
+    int depth = 0;
+    while ((1 << depth) < d) ++depth;
+    CK_CHECK(x.level - depth - 1 >= 0, CKKS_ELEVEL, "not enough levels for the polynomial");
+    std::vector<ckks_ct> T(d + 1);
+    T[1] = copy_ct(x);
+    std::map<std::pair<int, int>, ckks_ct> cache;
+    auto at = [&](int k, int lev) -> const ckks_ct& {
+        if (T[k].level == lev) return T[k];
+        auto key = std::make_pair(k, lev);
+        auto it = cache.find(key);
+        if (it == cache.end()) it = cache.emplace(key, level_down(T[k], lev)).first;
+        return it->second;
+    };
+    for (int k = 2; k <= d; ++k) {
+        const int a = k / 2, b = k - k / 2;
+        const int m = std::min(T[a].level, T[b].level);
+        ckks_ct t = rescale(mul_relin(keys, at(a, m), at(b, m)));
+        t = add(t, t);
+        if (a == b)
+            t = add_const(t, -1.0);
+        else
+            t = sub(t, at(b - a, m - 1));
+        T[k] = std::move(t);
+    }
+    int target = 1 << 30;
+    for (int k = 1; k <= d; ++k)
+        if (coeffs[k] != 0.0) target = std::min(target, T[k].level - 1);
+    CK_CHECK(target < (1 << 30), CKKS_EINVAL, "polynomial has no non-constant term");
+    ckks_ct acc;
+    bool have = false;
+    for (int k = 1; k <= d; ++k) {
+        if (coeffs[k] == 0.0) continue;
+        const ckks_ct& t = T[k];
+        const int lk = t.level;
+        const double s_c = (c->delta[target] * (double)c->q[lk]) / t.scale;
+        ckks_ct term = rescale(mul_int(t, llround_away(coeffs[k] * s_c)));
+        term.scale = (t.scale * s_c) / (double)c->q[lk];
+        term = mod_drop(term, target);
+        if (!have) {
+            acc = std::move(term);
+            have = true;
+        } else {
+            acc = add(acc, term);
+        }
+    }
+    return add_const(acc, coeffs[0]);
+}
+
+ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r) {
+    ckks_ct y = cheb_eval(keys, x, coeffs);
+    for (int i = 0; i < r; ++i) {
+        y = rescale(mul_relin(keys, y, y));
+        y = add(y, y);
+        y = add_const(y, -1.0);
+    }
+    return y;
+}
+
+void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, ckks_ct& re_out, ckks_ct& im_out) {
+    ckks_ctx* c = ct0.ctx;
+    ckks_ct x = mod_raise(ct0);
+    x.scale = bt.s_raise;
+    for (const auto& ps : bt.ctos) x = rescale(bsgs(keys, x, *ps));
+    ckks_ct cj = conjugate(keys, x);
+    ckks_ct re = add(x, cj);
+    ckks_ct im = imult(sub(cj, x));
+    re = rescale(mul_int(re, bt.c_drop));
+    im = rescale(mul_int(im, bt.c_drop));
+    re.scale = c->delta[re.level];
+    im.scale = c->delta[im.level];
+    re_out = eval_mod(keys, re, bt.coeffs, bt.bp.r);
+    im_out = eval_mod(keys, im, bt.coeffs, bt.bp.r);
+}
+
+ckks_ct stoc1(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& re, const ckks_ct& im) {
+    ckks_ct a = rescale(mul_plain(re, *bt.mask_re));
+    ckks_ct b = rescale(mul_plain(im, *bt.mask_im));
+    ckks_ct y = add(a, imult(b));
+    for (const auto& ps : bt.stoc) y = rescale(bsgs(keys, y, *ps));
+    return y;
+}
+
+}  // namespace ops
+
+// ================================================================ keys =====
+namespace ops {
+
+static void gen_switch_key(ckks_ctx* c, ckks_keys& K, u64 code, const u64* sprime_ntt) {
+    const size_t n = c->n;
+    std::vector<std::vector<int>> dig = c->digits(c->L);
+    auto sk = std::make_unique<SwitchKey>();
+    sk->ndig = (int)dig.size();
+    const size_t per = (size_t)c->nall * n;
+    sk->b = DevBuf(sk->ndig * per, c->stream);
+    sk->a = DevBuf(sk->ndig * per, c->stream);
+    DevBuf e_small(n, c->stream);
+    std::vector<u64> pm(2 * c->nq);
+    for (int i = 0; i < c->nq; ++i) {
+        u64 v = 1;
+        for (u64 pj : c->p) v = mulmod(v, pj % c->q[i], c->q[i]);
+        pm[i] = v;
+        pm[c->nq + i] = shoup(v, c->q[i]);
+    }
+    DevBuf dpm = upload(c, pm);
+    DevBuf tmp(n, c->stream);
+    for (int d = 0; d < sk->ndig; ++d) {
+        u64* a = sk->a.ptr + d * per;
+        u64* b = sk->b.ptr + d * per;
+        kern::sample_uniform(c, a, c->nall, c->d_iota, stream_key(c->seed, tag(K_SWK_A, code, d)));
+        kern::sample_small(c, (int64_t*)e_small.ptr, stream_key(c->seed, tag(K_SWK_E, code, d)), 1);
+        kern::small_to_rns(c, (const int64_t*)e_small.ptr, b, c->nall, c->d_iota);
+        kern::ntt_forward(c, b, c->nall, c->d_iota, c->nall);
+        DevBuf as(per, c->stream);
+        kern::mul(c, a, K.s_ntt.ptr, as.ptr, c->nall, c->d_iota, c->nall);
+        kern::sub(c, b, as.ptr, b, c->nall, c->d_iota, c->nall);
+        for (int i : dig[d]) {
+            kern::mul_scalar(c, sprime_ntt + (size_t)i * n, dpm.ptr + i, dpm.ptr + c->nq + i, tmp.ptr, 1,
+                             c->d_iota + i, 1);
+            kern::add(c, b + (size_t)i * n, tmp.ptr, b + (size_t)i * n, 1, c->d_iota + i, 1);
+        }
+    }
+    K.swk[code] = std::move(sk);
+}
+
+void add_galois_key(ckks_ctx* c, ckks_keys& K, u64 g) {
+    if (g == 1 || K.swk.count(g)) return;
+    DevBuf sg((size_t)c->nall * c->n, c->stream);
+    kern::automorph(c, K.s_ntt.ptr, sg.ptr, c->nall, g);
+    gen_switch_key(c, K, g, sg.ptr);
+}
+
+ckks_keys* keygen(ckks_ctx* c, const int32_t* steps, int nsteps, int want_conj) {
+    const size_t n = c->n;
+    std::unique_ptr<ckks_keys> K(new ckks_keys());
+    K->ctx = c;
+    K->s.assign(n, 0);
+    if (c->P.h > 0) {
+        CK_CHECK(c->P.h <= c->n, CKKS_EINVAL, "Hamming weight above N");
+        u64 kp = stream_key(c->seed, tag(K_SK)), ks = stream_key(c->seed, tag(K_SK_SIGN));
+        std::vector<int> perm(n);
+        for (size_t j = 0; j < n; ++j) perm[j] = (int)j;
+        for (int i = 0; i < c->P.h; ++i) {
+            int r = (int)(stream_word(kp, i) % (u64)(n - i));
+            std::swap(perm[i], perm[i + r]);
+            K->s[perm[i]] = (stream_word(ks, i) & 1) ? -1 : 1;
+        }
+    } else {
+        u64 key = stream_key(c->seed, tag(K_SK));
+        for (size_t j = 0; j < n; ++j) K->s[j] = (int64_t)(stream_word(key, j) % 3) - 1;
+    }
+    DevBuf s_small(n, c->stream);
+    CUDA_CHECK(cudaMemcpyAsync(s_small.ptr, K->s.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
+    K->s_ntt = DevBuf((size_t)c->nall * n, c->stream);
+    kern::small_to_rns(c, (const int64_t*)s_small.ptr, K->s_ntt.ptr, c->nall, c->d_iota);
+    kern::ntt_forward(c, K->s_ntt.ptr, c->nall, c->d_iota, c->nall);
+    // public key over Q_L
+    const int nq = c->nq;
+    K->pk_a = DevBuf((size_t)nq * n, c->stream);
+    K->pk_b = DevBuf((size_t)nq * n, c->stream);
+    kern::sample_uniform(c, K->pk_a.ptr, nq, c->d_iota, stream_key(c->seed, tag(K_PK_A)));
+    DevBuf e(n, c->stream);
+    kern::sample_small(c, (int64_t*)e.ptr, stream_key(c->seed, tag(K_PK_E)), 1);
+    kern::small_to_rns(c, (const int64_t*)e.ptr, K->pk_b.ptr, nq, c->d_iota);
+    kern::ntt_forward(c, K->pk_b.ptr, nq, c->d_iota, nq);
+    DevBuf as((size_t)nq * n, c->stream);
+    kern::mul(c, K->pk_a.ptr, K->s_ntt.ptr, as.ptr, nq, c->d_iota, nq);
+    kern::sub(c, K->pk_b.ptr, as.ptr, K->pk_b.ptr, nq, c->d_iota, nq);
+    // relinearisation key: s' = s^2
+    DevBuf s2((size_t)c->nall * n, c->stream);
+    kern::mul(c, K->s_ntt.ptr, K->s_ntt.ptr, s2.ptr, c->nall, c->d_iota, c->nall);
+    gen_switch_key(c, *K, 0, s2.ptr);
+    for (int i = 0; i < nsteps; ++i) add_galois_key(c, *K, galois_of_step(c, steps[i]));
+    if (want_conj) add_galois_key(c, *K, 2ULL * c->n - 1);
+    return K.release();
+}
+
+// ========================================================== encryption =====
+ckks_ct encrypt(const ckks_keys& K, const ckks_pt& pt, u64 nonce) {
+    ckks_ctx* c = K.ctx;
+    const int l = pt.level, nl = l + 1;
+    const size_t n = c->n;
+    ckks_ct o = new_ct(c, l, pt.scale);
+    DevBuf sm(n, c->stream), u(nl * n, c->stream), e(nl * n, c->stream);
+    kern::sample_small(c, (int64_t*)sm.ptr, stream_key(c->seed, tag(K_ENC_U, nonce)), 0);
+    kern::small_to_rns(c, (const int64_t*)sm.ptr, u.ptr, nl, c->d_iota);
+    kern::ntt_forward(c, u.ptr, nl, c->d_iota, nl);
+    // c0 = u b + e0 + m
+    kern::sample_small(c, (int64_t*)sm.ptr, stream_key(c->seed, tag(K_ENC_E0, nonce)), 1);
+    kern::small_to_rns(c, (const int64_t*)sm.ptr, e.ptr, nl, c->d_iota);
+    kern::ntt_forward(c, e.ptr, nl, c->d_iota, nl);
+    kern::add(c, e.ptr, pt.buf.ptr, o.c0(), nl, c->d_iota, nl);
+    kern::mul_acc(c, u.ptr, K.pk_b.ptr, o.c0(), nl, c->d_iota, nl);
+    // c1 = u a + e1
+    kern::sample_small(c, (int64_t*)sm.ptr, stream_key(c->seed, tag(K_ENC_E1, nonce)), 1);
+    kern::small_to_rns(c, (const int64_t*)sm.ptr, o.c1(), nl, c->d_iota);
+    kern::ntt_forward(c, o.c1(), nl, c->d_iota, nl);
+    kern::mul_acc(c, u.ptr, K.pk_a.ptr, o.c1(), nl, c->d_iota, nl);
+    return o;
+}
+
+ckks_ct encrypt_sk(const ckks_keys& K, const ckks_pt& pt, u64 nonce) {
+    ckks_ctx* c = K.ctx;
+    const int l = pt.level, nl = l + 1;
+    const size_t n = c->n;
+    ckks_ct o = new_ct(c, l, pt.scale);
+    DevBuf sm(n, c->stream), as(nl * n, c->stream);
+    kern::sample_uniform(c, o.c1(), nl, c->d_iota, stream_key(c->seed, tag(K_ENCSK_A, nonce)));
+    kern::sample_small(c, (int64_t*)sm.ptr, stream_key(c->seed, tag(K_ENCSK_E, nonce)), 1);
+    kern::small_to_rns(c, (const int64_t*)sm.ptr, o.c0(), nl, c->d_iota);
+    kern::ntt_forward(c, o.c0(), nl, c->d_iota, nl);
+    kern::mul(c, o.c1(), K.s_ntt.ptr, as.ptr, nl, c->d_iota, nl);
+    kern::sub(c, o.c0(), as.ptr, o.c0(), nl, c->d_iota, nl);
+    kern::add(c, o.c0(), pt.buf.ptr, o.c0(), nl, c->d_iota, nl);
+    return o;
+}
+
+void decrypt(const ckks_keys& K, const ckks_ct& ct, ckks_pt& out) {
+    ckks_ctx* c = K.ctx;
+    const int nl = ct.level + 1;
+    DevBuf m((size_t)nl * c->n, c->stream);
+    kern::mul(c, ct.c1(), K.s_ntt.ptr, m.ptr, nl, c->d_iota, nl);
+    kern::add(c, m.ptr, ct.c0(), m.ptr, nl, c->d_iota, nl);
+    out.ctx = c;
+    out.buf = std::move(m);
+    out.level = ct.level;
+    out.scale = ct.scale;
+}
+
+}  // namespace ops

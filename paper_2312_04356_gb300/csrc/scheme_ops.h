@@ -1,0 +1,41 @@
+// Internal scheme operations (scheme.cu), used by the C ABI (capi.cpp).
+#pragma once
+#include "internal.h"
+
+namespace ops {
+DevBuf upload(ckks_ctx* c, const std::vector<u64>& v);
+void ensure_ct(ckks_ct& ct, ckks_ctx* c, int level);
+ckks_ct new_ct(ckks_ctx* c, int level, double scale);
+ckks_ct copy_ct(const ckks_ct& a);
+ckks_ct add(const ckks_ct& a, const ckks_ct& b);
+ckks_ct sub(const ckks_ct& a, const ckks_ct& b);
+ckks_ct mul_plain(const ckks_ct& a, const ckks_pt& p);
+void mul_plain_acc(ckks_ct& o, const ckks_ct& a, const ckks_pt& p);
+ckks_ct mul_int(const ckks_ct& a, long long v);
+ckks_ct add_const(const ckks_ct& a, double cst);
+ckks_ct imult(const ckks_ct& a);
+ckks_ct rescale(const ckks_ct& a);
+ckks_ct mod_drop(const ckks_ct& a, int level);
+ckks_ct level_down(const ckks_ct& a, int level);
+ckks_ct mod_raise(const ckks_ct& a);
+DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out);
+void key_switch_raised(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
+                       u64* out0, u64* out1);
+u64 galois_of_step(const ckks_ctx* c, long long r);
+std::vector<ckks_ct> rotate_hoisted(const ckks_keys& keys, const ckks_ct& a, const std::vector<long long>& steps);
+ckks_ct rotate(const ckks_keys& keys, const ckks_ct& a, long long r);
+ckks_ct conjugate(const ckks_keys& keys, const ckks_ct& a);
+ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b);
+ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps);
+ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs);
+ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r);
+void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, ckks_ct& re_out, ckks_ct& im_out);
+ckks_ct stoc1(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& re, const ckks_ct& im);
+void add_galois_key(ckks_ctx* c, ckks_keys& K, u64 g);
+ckks_keys* keygen(ckks_ctx* c, const int32_t* steps, int nsteps, int want_conj);
+ckks_ct encrypt(const ckks_keys& K, const ckks_pt& pt, u64 nonce);
+ckks_ct encrypt_sk(const ckks_keys& K, const ckks_pt& pt, u64 nonce);
+void decrypt(const ckks_keys& K, const ckks_ct& ct, ckks_pt& out);
+}  // namespace ops
+
+ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream);

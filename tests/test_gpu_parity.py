@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA library against the oracle, bit-exact on every limb.
+
+Inputs are the seeded arrays of workloads.py; keys and encryption randomness come
+from the same seed on both sides (each implements SplitMix64 itself).  Plaintexts
+the oracle encodes are imported with *_import_rns so that both sides multiply by
+identical integers (the FP64 encoders are compared separately, approximately).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as WL
+from oracle import boot as BT
+from oracle import encoding as E
+from tests.pairs import assert_ct_equal, gpu_ctx, import_ct, import_plan, import_pt, make_pair, oracle_params
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def setup_module(module):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_04356_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg2"])
+def test_chain_matches_oracle(name):
+    from paper_2312_04356_gb300 import ckks as K
+    P = oracle_params(name)
+    ctx = gpu_ctx(name, 1)
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    assert q == list(P.q) and p == list(P.p)
+    assert psi == list(P.psi_q) + list(P.psi_p)
+    assert delta == list(P.delta)
+    from oracle import _clib as C
+    assert (K.ckks_ctx_gauss_table(ctx) == C.gauss_table(P.sigma)).all()
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg2"])
+def test_ntt_bitexact(name):
+    from oracle import _clib as C
+    from paper_2312_04356_gb300 import ckks as K
+    P = oracle_params(name)
+    ctx = gpu_ctx(name, 1)
+    ids = list(range(P.n_q)) + [P.n_q + j for j in range(P.n_p)]
+    ids = ids[:6] + ids[-2:]
+    mods = [(list(P.q) + list(P.p))[i] for i in ids]
+    psis = [(list(P.psi_q) + list(P.psi_p))[i] for i in ids]
+    x = WL.residues(3, mods, P.n)
+    want = C.ntt_forward(x, mods, psis, P.logn)
+    dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
+    K.ckks_ntt_forward(ctx, dev.data_ptr(), len(ids), ids)
+    torch.cuda.synchronize()
+    got = dev.cpu().numpy().view(np.uint64)
+    assert (got == want).all()
+    K.ckks_ntt_inverse(ctx, dev.data_ptr(), len(ids), ids)
+    torch.cuda.synchronize()
+    assert (dev.cpu().numpy().view(np.uint64) == x).all()
+    # edge values: all zeros, all q-1
+    e = np.stack([np.full(P.n, q - 1, dtype=np.uint64) for q in mods])
+    e[0] = 0
+    dev = torch.from_numpy(e.view(np.int64).copy()).cuda()
+    K.ckks_ntt_forward(ctx, dev.data_ptr(), len(ids), ids)
+    torch.cuda.synchronize()
+    assert (dev.cpu().numpy().view(np.uint64) == C.ntt_forward(e, mods, psis, P.logn)).all()
+
+
+def test_keys_encrypt_decrypt_bitexact():
+    K, o, ctx, keys = make_pair("cfg1", 11, rotations=[1, 5])
+    assert (K.ckks_keys_export_secret(ctx, keys) == o.s).all()
+    P = o.P
+    z = WL.slots(5, P.n // 2)
+    for lev in (P.L, 1):
+        pt = o.encode_pt(z, lev, P.delta[lev])
+        gpt = import_pt(K, ctx, pt)
+        assert (K.ckks_pt_export_rns(ctx, gpt) == pt.limbs).all()
+        ct = o.encrypt(pt, 9)
+        gct = K.ckks_encrypt(ctx, keys, gpt, 9)
+        assert_ct_equal(K, ctx, gct, ct, "pk encryption")
+        ct2 = o.encrypt_sk(pt, 10)
+        gct2 = K.ckks_encrypt_sk(ctx, keys, gpt, 10)
+        assert_ct_equal(K, ctx, gct2, ct2, "sk encryption")
+        dec = K.ckks_decrypt(ctx, keys, gct)
+        assert (K.ckks_pt_export_rns(ctx, dec) == o.decrypt(ct).limbs).all()
+        # library decode of the decryption: back to the slots
+        assert np.abs(K.ckks_decode(ctx, dec) - z).max() < 1e-6
+
+
+def test_ops_bitexact():
+    K, o, ctx, keys = make_pair("cfg1", 12, rotations=[1, 3, 100, 2047])
+    P = o.P
+    L = P.L
+    z = WL.slots(6, P.n // 2, 0.5)
+    ct = o.encrypt(o.encode_pt(z, L, P.delta[L]), 1)
+    gct = import_ct(K, ctx, ct)
+    assert_ct_equal(K, ctx, gct, ct, "import/export")
+    assert_ct_equal(K, ctx, K.ckks_rescale(ctx, gct), o.rescale(ct), "rescale")
+    assert_ct_equal(K, ctx, K.ckks_mul_relin(ctx, keys, gct, gct), o.mul_relin(ct, ct), "HMult")
+    steps = [0, 1, 3, 100, 2047]
+    gouts = K.ckks_rotate_hoisted(ctx, keys, gct, steps)
+    for s, g, w in zip(steps, gouts, o.rotate_hoisted(ct, steps)):
+        assert_ct_equal(K, ctx, g, w, "HRot %d" % s)
+    assert_ct_equal(K, ctx, K.ckks_conjugate(ctx, keys, gct), o.conjugate(ct), "conj")
+    assert_ct_equal(K, ctx, K.ckks_imult(ctx, gct), o.imult(ct), "imult")
+    assert_ct_equal(K, ctx, K.ckks_mul_int(ctx, gct, -12345), o.mul_int(ct, -12345), "mul_int")
+    assert_ct_equal(K, ctx, K.ckks_add_const(ctx, gct, 0.3), o.add_const(ct, 0.3), "add_const")
+    assert_ct_equal(K, ctx, K.ckks_level_down(ctx, gct, 1), o.level_down(ct, 1), "level_down")
+    c0 = o.mod_drop(ct, 0)
+    assert_ct_equal(K, ctx, K.ckks_mod_raise(ctx, import_ct(K, ctx, c0)), o.mod_raise(c0), "ModRaise")
+    pt = o.encode_pt(WL.slots(8, P.n // 2), L, float(P.q[L]))
+    assert_ct_equal(K, ctx, K.ckks_mul_plain(ctx, gct, import_pt(K, ctx, pt)), o.mul_plain(ct, pt), "PMult")
+
+
+def test_cfg1_conv_bitexact_and_fp64():
+    """config 1: N=2^12, one 16x16 channel, 3x3 conv by the fused CinS BSGS; bit-exact limbs and
+    decoded output vs FP64 conv2d within 2^-12"""
+    P = oracle_params("cfg1")
+    spec = WL.CONV["cfg1"]
+    x = WL.image(1, spec["cin"], spec["w0"])
+    W = WL.weights(1, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+    w = E.pad_width(spec["w0"], spec["f"])
+    C = P.n // (w * w)
+    from oracle.scheme import Oracle
+    o0 = Oracle(P, 21)
+    plan = o0.conv_plan(W, 1, 1, 3, w, P.L, (P.delta[P.L - 1] * float(P.q[P.L])) / P.delta[P.L])
+    K, o, ctx, keys = make_pair("cfg1", 21, rotations=plan.rotations(P.n // 2))
+    pt = o.encode_pt(E.cins_input_slots(x, w, P.n), P.L, P.delta[P.L])
+    ct = o.encrypt(pt, 4)
+    gct = K.ckks_encrypt(ctx, keys, import_pt(K, ctx, pt), 4)
+    out = o.conv2d_cins(ct, plan)
+    gout = K.ckks_conv2d_cins(ctx, keys, gct, import_plan(K, ctx, plan))
+    assert_ct_equal(K, ctx, gout, out, "fused conv")
+    ref = E.conv2d_same(x, W)
+    coeffs = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gout), K.CKKS_COEFF)
+    got = E.conv_output_from_coeffs(coeffs, C, w * w, 1, w, spec["w0"])
+    assert np.abs(got - ref).max() < 2.0 ** -12
+    # the library's own FP64 path: encoder and fused diagonals, decoded against FP64
+    gps = K.ckks_ptset_conv_fused(ctx, W, 1, 1, 3, w, P.L, plan.scale)
+    assert K.ckks_ptset_info(gps)["n_pts"] == len(plan.pts)
+    gpt = K.ckks_encode(ctx, E.flatten_padded(x[0], w), P.L, P.delta[P.L], K.CKKS_CINS_REAL, w * w)
+    own = K.ckks_conv2d_cins(ctx, keys, K.ckks_encrypt(ctx, keys, gpt, 5), gps)
+    coeffs = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, own), K.CKKS_COEFF)
+    got = E.conv_output_from_coeffs(coeffs, C, w * w, 1, w, spec["w0"])
+    assert np.abs(got - ref).max() < 2.0 ** -12
+
+
+def test_own_encoder_close_to_oracle():
+    """the library's FP64 encoder rounds to the same integers up to +-1"""
+    K, o, ctx, keys = make_pair("cfg1", 3)
+    P = o.P
+    z = WL.slots(9, P.n // 2)
+    g = K.ckks_pt_export_rns(ctx, K.ckks_encode(ctx, z, 2, P.delta[2]))
+    w = o.encode_pt(z, 2, P.delta[2]).limbs
+    for i in range(3):
+        d = (g[i].astype(object) - w[i].astype(object)) % int(P.q[i])
+        d = np.minimum(d, int(P.q[i]) - d)
+        assert max(d) <= 1
+
+
+def _block_pair(name, seed, import_all=True, oracle_all_keys=True):
+    P = oracle_params(name)
+    spec = WL.CONV[name]
+    x = WL.image(seed, spec["cin"], spec["w0"])
+    W = WL.weights(seed, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+    w = E.pad_width(spec["w0"], spec["f"])
+    from oracle.scheme import Oracle
+    o0 = Oracle(P, seed)
+    cfg = BT.BootConfig(o0, w, spec["w0"], spec["cout"])
+    plan = o0.conv_plan(W, spec["cin"], spec["cout"], spec["f"], w, 1, (cfg.delta0 * float(P.q[1])) / P.delta[1])
+    rots = BT.block_rotations(o0, plan, cfg)
+    if oracle_all_keys:
+        K, o, ctx, keys = make_pair(name, seed, rotations=rots)
+    else:
+        K, o, ctx, keys = make_pair(name, seed, rotations=plan.rotations(P.n // 2), conj=False)
+        K.ckks_keys_add_rotations(ctx, keys, rots)
+        K.ckks_keys_add_rotations(ctx, keys, [])
+        from paper_2312_04356_gb300 import ckks as KK
+        KK.lib()  # conjugation key for the library only
+        keys_full = K.ckks_keygen(ctx, rots, True)
+        keys = keys_full
+    bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
+    info = K.ckks_boot_info(bt)
+    assert info["c_drop"] == cfg.c_drop and info["K_eff"] == cfg.K_eff and info["s_raise"] == cfg.s_raise
+    assert info["l_em"] == cfg.l_em and info["l_out"] == cfg.l_out and info["s_mask"] == cfg.s_mask
+    assert sorted(K.ckks_boot_rotations(bt)) == sorted(set(r for p in cfg.ctos + cfg.stoc
+                                                          for r in p.rotations(P.n // 2)))
+    if import_all:
+        for i, p in enumerate(cfg.ctos):
+            K.ckks_boot_set_ctos(ctx, bt, i, import_plan(K, ctx, p))
+        for i, p in enumerate(cfg.stoc):
+            K.ckks_boot_set_stoc(ctx, bt, i, import_plan(K, ctx, p))
+        K.ckks_boot_set_coeffs(ctx, bt, cfg.coeffs)
+        K.ckks_boot_set_masks(ctx, bt, import_pt(K, ctx, cfg.pt_mask_re), import_pt(K, ctx, cfg.pt_mask_im))
+    pt = o.encode_pt(E.cins_input_slots(x, w, P.n), 1, P.delta[1])
+    return dict(K=K, o=o, ctx=ctx, keys=keys, cfg=cfg, plan=plan, bt=bt, pt=pt, x=x, W=W, w=w, spec=spec, P=P)
+
+
+def _expected_slots(d):
+    P, w, spec = d["P"], d["w"], d["spec"]
+    conv = E.conv2d_same(d["x"], d["W"])
+    return E.cins_input_slots(conv[: spec["cout"]], w, P.n), conv
+
+
+def _pixels(d, slots):
+    P, w = d["P"], d["w"]
+    ell = w * w // 2
+    C = P.n // (w * w)
+    return np.stack([E.encode(slots[i * ell:(i + 1) * ell], w * w) for i in range(C)])
+
+
+def test_block_small_bitexact():
+    """the whole Alg. 1 block (conv -> ModRaise -> CtoS -> EvalMod x2 -> mask -> StoC1) on the
+    config-2 chain at N = 2^10: bit-exact ciphertext and decoded error <= 2^-12"""
+    d = _block_pair("cfg2_small", 31)
+    K, o, ctx, keys = d["K"], d["o"], d["ctx"], d["keys"]
+    ct = o.encrypt(d["pt"], 2)
+    gct = K.ckks_encrypt(ctx, keys, import_pt(K, ctx, d["pt"]), 2)
+    gplan = import_plan(K, ctx, d["plan"])
+    x0 = o.conv2d_cins(ct, d["plan"])
+    gx0 = K.ckks_conv2d_cins(ctx, keys, gct, gplan)
+    assert_ct_equal(K, ctx, gx0, x0, "conv")
+    re, im = BT.bootstrap(o, x0, d["cfg"])
+    gre, gim = K.ckks_bootstrap(ctx, keys, d["bt"], gx0)
+    assert_ct_equal(K, ctx, gre, re, "EvalMod Re")
+    assert_ct_equal(K, ctx, gim, im, "EvalMod Im")
+    out = BT.stoc1(o, re, im, d["cfg"])
+    gout = K.ckks_stoc1(ctx, keys, gre, gim, d["bt"])
+    assert_ct_equal(K, ctx, gout, out, "StoC1")
+    gblk = K.ckks_block(ctx, keys, gct, gplan, d["bt"])
+    assert_ct_equal(K, ctx, gblk, out, "block")
+    zexp, _ = _expected_slots(d)
+    got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gblk))
+    assert np.abs(_pixels(d, got) - _pixels(d, zexp)).max() < 2.0 ** -12
+
+
+def test_block_small_own_plans():
+    """same block with the library's own FP64 plans, masks and Chebyshev fit: decoded within 2^-12"""
+    d = _block_pair("cfg2_small", 32, import_all=False)
+    K, ctx, keys = d["K"], d["ctx"], d["keys"]
+    gct = K.ckks_encrypt(ctx, keys, import_pt(K, ctx, d["pt"]), 2)
+    spec = d["spec"]
+    gplan = K.ckks_ptset_conv_fused(ctx, d["W"], spec["cin"], spec["cout"], spec["f"], d["w"], 1, d["plan"].scale)
+    gblk = K.ckks_block(ctx, keys, gct, gplan, d["bt"])
+    zexp, _ = _expected_slots(d)
+    got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gblk))
+    assert np.abs(_pixels(d, got) - _pixels(d, zexp)).max() < 2.0 ** -12
+
+
+def test_eval_poly_bitexact():
+    K, o, ctx, keys = make_pair("cfg2_small", 41)
+    P = o.P
+    y = np.random.default_rng(4).uniform(-1, 1, P.n // 2)
+    pt = o.encode_pt(y, P.L, P.delta[P.L])
+    ct = o.encrypt(pt, 1)
+    coeffs = list(np.polynomial.chebyshev.chebinterpolate(lambda t: t * (1 + np.tanh(4 * t)) / 2, 15))
+    coeffs = [c if k % 2 == 1 or k == 0 else 0.0 for k, c in enumerate(coeffs)]
+    want = o.cheb_eval(ct, coeffs)
+    got = K.ckks_eval_poly(ctx, keys, import_ct(K, ctx, ct), coeffs)
+    assert_ct_equal(K, ctx, got, want, "eval_poly")
+
+
+@pytest.mark.slow
+def test_cfg2_block_full_size():
+    """config 2 at full size (N = 2^16, 24 limbs, 16 channels of 32x32, Gaussian weights):
+    the conv output and the CtoS input are bit-exact against the oracle; the whole block
+    decodes to the masked FP64 conv2d within 2^-12"""
+    d = _block_pair("cfg2", 7, import_all=False, oracle_all_keys=False)
+    K, o, ctx, keys = d["K"], d["o"], d["ctx"], d["keys"]
+    ct = o.encrypt(d["pt"], 2)
+    gct = K.ckks_encrypt(ctx, keys, import_pt(K, ctx, d["pt"]), 2)
+    assert_ct_equal(K, ctx, gct, ct, "encryption")
+    gplan = import_plan(K, ctx, d["plan"])
+    x0 = o.conv2d_cins(ct, d["plan"])
+    gx0 = K.ckks_conv2d_cins(ctx, keys, gct, gplan)
+    assert_ct_equal(K, ctx, gx0, x0, "conv")
+    assert_ct_equal(K, ctx, K.ckks_mod_raise(ctx, gx0), o.mod_raise(x0), "ModRaise")
+    gblk = K.ckks_block(ctx, keys, gct, gplan, d["bt"])
+    zexp, conv = _expected_slots(d)
+    got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gblk))
+    err = np.abs(_pixels(d, got) - _pixels(d, zexp)).max()
+    assert err < 2.0 ** -12, err
