@@ -174,13 +174,12 @@ def _block_pair(name, seed, import_all=True, oracle_all_keys=True):
     if oracle_all_keys:
         K, o, ctx, keys = make_pair(name, seed, rotations=rots)
     else:
-        K, o, ctx, keys = make_pair(name, seed, rotations=plan.rotations(P.n // 2), conj=False)
-        K.ckks_keys_add_rotations(ctx, keys, rots)
-        K.ckks_keys_add_rotations(ctx, keys, [])
-        from paper_2312_04356_gb300 import ckks as KK
-        KK.lib()  # conjugation key for the library only
-        keys_full = K.ckks_keygen(ctx, rots, True)
-        keys = keys_full
+        # the oracle only runs the conv here: it needs the conv's rotation keys alone
+        from paper_2312_04356_gb300 import ckks as K
+        o = Oracle(P, seed)
+        o.gen_rotation_keys(plan.rotations(P.n // 2))
+        ctx = gpu_ctx(name, seed)
+        keys = K.ckks_keygen(ctx, rots, True)
     bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
     info = K.ckks_boot_info(bt)
     assert info["c_drop"] == cfg.c_drop and info["K_eff"] == cfg.K_eff and info["s_raise"] == cfg.s_raise
