@@ -40,6 +40,9 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
+    ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
+    ap.add_argument("--kernel", default=None, choices=["ntt"],
+                    help="time one kernel family alone on a buffer larger than L2 (for profiling)")
     return ap.parse_args()
 
 
@@ -259,11 +262,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches0 = K.ckks_ctx_counters(ctx)["launches"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.nvtx:
+        torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
         K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
     e1.record(stream)
     torch.cuda.synchronize()
+    if args.nvtx:
+        torch.cuda.nvtx.range_pop()
     if dist:
         dist.barrier()
     t_ms = e0.elapsed_time(e1)
@@ -333,9 +340,42 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kernel_ntt(args):
+    """forward + inverse NTT of 256 limbs (256 MiB, > L2) cycling over the config-2 primes"""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    d = WL.PARAMS[CONFIG]
+    ctx = K.ckks_ctx_create(d, 1, torch.cuda.current_stream().cuda_stream)
+    q, p, _, _ = K.ckks_ctx_info(ctx)
+    mods = q + p
+    nl = 256
+    ids = [i % len(mods) for i in range(nl)]
+    x = WL.residues(1, [mods[i] for i in ids], ctx.n)
+    dev = torch.from_numpy(x.view(np.int64)).cuda()
+    for _ in range(args.warmup):
+        K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)
+        K.ckks_ntt_inverse(ctx, dev.data_ptr(), nl, ids)
+    torch.cuda.synchronize()
+    K.ckks_ctx_reset_counters(ctx)
+    K.ckks_ctx_set_timing(ctx, 1)
+    for _ in range(args.steps):
+        K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)
+        K.ckks_ntt_inverse(ctx, dev.data_ptr(), nl, ids)
+    K.ckks_ctx_set_timing(ctx, 0)
+    st = K.ckks_ctx_kernel_stats(ctx)
+    ok = bool((dev.cpu().numpy().view(np.uint64) == x).all())
+    out = {k: {"launches": v["launches"], "us_per_launch": round(1e3 * v["ms"] / v["launches"], 2),
+               "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)} for k, v in st.items()}
+    print(json.dumps({"kernel": "ntt", "limbs": nl, "N": ctx.n, "roundtrip_exact": ok, "stats": out}))
+
+
 if __name__ == "__main__":
     a = parse_args()
-    if a.impl == "reference":
+    if a.kernel == "ntt":
+        run_kernel_ntt(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

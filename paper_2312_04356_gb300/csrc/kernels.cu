@@ -177,6 +177,153 @@ __global__ void __launch_bounds__(NTT_THREADS)
     }
 }
 
+// ---- fast path for N = 2^16: two passes of 8 stages, each as two radix-16 rounds ----
+// A pass works on 256-element sub-problems (k = 0..255), 16 threads per sub-problem,
+// 16 values per thread in registers.  Round A covers local stages u = 0..3 on the
+// elements k = t + 16 i, round B covers u = 4..7 on k = 16 t + i; one shared-memory
+// exchange separates them.  Butterflies are Harvey's lazy forms: forward values stay in
+// [0, 4q), inverse values in [0, 2q); the last forward pass and the N^{-1} scaling
+// return canonical residues.  Twiddle of local stage u for element k of sub-problem hi:
+// index 2^(s0+u) + hi 2^u + (k >> (8 - u)).
+constexpr int F_SUB = 16;                 // sub-problems per CTA
+constexpr int F_STRIDE = 273;             // shared words per sub-problem: 256 + 16 pad, odd
+__device__ __forceinline__ int f_slot(int sp, int k) { return sp * F_STRIDE + k + (k >> 4); }
+
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 wp, u64 q, u64 q2) {
+    if (x >= q2) x -= q2;
+    const u64 t = y * w - __umul64hi(y, wp) * q;   // [0, 2q)
+    y = x - t + q2;
+    x = x + t;
+}
+__device__ __forceinline__ void gs_bfly(u64& x, u64& y, u64 w, u64 wp, u64 q, u64 q2) {
+    u64 s = x + y;
+    if (s >= q2) s -= q2;
+    const u64 d = x - y + q2;
+    y = d * w - __umul64hi(d, wp) * q;             // [0, 2q)
+    x = s;
+}
+
+// forward round over 4 local stages u0..u0+3; element i of the thread has index k(i);
+// tw index offset for lower element i at stage u: base_u + (k(i) >> (8 - u))
+template <bool ROUND_B>
+__device__ __forceinline__ void fwd_round(u64 (&x)[16], int t, int hi, int s0, const DevPrime* __restrict__ P,
+                                          u64 q, u64 q2) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int u = (ROUND_B ? 4 : 0) + s;
+        const int is = 8 >> s;
+        const int base = (1 << (s0 + u)) + (hi << u);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i & is) continue;
+            const int idx = ROUND_B ? base + (t << s) + (i >> (4 - s)) : base + (i >> (4 - s));
+            ct_bfly(x[i], x[i + is], __ldg(P->tw + idx), __ldg(P->twp + idx), q, q2);
+        }
+    }
+}
+
+template <bool ROUND_B>
+__device__ __forceinline__ void inv_round(u64 (&x)[16], int t, int hi, int s0, const DevPrime* __restrict__ P,
+                                          u64 q, u64 q2) {
+#pragma unroll
+    for (int s = 3; s >= 0; --s) {
+        const int u = (ROUND_B ? 4 : 0) + s;
+        const int is = 8 >> s;
+        const int base = (1 << (s0 + u)) + (hi << u);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i & is) continue;
+            const int idx = ROUND_B ? base + (t << s) + (i >> (4 - s)) : base + (i >> (4 - s));
+            gs_bfly(x[i], x[i + is], __ldg(P->itw + idx), __ldg(P->itwp + idx), q, q2);
+        }
+    }
+}
+
+// COL: sub-problems are columns (s0 = 0, T1 = 256, element j = k*256 + lo), threads with
+//      consecutive tid take consecutive columns.  ROW: sub-problems are contiguous rows
+//      (s0 = 8, T1 = 1, j = hi*256 + k), consecutive tid take consecutive k.
+template <bool COL, bool INV>
+__global__ void __launch_bounds__(256) k_ntt16(u64* __restrict__ data, const DevPrime* __restrict__ primes,
+                                              const int* __restrict__ ids, int lpp) {
+    __shared__ u64 sm[F_SUB * F_STRIDE];
+    const int limb = blockIdx.y;
+    const DevPrime* P = primes + ids[limb % lpp];
+    const u64 q = P->m.q, q2 = 2 * q;
+    u64* a = data + ((size_t)limb << 16);
+    const int tid = threadIdx.x;
+    const int sp = COL ? (tid & 15) : (tid >> 4);
+    const int t = COL ? (tid >> 4) : (tid & 15);
+    const int sub = blockIdx.x * F_SUB + sp;           // global sub-problem: column lo or row hi
+    const int s0 = COL ? 0 : 8;
+    const int hi = COL ? 0 : sub;
+    u64 x[16];
+    auto gidx = [&](int k) -> size_t { return COL ? ((size_t)k << 8) + sub : ((size_t)sub << 8) + k; };
+
+    if (!INV) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = a[gidx(t + 16 * i)];
+        fwd_round<false>(x, t, hi, s0, P, q, q2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[f_slot(sp, t + 16 * i)] = x[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(sp, 16 * t + i)];
+        fwd_round<true>(x, t, hi, s0, P, q, q2);
+        if (COL) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[gidx(16 * t + i)] = x[i];     // lazy, [0, 4q)
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                u64 v = x[i];
+                if (v >= q2) v -= q2;
+                if (v >= q) v -= q;
+                x[i] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sm[f_slot(sp, 16 * t + i)] = x[i];
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[gidx(t + 16 * i)] = sm[f_slot(sp, t + 16 * i)];
+        }
+    } else {
+        if (COL) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = a[gidx(16 * t + i)];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sm[f_slot(sp, t + 16 * i)] = a[gidx(t + 16 * i)];
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(sp, 16 * t + i)];
+            __syncthreads();
+        }
+        inv_round<true>(x, t, hi, s0, P, q, q2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[f_slot(sp, 16 * t + i)] = x[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(sp, t + 16 * i)];
+        inv_round<false>(x, t, hi, s0, P, q, q2);
+        if (COL) {
+            const u64 ni = P->n_inv, nip = P->n_inv_p;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[gidx(t + 16 * i)] = mul_shoup(x[i], ni, nip, q);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[gidx(t + 16 * i)] = x[i];     // lazy, [0, 2q)
+        }
+    }
+}
+
+template <bool COL, bool INV>
+void launch_ntt16(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp) {
+    dim3 grid(256 / F_SUB, nlimbs);
+    KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0);
+    k_ntt16<COL, INV><<<grid, 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp);
+}
+
 struct PassPlan {
     int s0, c;
 };
@@ -300,34 +447,65 @@ __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const
 
 // ------------------------------------------------------- base conversion ----
 // y_m = sum_i [x_i * qhat_i^{-1}]_{q_i} * (qhat_i mod p_m)  (no correction term)
+// One thread per coefficient; grid.z splits the outputs in groups of CONV_OUT.  The
+// products are summed exactly in 128 bits (each < 2^122, at most 16 terms) and reduced
+// once: (H 2^64 + L) mod p = H (2^64 mod p) + L mod p.
 constexpr int MAX_CONV_IN = 16;
-__global__ void k_base_convert(const u64* __restrict__ in, size_t in_stride, u64* __restrict__ out,
-                               size_t out_stride, int nin, int nout, const int* __restrict__ in_ids,
-                               const int* __restrict__ out_ids, const int* __restrict__ out_rows,
-                               const u64* __restrict__ qinv, const u64* __restrict__ qmod,
-                               const DevPrime* __restrict__ P, int logn, size_t in_pstride, size_t out_pstride) {
+constexpr int CONV_OUT = 8;
+__global__ void __launch_bounds__(256)
+    k_base_convert(const u64* __restrict__ in, size_t in_stride, u64* __restrict__ out, size_t out_stride, int nin,
+                   int nout, const int* __restrict__ in_ids, const int* __restrict__ out_ids,
+                   const int* __restrict__ out_rows, const u64* __restrict__ qinv, const u64* __restrict__ qmod,
+                   const DevPrime* __restrict__ P, int logn, size_t in_pstride, size_t out_pstride) {
+    __shared__ u64 s_qi[MAX_CONV_IN], s_qinv[MAX_CONV_IN], s_qinvp[MAX_CONV_IN];
+    __shared__ u64 s_c[CONV_OUT][MAX_CONV_IN];
+    __shared__ DevMod s_pm[CONV_OUT];
+    __shared__ u64 s_two64[CONV_OUT], s_two64p[CONV_OUT];
+    __shared__ int s_row[CONV_OUT];
+    const int m0 = blockIdx.z * CONV_OUT;
+    const int mcount = min(CONV_OUT, nout - m0);
+    const int tid = threadIdx.x;
+    if (tid < nin) {
+        s_qi[tid] = P[in_ids[tid]].m.q;
+        s_qinv[tid] = qinv[tid];
+        s_qinvp[tid] = qinv[nin + tid];
+    }
+    if (tid < mcount * MAX_CONV_IN) {
+        const int m = tid / MAX_CONV_IN, i = tid % MAX_CONV_IN;
+        s_c[m][i] = i < nin ? qmod[(size_t)(m0 + m) * nin + i] : 0;
+    }
+    if (tid < mcount) {
+        const DevMod pm = P[out_ids[m0 + tid]].m;
+        s_pm[tid] = pm;
+        const u64 t64 = barrett_reduce128(1, 0, pm);   // 2^64 mod p
+        s_two64[tid] = t64;
+        s_two64p[tid] = (u64)(((unsigned __int128)t64 << 64) / pm.q);
+        s_row[tid] = out_rows[m0 + tid];
+    }
+    __syncthreads();
     const int poly = blockIdx.y;
     in += poly * in_pstride;
     out += poly * out_pstride;
-    EW_LOOP(1 << logn) {
-        u64 xh[MAX_CONV_IN];
+    const int j = blockIdx.x * blockDim.x + tid;
+    if (j >= (1 << logn)) return;
+    u64 xh[MAX_CONV_IN];
+#pragma unroll
+    for (int i = 0; i < MAX_CONV_IN; ++i)
+        if (i < nin) xh[i] = mul_shoup(in[i * in_stride + j], s_qinv[i], s_qinvp[i], s_qi[i]);
+    for (int m = 0; m < mcount; ++m) {
+        u64 lo = 0, hi = 0;
 #pragma unroll
         for (int i = 0; i < MAX_CONV_IN; ++i) {
             if (i < nin) {
-                const u64 qi = P[in_ids[i]].m.q;
-                xh[i] = mul_shoup(in[i * in_stride + j], qinv[i], qinv[nin + i], qi);
+                const u64 c = s_c[m][i];
+                const u64 pl = xh[i] * c, ph = __umul64hi(xh[i], c);
+                lo += pl;
+                hi += ph + (lo < pl ? 1ull : 0ull);
             }
         }
-        for (int m = 0; m < nout; ++m) {
-            const u64 pm = P[out_ids[m]].m.q;
-            const u64* cm = qmod + (size_t)m * nin;
-            const u64* cmp = qmod + (size_t)nout * nin + (size_t)m * nin;
-            u64 acc = 0;
-#pragma unroll
-            for (int i = 0; i < MAX_CONV_IN; ++i)
-                if (i < nin) acc = add_mod(acc, mul_shoup(xh[i], cm[i], cmp[i], pm), pm);
-            out[(size_t)out_rows[m] * out_stride + j] = acc;
-        }
+        const DevMod pm = s_pm[m];
+        const u64 r = add_mod(mul_shoup(hi, s_two64[m], s_two64p[m], pm.q), reduce64(lo, pm), pm.q);
+        out[(size_t)s_row[m] * out_stride + j] = r;
     }
 }
 
@@ -396,12 +574,24 @@ namespace kern {
 
 void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp) {
     if (nlimbs <= 0) return;
+    if (c->logn == 16) {
+        launch_ntt16<true, false>(c, data, nlimbs, ids, lpp);
+        launch_ntt16<false, false>(c, data, nlimbs, ids, lpp);
+        LAUNCH_CHECK();
+        return;
+    }
     for (const PassPlan& p : ntt_passes(c->logn)) launch_pass<false>(c, data, nlimbs, ids, lpp, p, 0);
     LAUNCH_CHECK();
 }
 
 void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp) {
     if (nlimbs <= 0) return;
+    if (c->logn == 16) {
+        launch_ntt16<false, true>(c, data, nlimbs, ids, lpp);
+        launch_ntt16<true, true>(c, data, nlimbs, ids, lpp);
+        LAUNCH_CHECK();
+        return;
+    }
     std::vector<PassPlan> ps = ntt_passes(c->logn);
     for (int i = (int)ps.size() - 1; i >= 0; --i)
         launch_pass<true>(c, data, nlimbs, ids, lpp, ps[i], ps[i].s0 == 0 ? 1 : 0);
@@ -500,10 +690,10 @@ void base_convert(const ckks_ctx* c, const ConvTab& t, const u64* in, size_t in_
                   size_t out_stride, int npoly, size_t in_pstride, size_t out_pstride) {
     CK_CHECK(t.nin <= MAX_CONV_IN, CKKS_EINVAL, "base conversion with more than 16 input limbs");
     if (t.nout == 0) return;
-    dim3 grid(ew_grid(c->n, 1).x, npoly);
+    dim3 grid((c->n + 255) / 256, npoly, (t.nout + CONV_OUT - 1) / CONV_OUT);
     // d_out_ids is followed by out_rows in the same allocation
     { KTimer kt_(c, "base_convert", (double)npoly * (t.nin + t.nout) * c->n * 8.0);
-    k_base_convert<<<grid, EW_THREADS, 0, c->stream>>>(in, in_stride, out, out_stride, t.nin, t.nout, t.d_in_ids,
+    k_base_convert<<<grid, 256, 0, c->stream>>>(in, in_stride, out, out_stride, t.nin, t.nout, t.d_in_ids,
                                                        t.d_out_ids, t.d_out_ids + t.nout, t.d_qhat_inv, t.d_qhat_mod,
                                                        c->d_primes, c->logn, in_pstride, out_pstride);
     }
