@@ -815,6 +815,7 @@ int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out)
                 if (p1 / bp->w < bp->w0 && p1 % bp->w < bp->w0) mre[(size_t)i * bt->ell + u] = val;
                 if (p2 / bp->w < bp->w0 && p2 % bp->w < bp->w0) mim[(size_t)i * bt->ell + u] = val;
             }
+        bt->mask_im_zero = std::all_of(mim.begin(), mim.end(), [](const cplx& v) { return v == cplx(0, 0); });
         bt->mask_re = std::make_unique<ckks_pt>();
         bt->mask_im = std::make_unique<ckks_pt>();
         encode_complex(ctx, mre, le, bt->s_mask, bt->mask_re.get());
@@ -934,6 +935,8 @@ int ckks_boot_set_masks(ckks_ctx* ctx, ckks_boot* bt, const ckks_pt* re, const c
             CUDA_CHECK(cudaMemcpyAsync(pt->buf.ptr, src->buf.ptr, words * 8, cudaMemcpyDeviceToDevice, ctx->stream));
             (k ? bt->mask_im : bt->mask_re) = std::move(pt);
         }
+        std::vector<u64> h = download(ctx, bt->mask_im->buf.ptr, (size_t)(bt->mask_im->level + 1) * ctx->n);
+        bt->mask_im_zero = std::all_of(h.begin(), h.end(), [](u64 v) { return v == 0; });
     });
 }
 
@@ -972,10 +975,7 @@ int ckks_block(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ck
         REQ(conv);
         REQ(bt);
         REQ(out);
-        ckks_ct x = ops::rescale(ops::bsgs(*keys, *in, *conv));
-        ckks_ct re, im;
-        ops::bootstrap(*keys, *bt, x, re, im);
-        assign(out, ops::stoc1(*keys, *bt, re, im));
+        assign(out, ops::block(*keys, *bt, *conv, *in));
     });
 }
 

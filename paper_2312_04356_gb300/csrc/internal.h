@@ -160,6 +160,7 @@ struct ckks_boot {
     std::vector<double> coeffs;
     std::vector<std::unique_ptr<ckks_ptset>> ctos, stoc;
     std::unique_ptr<ckks_pt> mask_re, mask_im;
+    bool mask_im_zero = false;   // the Im half of every slice is padding: its mask is exactly 0
 };
 
 // Scope object placed around one kernel launch: counts it and, if the context's
@@ -177,8 +178,9 @@ struct KTimer {
 // All launchers enqueue on ctx->stream.  `ids` are device arrays of prime ids
 // (length lpp = limbs per polynomial); limb k of a multi-polynomial array uses ids[k % lpp].
 namespace kern {
-void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp);
-void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp);
+// pstride: words between consecutive polynomials of lpp limbs (0 = lpp * N, contiguous)
+void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
+void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void sub(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void neg(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, const int* ids, int lpp);

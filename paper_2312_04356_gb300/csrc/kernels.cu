@@ -185,7 +185,6 @@ __global__ void __launch_bounds__(NTT_THREADS)
 // [0, 4q), inverse values in [0, 2q); the last forward pass and the N^{-1} scaling
 // return canonical residues.  Twiddle of local stage u for element k of sub-problem hi:
 // index 2^(s0+u) + hi 2^u + (k >> (8 - u)).
-constexpr int F_SUB = 16;                 // sub-problems per CTA
 constexpr int F_STRIDE = 273;             // shared words per sub-problem: 256 + 16 pad, odd
 __device__ __forceinline__ int f_slot(int sp, int k) { return sp * F_STRIDE + k + (k >> 4); }
 
@@ -242,18 +241,19 @@ __device__ __forceinline__ void inv_round(u64 (&x)[16], int t, int hi, int s0, c
 // COL: sub-problems are columns (s0 = 0, T1 = 256, element j = k*256 + lo), threads with
 //      consecutive tid take consecutive columns.  ROW: sub-problems are contiguous rows
 //      (s0 = 8, T1 = 1, j = hi*256 + k), consecutive tid take consecutive k.
-template <bool COL, bool INV>
-__global__ void __launch_bounds__(256) k_ntt16(u64* __restrict__ data, const DevPrime* __restrict__ primes,
-                                              const int* __restrict__ ids, int lpp) {
-    __shared__ u64 sm[F_SUB * F_STRIDE];
+template <bool COL, bool INV, int SUBS>
+__global__ void __launch_bounds__(16 * SUBS) k_ntt16(u64* __restrict__ data, const DevPrime* __restrict__ primes,
+                                                    const int* __restrict__ ids, int lpp, size_t pstride) {
+    __shared__ u64 sm[SUBS * F_STRIDE];
     const int limb = blockIdx.y;
-    const DevPrime* P = primes + ids[limb % lpp];
+    const int r = limb % lpp;
+    const DevPrime* P = primes + ids[r];
     const u64 q = P->m.q, q2 = 2 * q;
-    u64* a = data + ((size_t)limb << 16);
+    u64* a = data + (size_t)(limb / lpp) * pstride + ((size_t)r << 16);
     const int tid = threadIdx.x;
-    const int sp = COL ? (tid & 15) : (tid >> 4);
-    const int t = COL ? (tid >> 4) : (tid & 15);
-    const int sub = blockIdx.x * F_SUB + sp;           // global sub-problem: column lo or row hi
+    const int sp = COL ? (tid % SUBS) : (tid >> 4);
+    const int t = COL ? (tid / SUBS) : (tid & 15);
+    const int sub = blockIdx.x * SUBS + sp;            // global sub-problem: column lo or row hi
     const int s0 = COL ? 0 : 8;
     const int hi = COL ? 0 : sub;
     u64 x[16];
@@ -317,11 +317,15 @@ __global__ void __launch_bounds__(256) k_ntt16(u64* __restrict__ data, const Dev
     }
 }
 
+// few limbs: 64-thread CTAs (4 sub-problems) so that the grid still covers the SMs
 template <bool COL, bool INV>
-void launch_ntt16(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp) {
-    dim3 grid(256 / F_SUB, nlimbs);
+void launch_ntt16(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride) {
     KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0);
-    k_ntt16<COL, INV><<<grid, 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp);
+    if (nlimbs >= 16) {
+        k_ntt16<COL, INV, 16><<<dim3(256 / 16, nlimbs), 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride);
+    } else {
+        k_ntt16<COL, INV, 4><<<dim3(256 / 4, nlimbs), 64, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride);
+    }
 }
 
 struct PassPlan {
@@ -572,26 +576,30 @@ namespace kern {
 
 #define LAUNCH_CHECK() CUDA_CHECK(cudaGetLastError())
 
-void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp) {
+void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride) {
     if (nlimbs <= 0) return;
+    if (pstride == 0) pstride = (size_t)lpp * c->n;
     if (c->logn == 16) {
-        launch_ntt16<true, false>(c, data, nlimbs, ids, lpp);
-        launch_ntt16<false, false>(c, data, nlimbs, ids, lpp);
+        launch_ntt16<true, false>(c, data, nlimbs, ids, lpp, pstride);
+        launch_ntt16<false, false>(c, data, nlimbs, ids, lpp, pstride);
         LAUNCH_CHECK();
         return;
     }
+    CK_CHECK(pstride == (size_t)lpp * c->n, CKKS_EINVAL, "strided polynomials need N = 2^16");
     for (const PassPlan& p : ntt_passes(c->logn)) launch_pass<false>(c, data, nlimbs, ids, lpp, p, 0);
     LAUNCH_CHECK();
 }
 
-void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp) {
+void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride) {
     if (nlimbs <= 0) return;
+    if (pstride == 0) pstride = (size_t)lpp * c->n;
     if (c->logn == 16) {
-        launch_ntt16<false, true>(c, data, nlimbs, ids, lpp);
-        launch_ntt16<true, true>(c, data, nlimbs, ids, lpp);
+        launch_ntt16<false, true>(c, data, nlimbs, ids, lpp, pstride);
+        launch_ntt16<true, true>(c, data, nlimbs, ids, lpp, pstride);
         LAUNCH_CHECK();
         return;
     }
+    CK_CHECK(pstride == (size_t)lpp * c->n, CKKS_EINVAL, "strided polynomials need N = 2^16");
     std::vector<PassPlan> ps = ntt_passes(c->logn);
     for (int i = (int)ps.size() - 1; i >= 0; --i)
         launch_pass<true>(c, data, nlimbs, ids, lpp, ps[i], ps[i].s0 == 0 ? 1 : 0);

@@ -458,8 +458,12 @@ void key_switch_raised(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndi
     kern::ks_inner(c, D, ndig, next, c->d_ext_ids[level], k.b.ptr, k.a.ptr, ab, aa, g);
     // ModDown of both halves
     const int* pid = c->d_ext_ids[level] + nl;
-    kern::ntt_inverse(c, ab + (size_t)nl * n, c->np, pid, c->np);
-    kern::ntt_inverse(c, aa + (size_t)nl * n, c->np, pid, c->np);
+    if (c->logn == 16) {
+        kern::ntt_inverse(c, ab + (size_t)nl * n, 2 * c->np, pid, c->np, (size_t)next * n);
+    } else {
+        kern::ntt_inverse(c, ab + (size_t)nl * n, c->np, pid, c->np);
+        kern::ntt_inverse(c, aa + (size_t)nl * n, c->np, pid, c->np);
+    }
     DevBuf conv(2 * (size_t)nl * n, c->stream);
     kern::base_convert(c, c->moddown_tab(level), ab + (size_t)nl * n, n, conv.ptr, n, 2, (size_t)next * n,
                        (size_t)nl * n);
@@ -659,6 +663,29 @@ void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, c
     im.scale = c->delta[im.level];
     re_out = eval_mod(keys, re, bt.coeffs, bt.bp.r);
     im_out = eval_mod(keys, im, bt.coeffs, bt.bp.r);
+}
+
+// Alg. 1 block.  When the Im mask is exactly zero (the second half of every slice is
+// padding), PMult(ct_Im, mask_Im) is the zero ciphertext whatever ct_Im holds, so the Im
+// branch (its scale drop and EvalMod) is skipped; the output is bit-identical.
+ckks_ct block(const ckks_keys& keys, const ckks_boot& bt, const ckks_ptset& conv, const ckks_ct& in) {
+    ckks_ctx* c = in.ctx;
+    ckks_ct x0 = rescale(bsgs(keys, in, conv));
+    if (!bt.mask_im_zero) {
+        ckks_ct re, im;
+        bootstrap(keys, bt, x0, re, im);
+        return stoc1(keys, bt, re, im);
+    }
+    ckks_ct x = mod_raise(x0);
+    x.scale = bt.s_raise;
+    for (const auto& ps : bt.ctos) x = rescale(bsgs(keys, x, *ps));
+    ckks_ct re = add(x, conjugate(keys, x));
+    re = rescale(mul_int(re, bt.c_drop));
+    re.scale = c->delta[re.level];
+    re = eval_mod(keys, re, bt.coeffs, bt.bp.r);
+    ckks_ct y = rescale(mul_plain(re, *bt.mask_re));
+    for (const auto& ps : bt.stoc) y = rescale(bsgs(keys, y, *ps));
+    return y;
 }
 
 ckks_ct stoc1(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& re, const ckks_ct& im) {
