@@ -272,6 +272,25 @@ int ckks_block(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ck
 int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, int deg,
                    int basis, double a, double b, ckks_ct* out);
 
+/* ---- rescale without device allocation ------------------------------------ */
+/* The paper has no counterpart to this call; it exists for callers that cannot allocate
+ * device memory while they run (graphs recorded without memory-pool nodes, serving loops
+ * that forbid cudaMalloc because it may synchronise the device, hosts that give the
+ * library a fixed memory budget).  It computes exactly what ckks_rescale computes, on
+ * raw device arrays: d_in is a ciphertext at `level` ([2][level+1][N] uint64, NTT domain,
+ * c0 then c1), d_out receives the rescaled ciphertext ([2][level][N], NTT domain); d_out
+ * must not overlap d_in.  The caller tracks the scale (divide it by q_level).
+ * Scratch comes from one static device array of 2^22 words (32 MiB) that every GPU loading
+ * the library holds until exit; calls needing more than (2 level + 2) N <= 2^22 words are
+ * rejected with CKKS_EINVAL.  No cudaMalloc / cudaFree (or any allocating routine) is
+ * called; per-kernel timing is suspended during the call.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current: make that
+ * first call before any stream capture.  Every call shares the array and leaves its
+ * contents behind; nothing in it needs to start at zero (each word is written before it is
+ * read), but calls that overlap on the GPU (other streams, other contexts on the same
+ * device) race on it. */
+int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, int level, uint64_t* d_out);
+
 /* ---- raw kernels on caller device memory ---------------------------------- */
 /* In-place forward / inverse negacyclic NTT of n_limbs limbs at `dev` ([n_limbs][N]
  * uint64 device memory, residues < q); limb i uses the prime with global id

@@ -114,6 +114,7 @@ _SIGS = {
     "ckks_stoc1": [VP, VP, VP, VP, VP, VP],
     "ckks_block": [VP, VP, VP, VP, VP, VP],
     "ckks_eval_poly": [VP, VP, VP, VP, I, I, D, D, VP],
+    "ckks_rescale_noalloc": [VP, VP, I, VP],
     "ckks_ntt_forward": [VP, VP, I, VP],
     "ckks_ntt_inverse": [VP, VP, I, VP],
 }
@@ -593,6 +594,13 @@ def ckks_eval_poly(ctx, keys, ct, coeffs, basis=CKKS_BASIS_CHEB, a=-1.0, b=1.0, 
     c = _f64(coeffs)
     ctx.check(lib().ckks_eval_poly(ctx, keys, ct, _ptr(c), len(c) - 1, basis, a, b, out))
     return out
+
+
+# --------------------------------------------- rescale without allocation ---
+def ckks_rescale_noalloc(ctx, d_in, level, d_out):
+    """rescale of raw device arrays ([2][level+1][N] -> [2][level][N], NTT domain) using the
+    library's static scratch array instead of allocating (see include/ckks.h)"""
+    ctx.check(lib().ckks_rescale_noalloc(ctx, ctypes.c_void_p(d_in), level, ctypes.c_void_p(d_out)))
 
 
 # ------------------------------------------------------------- raw NTT ------
