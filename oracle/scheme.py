@@ -435,11 +435,10 @@ class Oracle:
         return self.rescale(self.bsgs(ct, plan))
 
     # ------------------------------------------------------- bootstrapping ----
-    def cheb_eval(self, x, coeffs):
-        """sum_k c_k T_k(x): T_k from T_{ceil(k/2)}, T_{floor(k/2)}; each c_k T_k lands on the
-        canonical scale of the common target level after one rescale."""
-        P = self.P
-        d = len(coeffs) - 1
+    # ------------------------------------------------ Chebyshev evaluation ----
+    def cheb_powers(self, x, ks):
+        """T_k(x) for every k in ks (and what they need): T_k = 2 T_ceil(k/2) T_floor(k/2) -
+        T_(k mod 2 ? 1 : 0), operands brought to a common level by level_down."""
         T = {1: x}
         cache = {}
 
@@ -450,29 +449,111 @@ class Oracle:
                 cache[(k, lev)] = self.level_down(T[k], lev)
             return cache[(k, lev)]
 
-        for k in range(2, d + 1):
+        def need(k):
+            if k in T:
+                return
             a, b = k // 2, k - k // 2
+            need(a)
+            need(b)
+            if a != b:
+                need(b - a)
             m = min(T[a].level, T[b].level)
             t = self.rescale(self.mul_relin(at(a, m), at(b, m)))
             t = self.add(t, t)
-            if a == b:
-                t = self.add_const(t, -1.0)
-            else:
-                t = self.sub(t, at(b - a, m - 1))
+            t = self.add_const(t, -1.0) if a == b else self.sub(t, at(b - a, m - 1))
             T[k] = t
-        target = min(T[k].level for k in range(1, d + 1) if coeffs[k] != 0.0) - 1
+
+        for k in sorted(ks):
+            need(k)
+        return T, at
+
+    def cheb_leaf(self, T, coeffs):
+        """sum_k c_k T_k for a low-degree piece: terms grouped by the level of T_k; each group
+        is summed after multiplying by llround(c_k s_c), s_c = Delta_target q_lk / scale(T_k),
+        rescaled once and dropped to the target level (the lowest group's level - 1).
+        Returns a ciphertext, or a float when only the constant term is non-zero."""
+        P = self.P
+        ks = [k for k in range(1, len(coeffs)) if coeffs[k] != 0.0]
+        if not ks:
+            return float(coeffs[0])
+        target = min(T[k].level for k in ks) - 1
         acc = None
-        for k in range(1, d + 1):
-            if coeffs[k] == 0.0:
-                continue
-            t = T[k]
-            lk = t.level
-            s_c = (P.delta[target] * float(P.q[lk])) / t.scale
-            term = self.rescale(self.mul_int(t, round_half_away(coeffs[k] * s_c)))
-            term.scale = (t.scale * s_c) / float(P.q[lk])
-            term = self.mod_drop(term, target)
-            acc = term if acc is None else self.add(acc, term)
+        for lev in sorted({T[k].level for k in ks}, reverse=True):
+            grp = None
+            scale = None
+            for k in ks:
+                t = T[k]
+                if t.level != lev:
+                    continue
+                s_c = (P.delta[target] * float(P.q[lev])) / t.scale
+                term = self.mul_int(t, round_half_away(coeffs[k] * s_c))
+                if grp is None:
+                    grp, scale = term, (t.scale * s_c) / float(P.q[lev])
+                else:
+                    grp = Ciphertext(C.add(grp.c0, term.c0, P.moduli(lev)), C.add(grp.c1, term.c1, P.moduli(lev)),
+                                     lev, grp.scale)
+            grp = self.rescale(grp)
+            grp.scale = scale
+            grp = self.mod_drop(grp, target)
+            acc = grp if acc is None else self.add(acc, grp)
         return self.add_const(acc, coeffs[0])
+
+    def cheb_eval(self, x, coeffs):
+        """sum_k c_k T_k(x) by baby-step giant-step: baby steps T_1..T_b, giant steps
+        T_b, T_2b, T_4b, ... (b = 2^ceil(m/2), m = ceil(log2(deg + 1))); the polynomial is split
+        by Chebyshev division p = q T_n + r (n the largest giant <= deg; q_0 = c_n,
+        q_j = 2 c_(n+j), r_(n-j) = c_(n-j) - c_(n+j)) down to pieces of degree < b, which are
+        evaluated as leaves.  Depth ceil(log2 deg) + 1 for the degrees used here; the result
+        is brought down to level(x) - ceil(log2 deg) - 1."""
+        coeffs = [float(c) for c in coeffs]
+        d = len(coeffs) - 1
+        assert d >= 1
+        m = math.ceil(math.log2(d + 1))
+        b = 1 << ((m + 1) // 2)
+        giants = []
+        n = b
+        while n <= d:
+            giants.append(n)
+            n *= 2
+        T, at = self.cheb_powers(x, list(range(1, min(b, d + 1))) + giants)
+
+        def rec(c):
+            deg = len(c) - 1
+            while deg > 0 and c[deg] == 0.0:
+                deg -= 1
+            c = c[: deg + 1]
+            if deg < b:
+                return self.cheb_leaf(T, c)
+            n = max(g for g in giants if g <= deg)
+            q = [c[n]] + [2.0 * c[n + j] for j in range(1, deg - n + 1)]
+            r = list(c[:n])
+            for j in range(1, deg - n + 1):
+                r[n - j] -= c[n + j]
+            Q, R = rec(q), rec(r)
+            Tn = T[n]
+            if isinstance(Q, float):
+                if Q == 0.0:
+                    prod = None
+                else:
+                    lk = Tn.level
+                    s_c = (self.P.delta[lk - 1] * float(self.P.q[lk])) / Tn.scale
+                    prod = self.rescale(self.mul_int(Tn, round_half_away(Q * s_c)))
+                    prod.scale = (Tn.scale * s_c) / float(self.P.q[lk])
+            else:
+                lev = min(Q.level, Tn.level)
+                prod = self.rescale(self.mul_relin(self.level_down(Q, lev), at(n, lev)))
+            if isinstance(R, float):
+                return R if prod is None else self.add_const(prod, R)
+            if prod is None:
+                return R
+            lev = min(prod.level, R.level)
+            return self.add(self.level_down(prod, lev), self.level_down(R, lev))
+
+        out = rec(coeffs)
+        assert not isinstance(out, float), "polynomial evaluates to a constant"
+        want = x.level - math.ceil(math.log2(d)) - 1 if d > 1 else x.level - 1
+        assert out.level >= want, (out.level, want)
+        return self.level_down(out, want)
 
     def eval_mod(self, x, coeffs, r):
         """cos(2 pi (K y - 1/4) / 2^r) by Chebyshev, then r double angles -> sin(2 pi K y)"""

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <set>
 
 #include "internal.h"
@@ -587,56 +588,162 @@ ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps) {
 }
 
 // ------------------------------------------------ Chebyshev / EvalMod -----
+// T_k(x) for the requested k (and what they need): T_k = 2 T_ceil(k/2) T_floor(k/2) -
+// T_(k mod 2 ? 1 : 0), operands brought to a common level by level_down.
+struct ChebPowers {
+    const ckks_keys* keys;
+    std::map<int, ckks_ct> T;
+    std::map<std::pair<int, int>, ckks_ct> cache;
+    const ckks_ct& at(int k, int lev) {
+        const ckks_ct& t = T.at(k);
+        if (t.level == lev) return t;
+        auto key = std::make_pair(k, lev);
+        auto it = cache.find(key);
+        if (it == cache.end()) it = cache.emplace(key, level_down(t, lev)).first;
+        return it->second;
+    }
+    void need(int k) {
+        if (T.count(k)) return;
+        const int a = k / 2, b = k - k / 2;
+        need(a);
+        need(b);
+        if (a != b) need(b - a);
+        const int m = std::min(T.at(a).level, T.at(b).level);
+        ckks_ct t = rescale(mul_relin(*keys, at(a, m), at(b, m)));
+        t = add(t, t);
+        t = (a == b) ? add_const(t, -1.0) : sub(t, at(b - a, m - 1));
+        T[k] = std::move(t);
+    }
+};
+
+// Result of evaluating a piece: a ciphertext, or a plain constant when only c_0 is non-zero.
+struct PolyVal {
+    bool is_const = false;
+    double cst = 0.0;
+    ckks_ct ct;
+};
+
+// sum_k c_k T_k for a piece of degree < b: terms grouped by the level of T_k; each group is
+// summed after multiplying by llround(c_k s_c), s_c = Delta_target q_lk / scale(T_k),
+// rescaled once and dropped to the target level (the lowest group's level - 1).
+static PolyVal cheb_leaf(ChebPowers& pw, const std::vector<double>& c) {
+    ckks_ctx* ctx = pw.T.at(1).ctx;
+    PolyVal out;
+    std::vector<int> ks;
+    for (int k = 1; k < (int)c.size(); ++k)
+        if (c[k] != 0.0) ks.push_back(k);
+    if (ks.empty()) {
+        out.is_const = true;
+        out.cst = c[0];
+        return out;
+    }
+    int target = 1 << 30;
+    std::set<int, std::greater<int>> levels;
+    for (int k : ks) {
+        target = std::min(target, pw.T.at(k).level - 1);
+        levels.insert(pw.T.at(k).level);
+    }
+    ckks_ct acc;
+    bool have = false;
+    for (int lev : levels) {
+        ckks_ct grp;
+        bool hg = false;
+        double scale = 0;
+        for (int k : ks) {
+            const ckks_ct& t = pw.T.at(k);
+            if (t.level != lev) continue;
+            const double s_c = (ctx->delta[target] * (double)ctx->q[lev]) / t.scale;
+            ckks_ct term = mul_int(t, llround_away(c[k] * s_c));
+            if (!hg) {
+                grp = std::move(term);
+                scale = (t.scale * s_c) / (double)ctx->q[lev];
+                hg = true;
+            } else {
+                kern::add(ctx, grp.buf.ptr, term.buf.ptr, grp.buf.ptr, 2 * (lev + 1), ctx->d_iota, lev + 1);
+            }
+        }
+        grp = rescale(grp);
+        grp.scale = scale;
+        grp = mod_drop(grp, target);
+        if (!have) {
+            acc = std::move(grp);
+            have = true;
+        } else {
+            acc = add(acc, grp);
+        }
+    }
+    out.ct = add_const(acc, c[0]);
+    return out;
+}
+
+// sum_k c_k T_k(x) by baby-step giant-step: baby steps T_1..T_b, giant steps T_b, T_2b, ...
+// (b = 2^ceil(m/2), m = ceil(log2(deg + 1))); p = q T_n + r by Chebyshev division (n the
+// largest giant <= deg; q_0 = c_n, q_j = 2 c_(n+j), r_(n-j) = c_(n-j) - c_(n+j)) down to
+// pieces of degree < b; the result is brought down to level(x) - ceil(log2 deg) - 1.
 ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs) {
-    ckks_ctx* c = x.ctx;
     const int d = (int)coeffs.size() - 1;
     CK_CHECK(d >= 1, CKKS_EINVAL, "polynomial degree must be >= 1");
     int depth = 0;
     while ((1 << depth) < d) ++depth;
-    CK_CHECK(x.level - depth - 1 >= 0, CKKS_ELEVEL, "not enough levels for the polynomial");
-    std::vector<ckks_ct> T(d + 1);
-    T[1] = copy_ct(x);
-    std::map<std::pair<int, int>, ckks_ct> cache;
-    auto at = [&](int k, int lev) -> const ckks_ct& {
-        if (T[k].level == lev) return T[k];
-        auto key = std::make_pair(k, lev);
-        auto it = cache.find(key);
-        if (it == cache.end()) it = cache.emplace(key, level_down(T[k], lev)).first;
-        return it->second;
-    };
-    for (int k = 2; k <= d; ++k) {
-        const int a = k / 2, b = k - k / 2;
-        const int m = std::min(T[a].level, T[b].level);
-        ckks_ct t = rescale(mul_relin(keys, at(a, m), at(b, m)));
-        t = add(t, t);
-        if (a == b)
-            t = add_const(t, -1.0);
-        else
-            t = sub(t, at(b - a, m - 1));
-        T[k] = std::move(t);
-    }
-    int target = 1 << 30;
-    for (int k = 1; k <= d; ++k)
-        if (coeffs[k] != 0.0) target = std::min(target, T[k].level - 1);
-    CK_CHECK(target < (1 << 30), CKKS_EINVAL, "polynomial has no non-constant term");
-    ckks_ct acc;
-    bool have = false;
-    for (int k = 1; k <= d; ++k) {
-        if (coeffs[k] == 0.0) continue;
-        const ckks_ct& t = T[k];
-        const int lk = t.level;
-        const double s_c = (c->delta[target] * (double)c->q[lk]) / t.scale;
-        ckks_ct term = rescale(mul_int(t, llround_away(coeffs[k] * s_c)));
-        term.scale = (t.scale * s_c) / (double)c->q[lk];
-        term = mod_drop(term, target);
-        if (!have) {
-            acc = std::move(term);
-            have = true;
-        } else {
-            acc = add(acc, term);
+    const int want = x.level - depth - 1;
+    CK_CHECK(want >= 0, CKKS_ELEVEL, "not enough levels for the polynomial");
+    int m = 0;
+    while ((1 << m) < d + 1) ++m;
+    const int b = 1 << ((m + 1) / 2);
+    std::vector<int> giants;
+    for (int n = b; n <= d; n *= 2) giants.push_back(n);
+    ChebPowers pw;
+    pw.keys = &keys;
+    pw.T[1] = copy_ct(x);
+    for (int k = 1; k < std::min(b, d + 1); ++k) pw.need(k);
+    for (int g : giants) pw.need(g);
+    std::function<PolyVal(std::vector<double>)> rec = [&](std::vector<double> c) -> PolyVal {
+        int deg = (int)c.size() - 1;
+        while (deg > 0 && c[deg] == 0.0) --deg;
+        c.resize(deg + 1);
+        if (deg < b) return cheb_leaf(pw, c);
+        int n = 0;
+        for (int g : giants)
+            if (g <= deg) n = g;
+        std::vector<double> q(deg - n + 1), r(c.begin(), c.begin() + n);
+        q[0] = c[n];
+        for (int j = 1; j <= deg - n; ++j) {
+            q[j] = 2.0 * c[n + j];
+            r[n - j] -= c[n + j];
         }
-    }
-    return add_const(acc, coeffs[0]);
+        PolyVal Q = rec(q), R = rec(r);
+        const ckks_ct& Tn = pw.T.at(n);
+        ckks_ctx* ctx = Tn.ctx;
+        ckks_ct prod;
+        bool hp = false;
+        if (Q.is_const) {
+            if (Q.cst != 0.0) {
+                const int lk = Tn.level;
+                const double s_c = (ctx->delta[lk - 1] * (double)ctx->q[lk]) / Tn.scale;
+                prod = rescale(mul_int(Tn, llround_away(Q.cst * s_c)));
+                prod.scale = (Tn.scale * s_c) / (double)ctx->q[lk];
+                hp = true;
+            }
+        } else {
+            const int lev = std::min(Q.ct.level, Tn.level);
+            prod = rescale(mul_relin(keys, level_down(Q.ct, lev), pw.at(n, lev)));
+            hp = true;
+        }
+        PolyVal out;
+        if (R.is_const) {
+            if (!hp) return R;
+            out.ct = add_const(prod, R.cst);
+            return out;
+        }
+        if (!hp) return R;
+        const int lev = std::min(prod.level, R.ct.level);
+        out.ct = add(level_down(prod, lev), level_down(R.ct, lev));
+        return out;
+    };
+    PolyVal res = rec(coeffs);
+    CK_CHECK(!res.is_const, CKKS_EINVAL, "polynomial evaluates to a constant");
+    CK_CHECK(res.ct.level >= want, CKKS_ELEVEL, "polynomial evaluation ended below its level budget");
+    return level_down(res.ct, want);
 }
 
 ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r) {
