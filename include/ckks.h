@@ -291,6 +291,15 @@ int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, cons
  * device) race on it. */
 int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, int level, uint64_t* d_out);
 
+/* HActivation (Sec. 2.4.2; Alg. 1 lines 3-4) as a composite polynomial ReLU:
+ * y = s_k(...s_1(x)) with each stage a Chebyshev series (coefficients concatenated in
+ * `coeffs`, degrees in degs[n_stages], evaluated as by ckks_eval_poly), then x * y with x
+ * brought down to y's level.  With s_1..s_{k-1} normalised odd sign approximations and
+ * s_k = (1 + sign approximation) / 2 this is x (1 + sign(x)) / 2.  Levels used:
+ * sum_i (ceil(log2 deg_i) + 1) + 1. */
+int ckks_eval_relu(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, const int* degs,
+                   int n_stages, ckks_ct* out);
+
 /* ---- raw kernels on caller device memory ---------------------------------- */
 /* In-place forward / inverse negacyclic NTT of n_limbs limbs at `dev` ([n_limbs][N]
  * uint64 device memory, residues < q); limb i uses the prime with global id

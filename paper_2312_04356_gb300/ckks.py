@@ -114,6 +114,7 @@ _SIGS = {
     "ckks_stoc1": [VP, VP, VP, VP, VP, VP],
     "ckks_block": [VP, VP, VP, VP, VP, VP],
     "ckks_eval_poly": [VP, VP, VP, VP, I, I, D, D, VP],
+    "ckks_eval_relu": [VP, VP, VP, VP, VP, I, VP],
     "ckks_rescale_noalloc": [VP, VP, I, VP],
     "ckks_ntt_forward": [VP, VP, I, VP],
     "ckks_ntt_inverse": [VP, VP, I, VP],
@@ -593,6 +594,15 @@ def ckks_eval_poly(ctx, keys, ct, coeffs, basis=CKKS_BASIS_CHEB, a=-1.0, b=1.0, 
     out = out or ckks_ct_create(ctx)
     c = _f64(coeffs)
     ctx.check(lib().ckks_eval_poly(ctx, keys, ct, _ptr(c), len(c) - 1, basis, a, b, out))
+    return out
+
+
+def ckks_eval_relu(ctx, keys, ct, stages, out=None):
+    """composite polynomial ReLU: stages = list of Chebyshev coefficient lists"""
+    out = out or ckks_ct_create(ctx)
+    c = _f64(np.concatenate([np.asarray(s, dtype=np.float64) for s in stages]))
+    degs = np.ascontiguousarray([len(s) - 1 for s in stages], dtype=np.int32)
+    ctx.check(lib().ckks_eval_relu(ctx, keys, ct, _ptr(c), _ptr(degs), len(stages), out))
     return out
 
 

@@ -993,6 +993,26 @@ int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, cons
     });
 }
 
+int ckks_eval_relu(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, const int* degs,
+                   int n_stages, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(in);
+        REQ(coeffs);
+        REQ(degs);
+        REQ(out);
+        CK_CHECK(n_stages >= 1, CKKS_EINVAL, "n_stages must be >= 1");
+        std::vector<std::vector<double>> st;
+        size_t off = 0;
+        for (int i = 0; i < n_stages; ++i) {
+            CK_CHECK(degs[i] >= 1, CKKS_EINVAL, "stage degree must be >= 1");
+            st.emplace_back(coeffs + off, coeffs + off + degs[i] + 1);
+            off += degs[i] + 1;
+        }
+        assign(out, ops::eval_relu(*keys, *in, st));
+    });
+}
+
 // ------------------------------------------------------------ raw NTT -------
 static int raw_ntt(ckks_ctx* ctx, uint64_t* dev, int n_limbs, const int32_t* ids, bool inv) {
     return guard(ctx, [&] {

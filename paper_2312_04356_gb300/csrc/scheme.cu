@@ -746,6 +746,16 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
     return level_down(res.ct, want);
 }
 
+// HActivation as a composite polynomial: y = s_k(...s_1(x)) by chained Chebyshev
+// evaluations, then x y with x brought down to y's level
+ckks_ct eval_relu(const ckks_keys& keys, const ckks_ct& x, const std::vector<std::vector<double>>& stages) {
+    CK_CHECK(!stages.empty(), CKKS_EINVAL, "no activation stages");
+    ckks_ct y = cheb_eval(keys, x, stages[0]);
+    for (size_t i = 1; i < stages.size(); ++i) y = cheb_eval(keys, y, stages[i]);
+    CK_CHECK(y.level >= 1, CKKS_ELEVEL, "not enough levels for the final product");
+    return rescale(mul_relin(keys, level_down(x, y.level), y));
+}
+
 ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r) {
     ckks_ct y = cheb_eval(keys, x, coeffs);
     for (int i = 0; i < r; ++i) {

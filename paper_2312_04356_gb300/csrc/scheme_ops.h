@@ -29,6 +29,7 @@ ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b);
 ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps);
 ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs);
 ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r);
+ckks_ct eval_relu(const ckks_keys& keys, const ckks_ct& x, const std::vector<std::vector<double>>& stages);
 void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, ckks_ct& re_out, ckks_ct& im_out);
 ckks_ct stoc1(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& re, const ckks_ct& im);
 ckks_ct block(const ckks_keys& keys, const ckks_boot& bt, const ckks_ptset& conv, const ckks_ct& in);

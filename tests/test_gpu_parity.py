@@ -261,6 +261,22 @@ def test_eval_poly_bitexact():
     assert_ct_equal(K, ctx, got, want, "eval_poly")
 
 
+def test_eval_relu_bitexact():
+    """HActivation: the (15, 15, 27) composite ReLU fitted by the oracle, bit-exact on the GPU,
+    decoded within 2^-12 of the FP64 polynomial ReLU"""
+    from oracle import relu as R
+    stages, _ = R.composite_relu_stages()
+    K, o, ctx, keys = make_pair("cfg2_small", 43)
+    P = o.P
+    v = np.random.default_rng(5).uniform(-1, 1, P.n // 2)
+    ct = o.encrypt(o.encode_pt(v, P.L, P.delta[P.L]), 1)
+    want = R.relu_eval(o, ct, stages)
+    got = K.ckks_eval_relu(ctx, keys, import_ct(K, ctx, ct), stages)
+    assert_ct_equal(K, ctx, got, want, "composite ReLU")
+    dec = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, got)).real
+    assert np.abs(dec - R.relu_poly_fp64(v, stages)).max() < 2.0 ** -12
+
+
 @pytest.mark.slow
 def test_cfg2_block_full_size():
     """config 2 at full size (N = 2^16, 24 limbs, 16 channels of 32x32, Gaussian weights):

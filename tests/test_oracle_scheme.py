@@ -183,3 +183,35 @@ def test_block_matches_fp64_conv():
     for i in range(cout):
         ref[i] = E.flatten_padded(conv[i], w)
     assert np.abs(pix - ref).max() < 2.0 ** -12
+
+
+def test_composite_relu_fit_and_eval():
+    """the fitted stages meet their minimax bounds on a dense grid; the composite is odd in
+    its sign part; decrypting the HActivation gives the FP64 polynomial ReLU"""
+    from oracle import relu as R
+    stages, info = R.composite_relu_stages()
+    assert [i["deg"] for i in info] == [15, 15, 27]
+    x = np.linspace(info[0]["eps"], 1, 20001)
+    y = x.copy()
+    for k, (s, inf) in enumerate(zip(stages, info)):
+        y = np.polynomial.chebyshev.chebval(y, s)
+        if k < len(stages) - 1:
+            # the LP is solved on a grid: off-grid points may exceed its bound by a hair
+            assert y.min() >= (1 - inf["tau"]) / (1 + inf["tau"]) - 1e-7 and y.max() <= 1 + 1e-7
+    # g = (1 + sign)/2 ~ 1 on [eps, 1] within the last stage's tau / 2
+    assert np.abs(y - 1).max() <= info[-1]["tau"] / 2 + 1e-7
+    assert info[-1]["tau"] < 1e-5
+    xs = np.linspace(-1, 1, 4001)
+    relu = R.relu_poly_fp64(xs, stages)
+    assert np.abs(relu - np.maximum(xs, 0)).max() <= info[0]["eps"]
+    # encrypted evaluation at small N
+    P = PP.Params(9, 20, 3, 60, 42, 60, h=32)
+    o = Oracle(P, 8)
+    o.gen_relin_key()
+    m = P.n // 2
+    v = np.random.default_rng(2).uniform(-1, 1, m)
+    ct = o.encrypt(o.encode_pt(v, P.L, P.delta[P.L]), 1)
+    out = R.relu_eval(o, ct, stages)
+    assert out.level == P.L - 17
+    got = slots(o, out).real
+    assert np.abs(got - R.relu_poly_fp64(v, stages)).max() < 2.0 ** -12
