@@ -41,6 +41,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
+    ap.add_argument("--batch", type=int, default=8, help="ciphertexts run concurrently for the batched figure")
     ap.add_argument("--kernel", default=None, choices=["ntt"],
                     help="time one kernel family alone on a buffer larger than L2 (for profiling)")
     return ap.parse_args()
@@ -139,7 +140,7 @@ def check_accuracy(K, s, out):
 
 
 # ------------------------------------------------------------ oracle arm -----
-def oracle_sample(seconds_budget):
+def oracle_sample(seconds_budget, counts=None):
     """Time the CPU oracle on a bounded sample of the block and scale it to ms per block.
 
     Sample: the fused conv at level 1, then at level 19 one hoisted rotation (one key
@@ -185,7 +186,7 @@ def oracle_sample(seconds_budget):
         if time.perf_counter() - start > seconds_budget * 0.5 or reps >= 8:
             break
     t_ks, t_rs, t_pm = t_ks / reps, t_rs / reps, t_pm / reps
-    counts = block_op_counts()
+    counts = counts or block_op_counts()
     est = t_conv + counts["keyswitch"] * t_ks + counts["rescale"] * t_rs + counts["pmult"] * t_pm
     cores = os.cpu_count()
     sample = ("oracle at N=2^16, config-2 chain: fused conv at level 1 (%.2f s) + %d x [1 key switch, 1 rescale, "
@@ -241,6 +242,8 @@ def run_ours(args):
     build.build()
     import paper_2312_04356_gb300.ckks as K
 
+    stream = torch.cuda.Stream()          # graphs cannot be captured on the legacy default stream
+    torch.cuda.set_stream(stream)
     s = block_setup(K, torch, seed=1 + rank)
     ctx = s["ctx"]
     out = K.ckks_ct_create(ctx)
@@ -248,13 +251,28 @@ def run_ours(args):
         K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
     K.ckks_sync(ctx)
     err = check_accuracy(K, s, out)
-    # operation counts of one block
+    # operation counts of one block, and of the same block without the zero-mask shortcut
     K.ckks_ctx_reset_counters(ctx)
     K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
     K.ckks_sync(ctx)
     counts = K.ckks_ctx_counters(ctx)
+    K.ckks_ctx_reset_counters(ctx)
+    x0 = K.ckks_conv2d_cins(ctx, s["keys"], s["ct"], s["conv"])
+    re, im = K.ckks_bootstrap(ctx, s["keys"], s["bt"], x0)
+    K.ckks_stoc1(ctx, s["keys"], re, im, s["bt"])
+    K.ckks_sync(ctx)
+    counts_full = K.ckks_ctx_counters(ctx)
+    del x0, re, im
 
-    stream = torch.cuda.current_stream()
+    # the block as a CUDA graph (one eager run inside, then capture)
+    gout = K.ckks_ct_create(ctx)
+    graph = K.ckks_block_graph_create(ctx, s["keys"], s["ct"], s["conv"], s["bt"], gout)
+    per_graph = K.ckks_graph_info(graph)
+    for _ in range(args.warmup):
+        K.ckks_graph_launch(graph)
+    K.ckks_sync(ctx)
+    err_graph = check_accuracy(K, s, gout)
+
     sampler = ClockSampler(local)
     sampler.start()
     if dist:
@@ -266,7 +284,7 @@ def run_ours(args):
         torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
-        K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
+        K.ckks_graph_launch(graph)
     e1.record(stream)
     torch.cuda.synchronize()
     if args.nvtx:
@@ -274,7 +292,6 @@ def run_ours(args):
     if dist:
         dist.barrier()
     t_ms = e0.elapsed_time(e1)
-    clocks = sampler.stop()
     launches = K.ckks_ctx_counters(ctx)["launches"] - launches0
     if dist:
         t = torch.tensor([t_ms], device="cuda")
@@ -283,23 +300,62 @@ def run_ours(args):
     ms_per_step = t_ms / args.steps
     value = t_ms / (args.steps * world)
 
-    # end to end through the C ABI with host buffers: import (H2D + NTT), block, export (iNTT + D2H)
+    # batched: B independent inputs, one graph each, on B streams at once
+    B = max(1, args.batch)
+    d = WL.PARAMS[CONFIG]
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    ins, outs, graphs = [], [], []
+    for b in range(B):
+        xb = WL.image(100 + b, s["spec"]["cin"], s["spec"]["w0"])
+        ins.append(K.ckks_encrypt(ctx, s["keys"], K.ckks_encode_image(ctx, xb, s["w"], 1, delta[1]), 100 + b))
+        outs.append(K.ckks_ct_create(ctx))
+        graphs.append(K.ckks_block_graph_create(ctx, s["keys"], ins[b], s["conv"], s["bt"], outs[b]))
+    streams = [torch.cuda.Stream() for _ in range(B)]
+    K.ckks_sync(ctx)
+
+    def batched_round(k):
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for st in streams:
+            st.wait_event(start)
+        for _ in range(k):
+            for b in range(B):
+                K.ckks_graph_launch(graphs[b], streams[b].cuda_stream)
+        for st in streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            stream.wait_event(ev)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        return start.elapsed_time(stop)
+
+    batched_round(1)
+    tb = batched_round(args.steps)
+    clocks = sampler.stop()
+    batched = {"B": B, "ct_per_s": round(B * args.steps / (tb / 1e3), 2),
+               "ms_per_ct": round(tb / (B * args.steps), 3), "streams": B,
+               "how": "B block graphs launched round-robin on B CUDA streams"}
+
+    # end to end through the C ABI with host buffers: import (H2D + NTT) into a staging handle,
+    # copy into the graph's input, replay, export (iNTT + D2H)
     host_in = torch.empty(K.ckks_ct_export_rns(ctx, s["ct"]).size, dtype=torch.int64, pin_memory=True).numpy()
     host_in[:] = K.ckks_ct_export_rns(ctx, s["ct"]).reshape(-1).view(np.int64)
     lev_in, sc_in = K.ckks_ct_info(s["ct"])
-    lev_out, _ = K.ckks_ct_info(out)
+    lev_out, _ = K.ckks_ct_info(gout)
     host_out = torch.empty(2 * (lev_out + 1) * ctx.n, dtype=torch.int64, pin_memory=True).numpy()
-    ct_in = K.ckks_ct_create(ctx)
+    stage = K.ckks_ct_create(ctx)
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        K.ckks_ct_import_rns(ctx, host_in.view(np.uint64), lev_in, sc_in, ct_in)
-        K.ckks_block(ctx, s["keys"], ct_in, s["conv"], s["bt"], out)
-        K.lib().ckks_ct_export_rns(ctx, out, host_out.ctypes.data_as(K.ctypes.c_void_p))
+        K.ckks_ct_import_rns(ctx, host_in.view(np.uint64), lev_in, sc_in, stage)
+        K.ckks_ct_copy_into(ctx, stage, s["ct"])
+        K.ckks_graph_launch(graph)
+        K.lib().ckks_ct_export_rns(ctx, gout, host_out.ctypes.data_as(K.ctypes.c_void_p))
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
 
-    # per-kernel CUDA-event timing of one more block (roofline of the dominant kernel)
+    # per-kernel CUDA-event timing of one more (eager) block: roofline of the dominant kernel
     K.ckks_ctx_reset_counters(ctx)
     K.ckks_ctx_set_timing(ctx, 1)
     K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
@@ -312,6 +368,7 @@ def run_ours(args):
     roof = {"kernel": top[0], "bound": "hbm", "achieved": round(achieved, 1), "peak": pk.get("hbm_gbs"),
             "unit": "GB/s", "frac": round(achieved / pk.get("hbm_gbs"), 4), "traffic": None,
             "share": round(top[1]["ms"] / total, 4),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if not pk.get("fallback") else "fallback",
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                             "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
                         for k, v in sorted(kst.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
@@ -320,7 +377,7 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         try:
-            v, cores, sample = oracle_sample(args.cpu_sample_seconds)
+            v, cores, sample = oracle_sample(args.cpu_sample_seconds, counts_full)
             cpu = {"value": round(v, 1), "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
         except Exception as e:  # the baseline is reported, never required
             cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": "failed: %s" % e}
@@ -330,11 +387,15 @@ def run_ours(args):
             "config": {"workload": "config-2 block: 16x32x32 -> 16, 3x3 conv fused with StoC2, full bootstrap "
                                    "(CtoS 3 levels, EvalMod deg 59 + 3 double angles, StoC1 3 levels), "
                                    "N=2^16, 24 limbs", "batch": 1, "l2": "working set > L2 (keys ~GBs)",
-                       "decoded_max_abs_err": err, "parallelism": "replicas" if world > 1 else "single"},
-            "clocks": clocks, "gpu_launches": launches,
+                       "decoded_max_abs_err": err, "decoded_max_abs_err_graph": err_graph,
+                       "execution": "CUDA graph replay of the block",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "clocks": clocks, "gpu_launches": launches, "launches_per_block": per_graph,
+            "batched": batched,
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(host_in.nbytes),
                     "d2h_bytes_per_step": int(host_out.nbytes)},
-            "roofline": roof, "op_counts": counts, "cpu_baseline": cpu}
+            "roofline": roof, "op_counts": counts, "op_counts_without_zero_mask_skip": counts_full,
+            "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

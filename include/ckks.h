@@ -130,6 +130,10 @@ int ckks_ct_set_scale(ckks_ct* ct, double scale);
 /* host [2][level+1][N] coefficient domain <-> device (NTT domain inside) */
 int ckks_ct_import_rns(ckks_ctx* ctx, const uint64_t* host, int level, double scale, ckks_ct* out);
 int ckks_ct_export_rns(ckks_ctx* ctx, const ckks_ct* ct, uint64_t* host);
+/* Copies src into dst's existing device buffer (same level required; dst keeps its
+ * address).  Every other call that writes a ciphertext handle may give it a new buffer,
+ * which matters to a CUDA graph that recorded the old one (see ckks_block_graph_create). */
+int ckks_ct_copy_into(ckks_ctx* ctx, const ckks_ct* src, ckks_ct* dst);
 int ckks_pt_create(ckks_ctx* ctx, ckks_pt** out);
 int ckks_pt_destroy(ckks_pt* pt);
 int ckks_pt_info(const ckks_pt* pt, int* level, double* scale);
@@ -263,6 +267,24 @@ int ckks_stoc1(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* re, const ck
 /* one conv2d + bootstrap block: conv2d_cins -> bootstrap -> stoc1 */
 int ckks_block(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
                const ckks_boot* bt, ckks_ct* out);
+
+/* ---- CUDA graphs ------------------------------------------------------------- */
+typedef struct ckks_graph ckks_graph;
+/* Records one ckks_block (in -> out) into a CUDA graph.  Runs the block once eagerly
+ * first (this sizes `out`), then captures a second run on the context's stream, whose
+ * result is copied into out's device buffer; intermediates are allocated and freed inside
+ * the graph.  The context must have been created on a non-default stream.  Each launch
+ * recomputes the block from whatever `in` holds then; `in` and `out` must stay alive and
+ * keep their device buffers while the graph exists: write new inputs with
+ * ckks_ct_copy_into, not with calls that reassign the handle.  Launches of one graph run one at a time;
+ * independent graphs (capture one per input) may run concurrently on different streams. */
+int ckks_block_graph_create(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
+                            const ckks_boot* bt, ckks_ct* out, ckks_graph** graph);
+/* cudaGraphLaunch on `stream` (a cudaStream_t; NULL = the context's stream) */
+int ckks_graph_launch(ckks_graph* graph, void* stream);
+/* number of kernel launches one replay performs */
+int ckks_graph_info(const ckks_graph* graph, int64_t* kernel_launches);
+int ckks_graph_destroy(ckks_graph* graph);
 
 /* ---- polynomial evaluation (HActivation) --------------------------------- */
 #define CKKS_BASIS_CHEB 0

@@ -74,4 +74,5 @@ def relu_eval(orc: Oracle, ct, stages):
     y = ct
     for s in stages:
         y = orc.cheb_eval(y, s)
-    return orc.rescale(orc.mul_relin(orc.level_down(ct, y.level), y))
+    lev = orc.prod_level(y.level)
+    return orc.rescale(orc.mul_relin(orc.level_down(ct, lev), orc.level_down(y, lev)))

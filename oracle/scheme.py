@@ -436,6 +436,24 @@ class Oracle:
 
     # ------------------------------------------------------- bootstrapping ----
     # ------------------------------------------------ Chebyshev evaluation ----
+    def prod_level(self, m):
+        """level at which to multiply two ciphertexts available at level m: a product at the
+        bottom level of the bootstrapping segment would not rescale onto the circuit
+        segment's canonical scale, so it is taken one level lower"""
+        P = self.P
+        if P.n_boot > 0 and P.n_circuit >= 1 and m == P.n_circuit + 1:
+            return m - 1
+        return m
+
+    def poly_out_level(self, level, depth):
+        """level after `depth` multiplicative levels from `level` (one more if the segment
+        boundary lies in between)"""
+        P = self.P
+        want = level - depth
+        if P.n_boot > 0 and P.n_circuit >= 1 and want <= P.n_circuit < level:
+            want -= 1
+        return want
+
     def cheb_powers(self, x, ks):
         """T_k(x) for every k in ks (and what they need): T_k = 2 T_ceil(k/2) T_floor(k/2) -
         T_(k mod 2 ? 1 : 0), operands brought to a common level by level_down."""
@@ -457,7 +475,7 @@ class Oracle:
             need(b)
             if a != b:
                 need(b - a)
-            m = min(T[a].level, T[b].level)
+            m = self.prod_level(min(T[a].level, T[b].level))
             t = self.rescale(self.mul_relin(at(a, m), at(b, m)))
             t = self.add(t, t)
             t = self.add_const(t, -1.0) if a == b else self.sub(t, at(b - a, m - 1))
@@ -540,7 +558,7 @@ class Oracle:
                     prod = self.rescale(self.mul_int(Tn, round_half_away(Q * s_c)))
                     prod.scale = (Tn.scale * s_c) / float(self.P.q[lk])
             else:
-                lev = min(Q.level, Tn.level)
+                lev = self.prod_level(min(Q.level, Tn.level))
                 prod = self.rescale(self.mul_relin(self.level_down(Q, lev), at(n, lev)))
             if isinstance(R, float):
                 return R if prod is None else self.add_const(prod, R)
@@ -551,7 +569,8 @@ class Oracle:
 
         out = rec(coeffs)
         assert not isinstance(out, float), "polynomial evaluates to a constant"
-        want = x.level - math.ceil(math.log2(d)) - 1 if d > 1 else x.level - 1
+        depth = math.ceil(math.log2(d)) if d > 1 else 0
+        want = self.poly_out_level(x.level, depth + 1)
         assert out.level >= want, (out.level, want)
         return self.level_down(out, want)
 

@@ -69,6 +69,7 @@ _SIGS = {
     "ckks_ct_set_scale": [VP, D],
     "ckks_ct_import_rns": [VP, VP, I, D, VP],
     "ckks_ct_export_rns": [VP, VP, VP],
+    "ckks_ct_copy_into": [VP, VP, VP],
     "ckks_pt_create": [VP, PVP],
     "ckks_pt_destroy": [VP],
     "ckks_pt_info": [VP, VP, VP],
@@ -114,6 +115,10 @@ _SIGS = {
     "ckks_stoc1": [VP, VP, VP, VP, VP, VP],
     "ckks_block": [VP, VP, VP, VP, VP, VP],
     "ckks_eval_poly": [VP, VP, VP, VP, I, I, D, D, VP],
+    "ckks_block_graph_create": [VP, VP, VP, VP, VP, VP, PVP],
+    "ckks_graph_launch": [VP, VP],
+    "ckks_graph_info": [VP, VP],
+    "ckks_graph_destroy": [VP],
     "ckks_eval_relu": [VP, VP, VP, VP, VP, I, VP],
     "ckks_rescale_noalloc": [VP, VP, I, VP],
     "ckks_ntt_forward": [VP, VP, I, VP],
@@ -213,6 +218,10 @@ class PtSet(_Handle):
 
 class Boot(_Handle):
     _destroy = "ckks_boot_destroy"
+
+
+class Graph(_Handle):
+    _destroy = "ckks_graph_destroy"
 
 
 # ------------------------------------------------------------- context ------
@@ -327,6 +336,10 @@ def ckks_ct_export_rns(ctx, ct):
     a = np.zeros((2, lev + 1, ctx.n), dtype=np.uint64)
     ctx.check(lib().ckks_ct_export_rns(ctx, ct, _ptr(a)))
     return a
+
+
+def ckks_ct_copy_into(ctx, src, dst):
+    ctx.check(lib().ckks_ct_copy_into(ctx, src, dst))
 
 
 def ckks_pt_create(ctx) -> Plaintext:
@@ -588,6 +601,24 @@ def ckks_block(ctx, keys, ct, conv, bt, out=None):
     out = out or ckks_ct_create(ctx)
     ctx.check(lib().ckks_block(ctx, keys, ct, conv, bt, out))
     return out
+
+
+def ckks_block_graph_create(ctx, keys, ct, conv, bt, out) -> Graph:
+    g = ctypes.c_void_p()
+    ctx.check(lib().ckks_block_graph_create(ctx, keys, ct, conv, bt, out, ctypes.byref(g)))
+    gr = Graph(g.value, ctx)
+    gr.refs = (keys, ct, conv, bt, out)     # the graph reads and writes these buffers
+    return gr
+
+
+def ckks_graph_launch(graph, stream=0):
+    graph.ctx.check(lib().ckks_graph_launch(graph, ctypes.c_void_p(stream)))
+
+
+def ckks_graph_info(graph):
+    n = ctypes.c_int64()
+    lib().ckks_graph_info(graph, ctypes.byref(n))
+    return n.value
 
 
 def ckks_eval_poly(ctx, keys, ct, coeffs, basis=CKKS_BASIS_CHEB, a=-1.0, b=1.0, out=None):

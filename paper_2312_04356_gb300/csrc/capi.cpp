@@ -32,6 +32,7 @@ int guard(const ckks_ctx* c, F&& f) {
 }
 
 #define REQ(p) CK_CHECK((p) != nullptr, CKKS_EINVAL, #p " is NULL")
+#define CT_OK(x) CK_CHECK((x) && (x)->level >= 0, CKKS_EINVAL, #x " is NULL or empty")
 
 void upload_coeffs(ckks_ctx* c, const std::vector<int64_t>& v, int level, double scale, ckks_pt* out) {
     const size_t n = c->n;
@@ -323,6 +324,18 @@ int ckks_ct_import_rns(ckks_ctx* ctx, const uint64_t* host, int level, double sc
     });
 }
 
+int ckks_ct_copy_into(ckks_ctx* ctx, const ckks_ct* src, ckks_ct* dst) {
+    return guard(ctx, [&] {
+        CT_OK(src);
+        CT_OK(dst);
+        CK_CHECK(src->level == dst->level, CKKS_EINVAL, "copy_into needs equal levels");
+        if (src == dst) return;
+        CUDA_CHECK(cudaMemcpyAsync(dst->buf.ptr, src->buf.ptr, 2 * (size_t)(src->level + 1) * ctx->n * 8,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+        dst->scale = src->scale;
+    });
+}
+
 int ckks_ct_export_rns(ckks_ctx* ctx, const ckks_ct* ct, uint64_t* host) {
     return guard(ctx, [&] {
         REQ(ctx);
@@ -536,7 +549,6 @@ int ckks_decrypt(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, ckks_p
 }
 
 // -------------------------------------------------------------- HE ops ------
-#define CT_OK(x) CK_CHECK((x) && (x)->level >= 0, CKKS_EINVAL, #x " is NULL or empty")
 
 int ckks_add(ckks_ctx* ctx, const ckks_ct* a, const ckks_ct* b, ckks_ct* out) {
     return guard(ctx, [&] {
@@ -977,6 +989,77 @@ int ckks_block(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ck
         REQ(out);
         assign(out, ops::block(*keys, *bt, *conv, *in));
     });
+}
+
+}  // extern "C"
+
+struct ckks_graph {
+    ckks_ctx* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    ~ckks_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+extern "C" {
+
+int ckks_block_graph_create(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
+                            const ckks_boot* bt, ckks_ct* out, ckks_graph** g) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(keys);
+        CT_OK(in);
+        REQ(conv);
+        REQ(bt);
+        REQ(out);
+        REQ(g);
+        CK_CHECK(ctx->stream != nullptr, CKKS_EINVAL, "graphs need a context created on a non-default stream");
+        CK_CHECK(out != in, CKKS_EINVAL, "out must not alias in");
+        // one eager block: sizes `out` and leaves every lazily built table in place
+        assign(out, ops::block(*keys, *bt, *conv, *in));
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        std::unique_ptr<ckks_graph> gr(new ckks_graph());
+        gr->ctx = ctx;
+        const long long l0 = ctx->launches;
+        CUDA_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            ckks_ct r = ops::block(*keys, *bt, *conv, *in);
+            CK_CHECK(r.level == out->level, CKKS_EINVAL, "captured block changed level");
+            CUDA_CHECK(cudaMemcpyAsync(out->buf.ptr, r.buf.ptr, 2 * (size_t)(r.level + 1) * ctx->n * 8,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        } catch (...) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(ctx->stream, &tmp);
+            if (tmp) cudaGraphDestroy(tmp);
+            throw;
+        }
+        CUDA_CHECK(cudaStreamEndCapture(ctx->stream, &gr->graph));
+        CUDA_CHECK(cudaGraphInstantiate(&gr->exec, gr->graph, 0));
+        gr->launches = ctx->launches - l0;
+        *g = gr.release();
+    });
+}
+
+int ckks_graph_launch(ckks_graph* g, void* stream) {
+    if (!g) return CKKS_EINVAL;
+    return guard(g->ctx, [&] {
+        CUDA_CHECK(cudaGraphLaunch(g->exec, stream ? (cudaStream_t)stream : g->ctx->stream));
+        g->ctx->launches += g->launches;
+    });
+}
+
+int ckks_graph_info(const ckks_graph* g, int64_t* kernel_launches) {
+    if (!g) return CKKS_EINVAL;
+    if (kernel_launches) *kernel_launches = g->launches;
+    return CKKS_OK;
+}
+
+int ckks_graph_destroy(ckks_graph* g) {
+    delete g;
+    return CKKS_OK;
 }
 
 int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, int deg, int basis,

@@ -174,6 +174,13 @@ struct KTimer {
     ~KTimer();
 };
 
+// Per-limb residues (and Shoup companions) passed to a kernel by value.
+struct ScalarVec {
+    static constexpr int MAX = 40;
+    u64 v[MAX];
+    u64 vp[MAX];
+};
+
 // ----------------------------------------------------------- kernel API --
 // All launchers enqueue on ctx->stream.  `ids` are device arrays of prime ids
 // (length lpp = limbs per polynomial); limb k of a multi-polynomial array uses ids[k % lpp].
@@ -190,6 +197,9 @@ void mul_acc(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, 
 // o = a * s[limb % lpp] (s residues, sp their Shoup companions; device arrays)
 void mul_scalar(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nlimbs, const int* ids,
                 int lpp);
+// by-value variants (no upload; usable inside stream capture)
+void mul_scalar_v(const ckks_ctx* c, const u64* a, const ScalarVec& sv, u64* o, int nlimbs, const int* ids, int lpp);
+void add_scalar_v(const ckks_ctx* c, u64* a, const ScalarVec& sv, int nlimbs, const int* ids, int lpp);
 // a[limb][*] += v[limb]: adds the constant polynomial v in the NTT domain (device array v)
 void add_const_term(const ckks_ctx* c, u64* a, const u64* v, int nlimbs, const int* ids);
 // signed small ints (device int64 [N]) -> residues [nlimbs][N] (coefficient domain)

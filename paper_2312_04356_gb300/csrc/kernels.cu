@@ -394,6 +394,24 @@ __global__ void k_mul_scalar(const u64* a, const u64* s, const u64* sp, u64* o, 
     const size_t off = (size_t)limb << logn;
     EW_LOOP(1 << logn) o[off + j] = mul_shoup(a[off + j], w, wp, q);
 }
+// per-limb scalars passed by value (no host-to-device copy, so the launch can be captured)
+__global__ void k_mul_scalar_v(const u64* a, ScalarVec sv, u64* o, const DevPrime* P, const int* ids, int lpp,
+                               int logn) {
+    const int limb = blockIdx.y;
+    const int r = limb % lpp;
+    const u64 q = P[ids[r]].m.q;
+    const u64 w = sv.v[r], wp = sv.vp[r];
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = mul_shoup(a[off + j], w, wp, q);
+}
+__global__ void k_add_scalar_v(u64* a, ScalarVec sv, const DevPrime* P, const int* ids, int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const int r = limb % lpp;
+    const u64 q = P[ids[r]].m.q;
+    const u64 c = sv.v[r];
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) a[off + j] = add_mod(a[off + j], c, q);
+}
 __global__ void k_add_scalar(u64* a, const u64* v, const DevPrime* P, const int* ids, int logn) {
     const int limb = blockIdx.y;
     const u64 q = P[ids[limb]].m.q;
@@ -646,6 +664,22 @@ void mul_scalar(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u6
     if (nl <= 0) return;
     { KTimer kt_(c, "mul_scalar", 2.0 * (double)nl * c->n * 8.0);
     k_mul_scalar<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, s, sp, o, c->d_primes, ids, lpp, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void mul_scalar_v(const ckks_ctx* c, const u64* a, const ScalarVec& sv, u64* o, int nl, const int* ids, int lpp) {
+    if (nl <= 0) return;
+    CK_CHECK(lpp <= ScalarVec::MAX, CKKS_EINVAL, "too many limbs for a by-value scalar vector");
+    { KTimer kt_(c, "mul_scalar", 2.0 * (double)nl * c->n * 8.0);
+    k_mul_scalar_v<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, sv, o, c->d_primes, ids, lpp, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void add_scalar_v(const ckks_ctx* c, u64* a, const ScalarVec& sv, int nl, const int* ids, int lpp) {
+    if (nl <= 0) return;
+    CK_CHECK(lpp <= ScalarVec::MAX, CKKS_EINVAL, "too many limbs for a by-value scalar vector");
+    { KTimer kt_(c, "add_scalar", 2.0 * (double)nl * c->n * 8.0);
+    k_add_scalar_v<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, sv, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }

@@ -243,6 +243,11 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
         }
     c->d_pinv = dev_upload_persistent(pinv);
     c->d_qlinv = dev_upload_persistent(qlinv);
+    // every base-conversion table up front (no allocation later, e.g. inside stream capture)
+    for (int l = 0; l <= c->L; ++l) {
+        c->moddown_tab(l);
+        for (int d = 0; d < (int)c->digits(l).size(); ++d) c->modup_tab(l, d);
+    }
     cudaMemPool_t pool;
     int dev = 0;
     CUDA_CHECK(cudaGetDevice(&dev));
@@ -322,14 +327,13 @@ void mul_plain_acc(ckks_ct& o, const ckks_ct& a, const ckks_pt& p) {
 ckks_ct mul_int(const ckks_ct& a, long long v) {
     ckks_ctx* c = a.ctx;
     const int nl = a.level + 1;
-    std::vector<u64> s(2 * nl);
+    ScalarVec sv;
     for (int i = 0; i < nl; ++i) {
-        s[i] = from_signed(v, c->q[i]);
-        s[nl + i] = shoup(s[i], c->q[i]);
+        sv.v[i] = from_signed(v, c->q[i]);
+        sv.vp[i] = shoup(sv.v[i], c->q[i]);
     }
-    DevBuf d = upload(c, s);
     ckks_ct o = new_ct(c, a.level, a.scale);
-    kern::mul_scalar(c, a.buf.ptr, d.ptr, d.ptr + nl, o.buf.ptr, 2 * nl, c->d_iota, nl);
+    kern::mul_scalar_v(c, a.buf.ptr, sv, o.buf.ptr, 2 * nl, c->d_iota, nl);
     return o;
 }
 
@@ -337,11 +341,10 @@ ckks_ct add_const(const ckks_ct& a, double cst) {
     ckks_ctx* c = a.ctx;
     const int nl = a.level + 1;
     long long v = llround_away(cst * a.scale);
-    std::vector<u64> s(nl);
-    for (int i = 0; i < nl; ++i) s[i] = from_signed(v, c->q[i]);
-    DevBuf d = upload(c, s);
+    ScalarVec sv;
+    for (int i = 0; i < nl; ++i) sv.v[i] = from_signed(v, c->q[i]);
     ckks_ct o = copy_ct(a);
-    kern::add_const_term(c, o.c0(), d.ptr, nl, c->d_iota);
+    kern::add_scalar_v(c, o.c0(), sv, nl, c->d_iota, nl);
     return o;
 }
 
@@ -588,6 +591,20 @@ ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps) {
 }
 
 // ------------------------------------------------ Chebyshev / EvalMod -----
+// Level at which to multiply two ciphertexts available at level m: a product at the
+// bottom level of the bootstrapping segment would not rescale onto the circuit segment's
+// canonical scale, so it is taken one level lower.
+static int prod_level(const ckks_ctx* c, int m) {
+    if (c->P.n_boot > 0 && c->n_circuit >= 1 && m == c->n_circuit + 1) return m - 1;
+    return m;
+}
+// level after `depth` multiplicative levels from `level` (one more across the boundary)
+static int poly_out_level(const ckks_ctx* c, int level, int depth) {
+    int want = level - depth;
+    if (c->P.n_boot > 0 && c->n_circuit >= 1 && want <= c->n_circuit && c->n_circuit < level) --want;
+    return want;
+}
+
 // T_k(x) for the requested k (and what they need): T_k = 2 T_ceil(k/2) T_floor(k/2) -
 // T_(k mod 2 ? 1 : 0), operands brought to a common level by level_down.
 struct ChebPowers {
@@ -608,7 +625,7 @@ struct ChebPowers {
         need(a);
         need(b);
         if (a != b) need(b - a);
-        const int m = std::min(T.at(a).level, T.at(b).level);
+        const int m = prod_level(T.at(a).ctx, std::min(T.at(a).level, T.at(b).level));
         ckks_ct t = rescale(mul_relin(*keys, at(a, m), at(b, m)));
         t = add(t, t);
         t = (a == b) ? add_const(t, -1.0) : sub(t, at(b - a, m - 1));
@@ -685,7 +702,7 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
     CK_CHECK(d >= 1, CKKS_EINVAL, "polynomial degree must be >= 1");
     int depth = 0;
     while ((1 << depth) < d) ++depth;
-    const int want = x.level - depth - 1;
+    const int want = poly_out_level(x.ctx, x.level, depth + 1);
     CK_CHECK(want >= 0, CKKS_ELEVEL, "not enough levels for the polynomial");
     int m = 0;
     while ((1 << m) < d + 1) ++m;
@@ -725,7 +742,7 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
                 hp = true;
             }
         } else {
-            const int lev = std::min(Q.ct.level, Tn.level);
+            const int lev = prod_level(ctx, std::min(Q.ct.level, Tn.level));
             prod = rescale(mul_relin(keys, level_down(Q.ct, lev), pw.at(n, lev)));
             hp = true;
         }
@@ -752,8 +769,9 @@ ckks_ct eval_relu(const ckks_keys& keys, const ckks_ct& x, const std::vector<std
     CK_CHECK(!stages.empty(), CKKS_EINVAL, "no activation stages");
     ckks_ct y = cheb_eval(keys, x, stages[0]);
     for (size_t i = 1; i < stages.size(); ++i) y = cheb_eval(keys, y, stages[i]);
-    CK_CHECK(y.level >= 1, CKKS_ELEVEL, "not enough levels for the final product");
-    return rescale(mul_relin(keys, level_down(x, y.level), y));
+    const int lev = prod_level(x.ctx, y.level);
+    CK_CHECK(lev >= 1, CKKS_ELEVEL, "not enough levels for the final product");
+    return rescale(mul_relin(keys, level_down(x, lev), level_down(y, lev)));
 }
 
 ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r) {

@@ -235,6 +235,34 @@ def test_block_small_bitexact():
     assert np.abs(_pixels(d, got) - _pixels(d, zexp)).max() < 2.0 ** -12
 
 
+def test_block_graph_replays_bitexact():
+    """the block recorded as a CUDA graph gives the eager block's ciphertext on every replay,
+    also for a new input written into the same handle"""
+    d = _block_pair("cfg2_small", 33)
+    K, o, ctx0, keys0 = d["K"], d["o"], d["ctx"], d["keys"]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = gpu_ctx("cfg2_small", 33)
+        keys = K.ckks_keygen(ctx, K.ckks_boot_rotations(d["bt"]) + [d["w"] ** 2 // 2 * k for k in range(1, 16)], True)
+        bt = K.ckks_boot_create(ctx, d["w"], d["spec"]["w0"], d["spec"]["cout"])
+        spec = d["spec"]
+        conv = K.ckks_ptset_conv_fused(ctx, d["W"], spec["cin"], spec["cout"], spec["f"], d["w"], 1, d["plan"].scale)
+        ct = K.ckks_encrypt(ctx, keys, import_pt(K, ctx, d["pt"]), 2)
+        want = K.ckks_ct_export_rns(ctx, K.ckks_block(ctx, keys, ct, conv, bt))
+        out = K.ckks_ct_create(ctx)
+        g = K.ckks_block_graph_create(ctx, keys, ct, conv, bt, out)
+        assert K.ckks_graph_info(g) > 100
+        for _ in range(2):
+            K.ckks_graph_launch(g)
+            K.ckks_sync(ctx)
+            assert (K.ckks_ct_export_rns(ctx, out) == want).all()
+        K.ckks_ct_copy_into(ctx, K.ckks_encrypt(ctx, keys, import_pt(K, ctx, d["pt"]), 9), ct)   # new input
+        want2 = K.ckks_ct_export_rns(ctx, K.ckks_block(ctx, keys, ct, conv, bt))
+        K.ckks_graph_launch(g)
+        K.ckks_sync(ctx)
+        assert (K.ckks_ct_export_rns(ctx, out) == want2).all()
+
+
 def test_block_small_own_plans():
     """same block with the library's own FP64 plans, masks and Chebyshev fit: decoded within 2^-12"""
     d = _block_pair("cfg2_small", 32, import_all=False)

@@ -215,3 +215,17 @@ def test_composite_relu_fit_and_eval():
     assert out.level == P.L - 17
     got = slots(o, out).real
     assert np.abs(got - R.relu_poly_fp64(v, stages)).max() < 2.0 ** -12
+
+
+def test_relu_across_segment_boundary():
+    """on the two-segment chain (48-bit bootstrapping levels over 42-bit circuit levels) the
+    composite ReLU, which runs across the boundary, still decodes to the FP64 polynomial"""
+    from oracle import relu as R
+    stages, _ = R.composite_relu_stages()
+    P = PP.Params(9, 24, 3, 60, 42, 60, h=32, n_p=7, boot_bits=48, n_boot=14)
+    o = Oracle(P, 43)
+    o.gen_relin_key()
+    v = np.random.default_rng(6).uniform(-1, 1, P.n // 2)
+    out = R.relu_eval(o, o.encrypt(o.encode_pt(v, P.L, P.delta[P.L]), 1), stages)
+    assert out.level == P.L - 18          # 17 levels + 1 for the boundary
+    assert np.abs(slots(o, out).real - R.relu_poly_fp64(v, stages)).max() < 2.0 ** -12
