@@ -246,6 +246,7 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     s = block_setup(K, torch, seed=1 + rank)
     ctx = s["ctx"]
+    tuned = K.ckks_autotune(ctx, 3)
     out = K.ckks_ct_create(ctx)
     for _ in range(args.warmup):
         K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
@@ -391,7 +392,7 @@ def run_ours(args):
                        "execution": "CUDA graph replay of the block",
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "gpu_launches": launches, "launches_per_block": per_graph,
-            "batched": batched,
+            "batched": batched, "autotune_ntt_variant_per_size_class": tuned,
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(host_in.nbytes),
                     "d2h_bytes_per_step": int(host_out.nbytes)},
             "roofline": roof, "op_counts": counts, "op_counts_without_zero_mask_skip": counts_full,
@@ -415,21 +416,25 @@ def run_kernel_ntt(args):
     ids = [i % len(mods) for i in range(nl)]
     x = WL.residues(1, [mods[i] for i in ids], ctx.n)
     dev = torch.from_numpy(x.view(np.int64)).cuda()
-    for _ in range(args.warmup):
-        K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)
-        K.ckks_ntt_inverse(ctx, dev.data_ptr(), nl, ids)
-    torch.cuda.synchronize()
-    K.ckks_ctx_reset_counters(ctx)
-    K.ckks_ctx_set_timing(ctx, 1)
-    for _ in range(args.steps):
-        K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)
-        K.ckks_ntt_inverse(ctx, dev.data_ptr(), nl, ids)
-    K.ckks_ctx_set_timing(ctx, 0)
-    st = K.ckks_ctx_kernel_stats(ctx)
-    ok = bool((dev.cpu().numpy().view(np.uint64) == x).all())
-    out = {k: {"launches": v["launches"], "us_per_launch": round(1e3 * v["ms"] / v["launches"], 2),
-               "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)} for k, v in st.items()}
-    print(json.dumps({"kernel": "ntt", "limbs": nl, "N": ctx.n, "roundtrip_exact": ok, "stats": out}))
+    res = {}
+    ok = True
+    for variant in (0, 1, 2, 3):
+        K.ckks_ctx_set_ntt_variant(ctx, variant)
+        for _ in range(args.warmup):
+            K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)
+            K.ckks_ntt_inverse(ctx, dev.data_ptr(), nl, ids)
+        torch.cuda.synchronize()
+        K.ckks_ctx_reset_counters(ctx)
+        K.ckks_ctx_set_timing(ctx, 1)
+        for _ in range(args.steps):
+            K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)
+            K.ckks_ntt_inverse(ctx, dev.data_ptr(), nl, ids)
+        K.ckks_ctx_set_timing(ctx, 0)
+        st = K.ckks_ctx_kernel_stats(ctx)
+        ok = ok and bool((dev.cpu().numpy().view(np.uint64) == x).all())
+        res[variant] = {k: {"launches": v["launches"], "us_per_launch": round(1e3 * v["ms"] / v["launches"], 2),
+                            "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)} for k, v in st.items()}
+    print(json.dumps({"kernel": "ntt", "limbs": nl, "N": ctx.n, "roundtrip_exact": ok, "per_variant": res}))
 
 
 if __name__ == "__main__":

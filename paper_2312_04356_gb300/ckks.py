@@ -59,6 +59,8 @@ _SIGS = {
     "ckks_ctx_counters": [VP, VP],
     "ckks_ctx_reset_counters": [VP],
     "ckks_ctx_kernel_stats": [VP, VP, I, VP],
+    "ckks_autotune": [VP, I, VP],
+    "ckks_ctx_set_ntt_variant": [VP, I],
     "ckks_keygen": [VP, VP, I, I, PVP],
     "ckks_keys_add_rotations": [VP, VP, VP, I],
     "ckks_keys_destroy": [VP],
@@ -284,6 +286,17 @@ def ckks_ctx_kernel_stats(ctx):
     ctx.check(lib().ckks_ctx_kernel_stats(ctx, buf, n.value + 1, ctypes.byref(n)))
     return {k: dict(launches=int(v[0]), ms=float(v[1]), bytes=float(v[2]))
             for k, v in json.loads(buf.value.decode()).items()}
+
+
+def ckks_autotune(ctx, reps=3):
+    """time the NTT launch variants per limb-count class and keep the fastest"""
+    a = np.zeros(8, dtype=np.int32)
+    ctx.check(lib().ckks_autotune(ctx, reps, _ptr(a)))
+    return [int(x) for x in a]
+
+
+def ckks_ctx_set_ntt_variant(ctx, variant):
+    ctx.check(lib().ckks_ctx_set_ntt_variant(ctx, variant))
 
 
 # ---------------------------------------------------------------- keys ------

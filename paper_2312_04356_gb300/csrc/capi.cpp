@@ -256,6 +256,23 @@ int ckks_ctx_kernel_stats(ckks_ctx* ctx, char* buf, int cap, int* len) {
     });
 }
 
+int ckks_autotune(ckks_ctx* ctx, int reps, int32_t* choice8) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        kern::autotune_ntt(ctx, reps > 0 ? reps : 3);
+        if (choice8)
+            for (int i = 0; i < 8; ++i) choice8[i] = ctx->ntt_choice[i];
+    });
+}
+
+int ckks_ctx_set_ntt_variant(ckks_ctx* ctx, int variant) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        CK_CHECK(variant >= -1 && variant <= 3, CKKS_EINVAL, "variant must be -1..3");
+        for (int i = 0; i < 8; ++i) ctx->ntt_choice[i] = variant;
+    });
+}
+
 // ---------------------------------------------------------------- keys ------
 int ckks_keygen(ckks_ctx* ctx, const int32_t* steps, int n, int want_conj, ckks_keys** out) {
     return guard(ctx, [&] {

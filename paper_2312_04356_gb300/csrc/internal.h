@@ -36,11 +36,10 @@ struct CkksError {
 // Per-prime constants, indexed by global prime id (q_0..q_L, then p_0..p_{np-1}).
 struct DevPrime {
     DevMod m;
-    const u64* tw;   // psi^rev(k), k < N          (forward, Cooley-Tukey)
-    const u64* twp;  // Shoup companions
-    const u64* itw;  // psi^-rev(k)                 (inverse, Gentleman-Sande)
-    const u64* itwp;
+    const ulonglong2* tw;    // (psi^rev(k), Shoup companion), k < N   (forward, Cooley-Tukey)
+    const ulonglong2* itw;   // (psi^-rev(k), Shoup companion)          (inverse, Gentleman-Sande)
     u64 n_inv, n_inv_p;
+    u64 r64, r64p;           // 2^64 mod q and its Shoup companion (128-bit lazy sums)
 };
 
 // Base-conversion table: inputs (prime ids in_ids, count nin) -> outputs (out_ids, nout).
@@ -86,9 +85,14 @@ struct ckks_ctx {
     u64* d_pinv = nullptr;                   // P^{-1} mod q_i [nq], Shoup [nq]
     u64* d_qlinv = nullptr;                  // q_l^{-1} mod q_i [nq][nq], Shoup [nq][nq]
     std::vector<int*> d_ext_ids;             // per level: [0..l] + specials
+    // per level: the rows of the raised digits that ModUp converts (offsets in limbs
+    // from the start of [ndig][next][N]) and their prime ids, for one NTT launch
+    std::vector<int*> d_modup_off, d_modup_pid;
+    std::vector<int> modup_nrows;
     std::map<std::pair<int, int>, std::unique_ptr<ConvTab>> modup_tabs;  // (level, digit)
     std::map<int, std::unique_ptr<ConvTab>> moddown_tabs;               // level
     std::string err;
+    int ntt_choice[8] = {-1, -1, -1, -1, -1, -1, -1, -1};   // tuned NTT variant per limb-count class
     std::map<std::string, long> ops;   // op counters (PMult, HRot, keyswitch, ...)
     // measurement: kernel launch count and, when timing is on, CUDA events around launches
     mutable long long launches = 0;
@@ -187,6 +191,17 @@ struct ScalarVec {
 namespace kern {
 // pstride: words between consecutive polynomials of lpp limbs (0 = lpp * N, contiguous)
 void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
+// forward NTT of an arbitrary list of limbs: limb i at data + off[i] * N with prime ids[i] (N = 2^16)
+void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, const int* ids);
+// o[poly][limb] = sum_t a_t[poly][limb] * p_t[limb] (two polynomials of nl limbs, t < n <= 16)
+struct BsgsTerms {
+    static constexpr int MAX = 16;
+    const u64* a[MAX];
+    const u64* p[MAX];
+    int n;
+};
+void bsgs_inner(const ckks_ctx* c, const BsgsTerms& t, u64* o, int nl);
+void autotune_ntt(ckks_ctx* c, int reps);
 void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void sub(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);

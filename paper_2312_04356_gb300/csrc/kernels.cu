@@ -148,12 +148,14 @@ __global__ void __launch_bounds__(NTT_THREADS)
             u64* py = sm + (k + tk) * stride + s;
             const u64 x = *px, y = *py;
             if (!INV) {
-                const u64 v = mul_shoup(y, P->tw[widx], P->twp[widx], q);
+                const ulonglong2 w = P->tw[widx];
+                const u64 v = mul_shoup(y, w.x, w.y, q);
                 *px = add_mod(x, v, q);
                 *py = sub_mod(x, v, q);
             } else {
                 *px = add_mod(x, y, q);
-                *py = mul_shoup(sub_mod(x, y, q), P->itw[widx], P->itwp[widx], q);
+                const ulonglong2 w = P->itw[widx];
+                *py = mul_shoup(sub_mod(x, y, q), w.x, w.y, q);
             }
         }
         __syncthreads();
@@ -216,7 +218,8 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[16], int t, int hi, int s0, c
         for (int i = 0; i < 16; ++i) {
             if (i & is) continue;
             const int idx = ROUND_B ? base + (t << s) + (i >> (4 - s)) : base + (i >> (4 - s));
-            ct_bfly(x[i], x[i + is], __ldg(P->tw + idx), __ldg(P->twp + idx), q, q2);
+            const ulonglong2 w = __ldg(P->tw + idx);
+            ct_bfly(x[i], x[i + is], w.x, w.y, q, q2);
         }
     }
 }
@@ -233,7 +236,8 @@ __device__ __forceinline__ void inv_round(u64 (&x)[16], int t, int hi, int s0, c
         for (int i = 0; i < 16; ++i) {
             if (i & is) continue;
             const int idx = ROUND_B ? base + (t << s) + (i >> (4 - s)) : base + (i >> (4 - s));
-            gs_bfly(x[i], x[i + is], __ldg(P->itw + idx), __ldg(P->itwp + idx), q, q2);
+            const ulonglong2 w = __ldg(P->itw + idx);
+            gs_bfly(x[i], x[i + is], w.x, w.y, q, q2);
         }
     }
 }
@@ -241,15 +245,17 @@ __device__ __forceinline__ void inv_round(u64 (&x)[16], int t, int hi, int s0, c
 // COL: sub-problems are columns (s0 = 0, T1 = 256, element j = k*256 + lo), threads with
 //      consecutive tid take consecutive columns.  ROW: sub-problems are contiguous rows
 //      (s0 = 8, T1 = 1, j = hi*256 + k), consecutive tid take consecutive k.
-template <bool COL, bool INV, int SUBS>
-__global__ void __launch_bounds__(16 * SUBS) k_ntt16(u64* __restrict__ data, const DevPrime* __restrict__ primes,
-                                                    const int* __restrict__ ids, int lpp, size_t pstride) {
+template <bool COL, bool INV, int SUBS, int MINB>
+__global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ data, const DevPrime* __restrict__ primes,
+                                                    const int* __restrict__ ids, int lpp, size_t pstride,
+                                                    const int* __restrict__ loff) {
     __shared__ u64 sm[SUBS * F_STRIDE];
     const int limb = blockIdx.y;
-    const int r = limb % lpp;
+    const int r = loff ? limb : limb % lpp;
     const DevPrime* P = primes + ids[r];
     const u64 q = P->m.q, q2 = 2 * q;
-    u64* a = data + (size_t)(limb / lpp) * pstride + ((size_t)r << 16);
+    u64* a = loff ? data + ((size_t)loff[limb] << 16)
+                  : data + (size_t)(limb / lpp) * pstride + ((size_t)r << 16);
     const int tid = threadIdx.x;
     const int sp = COL ? (tid % SUBS) : (tid >> 4);
     const int t = COL ? (tid / SUBS) : (tid & 15);
@@ -318,14 +324,47 @@ __global__ void __launch_bounds__(16 * SUBS) k_ntt16(u64* __restrict__ data, con
 }
 
 // few limbs: 64-thread CTAs (4 sub-problems) so that the grid still covers the SMs
+// Variants (identical results): CTA of 16 or 4 sub-problems, register budget for 3 or 4
+// resident 256-thread CTAs per SM.  ckks_autotune times them per limb-count class; the
+// default (no tuning) is 16 sub-problems at >= 16 limbs, else 4, 80 registers.
+enum NttVariant { NTT_V16_R80 = 0, NTT_V16_R64 = 1, NTT_V4_R80 = 2, NTT_V4_R64 = 3, NTT_NVARIANTS = 4 };
+
 template <bool COL, bool INV>
-void launch_ntt16(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride) {
-    KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0);
-    if (nlimbs >= 16) {
-        k_ntt16<COL, INV, 16><<<dim3(256 / 16, nlimbs), 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride);
-    } else {
-        k_ntt16<COL, INV, 4><<<dim3(256 / 4, nlimbs), 64, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride);
+void launch_ntt16_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp,
+                          size_t pstride, const int* loff) {
+    switch (v) {
+        case NTT_V16_R80:
+            k_ntt16<COL, INV, 16, 3>
+                <<<dim3(256 / 16, nlimbs), 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
+            break;
+        case NTT_V16_R64:
+            k_ntt16<COL, INV, 16, 4>
+                <<<dim3(256 / 16, nlimbs), 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
+            break;
+        case NTT_V4_R80:
+            k_ntt16<COL, INV, 4, 8>
+                <<<dim3(256 / 4, nlimbs), 64, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
+            break;
+        default:
+            k_ntt16<COL, INV, 4, 12>
+                <<<dim3(256 / 4, nlimbs), 64, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
+            break;
     }
+}
+
+inline int ntt_class(int nlimbs) {
+    int c = 0;
+    while (c < 7 && (2 << c) <= nlimbs) ++c;   // classes: 1, 2-3, 4-7, 8-15, 16-31, 32-63, 64-127, >=128
+    return c;
+}
+
+template <bool COL, bool INV>
+void launch_ntt16(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
+                  const int* loff = nullptr) {
+    KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0);
+    int v = cx->ntt_choice[ntt_class(nlimbs)];
+    if (v < 0) v = nlimbs >= 16 ? NTT_V16_R80 : NTT_V4_R80;
+    launch_ntt16_variant<COL, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff);
 }
 
 struct PassPlan {
@@ -443,7 +482,7 @@ __global__ void k_imult(const u64* a, u64* o, const DevPrime* P, const int* ids,
     const u64 q = pr->m.q;
     // X^{N/2} at psi^(2r+1): psi^{N/2} when r is even, -psi^{N/2} when r is odd;
     // psi^{N/2} = tw[1] since rev(1) = N/2
-    const u64 w = pr->tw[1], wp = pr->twp[1];
+    const u64 w = pr->tw[1].x, wp = pr->tw[1].y;
     const size_t off = (size_t)limb << logn;
     EW_LOOP(1 << logn) {
         u64 v = mul_shoup(a[off + j], w, wp, q);
@@ -465,6 +504,30 @@ __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const
     const u64 w = s[r], wp = sp[r];
     const size_t off = (size_t)limb << logn;
     EW_LOOP(1 << logn) o[off + j] = mul_shoup(sub_mod(a[off + j], b[off + j], q), w, wp, q);
+}
+
+// ------------------------------------------------- BSGS inner products ----
+// o[poly][limb] = sum_t a_t[poly][limb] * p_t[limb]: the products are summed exactly in
+// 128 bits (each < 2^122, at most 16 terms) and reduced once.
+__device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P) {
+    return add_mod(mul_shoup(hi, P.r64, P.r64p, P.m.q), reduce64(lo, P.m), P.m.q);
+}
+__global__ void k_bsgs_inner(kern::BsgsTerms T, u64* __restrict__ o, const DevPrime* __restrict__ primes, int nl,
+                             int logn) {
+    const int limb = blockIdx.y;           // 0 .. 2 nl - 1, polynomial-major
+    const int r = limb % nl;
+    const DevPrime P = primes[r];
+    const size_t offa = (size_t)limb << logn, offp = (size_t)r << logn;
+    EW_LOOP(1 << logn) {
+        u64 lo = 0, hi = 0;
+        for (int t = 0; t < T.n; ++t) {
+            const u64 x = T.a[t][offa + j], y = T.p[t][offp + j];
+            const u64 pl = x * y, ph = __umul64hi(x, y);
+            lo += pl;
+            hi += ph + (lo < pl ? 1ull : 0ull);
+        }
+        o[offa + j] = reduce128_lazy(hi, lo, P);
+    }
 }
 
 // ------------------------------------------------------- base conversion ----
@@ -605,6 +668,67 @@ void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
     }
     CK_CHECK(pstride == (size_t)lpp * c->n, CKKS_EINVAL, "strided polynomials need N = 2^16");
     for (const PassPlan& p : ntt_passes(c->logn)) launch_pass<false>(c, data, nlimbs, ids, lpp, p, 0);
+    LAUNCH_CHECK();
+}
+
+// Time every NTT variant (forward + inverse) on scratch limbs of each size class and keep the
+// fastest per class in ctx->ntt_choice.  Results are identical for every variant.
+void autotune_ntt(ckks_ctx* c, int reps) {
+    if (c->logn != 16) return;
+    const int sizes[8] = {1, 2, 7, 14, 24, 48, 96, 192};
+    DevBuf buf((size_t)192 << 16, c->stream);
+    CUDA_CHECK(cudaMemsetAsync(buf.ptr, 0, ((size_t)192 << 16) * 8, c->stream));
+    std::vector<int> ids(192);
+    for (int i = 0; i < 192; ++i) ids[i] = i % c->nall;
+    DevBuf dids(96, c->stream);
+    CUDA_CHECK(cudaMemcpyAsync(dids.ptr, ids.data(), 192 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int k = 0; k < 8; ++k) {
+        const int nl = sizes[k];
+        float best = 1e30f;
+        int bestv = -1;
+        for (int v = 0; v < NTT_NVARIANTS; ++v) {
+            for (int w = 0; w < 2; ++w) {   // warm up, then time
+                cudaEventRecord(e0, c->stream);
+                for (int r = 0; r < reps; ++r) {
+                    const int* d = (const int*)dids.ptr;
+                    launch_ntt16_variant<true, false>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
+                    launch_ntt16_variant<false, false>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
+                    launch_ntt16_variant<false, true>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
+                    launch_ntt16_variant<true, true>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
+                }
+                cudaEventRecord(e1, c->stream);
+                CUDA_CHECK(cudaEventSynchronize(e1));
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bestv = v;
+            }
+        }
+        c->ntt_choice[k] = bestv;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    LAUNCH_CHECK();
+}
+
+void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, const int* ids) {
+    if (nlimbs <= 0) return;
+    CK_CHECK(c->logn == 16, CKKS_EINVAL, "limb-list NTT needs N = 2^16");
+    launch_ntt16<true, false>(c, data, nlimbs, ids, nlimbs, 0, off);
+    launch_ntt16<false, false>(c, data, nlimbs, ids, nlimbs, 0, off);
+    LAUNCH_CHECK();
+}
+
+void bsgs_inner(const ckks_ctx* c, const BsgsTerms& t, u64* o, int nl) {
+    CK_CHECK(t.n >= 1 && t.n <= BsgsTerms::MAX, CKKS_EINVAL, "1..16 BSGS terms per kernel");
+    { KTimer kt_(c, "bsgs_inner", (2.0 * t.n + t.n + 2.0) * nl * c->n * 8.0);
+    k_bsgs_inner<<<ew_grid(c->n, 2 * nl), EW_THREADS, 0, c->stream>>>(t, o, c->d_primes, nl, c->logn);
+    }
     LAUNCH_CHECK();
 }
 

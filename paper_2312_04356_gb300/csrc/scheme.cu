@@ -144,6 +144,8 @@ ckks_ctx::~ckks_ctx() {
     for (auto& kv : modup_tabs) free_tab(kv.second.get());
     for (auto& kv : moddown_tabs) free_tab(kv.second.get());
     for (int* p : d_ext_ids) cudaFree(p);
+    for (int* p : d_modup_off) cudaFree(p);
+    for (int* p : d_modup_pid) cudaFree(p);
     cudaFree(d_iota);
     cudaFree(d_primes);
     cudaFree(d_tables);
@@ -183,7 +185,7 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
     c->mod_of = c->q;
     c->mod_of.insert(c->mod_of.end(), c->p.begin(), c->p.end());
     const int n = c->n, logn = c->logn;
-    // twiddle tables: per prime 4 arrays of N words
+    // twiddle tables: per prime 2 arrays of N (value, Shoup companion) pairs
     std::vector<u64> tables((size_t)c->nall * 4 * n);
     std::vector<DevPrime> primes(c->nall);
     c->psi.resize(c->nall);
@@ -204,20 +206,20 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
         u64* base = tables.data() + (size_t)id * 4 * n;
         for (int k = 0; k < n; ++k) {
             unsigned r = brev_host(k, logn);
-            base[k] = pw[r];
-            base[n + k] = shoup(pw[r], qq);
-            base[2 * n + k] = ipw[r];
-            base[3 * n + k] = shoup(ipw[r], qq);
+            base[2 * k] = pw[r];
+            base[2 * k + 1] = shoup(pw[r], qq);
+            base[2 * n + 2 * k] = ipw[r];
+            base[2 * n + 2 * k + 1] = shoup(ipw[r], qq);
         }
         DevPrime& dp = primes[id];
         dp.m = c->mods[id];
         const u64* dbase = c->d_tables + (size_t)id * 4 * n;
-        dp.tw = dbase;
-        dp.twp = dbase + n;
-        dp.itw = dbase + 2 * n;
-        dp.itwp = dbase + 3 * n;
+        dp.tw = reinterpret_cast<const ulonglong2*>(dbase);
+        dp.itw = reinterpret_cast<const ulonglong2*>(dbase + 2 * n);
         dp.n_inv = invmod((u64)n % qq, qq);
         dp.n_inv_p = shoup(dp.n_inv, qq);
+        dp.r64 = (u64)(((unsigned __int128)1 << 64) % qq);
+        dp.r64p = shoup(dp.r64, qq);
     }
     CUDA_CHECK(cudaMemcpy(c->d_tables, tables.data(), tables.size() * sizeof(u64), cudaMemcpyHostToDevice));
     c->d_primes = dev_upload_persistent(primes);
@@ -246,7 +248,20 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
     // every base-conversion table up front (no allocation later, e.g. inside stream capture)
     for (int l = 0; l <= c->L; ++l) {
         c->moddown_tab(l);
-        for (int d = 0; d < (int)c->digits(l).size(); ++d) c->modup_tab(l, d);
+        std::vector<std::vector<int>> dig = c->digits(l);
+        std::vector<int> ext = c->ext_ids(l), off, pid;
+        const int next = (int)ext.size();
+        for (int d = 0; d < (int)dig.size(); ++d) {
+            c->modup_tab(l, d);
+            for (int r = 0; r < next; ++r) {
+                if (r >= dig[d].front() && r <= dig[d].back()) continue;
+                off.push_back(d * next + r);
+                pid.push_back(ext[r]);
+            }
+        }
+        c->d_modup_off.push_back(dev_upload_persistent(off));
+        c->d_modup_pid.push_back(dev_upload_persistent(pid));
+        c->modup_nrows.push_back((int)off.size());
     }
     cudaMemPool_t pool;
     int dev = 0;
@@ -439,9 +454,13 @@ DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out) {
         kern::base_convert(c, t, coef.ptr + (size_t)lo * n, n, Dd, n, 1, 0, 0);
         CUDA_CHECK(cudaMemcpyAsync(Dd + (size_t)lo * n, x + (size_t)lo * n, (size_t)(hi - lo) * n * 8,
                                    cudaMemcpyDeviceToDevice, c->stream));
-        if (lo > 0) kern::ntt_forward(c, Dd, lo, ext, lo);
-        if (next > hi) kern::ntt_forward(c, Dd + (size_t)hi * n, next - hi, ext + hi, next - hi);
+        if (c->logn != 16) {
+            if (lo > 0) kern::ntt_forward(c, Dd, lo, ext, lo);
+            if (next > hi) kern::ntt_forward(c, Dd + (size_t)hi * n, next - hi, ext + hi, next - hi);
+        }
     }
+    if (c->logn == 16)   // every converted row of every digit in one launch
+        kern::ntt_forward_list(c, D.ptr, c->modup_nrows[level], c->d_modup_off[level], c->d_modup_pid[level]);
     *ndig_out = ndig;
     return D;
 }
@@ -564,20 +583,22 @@ ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps) {
     ckks_ct out;
     bool have = false;
     for (int g = 0; g < ps.G(); ++g) {
-        ckks_ct inner;
-        bool hin = false;
+        kern::BsgsTerms terms;
+        terms.n = 0;
+        double sc = 0;
         for (int b = 0; b < ps.B; ++b) {
             auto it = ps.pts.find(std::make_pair(g, b));
             if (it == ps.pts.end()) continue;
-            const ckks_ct& x = baby[bidx[b]];
-            if (!hin) {
-                inner = mul_plain(x, *it->second);
-                hin = true;
-            } else {
-                mul_plain_acc(inner, x, *it->second);
-            }
+            CK_CHECK(terms.n < kern::BsgsTerms::MAX, CKKS_EINVAL, "more than 16 baby steps");
+            terms.a[terms.n] = baby[bidx[b]].buf.ptr;
+            terms.p[terms.n] = it->second->buf.ptr;
+            sc = a.scale * it->second->scale;
+            ++terms.n;
+            c->ops["pmult"]++;
         }
-        if (!hin) continue;
+        if (!terms.n) continue;
+        ckks_ct inner = new_ct(c, a.level, sc);
+        kern::bsgs_inner(c, terms, inner.buf.ptr, a.level + 1);
         const long long R = (((long long)ps.a0 + (long long)ps.step * g * ps.B) % m + m) % m;
         if (R) inner = rotate(keys, inner, R);
         if (!have) {
