@@ -232,6 +232,22 @@ void sub_mul_scalar(const ckks_ctx* c, const u64* a, const u64* b, const u64* s,
 // out rows written at out + out_row[m]*N
 void base_convert(const ckks_ctx* c, const ConvTab& t, const u64* in, size_t in_stride, u64* out,
                   size_t out_stride, int npoly, size_t in_poly_stride, size_t out_poly_stride);
+// several conversions in one launch (e.g. every digit of a ModUp)
+struct ConvJob {
+    const u64* in;
+    u64* out;
+    const int *in_ids, *out_ids, *out_rows;
+    const u64 *qinv, *qmod;
+    int nin, nout, ngroups;
+    size_t in_pstride, out_pstride;
+};
+struct ConvJobs {
+    static constexpr int MAX = 4;
+    int n;
+    ConvJob job[MAX];
+};
+void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t in_pstride, size_t out_pstride);
+void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly);
 // key-switch inner product: D [ndig][next][N], key rows krow[e] of [ndig][nall][N];
 // ob/oa [next][N] = sum_d D_d(sigma_g) * key_d ; g = 1 means no automorphism
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,

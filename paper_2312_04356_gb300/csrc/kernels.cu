@@ -532,66 +532,70 @@ __global__ void k_bsgs_inner(kern::BsgsTerms T, u64* __restrict__ o, const DevPr
 
 // ------------------------------------------------------- base conversion ----
 // y_m = sum_i [x_i * qhat_i^{-1}]_{q_i} * (qhat_i mod p_m)  (no correction term)
-// One thread per coefficient; grid.z splits the outputs in groups of CONV_OUT.  The
-// products are summed exactly in 128 bits (each < 2^122, at most 16 terms) and reduced
-// once: (H 2^64 + L) mod p = H (2^64 mod p) + L mod p.
+// One thread per coefficient; grid.z walks over (job, group of CONV_OUT outputs), so the
+// digits of one ModUp (or the two halves of one ModDown) share a launch.  The products are
+// summed exactly in 128 bits (each < 2^122, at most 16 terms) and reduced once:
+// (H 2^64 + L) mod p = H (2^64 mod p) + L mod p.  The output loop is unrolled so that the
+// CONV_OUT independent accumulations interleave.
 constexpr int MAX_CONV_IN = 16;
 constexpr int CONV_OUT = 8;
-__global__ void __launch_bounds__(256)
-    k_base_convert(const u64* __restrict__ in, size_t in_stride, u64* __restrict__ out, size_t out_stride, int nin,
-                   int nout, const int* __restrict__ in_ids, const int* __restrict__ out_ids,
-                   const int* __restrict__ out_rows, const u64* __restrict__ qinv, const u64* __restrict__ qmod,
-                   const DevPrime* __restrict__ P, int logn, size_t in_pstride, size_t out_pstride) {
+__global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn) {
     __shared__ u64 s_qi[MAX_CONV_IN], s_qinv[MAX_CONV_IN], s_qinvp[MAX_CONV_IN];
     __shared__ u64 s_c[CONV_OUT][MAX_CONV_IN];
-    __shared__ DevMod s_pm[CONV_OUT];
-    __shared__ u64 s_two64[CONV_OUT], s_two64p[CONV_OUT];
+    __shared__ DevPrime s_pm[CONV_OUT];
     __shared__ int s_row[CONV_OUT];
-    const int m0 = blockIdx.z * CONV_OUT;
+    // which job and output group this CTA serves
+    int z = blockIdx.z, jb = 0;
+    while (jb < J.n - 1 && z >= J.job[jb].ngroups) {
+        z -= J.job[jb].ngroups;
+        ++jb;
+    }
+    const kern::ConvJob& job = J.job[jb];
+    const int nin = job.nin, nout = job.nout;
+    const int m0 = z * CONV_OUT;
     const int mcount = min(CONV_OUT, nout - m0);
     const int tid = threadIdx.x;
     if (tid < nin) {
-        s_qi[tid] = P[in_ids[tid]].m.q;
-        s_qinv[tid] = qinv[tid];
-        s_qinvp[tid] = qinv[nin + tid];
+        s_qi[tid] = P[job.in_ids[tid]].m.q;
+        s_qinv[tid] = job.qinv[tid];
+        s_qinvp[tid] = job.qinv[nin + tid];
     }
-    if (tid < mcount * MAX_CONV_IN) {
+    if (tid < CONV_OUT * MAX_CONV_IN) {
         const int m = tid / MAX_CONV_IN, i = tid % MAX_CONV_IN;
-        s_c[m][i] = i < nin ? qmod[(size_t)(m0 + m) * nin + i] : 0;
+        s_c[m][i] = (m < mcount && i < nin) ? job.qmod[(size_t)(m0 + m) * nin + i] : 0;
     }
     if (tid < mcount) {
-        const DevMod pm = P[out_ids[m0 + tid]].m;
-        s_pm[tid] = pm;
-        const u64 t64 = barrett_reduce128(1, 0, pm);   // 2^64 mod p
-        s_two64[tid] = t64;
-        s_two64p[tid] = (u64)(((unsigned __int128)t64 << 64) / pm.q);
-        s_row[tid] = out_rows[m0 + tid];
+        s_pm[tid] = P[job.out_ids[m0 + tid]];
+        s_row[tid] = job.out_rows[m0 + tid];
     }
     __syncthreads();
-    const int poly = blockIdx.y;
-    in += poly * in_pstride;
-    out += poly * out_pstride;
+    const u64* in = job.in + blockIdx.y * job.in_pstride;
+    u64* out = job.out + blockIdx.y * job.out_pstride;
     const int j = blockIdx.x * blockDim.x + tid;
     if (j >= (1 << logn)) return;
+    const size_t n = (size_t)1 << logn;
     u64 xh[MAX_CONV_IN];
 #pragma unroll
     for (int i = 0; i < MAX_CONV_IN; ++i)
-        if (i < nin) xh[i] = mul_shoup(in[i * in_stride + j], s_qinv[i], s_qinvp[i], s_qi[i]);
-    for (int m = 0; m < mcount; ++m) {
-        u64 lo = 0, hi = 0;
+        if (i < nin) xh[i] = mul_shoup(in[i * n + j], s_qinv[i], s_qinvp[i], s_qi[i]);
+    u64 lo[CONV_OUT], hi[CONV_OUT];
 #pragma unroll
-        for (int i = 0; i < MAX_CONV_IN; ++i) {
-            if (i < nin) {
+    for (int m = 0; m < CONV_OUT; ++m) lo[m] = hi[m] = 0;
+#pragma unroll
+    for (int i = 0; i < MAX_CONV_IN; ++i) {
+        if (i < nin) {
+#pragma unroll
+            for (int m = 0; m < CONV_OUT; ++m) {
                 const u64 c = s_c[m][i];
                 const u64 pl = xh[i] * c, ph = __umul64hi(xh[i], c);
-                lo += pl;
-                hi += ph + (lo < pl ? 1ull : 0ull);
+                lo[m] += pl;
+                hi[m] += ph + (lo[m] < pl ? 1ull : 0ull);
             }
         }
-        const DevMod pm = s_pm[m];
-        const u64 r = add_mod(mul_shoup(hi, s_two64[m], s_two64p[m], pm.q), reduce64(lo, pm), pm.q);
-        out[(size_t)s_row[m] * out_stride + j] = r;
     }
+#pragma unroll
+    for (int m = 0; m < CONV_OUT; ++m)
+        if (m < mcount) out[(size_t)s_row[m] * n + j] = reduce128_lazy(hi[m], lo[m], s_pm[m]);
 }
 
 // ---------------------------------------------------- key-switch product ----
@@ -854,17 +858,46 @@ void sub_mul_scalar(const ckks_ctx* c, const u64* a, const u64* b, const u64* s,
 }
 void base_convert(const ckks_ctx* c, const ConvTab& t, const u64* in, size_t in_stride, u64* out,
                   size_t out_stride, int npoly, size_t in_pstride, size_t out_pstride) {
+    CK_CHECK(in_stride == (size_t)c->n && out_stride == (size_t)c->n, CKKS_EINVAL, "limbs must be contiguous");
+    ConvJobs J;
+    J.n = 0;
+    add_conv_job(J, t, in, out, in_pstride, out_pstride);
+    base_convert_jobs(c, J, npoly);
+}
+
+void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t in_pstride, size_t out_pstride) {
+    CK_CHECK(J.n < ConvJobs::MAX, CKKS_EINVAL, "too many base-conversion jobs");
     CK_CHECK(t.nin <= MAX_CONV_IN, CKKS_EINVAL, "base conversion with more than 16 input limbs");
-    if (t.nout == 0) return;
-    dim3 grid((c->n + 255) / 256, npoly, (t.nout + CONV_OUT - 1) / CONV_OUT);
-    // d_out_ids is followed by out_rows in the same allocation
-    { KTimer kt_(c, "base_convert", (double)npoly * (t.nin + t.nout) * c->n * 8.0);
-    k_base_convert<<<grid, 256, 0, c->stream>>>(in, in_stride, out, out_stride, t.nin, t.nout, t.d_in_ids,
-                                                       t.d_out_ids, t.d_out_ids + t.nout, t.d_qhat_inv, t.d_qhat_mod,
-                                                       c->d_primes, c->logn, in_pstride, out_pstride);
+    ConvJob& j = J.job[J.n++];
+    j.in = in;
+    j.out = out;
+    j.in_ids = t.d_in_ids;
+    j.out_ids = t.d_out_ids;
+    j.out_rows = t.d_out_ids + t.nout;
+    j.qinv = t.d_qhat_inv;
+    j.qmod = t.d_qhat_mod;
+    j.nin = t.nin;
+    j.nout = t.nout;
+    j.ngroups = (t.nout + CONV_OUT - 1) / CONV_OUT;
+    j.in_pstride = in_pstride;
+    j.out_pstride = out_pstride;
+}
+
+void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly) {
+    int groups = 0;
+    double bytes = 0;
+    for (int i = 0; i < J.n; ++i) {
+        groups += J.job[i].ngroups;
+        bytes += (double)npoly * (J.job[i].nin + J.job[i].nout) * c->n * 8.0;
+    }
+    if (groups == 0) return;
+    dim3 grid((c->n + 255) / 256, npoly, groups);
+    { KTimer kt_(c, "base_convert", bytes);
+    k_base_convert<<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
     }
     LAUNCH_CHECK();
 }
+
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
               const u64* ka, u64* ob, u64* oa, u64 g) {
     { KTimer kt_(c, "ks_inner", (3.0 * ndig + 2.0) * next * c->n * 8.0);

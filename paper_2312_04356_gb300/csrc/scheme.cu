@@ -447,11 +447,15 @@ DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out) {
     kern::ntt_inverse(c, coef.ptr, nl, c->d_iota, nl);
     DevBuf D((size_t)ndig * next * n, c->stream);
     const int* ext = c->d_ext_ids[level];
+    kern::ConvJobs jobs;
+    jobs.n = 0;
+    for (int d = 0; d < ndig; ++d)
+        kern::add_conv_job(jobs, c->modup_tab(level, d), coef.ptr + (size_t)dig[d].front() * n,
+                           D.ptr + (size_t)d * next * n, 0, 0);
+    kern::base_convert_jobs(c, jobs, 1);
     for (int d = 0; d < ndig; ++d) {
         u64* Dd = D.ptr + (size_t)d * next * n;
         const int lo = dig[d].front(), hi = dig[d].back() + 1;
-        const ConvTab& t = c->modup_tab(level, d);
-        kern::base_convert(c, t, coef.ptr + (size_t)lo * n, n, Dd, n, 1, 0, 0);
         CUDA_CHECK(cudaMemcpyAsync(Dd + (size_t)lo * n, x + (size_t)lo * n, (size_t)(hi - lo) * n * 8,
                                    cudaMemcpyDeviceToDevice, c->stream));
         if (c->logn != 16) {
