@@ -242,6 +242,15 @@ int ckks_ptset_conv_fused(ckks_ctx* ctx, const double* weights, int cin, int cou
 int ckks_conv2d_cins(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
                      ckks_ct* out);
 
+/* Depthwise conv2d (Sec. 3.3.4; Table 1: 1 PMult, 0 HRot, 1 level): the c kernels
+ * K[c][f][f] (cross-correlation, 'same' padding, kernel vectors of Fig. 1) packed in one
+ * real-CinS plaintext <k_1 | ... | k_C>, so that one PMult gives k_i * i_i in every slice
+ * (Eq. 6).  ckks_dwconv_cins = PMult + rescale; the output stays real-CinS.  Average
+ * pooling with stride 1 is the case of equal kernels 1 / f^2. */
+int ckks_encode_dwconv_kernel(ckks_ctx* ctx, const double* K, int c, int f, int w, int level, double scale,
+                              ckks_pt* out);
+int ckks_dwconv_cins(ckks_ctx* ctx, const ckks_ct* in, const ckks_pt* kernel, ckks_ct* out);
+
 /* ---- bootstrapping and the Alg. 1 block ----------------------------------- */
 typedef struct ckks_boot_params {
     int w, w0, cout;      /* padded width, image width, output channels (masks) */

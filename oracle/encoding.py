@@ -382,3 +382,30 @@ def conv_output_from_coeffs(coeff, C, two_l, cout, w, w0):
         v = coeff[np.arange(two_l) * C + rev[i]]
         out[i] = v.reshape(w, w)[:w0, :w0]
     return out
+
+
+# ---------------------------------------------------- depthwise conv2d -----
+def dwconv_same(x, K):
+    """FP64 depthwise cross-correlation, stride 1, zero 'same' padding: x (C, h, h), K (C, f, f)"""
+    C, h, _ = x.shape
+    f = K.shape[1]
+    c = f // 2
+    xp = np.zeros((C, h + 2 * c, h + 2 * c))
+    xp[:, c: c + h, c: c + h] = x
+    out = np.zeros((C, h, h))
+    for i in range(C):
+        for a in range(f):
+            for b in range(f):
+                out[i] += K[i, a, b] * xp[i, a: a + h, b: b + h]
+    return out
+
+
+def dwconv_kernel_slots(K, w, n_ring):
+    """Sec. 3.3.4: the C kernels packed in one real-CinS plaintext <k_1 | ... | k_C>_CinS, so that
+    one PMult gives k_i * i_i in every slice (Eq. 6)"""
+    two_l = w * w
+    C = n_ring // two_l
+    slices = np.zeros((C, two_l))
+    for i in range(K.shape[0]):
+        slices[i] = kernel_vector(K[i], w)
+    return real_cins_slots(slices)

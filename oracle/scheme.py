@@ -434,6 +434,10 @@ class Oracle:
     def conv2d_cins(self, ct, plan):
         return self.rescale(self.bsgs(ct, plan))
 
+    def dwconv_cins(self, ct, pt_kernel):
+        """depthwise conv2d (Sec. 3.3.4): one PMult by the packed kernels, then rescale"""
+        return self.rescale(self.mul_plain(ct, pt_kernel))
+
     # ------------------------------------------------------- bootstrapping ----
     # ------------------------------------------------ Chebyshev evaluation ----
     def prod_level(self, m):

@@ -105,6 +105,8 @@ _SIGS = {
     "ckks_bsgs": [VP, VP, VP, VP, VP],
     "ckks_ptset_conv_fused": [VP, VP, I, I, I, I, I, D, I, PVP],
     "ckks_conv2d_cins": [VP, VP, VP, VP, VP],
+    "ckks_encode_dwconv_kernel": [VP, VP, I, I, I, I, D, VP],
+    "ckks_dwconv_cins": [VP, VP, VP, VP],
     "ckks_boot_create": [VP, ctypes.POINTER(ckks_boot_params), PVP],
     "ckks_boot_destroy": [VP],
     "ckks_boot_info": [VP, VP],
@@ -553,6 +555,20 @@ def ckks_ptset_conv_fused(ctx, weights, cin, cout, f, w, level, pt_scale, bsgs_B
 def ckks_conv2d_cins(ctx, keys, ct, conv, out=None):
     out = out or ckks_ct_create(ctx)
     ctx.check(lib().ckks_conv2d_cins(ctx, keys, ct, conv, out))
+    return out
+
+
+def ckks_encode_dwconv_kernel(ctx, K, w, level, scale, out=None):
+    """K: (c, f, f) depthwise kernels -> one real-CinS plaintext"""
+    a = _f64(K)
+    out = out or ckks_pt_create(ctx)
+    ctx.check(lib().ckks_encode_dwconv_kernel(ctx, _ptr(a), a.shape[0], a.shape[1], w, level, scale, out))
+    return out
+
+
+def ckks_dwconv_cins(ctx, ct, kernel, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_dwconv_cins(ctx, ct, kernel, out))
     return out
 
 

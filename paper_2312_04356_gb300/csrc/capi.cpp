@@ -771,6 +771,27 @@ int ckks_ptset_conv_fused(ckks_ctx* ctx, const double* W, int cin, int cout, int
     });
 }
 
+int ckks_encode_dwconv_kernel(ckks_ctx* ctx, const double* K, int c, int f, int w, int level, double scale,
+                              ckks_pt* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(K);
+        REQ(out);
+        CK_CHECK(w >= 2 && (w & (w - 1)) == 0 && w * w <= ctx->n, CKKS_EINVAL, "w must be a power of two, w^2 <= N");
+        CK_CHECK(f >= 1 && f % 2 == 1 && f <= w, CKKS_EINVAL, "kernel size must be odd and <= w");
+        encode_complex(ctx, fp64::dwconv_kernel_slots(K, c, f, w, ctx->n), level, scale, out);
+    });
+}
+
+int ckks_dwconv_cins(ckks_ctx* ctx, const ckks_ct* in, const ckks_pt* kernel, ckks_ct* out) {
+    return guard(ctx, [&] {
+        CT_OK(in);
+        REQ(kernel);
+        REQ(out);
+        assign(out, ops::rescale(ops::mul_plain(*in, *kernel)));
+    });
+}
+
 int ckks_conv2d_cins(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv, ckks_ct* out) {
     return guard(ctx, [&] {
         REQ(keys);

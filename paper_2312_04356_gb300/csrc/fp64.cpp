@@ -232,6 +232,18 @@ static std::vector<double> kernel_vector(const double* K, int f, int w) {
     return v;
 }
 
+// Sec. 3.3.4: the C depthwise kernels packed as one real-CinS slot vector <k_1 | ... | k_C>
+std::vector<cplx> dwconv_kernel_slots(const double* K, int c, int f, int w, int n) {
+    const int two_l = w * w, C = n / two_l;
+    CK_CHECK(c >= 1 && c <= C, CKKS_EINVAL, "channels do not fit in one ciphertext");
+    std::vector<double> m((size_t)C * two_l, 0.0);
+    for (int i = 0; i < c; ++i) {
+        std::vector<double> v = kernel_vector(K + (size_t)i * f * f, f, w);
+        std::copy(v.begin(), v.end(), m.begin() + (size_t)i * two_l);
+    }
+    return real_cins_slots(m.data(), C, two_l);
+}
+
 std::vector<std::vector<cplx>> fused_conv_diagonals(const double* W, int cin, int cout, int f, int w, int n) {
     const int two_l = w * w, ell = two_l / 2, C = n / two_l, m = n / 2;
     CK_CHECK(C >= 1 && cin <= C && cout <= C, CKKS_EINVAL, "channels do not fit in one ciphertext");

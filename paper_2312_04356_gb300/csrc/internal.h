@@ -286,6 +286,7 @@ Diag s_product(const std::vector<int>& strides, int m, bool inverse);
 std::vector<std::vector<int>> split_groups(const std::vector<int>& stages, int levels);
 void ap_of_group(const std::vector<int>& strides, int m, int* a0, int* step, int* count);
 std::vector<std::vector<cplx>> fused_conv_diagonals(const double* W, int cin, int cout, int f, int w, int n);
+std::vector<cplx> dwconv_kernel_slots(const double* K, int c, int f, int w, int n);
 std::vector<cplx> real_cins_slots(const double* m, int C, int two_l);
 std::vector<double> cins_to_reals(const std::vector<cplx>& z, int C, int two_l);
 std::vector<double> cheb_interp_cos(double K, int r, int deg);

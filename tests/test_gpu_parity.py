@@ -152,6 +152,29 @@ def test_cfg1_conv_bitexact_and_fp64():
     assert np.abs(got - ref).max() < 2.0 ** -12
 
 
+def test_dwconv_bitexact_and_fp64():
+    """depthwise conv: one PMult (Sec. 3.3.4) bit-exact against the oracle; the library's own
+    kernel packing decodes to FP64 depthwise conv2d"""
+    K, o, ctx, keys = make_pair("cfg2_small", 44, conj=False)
+    P = o.P
+    w0, w, f = 5, 8, 3
+    C = P.n // (w * w)
+    x = WL.image(44, C, w0)
+    Kw = np.random.default_rng(44).normal(0, 0.3, (C, f, f))
+    lev = 3
+    pt = o.encode_pt(E.cins_input_slots(x, w, P.n), lev, P.delta[lev])
+    pk = o.encode_pt(E.dwconv_kernel_slots(Kw, w, P.n), lev, P.delta[lev])
+    ct = o.encrypt(pt, 1)
+    want = o.dwconv_cins(ct, pk)
+    got = K.ckks_dwconv_cins(ctx, import_ct(K, ctx, ct), import_pt(K, ctx, pk))
+    assert_ct_equal(K, ctx, got, want, "dwconv")
+    gk = K.ckks_encode_dwconv_kernel(ctx, Kw, w, lev, P.delta[lev])
+    gx = K.ckks_encode_image(ctx, x, w, lev, P.delta[lev])
+    own = K.ckks_dwconv_cins(ctx, K.ckks_encrypt(ctx, keys, gx, 2), gk)
+    dec = K.ckks_decode_image(ctx, K.ckks_decrypt(ctx, keys, own), C, w0, w)
+    assert np.abs(dec - E.dwconv_same(x, Kw)).max() < 2.0 ** -12
+
+
 def test_own_encoder_close_to_oracle():
     """the library's FP64 encoder rounds to the same integers up to +-1"""
     K, o, ctx, keys = make_pair("cfg1", 3)

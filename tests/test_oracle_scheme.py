@@ -229,3 +229,23 @@ def test_relu_across_segment_boundary():
     out = R.relu_eval(o, o.encrypt(o.encode_pt(v, P.L, P.delta[P.L]), 1), stages)
     assert out.level == P.L - 18          # 17 levels + 1 for the boundary
     assert np.abs(slots(o, out).real - R.relu_poly_fp64(v, stages)).max() < 2.0 ** -12
+
+
+def test_dwconv_one_pmult():
+    """depthwise conv (Sec. 3.3.4, Table 1 row Dwconv2d: 1 PMult, 0 HRot, 1 level) decodes to
+    FP64 depthwise conv2d at the real pixels"""
+    P = PP.Params(10, 3, 1, 60, 42, 60)
+    o = Oracle(P, 3)
+    w0, w, f = 5, 8, 3
+    C = P.n // (w * w)
+    x = rng.random((C, w0, w0))
+    K = rng.normal(0, 0.3, (C, f, f))
+    ct = o.encrypt(o.encode_pt(E.cins_input_slots(x, w, P.n), 2, P.delta[2]), 1)
+    pk = o.encode_pt(E.dwconv_kernel_slots(K, w, P.n), 2, P.delta[2])
+    o.ops = {k: 0 for k in o.ops}
+    out = o.dwconv_cins(ct, pk)
+    assert o.ops["pmult"] == 1 and o.ops["hrot"] == 0 and out.level == 1
+    z = slots(o, out)
+    ell = w * w // 2
+    pix = np.stack([E.encode(z[i * ell:(i + 1) * ell], w * w).reshape(w, w)[:w0, :w0] for i in range(C)])
+    assert np.abs(pix - E.dwconv_same(x, K)).max() < 1e-6
