@@ -23,6 +23,10 @@ defers them to the CKKS bootstrapping papers it cites in Sec. 2.4):
 * HActivation is not part of this block (it is evaluated by cheb_eval/eval_poly
   on its own).  Recombine Re + i Im, then HMatmul(S_{l<-1}) (StoC1) in
   `stoc_levels` BSGS levels at canonical scales (Alg. 1 lines 5-6).
+* stride = 2 (the next conv downsamples, Alg. 2): between the recombination and the
+  StoC1 the tail applies the decomposition of Alg. 2 lines 1-8 (one HMatmul by the
+  permutation sum_j (>> j l/4) calG_l (<< r_j), at canonical scale), and the StoC1 becomes
+  S_{l/4<-1} (line 9): the output holds 4C polyphase slices of (w/2)^2 reals.
 """
 import math
 
@@ -34,7 +38,7 @@ from .scheme import Oracle, round_half_away
 
 class BootConfig:
     def __init__(self, orc: Oracle, w, w0, cout, K=28, r=3, deg=59, ctos_levels=3,
-                 stoc_levels=3, delta0=2.0 ** 49, ctos_B=None, stoc_B=None, coeffs=None):
+                 stoc_levels=3, delta0=2.0 ** 49, ctos_B=None, stoc_B=None, coeffs=None, stride=1):
         P = orc.P
         n, m = P.n, P.n // 2
         self.w, self.w0, self.cout = w, w0, cout
@@ -81,14 +85,25 @@ class BootConfig:
         self.mask_re, self.mask_im = self.mask_vectors(q0 / (2.0 * np.pi * self.delta0))
         self.pt_mask_re = orc.encode_pt(self.mask_re, le, self.s_mask)
         self.pt_mask_im = orc.encode_pt(self.mask_im, le, self.s_mask)
+        # --- stride 2: the Alg. 2 decomposition, then StoC1 over slices of l/4
+        assert stride in (1, 2)
+        self.stride = stride
+        self.decomp = None
+        top, ell_out = self.l_em - 1, self.ell
+        if stride == 2:
+            assert w >= 4 and w0 % 2 == 0
+            a0, step, count = E.decompose_ap(w, n)
+            self.decomp = orc.make_plan(E.decompose_diag(w, n), a0, step, count, top, P.delta[top])
+            top, ell_out = top - 1, self.ell // 4
         # --- StoC1 plans
         self.stoc = []
-        for i, (D, strides) in enumerate(E.stoc1_groups(n, self.ell, stoc_levels)):
+        for i, (D, strides) in enumerate(E.stoc1_groups(n, ell_out, stoc_levels)):
             a0, step, count = E.ap_of_group(strides, m)
-            lev = self.l_em - 1 - i
+            lev = top - i
             B = stoc_B[i] if stoc_B else None
             self.stoc.append(orc.make_plan(D, a0, step, count, lev, P.delta[lev], B))
-        self.l_out = self.l_em - 1 - len(self.stoc)
+        self.l_out = top - len(self.stoc)
+        assert self.l_out >= 1, "not enough levels for the block"
 
     def mask_vectors(self, value):
         """slot i*l + u carries pixel rev_l(u) (Re) or rev_l(u) + l (Im) of output channel i;
@@ -130,6 +145,8 @@ def stoc1(orc: Oracle, re, im, cfg: BootConfig):
     a = orc.rescale(orc.mul_plain(re, cfg.pt_mask_re))
     b = orc.rescale(orc.mul_plain(im, cfg.pt_mask_im))
     y = orc.add(a, orc.imult(b))
+    if cfg.decomp is not None:
+        y = orc.rescale(orc.bsgs(y, cfg.decomp))
     for plan in cfg.stoc:
         y = orc.rescale(orc.bsgs(y, plan))
     return y
@@ -143,9 +160,25 @@ def block(orc: Oracle, ct_in, conv_plan, cfg: BootConfig):
     return stoc1(orc, re, im, cfg)
 
 
+def block_multi(orc: Oracle, cts, conv_plans, cfg: BootConfig):
+    """conv2d over several input ciphertexts, then bootstrap + StoC1 tail.  With the
+    decomposed kernels of a stride-2 conv this is Alg. 2 lines 10-17 (BSGS per input
+    ciphertext, HAdd, one rescale); with plain kernels it is the C_in > C generalisation
+    (Sec. 3.3.3: the block matrix-vector product, one output ciphertext)."""
+    x = None
+    for ct, plan in zip(cts, conv_plans):
+        y = orc.bsgs(ct, plan)
+        x = y if x is None else orc.add(x, y)
+    x = orc.rescale(x)
+    assert abs(x.scale - cfg.delta0) <= 1e-9 * cfg.delta0
+    re, im = bootstrap(orc, x, cfg)
+    return stoc1(orc, re, im, cfg)
+
+
 def block_rotations(orc: Oracle, conv_plan, cfg: BootConfig):
     m = orc.P.n // 2
-    rots = set(conv_plan.rotations(m))
-    for p in cfg.ctos + cfg.stoc:
+    rots = set(conv_plan.rotations(m)) if conv_plan is not None else set()
+    extra = [cfg.decomp] if cfg.decomp is not None else []
+    for p in cfg.ctos + cfg.stoc + extra:
         rots |= set(p.rotations(m))
     return sorted(rots)

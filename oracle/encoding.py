@@ -409,3 +409,115 @@ def dwconv_kernel_slots(K, w, n_ring):
     for i in range(K.shape[0]):
         slices[i] = kernel_vector(K[i], w)
     return real_cins_slots(slices)
+
+
+# ------------------------------------------- downsampling conv2d (Alg. 2) -----
+def G_matrix(w):
+    """G_l of Appendix B, l = w^2/2: a 2w x 2w grid of (w/4 x w/4) blocks whose block (i, 2i) is
+    the identity for i < w/2 and zero elsewhere.  (The appendix bounds i by <= w/2; a block at
+    i = w/2 would write the slots that the j = 1 term of Alg. 2 fills, so the bound is strict.)"""
+    ell = w * w // 2
+    b = w // 4
+    G = np.zeros((ell, ell))
+    for i in range(w // 2):
+        G[i * b:(i + 1) * b, 2 * i * b:(2 * i + 1) * b] = np.eye(b)
+    return G
+
+
+def blockdiag_to_diag(Gb, m):
+    """diag(Gb, Gb, ...) on C^m as a diagonal dict"""
+    ell = Gb.shape[0]
+    D = {}
+    rows, cols = np.nonzero(Gb)
+    for r, c in zip(rows, cols):
+        o = int(c - r) % m
+        if o not in D:
+            D[o] = np.zeros(m, dtype=np.complex128)
+        D[o][r::ell] += Gb[r, c]
+    return D
+
+
+def rotation_diag(r, m):
+    """ct << r, i.e. rot(z, r)_j = z_{j+r}, as a diagonal dict (ct >> r is r -> -r)"""
+    return {r % m: np.ones(m, dtype=np.complex128)}
+
+
+def decompose_diag(w, n_ring):
+    """Alg. 2 lines 1-8 as one linear map on the slots:
+    D = sum_{j<4} (>> j l/4) calG_l (<< r_j),  r = (0, l/2, w/4, l/2 + w/4)"""
+    m = n_ring // 2
+    ell = w * w // 2
+    G = blockdiag_to_diag(G_matrix(w), m)
+    r = [0, ell // 2, w // 4, ell // 2 + w // 4]
+    D = {}
+    for j in range(4):
+        t = diag_mul(rotation_diag(-j * (ell // 4), m), diag_mul(G, rotation_diag(r[j], m), m), m)
+        for o, v in t.items():
+            D[o] = D[o] + v if o in D else v
+    return D
+
+
+def decompose_ap(w, n_ring):
+    """the offsets of decompose_diag: b w/4 for 1 - w <= b <= w - 1 -> (a0, step, count)"""
+    m = n_ring // 2
+    return ((1 - w) * (w // 4)) % m, w // 4, 2 * w - 1
+
+
+def decompose_source(w, n_ring):
+    """The same permutation from the layouts alone.  Slot i l + rev_l(k) holds pixels k and
+    k + l of channel i (k = r w + c, r < w/2).  The polyphase image (p, q) of channel i,
+    x_pq[u][v] = x[2u + p][2v + q] (w/2 x w/2), becomes slice 4i + q + 2p of length l/4, whose
+    slot rev_{l/4}(u w/2 + v) holds its pixels (u, v) and (u + w/4, v).
+    Returns src with new[x] = old[src[x]]."""
+    m = n_ring // 2
+    ell = w * w // 2
+    l4 = ell // 4
+    rev_l = bitrev_indices(ell)
+    rev_4 = bitrev_indices(l4)
+    src = np.full(m, -1, dtype=np.int64)
+    for i in range(m // ell):
+        for p in range(2):
+            for q in range(2):
+                for u in range(w // 4):
+                    for v in range(w // 2):
+                        k = (2 * u + p) * w + 2 * v + q
+                        src[(4 * i + q + 2 * p) * l4 + rev_4[u * (w // 2) + v]] = i * ell + rev_l[k]
+    return src
+
+
+def decompose_images(x):
+    """the polyphase images of x (C, h, h), h even: (4C, h/2, h/2), image 4i + q + 2p = x_i[p::2, q::2]"""
+    C, h, _ = x.shape
+    out = np.zeros((4 * C, h // 2, h // 2))
+    for i in range(C):
+        for p in range(2):
+            for q in range(2):
+                out[4 * i + q + 2 * p] = x[i, p::2, q::2]
+    return out
+
+
+def conv2d_stride2(x, W):
+    """FP64 cross-correlation, stride 2, zero padding f//2 (PyTorch semantics), h even:
+    out[o][y][x] = sum W[o,i,a,b] x[i][2y + a - c][2x + b - c]"""
+    return conv2d_same(x, W)[:, ::2, ::2]
+
+
+def decompose_kernels(W, C, t):
+    """Alg. 2's decomposed kernels for input ciphertext t (channels tC .. tC + C - 1): the stride-2
+    conv as a unit-stride conv over the polyphase images.  Tap (a, b) of W[o][tC + i] goes to
+    slice 4i + q + 2p at offset (dy, dx), a - c = 2 dy + p, b - c = 2 dx + q; the result is a
+    centred kernel of size 2R + 1, R = (c + 1) // 2.  Returns (cout, 4C, 2R + 1, 2R + 1)."""
+    cout, cin, f, _ = W.shape
+    c = f // 2
+    R = (c + 1) // 2
+    out = np.zeros((cout, 4 * C, 2 * R + 1, 2 * R + 1))
+    for i in range(C):
+        ch = t * C + i
+        if ch >= cin:
+            break
+        for a in range(f):
+            for b in range(f):
+                p, q = (a - c) % 2, (b - c) % 2
+                dy, dx = (a - c - p) // 2, (b - c - q) // 2
+                out[:, 4 * i + q + 2 * p, dy + R, dx + R] += W[:, ch, a, b]
+    return out

@@ -81,7 +81,7 @@ class Oracle:
         P = self.P = params
         self.seed = int(seed)
         n = P.n
-        self.ops = {"pmult": 0, "hrot": 0, "keyswitch": 0, "hmult": 0, "rescale": 0}
+        self.ops = {"pmult": 0, "hrot": 0, "keyswitch": 0, "hmult": 0, "rescale": 0, "modraise": 0}
         if P.h:
             s = C.sample_hw(n, P.h, self.seed, tag(K_SK), tag(K_SK_SIGN))
         else:
@@ -297,6 +297,7 @@ class Oracle:
 
     def mod_raise(self, ct):
         assert ct.level == 0
+        self.ops["modraise"] += 1
         q = self.P.moduli(self.P.L)
         return Ciphertext(C.mod_raise(ct.c0[0], q), C.mod_raise(ct.c1[0], q), self.P.L, ct.scale)
 
