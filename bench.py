@@ -42,6 +42,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
     ap.add_argument("--batch", type=int, default=8, help="ciphertexts run concurrently for the batched figure")
+    ap.add_argument("--workload", default="block", choices=["block", "ds"],
+                    help="block: the Alg. 1 block (default); ds: the downsampling layer of Alg. 2")
     ap.add_argument("--kernel", default=None, choices=["ntt"],
                     help="time one kernel family alone on a buffer larger than L2 (for profiling)")
     return ap.parse_args()
@@ -402,6 +404,105 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ds(args):
+    """Alg. 2 at N = 2^16: two ciphertexts of 16 channels 32 x 32 (w = 64), each the EvalMod
+    output of a config-2 block, -> stride-2 tail (masks, Re + i Im, decomposition, S_{l/4<-1})
+    -> two decomposed 3x3 stride-2 convs -> one bootstrap -> tail: 64 channels 16 x 16 (w = 32)"""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = block_setup(K, torch, seed=1)
+    ctx, spec, w = s["ctx"], s["spec"], s["w"]
+    K.ckks_autotune(ctx, 3)
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    C, w0 = spec["cout"], spec["w0"]
+    bt_in = K.ckks_boot_create(ctx, w, w0, C, stride=2)
+    bt_out = K.ckks_boot_create(ctx, w // 2, w0 // 2, 4 * C)
+    W2 = WL.weights(2, 4 * C, 2 * C, 3, "normal")
+    # inputs: the EvalMod outputs of two config-2 blocks (images 1 and 2)
+    xs, res, ims = [], [], []
+    for t in range(2):
+        x = WL.image(1 + t, spec["cin"], w0)
+        xs.append(x)
+        ct = K.ckks_encrypt(ctx, s["keys"], K.ckks_encode_image(ctx, x, w, 1, delta[1]), 1 + t)
+        x0 = K.ckks_conv2d_cins(ctx, s["keys"], ct, s["conv"])
+        re, im = K.ckks_bootstrap(ctx, s["keys"], s["bt"], x0)
+        res.append(re)
+        ims.append(im)
+    lev_c = 1       # the tails' outputs are brought to level 1 at its canonical scale
+    convs = [K.ckks_ptset_conv_fused_s2(ctx, W2, 2 * C, 4 * C, 3, w, t, lev_c, (2.0 ** 49 * q[1]) / delta[1])
+             for t in range(2)]
+    rots = sorted((set(K.ckks_boot_rotations(bt_in)) | set(K.ckks_boot_rotations(bt_out))
+                   | set(K.ckks_ptset_rotations(convs[0])) | set(K.ckks_ptset_rotations(convs[1])))
+                  - set(s["rots"]))
+    K.ckks_keys_add_rotations(ctx, s["keys"], rots)
+    out = K.ckks_ct_create(ctx)
+    K.ckks_ctx_reset_counters(ctx)
+    K.ckks_downsample_layer(ctx, s["keys"], res, ims, bt_in, convs, bt_out, out)
+    K.ckks_sync(ctx)
+    counts = K.ckks_ctx_counters(ctx)
+    # FP64 reference: stride-2 conv of the two blocks' (masked) conv outputs
+    c1 = [np.zeros((C, w0, w0)) for _ in range(2)]
+    for t in range(2):
+        xp = np.zeros((spec["cin"], w0 + 2, w0 + 2))
+        xp[:, 1:1 + w0, 1:1 + w0] = xs[t]
+        for a in range(3):
+            for b in range(3):
+                c1[t] += np.einsum("oi,ihw->ohw", s["W"][:, :, a, b], xp[:, a:a + w0, b:b + w0])
+    x1 = np.concatenate(c1)
+    xp = np.zeros((2 * C, w0 + 2, w0 + 2))
+    xp[:, 1:1 + w0, 1:1 + w0] = x1
+    ref = np.zeros((4 * C, w0 // 2, w0 // 2))
+    for a in range(3):
+        for b in range(3):
+            ref += np.einsum("oi,ihw->ohw", W2[:, :, a, b], xp[:, a:a + w0:2, b:b + w0:2])
+    got = K.ckks_decode_image(ctx, K.ckks_decrypt(ctx, s["keys"], out), 4 * C, w0 // 2, w // 2)
+    err = float(np.abs(got - ref).max())
+    gout = K.ckks_ct_create(ctx)
+    graph = K.ckks_downsample_layer_graph_create(ctx, s["keys"], res, ims, bt_in, convs, bt_out, gout)
+    per_graph = K.ckks_graph_info(graph)
+    for _ in range(args.warmup):
+        K.ckks_graph_launch(graph)
+    K.ckks_sync(ctx)
+    same = bool((K.ckks_ct_export_rns(ctx, gout) == K.ckks_ct_export_rns(ctx, out)).all())
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        K.ckks_graph_launch(graph)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_ms = e0.elapsed_time(e1) / args.steps
+    # the same layer's share per stage: the two tails, then conv + bootstrap + tail
+    K.ckks_ctx_set_timing(ctx, 1)
+    K.ckks_ctx_reset_counters(ctx)
+    K.ckks_downsample_layer(ctx, s["keys"], res, ims, bt_in, convs, bt_out, out)
+    K.ckks_ctx_set_timing(ctx, 0)
+    kst = K.ckks_ctx_kernel_stats(ctx)
+    top = max(kst.items(), key=lambda kv: kv[1]["ms"])
+    pk = peaks()
+    achieved = top[1]["bytes"] / (top[1]["ms"] * 1e-3) / 1e9
+    line = {"metric": "ms per downsampling layer (Alg. 2) at N=2^16", "value": round(t_ms, 3), "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms, 3),
+            "higher_is_better": False, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "2 x (16 ch 32x32, w=64) EvalMod outputs -> stride-2 tail -> 2 decomposed "
+                                   "3x3 stride-2 convs (64 out) -> 1 bootstrap -> StoC1 at w=32",
+                       "decoded_max_abs_err": err, "graph_equals_eager": same,
+                       "execution": "CUDA graph replay of the layer", "l2": "working set > L2 (keys ~GBs)"},
+            "clocks": clocks, "launches_per_layer": per_graph, "op_counts": counts,
+            "roofline": {"kernel": top[0], "bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": round(achieved / pk.get("hbm_gbs"), 4),
+                         "traffic": None},
+            "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def run_kernel_ntt(args):
     """forward + inverse NTT of 256 limbs (256 MiB, > L2) cycling over the config-2 primes"""
     import torch
@@ -441,6 +542,8 @@ if __name__ == "__main__":
     a = parse_args()
     if a.kernel == "ntt":
         run_kernel_ntt(a)
+    elif a.workload == "ds" and a.impl == "ours":
+        run_ds(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

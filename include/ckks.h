@@ -242,6 +242,21 @@ int ckks_ptset_conv_fused(ckks_ctx* ctx, const double* weights, int cin, int cou
 int ckks_conv2d_cins(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
                      ckks_ct* out);
 
+/* Decomposed downsampling conv2d (Alg. 2 lines 10-11).  W[cout][cin][f][f] is a stride-2
+ * cross-correlation with zero padding f/2 (PyTorch semantics, even image width).  Input
+ * ciphertext t holds channels tC .. tC + C - 1 (C = N / w_in^2) as the stride-2 tail of
+ * ckks_boot_create leaves them: 4C polyphase slices of width w_in/2.  The set rewrites the
+ * taps of those channels as a unit-stride conv over the polyphase slices (tap (a, b) ->
+ * slice 4i + q + 2p, offset (dy, dx) with a - f/2 = 2 dy + p, b - f/2 = 2 dx + q) and fuses
+ * it with StoC2 at width w_in/2 like ckks_ptset_conv_fused (cout <= 4C outputs).  Summing
+ * the sets' BSGS over t = 0, 1, ... gives the stride-2 conv (ckks_block_multi). */
+int ckks_ptset_conv_fused_s2(ckks_ctx* ctx, const double* weights, int cin, int cout, int f, int w_in, int t,
+                             int level, double pt_scale, int bsgs_B, ckks_ptset** out);
+/* The Alg. 2 decomposition (lines 1-8) as one plaintext set: diagonals at offsets b w/4,
+ * |b| < w (0/1 masks), encoded at (level, scale); the slot permutation described at
+ * ckks_boot_create.  Apply with ckks_bsgs + ckks_rescale. */
+int ckks_ptset_decompose(ckks_ctx* ctx, int w, int level, double scale, int bsgs_B, ckks_ptset** out);
+
 /* Depthwise conv2d (Sec. 3.3.4; Table 1: 1 PMult, 0 HRot, 1 level): the c kernels
  * K[c][f][f] (cross-correlation, 'same' padding, kernel vectors of Fig. 1) packed in one
  * real-CinS plaintext <k_1 | ... | k_C>, so that one PMult gives k_i * i_i in every slice
@@ -259,12 +274,19 @@ typedef struct ckks_boot_params {
     int deg;              /* Chebyshev degree of the cosine */
     int ctos_levels, stoc_levels;
     double delta0;        /* scale of the level-0 ciphertext entering ModRaise */
+    int stride;           /* 0 or 1; 2 when the next conv downsamples (Alg. 2, see below) */
 } ckks_boot_params;
 /* Builds: ModRaise scale q0*K_eff and drop constant c_drop = llround((Delta_{ld-1} q_ld) /
  * (q0 K)) with ld = L - ctos_levels, K_eff = (Delta_{ld-1} q_ld) / (q0 c_drop); CtoS =
  * T_{N/2}^{-1} in ctos_levels BSGS levels (largest stride first, plaintext scale q_l,
  * last level times 1/2); Chebyshev coefficients of cos(2 pi (K_eff y - 1/4) / 2^r);
- * padding masks times q0 / (2 pi delta0); StoC1 = S_{l <- 1} in stoc_levels levels. */
+ * padding masks times q0 / (2 pi delta0); StoC1 = S_{l <- 1} in stoc_levels levels.
+ * stride = 2 (Alg. 2 lines 1-9): after Re + i Im the tail applies the decomposition (one
+ * HMatmul by the slot permutation sum_j (>> j l/4) calG_l (<< r_j), r = (0, l/2, w/4,
+ * l/2 + w/4), calG_l of Appendix B, plaintexts at canonical scale; see
+ * ckks_ptset_decompose) and StoC1 becomes S_{l/4 <- 1}: the output holds, in slice
+ * 4i + q + 2p, the polyphase image x_i[p::2][q::2] of channel i as real CinS of width w/2.
+ * Needs w >= 4 and an even w0; l_out is one level lower than with stride 1. */
 int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out);
 int ckks_boot_destroy(ckks_boot* bt);
 /* info[0..7] = K_eff, s_raise, c_drop, l_drop, l_em, l_out, s_em, s_mask */
@@ -274,6 +296,7 @@ int ckks_boot_rotations(const ckks_boot* bt, int32_t* steps, int cap, int* n_out
  * (used to feed identical plaintexts to two implementations) */
 int ckks_boot_set_ctos(ckks_ctx* ctx, ckks_boot* bt, int i, const ckks_ptset* ps);
 int ckks_boot_set_stoc(ckks_ctx* ctx, ckks_boot* bt, int i, const ckks_ptset* ps);
+int ckks_boot_set_decomp(ckks_ctx* ctx, ckks_boot* bt, const ckks_ptset* ps);
 int ckks_boot_set_coeffs(ckks_ctx* ctx, ckks_boot* bt, const double* coeffs, int deg);
 int ckks_boot_set_masks(ckks_ctx* ctx, ckks_boot* bt, const ckks_pt* re, const ckks_pt* im);
 /* ModRaise -> CtoS -> conjugate split (Re = ct + conj, Im = i (conj - ct)) -> scale drop
@@ -286,6 +309,14 @@ int ckks_stoc1(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* re, const ck
 /* one conv2d + bootstrap block: conv2d_cins -> bootstrap -> stoc1 */
 int ckks_block(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
                const ckks_boot* bt, ckks_ct* out);
+/* The same block over n_in input ciphertexts: sum_t BSGS(in[t], conv[t]) (HAdd, one
+ * rescale) -> bootstrap -> stoc1.  With the plaintext sets of ckks_ptset_conv_fused_s2 this
+ * is Alg. 2 lines 10-17 (the downsampling conv bootstraps one ciphertext where a stride-1
+ * conv followed by densify bootstraps s^2 = 4); with ckks_ptset_conv_fused sets over
+ * different input channels it is the C_in > C block matrix-vector product (Sec. 3.3.3).
+ * All inputs share level and scale, all sets share level and scale; 1 <= n_in <= 64. */
+int ckks_block_multi(ckks_ctx* ctx, const ckks_keys* keys, int n_in, const ckks_ct* const* in,
+                     const ckks_ptset* const* conv, const ckks_boot* bt, ckks_ct* out);
 
 /* ---- CUDA graphs ------------------------------------------------------------- */
 typedef struct ckks_graph ckks_graph;
@@ -304,6 +335,22 @@ int ckks_graph_launch(ckks_graph* graph, void* stream);
 /* number of kernel launches one replay performs */
 int ckks_graph_info(const ckks_graph* graph, int64_t* kernel_launches);
 int ckks_graph_destroy(ckks_graph* graph);
+
+/* ---- the downsampling layer (Alg. 2) ------------------------------------------ */
+/* Alg. 2 without HActivation, from the EvalMod outputs of the previous block: for each of
+ * the n_in input ciphertexts, ckks_stoc1 with the stride-2 configuration bt_in (masks,
+ * Re + i Im, decomposition, S_{l/4<-1}) and a level drop to the conv sets' level; then
+ * ckks_block_multi over the decomposed conv sets (ckks_ptset_conv_fused_s2, t = 0 .. n_in-1)
+ * with bt_out.  re[t], im[t] sit at bt_in's l_em with its s_em; 1 <= n_in <= 64. */
+int ckks_downsample_layer(ckks_ctx* ctx, const ckks_keys* keys, int n_in, const ckks_ct* const* re,
+                          const ckks_ct* const* im, const ckks_boot* bt_in, const ckks_ptset* const* conv,
+                          const ckks_boot* bt_out, ckks_ct* out);
+/* The same layer recorded as a CUDA graph, under the rules of ckks_block_graph_create
+ * (non-default stream; inputs and out keep their buffers while the graph lives). */
+int ckks_downsample_layer_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int n_in, const ckks_ct* const* re,
+                                       const ckks_ct* const* im, const ckks_boot* bt_in,
+                                       const ckks_ptset* const* conv, const ckks_boot* bt_out, ckks_ct* out,
+                                       ckks_graph** graph);
 
 /* ---- polynomial evaluation (HActivation) --------------------------------- */
 #define CKKS_BASIS_CHEB 0

@@ -39,7 +39,7 @@ class ckks_params(ctypes.Structure):
 class ckks_boot_params(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int), ("w0", ctypes.c_int), ("cout", ctypes.c_int), ("K", ctypes.c_int),
                 ("r", ctypes.c_int), ("deg", ctypes.c_int), ("ctos_levels", ctypes.c_int),
-                ("stoc_levels", ctypes.c_int), ("delta0", ctypes.c_double)]
+                ("stoc_levels", ctypes.c_int), ("delta0", ctypes.c_double), ("stride", ctypes.c_int)]
 
 
 VP = ctypes.c_void_p
@@ -106,6 +106,12 @@ _SIGS = {
     "ckks_ptset_conv_fused": [VP, VP, I, I, I, I, I, D, I, PVP],
     "ckks_conv2d_cins": [VP, VP, VP, VP, VP],
     "ckks_encode_dwconv_kernel": [VP, VP, I, I, I, I, D, VP],
+    "ckks_ptset_conv_fused_s2": [VP, VP, I, I, I, I, I, I, D, I, PVP],
+    "ckks_ptset_decompose": [VP, I, I, D, I, PVP],
+    "ckks_boot_set_decomp": [VP, VP, VP],
+    "ckks_block_multi": [VP, VP, I, PVP, PVP, VP, VP],
+    "ckks_downsample_layer": [VP, VP, I, PVP, PVP, VP, PVP, VP, VP],
+    "ckks_downsample_layer_graph_create": [VP, VP, I, PVP, PVP, VP, PVP, VP, VP, PVP],
     "ckks_dwconv_cins": [VP, VP, VP, VP],
     "ckks_boot_create": [VP, ctypes.POINTER(ckks_boot_params), PVP],
     "ckks_boot_destroy": [VP],
@@ -552,6 +558,21 @@ def ckks_ptset_conv_fused(ctx, weights, cin, cout, f, w, level, pt_scale, bsgs_B
     return PtSet(out.value, ctx)
 
 
+def ckks_ptset_conv_fused_s2(ctx, weights, cin, cout, f, w_in, t, level, pt_scale, bsgs_B=0) -> PtSet:
+    W = _f64(weights)
+    assert W.size == cout * cin * f * f
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_ptset_conv_fused_s2(ctx, _ptr(W), cin, cout, f, w_in, t, level, pt_scale, bsgs_B,
+                                             ctypes.byref(out)))
+    return PtSet(out.value, ctx)
+
+
+def ckks_ptset_decompose(ctx, w, level, scale, bsgs_B=0) -> PtSet:
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_ptset_decompose(ctx, w, level, scale, bsgs_B, ctypes.byref(out)))
+    return PtSet(out.value, ctx)
+
+
 def ckks_conv2d_cins(ctx, keys, ct, conv, out=None):
     out = out or ckks_ct_create(ctx)
     ctx.check(lib().ckks_conv2d_cins(ctx, keys, ct, conv, out))
@@ -573,9 +594,10 @@ def ckks_dwconv_cins(ctx, ct, kernel, out=None):
 
 
 # -------------------------------------------------------- bootstrapping -----
-def ckks_boot_create(ctx, w, w0, cout, K=28, r=3, deg=59, ctos_levels=3, stoc_levels=3, delta0=2.0 ** 49) -> Boot:
+def ckks_boot_create(ctx, w, w0, cout, K=28, r=3, deg=59, ctos_levels=3, stoc_levels=3, delta0=2.0 ** 49,
+                     stride=1) -> Boot:
     bp = ckks_boot_params(w=w, w0=w0, cout=cout, K=K, r=r, deg=deg, ctos_levels=ctos_levels,
-                          stoc_levels=stoc_levels, delta0=delta0)
+                          stoc_levels=stoc_levels, delta0=delta0, stride=stride)
     out = ctypes.c_void_p()
     ctx.check(lib().ckks_boot_create(ctx, ctypes.byref(bp), ctypes.byref(out)))
     return Boot(out.value, ctx)
@@ -604,6 +626,10 @@ def ckks_boot_set_stoc(ctx, bt, i, ps):
     ctx.check(lib().ckks_boot_set_stoc(ctx, bt, i, ps))
 
 
+def ckks_boot_set_decomp(ctx, bt, ps):
+    ctx.check(lib().ckks_boot_set_decomp(ctx, bt, ps))
+
+
 def ckks_boot_set_coeffs(ctx, bt, coeffs):
     c = _f64(coeffs)
     ctx.check(lib().ckks_boot_set_coeffs(ctx, bt, _ptr(c), len(c) - 1))
@@ -630,6 +656,39 @@ def ckks_block(ctx, keys, ct, conv, bt, out=None):
     out = out or ckks_ct_create(ctx)
     ctx.check(lib().ckks_block(ctx, keys, ct, conv, bt, out))
     return out
+
+
+def ckks_block_multi(ctx, keys, cts, convs, bt, out=None):
+    out = out or ckks_ct_create(ctx)
+    n = len(cts)
+    assert n == len(convs)
+    a = (ctypes.c_void_p * n)(*[c.ptr for c in cts])
+    b = (ctypes.c_void_p * n)(*[c.ptr for c in convs])
+    ctx.check(lib().ckks_block_multi(ctx, keys, n, a, b, bt, out))
+    return out
+
+
+def _ptrs(hs):
+    return (ctypes.c_void_p * len(hs))(*[h.ptr for h in hs])
+
+
+def ckks_downsample_layer(ctx, keys, res, ims, bt_in, convs, bt_out, out=None):
+    out = out or ckks_ct_create(ctx)
+    n = len(res)
+    assert n == len(ims) == len(convs)
+    ctx.check(lib().ckks_downsample_layer(ctx, keys, n, _ptrs(res), _ptrs(ims), bt_in, _ptrs(convs), bt_out, out))
+    return out
+
+
+def ckks_downsample_layer_graph_create(ctx, keys, res, ims, bt_in, convs, bt_out, out) -> "Graph":
+    n = len(res)
+    assert n == len(ims) == len(convs)
+    g = ctypes.c_void_p()
+    ctx.check(lib().ckks_downsample_layer_graph_create(ctx, keys, n, _ptrs(res), _ptrs(ims), bt_in, _ptrs(convs),
+                                                       bt_out, out, ctypes.byref(g)))
+    gr = Graph(g.value, ctx)
+    gr.refs = (keys, list(res), list(ims), bt_in, list(convs), bt_out, out)
+    return gr
 
 
 def ckks_block_graph_create(ctx, keys, ct, conv, bt, out) -> Graph:

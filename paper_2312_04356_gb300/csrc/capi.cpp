@@ -771,6 +771,45 @@ int ckks_ptset_conv_fused(ckks_ctx* ctx, const double* W, int cin, int cout, int
     });
 }
 
+int ckks_ptset_conv_fused_s2(ckks_ctx* ctx, const double* W, int cin, int cout, int f, int w_in, int t, int level,
+                             double pt_scale, int B, ckks_ptset** out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(W);
+        REQ(out);
+        CK_CHECK(w_in >= 4 && (w_in & (w_in - 1)) == 0 && w_in * w_in <= ctx->n, CKKS_EINVAL,
+                 "w_in must be a power of two, 4 <= w_in, w_in^2 <= N");
+        CK_CHECK(f >= 1 && f % 2 == 1, CKKS_EINVAL, "kernel size must be odd");
+        const int C = ctx->n / (w_in * w_in), w = w_in / 2;
+        CK_CHECK(t >= 0 && t * C < cin, CKKS_EINVAL, "input ciphertext index out of range");
+        CK_CHECK(cout >= 1 && cout <= 4 * C, CKKS_EINVAL, "more output channels than slices");
+        CK_CHECK(level >= 1 && level <= ctx->L, CKKS_EINVAL, "the fused conv needs level >= 1");
+        int fo = 0;
+        std::vector<double> Wd = fp64::decompose_kernels(W, cout, cin, f, C, t, &fo);
+        CK_CHECK(fo <= w, CKKS_EINVAL, "decomposed kernel wider than the output image");
+        const int two_l = w * w, ell = two_l / 2, Cn = ctx->n / two_l, m = ctx->n / 2;
+        std::vector<std::vector<cplx>> diags = fp64::fused_conv_diagonals(Wd.data(), 4 * C, cout, fo, w, ctx->n);
+        fp64::Diag D;
+        for (int d = 0; d < Cn; ++d) {
+            double mx = 0;
+            for (const cplx& v : diags[d]) mx = std::max(mx, std::abs(v));
+            if (mx > 0) D[(int)(((long long)d * ell) % m)] = diags[d];
+        }
+        *out = make_plan(ctx, D, 0, ell, Cn, level, pt_scale, B);
+    });
+}
+
+int ckks_ptset_decompose(ckks_ctx* ctx, int w, int level, double scale, int B, ckks_ptset** out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(out);
+        CK_CHECK(w >= 4 && (w & (w - 1)) == 0 && w * w <= ctx->n, CKKS_EINVAL, "w must be a power of two, 4 <= w");
+        CK_CHECK(level >= 1 && level <= ctx->L, CKKS_EINVAL, "bad level");
+        *out = make_plan(ctx, fp64::decompose_diag(w, ctx->n / 2), (1 - w) * (w / 4), w / 4, 2 * w - 1, level, scale,
+                         B);
+    });
+}
+
 int ckks_encode_dwconv_kernel(ckks_ctx* ctx, const double* K, int c, int f, int w, int level, double scale,
                               ckks_pt* out) {
     return guard(ctx, [&] {
@@ -870,19 +909,30 @@ int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out)
         bt->mask_im = std::make_unique<ckks_pt>();
         encode_complex(ctx, mre, le, bt->s_mask, bt->mask_re.get());
         encode_complex(ctx, mim, le, bt->s_mask, bt->mask_im.get());
-        // StoC1 = S_{l <- 1}: stages 1, 2, ..., l/2, smallest stride first
+        // stride 2 (Alg. 2): the decomposition at canonical scale, then StoC1 over slices of l/4
+        CK_CHECK(bp->stride == 0 || bp->stride == 1 || bp->stride == 2, CKKS_EINVAL, "stride must be 1 or 2");
+        int top = le - 1, ell_out = bt->ell;
+        if (bp->stride == 2) {
+            CK_CHECK(bp->w >= 4 && bp->w0 % 2 == 0, CKKS_EINVAL, "stride 2 needs w >= 4 and an even image width");
+            bt->decomp.reset(make_plan(ctx, fp64::decompose_diag(bp->w, m), (1 - bp->w) * (bp->w / 4), bp->w / 4,
+                                       2 * bp->w - 1, top, ctx->delta[top], 0));
+            --top;
+            ell_out /= 4;
+        }
+        // StoC1 = S_{l' <- 1}: stages 1, 2, ..., l'/2, smallest stride first
         std::vector<int> st;
-        for (int k = 1; k < bt->ell; k *= 2) st.push_back(k);
+        for (int k = 1; k < ell_out; k *= 2) st.push_back(k);
         std::vector<std::vector<int>> sg = fp64::split_groups(st, bp->stoc_levels);
         for (size_t i = 0; i < sg.size(); ++i) {
             std::vector<int> rev(sg[i].rbegin(), sg[i].rend());
             fp64::Diag D = fp64::s_product(rev, m, false);
             int a0, step, count;
             fp64::ap_of_group(sg[i], m, &a0, &step, &count);
-            const int lev = le - 1 - (int)i;
+            const int lev = top - (int)i;
             bt->stoc.emplace_back(make_plan(ctx, D, a0, step, count, lev, ctx->delta[lev], 0));
         }
-        bt->l_out = le - 1 - (int)bt->stoc.size();
+        bt->l_out = top - (int)bt->stoc.size();
+        CK_CHECK(bt->l_out >= 1, CKKS_ELEVEL, "not enough levels for the block");
         *out = bt.release();
     });
 }
@@ -910,6 +960,7 @@ int ckks_boot_rotations(const ckks_boot* bt, int32_t* steps, int cap, int* n_out
     std::set<int> s;
     for (const auto& p : bt->ctos) plan_rotations(*p, s);
     for (const auto& p : bt->stoc) plan_rotations(*p, s);
+    if (bt->decomp) plan_rotations(*bt->decomp, s);
     int i = 0;
     for (int r : s) {
         if (steps && i < cap) steps[i] = r;
@@ -958,6 +1009,14 @@ int ckks_boot_set_stoc(ckks_ctx* ctx, ckks_boot* bt, int i, const ckks_ptset* ps
         CK_CHECK(i >= 0 && i < (int)bt->stoc.size() && ps->level == bt->stoc[i]->level, CKKS_EINVAL,
                  "bad StoC index or level");
         bt->stoc[i] = clone_ptset(ctx, *ps);
+    });
+}
+int ckks_boot_set_decomp(ckks_ctx* ctx, ckks_boot* bt, const ckks_ptset* ps) {
+    return guard(ctx, [&] {
+        REQ(bt);
+        REQ(ps);
+        CK_CHECK(bt->decomp && ps->level == bt->decomp->level, CKKS_EINVAL, "no decomposition at that level");
+        bt->decomp = clone_ptset(ctx, *ps);
     });
 }
 int ckks_boot_set_coeffs(ckks_ctx* ctx, ckks_boot* bt, const double* c, int deg) {
@@ -1029,6 +1088,31 @@ int ckks_block(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ck
     });
 }
 
+int ckks_block_multi(ckks_ctx* ctx, const ckks_keys* keys, int n_in, const ckks_ct* const* in,
+                     const ckks_ptset* const* conv, const ckks_boot* bt, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        REQ(in);
+        REQ(conv);
+        REQ(bt);
+        REQ(out);
+        CK_CHECK(n_in >= 1 && n_in <= 64, CKKS_EINVAL, "n_in must be in [1, 64]");
+        std::vector<const ckks_ct*> ins;
+        std::vector<const ckks_ptset*> convs;
+        for (int t = 0; t < n_in; ++t) {
+            CT_OK(in[t]);
+            REQ(conv[t]);
+            CK_CHECK(in[t]->level == in[0]->level && in[t]->scale == in[0]->scale, CKKS_EINVAL,
+                     "input ciphertexts differ in level or scale");
+            CK_CHECK(conv[t]->level == conv[0]->level && conv[t]->scale == conv[0]->scale, CKKS_EINVAL,
+                     "conv plaintext sets differ in level or scale");
+            ins.push_back(in[t]);
+            convs.push_back(conv[t]);
+        }
+        assign(out, ops::block_multi(*keys, *bt, convs, ins));
+    });
+}
+
 }  // extern "C"
 
 struct ckks_graph {
@@ -1042,6 +1126,58 @@ struct ckks_graph {
     }
 };
 
+// Runs `run` once eagerly (sizing `out`, building lazily created tables), then records a
+// second run on the context's stream and a copy of its result into out's buffer.  The
+// temporaries of the recorded run are allocated and freed inside the graph.
+template <class F>
+static void capture_graph(ckks_ctx* ctx, ckks_ct* out, ckks_graph** g, F run) {
+    CK_CHECK(ctx->stream != nullptr, CKKS_EINVAL, "graphs need a context created on a non-default stream");
+    assign(out, run());
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    std::unique_ptr<ckks_graph> gr(new ckks_graph());
+    gr->ctx = ctx;
+    const long long l0 = ctx->launches;
+    CUDA_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+        ckks_ct r = run();
+        CK_CHECK(r.level == out->level, CKKS_EINVAL, "captured run changed level");
+        CUDA_CHECK(cudaMemcpyAsync(out->buf.ptr, r.buf.ptr, 2 * (size_t)(r.level + 1) * ctx->n * 8,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+    } catch (...) {
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(ctx->stream, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        throw;
+    }
+    CUDA_CHECK(cudaStreamEndCapture(ctx->stream, &gr->graph));
+    CUDA_CHECK(cudaGraphInstantiate(&gr->exec, gr->graph, 0));
+    gr->launches = ctx->launches - l0;
+    *g = gr.release();
+}
+
+// checks of the downsampling layer's arguments; fills the pointer lists
+static void ds_args(int n_in, const ckks_ct* const* re, const ckks_ct* const* im, const ckks_ptset* const* conv,
+                    const ckks_boot* bt_in, const ckks_boot* bt_out, std::vector<const ckks_ct*>& vre,
+                    std::vector<const ckks_ct*>& vim, std::vector<const ckks_ptset*>& vconv) {
+    REQ(re);
+    REQ(im);
+    REQ(conv);
+    REQ(bt_in);
+    REQ(bt_out);
+    CK_CHECK(n_in >= 1 && n_in <= 64, CKKS_EINVAL, "n_in must be in [1, 64]");
+    CK_CHECK(bt_in->bp.stride == 2, CKKS_EINVAL, "bt_in must be a stride-2 configuration");
+    for (int t = 0; t < n_in; ++t) {
+        CT_OK(re[t]);
+        CT_OK(im[t]);
+        REQ(conv[t]);
+        CK_CHECK(conv[t]->level == conv[0]->level && conv[t]->scale == conv[0]->scale, CKKS_EINVAL,
+                 "conv plaintext sets differ in level or scale");
+        vre.push_back(re[t]);
+        vim.push_back(im[t]);
+        vconv.push_back(conv[t]);
+    }
+}
+
 extern "C" {
 
 int ckks_block_graph_create(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
@@ -1054,30 +1190,38 @@ int ckks_block_graph_create(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct*
         REQ(bt);
         REQ(out);
         REQ(g);
-        CK_CHECK(ctx->stream != nullptr, CKKS_EINVAL, "graphs need a context created on a non-default stream");
         CK_CHECK(out != in, CKKS_EINVAL, "out must not alias in");
-        // one eager block: sizes `out` and leaves every lazily built table in place
-        assign(out, ops::block(*keys, *bt, *conv, *in));
-        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
-        std::unique_ptr<ckks_graph> gr(new ckks_graph());
-        gr->ctx = ctx;
-        const long long l0 = ctx->launches;
-        CUDA_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        try {
-            ckks_ct r = ops::block(*keys, *bt, *conv, *in);
-            CK_CHECK(r.level == out->level, CKKS_EINVAL, "captured block changed level");
-            CUDA_CHECK(cudaMemcpyAsync(out->buf.ptr, r.buf.ptr, 2 * (size_t)(r.level + 1) * ctx->n * 8,
-                                       cudaMemcpyDeviceToDevice, ctx->stream));
-        } catch (...) {
-            cudaGraph_t tmp = nullptr;
-            cudaStreamEndCapture(ctx->stream, &tmp);
-            if (tmp) cudaGraphDestroy(tmp);
-            throw;
-        }
-        CUDA_CHECK(cudaStreamEndCapture(ctx->stream, &gr->graph));
-        CUDA_CHECK(cudaGraphInstantiate(&gr->exec, gr->graph, 0));
-        gr->launches = ctx->launches - l0;
-        *g = gr.release();
+        capture_graph(ctx, out, g, [&] { return ops::block(*keys, *bt, *conv, *in); });
+    });
+}
+
+int ckks_downsample_layer(ckks_ctx* ctx, const ckks_keys* keys, int n_in, const ckks_ct* const* re,
+                          const ckks_ct* const* im, const ckks_boot* bt_in, const ckks_ptset* const* conv,
+                          const ckks_boot* bt_out, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        REQ(out);
+        std::vector<const ckks_ct*> vre, vim;
+        std::vector<const ckks_ptset*> vconv;
+        ds_args(n_in, re, im, conv, bt_in, bt_out, vre, vim, vconv);
+        assign(out, ops::downsample_layer(*keys, *bt_in, *bt_out, vre, vim, vconv));
+    });
+}
+
+int ckks_downsample_layer_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int n_in, const ckks_ct* const* re,
+                                       const ckks_ct* const* im, const ckks_boot* bt_in,
+                                       const ckks_ptset* const* conv, const ckks_boot* bt_out, ckks_ct* out,
+                                       ckks_graph** g) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(keys);
+        REQ(out);
+        REQ(g);
+        std::vector<const ckks_ct*> vre, vim;
+        std::vector<const ckks_ptset*> vconv;
+        ds_args(n_in, re, im, conv, bt_in, bt_out, vre, vim, vconv);
+        for (int t = 0; t < n_in; ++t) CK_CHECK(out != re[t] && out != im[t], CKKS_EINVAL, "out must not alias an input");
+        capture_graph(ctx, out, g, [&] { return ops::downsample_layer(*keys, *bt_in, *bt_out, vre, vim, vconv); });
     });
 }
 

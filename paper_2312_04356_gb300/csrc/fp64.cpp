@@ -244,6 +244,64 @@ std::vector<cplx> dwconv_kernel_slots(const double* K, int c, int f, int w, int 
     return real_cins_slots(m.data(), C, two_l);
 }
 
+// ------------------------------------------- downsampling conv2d (Alg. 2) ---
+static int bit_reverse(int x, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) {
+        r = (r << 1) | (x & 1);
+        x >>= 1;
+    }
+    return r;
+}
+
+// The decomposition of Alg. 2 lines 1-8 is a permutation of the slots.  Before it, slot
+// i l + rev_l(k) holds pixels k and k + l of channel i (k = r w + c with r < w/2).  The
+// polyphase image (p, q) of channel i, x[2u + p][2v + q] of size (w/2)^2, goes to slice
+// 4i + q + 2p of length l/4, whose slot rev_{l/4}(u w/2 + v) holds its pixels (u, v) and
+// (u + w/4, v).  The nonzero diagonals (0/1 masks) sit at offsets b w/4, |b| < w.
+Diag decompose_diag(int w, int m) {
+    const int ell = w * w / 2, l4 = ell / 4;
+    int lb = 0, l4b = 0;
+    while ((1 << lb) < ell) ++lb;
+    while ((1 << l4b) < l4) ++l4b;
+    Diag D;
+    for (int i = 0; i < m / ell; ++i)
+        for (int p = 0; p < 2; ++p)
+            for (int q = 0; q < 2; ++q)
+                for (int u = 0; u < w / 4; ++u)
+                    for (int v = 0; v < w / 2; ++v) {
+                        const int k = (2 * u + p) * w + 2 * v + q;
+                        const long long dst = (long long)(4 * i + q + 2 * p) * l4 + bit_reverse(u * (w / 2) + v, l4b);
+                        const long long src = (long long)i * ell + bit_reverse(k, lb);
+                        const int off = (int)(((src - dst) % m + m) % m);
+                        std::vector<cplx>& d = D[off];
+                        if (d.empty()) d.assign(m, cplx(0, 0));
+                        d[dst] = cplx(1, 0);
+                    }
+    return D;
+}
+
+// The stride-2 conv W[cout][cin][f][f] over input ciphertext t (channels tC .. tC + C - 1) as
+// a unit-stride conv over their polyphase images: tap (a, b) of W[o][tC + i] becomes tap
+// (dy + R, dx + R) of the kernel on slice 4i + q + 2p, with a - f/2 = 2 dy + p and
+// b - f/2 = 2 dx + q, R = (f/2 + 1) / 2.  Returns W'[cout][4C][2R + 1][2R + 1].
+std::vector<double> decompose_kernels(const double* W, int cout, int cin, int f, int C, int t, int* f_out) {
+    const int c = f / 2, R = (c + 1) / 2, fo = 2 * R + 1;
+    std::vector<double> out((size_t)cout * 4 * C * fo * fo, 0.0);
+    for (int i = 0; i < C && t * C + i < cin; ++i)
+        for (int a = 0; a < f; ++a)
+            for (int b = 0; b < f; ++b) {
+                const int p = ((a - c) % 2 + 2) % 2, q = ((b - c) % 2 + 2) % 2;
+                const int dy = (a - c - p) / 2, dx = (b - c - q) / 2;
+                const int slice = 4 * i + q + 2 * p;
+                for (int o = 0; o < cout; ++o)
+                    out[(((size_t)o * 4 * C + slice) * fo + dy + R) * fo + dx + R] +=
+                        W[(((size_t)o * cin + t * C + i) * f + a) * f + b];
+            }
+    *f_out = fo;
+    return out;
+}
+
 std::vector<std::vector<cplx>> fused_conv_diagonals(const double* W, int cin, int cout, int f, int w, int n) {
     const int two_l = w * w, ell = two_l / 2, C = n / two_l, m = n / 2;
     CK_CHECK(C >= 1 && cin <= C && cout <= C, CKKS_EINVAL, "channels do not fit in one ciphertext");

@@ -163,6 +163,7 @@ struct ckks_boot {
     double K_eff = 0, s_raise = 0, s_em = 0, s_mask = 0;
     std::vector<double> coeffs;
     std::vector<std::unique_ptr<ckks_ptset>> ctos, stoc;
+    std::unique_ptr<ckks_ptset> decomp;   // stride 2: Alg. 2 decomposition before StoC1
     std::unique_ptr<ckks_pt> mask_re, mask_im;
     bool mask_im_zero = false;   // the Im half of every slice is padding: its mask is exactly 0
 };
@@ -287,6 +288,8 @@ std::vector<std::vector<int>> split_groups(const std::vector<int>& stages, int l
 void ap_of_group(const std::vector<int>& strides, int m, int* a0, int* step, int* count);
 std::vector<std::vector<cplx>> fused_conv_diagonals(const double* W, int cin, int cout, int f, int w, int n);
 std::vector<cplx> dwconv_kernel_slots(const double* K, int c, int f, int w, int n);
+Diag decompose_diag(int w, int m);
+std::vector<double> decompose_kernels(const double* W, int cout, int cin, int f, int C, int t, int* f_out);
 std::vector<cplx> real_cins_slots(const double* m, int C, int two_l);
 std::vector<double> cins_to_reals(const std::vector<cplx>& z, int C, int two_l);
 std::vector<double> cheb_interp_cos(double K, int r, int deg);

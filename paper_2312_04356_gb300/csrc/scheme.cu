@@ -825,12 +825,48 @@ void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, c
     im_out = eval_mod(keys, im, bt.coeffs, bt.bp.r);
 }
 
+// recombined slot ciphertext -> [Alg. 2 decomposition] -> HMatmul(S_{l'<-1})
+static ckks_ct tail(const ckks_keys& keys, const ckks_boot& bt, ckks_ct y) {
+    if (bt.decomp) y = rescale(bsgs(keys, y, *bt.decomp));
+    for (const auto& ps : bt.stoc) y = rescale(bsgs(keys, y, *ps));
+    return y;
+}
+
+static ckks_ct boot_tail(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& x0);
+
 // Alg. 1 block.  When the Im mask is exactly zero (the second half of every slice is
 // padding), PMult(ct_Im, mask_Im) is the zero ciphertext whatever ct_Im holds, so the Im
 // branch (its scale drop and EvalMod) is skipped; the output is bit-identical.
 ckks_ct block(const ckks_keys& keys, const ckks_boot& bt, const ckks_ptset& conv, const ckks_ct& in) {
-    ckks_ctx* c = in.ctx;
-    ckks_ct x0 = rescale(bsgs(keys, in, conv));
+    return boot_tail(keys, bt, rescale(bsgs(keys, in, conv)));
+}
+
+// conv over several input ciphertexts (BSGS each, HAdd, one rescale), then the block's
+// bootstrap and tail: Alg. 2 lines 10-17 with the decomposed stride-2 kernels, or the
+// C_in > C block matrix-vector product (Sec. 3.3.3).
+ckks_ct block_multi(const ckks_keys& keys, const ckks_boot& bt, const std::vector<const ckks_ptset*>& convs,
+                    const std::vector<const ckks_ct*>& ins) {
+    ckks_ct x = bsgs(keys, *ins[0], *convs[0]);
+    for (size_t t = 1; t < ins.size(); ++t) x = add(x, bsgs(keys, *ins[t], *convs[t]));
+    return boot_tail(keys, bt, rescale(x));
+}
+
+// Alg. 2 without HActivation: per input, the stride-2 tail of the previous block (masks,
+// Re + i Im, decomposition, S_{l/4<-1}) and a level drop to the conv's level; then the
+// decomposed convs, one bootstrap and the tail of bt_out.
+ckks_ct downsample_layer(const ckks_keys& keys, const ckks_boot& bt_in, const ckks_boot& bt_out,
+                         const std::vector<const ckks_ct*>& re, const std::vector<const ckks_ct*>& im,
+                         const std::vector<const ckks_ptset*>& convs) {
+    std::vector<ckks_ct> ys;
+    ys.reserve(re.size());
+    for (size_t t = 0; t < re.size(); ++t) ys.push_back(level_down(stoc1(keys, bt_in, *re[t], *im[t]), convs[t]->level));
+    std::vector<const ckks_ct*> ptrs;
+    for (const ckks_ct& y : ys) ptrs.push_back(&y);
+    return block_multi(keys, bt_out, convs, ptrs);
+}
+
+static ckks_ct boot_tail(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& x0) {
+    ckks_ctx* c = x0.ctx;
     if (!bt.mask_im_zero) {
         ckks_ct re, im;
         bootstrap(keys, bt, x0, re, im);
@@ -843,17 +879,13 @@ ckks_ct block(const ckks_keys& keys, const ckks_boot& bt, const ckks_ptset& conv
     re = rescale(mul_int(re, bt.c_drop));
     re.scale = c->delta[re.level];
     re = eval_mod(keys, re, bt.coeffs, bt.bp.r);
-    ckks_ct y = rescale(mul_plain(re, *bt.mask_re));
-    for (const auto& ps : bt.stoc) y = rescale(bsgs(keys, y, *ps));
-    return y;
+    return tail(keys, bt, rescale(mul_plain(re, *bt.mask_re)));
 }
 
 ckks_ct stoc1(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& re, const ckks_ct& im) {
     ckks_ct a = rescale(mul_plain(re, *bt.mask_re));
     ckks_ct b = rescale(mul_plain(im, *bt.mask_im));
-    ckks_ct y = add(a, imult(b));
-    for (const auto& ps : bt.stoc) y = rescale(bsgs(keys, y, *ps));
-    return y;
+    return tail(keys, bt, add(a, imult(b)));
 }
 
 }  // namespace ops

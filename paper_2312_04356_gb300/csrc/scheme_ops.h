@@ -33,6 +33,11 @@ ckks_ct eval_relu(const ckks_keys& keys, const ckks_ct& x, const std::vector<std
 void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, ckks_ct& re_out, ckks_ct& im_out);
 ckks_ct stoc1(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& re, const ckks_ct& im);
 ckks_ct block(const ckks_keys& keys, const ckks_boot& bt, const ckks_ptset& conv, const ckks_ct& in);
+ckks_ct block_multi(const ckks_keys& keys, const ckks_boot& bt, const std::vector<const ckks_ptset*>& convs,
+                    const std::vector<const ckks_ct*>& ins);
+ckks_ct downsample_layer(const ckks_keys& keys, const ckks_boot& bt_in, const ckks_boot& bt_out,
+                         const std::vector<const ckks_ct*>& re, const std::vector<const ckks_ct*>& im,
+                         const std::vector<const ckks_ptset*>& convs);
 void add_galois_key(ckks_ctx* c, ckks_keys& K, u64 g);
 ckks_keys* keygen(ckks_ctx* c, const int32_t* steps, int nsteps, int want_conj);
 ckks_ct encrypt(const ckks_keys& K, const ckks_pt& pt, u64 nonce);

@@ -353,3 +353,154 @@ def test_cfg2_block_full_size():
     got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gblk))
     err = np.abs(_pixels(d, got) - _pixels(d, zexp)).max()
     assert err < 2.0 ** -12, err
+
+
+# ------------------------------------------------- downsampling conv (Alg. 2) ----
+def _ds_tail_slots(P, cfg, x, seed):
+    """Re / Im slot vectors as the bootstrap hands them to the tail (slot i l + u: pixel
+    rev_l(u), resp. rev_l(u) + l, of channel i, divided by the mask value); pixels outside the
+    image carry noise that the masks remove"""
+    g = np.random.default_rng(seed)
+    val = float(P.q[0]) / (2.0 * np.pi * cfg.delta0)
+    ell, w = cfg.ell, cfg.w
+    rev = E.bitrev_indices(ell)
+    re, im = np.zeros(P.n // 2), np.zeros(P.n // 2)
+    for i in range(cfg.C):
+        img = g.uniform(-1, 1, (w, w))
+        if i < x.shape[0]:
+            img[:cfg.w0, :cfg.w0] = x[i]
+        f = img.reshape(-1)
+        re[i * ell:(i + 1) * ell] = f[rev] / val
+        im[i * ell:(i + 1) * ell] = f[rev + ell] / val
+    return re, im
+
+
+def _import_boot(K, ctx, bt, cfg):
+    for i, p in enumerate(cfg.ctos):
+        K.ckks_boot_set_ctos(ctx, bt, i, import_plan(K, ctx, p))
+    for i, p in enumerate(cfg.stoc):
+        K.ckks_boot_set_stoc(ctx, bt, i, import_plan(K, ctx, p))
+    if cfg.decomp is not None:
+        K.ckks_boot_set_decomp(ctx, bt, import_plan(K, ctx, cfg.decomp))
+    K.ckks_boot_set_coeffs(ctx, bt, cfg.coeffs)
+    K.ckks_boot_set_masks(ctx, bt, import_pt(K, ctx, cfg.pt_mask_re), import_pt(K, ctx, cfg.pt_mask_im))
+
+
+def _ds_case(seed):
+    """config-2 chain at N = 2^10: two ciphertexts of C = 16 channels (4 x 4 in w = 8) ->
+    stride-2 conv -> 64 channels of 2 x 2 in w = 4"""
+    P = oracle_params("cfg2_small")
+    w0, w, f = 4, 8, 3
+    C = P.n // (w * w)
+    x = WL.image(seed, 2 * C, w0)
+    W = WL.weights(seed, 4 * C, 2 * C, f, "normal")
+    return P, w0, w, f, C, x, W
+
+
+def test_downsample_bitexact():
+    """Alg. 2 on both sides with the oracle's plaintexts: stride-2 tail (mask, Re + i Im,
+    decomposition, S_{l/4<-1}) per input ciphertext, then the two decomposed convs + one
+    bootstrap + tail: bit-exact ciphertexts, decoded output within 2^-12 of the FP64 stride-2
+    conv2d"""
+    from oracle.scheme import Oracle
+    seed = 61
+    P, w0, w, f, C, x, W = _ds_case(seed)
+    o0 = Oracle(P, seed)
+    cfg_in = BT.BootConfig(o0, w, w0, C, stride=2)
+    cfg_out = BT.BootConfig(o0, w // 2, w0 // 2, 4 * C)
+    m = P.n // 2
+    conv_rots = {(d * (w * w // 8)) % m for d in range(1, 4 * C)}
+    rots = sorted(set(BT.block_rotations(o0, None, cfg_in)) | set(BT.block_rotations(o0, None, cfg_out)) | conv_rots)
+    K, o, ctx, keys = make_pair("cfg2_small", seed, rotations=rots)
+    cfg_in = BT.BootConfig(o, w, w0, C, stride=2)
+    cfg_out = BT.BootConfig(o, w // 2, w0 // 2, 4 * C)
+    bt_in = K.ckks_boot_create(ctx, w, w0, C, stride=2)
+    bt_out = K.ckks_boot_create(ctx, w // 2, w0 // 2, 4 * C)
+    assert K.ckks_boot_info(bt_in)["l_out"] == cfg_in.l_out
+    assert sorted(K.ckks_boot_rotations(bt_in)) == sorted(BT.block_rotations(o, None, cfg_in))
+    _import_boot(K, ctx, bt_in, cfg_in)
+    _import_boot(K, ctx, bt_out, cfg_out)
+    ins, gins, gres, gims = [], [], [], []
+    for t in range(2):
+        re, im = _ds_tail_slots(P, cfg_in, x[t * C:(t + 1) * C], seed + t)
+        cre = o.encrypt(o.encode_pt(re, cfg_in.l_em, cfg_in.s_em), 2 * t + 1)
+        cim = o.encrypt(o.encode_pt(im, cfg_in.l_em, cfg_in.s_em), 2 * t + 2)
+        y = BT.stoc1(o, cre, cim, cfg_in)
+        gres.append(import_ct(K, ctx, cre))
+        gims.append(import_ct(K, ctx, cim))
+        gy = K.ckks_stoc1(ctx, keys, gres[-1], gims[-1], bt_in)
+        assert_ct_equal(K, ctx, gy, y, "stride-2 tail %d" % t)
+        ins.append(o.level_down(y, 1))
+        gins.append(K.ckks_level_down(ctx, gy, 1))
+        assert_ct_equal(K, ctx, gins[-1], ins[-1], "level_down %d" % t)
+    s_pt = (cfg_out.delta0 * float(P.q[1])) / ins[0].scale
+    plans, gplans = [], []
+    for t in range(2):
+        Wt = E.decompose_kernels(W, C, t)
+        plans.append(o.conv_plan(Wt, 4 * C, 4 * C, Wt.shape[2], w // 2, 1, s_pt))
+        gplans.append(import_plan(K, ctx, plans[-1]))
+    out = BT.block_multi(o, ins, plans, cfg_out)
+    gout = K.ckks_block_multi(ctx, keys, gins, gplans, bt_out)
+    assert_ct_equal(K, ctx, gout, out, "Alg. 2 conv + bootstrap")
+    assert_ct_equal(K, ctx, K.ckks_downsample_layer(ctx, keys, gres, gims, bt_in, gplans, bt_out), out,
+                    "Alg. 2 layer")
+    got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gout))
+    ref = E.conv2d_stride2(x, W)
+    w2 = w // 2
+    ell2 = w2 * w2 // 2
+    pix = np.stack([E.encode(got[i * ell2:(i + 1) * ell2], w2 * w2) for i in range(4 * C)])
+    want = np.stack([E.flatten_padded(v, w2) for v in ref])
+    assert np.abs(pix - want).max() < 2.0 ** -12
+
+
+def test_downsample_own_plans():
+    """the library's own decomposition, S_{l/4<-1}, masks, EvalMod fit and decomposed conv sets
+    (ckks_ptset_conv_fused_s2) with its own encoder: decoded within 2^-12 of the FP64 stride-2
+    conv; the layer recorded as a CUDA graph replays the eager layer's ciphertext"""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        _downsample_own_plans()
+
+
+def _downsample_own_plans():
+    from oracle.scheme import Oracle
+    from paper_2312_04356_gb300 import ckks as K
+    seed = 62
+    P, w0, w, f, C, x, W = _ds_case(seed)
+    ctx = gpu_ctx("cfg2_small", seed)
+    m = P.n // 2
+    bt_in = K.ckks_boot_create(ctx, w, w0, C, stride=2)
+    bt_out = K.ckks_boot_create(ctx, w // 2, w0 // 2, 4 * C)
+    conv_rots = {(d * (w * w // 8)) % m for d in range(1, 4 * C)}
+    keys = K.ckks_keygen(ctx, sorted(set(K.ckks_boot_rotations(bt_in)) | set(K.ckks_boot_rotations(bt_out))
+                                     | conv_rots), True)
+    info = K.ckks_boot_info(bt_in)
+    o0 = Oracle(P, seed)
+    cfg_in = BT.BootConfig(o0, w, w0, C, stride=2)      # layout only: s_em, l_em, mask value
+    assert info["l_em"] == cfg_in.l_em and info["s_em"] == cfg_in.s_em
+    gins, gres, gims = [], [], []
+    for t in range(2):
+        re, im = _ds_tail_slots(P, cfg_in, x[t * C:(t + 1) * C], seed + t)
+        gres.append(K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, re, cfg_in.l_em, cfg_in.s_em), 2 * t + 1))
+        gims.append(K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, im, cfg_in.l_em, cfg_in.s_em), 2 * t + 2))
+        gins.append(K.ckks_level_down(ctx, K.ckks_stoc1(ctx, keys, gres[-1], gims[-1], bt_in), 1))
+    lev, sc = K.ckks_ct_info(gins[0])
+    s_pt = (2.0 ** 49 * float(P.q[1])) / sc
+    gplans = [K.ckks_ptset_conv_fused_s2(ctx, W, 2 * C, 4 * C, f, w, t, 1, s_pt) for t in range(2)]
+    gout = K.ckks_block_multi(ctx, keys, gins, gplans, bt_out)
+    want = K.ckks_ct_export_rns(ctx, gout)
+    assert (K.ckks_ct_export_rns(ctx, K.ckks_downsample_layer(ctx, keys, gres, gims, bt_in, gplans, bt_out))
+            == want).all()
+    gout2 = K.ckks_ct_create(ctx)
+    g = K.ckks_downsample_layer_graph_create(ctx, keys, gres, gims, bt_in, gplans, bt_out, gout2)
+    for _ in range(2):
+        K.ckks_graph_launch(g)
+        K.ckks_sync(ctx)
+        assert (K.ckks_ct_export_rns(ctx, gout2) == want).all()
+    got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gout))
+    ref = E.conv2d_stride2(x, W)
+    w2 = w // 2
+    ell2 = w2 * w2 // 2
+    pix = np.stack([E.encode(got[i * ell2:(i + 1) * ell2], w2 * w2) for i in range(4 * C)])
+    want = np.stack([E.flatten_padded(v, w2) for v in ref])
+    assert np.abs(pix - want).max() < 2.0 ** -12
