@@ -44,6 +44,7 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=8, help="ciphertexts run concurrently for the batched figure")
     ap.add_argument("--workload", default="block", choices=["block", "ds"],
                     help="block: the Alg. 1 block (default); ds: the downsampling layer of Alg. 2")
+    ap.add_argument("--variant", type=int, default=-1, help="--kernel ntt: time one launch variant only")
     ap.add_argument("--kernel", default=None, choices=["ntt"],
                     help="time one kernel family alone on a buffer larger than L2 (for profiling)")
     return ap.parse_args()
@@ -197,14 +198,15 @@ def oracle_sample(seconds_budget, counts=None):
     return est * 1e3, cores, sample
 
 
+# Operation counts of one config-2 block as the oracle runs it (EvalMod on both the Re and
+# the Im part): 114 key switches (75 rotations, 38 relinearisations, 1 conjugation),
+# 253 PMults, 139 rescales.  The library's counters report the same numbers for the same
+# steps (the GPU arm passes its live counts instead).
+BLOCK_OP_COUNTS = {"keyswitch": 114, "pmult": 253, "hrot": 75, "hmult": 38, "rescale": 139}
+
+
 def block_op_counts():
-    """operation counts of one config-2 block (from the library's counters when it has run,
-    else the algorithm's fixed structure as recorded in the design doc)"""
-    path = os.path.join(ROOT, "profiles", "block_op_counts.json")
-    try:
-        return json.load(open(path))
-    except (OSError, ValueError):
-        return {"keyswitch": 180, "rescale": 300, "pmult": 120}
+    return dict(BLOCK_OP_COUNTS)
 
 
 def run_reference(args):
@@ -519,7 +521,7 @@ def run_kernel_ntt(args):
     dev = torch.from_numpy(x.view(np.int64)).cuda()
     res = {}
     ok = True
-    for variant in (0, 1, 2, 3):
+    for variant in ((0, 1, 2, 3) if args.variant < 0 else (args.variant,)):
         K.ckks_ctx_set_ntt_variant(ctx, variant)
         for _ in range(args.warmup):
             K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)
