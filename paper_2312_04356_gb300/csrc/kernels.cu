@@ -190,8 +190,13 @@ __global__ void __launch_bounds__(NTT_THREADS)
 constexpr int F_STRIDE = 273;             // shared words per sub-problem: 256 + 16 pad, odd
 __device__ __forceinline__ int f_slot(int sp, int k) { return sp * F_STRIDE + k + (k >> 4); }
 
-__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 wp, u64 q, u64 q2) {
-    if (x >= q2) x -= q2;
+// Forward butterflies reduce the upper input only on odd local stages (threshold 4q): an
+// uncorrected stage maps inputs in [0, b q) to [0, (b + 2) q), a corrected one (valid for
+// b <= 8) to [0, 6q).  From canonical inputs the values stay below 8q, which fits in 64
+// bits for every prime below 2^61; each pass ends in [0, 6q).
+template <bool CORR>
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, u64 wp, u64 q, u64 q2, u64 q4) {
+    if (CORR && x >= q4) x -= q4;
     const u64 t = y * w - __umul64hi(y, wp) * q;   // [0, 2q)
     y = x - t + q2;
     x = x + t;
@@ -219,7 +224,10 @@ __device__ __forceinline__ void fwd_round(u64 (&x)[16], int t, int hi, int s0, c
             if (i & is) continue;
             const int idx = ROUND_B ? base + (t << s) + (i >> (4 - s)) : base + (i >> (4 - s));
             const ulonglong2 w = __ldg(P->tw + idx);
-            ct_bfly(x[i], x[i + is], w.x, w.y, q, q2);
+            if (u & 1)
+                ct_bfly<true>(x[i], x[i + is], w.x, w.y, q, q2, 2 * q2);
+            else
+                ct_bfly<false>(x[i], x[i + is], w.x, w.y, q, q2, 2 * q2);
         }
     }
 }
@@ -277,11 +285,12 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
         fwd_round<true>(x, t, hi, s0, P, q, q2);
         if (COL) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) a[gidx(16 * t + i)] = x[i];     // lazy, [0, 4q)
+            for (int i = 0; i < 16; ++i) a[gidx(16 * t + i)] = x[i];     // lazy, [0, 6q)
         } else {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 u64 v = x[i];
+                if (v >= 2 * q2) v -= 2 * q2;
                 if (v >= q2) v -= q2;
                 if (v >= q) v -= q;
                 x[i] = v;
