@@ -336,6 +336,60 @@ int ckks_graph_launch(ckks_graph* graph, void* stream);
 int ckks_graph_info(const ckks_graph* graph, int64_t* kernel_launches);
 int ckks_graph_destroy(ckks_graph* graph);
 
+/* ---- serving loop ----------------------------------------------------------------
+ * Continuous batching of inference requests (no counterpart in the paper, whose
+ * measurements are one image at a time; the benchmark spec asks for batched throughput).
+ * A model is a chain of Alg. 1 blocks: block b runs ckks_block with convs[b], boots[b]
+ * after a level drop of its input to convs[b]'s level.  For each of `slots` slots (a CUDA
+ * stream, device and pinned staging buffers) and each model, ckks_server_add_model runs
+ * one request eagerly (checking keys and levels and measuring the peak bytes of its
+ * temporaries in the device memory pool: the model's footprint), then records the whole
+ * request -- NTT of the input limbs, the blocks, iNTT of the output -- as a CUDA graph.
+ * After ckks_server_start a worker thread admits queued requests in submission order
+ * into free slots while the footprints of the requests in flight sum to at most
+ * hbm_budget bytes (0: no limit), and retires each as its slot's stream completes.
+ * The context (created on a non-default stream), keys, plaintext sets and bootstrapping
+ * configurations must outlive the server and must not be modified while it runs; the
+ * worker only launches the recorded graphs and copies, so other work may share the device.
+ * Requests carry coefficient-domain limbs [2][level+1][N] (the ckks_ct_export_rns /
+ * ckks_ct_import_rns format) at the model's input level and canonical scale; results
+ * are returned in the same format at the last block's l_out.  Errors: CKKS_EINVAL (bad
+ * model, level or scale, unknown request), CKKS_ENOKEY (a block needs a key `keys` lacks,
+ * found by the eager run), CKKS_ENOMEM (a request of the model exceeds hbm_budget). */
+typedef struct ckks_server ckks_server;
+typedef struct ckks_server_params {
+    int slots;               /* requests in flight at once, 1..64 */
+    long long hbm_budget;    /* bytes of temporaries the requests in flight may hold; 0 = no limit */
+} ckks_server_params;
+#define CKKS_REQ_QUEUED 0
+#define CKKS_REQ_RUNNING 1
+#define CKKS_REQ_DONE 2
+#define CKKS_REQ_FAILED 3
+#define CKKS_REQ_CANCELLED 4
+int ckks_server_create(ckks_ctx* ctx, const ckks_keys* keys, const ckks_server_params* sp, ckks_server** out);
+int ckks_server_add_model(ckks_server* s, int n_blocks, const ckks_ptset* const* convs, const ckks_boot* const* boots,
+                          int* model_id);
+/* info[0..5] = input level, input scale, output level, output scale, footprint bytes, kernels per request */
+int ckks_server_model_info(const ckks_server* s, int model_id, double* info6);
+int ckks_server_start(ckks_server* s);
+/* copies host_in; *request_id identifies the request from then on */
+int ckks_server_submit(ckks_server* s, int model_id, const uint64_t* host_in, int level, double scale,
+                       uint64_t* request_id);
+int ckks_server_poll(ckks_server* s, uint64_t request_id, int* state);
+/* waits until the request is DONE, FAILED or CANCELLED; CKKS_ETIMEOUT after timeout_s seconds */
+int ckks_server_wait(ckks_server* s, uint64_t request_id, double timeout_s, int* state);
+/* host_out NULL: only level and scale.  Otherwise copies the result and forgets the request. */
+int ckks_server_result(ckks_server* s, uint64_t request_id, uint64_t* host_out, int* level, double* scale);
+/* a queued request is dropped; a running one finishes on the device and its result is discarded */
+int ckks_server_cancel(ckks_server* s, uint64_t request_id);
+/* stats[0..7] = completed, failed, cancelled, p50 latency ms, p99 latency ms, mean latency ms,
+ * most requests in flight at once, kernel launches (submission to completion, host clock) */
+int ckks_server_stats(ckks_server* s, double* stats8);
+int ckks_server_reset_stats(ckks_server* s);
+const char* ckks_server_last_error(const ckks_server* s);
+/* stops admitting, waits for the requests in flight, abandons the queued ones */
+int ckks_server_destroy(ckks_server* s);
+
 /* ---- the downsampling layer (Alg. 2) ------------------------------------------ */
 /* Alg. 2 without HActivation, from the EvalMod outputs of the previous block: for each of
  * the n_in input ciphertexts, ckks_stoc1 with the stride-2 configuration bt_in (masks,

@@ -36,6 +36,10 @@ class ckks_params(ctypes.Structure):
                 ("sigma", ctypes.c_double)]
 
 
+class ckks_server_params(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_longlong)]
+
+
 class ckks_boot_params(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int), ("w0", ctypes.c_int), ("cout", ctypes.c_int), ("K", ctypes.c_int),
                 ("r", ctypes.c_int), ("deg", ctypes.c_int), ("ctos_levels", ctypes.c_int),
@@ -111,6 +115,19 @@ _SIGS = {
     "ckks_boot_set_decomp": [VP, VP, VP],
     "ckks_block_multi": [VP, VP, I, PVP, PVP, VP, VP],
     "ckks_downsample_layer": [VP, VP, I, PVP, PVP, VP, PVP, VP, VP],
+    "ckks_server_create": [VP, VP, ctypes.POINTER(ckks_server_params), PVP],
+    "ckks_server_add_model": [VP, I, PVP, PVP, ctypes.POINTER(I)],
+    "ckks_server_model_info": [VP, I, VP],
+    "ckks_server_start": [VP],
+    "ckks_server_submit": [VP, I, VP, I, D, ctypes.POINTER(U64)],
+    "ckks_server_poll": [VP, U64, ctypes.POINTER(I)],
+    "ckks_server_wait": [VP, U64, D, ctypes.POINTER(I)],
+    "ckks_server_result": [VP, U64, VP, ctypes.POINTER(I), ctypes.POINTER(D)],
+    "ckks_server_cancel": [VP, U64],
+    "ckks_server_stats": [VP, VP],
+    "ckks_server_reset_stats": [VP],
+    "ckks_server_last_error": [VP],
+    "ckks_server_destroy": [VP],
     "ckks_downsample_layer_graph_create": [VP, VP, I, PVP, PVP, VP, PVP, VP, VP, PVP],
     "ckks_dwconv_cins": [VP, VP, VP, VP],
     "ckks_boot_create": [VP, ctypes.POINTER(ckks_boot_params), PVP],
@@ -151,6 +168,7 @@ def lib():
         f.restype = ctypes.c_int
     L.ckks_last_error.argtypes = [VP]
     L.ckks_last_error.restype = ctypes.c_char_p
+    L.ckks_server_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
@@ -232,6 +250,15 @@ class Boot(_Handle):
 
 class Graph(_Handle):
     _destroy = "ckks_graph_destroy"
+
+
+class Server(_Handle):
+    """the serving loop (continuous batching); keeps the objects its models use alive"""
+    _destroy = "ckks_server_destroy"
+
+    def check(self, rc):
+        if rc != CKKS_OK:
+            raise CkksError(rc, lib().ckks_server_last_error(self.ptr).decode())
 
 
 # ------------------------------------------------------------- context ------
@@ -741,3 +768,80 @@ def ckks_ntt_forward(ctx, dev_ptr, n_limbs, prime_ids):
 def ckks_ntt_inverse(ctx, dev_ptr, n_limbs, prime_ids):
     ids = np.ascontiguousarray(prime_ids, dtype=np.int32)
     ctx.check(lib().ckks_ntt_inverse(ctx, ctypes.c_void_p(dev_ptr), n_limbs, _ptr(ids)))
+
+
+# ------------------------------------------------------------- serving loop -----
+CKKS_REQ_QUEUED, CKKS_REQ_RUNNING, CKKS_REQ_DONE, CKKS_REQ_FAILED, CKKS_REQ_CANCELLED = range(5)
+
+
+def ckks_server_create(ctx, keys, slots, hbm_budget=0) -> Server:
+    sp = ckks_server_params(slots=slots, hbm_budget=int(hbm_budget))
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_server_create(ctx, keys, ctypes.byref(sp), ctypes.byref(out)))
+    srv = Server(out.value, ctx)
+    srv.refs = [keys]
+    return srv
+
+
+def ckks_server_add_model(srv, convs, boots):
+    n = len(convs)
+    assert n == len(boots)
+    mid = ctypes.c_int()
+    srv.check(lib().ckks_server_add_model(srv, n, _ptrs(convs), _ptrs(boots), ctypes.byref(mid)))
+    srv.refs += list(convs) + list(boots)
+    return mid.value
+
+
+def ckks_server_model_info(srv, model_id):
+    a = np.zeros(6, dtype=np.float64)
+    srv.check(lib().ckks_server_model_info(srv, model_id, _ptr(a)))
+    keys = ["in_level", "in_scale", "out_level", "out_scale", "footprint", "kernels"]
+    return dict(zip(keys, [float(x) for x in a]))
+
+
+def ckks_server_start(srv):
+    srv.check(lib().ckks_server_start(srv))
+
+
+def ckks_server_submit(srv, model_id, limbs, level, scale):
+    a = np.ascontiguousarray(limbs, dtype=np.uint64)
+    rid = ctypes.c_uint64()
+    srv.check(lib().ckks_server_submit(srv, model_id, _ptr(a), level, scale, ctypes.byref(rid)))
+    return rid.value
+
+
+def ckks_server_poll(srv, rid):
+    st = ctypes.c_int()
+    srv.check(lib().ckks_server_poll(srv, rid, ctypes.byref(st)))
+    return st.value
+
+
+def ckks_server_wait(srv, rid, timeout_s=60.0):
+    st = ctypes.c_int()
+    rc = lib().ckks_server_wait(srv, rid, timeout_s, ctypes.byref(st))
+    if rc not in (CKKS_OK, CKKS_ETIMEOUT):
+        srv.check(rc)
+    return st.value
+
+
+def ckks_server_result(srv, rid, n):
+    lev, sc = ctypes.c_int(), ctypes.c_double()
+    srv.check(lib().ckks_server_result(srv, rid, None, ctypes.byref(lev), ctypes.byref(sc)))
+    out = np.zeros((2, lev.value + 1, n), dtype=np.uint64)
+    srv.check(lib().ckks_server_result(srv, rid, _ptr(out), ctypes.byref(lev), ctypes.byref(sc)))
+    return out, lev.value, sc.value
+
+
+def ckks_server_cancel(srv, rid):
+    srv.check(lib().ckks_server_cancel(srv, rid))
+
+
+def ckks_server_stats(srv):
+    a = np.zeros(8, dtype=np.float64)
+    srv.check(lib().ckks_server_stats(srv, _ptr(a)))
+    keys = ["completed", "failed", "cancelled", "p50_ms", "p99_ms", "mean_ms", "max_in_flight", "kernels"]
+    return dict(zip(keys, [float(x) for x in a]))
+
+
+def ckks_server_reset_stats(srv):
+    srv.check(lib().ckks_server_reset_stats(srv))
