@@ -42,8 +42,10 @@ def parse_args():
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
     ap.add_argument("--batch", type=int, default=8, help="ciphertexts run concurrently for the batched figure")
-    ap.add_argument("--workload", default="block", choices=["block", "ds"],
-                    help="block: the Alg. 1 block (default); ds: the downsampling layer of Alg. 2")
+    ap.add_argument("--workload", default="block", choices=["block", "ds", "serve"],
+                    help="block: the Alg. 1 block (default); ds: the downsampling layer of Alg. 2; "
+                         "serve: the serving loop under Poisson arrivals")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--variant", type=int, default=-1, help="--kernel ntt: time one launch variant only")
     ap.add_argument("--kernel", default=None, choices=["ntt"],
                     help="time one kernel family alone on a buffer larger than L2 (for profiling)")
@@ -505,6 +507,82 @@ def run_ds(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """The serving loop at N = 2^16 under Poisson arrivals: 70% one-block requests (a config-2
+    block) and 30% two-block chains, at three offered loads relative to the measured capacity;
+    8 slots, no HBM budget.  Reports completed requests/s, p50/p99/mean latency per load."""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = block_setup(K, torch, seed=1)
+    ctx = s["ctx"]
+    K.ckks_autotune(ctx, 3)
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    slots = max(1, args.batch)
+    srv = K.ckks_server_create(ctx, s["keys"], slots, 0)
+    A = K.ckks_server_add_model(srv, [s["conv"]], [s["bt"]])
+    B = K.ckks_server_add_model(srv, [s["conv"], s["conv"]], [s["bt"], s["bt"]])
+    infoA, infoB = K.ckks_server_model_info(srv, A), K.ckks_server_model_info(srv, B)
+    K.ckks_server_start(srv)
+    inputs = []
+    for i in range(4):
+        x = WL.image(200 + i, s["spec"]["cin"], s["spec"]["w0"])
+        ct = K.ckks_encrypt(ctx, s["keys"], K.ckks_encode_image(ctx, x, s["w"], 1, delta[1]), 200 + i)
+        inputs.append(K.ckks_ct_export_rns(ctx, ct))
+    K.ckks_sync(ctx)
+    g = np.random.default_rng(17)
+
+    def run(rate, seconds, closed=False):
+        K.ckks_server_reset_stats(srv)
+        ids = []
+        t0 = time.perf_counter()
+        t_next = t0
+        n_req = 0
+        while True:
+            now = time.perf_counter()
+            if now - t0 > seconds:
+                break
+            if closed or now >= t_next:
+                model = A if g.random() < 0.7 else B
+                ids.append(K.ckks_server_submit(srv, model, inputs[n_req % len(inputs)], 1, delta[1]))
+                n_req += 1
+                t_next += float(g.exponential(1.0 / rate)) if not closed else 0.0
+                if closed and len(ids) >= 4 * slots:
+                    K.ckks_server_wait(srv, ids[-3 * slots], 120)
+            else:
+                time.sleep(min(t_next - now, 0.001))
+        for r in ids:
+            K.ckks_server_wait(srv, r, 300)
+        t_end = time.perf_counter()
+        for r in ids:
+            K.ckks_server_result(srv, r, ctx.n)
+        st = K.ckks_server_stats(srv)
+        return {"offered_per_s": None if closed else rate, "requests": len(ids),
+                "completed_per_s": round(st["completed"] / (t_end - t0), 2), "p50_ms": round(st["p50_ms"], 2),
+                "p99_ms": round(st["p99_ms"], 2), "mean_ms": round(st["mean_ms"], 2),
+                "max_in_flight": int(st["max_in_flight"]), "failed": int(st["failed"])}
+
+    run(10.0, 1.0)                                   # warm-up
+    sampler = ClockSampler(0)
+    sampler.start()
+    cap = run(None, args.serve_seconds, closed=True)  # saturating closed loop: the capacity
+    loads = [run(f * cap["completed_per_s"], args.serve_seconds) for f in (0.5, 0.8, 0.95)]
+    clocks = sampler.stop()
+    line = {"metric": "serving: completed requests/s and latency at N=2^16 (Poisson mix)",
+            "value": cap["completed_per_s"], "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "70% one config-2 block, 30% chains of two blocks; requests carry host "
+                                   "coefficient limbs in and out (H2D, NTT, blocks, iNTT, D2H)",
+                       "slots": slots, "hbm_budget": 0, "footprint_bytes": [infoA["footprint"], infoB["footprint"]],
+                       "kernels_per_request": [infoA["kernels"], infoB["kernels"]]},
+            "capacity_closed_loop": cap, "poisson": loads, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def run_kernel_ntt(args):
     """forward + inverse NTT of 256 limbs (256 MiB, > L2) cycling over the config-2 primes"""
     import torch
@@ -546,6 +624,8 @@ if __name__ == "__main__":
         run_kernel_ntt(a)
     elif a.workload == "ds" and a.impl == "ours":
         run_ds(a)
+    elif a.workload == "serve" and a.impl == "ours":
+        run_serve(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -257,6 +257,20 @@ int ckks_ptset_conv_fused_s2(ckks_ctx* ctx, const double* weights, int cin, int 
  * ckks_boot_create.  Apply with ckks_bsgs + ckks_rescale. */
 int ckks_ptset_decompose(ckks_ctx* ctx, int w, int level, double scale, int bsgs_B, ckks_ptset** out);
 
+/* Fully-connected layer fused with the whole StoC (Sec. 4.3: slot encoding is CinS with
+ * l = 1, so the FC matrix merges with all of S_{N/2<-1}).  The input holds x (n_in reals,
+ * n_in a power of two) in slots 0 .. n_in - 1 and zeros elsewhere; the output holds
+ * y = M x (M row-major [n_out][n_in], n_out <= N/2) in its coefficients 0 .. n_out - 1
+ * (coefficient encoding: ready for ModRaise, or for ckks_decode with CKKS_COEFF).  The
+ * set holds the n_in diagonals of V M on x replicated with period n_in (d_o[i] =
+ * (V M)[i][(i + o) mod n_in]); ckks_fc_stoc replicates x with log2(N / 2n_in) rotations
+ * by -n_in 2^t, then BSGS + rescale (one level).  Rotation keys: those of the set and the
+ * replication steps. */
+int ckks_ptset_fc_stoc(ckks_ctx* ctx, const double* M, int n_out, int n_in, int level, double pt_scale, int bsgs_B,
+                       ckks_ptset** out);
+int ckks_fc_stoc(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* fc, int n_in,
+                 ckks_ct* out);
+
 /* Depthwise conv2d (Sec. 3.3.4; Table 1: 1 PMult, 0 HRot, 1 level): the c kernels
  * K[c][f][f] (cross-correlation, 'same' padding, kernel vectors of Fig. 1) packed in one
  * real-CinS plaintext <k_1 | ... | k_C>, so that one PMult gives k_i * i_i in every slice

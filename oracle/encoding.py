@@ -521,3 +521,27 @@ def decompose_kernels(W, C, t):
                 dy, dx = (a - c - p) // 2, (b - c - q) // 2
                 out[:, 4 * i + q + 2 * p, dy + R, dx + R] += W[:, ch, a, b]
     return out
+
+
+# ------------------------------------------------- FC fused with StoC (Sec. 4.3) -----
+def fc_stoc_matrix(M, n_ring):
+    """F = V M: the FC weights M (n_out x n_in) followed by the whole StoC.  With slot encoding
+    (CinS with l = 1) the StoC takes the slot vector V y to the coefficient encoding of y
+    (coefficients y_k, k < N/2), so HMatmul(F) on slots holding x leaves M x in the
+    coefficients.  Column j of F = slots of the real polynomial with coefficients M[:, j]."""
+    n_out, n_in = M.shape
+    F = np.zeros((n_ring // 2, n_in), dtype=np.complex128)
+    for j in range(n_in):
+        f = np.zeros(n_ring)
+        f[:n_out] = M[:, j]
+        F[:, j] = decode(f, n_ring)
+    return F
+
+
+def fc_stoc_diagonals(M, n_ring):
+    """diagonals of F acting on x replicated with period n_in (x_rep[j] = x[j mod n_in]):
+    d_o[i] = F[i][(i + o) mod n_in], o < n_in (a0 = 0, step 1, count n_in)"""
+    F = fc_stoc_matrix(M, n_ring)
+    m, n_in = F.shape
+    i = np.arange(m)
+    return {o: F[i, (i + o) % n_in] for o in range(n_in)}

@@ -435,6 +435,27 @@ class Oracle:
     def conv2d_cins(self, ct, plan):
         return self.rescale(self.bsgs(ct, plan))
 
+    def fc_plan(self, M, level, pt_scale, B=None):
+        """FC fused with the whole StoC (Sec. 4.3): BSGS plan over the n_in diagonals of V M"""
+        n_in = M.shape[1]
+        return self.make_plan(E.fc_stoc_diagonals(M, self.P.n), 0, 1, n_in, level, pt_scale, B)
+
+    def fc_replicate_steps(self, n_in):
+        """rotations that replicate slots [0, n_in) over all N/2 slots: -n_in 2^t"""
+        m = self.P.n // 2
+        steps, s = [], n_in
+        while s < m:
+            steps.append((-s) % m)
+            s *= 2
+        return steps
+
+    def fc_stoc(self, ct, plan, n_in):
+        """x in slots [0, n_in), zero elsewhere -> replicate (x += rot(x, -n_in 2^t)) ->
+        HMatmul(V M) -> rescale: the coefficients hold M x"""
+        for r in self.fc_replicate_steps(n_in):
+            ct = self.add(ct, self.rotate(ct, r))
+        return self.rescale(self.bsgs(ct, plan))
+
     def dwconv_cins(self, ct, pt_kernel):
         """depthwise conv2d (Sec. 3.3.4): one PMult by the packed kernels, then rescale"""
         return self.rescale(self.mul_plain(ct, pt_kernel))

@@ -112,6 +112,8 @@ _SIGS = {
     "ckks_encode_dwconv_kernel": [VP, VP, I, I, I, I, D, VP],
     "ckks_ptset_conv_fused_s2": [VP, VP, I, I, I, I, I, I, D, I, PVP],
     "ckks_ptset_decompose": [VP, I, I, D, I, PVP],
+    "ckks_ptset_fc_stoc": [VP, VP, I, I, I, D, I, PVP],
+    "ckks_fc_stoc": [VP, VP, VP, VP, I, VP],
     "ckks_boot_set_decomp": [VP, VP, VP],
     "ckks_block_multi": [VP, VP, I, PVP, PVP, VP, VP],
     "ckks_downsample_layer": [VP, VP, I, PVP, PVP, VP, PVP, VP, VP],
@@ -592,6 +594,20 @@ def ckks_ptset_conv_fused_s2(ctx, weights, cin, cout, f, w_in, t, level, pt_scal
     ctx.check(lib().ckks_ptset_conv_fused_s2(ctx, _ptr(W), cin, cout, f, w_in, t, level, pt_scale, bsgs_B,
                                              ctypes.byref(out)))
     return PtSet(out.value, ctx)
+
+
+def ckks_ptset_fc_stoc(ctx, M, level, pt_scale, bsgs_B=0) -> PtSet:
+    a = _f64(M)
+    n_out, n_in = a.shape
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_ptset_fc_stoc(ctx, _ptr(a), n_out, n_in, level, pt_scale, bsgs_B, ctypes.byref(out)))
+    return PtSet(out.value, ctx)
+
+
+def ckks_fc_stoc(ctx, keys, ct, fc, n_in, out=None):
+    out = out or ckks_ct_create(ctx)
+    ctx.check(lib().ckks_fc_stoc(ctx, keys, ct, fc, n_in, out))
+    return out
 
 
 def ckks_ptset_decompose(ctx, w, level, scale, bsgs_B=0) -> PtSet:

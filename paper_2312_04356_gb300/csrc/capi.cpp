@@ -799,6 +799,35 @@ int ckks_ptset_conv_fused_s2(ckks_ctx* ctx, const double* W, int cin, int cout, 
     });
 }
 
+int ckks_ptset_fc_stoc(ckks_ctx* ctx, const double* M, int n_out, int n_in, int level, double pt_scale, int B,
+                       ckks_ptset** out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(M);
+        REQ(out);
+        const int m = ctx->n / 2;
+        CK_CHECK(n_in >= 1 && n_in <= m && (n_in & (n_in - 1)) == 0, CKKS_EINVAL, "n_in must be a power of two <= N/2");
+        CK_CHECK(n_out >= 1 && n_out <= m, CKKS_EINVAL, "n_out must be in [1, N/2]");
+        CK_CHECK(level >= 1 && level <= ctx->L, CKKS_EINVAL, "the fused FC needs level >= 1");
+        *out = make_plan(ctx, fp64::fc_stoc_diagonals(M, n_out, n_in, ctx->n), 0, 1, n_in, level, pt_scale, B);
+    });
+}
+
+int ckks_fc_stoc(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* fc, int n_in, ckks_ct* out) {
+    return guard(ctx, [&] {
+        REQ(keys);
+        CT_OK(in);
+        REQ(fc);
+        REQ(out);
+        const int m = ctx->n / 2;
+        CK_CHECK(n_in >= 1 && n_in <= m && (n_in & (n_in - 1)) == 0 && fc->count == n_in, CKKS_EINVAL,
+                 "n_in must be the plaintext set's diagonal count, a power of two");
+        ckks_ct x = ops::copy_ct(*in);
+        for (int s = n_in; s < m; s *= 2) x = ops::add(x, ops::rotate(*keys, x, -s));
+        assign(out, ops::rescale(ops::bsgs(*keys, x, *fc)));
+    });
+}
+
 int ckks_ptset_decompose(ckks_ctx* ctx, int w, int level, double scale, int B, ckks_ptset** out) {
     return guard(ctx, [&] {
         REQ(ctx);

@@ -302,6 +302,27 @@ std::vector<double> decompose_kernels(const double* W, int cout, int cin, int f,
     return out;
 }
 
+// FC fused with the whole StoC (Sec. 4.3; slot encoding is CinS with l = 1): F = V M, whose
+// column j holds the slots of the real polynomial with coefficients M[:, j] (the StoC takes
+// slots V y to coefficients y).  On x replicated with period n_in the product needs only
+// the n_in diagonals d_o[i] = F[i][(i + o) mod n_in].
+Diag fc_stoc_diagonals(const double* M, int n_out, int n_in, int n) {
+    const int m = n / 2;
+    std::vector<std::vector<cplx>> F(n_in);
+    for (int j = 0; j < n_in; ++j) {
+        std::vector<double> f(n, 0.0);
+        for (int k = 0; k < n_out; ++k) f[k] = M[(size_t)k * n_in + j];
+        F[j] = decode_slots(f, n);
+    }
+    Diag D;
+    for (int o = 0; o < n_in; ++o) {
+        std::vector<cplx> d(m);
+        for (int i = 0; i < m; ++i) d[i] = F[(i + o) % n_in][i];
+        D[o] = std::move(d);
+    }
+    return D;
+}
+
 std::vector<std::vector<cplx>> fused_conv_diagonals(const double* W, int cin, int cout, int f, int w, int n) {
     const int two_l = w * w, ell = two_l / 2, C = n / two_l, m = n / 2;
     CK_CHECK(C >= 1 && cin <= C && cout <= C, CKKS_EINVAL, "channels do not fit in one ciphertext");

@@ -289,6 +289,7 @@ void ap_of_group(const std::vector<int>& strides, int m, int* a0, int* step, int
 std::vector<std::vector<cplx>> fused_conv_diagonals(const double* W, int cin, int cout, int f, int w, int n);
 std::vector<cplx> dwconv_kernel_slots(const double* K, int c, int f, int w, int n);
 Diag decompose_diag(int w, int m);
+Diag fc_stoc_diagonals(const double* M, int n_out, int n_in, int n);
 std::vector<double> decompose_kernels(const double* W, int cout, int cin, int f, int C, int t, int* f_out);
 std::vector<cplx> real_cins_slots(const double* m, int C, int two_l);
 std::vector<double> cins_to_reals(const std::vector<cplx>& z, int C, int two_l);

@@ -504,3 +504,32 @@ def _downsample_own_plans():
     pix = np.stack([E.encode(got[i * ell2:(i + 1) * ell2], w2 * w2) for i in range(4 * C)])
     want = np.stack([E.flatten_padded(v, w2) for v in ref])
     assert np.abs(pix - want).max() < 2.0 ** -12
+
+
+def test_fc_stoc_bitexact_and_fp64():
+    """FC fused with the whole StoC (Sec. 4.3): replication rotations + BSGS over the n_in
+    diagonals of V M, bit-exact against the oracle; the library's own set decodes (coefficient
+    encoding) to M x"""
+    from oracle.scheme import Oracle
+    seed = 81
+    P = oracle_params("cfg2_small")
+    m = P.n // 2
+    n_in, n_out = 16, 40
+    M = np.random.default_rng(seed).normal(0, 0.3, (n_out, n_in))
+    x = np.zeros(m)
+    x[:n_in] = WL.slots(seed, n_in).real
+    lev = 3
+    o0 = Oracle(P, seed)
+    plan = o0.fc_plan(M, lev, (P.delta[lev - 1] * float(P.q[lev])) / P.delta[lev])
+    K, o, ctx, keys = make_pair("cfg2_small", seed, rotations=plan.rotations(m) + o0.fc_replicate_steps(n_in),
+                                conj=False)
+    pt = o.encode_pt(x, lev, P.delta[lev])
+    ct = o.encrypt(pt, 3)
+    want = o.fc_stoc(ct, plan, n_in)
+    got = K.ckks_fc_stoc(ctx, keys, import_ct(K, ctx, ct), import_plan(K, ctx, plan), n_in)
+    assert_ct_equal(K, ctx, got, want, "FC (x) StoC")
+    own = K.ckks_ptset_fc_stoc(ctx, M, lev, plan.scale)
+    gct = K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, x, lev, P.delta[lev]), 4)
+    y = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, K.ckks_fc_stoc(ctx, keys, gct, own, n_in)), K.CKKS_COEFF)
+    assert np.abs(y[:n_out] - M @ x[:n_in]).max() < 2.0 ** -12
+    assert np.abs(y[n_out:]).max() < 2.0 ** -12

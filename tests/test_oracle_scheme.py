@@ -249,3 +249,33 @@ def test_dwconv_one_pmult():
     ell = w * w // 2
     pix = np.stack([E.encode(z[i * ell:(i + 1) * ell], w * w).reshape(w, w)[:w0, :w0] for i in range(C)])
     assert np.abs(pix - E.dwconv_same(x, K)).max() < 1e-6
+
+
+def test_fc_fused_with_stoc():
+    """FC fused with the whole StoC (Sec. 4.3, slot encoding = CinS with l = 1): V M equals the
+    explicit special-DFT product; the homomorphic layer leaves M x in the coefficients; it takes
+    log2(N/2 / n_in) replication rotations plus the BSGS rotations over n_in diagonals, 1 level"""
+    P = PP.Params(10, 3, 1, 60, 42, 60)
+    o = Oracle(P, 8)
+    n, m = P.n, P.n // 2
+    n_in, n_out = 16, 40
+    M = rng.normal(0, 0.3, (n_out, n_in))
+    F = E.fc_stoc_matrix(M, n)
+    Mfull = np.zeros((m, n_in))
+    Mfull[:n_out] = M
+    assert np.abs(F - E.V_matrix(n) @ Mfull).max() < 1e-9
+    x = np.zeros(m)
+    x[:n_in] = rng.uniform(-1, 1, n_in)
+    lev = 2
+    ct = o.encrypt(o.encode_pt(x, lev, P.delta[lev]), 4)
+    plan = o.fc_plan(M, lev, (P.delta[lev - 1] * float(P.q[lev])) / ct.scale)
+    o.gen_rotation_keys(plan.rotations(m) + o.fc_replicate_steps(n_in))
+    o.ops = {k: 0 for k in o.ops}
+    out = o.fc_stoc(ct, plan, n_in)
+    B = plan.B
+    G = -(-n_in // B)
+    assert o.ops["hrot"] == int(np.log2(m // n_in)) + (B - 1) + (G - 1)
+    assert out.level == lev - 1
+    y = o.decode_coeffs(o.decrypt(out))
+    assert np.abs(y[:n_out] - M @ x[:n_in]).max() < 1e-6
+    assert np.abs(y[n_out:]).max() < 1e-6
