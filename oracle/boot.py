@@ -127,7 +127,7 @@ def bootstrap(orc: Oracle, ct0, cfg: BootConfig):
     x = orc.mod_raise(ct0)
     x.scale = cfg.s_raise
     for plan in cfg.ctos:
-        x = orc.rescale(orc.bsgs(x, plan))
+        x = orc.bsgs(x, plan, rescale=True)
     cj = orc.conjugate(x)
     re = orc.add(x, cj)
     im = orc.imult(orc.sub(cj, x))
@@ -146,9 +146,9 @@ def stoc1(orc: Oracle, re, im, cfg: BootConfig):
     b = orc.rescale(orc.mul_plain(im, cfg.pt_mask_im))
     y = orc.add(a, orc.imult(b))
     if cfg.decomp is not None:
-        y = orc.rescale(orc.bsgs(y, cfg.decomp))
+        y = orc.bsgs(y, cfg.decomp, rescale=True)
     for plan in cfg.stoc:
-        y = orc.rescale(orc.bsgs(y, plan))
+        y = orc.bsgs(y, plan, rescale=True)
     return y
 
 
@@ -163,13 +163,10 @@ def block(orc: Oracle, ct_in, conv_plan, cfg: BootConfig):
 def block_multi(orc: Oracle, cts, conv_plans, cfg: BootConfig):
     """conv2d over several input ciphertexts, then bootstrap + StoC1 tail.  With the
     decomposed kernels of a stride-2 conv this is Alg. 2 lines 10-17 (BSGS per input
-    ciphertext, HAdd, one rescale); with plain kernels it is the C_in > C generalisation
+    ciphertext, HAdd, one rescale; the giant steps of both share one ModDown fused with the
+    rescale); with plain kernels it is the C_in > C generalisation
     (Sec. 3.3.3: the block matrix-vector product, one output ciphertext)."""
-    x = None
-    for ct, plan in zip(cts, conv_plans):
-        y = orc.bsgs(ct, plan)
-        x = y if x is None else orc.add(x, y)
-    x = orc.rescale(x)
+    x = orc.bsgs_multi(cts, conv_plans, rescale=True)
     assert abs(x.scale - cfg.delta0) <= 1e-9 * cfg.delta0
     re, im = bootstrap(orc, x, cfg)
     return stoc1(orc, re, im, cfg)

@@ -75,4 +75,4 @@ def relu_eval(orc: Oracle, ct, stages):
     for s in stages:
         y = orc.cheb_eval(y, s)
     lev = orc.prod_level(y.level)
-    return orc.rescale(orc.mul_relin(orc.level_down(ct, lev), orc.level_down(y, lev)))
+    return orc.mul_relin_rescale(orc.level_down(ct, lev), orc.level_down(y, lev))

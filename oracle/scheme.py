@@ -317,8 +317,9 @@ class Oracle:
             out.append(D)
         return out
 
-    def key_switch_raised(self, digits, code, level):
-        """inner product of raised digits with switching key `code`, then ModDown"""
+    def key_switch_inner(self, digits, code, level):
+        """inner product of raised digits with switching key `code`: two polynomials over
+        Q_l u P (coefficient domain), before ModDown"""
         P = self.P
         self.ops["keyswitch"] += 1
         ext = P.moduli(level, True)
@@ -330,10 +331,54 @@ class Oracle:
             Dn = self.ntt(D, level, True)
             C.mul_acc(acc_b, Dn, np.ascontiguousarray(kb[d][rows]), ext)
             C.mul_acc(acc_a, Dn, np.ascontiguousarray(ka[d][rows]), ext)
-        acc_b = self.intt(acc_b, level, True)
-        acc_a = self.intt(acc_a, level, True)
+        return self.intt(acc_b, level, True), self.intt(acc_a, level, True)
+
+    def key_switch_raised(self, digits, code, level):
+        """inner product of raised digits with switching key `code`, then ModDown"""
+        acc_b, acc_a = self.key_switch_inner(digits, code, level)
+        q = self.P.moduli(level)
+        return C.mod_down(acc_b, q, self.P.p), C.mod_down(acc_a, q, self.P.p)
+
+    def lift_p(self, acc, x, level):
+        """acc over Q_l u P plus P x (x over Q_l): rows 0..l += [P]_{q_i} x_i"""
+        P = self.P
         q = P.moduli(level)
-        return C.mod_down(acc_b, q, P.p), C.mod_down(acc_a, q, P.p)
+        pm = []
+        for qi in q:
+            v = 1
+            for pj in P.p:
+                v = v * (pj % qi) % qi
+            pm.append(v)
+        out = acc.copy()
+        out[: level + 1] = C.add(acc[: level + 1], C.mul_scalar(x, pm, q), q)
+        return out
+
+    def mod_down_rescale(self, acc_b, acc_a, level):
+        """ModDown fused with the rescale after it: the Q_l u P polynomials divided by M = q_l P
+        with rounding, out_i = (a_i - r) M^{-1} mod q_i (i < l), r the centred remainder of a
+        mod M.  Exact: r by CRT in Python integers."""
+        P = self.P
+        self.ops["rescale"] += 1
+        S = [int(P.q[level])] + [int(x) for x in P.p]
+        return self._div_round(acc_b, level, S), self._div_round(acc_a, level, S)
+
+    def _div_round(self, acc, level, S):
+        M = 1
+        for m in S:
+            M *= m
+        r = np.zeros(acc.shape[1], dtype=object)
+        for k, mk in enumerate(S):
+            Mk = M // mk
+            r = r + (acc[level + k].astype(object) * pow(Mk % mk, -1, mk)) % mk * Mk
+        r = r % M
+        r = np.where(r > M // 2, r - M, r)
+        q = self.P.moduli(level - 1)
+        out = np.empty((len(q), acc.shape[1]), dtype=np.uint64)
+        for i, qi in enumerate(q):
+            qi = int(qi)
+            inv = pow(M % qi, -1, qi)
+            out[i] = ((acc[i].astype(object) - r) % qi * inv % qi).astype(np.uint64)
+        return out
 
     def rotate_hoisted(self, ct, steps):
         """HRot(ct, r) for every r in steps, sharing one ModUp of c1"""
@@ -382,6 +427,21 @@ class Oracle:
         k0, k1 = self.key_switch_raised(self.mod_up(d2, l), 0, l)
         return Ciphertext(C.add(d0, k0, q), C.add(d1, k1, q), l, a.scale * b.scale)
 
+    def mul_relin_rescale(self, a, b):
+        """HMult, relinearisation and rescale, the relinearisation's ModDown fused with the
+        rescale: (d0, d1) + keyswitch(d2) kept over Q_l u P and divided by P q_l at once"""
+        assert a.level == b.level and a.level >= 1
+        self.ops["hmult"] += 1
+        l = a.level
+        q = self.P.moduli(l)
+        a0, a1, b0, b1 = (self.ntt(x, l) for x in (a.c0, a.c1, b.c0, b.c1))
+        d0 = self.intt(C.mul(a0, b0, q), l)
+        d1 = self.intt(C.add(C.mul(a0, b1, q), C.mul(a1, b0, q), q), l)
+        d2 = self.intt(C.mul(a1, b1, q), l)
+        kb, ka = self.key_switch_inner(self.mod_up(d2, l), 0, l)
+        c0, c1 = self.mod_down_rescale(self.lift_p(kb, d0, l), self.lift_p(ka, d1, l), l)
+        return Ciphertext(c0, c1, l - 1, a.scale * b.scale / float(self.P.q[l]))
+
     # ------------------------------------------------------------ BSGS -------
     def make_plan(self, diags, a0, step, count, level, scale, B=None):
         """diags: {offset: slot vector}; builds pre-rotated plaintexts d'_{g,b}"""
@@ -400,27 +460,51 @@ class Oracle:
                 plan.pts[(g, b)] = self.encode_pt(np.roll(diags[off], R), level, scale)
         return plan
 
-    def bsgs(self, ct, plan):
-        """sum_g rot_{a0+step*g*B}( sum_b pt_{g,b} (*) rot_{step*b}(ct) ), no rescale"""
-        assert ct.level == plan.level
-        m = self.P.n // 2
-        used_b = sorted({b for (_, b) in plan.pts})
-        baby = dict(zip(used_b, self.rotate_hoisted(ct, [plan.step * b % m for b in used_b])))
-        out = None
-        for g in range(plan.G):
-            inner = None
-            for b in range(plan.B):
-                if (g, b) not in plan.pts:
+    def bsgs(self, ct, plan, rescale=False):
+        """sum_g rot_{a0+step*g*B}( sum_b pt_{g,b} (*) rot_{step*b}(ct) )"""
+        return self.bsgs_multi([ct], [plan], rescale)
+
+    def bsgs_multi(self, cts, plans, rescale=False):
+        """sum over inputs t and giant steps g of rot_{R_g}(sum_b pt_{g,b} (*) rot_{step b}(ct_t)).
+        Baby-step rotations share one ModUp per input (hoisting).  The giant-step rotations'
+        key switches are summed over Q_l u P together with P times the parts that need no key
+        switch, and brought down once: ModDown, or ModDown fused with the rescale when
+        `rescale` is set."""
+        P = self.P
+        l = cts[0].level
+        m = P.n // 2
+        q, ext = P.moduli(l), P.moduli(l, True)
+        plain, acc = None, None
+        for ct, plan in zip(cts, plans):
+            assert ct.level == plan.level == l
+            used_b = sorted({b for (_, b) in plan.pts})
+            baby = dict(zip(used_b, self.rotate_hoisted(ct, [plan.step * b % m for b in used_b])))
+            for g in range(plan.G):
+                inner = None
+                for b in range(plan.B):
+                    if (g, b) not in plan.pts:
+                        continue
+                    t = self.mul_plain(baby[b], plan.pts[(g, b)])
+                    inner = t if inner is None else self.add(inner, t)
+                if inner is None:
                     continue
-                t = self.mul_plain(baby[b], plan.pts[(g, b)])
-                inner = t if inner is None else self.add(inner, t)
-            if inner is None:
-                continue
-            R = (plan.a0 + plan.step * g * plan.B) % m
-            if R:
-                inner = self.rotate(inner, R)
-            out = inner if out is None else self.add(out, inner)
-        return out
+                R = (plan.a0 + plan.step * g * plan.B) % m
+                if R:
+                    gal = self.galois(R)
+                    self.ops["hrot"] += 1
+                    dg = [C.automorphism(D, ext, gal, P.logn) for D in self.mod_up(inner.c1, l)]
+                    kb, ka = self.key_switch_inner(dg, gal, l)
+                    acc = [kb, ka] if acc is None else [C.add(acc[0], kb, ext), C.add(acc[1], ka, ext)]
+                    inner = Ciphertext(C.automorphism(inner.c0, q, gal, P.logn), np.zeros_like(inner.c1), l,
+                                       inner.scale)
+                plain = inner if plain is None else self.add(plain, inner)
+        if acc is None:
+            return self.rescale(plain) if rescale else plain
+        kb, ka = self.lift_p(acc[0], plain.c0, l), self.lift_p(acc[1], plain.c1, l)
+        if rescale:
+            c0, c1 = self.mod_down_rescale(kb, ka, l)
+            return Ciphertext(c0, c1, l - 1, plain.scale / float(P.q[l]))
+        return Ciphertext(C.mod_down(kb, q, P.p), C.mod_down(ka, q, P.p), l, plain.scale)
 
     # --------------------------------------------------- fused CinS conv ----
     def conv_plan(self, W, cin, cout, f, w, level, pt_scale, B=None):
@@ -433,7 +517,7 @@ class Oracle:
         return self.make_plan(dd, 0, ell, C_, level, pt_scale, B)
 
     def conv2d_cins(self, ct, plan):
-        return self.rescale(self.bsgs(ct, plan))
+        return self.bsgs(ct, plan, rescale=True)
 
     def fc_plan(self, M, level, pt_scale, B=None):
         """FC fused with the whole StoC (Sec. 4.3): BSGS plan over the n_in diagonals of V M"""
@@ -454,7 +538,7 @@ class Oracle:
         HMatmul(V M) -> rescale: the coefficients hold M x"""
         for r in self.fc_replicate_steps(n_in):
             ct = self.add(ct, self.rotate(ct, r))
-        return self.rescale(self.bsgs(ct, plan))
+        return self.bsgs(ct, plan, rescale=True)
 
     def dwconv_cins(self, ct, pt_kernel):
         """depthwise conv2d (Sec. 3.3.4): one PMult by the packed kernels, then rescale"""
@@ -502,7 +586,7 @@ class Oracle:
             if a != b:
                 need(b - a)
             m = self.prod_level(min(T[a].level, T[b].level))
-            t = self.rescale(self.mul_relin(at(a, m), at(b, m)))
+            t = self.mul_relin_rescale(at(a, m), at(b, m))
             t = self.add(t, t)
             t = self.add_const(t, -1.0) if a == b else self.sub(t, at(b - a, m - 1))
             T[k] = t
@@ -585,7 +669,7 @@ class Oracle:
                     prod.scale = (Tn.scale * s_c) / float(self.P.q[lk])
             else:
                 lev = self.prod_level(min(Q.level, Tn.level))
-                prod = self.rescale(self.mul_relin(self.level_down(Q, lev), at(n, lev)))
+                prod = self.mul_relin_rescale(self.level_down(Q, lev), at(n, lev))
             if isinstance(R, float):
                 return R if prod is None else self.add_const(prod, R)
             if prod is None:
@@ -604,7 +688,7 @@ class Oracle:
         """cos(2 pi (K y - 1/4) / 2^r) by Chebyshev, then r double angles -> sin(2 pi K y)"""
         y = self.cheb_eval(x, coeffs)
         for _ in range(r):
-            y = self.rescale(self.mul_relin(y, y))
+            y = self.mul_relin_rescale(y, y)
             y = self.add(y, y)
             y = self.add_const(y, -1.0)
         return y

@@ -824,7 +824,7 @@ int ckks_fc_stoc(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const 
                  "n_in must be the plaintext set's diagonal count, a power of two");
         ckks_ct x = ops::copy_ct(*in);
         for (int s = n_in; s < m; s *= 2) x = ops::add(x, ops::rotate(*keys, x, -s));
-        assign(out, ops::rescale(ops::bsgs(*keys, x, *fc)));
+        assign(out, ops::bsgs(*keys, x, *fc, true));
     });
 }
 
@@ -866,7 +866,7 @@ int ckks_conv2d_cins(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, co
         CT_OK(in);
         REQ(conv);
         REQ(out);
-        assign(out, ops::rescale(ops::bsgs(*keys, *in, *conv)));
+        assign(out, ops::bsgs(*keys, *in, *conv, true));
     });
 }
 

@@ -51,6 +51,9 @@ struct ConvTab {
     int* d_out_ids = nullptr;
     u64* d_qhat_inv = nullptr;   // [nin] and Shoup [nin]
     u64* d_qhat_mod = nullptr;   // [nout][nin] and Shoup [nout][nin]
+    // exact (rounded) conversion only: 1/q_i as doubles [nin], p_m - (prod q_i mod p_m) [nout]
+    double* d_inv_q = nullptr;
+    u64* d_corr = nullptr;
 };
 
 // Device buffer owned by RAII (stream-ordered allocation on the context's stream).
@@ -84,6 +87,8 @@ struct ckks_ctx {
     int* d_iota = nullptr;                   // 0..nall-1
     u64* d_pinv = nullptr;                   // P^{-1} mod q_i [nq], Shoup [nq]
     u64* d_qlinv = nullptr;                  // q_l^{-1} mod q_i [nq][nq], Shoup [nq][nq]
+    u64* d_pqlinv = nullptr;                 // (P q_l)^{-1} mod q_i [nq][nq], Shoup [nq][nq]
+    u64* d_pmod = nullptr;                   // P mod q_i [nq], Shoup [nq]
     std::vector<int*> d_ext_ids;             // per level: [0..l] + specials
     // per level: the rows of the raised digits that ModUp converts (offsets in limbs
     // from the start of [ndig][next][N]) and their prime ids, for one NTT launch
@@ -91,6 +96,7 @@ struct ckks_ctx {
     std::vector<int> modup_nrows;
     std::map<std::pair<int, int>, std::unique_ptr<ConvTab>> modup_tabs;  // (level, digit)
     std::map<int, std::unique_ptr<ConvTab>> moddown_tabs;               // level
+    std::map<int, std::unique_ptr<ConvTab>> mdrs_tabs;                  // level: {q_l, P} -> Q_{l-1}
     std::string err;
     int ntt_choice[8] = {-1, -1, -1, -1, -1, -1, -1, -1};   // tuned NTT variant per limb-count class
     std::map<std::string, long> ops;   // op counters (PMult, HRot, keyswitch, ...)
@@ -115,6 +121,7 @@ struct ckks_ctx {
     std::vector<int> ext_ids(int level) const;
     const ConvTab& modup_tab(int level, int d);
     const ConvTab& moddown_tab(int level);
+    const ConvTab& mdrs_tab(int level);
     ~ckks_ctx();
 };
 
@@ -239,6 +246,8 @@ struct ConvJob {
     u64* out;
     const int *in_ids, *out_ids, *out_rows;
     const u64 *qinv, *qmod;
+    const double* inv_q;   // non-null: subtract v Q, v = round(sum_i xhat_i / q_i) (centred remainder)
+    const u64* corr;
     int nin, nout, ngroups;
     size_t in_pstride, out_pstride;
 };
@@ -252,7 +261,10 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly);
 // key-switch inner product: D [ndig][next][N], key rows krow[e] of [ndig][nall][N];
 // ob/oa [next][N] = sum_d D_d(sigma_g) * key_d ; g = 1 means no automorphism
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
-              const u64* ka, u64* ob, u64* oa, u64 g);
+              const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate = false);
+// o += a * s[limb % lpp] (s residues, sp their Shoup companions; device arrays)
+void mul_scalar_acc(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nlimbs, const int* ids,
+                    int lpp);
 // uniform residues in the NTT domain drawn from the counter stream (see ckks.h)
 void sample_uniform(const ckks_ctx* c, u64* o, int nlimbs, const int* ids, u64 key);
 void sample_small(const ckks_ctx* c, int64_t* o, u64 key, int kind /*0 ternary, 1 gauss*/);

@@ -540,7 +540,10 @@ __global__ void k_bsgs_inner(kern::BsgsTerms T, u64* __restrict__ o, const DevPr
 }
 
 // ------------------------------------------------------- base conversion ----
-// y_m = sum_i [x_i * qhat_i^{-1}]_{q_i} * (qhat_i mod p_m)  (no correction term)
+// y_m = sum_i [x_i * qhat_i^{-1}]_{q_i} * (qhat_i mod p_m)  (no correction term), or, for an
+// exact table, minus v (Q mod p_m) with v = round(sum_i xhat_i / q_i) evaluated in FP64
+// (Halevi, Polyakov, Shoup 2019): y then represents the centred remainder of x mod Q, up
+// to an FP64 error that matters only within ~1e-15 of a half-integer.
 // One thread per coefficient; grid.z walks over (job, group of CONV_OUT outputs), so the
 // digits of one ModUp (or the two halves of one ModDown) share a launch.  The products are
 // summed exactly in 128 bits (each < 2^122, at most 16 terms) and reduced once:
@@ -553,6 +556,8 @@ __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const De
     __shared__ u64 s_c[CONV_OUT][MAX_CONV_IN];
     __shared__ DevPrime s_pm[CONV_OUT];
     __shared__ int s_row[CONV_OUT];
+    __shared__ double s_invq[MAX_CONV_IN];
+    __shared__ u64 s_corr[CONV_OUT];
     // which job and output group this CTA serves
     int z = blockIdx.z, jb = 0;
     while (jb < J.n - 1 && z >= J.job[jb].ngroups) {
@@ -564,10 +569,12 @@ __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const De
     const int m0 = z * CONV_OUT;
     const int mcount = min(CONV_OUT, nout - m0);
     const int tid = threadIdx.x;
+    const bool exact = job.inv_q != nullptr;
     if (tid < nin) {
         s_qi[tid] = P[job.in_ids[tid]].m.q;
         s_qinv[tid] = job.qinv[tid];
         s_qinvp[tid] = job.qinv[nin + tid];
+        s_invq[tid] = exact ? job.inv_q[tid] : 0.0;
     }
     if (tid < CONV_OUT * MAX_CONV_IN) {
         const int m = tid / MAX_CONV_IN, i = tid % MAX_CONV_IN;
@@ -576,6 +583,7 @@ __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const De
     if (tid < mcount) {
         s_pm[tid] = P[job.out_ids[m0 + tid]];
         s_row[tid] = job.out_rows[m0 + tid];
+        s_corr[tid] = exact ? job.corr[m0 + tid] : 0;
     }
     __syncthreads();
     const u64* in = job.in + blockIdx.y * job.in_pstride;
@@ -602,12 +610,24 @@ __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const De
             }
         }
     }
+    if (exact) {
+        double f = 0.0;
+        for (int i = 0; i < nin; ++i) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xh[i]), s_invq[i]));
+        const u64 v = (u64)__double2ll_rn(f);
+#pragma unroll
+        for (int m = 0; m < CONV_OUT; ++m) {
+            const u64 pl = v * s_corr[m], ph = __umul64hi(v, s_corr[m]);
+            lo[m] += pl;
+            hi[m] += ph + (lo[m] < pl ? 1ull : 0ull);
+        }
+    }
 #pragma unroll
     for (int m = 0; m < CONV_OUT; ++m)
         if (m < mcount) out[(size_t)s_row[m] * n + j] = reduce128_lazy(hi[m], lo[m], s_pm[m]);
 }
 
 // ---------------------------------------------------- key-switch product ----
+template <bool ACC>
 __global__ void k_ks_inner(const u64* __restrict__ D, int ndig, int next, const int* __restrict__ ext_ids,
                            const u64* __restrict__ kb, const u64* __restrict__ ka, u64* __restrict__ ob,
                            u64* __restrict__ oa, const DevPrime* __restrict__ P, int logn, u64 g, size_t kstride) {
@@ -624,9 +644,24 @@ __global__ void k_ks_inner(const u64* __restrict__ D, int ndig, int next, const 
             accb = add_mod(accb, mul_mod(x, kb[kk], m), m.q);
             acca = add_mod(acca, mul_mod(x, ka[kk], m), m.q);
         }
+        if (ACC) {
+            accb = add_mod(accb, ob[(size_t)e * n + j], m.q);
+            acca = add_mod(acca, oa[(size_t)e * n + j], m.q);
+        }
         ob[(size_t)e * n + j] = accb;
         oa[(size_t)e * n + j] = acca;
     }
+}
+
+// o += a * s[limb % lpp] (Shoup pairs s, sp)
+__global__ void k_mul_scalar_acc(const u64* a, const u64* s, const u64* sp, u64* o, const DevPrime* P, const int* ids,
+                                 int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const int r = limb % lpp;
+    const u64 q = P[ids[r]].m.q;
+    const u64 w = s[r], wp = sp[r];
+    const size_t off = (size_t)limb << logn;
+    EW_LOOP(1 << logn) o[off + j] = add_mod(o[off + j], mul_shoup(a[off + j], w, wp, q), q);
 }
 
 // ------------------------------------------------------------ sampling ----
@@ -885,6 +920,8 @@ void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t
     j.out_rows = t.d_out_ids + t.nout;
     j.qinv = t.d_qhat_inv;
     j.qmod = t.d_qhat_mod;
+    j.inv_q = t.d_inv_q;
+    j.corr = t.d_corr;
     j.nin = t.nin;
     j.nout = t.nout;
     j.ngroups = (t.nout + CONV_OUT - 1) / CONV_OUT;
@@ -908,11 +945,25 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly) {
 }
 
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
-              const u64* ka, u64* ob, u64* oa, u64 g) {
-    { KTimer kt_(c, "ks_inner", (3.0 * ndig + 2.0) * next * c->n * 8.0);
-    k_ks_inner<<<ew_grid(c->n, next), EW_THREADS, 0, c->stream>>>(D, ndig, next, ext_ids, kb, ka, ob, oa,
-                                                                   c->d_primes, c->logn, g,
-                                                                   (size_t)c->nall << c->logn);
+              const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate) {
+    if (accumulate) {
+        KTimer kt_(c, "ks_inner", (3.0 * ndig + 4.0) * next * c->n * 8.0);
+        k_ks_inner<true><<<ew_grid(c->n, next), EW_THREADS, 0, c->stream>>>(D, ndig, next, ext_ids, kb, ka, ob, oa,
+                                                                         c->d_primes, c->logn, g,
+                                                                         (size_t)c->nall << c->logn);
+    } else {
+        KTimer kt_(c, "ks_inner", (3.0 * ndig + 2.0) * next * c->n * 8.0);
+        k_ks_inner<false><<<ew_grid(c->n, next), EW_THREADS, 0, c->stream>>>(D, ndig, next, ext_ids, kb, ka, ob, oa,
+                                                                          c->d_primes, c->logn, g,
+                                                                          (size_t)c->nall << c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void mul_scalar_acc(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nl, const int* ids,
+                    int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "mul_scalar_acc", 3.0 * (double)nl * c->n * 8.0);
+    k_mul_scalar_acc<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, s, sp, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }

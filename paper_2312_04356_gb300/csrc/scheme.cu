@@ -71,7 +71,8 @@ std::vector<int> ckks_ctx::ext_ids(int level) const {
 }
 
 static std::unique_ptr<ConvTab> make_conv_tab(ckks_ctx* c, const std::vector<int>& in_ids,
-                                              const std::vector<int>& out_ids, const std::vector<int>& out_rows) {
+                                              const std::vector<int>& out_ids, const std::vector<int>& out_rows,
+                                              bool exact = false) {
     auto t = std::make_unique<ConvTab>();
     t->nin = (int)in_ids.size();
     t->nout = (int)out_ids.size();
@@ -100,6 +101,19 @@ static std::unique_ptr<ConvTab> make_conv_tab(ckks_ctx* c, const std::vector<int
     t->d_out_ids = dev_upload_persistent(ids_rows);
     t->d_qhat_inv = dev_upload_persistent(qinv);
     t->d_qhat_mod = dev_upload_persistent(qmod);
+    if (exact) {
+        std::vector<double> invq(t->nin);
+        for (int i = 0; i < t->nin; ++i) invq[i] = 1.0 / (double)c->mod_of[in_ids[i]];
+        std::vector<u64> corr(t->nout);
+        for (int m = 0; m < t->nout; ++m) {
+            const u64 pm = c->mod_of[out_ids[m]];
+            u64 v = 1;
+            for (int k = 0; k < t->nin; ++k) v = mulmod(v, c->mod_of[in_ids[k]] % pm, pm);
+            corr[m] = v ? pm - v : 0;
+        }
+        t->d_inv_q = dev_upload_persistent(invq);
+        t->d_corr = dev_upload_persistent(corr);
+    }
     return t;
 }
 
@@ -132,17 +146,36 @@ const ConvTab& ckks_ctx::moddown_tab(int level) {
     return *moddown_tabs[level];
 }
 
+// ModDown fused with a rescale: inputs q_l and the special primes (rows l .. l + np of the
+// extended layout), outputs q_0 .. q_{l-1}
+const ConvTab& ckks_ctx::mdrs_tab(int level) {
+    auto it = mdrs_tabs.find(level);
+    if (it != mdrs_tabs.end()) return *it->second;
+    std::vector<int> in_ids, out_ids, out_rows;
+    in_ids.push_back(level);
+    for (int j = 0; j < np; ++j) in_ids.push_back(nq + j);
+    for (int i = 0; i < level; ++i) {
+        out_ids.push_back(i);
+        out_rows.push_back(i);
+    }
+    mdrs_tabs[level] = make_conv_tab(this, in_ids, out_ids, out_rows, true);
+    return *mdrs_tabs[level];
+}
+
 static void free_tab(ConvTab* t) {
     cudaFree(t->d_in_ids);
     cudaFree(t->d_out_ids);
     cudaFree(t->d_qhat_inv);
     cudaFree(t->d_qhat_mod);
+    if (t->d_inv_q) cudaFree(t->d_inv_q);
+    if (t->d_corr) cudaFree(t->d_corr);
 }
 
 ckks_ctx::~ckks_ctx() {
     cudaStreamSynchronize(stream);
     for (auto& kv : modup_tabs) free_tab(kv.second.get());
     for (auto& kv : moddown_tabs) free_tab(kv.second.get());
+    for (auto& kv : mdrs_tabs) free_tab(kv.second.get());
     for (int* p : d_ext_ids) cudaFree(p);
     for (int* p : d_modup_off) cudaFree(p);
     for (int* p : d_modup_pid) cudaFree(p);
@@ -152,6 +185,8 @@ ckks_ctx::~ckks_ctx() {
     cudaFree(d_gauss);
     cudaFree(d_pinv);
     cudaFree(d_qlinv);
+    cudaFree(d_pqlinv);
+    cudaFree(d_pmod);
 }
 
 static unsigned brev_host(unsigned x, int bits) {
@@ -243,11 +278,28 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
             qlinv[(size_t)l * c->nq + i] = v;
             qlinv[(size_t)c->nq * c->nq + (size_t)l * c->nq + i] = shoup(v, c->q[i]);
         }
+    // (P q_l)^{-1} mod q_i (i < l) and P mod q_i (Shoup pairs)
+    std::vector<u64> pqlinv(2 * (size_t)c->nq * c->nq, 0), pmod(2 * c->nq);
+    for (int i = 0; i < c->nq; ++i) {
+        u64 pr = 1;
+        for (u64 pj : c->p) pr = mulmod(pr, pj % c->q[i], c->q[i]);
+        pmod[i] = pr;
+        pmod[c->nq + i] = shoup(pr, c->q[i]);
+    }
+    for (int l = 1; l < c->nq; ++l)
+        for (int i = 0; i < l; ++i) {
+            u64 v = invmod(mulmod(pmod[i], c->q[l] % c->q[i], c->q[i]), c->q[i]);
+            pqlinv[(size_t)l * c->nq + i] = v;
+            pqlinv[(size_t)c->nq * c->nq + (size_t)l * c->nq + i] = shoup(v, c->q[i]);
+        }
     c->d_pinv = dev_upload_persistent(pinv);
     c->d_qlinv = dev_upload_persistent(qlinv);
+    c->d_pqlinv = dev_upload_persistent(pqlinv);
+    c->d_pmod = dev_upload_persistent(pmod);
     // every base-conversion table up front (no allocation later, e.g. inside stream capture)
     for (int l = 0; l <= c->L; ++l) {
         c->moddown_tab(l);
+        if (l >= 1) c->mdrs_tab(l);
         std::vector<std::vector<int>> dig = c->digits(l);
         std::vector<int> ext = c->ext_ids(l), off, pid;
         const int next = (int)ext.size();
@@ -469,21 +521,61 @@ DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out) {
     return D;
 }
 
-// inner product with switching key `code` (automorphism g applied to D on the fly), ModDown
-void key_switch_raised(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
-                       u64* out0, u64* out1) {
+// inner product with switching key `code` (automorphism g applied to D on the fly) over
+// Q_l u P: acc [2][next][N], NTT domain; `accumulate` adds to what acc holds
+void key_switch_inner(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
+                      u64* acc, bool accumulate) {
     auto it = keys.swk.find(code);
     CK_CHECK(it != keys.swk.end(), CKKS_ENOKEY, "missing switching key (code " + std::to_string(code) + ")");
     const SwitchKey& k = *it->second;
     c->ops["keyswitch"]++;
+    const size_t next = (size_t)level + 1 + c->np;
+    kern::ks_inner(c, D, ndig, (int)next, c->d_ext_ids[level], k.b.ptr, k.a.ptr, acc, acc + next * c->n, g,
+                   accumulate);
+}
+
+// ModDown fused with the rescale after it: both halves of acc (Q_l u P, NTT domain) divided
+// by P q_l, (acc - Conv_{q_l, P -> Q_{l-1}}(acc)) (P q_l)^{-1}; out [2][l][N]
+void mod_down_rescale(ckks_ctx* c, u64* acc, int level, u64* out) {
+    CK_CHECK(level >= 1, CKKS_ELEVEL, "cannot rescale a level-0 ciphertext");
+    c->ops["rescale"]++;
+    const size_t n = c->n;
+    const int l = level, np1 = c->np + 1;
+    const size_t next = (size_t)l + 1 + c->np;
+    u64* ab = acc;
+    u64* aa = acc + next * n;
+    const int* pid = c->d_ext_ids[level] + l;      // q_l, then the special primes
+    if (c->logn == 16) {
+        kern::ntt_inverse(c, ab + (size_t)l * n, 2 * np1, pid, np1, next * n);
+    } else {
+        kern::ntt_inverse(c, ab + (size_t)l * n, np1, pid, np1);
+        kern::ntt_inverse(c, aa + (size_t)l * n, np1, pid, np1);
+    }
+    DevBuf conv(2 * (size_t)l * n, c->stream);
+    kern::base_convert(c, c->mdrs_tab(l), ab + (size_t)l * n, n, conv.ptr, n, 2, next * n, (size_t)l * n);
+    kern::ntt_forward(c, conv.ptr, 2 * l, c->d_iota, l);
+    const u64* s = c->d_pqlinv + (size_t)l * c->nq;
+    const u64* sp = c->d_pqlinv + (size_t)c->nq * c->nq + (size_t)l * c->nq;
+    kern::sub_mul_scalar(c, ab, conv.ptr, s, sp, out, l, c->d_iota, l);
+    kern::sub_mul_scalar(c, aa, conv.ptr + (size_t)l * n, s, sp, out + (size_t)l * n, l, c->d_iota, l);
+}
+
+// acc (Q_l u P) += P x on the Q rows, x [2][l+1][N]
+static void lift_p(ckks_ctx* c, const u64* x, u64* acc, int level) {
+    const int nl = level + 1;
+    const size_t next = (size_t)nl + c->np;
+    kern::mul_scalar_acc(c, x, c->d_pmod, c->d_pmod + c->nq, acc, nl, c->d_iota, nl);
+    kern::mul_scalar_acc(c, x + (size_t)nl * c->n, c->d_pmod, c->d_pmod + c->nq, acc + next * c->n, nl, c->d_iota,
+                         nl);
+}
+
+// ModDown of both halves of acc: out0, out1 [l+1][N]
+static void mod_down(ckks_ctx* c, u64* acc, int level, u64* out0, u64* out1) {
     const size_t n = c->n;
     const int nl = level + 1;
     const int next = nl + c->np;
-    DevBuf acc(2 * (size_t)next * n, c->stream);
-    u64* ab = acc.ptr;
-    u64* aa = acc.ptr + (size_t)next * n;
-    kern::ks_inner(c, D, ndig, next, c->d_ext_ids[level], k.b.ptr, k.a.ptr, ab, aa, g);
-    // ModDown of both halves
+    u64* ab = acc;
+    u64* aa = acc + (size_t)next * n;
     const int* pid = c->d_ext_ids[level] + nl;
     if (c->logn == 16) {
         kern::ntt_inverse(c, ab + (size_t)nl * n, 2 * c->np, pid, c->np, (size_t)next * n);
@@ -497,6 +589,14 @@ void key_switch_raised(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndi
     kern::ntt_forward(c, conv.ptr, 2 * nl, c->d_iota, nl);
     kern::sub_mul_scalar(c, ab, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out0, nl, c->d_iota, nl);
     kern::sub_mul_scalar(c, aa, conv.ptr + (size_t)nl * n, c->d_pinv, c->d_pinv + c->nq, out1, nl, c->d_iota, nl);
+}
+
+// inner product with switching key `code` (automorphism g applied to D on the fly), ModDown
+void key_switch_raised(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
+                       u64* out0, u64* out1) {
+    DevBuf acc(2 * ((size_t)level + 1 + c->np) * c->n, c->stream);
+    key_switch_inner(c, keys, D, ndig, level, code, g, acc.ptr, false);
+    mod_down(c, acc.ptr, level, out0, out1);
 }
 
 u64 galois_of_step(const ckks_ctx* c, long long r) {
@@ -570,23 +670,61 @@ ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
     return o;
 }
 
-// ---------------------------------------------------------------- BSGS -----
-ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps) {
+// HMult, relinearisation and rescale: (d0, d1) + keyswitch(d2) kept over Q_l u P and
+// divided by P q_l at once (the relinearisation's ModDown fused with the rescale)
+ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
     ckks_ctx* c = a.ctx;
-    CK_CHECK(a.level == ps.level, CKKS_EINVAL, "ciphertext level differs from the plaintext set's level");
-    CK_CHECK(!ps.pts.empty(), CKKS_EINVAL, "empty plaintext set");
+    CK_CHECK(a.level == b.level, CKKS_EINVAL, "HMult operands at different levels");
+    CK_CHECK(a.level >= 1, CKKS_ELEVEL, "cannot rescale a level-0 ciphertext");
+    c->ops["hmult"]++;
+    const int l = a.level, nl = l + 1;
+    const size_t n = c->n;
+    DevBuf d(3 * (size_t)nl * n, c->stream);       // d0, d1, d2
+    u64* d0 = d.ptr;
+    u64* d1 = d.ptr + (size_t)nl * n;
+    u64* d2 = d.ptr + 2 * (size_t)nl * n;
+    kern::mul(c, a.c0(), b.c0(), d0, nl, c->d_iota, nl);
+    kern::mul(c, a.c0(), b.c1(), d1, nl, c->d_iota, nl);
+    kern::mul_acc(c, a.c1(), b.c0(), d1, nl, c->d_iota, nl);
+    kern::mul(c, a.c1(), b.c1(), d2, nl, c->d_iota, nl);
+    int ndig = 0;
+    DevBuf D = mod_up(c, d2, l, &ndig);
+    DevBuf acc(2 * ((size_t)nl + c->np) * n, c->stream);
+    key_switch_inner(c, keys, D.ptr, ndig, l, 0, 1, acc.ptr, false);
+    lift_p(c, d0, acc.ptr, l);
+    ckks_ct o = new_ct(c, l - 1, a.scale * b.scale / (double)c->q[l]);
+    mod_down_rescale(c, acc.ptr, l, o.buf.ptr);
+    return o;
+}
+
+// ---------------------------------------------------------------- BSGS -----
+// sum over inputs t and giant steps g of rot_{R_g}(sum_b pt_{g,b} (*) rot_{step b}(in_t)).
+// Baby steps share one ModUp per input.  The giant-step rotations' key switches are summed
+// over Q_l u P together with P times the parts that need none, and brought down once:
+// ModDown, or ModDown fused with the rescale when rescale_out is set.
+ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins,
+                   const std::vector<const ckks_ptset*>& pss, bool rescale_out) {
+    ckks_ctx* c = ins[0]->ctx;
+    const int l = ins[0]->level, nl = l + 1;
+    const size_t n = c->n, next = (size_t)nl + c->np;
     const long long m = c->n / 2;
-    std::set<int> used;
-    for (const auto& kv : ps.pts) used.insert(kv.first.second);
-    std::vector<int> used_b(used.begin(), used.end());
-    std::vector<long long> steps;
-    for (int b : used_b) steps.push_back(((long long)ps.step * b) % m);
-    std::vector<ckks_ct> baby = rotate_hoisted(keys, a, steps);
-    std::map<int, int> bidx;
-    for (size_t i = 0; i < used_b.size(); ++i) bidx[used_b[i]] = (int)i;
-    ckks_ct out;
-    bool have = false;
-    for (int g = 0; g < ps.G(); ++g) {
+    DevBuf acc;
+    bool have_acc = false, have_plain = false;
+    ckks_ct plain;
+    for (size_t t = 0; t < ins.size(); ++t) {
+        const ckks_ct& a = *ins[t];
+        const ckks_ptset& ps = *pss[t];
+        CK_CHECK(a.level == ps.level && a.level == l, CKKS_EINVAL, "ciphertext level differs from the plaintext set's");
+        CK_CHECK(!ps.pts.empty(), CKKS_EINVAL, "empty plaintext set");
+        std::set<int> used;
+        for (const auto& kv : ps.pts) used.insert(kv.first.second);
+        std::vector<int> used_b(used.begin(), used.end());
+        std::vector<long long> steps;
+        for (int b : used_b) steps.push_back(((long long)ps.step * b) % m);
+        std::vector<ckks_ct> baby = rotate_hoisted(keys, a, steps);
+        std::map<int, int> bidx;
+        for (size_t i = 0; i < used_b.size(); ++i) bidx[used_b[i]] = (int)i;
+        for (int g = 0; g < ps.G(); ++g) {
         kern::BsgsTerms terms;
         terms.n = 0;
         double sc = 0;
@@ -604,15 +742,47 @@ ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps) {
         ckks_ct inner = new_ct(c, a.level, sc);
         kern::bsgs_inner(c, terms, inner.buf.ptr, a.level + 1);
         const long long R = (((long long)ps.a0 + (long long)ps.step * g * ps.B) % m + m) % m;
-        if (R) inner = rotate(keys, inner, R);
-        if (!have) {
-            out = std::move(inner);
-            have = true;
+        if (R) {
+            const u64 gal = galois_of_step(c, R);
+            c->ops["hrot"]++;
+            int ndig = 0;
+            DevBuf D = mod_up(c, inner.c1(), l, &ndig);
+            if (!have_acc) acc = DevBuf(2 * next * n, c->stream);
+            key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, acc.ptr, have_acc);
+            have_acc = true;
+            if (!have_plain) {
+                plain = new_ct(c, l, inner.scale);
+                kern::automorph(c, inner.c0(), plain.c0(), nl, gal);
+                CUDA_CHECK(cudaMemsetAsync(plain.c1(), 0, (size_t)nl * n * 8, c->stream));
+                have_plain = true;
+            } else {
+                DevBuf tmp((size_t)nl * n, c->stream);
+                kern::automorph(c, inner.c0(), tmp.ptr, nl, gal);
+                kern::add(c, plain.c0(), tmp.ptr, plain.c0(), nl, c->d_iota, nl);
+            }
+        } else if (!have_plain) {
+            plain = std::move(inner);
+            have_plain = true;
         } else {
-            kern::add(c, out.buf.ptr, inner.buf.ptr, out.buf.ptr, 2 * (out.level + 1), c->d_iota, out.level + 1);
+            kern::add(c, plain.buf.ptr, inner.buf.ptr, plain.buf.ptr, 2 * nl, c->d_iota, nl);
+        }
         }
     }
-    return out;
+    CK_CHECK(have_plain, CKKS_EINVAL, "empty plaintext set");
+    if (!have_acc) return rescale_out ? rescale(plain) : std::move(plain);
+    lift_p(c, plain.buf.ptr, acc.ptr, l);
+    if (rescale_out) {
+        ckks_ct o = new_ct(c, l - 1, plain.scale / (double)c->q[l]);
+        mod_down_rescale(c, acc.ptr, l, o.buf.ptr);
+        return o;
+    }
+    ckks_ct o = new_ct(c, l, plain.scale);
+    mod_down(c, acc.ptr, l, o.c0(), o.c1());
+    return o;
+}
+
+ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps, bool rescale_out) {
+    return bsgs_multi(keys, {&a}, {&ps}, rescale_out);
 }
 
 // ------------------------------------------------ Chebyshev / EvalMod -----
@@ -651,7 +821,7 @@ struct ChebPowers {
         need(b);
         if (a != b) need(b - a);
         const int m = prod_level(T.at(a).ctx, std::min(T.at(a).level, T.at(b).level));
-        ckks_ct t = rescale(mul_relin(*keys, at(a, m), at(b, m)));
+        ckks_ct t = mul_relin_rescale(*keys, at(a, m), at(b, m));
         t = add(t, t);
         t = (a == b) ? add_const(t, -1.0) : sub(t, at(b - a, m - 1));
         T[k] = std::move(t);
@@ -768,7 +938,7 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
             }
         } else {
             const int lev = prod_level(ctx, std::min(Q.ct.level, Tn.level));
-            prod = rescale(mul_relin(keys, level_down(Q.ct, lev), pw.at(n, lev)));
+            prod = mul_relin_rescale(keys, level_down(Q.ct, lev), pw.at(n, lev));
             hp = true;
         }
         PolyVal out;
@@ -796,13 +966,13 @@ ckks_ct eval_relu(const ckks_keys& keys, const ckks_ct& x, const std::vector<std
     for (size_t i = 1; i < stages.size(); ++i) y = cheb_eval(keys, y, stages[i]);
     const int lev = prod_level(x.ctx, y.level);
     CK_CHECK(lev >= 1, CKKS_ELEVEL, "not enough levels for the final product");
-    return rescale(mul_relin(keys, level_down(x, lev), level_down(y, lev)));
+    return mul_relin_rescale(keys, level_down(x, lev), level_down(y, lev));
 }
 
 ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r) {
     ckks_ct y = cheb_eval(keys, x, coeffs);
     for (int i = 0; i < r; ++i) {
-        y = rescale(mul_relin(keys, y, y));
+        y = mul_relin_rescale(keys, y, y);
         y = add(y, y);
         y = add_const(y, -1.0);
     }
@@ -813,7 +983,7 @@ void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, c
     ckks_ctx* c = ct0.ctx;
     ckks_ct x = mod_raise(ct0);
     x.scale = bt.s_raise;
-    for (const auto& ps : bt.ctos) x = rescale(bsgs(keys, x, *ps));
+    for (const auto& ps : bt.ctos) x = bsgs(keys, x, *ps, true);
     ckks_ct cj = conjugate(keys, x);
     ckks_ct re = add(x, cj);
     ckks_ct im = imult(sub(cj, x));
@@ -827,8 +997,8 @@ void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, c
 
 // recombined slot ciphertext -> [Alg. 2 decomposition] -> HMatmul(S_{l'<-1})
 static ckks_ct tail(const ckks_keys& keys, const ckks_boot& bt, ckks_ct y) {
-    if (bt.decomp) y = rescale(bsgs(keys, y, *bt.decomp));
-    for (const auto& ps : bt.stoc) y = rescale(bsgs(keys, y, *ps));
+    if (bt.decomp) y = bsgs(keys, y, *bt.decomp, true);
+    for (const auto& ps : bt.stoc) y = bsgs(keys, y, *ps, true);
     return y;
 }
 
@@ -838,7 +1008,7 @@ static ckks_ct boot_tail(const ckks_keys& keys, const ckks_boot& bt, const ckks_
 // padding), PMult(ct_Im, mask_Im) is the zero ciphertext whatever ct_Im holds, so the Im
 // branch (its scale drop and EvalMod) is skipped; the output is bit-identical.
 ckks_ct block(const ckks_keys& keys, const ckks_boot& bt, const ckks_ptset& conv, const ckks_ct& in) {
-    return boot_tail(keys, bt, rescale(bsgs(keys, in, conv)));
+    return boot_tail(keys, bt, bsgs(keys, in, conv, true));
 }
 
 // conv over several input ciphertexts (BSGS each, HAdd, one rescale), then the block's
@@ -846,9 +1016,7 @@ ckks_ct block(const ckks_keys& keys, const ckks_boot& bt, const ckks_ptset& conv
 // C_in > C block matrix-vector product (Sec. 3.3.3).
 ckks_ct block_multi(const ckks_keys& keys, const ckks_boot& bt, const std::vector<const ckks_ptset*>& convs,
                     const std::vector<const ckks_ct*>& ins) {
-    ckks_ct x = bsgs(keys, *ins[0], *convs[0]);
-    for (size_t t = 1; t < ins.size(); ++t) x = add(x, bsgs(keys, *ins[t], *convs[t]));
-    return boot_tail(keys, bt, rescale(x));
+    return boot_tail(keys, bt, bsgs_multi(keys, ins, convs, true));
 }
 
 // Alg. 2 without HActivation: per input, the stride-2 tail of the previous block (masks,
@@ -874,7 +1042,7 @@ static ckks_ct boot_tail(const ckks_keys& keys, const ckks_boot& bt, const ckks_
     }
     ckks_ct x = mod_raise(x0);
     x.scale = bt.s_raise;
-    for (const auto& ps : bt.ctos) x = rescale(bsgs(keys, x, *ps));
+    for (const auto& ps : bt.ctos) x = bsgs(keys, x, *ps, true);
     ckks_ct re = add(x, conjugate(keys, x));
     re = rescale(mul_int(re, bt.c_drop));
     re.scale = c->delta[re.level];

@@ -26,7 +26,10 @@ std::vector<ckks_ct> rotate_hoisted(const ckks_keys& keys, const ckks_ct& a, con
 ckks_ct rotate(const ckks_keys& keys, const ckks_ct& a, long long r);
 ckks_ct conjugate(const ckks_keys& keys, const ckks_ct& a);
 ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b);
-ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps);
+ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b);
+ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps, bool rescale_out = false);
+ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins,
+                   const std::vector<const ckks_ptset*>& pss, bool rescale_out);
 ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs);
 ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r);
 ckks_ct eval_relu(const ckks_keys& keys, const ckks_ct& x, const std::vector<std::vector<double>>& stages);
