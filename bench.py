@@ -47,7 +47,7 @@ def parse_args():
                          "serve: the serving loop under Poisson arrivals")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--variant", type=int, default=-1, help="--kernel ntt: time one launch variant only")
-    ap.add_argument("--kernel", default=None, choices=["ntt"],
+    ap.add_argument("--kernel", default=None, choices=["ntt", "ks"],
                     help="time one kernel family alone on a buffer larger than L2 (for profiling)")
     return ap.parse_args()
 
@@ -618,10 +618,41 @@ def run_kernel_ntt(args):
     print(json.dumps({"kernel": "ntt", "limbs": nl, "N": ctx.n, "roundtrip_exact": ok, "per_variant": res}))
 
 
+def run_kernel_ks(args):
+    """hoisted rotations of one config-2 ciphertext at the top level (ModUp, key-switch inner
+    product, ModDown): per-kernel times of the key switch alone, a few hundred MB on the device"""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    d = WL.PARAMS[CONFIG]
+    ctx = K.ckks_ctx_create(d, 1, torch.cuda.current_stream().cuda_stream)
+    q, p, _, delta = K.ckks_ctx_info(ctx)
+    L = len(q) - 1
+    steps = [1, 2, 3, 4]
+    keys = K.ckks_keygen(ctx, steps, False)
+    ct = K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, WL.slots(1, ctx.n // 2, 0.5), L, delta[L]), 1)
+    for _ in range(args.warmup):
+        K.ckks_rotate_hoisted(ctx, keys, ct, steps)
+    K.ckks_sync(ctx)
+    K.ckks_ctx_reset_counters(ctx)
+    K.ckks_ctx_set_timing(ctx, 1)
+    for _ in range(args.steps):
+        K.ckks_rotate_hoisted(ctx, keys, ct, steps)
+    K.ckks_ctx_set_timing(ctx, 0)
+    st = K.ckks_ctx_kernel_stats(ctx)
+    res = {k: {"launches": v["launches"], "us_per_launch": round(1e3 * v["ms"] / v["launches"], 2),
+               "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)} for k, v in st.items()}
+    print(json.dumps({"kernel": "keyswitch", "level": L, "rotations_per_step": len(steps), "N": ctx.n,
+                      "per_kernel": res}))
+
+
 if __name__ == "__main__":
     a = parse_args()
     if a.kernel == "ntt":
         run_kernel_ntt(a)
+    elif a.kernel == "ks":
+        run_kernel_ks(a)
     elif a.workload == "ds" and a.impl == "ours":
         run_ds(a)
     elif a.workload == "serve" and a.impl == "ours":

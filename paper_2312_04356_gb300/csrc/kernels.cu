@@ -89,6 +89,21 @@ inline dim3 ew_grid(int n, int nlimbs) {
 
 #define EW_LOOP(n) for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (n); j += gridDim.x * blockDim.x)
 
+// grid of the one-thread-per-V-words kernels
+inline dim3 ewv_grid(int n, int nlimbs, int v) {
+    int x = n / (EW_THREADS * v);
+    if (x < 1) x = 1;
+    return dim3(x, nlimbs);
+}
+inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+#define EWV_LAUNCH(K, vec, nl, ...)                                                          \
+    do {                                                                                     \
+        if (vec)                                                                             \
+            K<2><<<ewv_grid(c->n, (nl), 2), EW_THREADS, 0, c->stream>>>(__VA_ARGS__);        \
+        else                                                                                 \
+            K<1><<<ewv_grid(c->n, (nl), 1), EW_THREADS, 0, c->stream>>>(__VA_ARGS__);        \
+    } while (0)
+
 // ------------------------------------------------------------------ NTT ----
 // One pass covers `c` consecutive butterfly stages s0..s0+c-1 (stage s: 2^s groups,
 // stride t = N >> (s+1)).  Over those stages only index bits log2(T1)..log2(T0) move
@@ -403,36 +418,96 @@ void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int 
 }
 
 // ----------------------------------------------------------- elementwise ----
+// One thread per V consecutive words of a limb (V = 2: 16-byte loads and stores, used when
+// every pointer of the launch is 16-byte aligned); all operands are loaded before any
+// store, so in-place calls (o == a) are safe.
+template <int V>
+__device__ __forceinline__ void ldv(const u64* p, u64 (&r)[V]) {
+    if constexpr (V == 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p);
+        r[0] = t.x;
+        r[1] = t.y;
+    } else {
+        r[0] = p[0];
+    }
+}
+template <int V>
+__device__ __forceinline__ void stv(u64* p, const u64 (&r)[V]) {
+    if constexpr (V == 2)
+        *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(r[0], r[1]);
+    else
+        p[0] = r[0];
+}
+#define EWV_BEGIN(n)                                                \
+    const int j = V * (blockIdx.x * blockDim.x + threadIdx.x);      \
+    if (j >= (n)) return;
+
+template <int V>
 __global__ void k_add(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
     const int limb = blockIdx.y;
     const u64 q = P[ids[limb % lpp]].m.q;
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = add_mod(a[off + j], b[off + j], q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V], y[V];
+    ldv<V>(a + off + j, x);
+    ldv<V>(b + off + j, y);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = add_mod(x[v], y[v], q);
+    stv<V>(o + off + j, x);
 }
+template <int V>
 __global__ void k_sub(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
     const int limb = blockIdx.y;
     const u64 q = P[ids[limb % lpp]].m.q;
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = sub_mod(a[off + j], b[off + j], q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V], y[V];
+    ldv<V>(a + off + j, x);
+    ldv<V>(b + off + j, y);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = sub_mod(x[v], y[v], q);
+    stv<V>(o + off + j, x);
 }
+template <int V>
 __global__ void k_neg(const u64* a, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
     const int limb = blockIdx.y;
     const u64 q = P[ids[limb % lpp]].m.q;
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = neg_mod(a[off + j], q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V];
+    ldv<V>(a + off + j, x);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = neg_mod(x[v], q);
+    stv<V>(o + off + j, x);
 }
+template <int V>
 __global__ void k_mul(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
     const int limb = blockIdx.y;
     const DevMod m = P[ids[limb % lpp]].m;
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = mul_mod(a[off + j], b[off + j], m);
+    EWV_BEGIN(1 << logn)
+    u64 x[V], y[V];
+    ldv<V>(a + off + j, x);
+    ldv<V>(b + off + j, y);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = mul_mod(x[v], y[v], m);
+    stv<V>(o + off + j, x);
 }
+template <int V>
 __global__ void k_mul_acc(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
     const int limb = blockIdx.y;
     const DevMod m = P[ids[limb % lpp]].m;
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = add_mod(o[off + j], mul_mod(a[off + j], b[off + j], m), m.q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V], y[V], z[V];
+    ldv<V>(a + off + j, x);
+    ldv<V>(b + off + j, y);
+    ldv<V>(o + off + j, z);
+#pragma unroll
+    for (int v = 0; v < V; ++v) z[v] = add_mod(z[v], mul_mod(x[v], y[v], m), m.q);
+    stv<V>(o + off + j, z);
 }
+template <int V>
 __global__ void k_mul_scalar(const u64* a, const u64* s, const u64* sp, u64* o, const DevPrime* P, const int* ids,
                              int lpp, int logn) {
     const int limb = blockIdx.y;
@@ -440,9 +515,15 @@ __global__ void k_mul_scalar(const u64* a, const u64* s, const u64* sp, u64* o, 
     const u64 q = P[ids[r]].m.q;
     const u64 w = s[r], wp = sp[r];
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = mul_shoup(a[off + j], w, wp, q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V];
+    ldv<V>(a + off + j, x);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = mul_shoup(x[v], w, wp, q);
+    stv<V>(o + off + j, x);
 }
 // per-limb scalars passed by value (no host-to-device copy, so the launch can be captured)
+template <int V>
 __global__ void k_mul_scalar_v(const u64* a, ScalarVec sv, u64* o, const DevPrime* P, const int* ids, int lpp,
                                int logn) {
     const int limb = blockIdx.y;
@@ -450,22 +531,39 @@ __global__ void k_mul_scalar_v(const u64* a, ScalarVec sv, u64* o, const DevPrim
     const u64 q = P[ids[r]].m.q;
     const u64 w = sv.v[r], wp = sv.vp[r];
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = mul_shoup(a[off + j], w, wp, q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V];
+    ldv<V>(a + off + j, x);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = mul_shoup(x[v], w, wp, q);
+    stv<V>(o + off + j, x);
 }
+template <int V>
 __global__ void k_add_scalar_v(u64* a, ScalarVec sv, const DevPrime* P, const int* ids, int lpp, int logn) {
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
     const u64 c = sv.v[r];
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) a[off + j] = add_mod(a[off + j], c, q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V];
+    ldv<V>(a + off + j, x);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = add_mod(x[v], c, q);
+    stv<V>(a + off + j, x);
 }
-__global__ void k_add_scalar(u64* a, const u64* v, const DevPrime* P, const int* ids, int logn) {
+template <int V>
+__global__ void k_add_scalar(u64* a, const u64* vals, const DevPrime* P, const int* ids, int logn) {
     const int limb = blockIdx.y;
     const u64 q = P[ids[limb]].m.q;
-    const u64 c = v[limb];
+    const u64 c = vals[limb];
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) a[off + j] = add_mod(a[off + j], c, q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V];
+    ldv<V>(a + off + j, x);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = add_mod(x[v], c, q);
+    stv<V>(a + off + j, x);
 }
 __global__ void k_small_to_rns(const int64_t* v, u64* o, const DevPrime* P, const int* ids, int logn) {
     const int limb = blockIdx.y;
@@ -499,12 +597,19 @@ __global__ void k_imult(const u64* a, u64* o, const DevPrime* P, const int* ids,
         o[off + j] = (r & 1) ? neg_mod(v, q) : v;
     }
 }
+template <int V>
 __global__ void k_lift_centred(const u64* src, u64 qs, u64* o, const DevPrime* P, const int* ids, int logn) {
     const int limb = blockIdx.y;
     const DevMod t = P[ids[limb]].m;
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = centred_to(src[j], qs, t);
+    EWV_BEGIN(1 << logn)
+    u64 x[V];
+    ldv<V>(src + j, x);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = centred_to(x[v], qs, t);
+    stv<V>(o + off + j, x);
 }
+template <int V>
 __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const u64* sp, u64* o,
                                  const DevPrime* P, const int* ids, int lpp, int logn) {
     const int limb = blockIdx.y;
@@ -512,7 +617,13 @@ __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const
     const u64 q = P[ids[r]].m.q;
     const u64 w = s[r], wp = sp[r];
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = mul_shoup(sub_mod(a[off + j], b[off + j], q), w, wp, q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V], y[V];
+    ldv<V>(a + off + j, x);
+    ldv<V>(b + off + j, y);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = mul_shoup(sub_mod(x[v], y[v], q), w, wp, q);
+    stv<V>(o + off + j, x);
 }
 
 // ------------------------------------------------- BSGS inner products ----
@@ -521,22 +632,31 @@ __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const
 __device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P) {
     return add_mod(mul_shoup(hi, P.r64, P.r64p, P.m.q), reduce64(lo, P.m), P.m.q);
 }
+template <int V>
 __global__ void k_bsgs_inner(kern::BsgsTerms T, u64* __restrict__ o, const DevPrime* __restrict__ primes, int nl,
                              int logn) {
     const int limb = blockIdx.y;           // 0 .. 2 nl - 1, polynomial-major
     const int r = limb % nl;
     const DevPrime P = primes[r];
     const size_t offa = (size_t)limb << logn, offp = (size_t)r << logn;
-    EW_LOOP(1 << logn) {
-        u64 lo = 0, hi = 0;
-        for (int t = 0; t < T.n; ++t) {
-            const u64 x = T.a[t][offa + j], y = T.p[t][offp + j];
-            const u64 pl = x * y, ph = __umul64hi(x, y);
-            lo += pl;
-            hi += ph + (lo < pl ? 1ull : 0ull);
+    EWV_BEGIN(1 << logn)
+    u64 lo[V], hi[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) lo[v] = hi[v] = 0;
+    for (int t = 0; t < T.n; ++t) {
+        u64 x[V], y[V];
+        ldv<V>(T.a[t] + offa + j, x);
+        ldv<V>(T.p[t] + offp + j, y);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const u64 pl = x[v] * y[v], ph = __umul64hi(x[v], y[v]);
+            lo[v] += pl;
+            hi[v] += ph + (lo[v] < pl ? 1ull : 0ull);
         }
-        o[offa + j] = reduce128_lazy(hi, lo, P);
     }
+#pragma unroll
+    for (int v = 0; v < V; ++v) lo[v] = reduce128_lazy(hi[v], lo[v], P);
+    stv<V>(o + offa + j, lo);
 }
 
 // ------------------------------------------------------- base conversion ----
@@ -551,6 +671,9 @@ __global__ void k_bsgs_inner(kern::BsgsTerms T, u64* __restrict__ o, const DevPr
 // CONV_OUT independent accumulations interleave.
 constexpr int MAX_CONV_IN = 16;
 constexpr int CONV_OUT = 8;
+// MAXIN: compile-time bound on the jobs' input counts (4, 8 or 16), so that the unrolled
+// input loops carry no predicated-off iterations for the common 7- and 8-limb conversions.
+template <int MAXIN>
 __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn) {
     __shared__ u64 s_qi[MAX_CONV_IN], s_qinv[MAX_CONV_IN], s_qinvp[MAX_CONV_IN];
     __shared__ u64 s_c[CONV_OUT][MAX_CONV_IN];
@@ -591,15 +714,15 @@ __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const De
     const int j = blockIdx.x * blockDim.x + tid;
     if (j >= (1 << logn)) return;
     const size_t n = (size_t)1 << logn;
-    u64 xh[MAX_CONV_IN];
+    u64 xh[MAXIN];
 #pragma unroll
-    for (int i = 0; i < MAX_CONV_IN; ++i)
+    for (int i = 0; i < MAXIN; ++i)
         if (i < nin) xh[i] = mul_shoup(in[i * n + j], s_qinv[i], s_qinvp[i], s_qi[i]);
     u64 lo[CONV_OUT], hi[CONV_OUT];
 #pragma unroll
     for (int m = 0; m < CONV_OUT; ++m) lo[m] = hi[m] = 0;
 #pragma unroll
-    for (int i = 0; i < MAX_CONV_IN; ++i) {
+    for (int i = 0; i < MAXIN; ++i) {
         if (i < nin) {
 #pragma unroll
             for (int m = 0; m < CONV_OUT; ++m) {
@@ -612,7 +735,9 @@ __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const De
     }
     if (exact) {
         double f = 0.0;
-        for (int i = 0; i < nin; ++i) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xh[i]), s_invq[i]));
+#pragma unroll
+        for (int i = 0; i < MAXIN; ++i)
+            if (i < nin) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xh[i]), s_invq[i]));
         const u64 v = (u64)__double2ll_rn(f);
 #pragma unroll
         for (int m = 0; m < CONV_OUT; ++m) {
@@ -627,7 +752,7 @@ __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const De
 }
 
 // ---------------------------------------------------- key-switch product ----
-template <bool ACC>
+template <bool ACC, int V>
 __global__ void k_ks_inner(const u64* __restrict__ D, int ndig, int next, const int* __restrict__ ext_ids,
                            const u64* __restrict__ kb, const u64* __restrict__ ka, u64* __restrict__ ob,
                            u64* __restrict__ oa, const DevPrime* __restrict__ P, int logn, u64 g, size_t kstride) {
@@ -635,25 +760,42 @@ __global__ void k_ks_inner(const u64* __restrict__ D, int ndig, int next, const 
     const int id = ext_ids[e];
     const DevMod m = P[id].m;
     const size_t n = (size_t)1 << logn;
-    EW_LOOP(1 << logn) {
-        const unsigned src = g == 1 ? (unsigned)j : galois_src(j, g, logn);
-        u64 accb = 0, acca = 0;
-        for (int d = 0; d < ndig; ++d) {
-            const u64 x = D[((size_t)d * next + e) * n + src];
-            const size_t kk = d * kstride + (size_t)id * n + j;
-            accb = add_mod(accb, mul_mod(x, kb[kk], m), m.q);
-            acca = add_mod(acca, mul_mod(x, ka[kk], m), m.q);
+    EWV_BEGIN(1 << logn)
+    unsigned src[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) src[v] = g == 1 ? (unsigned)(j + v) : galois_src(j + v, g, logn);
+    u64 accb[V], acca[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) accb[v] = acca[v] = 0;
+    for (int d = 0; d < ndig; ++d) {
+        const u64* Dd = D + ((size_t)d * next + e) * n;
+        const size_t kk = d * kstride + (size_t)id * n + j;
+        u64 yb[V], ya[V];
+        ldv<V>(kb + kk, yb);
+        ldv<V>(ka + kk, ya);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const u64 x = Dd[src[v]];
+            accb[v] = add_mod(accb[v], mul_mod(x, yb[v], m), m.q);
+            acca[v] = add_mod(acca[v], mul_mod(x, ya[v], m), m.q);
         }
-        if (ACC) {
-            accb = add_mod(accb, ob[(size_t)e * n + j], m.q);
-            acca = add_mod(acca, oa[(size_t)e * n + j], m.q);
-        }
-        ob[(size_t)e * n + j] = accb;
-        oa[(size_t)e * n + j] = acca;
     }
+    if (ACC) {
+        u64 pb[V], pa[V];
+        ldv<V>(ob + (size_t)e * n + j, pb);
+        ldv<V>(oa + (size_t)e * n + j, pa);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            accb[v] = add_mod(accb[v], pb[v], m.q);
+            acca[v] = add_mod(acca[v], pa[v], m.q);
+        }
+    }
+    stv<V>(ob + (size_t)e * n + j, accb);
+    stv<V>(oa + (size_t)e * n + j, acca);
 }
 
 // o += a * s[limb % lpp] (Shoup pairs s, sp)
+template <int V>
 __global__ void k_mul_scalar_acc(const u64* a, const u64* s, const u64* sp, u64* o, const DevPrime* P, const int* ids,
                                  int lpp, int logn) {
     const int limb = blockIdx.y;
@@ -661,7 +803,13 @@ __global__ void k_mul_scalar_acc(const u64* a, const u64* s, const u64* sp, u64*
     const u64 q = P[ids[r]].m.q;
     const u64 w = s[r], wp = sp[r];
     const size_t off = (size_t)limb << logn;
-    EW_LOOP(1 << logn) o[off + j] = add_mod(o[off + j], mul_shoup(a[off + j], w, wp, q), q);
+    EWV_BEGIN(1 << logn)
+    u64 x[V], z[V];
+    ldv<V>(a + off + j, x);
+    ldv<V>(o + off + j, z);
+#pragma unroll
+    for (int v = 0; v < V; ++v) z[v] = add_mod(z[v], mul_shoup(x[v], w, wp, q), q);
+    stv<V>(o + off + j, z);
 }
 
 // ------------------------------------------------------------ sampling ----
@@ -775,7 +923,9 @@ void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, 
 void bsgs_inner(const ckks_ctx* c, const BsgsTerms& t, u64* o, int nl) {
     CK_CHECK(t.n >= 1 && t.n <= BsgsTerms::MAX, CKKS_EINVAL, "1..16 BSGS terms per kernel");
     { KTimer kt_(c, "bsgs_inner", (2.0 * t.n + t.n + 2.0) * nl * c->n * 8.0);
-    k_bsgs_inner<<<ew_grid(c->n, 2 * nl), EW_THREADS, 0, c->stream>>>(t, o, c->d_primes, nl, c->logn);
+    bool vec = al16(o);
+    for (int i = 0; i < t.n; ++i) vec = vec && al16(t.a[i]) && al16(t.p[i]);
+    EWV_LAUNCH(k_bsgs_inner, vec, 2 * nl, t, o, c->d_primes, nl, c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -799,35 +949,35 @@ void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "add", 3.0 * (double)nl * c->n * 8.0);
-    k_add<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_add, al16(a) && al16(b) && al16(o), nl, a, b, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
 void sub(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "sub", 3.0 * (double)nl * c->n * 8.0);
-    k_sub<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_sub, al16(a) && al16(b) && al16(o), nl, a, b, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
 void neg(const ckks_ctx* c, const u64* a, u64* o, int nl, const int* ids, int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "neg", 2.0 * (double)nl * c->n * 8.0);
-    k_neg<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_neg, al16(a) && al16(o), nl, a, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
 void mul(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "mul", 3.0 * (double)nl * c->n * 8.0);
-    k_mul<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_mul, al16(a) && al16(b) && al16(o), nl, a, b, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
 void mul_acc(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "mul_acc", 4.0 * (double)nl * c->n * 8.0);
-    k_mul_acc<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_mul_acc, al16(a) && al16(b) && al16(o), nl, a, b, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -835,7 +985,7 @@ void mul_scalar(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u6
                 int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "mul_scalar", 2.0 * (double)nl * c->n * 8.0);
-    k_mul_scalar<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, s, sp, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_mul_scalar, al16(a) && al16(o), nl, a, s, sp, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -843,7 +993,7 @@ void mul_scalar_v(const ckks_ctx* c, const u64* a, const ScalarVec& sv, u64* o, 
     if (nl <= 0) return;
     CK_CHECK(lpp <= ScalarVec::MAX, CKKS_EINVAL, "too many limbs for a by-value scalar vector");
     { KTimer kt_(c, "mul_scalar", 2.0 * (double)nl * c->n * 8.0);
-    k_mul_scalar_v<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, sv, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_mul_scalar_v, al16(a) && al16(o), nl, a, sv, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -851,14 +1001,14 @@ void add_scalar_v(const ckks_ctx* c, u64* a, const ScalarVec& sv, int nl, const 
     if (nl <= 0) return;
     CK_CHECK(lpp <= ScalarVec::MAX, CKKS_EINVAL, "too many limbs for a by-value scalar vector");
     { KTimer kt_(c, "add_scalar", 2.0 * (double)nl * c->n * 8.0);
-    k_add_scalar_v<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, sv, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_add_scalar_v, al16(a), nl, a, sv, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
 void add_const_term(const ckks_ctx* c, u64* a, const u64* v, int nl, const int* ids) {
     if (nl <= 0) return;
     { KTimer kt_(c, "add_scalar", 2.0 * (double)nl * c->n * 8.0);
-    k_add_scalar<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, v, c->d_primes, ids, c->logn);
+    EWV_LAUNCH(k_add_scalar, al16(a), nl, a, v, c->d_primes, ids, c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -886,8 +1036,7 @@ void imult(const ckks_ctx* c, const u64* a, u64* o, int nl, const int* ids, int 
 void lift_centred(const ckks_ctx* c, const u64* src, int src_id, u64* o, int nl, const int* ids) {
     if (nl <= 0) return;
     { KTimer kt_(c, "lift_centred", (nl + 1.0) * c->n * 8.0);
-    k_lift_centred<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(src, c->mod_of[src_id], o, c->d_primes, ids,
-                                                                     c->logn);
+    EWV_LAUNCH(k_lift_centred, al16(src) && al16(o), nl, src, c->mod_of[src_id], o, c->d_primes, ids, c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -895,8 +1044,7 @@ void sub_mul_scalar(const ckks_ctx* c, const u64* a, const u64* b, const u64* s,
                     const int* ids, int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "sub_mul_scalar", 3.0 * (double)nl * c->n * 8.0);
-    k_sub_mul_scalar<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, b, s, sp, o, c->d_primes, ids, lpp,
-                                                                       c->logn);
+    EWV_LAUNCH(k_sub_mul_scalar, al16(a) && al16(b) && al16(o), nl, a, b, s, sp, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -937,25 +1085,39 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly) {
         bytes += (double)npoly * (J.job[i].nin + J.job[i].nout) * c->n * 8.0;
     }
     if (groups == 0) return;
+    int maxin = 0;
+    for (int i = 0; i < J.n; ++i) maxin = std::max(maxin, J.job[i].nin);
     dim3 grid((c->n + 255) / 256, npoly, groups);
     { KTimer kt_(c, "base_convert", bytes);
-    k_base_convert<<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+    if (maxin <= 4)
+        k_base_convert<4><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+    else if (maxin <= 8)
+        k_base_convert<8><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+    else
+        k_base_convert<MAX_CONV_IN><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
     }
     LAUNCH_CHECK();
 }
 
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
               const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate) {
+    const bool vec = al16(kb) && al16(ka) && al16(ob) && al16(oa);
     if (accumulate) {
         KTimer kt_(c, "ks_inner", (3.0 * ndig + 4.0) * next * c->n * 8.0);
-        k_ks_inner<true><<<ew_grid(c->n, next), EW_THREADS, 0, c->stream>>>(D, ndig, next, ext_ids, kb, ka, ob, oa,
-                                                                         c->d_primes, c->logn, g,
-                                                                         (size_t)c->nall << c->logn);
+        if (vec)
+            k_ks_inner<true, 2><<<ewv_grid(c->n, next, 2), EW_THREADS, 0, c->stream>>>(
+                D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes, c->logn, g, (size_t)c->nall << c->logn);
+        else
+            k_ks_inner<true, 1><<<ewv_grid(c->n, next, 1), EW_THREADS, 0, c->stream>>>(
+                D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes, c->logn, g, (size_t)c->nall << c->logn);
     } else {
         KTimer kt_(c, "ks_inner", (3.0 * ndig + 2.0) * next * c->n * 8.0);
-        k_ks_inner<false><<<ew_grid(c->n, next), EW_THREADS, 0, c->stream>>>(D, ndig, next, ext_ids, kb, ka, ob, oa,
-                                                                          c->d_primes, c->logn, g,
-                                                                          (size_t)c->nall << c->logn);
+        if (vec)
+            k_ks_inner<false, 2><<<ewv_grid(c->n, next, 2), EW_THREADS, 0, c->stream>>>(
+                D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes, c->logn, g, (size_t)c->nall << c->logn);
+        else
+            k_ks_inner<false, 1><<<ewv_grid(c->n, next, 1), EW_THREADS, 0, c->stream>>>(
+                D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes, c->logn, g, (size_t)c->nall << c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -963,7 +1125,7 @@ void mul_scalar_acc(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp
                     int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "mul_scalar_acc", 3.0 * (double)nl * c->n * 8.0);
-    k_mul_scalar_acc<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, s, sp, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_mul_scalar_acc, al16(a) && al16(o), nl, a, s, sp, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
