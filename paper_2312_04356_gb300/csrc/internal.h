@@ -74,6 +74,7 @@ struct DevBuf {
 struct ckks_ctx {
     ckks_params P;
     int logn = 0, n = 0, nq = 0, L = 0, alpha = 0, np = 0, nall = 0, n_circuit = 0;
+    bool mods_below_2_60 = false;    // every modulus < 2^60 (enables the split base conversion)
     std::vector<u64> q, p, psi;      // psi indexed by prime id
     std::vector<u64> mod_of;         // modulus by prime id
     std::vector<double> delta;

@@ -673,14 +673,19 @@ constexpr int MAX_CONV_IN = 16;
 constexpr int CONV_OUT = 8;
 // MAXIN: compile-time bound on the jobs' input counts (4, 8 or 16), so that the unrolled
 // input loops carry no predicated-off iterations for the common 7- and 8-limb conversions.
-template <int MAXIN>
-__global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn) {
+// SPLIT (every modulus below 2^60, MAXIN <= 8): x = xu 2^30 + xl, c = cu 2^30 + cl; the four
+// partial products (each < 2^60) go into three 64-bit sums by one 32x32->64 multiply-add
+// each (at most 16 terms per sum: no overflow); the 128-bit total ll + m 2^30 + hh 2^60 is
+// then reduced as in the general path.
+template <int MAXIN, bool SPLIT>
+__global__ void __launch_bounds__(256, 3) k_base_convert(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn) {
     __shared__ u64 s_qi[MAX_CONV_IN], s_qinv[MAX_CONV_IN], s_qinvp[MAX_CONV_IN];
     __shared__ u64 s_c[CONV_OUT][MAX_CONV_IN];
     __shared__ DevPrime s_pm[CONV_OUT];
     __shared__ int s_row[CONV_OUT];
     __shared__ double s_invq[MAX_CONV_IN];
     __shared__ u64 s_corr[CONV_OUT];
+    __shared__ uint2 s_c2[CONV_OUT][MAXIN];     // SPLIT: (c mod 2^30, c >> 30)
     // which job and output group this CTA serves
     int z = blockIdx.z, jb = 0;
     while (jb < J.n - 1 && z >= J.job[jb].ngroups) {
@@ -701,7 +706,9 @@ __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const De
     }
     if (tid < CONV_OUT * MAX_CONV_IN) {
         const int m = tid / MAX_CONV_IN, i = tid % MAX_CONV_IN;
-        s_c[m][i] = (m < mcount && i < nin) ? job.qmod[(size_t)(m0 + m) * nin + i] : 0;
+        const u64 c = (m < mcount && i < nin) ? job.qmod[(size_t)(m0 + m) * nin + i] : 0;
+        s_c[m][i] = c;
+        if (SPLIT && i < MAXIN) s_c2[m][i] = make_uint2((unsigned)(c & ((1ull << 30) - 1)), (unsigned)(c >> 30));
     }
     if (tid < mcount) {
         s_pm[tid] = P[job.out_ids[m0 + tid]];
@@ -719,17 +726,50 @@ __global__ void __launch_bounds__(256) k_base_convert(kern::ConvJobs J, const De
     for (int i = 0; i < MAXIN; ++i)
         if (i < nin) xh[i] = mul_shoup(in[i * n + j], s_qinv[i], s_qinvp[i], s_qi[i]);
     u64 lo[CONV_OUT], hi[CONV_OUT];
+    if (SPLIT) {
+        constexpr u64 M30 = (1ull << 30) - 1;
+        u64 ll[CONV_OUT], mm[CONV_OUT], hh[CONV_OUT];
 #pragma unroll
-    for (int m = 0; m < CONV_OUT; ++m) lo[m] = hi[m] = 0;
+        for (int m = 0; m < CONV_OUT; ++m) ll[m] = mm[m] = hh[m] = 0;
 #pragma unroll
-    for (int i = 0; i < MAXIN; ++i) {
-        if (i < nin) {
+        for (int i = 0; i < MAXIN; ++i) {
+            if (i < nin) {
+                const unsigned xl = (unsigned)(xh[i] & M30), xu = (unsigned)(xh[i] >> 30);
 #pragma unroll
-            for (int m = 0; m < CONV_OUT; ++m) {
-                const u64 c = s_c[m][i];
-                const u64 pl = xh[i] * c, ph = __umul64hi(xh[i], c);
-                lo[m] += pl;
-                hi[m] += ph + (lo[m] < pl ? 1ull : 0ull);
+                for (int m = 0; m < CONV_OUT; ++m) {
+                    const uint2 cc = s_c2[m][i];
+                    ll[m] += (u64)xl * cc.x;
+                    mm[m] += (u64)xl * cc.y;
+                    mm[m] += (u64)xu * cc.x;
+                    hh[m] += (u64)xu * cc.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < CONV_OUT; ++m) {
+            u64 l = ll[m], h = (mm[m] >> 34) + (hh[m] >> 4);
+            const u64 t1 = mm[m] << 30;
+            l += t1;
+            h += l < t1 ? 1ull : 0ull;
+            const u64 t2 = hh[m] << 60;
+            l += t2;
+            h += l < t2 ? 1ull : 0ull;
+            lo[m] = l;
+            hi[m] = h;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < CONV_OUT; ++m) lo[m] = hi[m] = 0;
+#pragma unroll
+        for (int i = 0; i < MAXIN; ++i) {
+            if (i < nin) {
+#pragma unroll
+                for (int m = 0; m < CONV_OUT; ++m) {
+                    const u64 c = s_c[m][i];
+                    const u64 pl = xh[i] * c, ph = __umul64hi(xh[i], c);
+                    lo[m] += pl;
+                    hi[m] += ph + (lo[m] < pl ? 1ull : 0ull);
+                }
             }
         }
     }
@@ -1090,11 +1130,13 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly) {
     dim3 grid((c->n + 255) / 256, npoly, groups);
     { KTimer kt_(c, "base_convert", bytes);
     if (maxin <= 4)
-        k_base_convert<4><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+        k_base_convert<4, false><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+    else if (maxin <= 8 && c->mods_below_2_60)
+        k_base_convert<8, true><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
     else if (maxin <= 8)
-        k_base_convert<8><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+        k_base_convert<8, false><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
     else
-        k_base_convert<MAX_CONV_IN><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+        k_base_convert<MAX_CONV_IN, false><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
     }
     LAUNCH_CHECK();
 }

@@ -219,6 +219,7 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
     build_chain(*P, c->q, c->p, c->delta);
     c->mod_of = c->q;
     c->mod_of.insert(c->mod_of.end(), c->p.begin(), c->p.end());
+    c->mods_below_2_60 = std::all_of(c->mod_of.begin(), c->mod_of.end(), [](u64 m) { return m < (1ull << 60); });
     const int n = c->n, logn = c->logn;
     // twiddle tables: per prime 2 arrays of N (value, Shoup companion) pairs
     std::vector<u64> tables((size_t)c->nall * 4 * n);
