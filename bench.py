@@ -608,7 +608,7 @@ def run_kernel_ntt(args):
     dev = torch.from_numpy(x.view(np.int64)).cuda()
     res = {}
     ok = True
-    for variant in ((0, 1, 2, 3) if args.variant < 0 else (args.variant,)):
+    for variant in ((0, 1, 2, 3, 4) if args.variant < 0 else (args.variant,)):
         K.ckks_ctx_set_ntt_variant(ctx, variant)
         for _ in range(args.warmup):
             K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)

@@ -110,14 +110,15 @@ int ckks_ctx_reset_counters(ckks_ctx* ctx);
  * to cap bytes); *len receives the full length.  Synchronises the stream. */
 int ckks_ctx_kernel_stats(ckks_ctx* ctx, char* buf, int cap, int* len);
 
-/* Autotuner: times each NTT launch variant (16 or 4 sub-problems per CTA, 3 or 4 resident
- * CTAs per SM) for limb counts 1, 2, 7, 14, 24, 48, 96, 192 (forward + inverse, `reps`
- * repetitions, 0 = 3) and keeps the fastest per size class for this context.  All variants
- * compute the same residues.  choice8 (may be NULL) receives the chosen variant per class
- * (0: 16 sub-problems / 80 registers, 1: 16 / 64, 2: 4 / 80, 3: 4 / 64; -1: default).
- * Only N = 2^16 has variants.  Synchronises the stream. */
+/* Autotuner: times each NTT launch variant (16 values per thread with 16 or 4 sub-problems
+ * per CTA and 3 or 4 resident CTAs per SM, or 4 values per thread) for limb counts 1, 2, 7,
+ * 14, 24, 48, 96, 192 (forward + inverse, `reps` repetitions, 0 = 3) and keeps the fastest
+ * per size class for this context.  All variants compute the same residues.  choice8 (may
+ * be NULL) receives the chosen variant per class (0: 16 sub-problems / 80 registers,
+ * 1: 16 / 64, 2: 4 / 80, 3: 4 / 64, 4: 4 values per thread; -1: default).  Only N = 2^16
+ * has variants.  Synchronises the stream. */
 int ckks_autotune(ckks_ctx* ctx, int reps, int32_t* choice8);
-/* Use one NTT variant (0..3 as above) for every size, or -1 for the default rule. */
+/* Use one NTT variant (0..4 as above) for every size, or -1 for the default rule. */
 int ckks_ctx_set_ntt_variant(ckks_ctx* ctx, int variant);
 
 /* ---- keys (Sec. 2.1 KeyGen) ----------------------------------------------- */

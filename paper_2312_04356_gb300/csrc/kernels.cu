@@ -347,11 +347,128 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
     }
 }
 
+// ---- the same pass with 4 values per thread: four radix-4 register rounds (local stages
+// 2r, 2r+1), three shared-memory exchanges, 64 threads per sub-problem and 4 sub-problems
+// per 256-thread CTA: four times the threads of k_ntt16, for launches over few limbs.
+// In round r thread t holds k0 + {0, e, d, d + e} (d = 128 >> 2r, e = d / 2), k0 = t with
+// zero bits inserted at the positions of d and e.  Butterflies, twiddle indices and the
+// lazy bounds are those of k_ntt16, so both kernels return the same residues.
+__device__ __forceinline__ int ins0(int t, int p) { return ((t >> p) << (p + 1)) | (t & ((1 << p) - 1)); }
+
+template <bool COL, bool INV>
+__global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const DevPrime* __restrict__ primes,
+                                                const int* __restrict__ ids, int lpp, size_t pstride,
+                                                const int* __restrict__ loff) {
+    __shared__ u64 sm[4 * F_STRIDE];
+    const int limb = blockIdx.y;
+    const int r = loff ? limb : limb % lpp;
+    const DevPrime* P = primes + ids[r];
+    const u64 q = P->m.q, q2 = 2 * q;
+    u64* a = loff ? data + ((size_t)loff[limb] << 16) : data + (size_t)(limb / lpp) * pstride + ((size_t)r << 16);
+    const int tid = threadIdx.x;
+    const int sp = COL ? (tid & 3) : (tid >> 6);
+    const int t = COL ? (tid >> 2) : (tid & 63);
+    const int sub = blockIdx.x * 4 + sp;
+    const int s0 = COL ? 0 : 8;
+    const int hi = COL ? 0 : sub;
+    auto gidx = [&](int k) -> size_t { return COL ? ((size_t)k << 8) + sub : ((size_t)sub << 8) + k; };
+    u64 x[4];
+    int k0 = 0;
+    if (!INV) {
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int u = 2 * rr, d = 128 >> u, e = d >> 1;
+            k0 = ins0(ins0(t, 6 - u), 7 - u);
+            const int ks[4] = {k0, k0 + e, k0 + d, k0 + d + e};
+            if (rr == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = a[gidx(ks[i])];
+            } else {
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = sm[f_slot(sp, ks[i])];
+            }
+            // stage u (odd/even correction as in k_ntt16): pairs (0, 2), (1, 3), one twiddle
+            {
+                const ulonglong2 w = __ldg(P->tw + (1 << (s0 + u)) + (hi << u) + (k0 >> (8 - u)));
+                ct_bfly<false>(x[0], x[2], w.x, w.y, q, q2, 2 * q2);
+                ct_bfly<false>(x[1], x[3], w.x, w.y, q, q2, 2 * q2);
+            }
+            // stage u + 1 (odd): pairs (0, 1), (2, 3)
+            {
+                const int base = (1 << (s0 + u + 1)) + (hi << (u + 1));
+                const ulonglong2 w0 = __ldg(P->tw + base + (k0 >> (7 - u)));
+                const ulonglong2 w1 = __ldg(P->tw + base + ((k0 + d) >> (7 - u)));
+                ct_bfly<true>(x[0], x[1], w0.x, w0.y, q, q2, 2 * q2);
+                ct_bfly<true>(x[2], x[3], w1.x, w1.y, q, q2, 2 * q2);
+            }
+            if (rr < 3) {
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sm[f_slot(sp, ks[i])] = x[i];
+            } else if (COL) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[gidx(ks[i])] = x[i];     // lazy, [0, 6q)
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    u64 v = x[i];
+                    if (v >= 2 * q2) v -= 2 * q2;
+                    if (v >= q2) v -= q2;
+                    if (v >= q) v -= q;
+                    a[gidx(ks[i])] = v;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int rr = 3; rr >= 0; --rr) {
+            const int u = 2 * rr, d = 128 >> u, e = d >> 1;
+            k0 = ins0(ins0(t, 6 - u), 7 - u);
+            const int ks[4] = {k0, k0 + e, k0 + d, k0 + d + e};
+            if (rr == 3) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = a[gidx(ks[i])];
+            } else {
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = sm[f_slot(sp, ks[i])];
+            }
+            // stage u + 1 first: pairs (0, 1), (2, 3)
+            {
+                const int base = (1 << (s0 + u + 1)) + (hi << (u + 1));
+                const ulonglong2 w0 = __ldg(P->itw + base + (k0 >> (7 - u)));
+                const ulonglong2 w1 = __ldg(P->itw + base + ((k0 + d) >> (7 - u)));
+                gs_bfly(x[0], x[1], w0.x, w0.y, q, q2);
+                gs_bfly(x[2], x[3], w1.x, w1.y, q, q2);
+            }
+            // stage u: pairs (0, 2), (1, 3)
+            {
+                const ulonglong2 w = __ldg(P->itw + (1 << (s0 + u)) + (hi << u) + (k0 >> (8 - u)));
+                gs_bfly(x[0], x[2], w.x, w.y, q, q2);
+                gs_bfly(x[1], x[3], w.x, w.y, q, q2);
+            }
+            if (rr > 0) {
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sm[f_slot(sp, ks[i])] = x[i];
+            } else if (COL) {
+                const u64 ni = P->n_inv, nip = P->n_inv_p;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[gidx(ks[i])] = mul_shoup(x[i], ni, nip, q);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[gidx(ks[i])] = x[i];     // lazy, [0, 2q)
+            }
+        }
+    }
+}
+
 // few limbs: 64-thread CTAs (4 sub-problems) so that the grid still covers the SMs
 // Variants (identical results): CTA of 16 or 4 sub-problems, register budget for 3 or 4
 // resident 256-thread CTAs per SM.  ckks_autotune times them per limb-count class; the
 // default (no tuning) is 16 sub-problems at >= 16 limbs, else 4, 80 registers.
-enum NttVariant { NTT_V16_R80 = 0, NTT_V16_R64 = 1, NTT_V4_R80 = 2, NTT_V4_R64 = 3, NTT_NVARIANTS = 4 };
+enum NttVariant { NTT_V16_R80 = 0, NTT_V16_R64 = 1, NTT_V4_R80 = 2, NTT_V4_R64 = 3, NTT_X4 = 4, NTT_NVARIANTS = 5 };
 
 template <bool COL, bool INV>
 void launch_ntt16_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp,
@@ -369,9 +486,13 @@ void launch_ntt16_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, cons
             k_ntt16<COL, INV, 4, 8>
                 <<<dim3(256 / 4, nlimbs), 64, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
             break;
-        default:
+        case NTT_V4_R64:
             k_ntt16<COL, INV, 4, 12>
                 <<<dim3(256 / 4, nlimbs), 64, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
+            break;
+        default:
+            k_ntt16s<COL, INV><<<dim3(256 / 4, nlimbs), 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride,
+                                                                             loff);
             break;
     }
 }

@@ -51,7 +51,7 @@ def test_ntt_bitexact(name):
     psis = [(list(P.psi_q) + list(P.psi_p))[i] for i in ids]
     x = WL.residues(3, mods, P.n)
     want = C.ntt_forward(x, mods, psis, P.logn)
-    for variant in (-1, 0, 1, 2, 3):          # every launch variant the autotuner may pick
+    for variant in (-1, 0, 1, 2, 3, 4):       # every launch variant the autotuner may pick
         K.ckks_ctx_set_ntt_variant(ctx, variant)
         dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
         K.ckks_ntt_forward(ctx, dev.data_ptr(), len(ids), ids)
@@ -63,7 +63,7 @@ def test_ntt_bitexact(name):
         assert (dev.cpu().numpy().view(np.uint64) == x).all(), variant
     K.ckks_ctx_set_ntt_variant(ctx, -1)
     if P.logn == 16:
-        assert all(c in (0, 1, 2, 3) for c in K.ckks_autotune(ctx, 1))
+        assert all(c in (0, 1, 2, 3, 4) for c in K.ckks_autotune(ctx, 1))
     # edge values: all zeros, all q-1
     e = np.stack([np.full(P.n, q - 1, dtype=np.uint64) for q in mods])
     e[0] = 0
