@@ -105,6 +105,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------ replicas (N > 1) -----
+def rank_info():
+    """(rank, world, local rank) from the launcher's environment (1 process when absent)"""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, dist, device="cpu"):
+    """the slowest replica's value (every rank gets it); x unchanged without a process group"""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_block(t_ms_max, steps, world):
+    """replicas: `world` ranks each ran `steps` blocks within t_ms_max (the slowest rank's time),
+    so the whole job's ms per block is t_ms_max / (steps * world); per-step time is per rank"""
+    return t_ms_max / steps, t_ms_max / (steps * world)
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -217,8 +240,8 @@ def block_op_counts():
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    rank, _, _ = rank_info()
+    if rank != 0:      # under torchrun rank 0 alone times the oracle; the others exit without work
         return
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     vals = []
@@ -241,9 +264,7 @@ def run_reference(args):
 # --------------------------------------------------------------- GPU arm -----
 def run_ours(args):
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_info()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -305,12 +326,8 @@ def run_ours(args):
         dist.barrier()
     t_ms = e0.elapsed_time(e1)
     launches = K.ckks_ctx_counters(ctx)["launches"] - launches0
-    if dist:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    ms_per_step = t_ms / args.steps
-    value = t_ms / (args.steps * world)
+    t_ms = max_over_ranks(t_ms, dist, "cuda")
+    ms_per_step, value = job_ms_per_block(t_ms, args.steps, world)
 
     # batched: B independent inputs, one graph each, on B streams at once
     B = max(1, args.batch)
