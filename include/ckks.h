@@ -221,7 +221,8 @@ int ckks_conjugate(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, ckks
 int ckks_ptset_create(ckks_ctx* ctx, int a0, int step, int count, int bsgs_B, int level, double scale,
                       ckks_ptset** out);
 int ckks_ptset_destroy(ckks_ptset* ps);
-/* host [level+1][N] coefficient-domain limbs of pt_{g,b} (copied) */
+/* host [level+1+np][N] coefficient-domain limbs of pt_{g,b} over Q_level then the special
+ * primes (copied): BSGS diagonals are kept over Q_level u P for double hoisting */
 int ckks_ptset_set_rns(ckks_ctx* ctx, ckks_ptset* ps, int g, int b, const uint64_t* host);
 int ckks_ptset_info(const ckks_ptset* ps, int* a0, int* step, int* count, int* bsgs_B, int* level,
                     double* scale, int* n_pts);

@@ -9,6 +9,8 @@ defers them to the CKKS bootstrapping papers it cites in Sec. 2.4):
 * After the fused conv the level-0 ciphertext holds t = Delta_0 o + q0 I in its
   coefficients.  ModRaise keeps that polynomial; its scale is declared
   q0 * K_eff so that the message is y = t / (q0 K_eff) in [-1, 1].
+* Every HMatmul is a double-hoisted BSGS (Oracle.bsgs_multi); the bootstrapping plans take
+  the baby-step count of boot_bsgs_B (16 for 63 diagonals).
 * CtoS = T_{N/2}^{-1} (Sec. 2.4) in `ctos_levels` BSGS levels, largest stride first;
   every level's plaintexts are encoded at scale q_l, so the rescale keeps the
   scale; the 1/2 of the conjugate split is folded into the last level.
@@ -33,7 +35,7 @@ import math
 import numpy as np
 
 from . import encoding as E
-from .scheme import Oracle, round_half_away
+from .scheme import Oracle, boot_bsgs_B, round_half_away
 
 
 class BootConfig:
@@ -63,7 +65,7 @@ class BootConfig:
                 D = {o: 0.5 * v for o, v in D.items()}
             a0, step, count = E.ap_of_group(strides, m)
             lev = L - i
-            B = ctos_B[i] if ctos_B else None
+            B = ctos_B[i] if ctos_B else boot_bsgs_B(count)
             self.ctos.append(orc.make_plan(D, a0, step, count, lev, float(P.q[lev]), B))
         # --- EvalMod polynomial
         if coeffs is None:
@@ -93,14 +95,15 @@ class BootConfig:
         if stride == 2:
             assert w >= 4 and w0 % 2 == 0
             a0, step, count = E.decompose_ap(w, n)
-            self.decomp = orc.make_plan(E.decompose_diag(w, n), a0, step, count, top, P.delta[top])
+            self.decomp = orc.make_plan(E.decompose_diag(w, n), a0, step, count, top, P.delta[top],
+                                        boot_bsgs_B(count))
             top, ell_out = top - 1, self.ell // 4
         # --- StoC1 plans
         self.stoc = []
         for i, (D, strides) in enumerate(E.stoc1_groups(n, ell_out, stoc_levels)):
             a0, step, count = E.ap_of_group(strides, m)
             lev = top - i
-            B = stoc_B[i] if stoc_B else None
+            B = stoc_B[i] if stoc_B else boot_bsgs_B(count)
             self.stoc.append(orc.make_plan(D, a0, step, count, lev, P.delta[lev], B))
         self.l_out = top - len(self.stoc)
         assert self.l_out >= 1, "not enough levels for the block"

@@ -46,10 +46,11 @@ class Ciphertext:
 
 
 class Plaintext:
-    def __init__(self, limbs, level, scale):
+    def __init__(self, limbs, level, scale, ext=False):
         self.limbs = np.ascontiguousarray(limbs, dtype=np.uint64)   # coefficient domain
         self.level = level
         self.scale = float(scale)
+        self.ext = ext          # limbs over Q_level u P (BSGS diagonals), else over Q_level
 
 
 class BsgsPlan:
@@ -66,14 +67,31 @@ class BsgsPlan:
         return -(-self.count // self.B)
 
     def rotations(self, m):
-        baby = [self.step * b % m for b in range(1, self.B)]
-        giant = [(self.a0 + self.step * g * self.B) % m for g in range(self.G)]
+        """the rotation steps the plan's non-zero diagonals need (baby and giant)"""
+        baby = [self.step * b % m for (_, b) in self.pts]
+        giant = [(self.a0 + self.step * g * self.B) % m for (g, _) in self.pts]
         return sorted({r for r in baby + giant if r})
 
 
 def default_bsgs_B(count):
     """Baby-step count: 2^ceil(log2(count)/2)."""
     return 1 << math.ceil(math.log2(count) / 2) if count > 1 else 1
+
+
+def boot_bsgs_B(count):
+    """Baby-step count for the bootstrapping HMatmuls: with double hoisting a baby step costs a
+    key-switch inner product and a giant step about five times that (ModDown of c1, ModUp,
+    inner product), so B minimises (B - 1) + 5 (G - 1), G = ceil(count / B), over powers of
+    two (the smaller B on ties)."""
+    best, bestB, B = None, 1, 1
+    while True:
+        G = -(-count // B)
+        cost = (B - 1) + 5 * (G - 1)
+        if best is None or cost < best:
+            best, bestB = cost, B
+        if B >= count:
+            return bestB
+        B *= 2
 
 
 class Oracle:
@@ -160,15 +178,15 @@ class Oracle:
         self.gen_galois_key(2 * self.P.n - 1)
 
     # ------------------------------------------------------- enc / dec ------
-    def encode_pt(self, z, level, scale):
-        """slot vector z (N/2 complex) -> plaintext round(scale * f)"""
+    def encode_pt(self, z, level, scale, ext=False):
+        """slot vector z (N/2 complex) -> plaintext round(scale * f); ext: limbs over Q_level u P"""
         f = E.encode(z, self.P.n) * scale
-        return self.pt_from_real_coeffs(f, level, scale)
+        return self.pt_from_real_coeffs(f, level, scale, ext)
 
-    def pt_from_real_coeffs(self, f, level, scale):
+    def pt_from_real_coeffs(self, f, level, scale, ext=False):
         v = np.round(f)
         assert np.abs(v).max() < 2.0 ** 62, "plaintext coefficient too large"
-        return Plaintext(C.signed_to_rns(v.astype(np.int64), self.P.moduli(level)), level, scale)
+        return Plaintext(C.signed_to_rns(v.astype(np.int64), self.P.moduli(level, ext)), level, scale, ext)
 
     def encrypt(self, pt, nonce):
         P, l, n = self.P, pt.level, self.P.n
@@ -457,54 +475,86 @@ class Oracle:
                 off = (plan.a0 + step * i) % m
                 if off not in diags:
                     continue
-                plan.pts[(g, b)] = self.encode_pt(np.roll(diags[off], R), level, scale)
+                plan.pts[(g, b)] = self.encode_pt(np.roll(diags[off], R), level, scale, ext=True)
         return plan
 
     def bsgs(self, ct, plan, rescale=False):
         """sum_g rot_{a0+step*g*B}( sum_b pt_{g,b} (*) rot_{step*b}(ct) )"""
         return self.bsgs_multi([ct], [plan], rescale)
 
+    def rotate_hoisted_ext(self, ct, steps):
+        """rot_r(ct) for every r in steps, kept over Q_l u P before ModDown (double hoisting):
+        (P automorph(c0) + u0, u1) with u the key switch of the automorphed ModUp digits of c1;
+        r = 0 gives (P c0, P c1).  One ModUp of c1 serves all steps."""
+        P = self.P
+        l = ct.level
+        q, ext = P.moduli(l), P.moduli(l, True)
+        zeros = np.zeros((len(ext), P.n), dtype=np.uint64)
+        digits = None
+        outs = []
+        for r in steps:
+            g = self.galois(r)
+            if g == 1:
+                outs.append((self.lift_p(zeros, ct.c0, l), self.lift_p(zeros, ct.c1, l)))
+                continue
+            if digits is None:
+                digits = self.mod_up(ct.c1, l)
+            self.ops["hrot"] += 1
+            dg = [C.automorphism(D, ext, g, P.logn) for D in digits]
+            kb, ka = self.key_switch_inner(dg, g, l)
+            outs.append((self.lift_p(kb, C.automorphism(ct.c0, q, g, P.logn), l), ka))
+        return outs
+
     def bsgs_multi(self, cts, plans, rescale=False):
-        """sum over inputs t and giant steps g of rot_{R_g}(sum_b pt_{g,b} (*) rot_{step b}(ct_t)).
-        Baby-step rotations share one ModUp per input (hoisting).  The giant-step rotations'
-        key switches are summed over Q_l u P together with P times the parts that need no key
-        switch, and brought down once: ModDown, or ModDown fused with the rescale when
-        `rescale` is set."""
+        """sum over inputs t and giant steps g of rot_{R_g}(sum_b pt_{g,b} (*) rot_{step b}(ct_t)),
+        double hoisted: the baby-step rotations of each input share one ModUp and stay over
+        Q_l u P (no ModDown), the plaintext diagonals are over Q_l u P, and the inner sums of
+        all inputs with the same giant step are added there.  A giant step with R != 0 brings
+        only its c1 down (ModDown), raises it (ModUp) and key-switches it; its c0 is
+        automorphed over Q_l u P.  Everything is summed over Q_l u P and brought down once:
+        ModDown, or ModDown fused with the rescale when `rescale` is set."""
         P = self.P
         l = cts[0].level
         m = P.n // 2
         q, ext = P.moduli(l), P.moduli(l, True)
-        plain, acc = None, None
+        geo = {(p.a0, p.step, p.B, p.G) for p in plans}
+        assert len(geo) == 1, "the plans of one HMatmul share their BSGS geometry"
+        a0, step, B, G = geo.pop()
+        inner = {}
+        scale = None
         for ct, plan in zip(cts, plans):
             assert ct.level == plan.level == l
             used_b = sorted({b for (_, b) in plan.pts})
-            baby = dict(zip(used_b, self.rotate_hoisted(ct, [plan.step * b % m for b in used_b])))
-            for g in range(plan.G):
-                inner = None
-                for b in range(plan.B):
-                    if (g, b) not in plan.pts:
-                        continue
-                    t = self.mul_plain(baby[b], plan.pts[(g, b)])
-                    inner = t if inner is None else self.add(inner, t)
-                if inner is None:
-                    continue
-                R = (plan.a0 + plan.step * g * plan.B) % m
-                if R:
-                    gal = self.galois(R)
-                    self.ops["hrot"] += 1
-                    dg = [C.automorphism(D, ext, gal, P.logn) for D in self.mod_up(inner.c1, l)]
-                    kb, ka = self.key_switch_inner(dg, gal, l)
-                    acc = [kb, ka] if acc is None else [C.add(acc[0], kb, ext), C.add(acc[1], ka, ext)]
-                    inner = Ciphertext(C.automorphism(inner.c0, q, gal, P.logn), np.zeros_like(inner.c1), l,
-                                       inner.scale)
-                plain = inner if plain is None else self.add(plain, inner)
-        if acc is None:
-            return self.rescale(plain) if rescale else plain
-        kb, ka = self.lift_p(acc[0], plain.c0, l), self.lift_p(acc[1], plain.c1, l)
+            babies = dict(zip(used_b, self.rotate_hoisted_ext(ct, [step * b % m for b in used_b])))
+            bn = {b: (self.ntt(v[0], l, True), self.ntt(v[1], l, True)) for b, v in babies.items()}
+            for (g, b), pt in plan.pts.items():
+                assert pt.ext
+                self.ops["pmult"] += 1
+                pn = self.ntt(pt.limbs, l, True)
+                t0, t1 = C.mul(bn[b][0], pn, ext), C.mul(bn[b][1], pn, ext)
+                if g in inner:
+                    inner[g] = (C.add(inner[g][0], t0, ext), C.add(inner[g][1], t1, ext))
+                else:
+                    inner[g] = (t0, t1)
+                s_ = ct.scale * pt.scale
+                assert scale is None or abs(s_ - scale) <= 1e-9 * scale
+                scale = s_
+        acc = None
+        for g in sorted(inner):
+            i0, i1 = self.intt(inner[g][0], l, True), self.intt(inner[g][1], l, True)
+            R = (a0 + step * g * B) % m
+            if R:
+                gal = self.galois(R)
+                self.ops["hrot"] += 1
+                c1q = C.mod_down(i1, q, P.p)
+                dg = [C.automorphism(D, ext, gal, P.logn) for D in self.mod_up(c1q, l)]
+                kb, ka = self.key_switch_inner(dg, gal, l)
+                i0, i1 = C.add(C.automorphism(i0, ext, gal, P.logn), kb, ext), ka
+            acc = (i0, i1) if acc is None else (C.add(acc[0], i0, ext), C.add(acc[1], i1, ext))
         if rescale:
-            c0, c1 = self.mod_down_rescale(kb, ka, l)
-            return Ciphertext(c0, c1, l - 1, plain.scale / float(P.q[l]))
-        return Ciphertext(C.mod_down(kb, q, P.p), C.mod_down(ka, q, P.p), l, plain.scale)
+            c0, c1 = self.mod_down_rescale(acc[0], acc[1], l)
+            return Ciphertext(c0, c1, l - 1, scale / float(P.q[l]))
+        return Ciphertext(C.mod_down(acc[0], q, P.p), C.mod_down(acc[1], q, P.p), l, scale)
 
     # --------------------------------------------------- fused CinS conv ----
     def conv_plan(self, W, cin, cout, f, w, level, pt_scale, B=None):

@@ -34,16 +34,20 @@ int guard(const ckks_ctx* c, F&& f) {
 #define REQ(p) CK_CHECK((p) != nullptr, CKKS_EINVAL, #p " is NULL")
 #define CT_OK(x) CK_CHECK((x) && (x)->level >= 0, CKKS_EINVAL, #x " is NULL or empty")
 
-void upload_coeffs(ckks_ctx* c, const std::vector<int64_t>& v, int level, double scale, ckks_pt* out) {
+void upload_coeffs(ckks_ctx* c, const std::vector<int64_t>& v, int level, double scale, ckks_pt* out,
+                   bool ext = false) {
     const size_t n = c->n;
+    const int rows = level + 1 + (ext ? c->np : 0);
+    const int* ids = ext ? c->d_ext_ids[level] : c->d_iota;
     DevBuf sm(n, c->stream);
     CUDA_CHECK(cudaMemcpyAsync(sm.ptr, v.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
     out->ctx = c;
-    out->buf = DevBuf((size_t)(level + 1) * n, c->stream);
+    out->buf = DevBuf((size_t)rows * n, c->stream);
     out->level = level;
     out->scale = scale;
-    kern::small_to_rns(c, (const int64_t*)sm.ptr, out->buf.ptr, level + 1, c->d_iota);
-    kern::ntt_forward(c, out->buf.ptr, level + 1, c->d_iota, level + 1);
+    out->ext = ext;
+    kern::small_to_rns(c, (const int64_t*)sm.ptr, out->buf.ptr, rows, ids);
+    kern::ntt_forward(c, out->buf.ptr, rows, ids, rows);
 }
 
 std::vector<int64_t> round_coeffs(const std::vector<double>& f, double scale) {
@@ -56,11 +60,12 @@ std::vector<int64_t> round_coeffs(const std::vector<double>& f, double scale) {
     return v;
 }
 
-void encode_complex(ckks_ctx* c, const std::vector<cplx>& z, int level, double scale, ckks_pt* out) {
+void encode_complex(ckks_ctx* c, const std::vector<cplx>& z, int level, double scale, ckks_pt* out,
+                    bool ext = false) {
     CK_CHECK(level >= 0 && level <= c->L, CKKS_EINVAL, "level out of range");
     std::vector<cplx> zz(z);
     zz.resize(c->n / 2, cplx(0, 0));
-    upload_coeffs(c, round_coeffs(fp64::encode_slots(zz, c->n), scale), level, scale, out);
+    upload_coeffs(c, round_coeffs(fp64::encode_slots(zz, c->n), scale), level, scale, out, ext);
 }
 
 // limbs (host, coefficient domain, [nl][N]) -> centred values / scale, by Garner's mixed radix
@@ -133,7 +138,7 @@ ckks_ptset* make_plan(ckks_ctx* c, const fp64::Diag& D, int a0, int step, int co
             std::vector<cplx> v(m);
             for (int t = 0; t < m; ++t) v[t] = it->second[((t - R) % m + m) % m];
             auto pt = std::make_unique<ckks_pt>();
-            encode_complex(c, v, level, scale, pt.get());
+            encode_complex(c, v, level, scale, pt.get(), true);     // over Q_level u P (double hoisting)
             ps->pts[std::make_pair(g, b)] = std::move(pt);
         }
     }
@@ -698,9 +703,17 @@ int ckks_ptset_set_rns(ckks_ctx* ctx, ckks_ptset* ps, int g, int b, const uint64
         REQ(host);
         CK_CHECK(g >= 0 && g < ps->G() && b >= 0 && b < ps->B && g * ps->B + b < ps->count, CKKS_EINVAL,
                  "(g, b) outside the plan");
+        // limbs over Q_level u P, coefficient domain
+        const int rows = ps->level + 1 + ctx->np;
         auto pt = std::make_unique<ckks_pt>();
-        CK_CHECK(ckks_pt_import_rns(ctx, host, ps->level, ps->scale, pt.get()) == CKKS_OK, CKKS_EINVAL,
-                 "plaintext import failed");
+        DevBuf buf((size_t)rows * ctx->n, ctx->stream);
+        CUDA_CHECK(cudaMemcpyAsync(buf.ptr, host, (size_t)rows * ctx->n * 8, cudaMemcpyHostToDevice, ctx->stream));
+        kern::ntt_forward(ctx, buf.ptr, rows, ctx->d_ext_ids[ps->level], rows);
+        pt->ctx = ctx;
+        pt->buf = std::move(buf);
+        pt->level = ps->level;
+        pt->scale = ps->scale;
+        pt->ext = true;
         ps->pts[std::make_pair(g, b)] = std::move(pt);
     });
 }
@@ -907,7 +920,7 @@ int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out)
             int a0, step, count;
             fp64::ap_of_group(groups[i], m, &a0, &step, &count);
             const int lev = L - (int)i;
-            bt->ctos.emplace_back(make_plan(ctx, D, a0, step, count, lev, (double)ctx->q[lev], 0));
+            bt->ctos.emplace_back(make_plan(ctx, D, a0, step, count, lev, (double)ctx->q[lev], fp64::boot_bsgs_B(count)));
         }
         bt->coeffs = fp64::cheb_interp_cos(bt->K_eff, bp->r, bp->deg);
         int depth = 0;
@@ -944,7 +957,7 @@ int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out)
         if (bp->stride == 2) {
             CK_CHECK(bp->w >= 4 && bp->w0 % 2 == 0, CKKS_EINVAL, "stride 2 needs w >= 4 and an even image width");
             bt->decomp.reset(make_plan(ctx, fp64::decompose_diag(bp->w, m), (1 - bp->w) * (bp->w / 4), bp->w / 4,
-                                       2 * bp->w - 1, top, ctx->delta[top], 0));
+                                       2 * bp->w - 1, top, ctx->delta[top], fp64::boot_bsgs_B(2 * bp->w - 1)));
             --top;
             ell_out /= 4;
         }
@@ -958,7 +971,7 @@ int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out)
             int a0, step, count;
             fp64::ap_of_group(sg[i], m, &a0, &step, &count);
             const int lev = top - (int)i;
-            bt->stoc.emplace_back(make_plan(ctx, D, a0, step, count, lev, ctx->delta[lev], 0));
+            bt->stoc.emplace_back(make_plan(ctx, D, a0, step, count, lev, ctx->delta[lev], fp64::boot_bsgs_B(count)));
         }
         bt->l_out = top - (int)bt->stoc.size();
         CK_CHECK(bt->l_out >= 1, CKKS_ELEVEL, "not enough levels for the block");
@@ -1010,11 +1023,12 @@ static std::unique_ptr<ckks_ptset> clone_ptset(ckks_ctx* ctx, const ckks_ptset& 
     o->scale = ps.scale;
     for (const auto& kv : ps.pts) {
         auto pt = std::make_unique<ckks_pt>();
-        const size_t words = (size_t)(kv.second->level + 1) * ctx->n;
+        const size_t words = (size_t)(kv.second->level + 1 + (kv.second->ext ? ctx->np : 0)) * ctx->n;
         pt->ctx = ctx;
         pt->buf = DevBuf(words, ctx->stream);
         pt->level = kv.second->level;
         pt->scale = kv.second->scale;
+        pt->ext = kv.second->ext;
         CUDA_CHECK(cudaMemcpyAsync(pt->buf.ptr, kv.second->buf.ptr, words * 8, cudaMemcpyDeviceToDevice,
                                    ctx->stream));
         o->pts[kv.first] = std::move(pt);

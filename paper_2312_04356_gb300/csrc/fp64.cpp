@@ -193,6 +193,23 @@ int default_bsgs_B(int count) {
     return 1 << e;
 }
 
+// Bootstrapping HMatmuls are double hoisted: a baby step costs one key-switch inner product,
+// a giant step about five (ModDown of c1, ModUp, inner product).  B = the power of two that
+// minimises (B - 1) + 5 (G - 1), G = ceil(count / B); the smaller one on ties.
+int boot_bsgs_B(int count) {
+    long long best = -1;
+    int bestB = 1;
+    for (int B = 1;; B *= 2) {
+        const long long G = (count + B - 1) / B;
+        const long long cost = (B - 1) + 5 * (G - 1);
+        if (best < 0 || cost < best) {
+            best = cost;
+            bestB = B;
+        }
+        if (B >= count) return bestB;
+    }
+}
+
 // --------------------------------------------------------------- CinS ------
 std::vector<cplx> real_cins_slots(const double* m, int C, int two_l) {
     const int ell = two_l / 2;

@@ -137,9 +137,10 @@ struct ckks_ct {
 
 struct ckks_pt {
     ckks_ctx* ctx = nullptr;
-    DevBuf buf;           // [level+1][N], NTT domain
+    DevBuf buf;           // [level+1][N] (ext: [level+1+np][N], Q rows then P rows), NTT domain
     int level = -1;
     double scale = 1.0;
+    bool ext = false;     // also reduced modulo the special primes (BSGS diagonals)
 };
 
 struct SwitchKey {
@@ -202,14 +203,15 @@ namespace kern {
 void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
 // forward NTT of an arbitrary list of limbs: limb i at data + off[i] * N with prime ids[i] (N = 2^16)
 void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, const int* ids);
-// o[poly][limb] = sum_t a_t[poly][limb] * p_t[limb] (two polynomials of nl limbs, t < n <= 16)
+// o[poly][limb] = sum_t a_t[poly][limb] * p_t[limb] (two polynomials of nl limbs, t < n <= 32)
 struct BsgsTerms {
-    static constexpr int MAX = 16;
+    static constexpr int MAX = 32;
     const u64* a[MAX];
     const u64* p[MAX];
     int n;
 };
-void bsgs_inner(const ckks_ctx* c, const BsgsTerms& t, u64* o, int nl);
+// limb r of a polynomial (nl limbs) has prime ids[r]
+void bsgs_inner(const ckks_ctx* c, const BsgsTerms& t, u64* o, int nl, const int* ids);
 void autotune_ntt(ckks_ctx* c, int reps);
 void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
@@ -308,5 +310,6 @@ std::vector<cplx> real_cins_slots(const double* m, int C, int two_l);
 std::vector<double> cins_to_reals(const std::vector<cplx>& z, int C, int two_l);
 std::vector<double> cheb_interp_cos(double K, int r, int deg);
 int default_bsgs_B(int count);
+int boot_bsgs_B(int count);
 }  // namespace fp64
 

@@ -749,16 +749,16 @@ __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const
 
 // ------------------------------------------------- BSGS inner products ----
 // o[poly][limb] = sum_t a_t[poly][limb] * p_t[limb]: the products are summed exactly in
-// 128 bits (each < 2^122, at most 16 terms) and reduced once.
+// 128 bits (each < 2^122, at most 32 terms) and reduced once.
 __device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P) {
     return add_mod(mul_shoup(hi, P.r64, P.r64p, P.m.q), reduce64(lo, P.m), P.m.q);
 }
 template <int V>
 __global__ void k_bsgs_inner(kern::BsgsTerms T, u64* __restrict__ o, const DevPrime* __restrict__ primes, int nl,
-                             int logn) {
+                             const int* __restrict__ ids, int logn) {
     const int limb = blockIdx.y;           // 0 .. 2 nl - 1, polynomial-major
     const int r = limb % nl;
-    const DevPrime P = primes[r];
+    const DevPrime P = primes[ids[r]];
     const size_t offa = (size_t)limb << logn, offp = (size_t)r << logn;
     EWV_BEGIN(1 << logn)
     u64 lo[V], hi[V];
@@ -1081,12 +1081,12 @@ void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, 
     LAUNCH_CHECK();
 }
 
-void bsgs_inner(const ckks_ctx* c, const BsgsTerms& t, u64* o, int nl) {
-    CK_CHECK(t.n >= 1 && t.n <= BsgsTerms::MAX, CKKS_EINVAL, "1..16 BSGS terms per kernel");
+void bsgs_inner(const ckks_ctx* c, const BsgsTerms& t, u64* o, int nl, const int* ids) {
+    CK_CHECK(t.n >= 1 && t.n <= BsgsTerms::MAX, CKKS_EINVAL, "1..32 BSGS terms per kernel");
     { KTimer kt_(c, "bsgs_inner", (2.0 * t.n + t.n + 2.0) * nl * c->n * 8.0);
     bool vec = al16(o);
     for (int i = 0; i < t.n; ++i) vec = vec && al16(t.a[i]) && al16(t.p[i]);
-    EWV_LAUNCH(k_bsgs_inner, vec, 2 * nl, t, o, c->d_primes, nl, c->logn);
+    EWV_LAUNCH(k_bsgs_inner, vec, 2 * nl, t, o, c->d_primes, nl, ids, c->logn);
     }
     LAUNCH_CHECK();
 }

@@ -699,19 +699,66 @@ ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct
 }
 
 // ---------------------------------------------------------------- BSGS -----
-// sum over inputs t and giant steps g of rot_{R_g}(sum_b pt_{g,b} (*) rot_{step b}(in_t)).
-// Baby steps share one ModUp per input.  The giant-step rotations' key switches are summed
-// over Q_l u P together with P times the parts that need none, and brought down once:
-// ModDown, or ModDown fused with the rescale when rescale_out is set.
+// ModDown of one polynomial x over Q_l u P (NTT domain; its P rows are consumed): out [l+1][N]
+static void mod_down_poly(ckks_ctx* c, u64* x, int level, u64* out) {
+    const size_t n = c->n;
+    const int nl = level + 1;
+    kern::ntt_inverse(c, x + (size_t)nl * n, c->np, c->d_ext_ids[level] + nl, c->np);
+    DevBuf conv((size_t)nl * n, c->stream);
+    kern::base_convert(c, c->moddown_tab(level), x + (size_t)nl * n, n, conv.ptr, n, 1, 0, 0);
+    kern::ntt_forward(c, conv.ptr, nl, c->d_iota, nl);
+    kern::sub_mul_scalar(c, x, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out, nl, c->d_iota, nl);
+}
+
+// rot_r(a) for every r in steps kept over Q_l u P before ModDown (double hoisting), each
+// [2][l+1+np][N]: (P automorph(c0) + u0, u1), u the key switch of the automorphed ModUp
+// digits of c1 (one ModUp for all steps); r = 0 gives (P c0, P c1).
+static std::vector<DevBuf> rotate_hoisted_ext(const ckks_keys& keys, const ckks_ct& a,
+                                              const std::vector<long long>& steps) {
+    ckks_ctx* c = a.ctx;
+    const int l = a.level, nl = l + 1;
+    const size_t n = c->n, next = (size_t)nl + c->np;
+    std::vector<DevBuf> outs;
+    DevBuf D;
+    int ndig = 0;
+    for (long long r : steps) {
+        const u64 g = galois_of_step(c, r);
+        DevBuf o(2 * next * n, c->stream);
+        if (g == 1) {
+            CUDA_CHECK(cudaMemsetAsync(o.ptr, 0, 2 * next * n * 8, c->stream));
+            lift_p(c, a.buf.ptr, o.ptr, l);
+        } else {
+            if (!D.ptr) D = mod_up(c, a.c1(), l, &ndig);
+            c->ops["hrot"]++;
+            key_switch_inner(c, keys, D.ptr, ndig, l, g, g, o.ptr, false);
+            DevBuf t((size_t)nl * n, c->stream);
+            kern::automorph(c, a.c0(), t.ptr, nl, g);
+            kern::mul_scalar_acc(c, t.ptr, c->d_pmod, c->d_pmod + c->nq, o.ptr, nl, c->d_iota, nl);
+        }
+        outs.push_back(std::move(o));
+    }
+    return outs;
+}
+
+// sum over inputs t and giant steps g of rot_{R_g}(sum_b pt_{g,b} (*) rot_{step b}(in_t)),
+// double hoisted: baby steps stay over Q_l u P (one ModUp per input, no ModDown), the
+// diagonals are over Q_l u P, and the inner sums of all inputs with the same giant step are
+// added there.  A giant step with R != 0 brings only c1 down (ModDown), raises and
+// key-switches it; its c0 is automorphed over Q_l u P.  Everything is summed over Q_l u P
+// and brought down once: ModDown, or ModDown fused with the rescale when rescale_out is set.
 ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins,
                    const std::vector<const ckks_ptset*>& pss, bool rescale_out) {
     ckks_ctx* c = ins[0]->ctx;
     const int l = ins[0]->level, nl = l + 1;
     const size_t n = c->n, next = (size_t)nl + c->np;
     const long long m = c->n / 2;
-    DevBuf acc;
-    bool have_acc = false, have_plain = false;
-    ckks_ct plain;
+    const int* ext = c->d_ext_ids[l];
+    const ckks_ptset& p0 = *pss[0];
+    for (const ckks_ptset* ps : pss)
+        CK_CHECK(ps->a0 == p0.a0 && ps->step == p0.step && ps->B == p0.B && ps->G() == p0.G(), CKKS_EINVAL,
+                 "the plaintext sets of one HMatmul must share their BSGS geometry");
+    std::map<int, DevBuf> inner;
+    double scale = 0;
     for (size_t t = 0; t < ins.size(); ++t) {
         const ckks_ct& a = *ins[t];
         const ckks_ptset& ps = *pss[t];
@@ -722,62 +769,71 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
         std::vector<int> used_b(used.begin(), used.end());
         std::vector<long long> steps;
         for (int b : used_b) steps.push_back(((long long)ps.step * b) % m);
-        std::vector<ckks_ct> baby = rotate_hoisted(keys, a, steps);
+        std::vector<DevBuf> baby = rotate_hoisted_ext(keys, a, steps);
         std::map<int, int> bidx;
         for (size_t i = 0; i < used_b.size(); ++i) bidx[used_b[i]] = (int)i;
         for (int g = 0; g < ps.G(); ++g) {
-        kern::BsgsTerms terms;
-        terms.n = 0;
-        double sc = 0;
-        for (int b = 0; b < ps.B; ++b) {
-            auto it = ps.pts.find(std::make_pair(g, b));
-            if (it == ps.pts.end()) continue;
-            CK_CHECK(terms.n < kern::BsgsTerms::MAX, CKKS_EINVAL, "more than 16 baby steps");
-            terms.a[terms.n] = baby[bidx[b]].buf.ptr;
-            terms.p[terms.n] = it->second->buf.ptr;
-            sc = a.scale * it->second->scale;
-            ++terms.n;
-            c->ops["pmult"]++;
-        }
-        if (!terms.n) continue;
-        ckks_ct inner = new_ct(c, a.level, sc);
-        kern::bsgs_inner(c, terms, inner.buf.ptr, a.level + 1);
-        const long long R = (((long long)ps.a0 + (long long)ps.step * g * ps.B) % m + m) % m;
-        if (R) {
-            const u64 gal = galois_of_step(c, R);
-            c->ops["hrot"]++;
-            int ndig = 0;
-            DevBuf D = mod_up(c, inner.c1(), l, &ndig);
-            if (!have_acc) acc = DevBuf(2 * next * n, c->stream);
-            key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, acc.ptr, have_acc);
-            have_acc = true;
-            if (!have_plain) {
-                plain = new_ct(c, l, inner.scale);
-                kern::automorph(c, inner.c0(), plain.c0(), nl, gal);
-                CUDA_CHECK(cudaMemsetAsync(plain.c1(), 0, (size_t)nl * n * 8, c->stream));
-                have_plain = true;
-            } else {
-                DevBuf tmp((size_t)nl * n, c->stream);
-                kern::automorph(c, inner.c0(), tmp.ptr, nl, gal);
-                kern::add(c, plain.c0(), tmp.ptr, plain.c0(), nl, c->d_iota, nl);
+            kern::BsgsTerms terms;
+            terms.n = 0;
+            for (int b = 0; b < ps.B; ++b) {
+                auto it = ps.pts.find(std::make_pair(g, b));
+                if (it == ps.pts.end()) continue;
+                CK_CHECK(it->second->ext, CKKS_EINVAL, "BSGS diagonals must be over Q_l u P");
+                CK_CHECK(terms.n < kern::BsgsTerms::MAX, CKKS_EINVAL, "more than 32 baby steps per giant step");
+                terms.a[terms.n] = baby[bidx[b]].ptr;
+                terms.p[terms.n] = it->second->buf.ptr;
+                scale = a.scale * it->second->scale;
+                ++terms.n;
+                c->ops["pmult"]++;
             }
-        } else if (!have_plain) {
-            plain = std::move(inner);
-            have_plain = true;
-        } else {
-            kern::add(c, plain.buf.ptr, inner.buf.ptr, plain.buf.ptr, 2 * nl, c->d_iota, nl);
-        }
+            if (!terms.n) continue;
+            auto it = inner.find(g);
+            if (it == inner.end()) {
+                DevBuf s(2 * next * n, c->stream);
+                kern::bsgs_inner(c, terms, s.ptr, (int)next, ext);
+                inner.emplace(g, std::move(s));
+            } else {
+                DevBuf s(2 * next * n, c->stream);
+                kern::bsgs_inner(c, terms, s.ptr, (int)next, ext);
+                kern::add(c, it->second.ptr, s.ptr, it->second.ptr, 2 * (int)next, ext, (int)next);
+            }
         }
     }
-    CK_CHECK(have_plain, CKKS_EINVAL, "empty plaintext set");
-    if (!have_acc) return rescale_out ? rescale(plain) : std::move(plain);
-    lift_p(c, plain.buf.ptr, acc.ptr, l);
+    CK_CHECK(!inner.empty(), CKKS_EINVAL, "empty plaintext set");
+    DevBuf acc;
+    bool have_acc = false;
+    for (auto& kv : inner) {
+        const int g = kv.first;
+        u64* x = kv.second.ptr;
+        const long long R = (((long long)p0.a0 + (long long)p0.step * g * p0.B) % m + m) % m;
+        if (!R) {
+            if (!have_acc) {
+                acc = std::move(kv.second);
+                have_acc = true;
+            } else {
+                kern::add(c, acc.ptr, x, acc.ptr, 2 * (int)next, ext, (int)next);
+            }
+            continue;
+        }
+        const u64 gal = galois_of_step(c, R);
+        c->ops["hrot"]++;
+        DevBuf c1q((size_t)nl * n, c->stream);
+        mod_down_poly(c, x + next * n, l, c1q.ptr);
+        int ndig = 0;
+        DevBuf D = mod_up(c, c1q.ptr, l, &ndig);
+        if (!have_acc) acc = DevBuf(2 * next * n, c->stream);
+        key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, acc.ptr, have_acc);
+        have_acc = true;
+        DevBuf t(next * n, c->stream);
+        kern::automorph(c, x, t.ptr, (int)next, gal);
+        kern::add(c, acc.ptr, t.ptr, acc.ptr, (int)next, ext, (int)next);
+    }
     if (rescale_out) {
-        ckks_ct o = new_ct(c, l - 1, plain.scale / (double)c->q[l]);
+        ckks_ct o = new_ct(c, l - 1, scale / (double)c->q[l]);
         mod_down_rescale(c, acc.ptr, l, o.buf.ptr);
         return o;
     }
-    ckks_ct o = new_ct(c, l, plain.scale);
+    ckks_ct o = new_ct(c, l, scale);
     mod_down(c, acc.ptr, l, o.c0(), o.c1());
     return o;
 }

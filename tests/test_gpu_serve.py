@@ -135,15 +135,15 @@ def test_faults_leave_the_loop_serving(env):
     the server keeps serving the others"""
     K, ctx = env["K"], env["ctx"]
     q, p, psi, delta = K.ckks_ctx_info(ctx)
-    spec, w = env["spec"], env["w"]
-    # a conv set whose rotations the keys lack: a 2-channel conv at a different width
-    W2 = WL.weights(9, 2, 2, 3, "normal")
-    conv2 = K.ckks_ptset_conv_fused(ctx, W2, 2, 2, 3, w // 2, 1, (2.0 ** 49 * q[1]) / delta[1])
-    assert set(K.ckks_ptset_rotations(conv2)) - set(env["rots"])
-    srv = K.ckks_server_create(ctx, env["keys"], 1, 0)
+    # keys without one rotation that the conv needs: the model cannot be added
+    need = K.ckks_ptset_rotations(env["conv"])
+    short = K.ckks_keygen(ctx, [r for r in env["rots"] if r != need[-1]], True)
+    srv_short = K.ckks_server_create(ctx, short, 1, 0)
     with pytest.raises(K.CkksError) as ei:
-        K.ckks_server_add_model(srv, [conv2], [env["bt"]])
+        K.ckks_server_add_model(srv_short, [env["conv"]], [env["bt"]])
     assert ei.value.code == K.CKKS_ENOKEY
+    srv_short.close()
+    srv = K.ckks_server_create(ctx, env["keys"], 1, 0)
     A = K.ckks_server_add_model(srv, [env["conv"]], [env["bt"]])
     K.ckks_server_start(srv)
     _, limbs = env["make_input"](4)
