@@ -232,6 +232,9 @@ void add_const_term(const ckks_ctx* c, u64* a, const u64* v, int nlimbs, const i
 void small_to_rns(const ckks_ctx* c, const int64_t* v, u64* o, int nlimbs, const int* ids);
 // o[i] = a[galois_src(i)] in the NTT domain
 void automorph(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, u64 g);
+// o[limb] += s[limb % lpp] * automorph_g(a[limb]) (s = nullptr: o += automorph_g(a)), NTT domain
+void automorph_acc(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, u64 g, const u64* s, const u64* sp,
+                   const int* ids, int lpp);
 // X^{N/2} times a, NTT domain: pointwise by psi^((2 rev(i)+1) N/2)
 void imult(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, const int* ids, int lpp);
 // centred lift of one coefficient-domain limb with prime `src_id` into nlimbs limbs

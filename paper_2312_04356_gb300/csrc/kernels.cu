@@ -704,6 +704,27 @@ __global__ void k_automorph(const u64* a, u64* o, u64 g, int logn) {
     const size_t off = (size_t)blockIdx.y << logn;
     EW_LOOP(1 << logn) o[off + j] = a[off + galois_src(j, g, logn)];
 }
+// o[limb][j] += s[limb % lpp] * a[limb][src_g(j)] (s null: plain add), NTT domain
+template <int V>
+__global__ void k_automorph_acc(const u64* a, u64* o, u64 g, const u64* s, const u64* sp, const DevPrime* P,
+                                const int* ids, int lpp, int logn) {
+    const int limb = blockIdx.y;
+    const int r = limb % lpp;
+    const u64 q = P[ids[r]].m.q;
+    const size_t off = (size_t)limb << logn;
+    EWV_BEGIN(1 << logn)
+    u64 z[V];
+    ldv<V>(o + off + j, z);
+    if (s) {
+        const u64 w = s[r], wp = sp[r];
+#pragma unroll
+        for (int v = 0; v < V; ++v) z[v] = add_mod(z[v], mul_shoup(a[off + galois_src(j + v, g, logn)], w, wp, q), q);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) z[v] = add_mod(z[v], a[off + galois_src(j + v, g, logn)], q);
+    }
+    stv<V>(o + off + j, z);
+}
 __global__ void k_imult(const u64* a, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
     const int limb = blockIdx.y;
     const DevPrime* pr = P + ids[limb % lpp];
@@ -1184,6 +1205,14 @@ void automorph(const ckks_ctx* c, const u64* a, u64* o, int nl, u64 g) {
     if (nl <= 0) return;
     { KTimer kt_(c, "automorph", 2.0 * (double)nl * c->n * 8.0);
     k_automorph<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, o, g, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void automorph_acc(const ckks_ctx* c, const u64* a, u64* o, int nl, u64 g, const u64* s, const u64* sp,
+                   const int* ids, int lpp) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "automorph_acc", 3.0 * (double)nl * c->n * 8.0);
+    EWV_LAUNCH(k_automorph_acc, al16(o), nl, a, o, g, s, sp, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }

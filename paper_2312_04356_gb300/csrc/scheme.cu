@@ -731,9 +731,7 @@ static std::vector<DevBuf> rotate_hoisted_ext(const ckks_keys& keys, const ckks_
             if (!D.ptr) D = mod_up(c, a.c1(), l, &ndig);
             c->ops["hrot"]++;
             key_switch_inner(c, keys, D.ptr, ndig, l, g, g, o.ptr, false);
-            DevBuf t((size_t)nl * n, c->stream);
-            kern::automorph(c, a.c0(), t.ptr, nl, g);
-            kern::mul_scalar_acc(c, t.ptr, c->d_pmod, c->d_pmod + c->nq, o.ptr, nl, c->d_iota, nl);
+            kern::automorph_acc(c, a.c0(), o.ptr, nl, g, c->d_pmod, c->d_pmod + c->nq, c->d_iota, nl);
         }
         outs.push_back(std::move(o));
     }
@@ -824,9 +822,7 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
         if (!have_acc) acc = DevBuf(2 * next * n, c->stream);
         key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, acc.ptr, have_acc);
         have_acc = true;
-        DevBuf t(next * n, c->stream);
-        kern::automorph(c, x, t.ptr, (int)next, gal);
-        kern::add(c, acc.ptr, t.ptr, acc.ptr, (int)next, ext, (int)next);
+        kern::automorph_acc(c, x, acc.ptr, (int)next, gal, nullptr, nullptr, ext, (int)next);
     }
     if (rescale_out) {
         ckks_ct o = new_ct(c, l - 1, scale / (double)c->q[l]);
