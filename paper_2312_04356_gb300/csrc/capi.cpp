@@ -1325,12 +1325,12 @@ int ckks_eval_relu(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, cons
 static int raw_ntt(ckks_ctx* ctx, uint64_t* dev, int n_limbs, const int32_t* ids, bool inv) {
     return guard(ctx, [&] {
         REQ(ctx);
+        CK_CHECK(n_limbs >= 0, CKKS_EINVAL, "negative limb count");
+        if (n_limbs == 0) return;      // nothing to transform (dev and ids may be NULL)
         REQ(dev);
         REQ(ids);
-        CK_CHECK(n_limbs >= 0, CKKS_EINVAL, "negative limb count");
         for (int i = 0; i < n_limbs; ++i)
             CK_CHECK(ids[i] >= 0 && ids[i] < ctx->nall, CKKS_EINVAL, "prime id out of range");
-        if (n_limbs == 0) return;
         std::vector<u64> tmp(n_limbs);
         DevBuf d((n_limbs + 1) / 2, ctx->stream);
         std::vector<int> v(ids, ids + n_limbs);
