@@ -405,7 +405,7 @@ def run_ours(args):
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                             "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
                         for k, v in sorted(kst.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
-    # key switching as % of HBM (the benchmark spec's second roofline): the inner product streams
+    # key switching as % of HBM (the second roofline this bench reports): the inner product streams
     # the digits and the switching key; ModUp / ModDown conversions and NTTs are reported above
     ks = kst.get("ks_inner")
     roof_ks = None

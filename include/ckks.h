@@ -354,7 +354,7 @@ int ckks_graph_destroy(ckks_graph* graph);
 
 /* ---- serving loop ----------------------------------------------------------------
  * Continuous batching of inference requests (no counterpart in the paper, whose
- * measurements are one image at a time; the benchmark spec asks for batched throughput).
+ * measurements are one image at a time; a server needs batched throughput).
  * A model is a chain of Alg. 1 blocks: block b runs ckks_block with convs[b], boots[b]
  * after a level drop of its input to convs[b]'s level.  For each of `slots` slots (a CUDA
  * stream, device and pinned staging buffers) and each model, ckks_server_add_model runs

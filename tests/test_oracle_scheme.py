@@ -158,7 +158,7 @@ def test_chebyshev_and_evalmod(small):
 @pytest.mark.slow
 def test_block_matches_fp64_conv():
     """Alg. 1 block (no activation) at N = 2^10 with the config-2 prime chain: decoded output
-    is the masked conv output within 2^-12 (spec accuracy bar)"""
+    is the masked conv output within 2^-12 (the accuracy bar of the GPU path)"""
     P = PP.Params(10, 24, 3, 60, 42, 60, h=192, n_p=7, boot_bits=48, n_boot=14)
     o = Oracle(P, 5)
     w0, w, f = 4, 8, 3
