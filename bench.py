@@ -230,9 +230,9 @@ def oracle_sample(seconds_budget, counts=None):
 
 # Operation counts of one config-2 block as the oracle runs it (EvalMod on both the Re and
 # the Im part, double-hoisted HMatmuls): 142 key switches (103 rotations, 38
-# relinearisations, 1 conjugation), 253 PMults, 139 rescales.  The library's counters report
+# relinearisations, 1 conjugation), 253 PMults, 101 rescales.  The library's counters report
 # the same numbers for the same steps (the GPU arm passes its live counts instead).
-BLOCK_OP_COUNTS = {"keyswitch": 142, "pmult": 253, "hrot": 103, "hmult": 38, "rescale": 139}
+BLOCK_OP_COUNTS = {"keyswitch": 142, "pmult": 253, "hrot": 103, "hmult": 38, "rescale": 101}
 
 
 def block_op_counts():

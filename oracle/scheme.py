@@ -645,35 +645,30 @@ class Oracle:
             need(k)
         return T, at
 
-    def cheb_leaf(self, T, coeffs):
-        """sum_k c_k T_k for a low-degree piece: terms grouped by the level of T_k; each group
-        is summed after multiplying by llround(c_k s_c), s_c = Delta_target q_lk / scale(T_k),
-        rescaled once and dropped to the target level (the lowest group's level - 1).
+    def cheb_leaf(self, T, at, coeffs):
+        """sum_k c_k T_k for a low-degree piece.  The target level is the lowest level among
+        its T_k minus one; every T_k is first brought to target + 1 by level_down (cached, so
+        the leaves of one polynomial share it), multiplied by llround(c_k s_c) with
+        s_c = Delta_target q_(target+1) / scale, summed and rescaled once.
         Returns a ciphertext, or a float when only the constant term is non-zero."""
         P = self.P
         ks = [k for k in range(1, len(coeffs)) if coeffs[k] != 0.0]
         if not ks:
             return float(coeffs[0])
-        target = min(T[k].level for k in ks) - 1
+        lev = min(T[k].level for k in ks)
+        target = lev - 1
         acc = None
-        for lev in sorted({T[k].level for k in ks}, reverse=True):
-            grp = None
-            scale = None
-            for k in ks:
-                t = T[k]
-                if t.level != lev:
-                    continue
-                s_c = (P.delta[target] * float(P.q[lev])) / t.scale
-                term = self.mul_int(t, round_half_away(coeffs[k] * s_c))
-                if grp is None:
-                    grp, scale = term, (t.scale * s_c) / float(P.q[lev])
-                else:
-                    grp = Ciphertext(C.add(grp.c0, term.c0, P.moduli(lev)), C.add(grp.c1, term.c1, P.moduli(lev)),
-                                     lev, grp.scale)
-            grp = self.rescale(grp)
-            grp.scale = scale
-            grp = self.mod_drop(grp, target)
-            acc = grp if acc is None else self.add(acc, grp)
+        for k in ks:
+            t = at(k, lev)
+            s_c = (P.delta[target] * float(P.q[lev])) / t.scale
+            term = self.mul_int(t, round_half_away(coeffs[k] * s_c))
+            if acc is None:
+                acc = term
+            else:
+                acc = Ciphertext(C.add(acc.c0, term.c0, P.moduli(lev)), C.add(acc.c1, term.c1, P.moduli(lev)),
+                                 lev, acc.scale)
+        acc = self.rescale(acc)
+        acc.scale = P.delta[target]
         return self.add_const(acc, coeffs[0])
 
     def cheb_eval(self, x, coeffs):
@@ -701,7 +696,7 @@ class Oracle:
                 deg -= 1
             c = c[: deg + 1]
             if deg < b:
-                return self.cheb_leaf(T, c)
+                return self.cheb_leaf(T, at, c)
             n = max(g for g in giants if g <= deg)
             q = [c[n]] + [2.0 * c[n + j] for j in range(1, deg - n + 1)]
             r = list(c[:n])

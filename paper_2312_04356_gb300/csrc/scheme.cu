@@ -888,9 +888,10 @@ struct PolyVal {
     ckks_ct ct;
 };
 
-// sum_k c_k T_k for a piece of degree < b: terms grouped by the level of T_k; each group is
-// summed after multiplying by llround(c_k s_c), s_c = Delta_target q_lk / scale(T_k),
-// rescaled once and dropped to the target level (the lowest group's level - 1).
+// sum_k c_k T_k for a piece of degree < b.  The target level is the lowest level among its
+// T_k minus one; every T_k is brought to target + 1 by level_down (cached in ChebPowers, so the
+// leaves of one polynomial share it), multiplied by llround(c_k s_c), s_c = Delta_target
+// q_(target+1) / scale, summed and rescaled once.
 static PolyVal cheb_leaf(ChebPowers& pw, const std::vector<double>& c) {
     ckks_ctx* ctx = pw.T.at(1).ctx;
     PolyVal out;
@@ -902,41 +903,25 @@ static PolyVal cheb_leaf(ChebPowers& pw, const std::vector<double>& c) {
         out.cst = c[0];
         return out;
     }
-    int target = 1 << 30;
-    std::set<int, std::greater<int>> levels;
-    for (int k : ks) {
-        target = std::min(target, pw.T.at(k).level - 1);
-        levels.insert(pw.T.at(k).level);
-    }
+    int lev = 1 << 30;
+    for (int k : ks) lev = std::min(lev, pw.T.at(k).level);
+    const int target = lev - 1;
     ckks_ct acc;
     bool have = false;
-    for (int lev : levels) {
-        ckks_ct grp;
-        bool hg = false;
-        double scale = 0;
-        for (int k : ks) {
-            const ckks_ct& t = pw.T.at(k);
-            if (t.level != lev) continue;
-            const double s_c = (ctx->delta[target] * (double)ctx->q[lev]) / t.scale;
-            ckks_ct term = mul_int(t, llround_away(c[k] * s_c));
-            if (!hg) {
-                grp = std::move(term);
-                scale = (t.scale * s_c) / (double)ctx->q[lev];
-                hg = true;
-            } else {
-                kern::add(ctx, grp.buf.ptr, term.buf.ptr, grp.buf.ptr, 2 * (lev + 1), ctx->d_iota, lev + 1);
-            }
-        }
-        grp = rescale(grp);
-        grp.scale = scale;
-        grp = mod_drop(grp, target);
+    for (int k : ks) {
+        const ckks_ct& t = pw.at(k, lev);
+        const double s_c = (ctx->delta[target] * (double)ctx->q[lev]) / t.scale;
+        const int64_t w = llround_away(c[k] * s_c);
         if (!have) {
-            acc = std::move(grp);
+            acc = mul_int(t, w);
             have = true;
         } else {
-            acc = add(acc, grp);
+            ckks_ct term = mul_int(t, w);
+            kern::add(ctx, acc.buf.ptr, term.buf.ptr, acc.buf.ptr, 2 * (lev + 1), ctx->d_iota, lev + 1);
         }
     }
+    acc = rescale(acc);
+    acc.scale = ctx->delta[target];
     out.ct = add_const(acc, c[0]);
     return out;
 }
