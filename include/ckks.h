@@ -120,6 +120,12 @@ int ckks_ctx_kernel_stats(ckks_ctx* ctx, char* buf, int cap, int* len);
 int ckks_autotune(ckks_ctx* ctx, int reps, int32_t* choice8);
 /* Use one NTT variant (0..4 as above) for every size, or -1 for the default rule. */
 int ckks_ctx_set_ntt_variant(ckks_ctx* ctx, int variant);
+/* Launch mode of the context's kernels.  on != 0 (the default): kernels launched outside a
+ * CUDA graph capture use programmatic stream serialization, so the next kernel is set up
+ * while the previous one drains; each kernel waits for its predecessors to complete before
+ * its first memory access, so results are identical either way.  Captured launches are
+ * always plain.  on == 0: plain launches everywhere. */
+int ckks_ctx_set_pdl(ckks_ctx* ctx, int on);
 
 /* ---- keys (Sec. 2.1 KeyGen) ----------------------------------------------- */
 /* Secret key s (h-sparse or uniform ternary), public key (-a s + e, a) over Q_L,

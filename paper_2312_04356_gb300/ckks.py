@@ -60,6 +60,7 @@ _SIGS = {
     "ckks_ctx_info": [VP, VP, VP, VP, VP],
     "ckks_ctx_gauss_table": [VP, VP],
     "ckks_ctx_set_timing": [VP, I],
+    "ckks_ctx_set_pdl": [VP, I],
     "ckks_ctx_counters": [VP, VP],
     "ckks_ctx_reset_counters": [VP],
     "ckks_ctx_kernel_stats": [VP, VP, I, VP],
@@ -303,6 +304,10 @@ def ckks_ctx_gauss_table(ctx):
 
 def ckks_ctx_set_timing(ctx, on):
     ctx.check(lib().ckks_ctx_set_timing(ctx, int(on)))
+
+
+def ckks_ctx_set_pdl(ctx, on):
+    ctx.check(lib().ckks_ctx_set_pdl(ctx, int(on)))
 
 
 def ckks_ctx_counters(ctx):

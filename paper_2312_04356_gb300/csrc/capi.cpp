@@ -211,6 +211,13 @@ int ckks_ctx_set_timing(ckks_ctx* ctx, int on) {
     });
 }
 
+int ckks_ctx_set_pdl(ckks_ctx* ctx, int on) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        ctx->pdl = on != 0;
+    });
+}
+
 int ckks_ctx_counters(const ckks_ctx* ctx, int64_t* out) {
     return guard(ctx, [&] {
         REQ(ctx);

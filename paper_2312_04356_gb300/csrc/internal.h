@@ -100,6 +100,9 @@ struct ckks_ctx {
     std::map<int, std::unique_ptr<ConvTab>> mdrs_tabs;                  // level: {q_l, P} -> Q_{l-1}
     std::string err;
     int ntt_choice[8] = {-1, -1, -1, -1, -1, -1, -1, -1};   // tuned NTT variant per limb-count class
+    // eager kernels are launched with programmatic stream serialization: the next launch in
+    // the stream is set up while this one drains, and waits for it before touching memory
+    bool pdl = true;
     std::map<std::string, long> ops;   // op counters (PMult, HRot, keyswitch, ...)
     // measurement: kernel launch count and, when timing is on, CUDA events around launches
     mutable long long launches = 0;

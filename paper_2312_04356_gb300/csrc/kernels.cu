@@ -5,6 +5,33 @@
 // grid (blockIdx.y) is one limb, so the modulus is uniform inside a CTA.
 #include "internal.h"
 
+// ------------------------------------------------- dependent launches ----
+// Every kernel of this file begins with griddep_entry(): it waits until the grids it depends
+// on have completed and their writes are visible (griddepcontrol.wait; a no-op for a plain
+// launch).  With that wait ahead of every memory access, a launch with programmatic stream
+// serialization keeps stream order while the next grid is set up as the previous one
+// drains, which hides most of the launch latency of eager calls.  Inside a CUDA graph
+// capture the launches stay plain: a graph already removes that latency, and programmatic
+// edges measured slightly slower there.
+__device__ __forceinline__ void griddep_entry() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+static inline void klaunch(const ckks_ctx* c, void (*k)(P...), dim3 grid, dim3 block, size_t smem, A... args) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (c->pdl) cudaStreamIsCapturing(c->stream, &cs);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = (c->pdl && cs == cudaStreamCaptureStatusNone) ? 1 : 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // ------------------------------------------------------------ DevBuf -------
 DevBuf::DevBuf(size_t w, cudaStream_t s) : words(w), stream(s) {
     if (w) {
@@ -99,9 +126,9 @@ inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 #define EWV_LAUNCH(K, vec, nl, ...)                                                          \
     do {                                                                                     \
         if (vec)                                                                             \
-            K<2><<<ewv_grid(c->n, (nl), 2), EW_THREADS, 0, c->stream>>>(__VA_ARGS__);        \
+            klaunch(c, K<2>, ewv_grid(c->n, (nl), 2), EW_THREADS, 0, __VA_ARGS__);        \
         else                                                                                 \
-            K<1><<<ewv_grid(c->n, (nl), 1), EW_THREADS, 0, c->stream>>>(__VA_ARGS__);        \
+            klaunch(c, K<1>, ewv_grid(c->n, (nl), 1), EW_THREADS, 0, __VA_ARGS__);        \
     } while (0)
 
 // ------------------------------------------------------------------ NTT ----
@@ -117,6 +144,7 @@ template <bool INV>
 __global__ void __launch_bounds__(NTT_THREADS)
     k_ntt_pass(u64* __restrict__ data, const DevPrime* __restrict__ primes, const int* __restrict__ ids, int lpp,
                int logn, int s0, int c, int logsub, int scale_out) {
+    griddep_entry();
     extern __shared__ u64 sm[];
     const int limb = blockIdx.y;
     const DevPrime* P = primes + ids[limb % lpp];
@@ -272,6 +300,7 @@ template <bool COL, bool INV, int SUBS, int MINB>
 __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ data, const DevPrime* __restrict__ primes,
                                                     const int* __restrict__ ids, int lpp, size_t pstride,
                                                     const int* __restrict__ loff) {
+    griddep_entry();
     __shared__ u64 sm[SUBS * F_STRIDE];
     const int limb = blockIdx.y;
     const int r = loff ? limb : limb % lpp;
@@ -359,6 +388,7 @@ template <bool COL, bool INV>
 __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const DevPrime* __restrict__ primes,
                                                 const int* __restrict__ ids, int lpp, size_t pstride,
                                                 const int* __restrict__ loff) {
+    griddep_entry();
     __shared__ u64 sm[4 * F_STRIDE];
     const int limb = blockIdx.y;
     const int r = loff ? limb : limb % lpp;
@@ -475,24 +505,24 @@ void launch_ntt16_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, cons
                           size_t pstride, const int* loff) {
     switch (v) {
         case NTT_V16_R80:
-            k_ntt16<COL, INV, 16, 3>
-                <<<dim3(256 / 16, nlimbs), 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
+            klaunch(cx, k_ntt16<COL, INV, 16, 3>, dim3(256 / 16, nlimbs), 256, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff);
             break;
         case NTT_V16_R64:
-            k_ntt16<COL, INV, 16, 4>
-                <<<dim3(256 / 16, nlimbs), 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
+            klaunch(cx, k_ntt16<COL, INV, 16, 4>, dim3(256 / 16, nlimbs), 256, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff);
             break;
         case NTT_V4_R80:
-            k_ntt16<COL, INV, 4, 8>
-                <<<dim3(256 / 4, nlimbs), 64, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
+            klaunch(cx, k_ntt16<COL, INV, 4, 8>, dim3(256 / 4, nlimbs), 64, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff);
             break;
         case NTT_V4_R64:
-            k_ntt16<COL, INV, 4, 12>
-                <<<dim3(256 / 4, nlimbs), 64, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride, loff);
+            klaunch(cx, k_ntt16<COL, INV, 4, 12>, dim3(256 / 4, nlimbs), 64, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff);
             break;
         default:
-            k_ntt16s<COL, INV><<<dim3(256 / 4, nlimbs), 256, 0, cx->stream>>>(data, cx->d_primes, ids, lpp, pstride,
-                                                                             loff);
+            klaunch(cx, k_ntt16s<COL, INV>, dim3(256 / 4, nlimbs), 256, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff);
             break;
     }
 }
@@ -533,8 +563,8 @@ void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int 
     const size_t smem = (size_t)stride * (1 << p.c) * sizeof(u64);
     dim3 grid(tiles, nlimbs);
     { KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0);
-    k_ntt_pass<INV><<<grid, NTT_THREADS, smem, cx->stream>>>(data, cx->d_primes, ids, lpp, logn, p.s0, p.c, logsub,
-                                                             scale_out);
+    klaunch(cx, k_ntt_pass<INV>, grid, NTT_THREADS, smem, data, cx->d_primes, ids, lpp, logn, p.s0, p.c, logsub,
+            scale_out);
     }
 }
 
@@ -565,6 +595,7 @@ __device__ __forceinline__ void stv(u64* p, const u64 (&r)[V]) {
 
 template <int V>
 __global__ void k_add(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const u64 q = P[ids[limb % lpp]].m.q;
     const size_t off = (size_t)limb << logn;
@@ -578,6 +609,7 @@ __global__ void k_add(const u64* a, const u64* b, u64* o, const DevPrime* P, con
 }
 template <int V>
 __global__ void k_sub(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const u64 q = P[ids[limb % lpp]].m.q;
     const size_t off = (size_t)limb << logn;
@@ -591,6 +623,7 @@ __global__ void k_sub(const u64* a, const u64* b, u64* o, const DevPrime* P, con
 }
 template <int V>
 __global__ void k_neg(const u64* a, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const u64 q = P[ids[limb % lpp]].m.q;
     const size_t off = (size_t)limb << logn;
@@ -603,6 +636,7 @@ __global__ void k_neg(const u64* a, u64* o, const DevPrime* P, const int* ids, i
 }
 template <int V>
 __global__ void k_mul(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const DevMod m = P[ids[limb % lpp]].m;
     const size_t off = (size_t)limb << logn;
@@ -616,6 +650,7 @@ __global__ void k_mul(const u64* a, const u64* b, u64* o, const DevPrime* P, con
 }
 template <int V>
 __global__ void k_mul_acc(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const DevMod m = P[ids[limb % lpp]].m;
     const size_t off = (size_t)limb << logn;
@@ -631,6 +666,7 @@ __global__ void k_mul_acc(const u64* a, const u64* b, u64* o, const DevPrime* P,
 template <int V>
 __global__ void k_mul_scalar(const u64* a, const u64* s, const u64* sp, u64* o, const DevPrime* P, const int* ids,
                              int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
@@ -647,6 +683,7 @@ __global__ void k_mul_scalar(const u64* a, const u64* s, const u64* sp, u64* o, 
 template <int V>
 __global__ void k_mul_scalar_v(const u64* a, ScalarVec sv, u64* o, const DevPrime* P, const int* ids, int lpp,
                                int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
@@ -661,6 +698,7 @@ __global__ void k_mul_scalar_v(const u64* a, ScalarVec sv, u64* o, const DevPrim
 }
 template <int V>
 __global__ void k_add_scalar_v(u64* a, ScalarVec sv, const DevPrime* P, const int* ids, int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
@@ -675,6 +713,7 @@ __global__ void k_add_scalar_v(u64* a, ScalarVec sv, const DevPrime* P, const in
 }
 template <int V>
 __global__ void k_add_scalar(u64* a, const u64* vals, const DevPrime* P, const int* ids, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const u64 q = P[ids[limb]].m.q;
     const u64 c = vals[limb];
@@ -687,6 +726,7 @@ __global__ void k_add_scalar(u64* a, const u64* vals, const DevPrime* P, const i
     stv<V>(a + off + j, x);
 }
 __global__ void k_small_to_rns(const int64_t* v, u64* o, const DevPrime* P, const int* ids, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const DevMod m = P[ids[limb]].m;
     const size_t off = (size_t)limb << logn;
@@ -701,6 +741,7 @@ __global__ void k_small_to_rns(const int64_t* v, u64* o, const DevPrime* P, cons
     }
 }
 __global__ void k_automorph(const u64* a, u64* o, u64 g, int logn) {
+    griddep_entry();
     const size_t off = (size_t)blockIdx.y << logn;
     EW_LOOP(1 << logn) o[off + j] = a[off + galois_src(j, g, logn)];
 }
@@ -708,6 +749,7 @@ __global__ void k_automorph(const u64* a, u64* o, u64 g, int logn) {
 template <int V>
 __global__ void k_automorph_acc(const u64* a, u64* o, u64 g, const u64* s, const u64* sp, const DevPrime* P,
                                 const int* ids, int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
@@ -726,6 +768,7 @@ __global__ void k_automorph_acc(const u64* a, u64* o, u64 g, const u64* s, const
     stv<V>(o + off + j, z);
 }
 __global__ void k_imult(const u64* a, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const DevPrime* pr = P + ids[limb % lpp];
     const u64 q = pr->m.q;
@@ -741,6 +784,7 @@ __global__ void k_imult(const u64* a, u64* o, const DevPrime* P, const int* ids,
 }
 template <int V>
 __global__ void k_lift_centred(const u64* src, u64 qs, u64* o, const DevPrime* P, const int* ids, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const DevMod t = P[ids[limb]].m;
     const size_t off = (size_t)limb << logn;
@@ -754,6 +798,7 @@ __global__ void k_lift_centred(const u64* src, u64 qs, u64* o, const DevPrime* P
 template <int V>
 __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const u64* sp, u64* o,
                                  const DevPrime* P, const int* ids, int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
@@ -777,6 +822,7 @@ __device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P)
 template <int V>
 __global__ void k_bsgs_inner(kern::BsgsTerms T, u64* __restrict__ o, const DevPrime* __restrict__ primes, int nl,
                              const int* __restrict__ ids, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;           // 0 .. 2 nl - 1, polynomial-major
     const int r = limb % nl;
     const DevPrime P = primes[ids[r]];
@@ -821,6 +867,7 @@ constexpr int CONV_OUT = 8;
 // then reduced as in the general path.
 template <int MAXIN, bool SPLIT>
 __global__ void __launch_bounds__(256, 3) k_base_convert(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn) {
+    griddep_entry();
     __shared__ u64 s_qi[MAX_CONV_IN], s_qinv[MAX_CONV_IN], s_qinvp[MAX_CONV_IN];
     __shared__ u64 s_c[CONV_OUT][MAX_CONV_IN];
     __shared__ DevPrime s_pm[CONV_OUT];
@@ -938,6 +985,7 @@ template <bool ACC, int V>
 __global__ void k_ks_inner(const u64* __restrict__ D, int ndig, int next, const int* __restrict__ ext_ids,
                            const u64* __restrict__ kb, const u64* __restrict__ ka, u64* __restrict__ ob,
                            u64* __restrict__ oa, const DevPrime* __restrict__ P, int logn, u64 g, size_t kstride) {
+    griddep_entry();
     const int e = blockIdx.y;
     const int id = ext_ids[e];
     const DevMod m = P[id].m;
@@ -976,10 +1024,68 @@ __global__ void k_ks_inner(const u64* __restrict__ D, int ndig, int next, const 
     stv<V>(oa + (size_t)e * n + j, acca);
 }
 
+// The same product for a digit count fixed at compile time: every digit's key words and
+// gathered input are loaded before any arithmetic, the products are summed exactly in 128 bits
+// (each < 2^122, at most 4 terms) and reduced once per output word.
+template <bool ACC, int V, int NDIG>
+__global__ void k_ks_inner_d(const u64* __restrict__ D, int next, const int* __restrict__ ext_ids,
+                             const u64* __restrict__ kb, const u64* __restrict__ ka, u64* __restrict__ ob,
+                             u64* __restrict__ oa, const DevPrime* __restrict__ P, int logn, u64 g, size_t kstride) {
+    griddep_entry();
+    const int e = blockIdx.y;
+    const int id = ext_ids[e];
+    const DevPrime pr = P[id];
+    const size_t n = (size_t)1 << logn;
+    EWV_BEGIN(1 << logn)
+    unsigned src[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) src[v] = g == 1 ? (unsigned)(j + v) : galois_src(j + v, g, logn);
+    u64 x[NDIG][V], yb[NDIG][V], ya[NDIG][V];
+#pragma unroll
+    for (int d = 0; d < NDIG; ++d) {
+        const u64* Dd = D + ((size_t)d * next + e) * n;
+        const size_t kk = d * kstride + (size_t)id * n + j;
+        ldv<V>(kb + kk, yb[d]);
+        ldv<V>(ka + kk, ya[d]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[d][v] = Dd[src[v]];
+    }
+    u64 rb[V], ra[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        u64 bl = 0, bh = 0, al = 0, ah = 0;
+#pragma unroll
+        for (int d = 0; d < NDIG; ++d) {
+            const u64 pbl = x[d][v] * yb[d][v], pal = x[d][v] * ya[d][v];
+            bh += __umul64hi(x[d][v], yb[d][v]);
+            ah += __umul64hi(x[d][v], ya[d][v]);
+            bl += pbl;
+            bh += bl < pbl ? 1ull : 0ull;
+            al += pal;
+            ah += al < pal ? 1ull : 0ull;
+        }
+        rb[v] = reduce128_lazy(bh, bl, pr);
+        ra[v] = reduce128_lazy(ah, al, pr);
+    }
+    if (ACC) {
+        u64 pb[V], pa[V];
+        ldv<V>(ob + (size_t)e * n + j, pb);
+        ldv<V>(oa + (size_t)e * n + j, pa);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            rb[v] = add_mod(rb[v], pb[v], pr.m.q);
+            ra[v] = add_mod(ra[v], pa[v], pr.m.q);
+        }
+    }
+    stv<V>(ob + (size_t)e * n + j, rb);
+    stv<V>(oa + (size_t)e * n + j, ra);
+}
+
 // o += a * s[limb % lpp] (Shoup pairs s, sp)
 template <int V>
 __global__ void k_mul_scalar_acc(const u64* a, const u64* s, const u64* sp, u64* o, const DevPrime* P, const int* ids,
                                  int lpp, int logn) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
@@ -1003,6 +1109,7 @@ __device__ __forceinline__ u64 d_mix(u64 z) {
 __device__ __forceinline__ u64 d_word(u64 key, u64 i) { return d_mix(key + (i + 1) * 0x9E3779B97F4A7C15ULL); }
 
 __global__ void k_sample_uniform(u64* o, const DevPrime* P, const int* ids, int logn, u64 key) {
+    griddep_entry();
     const int limb = blockIdx.y;
     const int id = ids[limb];
     const DevMod m = P[id].m;
@@ -1015,6 +1122,7 @@ __global__ void k_sample_uniform(u64* o, const DevPrime* P, const int* ids, int 
     }
 }
 __global__ void k_sample_small(int64_t* o, int logn, u64 key, int kind, const u64* gauss) {
+    griddep_entry();
     EW_LOOP(1 << logn) {
         const u64 w = d_word(key, (u64)j);
         if (kind == 0) {
@@ -1197,14 +1305,14 @@ void add_const_term(const ckks_ctx* c, u64* a, const u64* v, int nl, const int* 
 void small_to_rns(const ckks_ctx* c, const int64_t* v, u64* o, int nl, const int* ids) {
     if (nl <= 0) return;
     { KTimer kt_(c, "small_to_rns", (nl + 1.0) * c->n * 8.0);
-    k_small_to_rns<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(v, o, c->d_primes, ids, c->logn);
+    klaunch(c, k_small_to_rns, ew_grid(c->n, nl), EW_THREADS, 0, v, o, c->d_primes, ids, c->logn);
     }
     LAUNCH_CHECK();
 }
 void automorph(const ckks_ctx* c, const u64* a, u64* o, int nl, u64 g) {
     if (nl <= 0) return;
     { KTimer kt_(c, "automorph", 2.0 * (double)nl * c->n * 8.0);
-    k_automorph<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, o, g, c->logn);
+    klaunch(c, k_automorph, ew_grid(c->n, nl), EW_THREADS, 0, a, o, g, c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -1219,7 +1327,7 @@ void automorph_acc(const ckks_ctx* c, const u64* a, u64* o, int nl, u64 g, const
 void imult(const ckks_ctx* c, const u64* a, u64* o, int nl, const int* ids, int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "imult", 2.0 * (double)nl * c->n * 8.0);
-    k_imult<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(a, o, c->d_primes, ids, lpp, c->logn);
+    klaunch(c, k_imult, ew_grid(c->n, nl), EW_THREADS, 0, a, o, c->d_primes, ids, lpp, c->logn);
     }
     LAUNCH_CHECK();
 }
@@ -1280,36 +1388,62 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly) {
     dim3 grid((c->n + 255) / 256, npoly, groups);
     { KTimer kt_(c, "base_convert", bytes);
     if (maxin <= 4)
-        k_base_convert<4, false><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+        klaunch(c, k_base_convert<4, false>, grid, 256, 0, J, c->d_primes, c->logn);
     else if (maxin <= 8 && c->mods_below_2_60)
-        k_base_convert<8, true><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+        klaunch(c, k_base_convert<8, true>, grid, 256, 0, J, c->d_primes, c->logn);
     else if (maxin <= 8)
-        k_base_convert<8, false><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+        klaunch(c, k_base_convert<8, false>, grid, 256, 0, J, c->d_primes, c->logn);
     else
-        k_base_convert<MAX_CONV_IN, false><<<grid, 256, 0, c->stream>>>(J, c->d_primes, c->logn);
+        klaunch(c, k_base_convert<MAX_CONV_IN, false>, grid, 256, 0, J, c->d_primes, c->logn);
     }
     LAUNCH_CHECK();
+}
+
+template <bool ACC, int V>
+static void launch_ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
+                            const u64* ka, u64* ob, u64* oa, u64 g) {
+    const dim3 grid = ewv_grid(c->n, next, V);
+    const size_t ks = (size_t)c->nall << c->logn;
+    switch (ndig) {
+        case 1:
+            klaunch(c, k_ks_inner_d<ACC, V, 1>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
+                    c->logn, g, ks);
+            break;
+        case 2:
+            klaunch(c, k_ks_inner_d<ACC, V, 2>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
+                    c->logn, g, ks);
+            break;
+        case 3:
+            klaunch(c, k_ks_inner_d<ACC, V, 3>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
+                    c->logn, g, ks);
+            break;
+        case 4:
+            klaunch(c, k_ks_inner_d<ACC, V, 4>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
+                    c->logn, g, ks);
+            break;
+        default:
+            klaunch(c, k_ks_inner<ACC, V>, grid, EW_THREADS, 0, D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes,
+                    c->logn, g, ks);
+            break;
+    }
 }
 
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
               const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate) {
     const bool vec = al16(kb) && al16(ka) && al16(ob) && al16(oa);
-    if (accumulate) {
-        KTimer kt_(c, "ks_inner", (3.0 * ndig + 4.0) * next * c->n * 8.0);
-        if (vec)
-            k_ks_inner<true, 2><<<ewv_grid(c->n, next, 2), EW_THREADS, 0, c->stream>>>(
-                D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes, c->logn, g, (size_t)c->nall << c->logn);
-        else
-            k_ks_inner<true, 1><<<ewv_grid(c->n, next, 1), EW_THREADS, 0, c->stream>>>(
-                D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes, c->logn, g, (size_t)c->nall << c->logn);
-    } else {
-        KTimer kt_(c, "ks_inner", (3.0 * ndig + 2.0) * next * c->n * 8.0);
-        if (vec)
-            k_ks_inner<false, 2><<<ewv_grid(c->n, next, 2), EW_THREADS, 0, c->stream>>>(
-                D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes, c->logn, g, (size_t)c->nall << c->logn);
-        else
-            k_ks_inner<false, 1><<<ewv_grid(c->n, next, 1), EW_THREADS, 0, c->stream>>>(
-                D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes, c->logn, g, (size_t)c->nall << c->logn);
+    {
+        KTimer kt_(c, "ks_inner", (3.0 * ndig + (accumulate ? 4.0 : 2.0)) * next * c->n * 8.0);
+        if (accumulate) {
+            if (vec)
+                launch_ks_inner<true, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g);
+            else
+                launch_ks_inner<true, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g);
+        } else {
+            if (vec)
+                launch_ks_inner<false, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g);
+            else
+                launch_ks_inner<false, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g);
+        }
     }
     LAUNCH_CHECK();
 }
@@ -1324,13 +1458,13 @@ void mul_scalar_acc(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp
 void sample_uniform(const ckks_ctx* c, u64* o, int nl, const int* ids, u64 key) {
     if (nl <= 0) return;
     { KTimer kt_(c, "sample_uniform", (double)nl * c->n * 8.0);
-    k_sample_uniform<<<ew_grid(c->n, nl), EW_THREADS, 0, c->stream>>>(o, c->d_primes, ids, c->logn, key);
+    klaunch(c, k_sample_uniform, ew_grid(c->n, nl), EW_THREADS, 0, o, c->d_primes, ids, c->logn, key);
     }
     LAUNCH_CHECK();
 }
 void sample_small(const ckks_ctx* c, int64_t* o, u64 key, int kind) {
     { KTimer kt_(c, "sample_small", c->n * 8.0);
-    k_sample_small<<<ew_grid(c->n, 1), EW_THREADS, 0, c->stream>>>(o, c->logn, key, kind, c->d_gauss);
+    klaunch(c, k_sample_small, ew_grid(c->n, 1), EW_THREADS, 0, o, c->logn, key, kind, c->d_gauss);
     }
     LAUNCH_CHECK();
 }

@@ -240,7 +240,8 @@ def _pixels(d, slots):
 
 def test_block_small_bitexact():
     """the whole Alg. 1 block (conv -> ModRaise -> CtoS -> EvalMod x2 -> mask -> StoC1) on the
-    config-2 chain at N = 2^10: bit-exact ciphertext and decoded error <= 2^-12"""
+    config-2 chain at N = 2^10: bit-exact ciphertext and decoded error <= 2^-12, with
+    dependent (default) and plain kernel launches"""
     d = _block_pair("cfg2_small", 31)
     K, o, ctx, keys = d["K"], d["o"], d["ctx"], d["keys"]
     ct = o.encrypt(d["pt"], 2)
@@ -258,6 +259,10 @@ def test_block_small_bitexact():
     assert_ct_equal(K, ctx, gout, out, "StoC1")
     gblk = K.ckks_block(ctx, keys, gct, gplan, d["bt"])
     assert_ct_equal(K, ctx, gblk, out, "block")
+    K.ckks_ctx_set_pdl(ctx, 0)                     # plain launches: the same residues
+    gblk0 = K.ckks_block(ctx, keys, gct, gplan, d["bt"])
+    K.ckks_ctx_set_pdl(ctx, 1)
+    assert (K.ckks_ct_export_rns(ctx, gblk0) == K.ckks_ct_export_rns(ctx, gblk)).all()
     zexp, _ = _expected_slots(d)
     got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gblk))
     assert np.abs(_pixels(d, got) - _pixels(d, zexp)).max() < 2.0 ** -12
