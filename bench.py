@@ -135,8 +135,36 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
 
 
+# Integer-multiply roofline of the N = 2^16 NTT.  A 64-bit Shoup butterfly needs a 64x64 high
+# product (four 32x32 -> 64 partial products) and two 64x64 low products (one 32x32 -> 64 and
+# two 32x32 -> 32 each): 6 wide + 4 narrow 32-bit multiplies, 16 lane-cycles of the integer
+# multiply (fmaheavy) pipe counting a wide product as two.  That pipe retires 16 lanes per
+# SM sub-partition per clock, 64 per SM: peak butterflies/s = 64 * SMs * clock / 16.  Each
+# k_ntt16 pass of one limb does 8 stages of N/2 butterflies and moves 2 N 8 algorithmic bytes,
+# so a pass's butterflies are its algorithmic bytes / 4.
+NTT_MUL_LANE_CYCLES_PER_BUTTERFLY = 16
+GB300_SMS = 152
+
+
+def ntt_alu_roofline(kst, pk):
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    peak = 64.0 * GB300_SMS * mhz * 1e6 / NTT_MUL_LANE_CYCLES_PER_BUTTERFLY / 1e9     # G butterflies/s
+    out = {"bound": "alu", "pipe": "integer multiply (fmaheavy)", "unit": "Gbutterfly/s",
+           "peak": round(peak, 1), "peak_source": "152 SMs x 64 multiply lanes x %.0f MHz / %d lane-cycles "
+           "per 64-bit Shoup butterfly (derived)" % (mhz, NTT_MUL_LANE_CYCLES_PER_BUTTERFLY)}
+    for k in ("ntt_fwd", "ntt_inv"):
+        v = kst.get(k)
+        if v:
+            ach = v["bytes"] / 4.0 / (v["ms"] * 1e-3) / 1e9
+            out[k] = {"achieved": round(ach, 1), "frac": round(ach / peak, 4)}
+    return out
+
+
 # ------------------------------------------------------------- workload -----
-def block_setup(K, torch, seed=1):
+def block_setup(K, torch, seed=1, tune=False):
+    """context, conv plan, bootstrapping configuration, keys and one encrypted input of the
+    config-2 block; with tune, the NTT launch variants and then the BSGS split of every
+    bootstrapping level are autotuned before the keys are generated"""
     d = WL.PARAMS[CONFIG]
     spec = WL.CONV[CONFIG]
     w = 1
@@ -145,6 +173,11 @@ def block_setup(K, torch, seed=1):
     ctx = K.ckks_ctx_create(d, seed, torch.cuda.current_stream().cuda_stream)
     q, p, psi, delta = K.ckks_ctx_info(ctx)
     bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
+    tuned = {}
+    if tune:
+        tuned["ntt_variant_per_size_class"] = K.ckks_autotune(ctx, 3)
+        tuned["bsgs_B_default"] = K.ckks_boot_bsgs_splits(bt)
+        tuned["bsgs_B"] = K.ckks_boot_tune_bsgs(ctx, bt, 3)
     delta0 = 2.0 ** 49
     x = WL.image(seed, spec["cin"], spec["w0"])
     W = WL.weights(seed, spec["cout"], spec["cin"], spec["f"], spec["weight"])
@@ -153,7 +186,7 @@ def block_setup(K, torch, seed=1):
     keys = K.ckks_keygen(ctx, rots, True)
     ct = K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, x, w, 1, delta[1]), 1)
     K.ckks_sync(ctx)
-    return dict(ctx=ctx, keys=keys, bt=bt, conv=conv, ct=ct, x=x, W=W, w=w, spec=spec, rots=rots)
+    return dict(ctx=ctx, keys=keys, bt=bt, conv=conv, ct=ct, x=x, W=W, w=w, spec=spec, rots=rots, tuned=tuned)
 
 
 def check_accuracy(K, s, out):
@@ -276,9 +309,9 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()          # graphs cannot be captured on the legacy default stream
     torch.cuda.set_stream(stream)
-    s = block_setup(K, torch, seed=1 + rank)
+    s = block_setup(K, torch, seed=1 + rank, tune=True)
     ctx = s["ctx"]
-    tuned = K.ckks_autotune(ctx, 3)
+    tuned = s["tuned"]
     out = K.ckks_ct_create(ctx)
     for _ in range(args.warmup):
         K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
@@ -414,6 +447,7 @@ def run_ours(args):
         roof_ks = {"kernel": "ks_inner", "bound": "hbm", "achieved": round(ks_gbs, 1), "peak": pk.get("hbm_gbs"),
                    "unit": "GB/s", "frac": round(ks_gbs / pk.get("hbm_gbs"), 4), "launches": ks["launches"],
                    "share": round(ks["ms"] / total, 4)}
+    roof_alu = ntt_alu_roofline(kst, pk)
     if rank != 0:
         return
     cpu = None
@@ -433,10 +467,10 @@ def run_ours(args):
                        "execution": "CUDA graph replay of the block",
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "gpu_launches": launches, "launches_per_block": per_graph,
-            "batched": batched, "autotune_ntt_variant_per_size_class": tuned,
+            "batched": batched, "autotune": tuned,
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(host_in.nbytes),
                     "d2h_bytes_per_step": int(host_out.nbytes)},
-            "roofline": roof, "roofline_keyswitch": roof_ks, "op_counts": counts,
+            "roofline": roof, "roofline_keyswitch": roof_ks, "roofline_ntt_alu": roof_alu, "op_counts": counts,
             "op_counts_without_zero_mask_skip": counts_full,
             "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
@@ -651,6 +685,12 @@ def run_kernel_ntt(args):
         ok = ok and bool((dev.cpu().numpy().view(np.uint64) == x).all())
         res[variant] = {k: {"launches": v["launches"], "us_per_launch": round(1e3 * v["ms"] / v["launches"], 2),
                             "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)} for k, v in st.items()}
+        alu = ntt_alu_roofline(st, peaks())
+        for k in ("ntt_fwd", "ntt_inv"):
+            if k in res[variant] and k in alu:
+                res[variant][k]["hbm_frac"] = round(res[variant][k]["GBps"] / peaks()["hbm_gbs"], 4)
+                res[variant][k]["Gbutterfly_s"] = alu[k]["achieved"]
+                res[variant][k]["alu_frac"] = alu[k]["frac"]
     print(json.dumps({"kernel": "ntt", "limbs": nl, "N": ctx.n, "roundtrip_exact": ok, "per_variant": res}))
 
 

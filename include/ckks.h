@@ -314,6 +314,25 @@ int ckks_boot_destroy(ckks_boot* bt);
 /* info[0..7] = K_eff, s_raise, c_drop, l_drop, l_em, l_out, s_em, s_mask */
 int ckks_boot_info(const ckks_boot* bt, double* info8);
 int ckks_boot_rotations(const ckks_boot* bt, int32_t* steps, int cap, int* n_out);
+/* ---- BSGS split per level (Sec. 2.6: an HMatmul with `count` diagonals as B baby steps
+ * and ceil(count / B) giant steps).  Levels in evaluation order: the CtoS levels, the
+ * stride-2 decomposition (if any), the StoC1 levels; n_out receives their number.
+ * ckks_boot_create picks B by the cost model (B - 1) + 5 (G - 1) (HRots, a giant step
+ * costing about five baby rotations under double hoisting).  The rotation keys a block
+ * needs (ckks_boot_rotations) follow the splits in force. */
+int ckks_boot_bsgs_splits(const ckks_boot* bt, int32_t* B, int cap, int* n_out);
+/* Rebuild every level's plan with the given baby-step counts, 1 <= B[i] <= 32 (B above the
+ * level's diagonal count means one giant step); n must equal the number of levels.
+ * CKKS_EINVAL otherwise (plans unchanged). */
+int ckks_boot_set_bsgs_splits(ckks_ctx* ctx, ckks_boot* bt, const int32_t* B, int n);
+/* Autotuner: per level, times one HMatmul with rescale for B in {2, 4, ..., 32} (up to the
+ * level's diagonal count) and the cost-model choice, `reps` runs each after one warm-up,
+ * on a fresh encryption at the level's input level, with temporary switching keys for the
+ * candidates' rotations (freed before the next level: at N = 2^16 a few GB at a time), and
+ * keeps the fastest plan.  B_out (may be NULL, cap entries) receives the chosen counts.
+ * Run it before generating the keys a block will use.  Op and launch counters are left
+ * unchanged; synchronises the stream. */
+int ckks_boot_tune_bsgs(ckks_ctx* ctx, ckks_boot* bt, int reps, int32_t* B_out, int cap, int* n_out);
 /* replace one CtoS / StoC1 level, the EvalMod coefficients, or the masks
  * (used to feed identical plaintexts to two implementations) */
 int ckks_boot_set_ctos(ckks_ctx* ctx, ckks_boot* bt, int i, const ckks_ptset* ps);

@@ -40,7 +40,8 @@ from .scheme import Oracle, boot_bsgs_B, round_half_away
 
 class BootConfig:
     def __init__(self, orc: Oracle, w, w0, cout, K=28, r=3, deg=59, ctos_levels=3,
-                 stoc_levels=3, delta0=2.0 ** 49, ctos_B=None, stoc_B=None, coeffs=None, stride=1):
+                 stoc_levels=3, delta0=2.0 ** 49, ctos_B=None, stoc_B=None, coeffs=None, stride=1,
+                 decomp_B=None):
         P = orc.P
         n, m = P.n, P.n // 2
         self.w, self.w0, self.cout = w, w0, cout
@@ -96,7 +97,7 @@ class BootConfig:
             assert w >= 4 and w0 % 2 == 0
             a0, step, count = E.decompose_ap(w, n)
             self.decomp = orc.make_plan(E.decompose_diag(w, n), a0, step, count, top, P.delta[top],
-                                        boot_bsgs_B(count))
+                                        decomp_B if decomp_B else boot_bsgs_B(count))
             top, ell_out = top - 1, self.ell // 4
         # --- StoC1 plans
         self.stoc = []

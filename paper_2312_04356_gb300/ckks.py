@@ -137,6 +137,9 @@ _SIGS = {
     "ckks_boot_destroy": [VP],
     "ckks_boot_info": [VP, VP],
     "ckks_boot_rotations": [VP, VP, I, VP],
+    "ckks_boot_bsgs_splits": [VP, VP, I, VP],
+    "ckks_boot_set_bsgs_splits": [VP, VP, VP, I],
+    "ckks_boot_tune_bsgs": [VP, VP, I, VP, I, VP],
     "ckks_boot_set_ctos": [VP, VP, I, VP],
     "ckks_boot_set_stoc": [VP, VP, I, VP],
     "ckks_boot_set_coeffs": [VP, VP, VP, I],
@@ -663,6 +666,26 @@ def ckks_boot_rotations(bt):
     lib().ckks_boot_rotations(bt, None, 0, ctypes.byref(n))
     a = np.zeros(max(n.value, 1), dtype=np.int32)
     lib().ckks_boot_rotations(bt, _ptr(a), n.value, ctypes.byref(n))
+    return [int(x) for x in a[: n.value]]
+
+
+def ckks_boot_bsgs_splits(bt):
+    n = ctypes.c_int()
+    a = np.zeros(64, dtype=np.int32)
+    if lib().ckks_boot_bsgs_splits(bt, _ptr(a), 64, ctypes.byref(n)) != CKKS_OK:
+        raise CkksError(CKKS_EINVAL, "ckks_boot_bsgs_splits")
+    return [int(x) for x in a[: n.value]]
+
+
+def ckks_boot_set_bsgs_splits(ctx, bt, B):
+    a = np.ascontiguousarray(B, dtype=np.int32)
+    ctx.check(lib().ckks_boot_set_bsgs_splits(ctx, bt, _ptr(a), len(a)))
+
+
+def ckks_boot_tune_bsgs(ctx, bt, reps=3):
+    n = ctypes.c_int()
+    a = np.zeros(64, dtype=np.int32)
+    ctx.check(lib().ckks_boot_tune_bsgs(ctx, bt, int(reps), _ptr(a), 64, ctypes.byref(n)))
     return [int(x) for x in a[: n.value]]
 
 

@@ -891,6 +891,29 @@ int ckks_conv2d_cins(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, co
 }
 
 // -------------------------------------------------------- bootstrapping -----
+// diagonals of one BSGS level of a bootstrapping configuration
+static fp64::Diag boot_level_diag(const ckks_boot& bt, const ckks_boot::Level& lv, int m) {
+    if (lv.kind == 1) return fp64::decompose_diag(bt.bp.w, m);
+    std::vector<int> rev(lv.strides.rbegin(), lv.strides.rend());
+    fp64::Diag D = fp64::s_product(rev, m, lv.kind == 0);
+    if (lv.half)
+        for (auto& kv : D)
+            for (cplx& v : kv.second) v *= 0.5;
+    return D;
+}
+
+static std::unique_ptr<ckks_ptset>& boot_level_slot(ckks_boot& bt, const ckks_boot::Level& lv) {
+    if (lv.kind == 0) return bt.ctos[lv.index];
+    if (lv.kind == 1) return bt.decomp;
+    return bt.stoc[lv.index];
+}
+
+static std::unique_ptr<ckks_ptset> boot_level_plan(ckks_ctx* ctx, const ckks_boot& bt, const ckks_boot::Level& lv,
+                                                   int B) {
+    return std::unique_ptr<ckks_ptset>(make_plan(ctx, boot_level_diag(bt, lv, ctx->n / 2), lv.a0, lv.step, lv.count,
+                                                 lv.level, lv.scale, B));
+}
+
 int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out) {
     return guard(ctx, [&] {
         REQ(ctx);
@@ -918,16 +941,18 @@ int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out)
         std::vector<int> stages;
         for (int k = m / 2; k >= 1; k /= 2) stages.push_back(k);
         std::vector<std::vector<int>> groups = fp64::split_groups(stages, bp->ctos_levels);
+        bt->ctos.resize(groups.size());
         for (size_t i = 0; i < groups.size(); ++i) {
-            std::vector<int> rev(groups[i].rbegin(), groups[i].rend());
-            fp64::Diag D = fp64::s_product(rev, m, true);
-            if (i + 1 == groups.size())
-                for (auto& kv : D)
-                    for (cplx& v : kv.second) v *= 0.5;
-            int a0, step, count;
-            fp64::ap_of_group(groups[i], m, &a0, &step, &count);
-            const int lev = L - (int)i;
-            bt->ctos.emplace_back(make_plan(ctx, D, a0, step, count, lev, (double)ctx->q[lev], fp64::boot_bsgs_B(count)));
+            ckks_boot::Level lv;
+            lv.kind = 0;
+            lv.index = (int)i;
+            lv.strides = groups[i];
+            lv.half = i + 1 == groups.size();
+            fp64::ap_of_group(groups[i], m, &lv.a0, &lv.step, &lv.count);
+            lv.level = L - (int)i;
+            lv.scale = (double)ctx->q[lv.level];
+            bt->ctos[i] = boot_level_plan(ctx, *bt, lv, fp64::boot_bsgs_B(lv.count));
+            bt->levels.push_back(lv);
         }
         bt->coeffs = fp64::cheb_interp_cos(bt->K_eff, bp->r, bp->deg);
         int depth = 0;
@@ -963,8 +988,15 @@ int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out)
         int top = le - 1, ell_out = bt->ell;
         if (bp->stride == 2) {
             CK_CHECK(bp->w >= 4 && bp->w0 % 2 == 0, CKKS_EINVAL, "stride 2 needs w >= 4 and an even image width");
-            bt->decomp.reset(make_plan(ctx, fp64::decompose_diag(bp->w, m), (1 - bp->w) * (bp->w / 4), bp->w / 4,
-                                       2 * bp->w - 1, top, ctx->delta[top], fp64::boot_bsgs_B(2 * bp->w - 1)));
+            ckks_boot::Level lv;
+            lv.kind = 1;
+            lv.a0 = (1 - bp->w) * (bp->w / 4);
+            lv.step = bp->w / 4;
+            lv.count = 2 * bp->w - 1;
+            lv.level = top;
+            lv.scale = ctx->delta[top];
+            bt->decomp = boot_level_plan(ctx, *bt, lv, fp64::boot_bsgs_B(lv.count));
+            bt->levels.push_back(lv);
             --top;
             ell_out /= 4;
         }
@@ -972,13 +1004,17 @@ int ckks_boot_create(ckks_ctx* ctx, const ckks_boot_params* bp, ckks_boot** out)
         std::vector<int> st;
         for (int k = 1; k < ell_out; k *= 2) st.push_back(k);
         std::vector<std::vector<int>> sg = fp64::split_groups(st, bp->stoc_levels);
+        bt->stoc.resize(sg.size());
         for (size_t i = 0; i < sg.size(); ++i) {
-            std::vector<int> rev(sg[i].rbegin(), sg[i].rend());
-            fp64::Diag D = fp64::s_product(rev, m, false);
-            int a0, step, count;
-            fp64::ap_of_group(sg[i], m, &a0, &step, &count);
-            const int lev = top - (int)i;
-            bt->stoc.emplace_back(make_plan(ctx, D, a0, step, count, lev, ctx->delta[lev], fp64::boot_bsgs_B(count)));
+            ckks_boot::Level lv;
+            lv.kind = 2;
+            lv.index = (int)i;
+            lv.strides = sg[i];
+            fp64::ap_of_group(sg[i], m, &lv.a0, &lv.step, &lv.count);
+            lv.level = top - (int)i;
+            lv.scale = ctx->delta[lv.level];
+            bt->stoc[i] = boot_level_plan(ctx, *bt, lv, fp64::boot_bsgs_B(lv.count));
+            bt->levels.push_back(lv);
         }
         bt->l_out = top - (int)bt->stoc.size();
         CK_CHECK(bt->l_out >= 1, CKKS_ELEVEL, "not enough levels for the block");
@@ -1017,6 +1053,93 @@ int ckks_boot_rotations(const ckks_boot* bt, int32_t* steps, int cap, int* n_out
     }
     *n_out = i;
     return CKKS_OK;
+}
+
+int ckks_boot_bsgs_splits(const ckks_boot* bt, int32_t* B, int cap, int* n_out) {
+    if (!bt || !n_out) return CKKS_EINVAL;
+    int i = 0;
+    for (const auto& lv : bt->levels) {
+        const ckks_ptset* p = lv.kind == 0 ? bt->ctos[lv.index].get()
+                              : lv.kind == 1 ? bt->decomp.get() : bt->stoc[lv.index].get();
+        if (B && i < cap) B[i] = p ? p->B : 0;
+        ++i;
+    }
+    *n_out = i;
+    return CKKS_OK;
+}
+
+int ckks_boot_set_bsgs_splits(ckks_ctx* ctx, ckks_boot* bt, const int32_t* B, int n) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(bt);
+        CK_CHECK(n == (int)bt->levels.size() && (n == 0 || B), CKKS_EINVAL, "one baby-step count per BSGS level");
+        for (int i = 0; i < n; ++i)
+            CK_CHECK(B[i] >= 1 && B[i] <= kern::BsgsTerms::MAX, CKKS_EINVAL, "baby-step count out of range");
+        for (int i = 0; i < n; ++i) boot_level_slot(*bt, bt->levels[i]) = boot_level_plan(ctx, *bt, bt->levels[i], B[i]);
+    });
+}
+
+// For every BSGS level: candidate baby-step counts (powers of two up to 32 and the cost-model
+// choice), each timed as one HMatmul with rescale on a fresh encryption at the level's input
+// level, with switching keys generated for the candidates' rotations only while the level is
+// tuned; the fastest plan is kept.  Op and launch counters are left as they were.
+int ckks_boot_tune_bsgs(ckks_ctx* ctx, ckks_boot* bt, int reps, int32_t* B_out, int cap, int* n_out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(bt);
+        CK_CHECK(reps >= 1, CKKS_EINVAL, "reps must be >= 1");
+        const auto ops_saved = ctx->ops;
+        const long long launches_saved = ctx->launches;
+        cudaEvent_t e0, e1;
+        CUDA_CHECK(cudaEventCreate(&e0));
+        CUDA_CHECK(cudaEventCreate(&e1));
+        std::vector<int> chosen;
+        for (const auto& lv : bt->levels) {
+            std::vector<int> cand;
+            for (int b = 2; b <= std::min(lv.count, kern::BsgsTerms::MAX); b *= 2) cand.push_back(b);
+            const int def = fp64::boot_bsgs_B(lv.count);
+            if (std::find(cand.begin(), cand.end(), def) == cand.end()) cand.push_back(def);
+            if (cand.size() < 2) {
+                chosen.push_back(boot_level_slot(*bt, lv)->B);
+                continue;
+            }
+            std::vector<std::unique_ptr<ckks_ptset>> plans;
+            std::set<int> rots;
+            for (int b : cand) {
+                plans.push_back(boot_level_plan(ctx, *bt, lv, b));
+                plan_rotations(*plans.back(), rots);
+            }
+            std::vector<int32_t> steps(rots.begin(), rots.end());
+            std::unique_ptr<ckks_keys> keys(ops::keygen(ctx, steps.data(), (int)steps.size(), 0));
+            ckks_pt pt;
+            encode_complex(ctx, std::vector<cplx>(ctx->n / 2, cplx(0, 0)), lv.level, ctx->delta[lv.level], &pt);
+            const ckks_ct x = ops::encrypt(*keys, pt, 1);
+            int best = -1;
+            float best_ms = 0;
+            for (size_t k = 0; k < plans.size(); ++k) {
+                ops::bsgs(*keys, x, *plans[k], true);      // warm-up
+                CUDA_CHECK(cudaEventRecord(e0, ctx->stream));
+                for (int r = 0; r < reps; ++r) ops::bsgs(*keys, x, *plans[k], true);
+                CUDA_CHECK(cudaEventRecord(e1, ctx->stream));
+                CUDA_CHECK(cudaEventSynchronize(e1));
+                float ms = 0;
+                CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+                if (best < 0 || ms < best_ms) {
+                    best = (int)k;
+                    best_ms = ms;
+                }
+            }
+            chosen.push_back(plans[best]->B);
+            boot_level_slot(*bt, lv) = std::move(plans[best]);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->ops = ops_saved;
+        ctx->launches = launches_saved;
+        for (size_t i = 0; i < chosen.size(); ++i)
+            if (B_out && (int)i < cap) B_out[i] = chosen[i];
+        if (n_out) *n_out = (int)chosen.size();
+    });
 }
 
 static std::unique_ptr<ckks_ptset> clone_ptset(ckks_ctx* ctx, const ckks_ptset& ps) {

@@ -178,6 +178,17 @@ struct ckks_boot {
     std::unique_ptr<ckks_ptset> decomp;   // stride 2: Alg. 2 decomposition before StoC1
     std::unique_ptr<ckks_pt> mask_re, mask_im;
     bool mask_im_zero = false;   // the Im half of every slice is padding: its mask is exactly 0
+    // What each BSGS level's plan is built from (CtoS levels, the stride-2 decomposition, the
+    // StoC1 levels, in evaluation order), so that it can be rebuilt with another baby-step count.
+    struct Level {
+        int kind = 0;                 // 0 CtoS, 1 decomposition, 2 StoC1
+        int index = 0;                // position in ctos / stoc
+        std::vector<int> strides;     // DFT stages of a CtoS / StoC1 level
+        bool half = false;            // the last CtoS level carries the factor 1/2
+        int a0 = 0, step = 0, count = 0, level = 0;
+        double scale = 0;
+    };
+    std::vector<Level> levels;
 };
 
 // Scope object placed around one kernel launch: counts it and, if the context's

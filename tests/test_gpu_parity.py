@@ -188,7 +188,7 @@ def test_own_encoder_close_to_oracle():
         assert max(d) <= 1
 
 
-def _block_pair(name, seed, import_all=True, oracle_all_keys=True):
+def _block_pair(name, seed, import_all=True, oracle_all_keys=True, splits=None):
     P = oracle_params(name)
     spec = WL.CONV[name]
     x = WL.image(seed, spec["cin"], spec["w0"])
@@ -196,7 +196,8 @@ def _block_pair(name, seed, import_all=True, oracle_all_keys=True):
     w = E.pad_width(spec["w0"], spec["f"])
     from oracle.scheme import Oracle
     o0 = Oracle(P, seed)
-    cfg = BT.BootConfig(o0, w, spec["w0"], spec["cout"])
+    ctos_B, stoc_B = splits if splits else (None, None)
+    cfg = BT.BootConfig(o0, w, spec["w0"], spec["cout"], ctos_B=ctos_B, stoc_B=stoc_B)
     plan = o0.conv_plan(W, spec["cin"], spec["cout"], spec["f"], w, 1, (cfg.delta0 * float(P.q[1])) / P.delta[1])
     rots = BT.block_rotations(o0, plan, cfg)
     if oracle_all_keys:
@@ -209,6 +210,9 @@ def _block_pair(name, seed, import_all=True, oracle_all_keys=True):
         ctx = gpu_ctx(name, seed)
         keys = K.ckks_keygen(ctx, rots, True)
     bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
+    if splits:
+        K.ckks_boot_set_bsgs_splits(ctx, bt, list(ctos_B) + list(stoc_B))
+        assert K.ckks_boot_bsgs_splits(bt) == list(ctos_B) + list(stoc_B)
     info = K.ckks_boot_info(bt)
     assert info["c_drop"] == cfg.c_drop and info["K_eff"] == cfg.K_eff and info["s_raise"] == cfg.s_raise
     assert info["l_em"] == cfg.l_em and info["l_out"] == cfg.l_out and info["s_mask"] == cfg.s_mask
@@ -266,6 +270,53 @@ def test_block_small_bitexact():
     zexp, _ = _expected_slots(d)
     got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gblk))
     assert np.abs(_pixels(d, got) - _pixels(d, zexp)).max() < 2.0 ** -12
+
+
+def test_block_bsgs_splits_bitexact():
+    """every CtoS / StoC1 level evaluated with B = 2 and B = 4 baby steps instead of the
+    cost-model choice: the rotation set follows the splits and the block stays bit-exact
+    against the oracle built with the same splits"""
+    for B in (2, 4):
+        d = _block_pair("cfg2_small", 34, splits=([B] * 3, [B] * 3))
+        K, o, ctx, keys = d["K"], d["o"], d["ctx"], d["keys"]
+        assert [p.B for p in d["cfg"].ctos + d["cfg"].stoc] == [B] * 6
+        ct = o.encrypt(d["pt"], 2)
+        gct = K.ckks_encrypt(ctx, keys, import_pt(K, ctx, d["pt"]), 2)
+        out = BT.block(o, ct, d["plan"], d["cfg"])
+        gblk = K.ckks_block(ctx, keys, gct, import_plan(K, ctx, d["plan"]), d["bt"])
+        assert_ct_equal(K, ctx, gblk, out, "block with B = %d" % B)
+
+
+def test_bsgs_split_autotuner():
+    """the autotuner picks one baby-step count per level among the timed candidates, leaves
+    the op counters alone, and the tuned block (the library's own plans and keys for the
+    tuned rotation set) decodes within 2^-12; the rotation set is the oracle's for the
+    same splits"""
+    from paper_2312_04356_gb300 import ckks as K
+    from oracle.scheme import Oracle, boot_bsgs_B
+    P = oracle_params("cfg2_small")
+    spec = WL.CONV["cfg2_small"]
+    w = E.pad_width(spec["w0"], spec["f"])
+    ctx = gpu_ctx("cfg2_small", 35)
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
+    before = K.ckks_ctx_counters(ctx)
+    B = K.ckks_boot_tune_bsgs(ctx, bt, 2)
+    assert K.ckks_ctx_counters(ctx) == before
+    cfg = BT.BootConfig(Oracle(P, 35), w, spec["w0"], spec["cout"], ctos_B=B[:3], stoc_B=B[3:])
+    for b, pl in zip(B, cfg.ctos + cfg.stoc):
+        assert b in [c for c in (2, 4, 8, 16, 32) if c <= min(pl.count, 32)] + [boot_bsgs_B(pl.count)]
+    assert K.ckks_boot_bsgs_splits(bt) == B
+    assert sorted(K.ckks_boot_rotations(bt)) == sorted(set(r for pl in cfg.ctos + cfg.stoc
+                                                           for r in pl.rotations(P.n // 2)))
+    W = WL.weights(35, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+    x = WL.image(35, spec["cin"], spec["w0"])
+    conv = K.ckks_ptset_conv_fused(ctx, W, spec["cin"], spec["cout"], spec["f"], w, 1, (cfg.delta0 * q[1]) / delta[1])
+    keys = K.ckks_keygen(ctx, sorted(set(K.ckks_ptset_rotations(conv)) | set(K.ckks_boot_rotations(bt))), True)
+    ct = K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, x, w, 1, delta[1]), 3)
+    out = K.ckks_block(ctx, keys, ct, conv, bt)
+    got = K.ckks_decode_image(ctx, K.ckks_decrypt(ctx, keys, out), spec["cout"], spec["w0"], w)
+    assert np.abs(got - E.conv2d_same(x, W)[: spec["cout"]]).max() < 2.0 ** -12
 
 
 def test_block_graph_replays_bitexact():
