@@ -47,9 +47,11 @@ def parse_args():
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
     ap.add_argument("--batch", type=int, default=8, help="ciphertexts run concurrently for the batched figure")
-    ap.add_argument("--workload", default="block", choices=["block", "ds", "serve"],
+    ap.add_argument("--workload", default="block", choices=["block", "ds", "serve", "batch"],
                     help="block: the Alg. 1 block (default); ds: the downsampling layer of Alg. 2; "
-                         "serve: the serving loop under Poisson arrivals")
+                         "serve: the serving loop under Poisson arrivals; batch: 64 uneven-shape blocks "
+                         "(ResNet-20 stage shapes) batched through the serving runtime")
+    ap.add_argument("--batch-size", type=int, default=64, help="batch: number of seeded inputs")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--variant", type=int, default=-1, help="--kernel ntt: time one launch variant only")
     ap.add_argument("--kernel", default=None, choices=["ntt", "ks"],
@@ -653,6 +655,109 @@ def run_serve(args):
     srv.close()
 
 
+def run_batch(args):
+    """Batched uneven-shape blocks at N = 2^16: the stride-1 conv2d + bootstrap blocks of the three
+    stages of a ResNet-20-shaped network (16 x 32 x 32, 32 x 16 x 16 and 64 x 8 x 8 channels x
+    pixels), B seeded inputs mixed over the three shapes, run through the serving runtime with
+    --batch slots (each slot a stream replaying the shape's recorded block graph; inputs and
+    outputs as host limbs).  The plain figure runs the same B requests one at a time (one
+    slot).  Batched outputs must equal the one-at-a-time outputs bit for bit; one output per
+    shape is decoded against the FP64 conv2d."""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = K.ckks_ctx_create(WL.PARAMS[CONFIG], 1, stream.cuda_stream)
+    tuned = K.ckks_autotune(ctx, 3)
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    delta0 = 2.0 ** 49
+    names = ["cfg3_s1", "cfg3_s2", "cfg3_s3"]
+    shapes = []
+    rots = set()
+    for nm in names:
+        spec = WL.CONV[nm]
+        w = 1
+        while w < spec["w0"] + spec["f"] // 2:
+            w *= 2
+        bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
+        W = WL.weights(11, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+        conv = K.ckks_ptset_conv_fused(ctx, W, spec["cin"], spec["cout"], spec["f"], w, 1, (delta0 * q[1]) / delta[1])
+        rots |= set(K.ckks_ptset_rotations(conv)) | set(K.ckks_boot_rotations(bt))
+        shapes.append(dict(name=nm, spec=spec, w=w, bt=bt, W=W, conv=conv))
+    keys = K.ckks_keygen(ctx, sorted(rots), True)
+    nreq = max(1, args.batch_size)
+    pick = np.random.default_rng(23).integers(0, len(shapes), size=nreq)
+    reqs = []
+    for i in range(nreq):
+        sh = shapes[int(pick[i])]
+        x = WL.image(1000 + i, sh["spec"]["cin"], sh["spec"]["w0"])
+        ct = K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, x, sh["w"], 1, delta[1]), 1000 + i)
+        reqs.append((int(pick[i]), x, K.ckks_ct_export_rns(ctx, ct)))
+    K.ckks_sync(ctx)
+
+    def serve_all(slots):
+        srv = K.ckks_server_create(ctx, keys, slots, 0)
+        models = [K.ckks_server_add_model(srv, [sh["conv"]], [sh["bt"]]) for sh in shapes]
+        K.ckks_server_start(srv)
+        for mi, m in enumerate(models):                     # warm-up: one request per shape
+            r = next(x for x in reqs if x[0] == mi) if any(x[0] == mi for x in reqs) else None
+            if r is not None:
+                K.ckks_server_wait(srv, K.ckks_server_submit(srv, m, r[2], 1, delta[1]), 300)
+        K.ckks_server_reset_stats(srv)
+        t0 = time.perf_counter()
+        ids = [K.ckks_server_submit(srv, models[si], limbs, 1, delta[1]) for si, _, limbs in reqs]
+        for rid in ids:
+            assert K.ckks_server_wait(srv, rid, 600) == K.CKKS_REQ_DONE
+        dt = time.perf_counter() - t0
+        outs = [K.ckks_server_result(srv, rid, ctx.n) for rid in ids]
+        st = K.ckks_server_stats(srv)
+        info = [K.ckks_server_model_info(srv, m) for m in models]
+        srv.close()
+        return dt, outs, st, info
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    dt_b, outs_b, st_b, info = serve_all(max(1, args.batch))
+    dt_1, outs_1, st_1, _ = serve_all(1)
+    clocks = sampler.stop()
+    identical = all((a[0] == b[0]).all() for a, b in zip(outs_b, outs_1))
+    errs = {}
+    for si, sh in enumerate(shapes):
+        k = next((i for i, r in enumerate(reqs) if r[0] == si), None)
+        if k is None:
+            continue
+        limbs, lev, sc = outs_b[k]
+        got = K.ckks_decode_image(ctx, K.ckks_decrypt(ctx, keys, K.ckks_ct_import_rns(ctx, limbs, lev, sc)),
+                                  sh["spec"]["cout"], sh["spec"]["w0"], sh["w"])
+        x = reqs[k][1]
+        c = sh["spec"]["f"] // 2
+        h = sh["spec"]["w0"]
+        xp = np.zeros((x.shape[0], h + 2 * c, h + 2 * c))
+        xp[:, c:c + h, c:c + h] = x
+        ref = np.zeros((sh["W"].shape[0], h, h))
+        for a in range(sh["spec"]["f"]):
+            for b in range(sh["spec"]["f"]):
+                ref += np.einsum("oi,ihw->ohw", sh["W"][:, :, a, b], xp[:, a:a + h, b:b + h])
+        errs[sh["name"]] = float(np.abs(got - ref).max())
+    counts = [int((pick == i).sum()) for i in range(len(shapes))]
+    line = {"metric": "batched ct/s: uneven-shape conv2d+bootstrap blocks at N=2^16",
+            "value": round(nreq / dt_b, 2), "unit": "ct/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "ResNet-20 stage shapes (stride-1 blocks): 16x32x32, 32x16x16, 64x8x8; "
+                                   "3x3 conv fused with StoC2 + full bootstrap each; host limbs in and out",
+                       "batch": nreq, "per_shape_count": dict(zip(names, counts)), "slots": max(1, args.batch),
+                       "footprint_bytes": [i["footprint"] for i in info],
+                       "kernels_per_block": [i["kernels"] for i in info]},
+            "plain_one_at_a_time": {"value": round(nreq / dt_1, 2), "unit": "ct/s", "p50_ms": round(st_1["p50_ms"], 2)},
+            "batched_latency": {"p50_ms": round(st_b["p50_ms"], 2), "p99_ms": round(st_b["p99_ms"], 2),
+                                "max_in_flight": int(st_b["max_in_flight"])},
+            "outputs_identical_batched_vs_alone": bool(identical), "decoded_max_abs_err": errs,
+            "autotune_ntt_variant_per_size_class": tuned, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_kernel_ntt(args):
     """forward + inverse NTT of 256 limbs (256 MiB, > L2) cycling over the config-2 primes"""
     import torch
@@ -733,6 +838,8 @@ if __name__ == "__main__":
         run_ds(a)
     elif a.workload == "serve" and a.impl == "ours":
         run_serve(a)
+    elif a.workload == "batch" and a.impl == "ours":
+        run_batch(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

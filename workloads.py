@@ -27,6 +27,10 @@ CONV = {
     "cfg1": dict(cin=1, cout=1, w0=16, f=3, weight="uniform"),
     "cfg2": dict(cin=16, cout=16, w0=32, f=3, weight="gauss"),
     "cfg2_small": dict(cin=4, cout=4, w0=4, f=3, weight="gauss"),
+    # the stride-1 block shapes of the three stages of a ResNet-20-shaped network (config 3)
+    "cfg3_s1": dict(cin=16, cout=16, w0=32, f=3, weight="gauss"),
+    "cfg3_s2": dict(cin=32, cout=32, w0=16, f=3, weight="gauss"),
+    "cfg3_s3": dict(cin=64, cout=64, w0=8, f=3, weight="gauss"),
 }
 
 
