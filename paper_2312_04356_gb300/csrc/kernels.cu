@@ -852,11 +852,11 @@ __global__ void k_bsgs_inner(kern::BsgsTerms T, u64* __restrict__ o, const DevPr
 // exact table, minus v (Q mod p_m) with v = round(sum_i xhat_i / q_i) evaluated in FP64
 // (Halevi, Polyakov, Shoup 2019): y then represents the centred remainder of x mod Q, up
 // to an FP64 error that matters only within ~1e-15 of a half-integer.
-// One thread per coefficient; grid.z walks over (job, group of CONV_OUT outputs), so the
-// digits of one ModUp (or the two halves of one ModDown) share a launch.  The products are
-// summed exactly in 128 bits (each < 2^122, at most 16 terms) and reduced once:
+// One thread per coefficient; grid.z walks over (job, group of MC <= CONV_OUT outputs), so
+// the digits of one ModUp (or the two halves of one ModDown) share a launch.  The products
+// are summed exactly in 128 bits (each < 2^122, at most 16 terms) and reduced once:
 // (H 2^64 + L) mod p = H (2^64 mod p) + L mod p.  The output loop is unrolled so that the
-// CONV_OUT independent accumulations interleave.
+// MC independent accumulations interleave.
 constexpr int MAX_CONV_IN = 16;
 constexpr int CONV_OUT = 8;
 // MAXIN: compile-time bound on the jobs' input counts (4, 8 or 16), so that the unrolled
@@ -865,7 +865,8 @@ constexpr int CONV_OUT = 8;
 // partial products (each < 2^60) go into three 64-bit sums by one 32x32->64 multiply-add
 // each (at most 16 terms per sum: no overflow); the 128-bit total ll + m 2^30 + hh 2^60 is
 // then reduced as in the general path.
-template <int MAXIN, bool SPLIT>
+// MC: outputs per CTA group (4..8), chosen per launch to leave the fewest idle output slots.
+template <int MAXIN, bool SPLIT, int MC>
 __global__ void __launch_bounds__(256, 3) k_base_convert(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn) {
     griddep_entry();
     __shared__ u64 s_qi[MAX_CONV_IN], s_qinv[MAX_CONV_IN], s_qinvp[MAX_CONV_IN];
@@ -883,8 +884,8 @@ __global__ void __launch_bounds__(256, 3) k_base_convert(kern::ConvJobs J, const
     }
     const kern::ConvJob& job = J.job[jb];
     const int nin = job.nin, nout = job.nout;
-    const int m0 = z * CONV_OUT;
-    const int mcount = min(CONV_OUT, nout - m0);
+    const int m0 = z * MC;
+    const int mcount = min(MC, nout - m0);
     const int tid = threadIdx.x;
     const bool exact = job.inv_q != nullptr;
     if (tid < nin) {
@@ -914,18 +915,18 @@ __global__ void __launch_bounds__(256, 3) k_base_convert(kern::ConvJobs J, const
 #pragma unroll
     for (int i = 0; i < MAXIN; ++i)
         if (i < nin) xh[i] = mul_shoup(in[i * n + j], s_qinv[i], s_qinvp[i], s_qi[i]);
-    u64 lo[CONV_OUT], hi[CONV_OUT];
+    u64 lo[MC], hi[MC];
     if (SPLIT) {
         constexpr u64 M30 = (1ull << 30) - 1;
-        u64 ll[CONV_OUT], mm[CONV_OUT], hh[CONV_OUT];
+        u64 ll[MC], mm[MC], hh[MC];
 #pragma unroll
-        for (int m = 0; m < CONV_OUT; ++m) ll[m] = mm[m] = hh[m] = 0;
+        for (int m = 0; m < MC; ++m) ll[m] = mm[m] = hh[m] = 0;
 #pragma unroll
         for (int i = 0; i < MAXIN; ++i) {
             if (i < nin) {
                 const unsigned xl = (unsigned)(xh[i] & M30), xu = (unsigned)(xh[i] >> 30);
 #pragma unroll
-                for (int m = 0; m < CONV_OUT; ++m) {
+                for (int m = 0; m < MC; ++m) {
                     const uint2 cc = s_c2[m][i];
                     ll[m] += (u64)xl * cc.x;
                     mm[m] += (u64)xl * cc.y;
@@ -935,7 +936,7 @@ __global__ void __launch_bounds__(256, 3) k_base_convert(kern::ConvJobs J, const
             }
         }
 #pragma unroll
-        for (int m = 0; m < CONV_OUT; ++m) {
+        for (int m = 0; m < MC; ++m) {
             u64 l = ll[m], h = (mm[m] >> 34) + (hh[m] >> 4);
             const u64 t1 = mm[m] << 30;
             l += t1;
@@ -948,12 +949,12 @@ __global__ void __launch_bounds__(256, 3) k_base_convert(kern::ConvJobs J, const
         }
     } else {
 #pragma unroll
-        for (int m = 0; m < CONV_OUT; ++m) lo[m] = hi[m] = 0;
+        for (int m = 0; m < MC; ++m) lo[m] = hi[m] = 0;
 #pragma unroll
         for (int i = 0; i < MAXIN; ++i) {
             if (i < nin) {
 #pragma unroll
-                for (int m = 0; m < CONV_OUT; ++m) {
+                for (int m = 0; m < MC; ++m) {
                     const u64 c = s_c[m][i];
                     const u64 pl = xh[i] * c, ph = __umul64hi(xh[i], c);
                     lo[m] += pl;
@@ -969,14 +970,14 @@ __global__ void __launch_bounds__(256, 3) k_base_convert(kern::ConvJobs J, const
             if (i < nin) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xh[i]), s_invq[i]));
         const u64 v = (u64)__double2ll_rn(f);
 #pragma unroll
-        for (int m = 0; m < CONV_OUT; ++m) {
+        for (int m = 0; m < MC; ++m) {
             const u64 pl = v * s_corr[m], ph = __umul64hi(v, s_corr[m]);
             lo[m] += pl;
             hi[m] += ph + (lo[m] < pl ? 1ull : 0ull);
         }
     }
 #pragma unroll
-    for (int m = 0; m < CONV_OUT; ++m)
+    for (int m = 0; m < MC; ++m)
         if (m < mcount) out[(size_t)s_row[m] * n + j] = reduce128_lazy(hi[m], lo[m], s_pm[m]);
 }
 
@@ -1375,10 +1376,34 @@ void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t
     j.out_pstride = out_pstride;
 }
 
-void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly) {
+template <int MAXIN, bool SPLIT>
+static void launch_base_convert(const ckks_ctx* c, const ConvJobs& J, dim3 grid, int mc) {
+    switch (mc) {
+        case 4: klaunch(c, k_base_convert<MAXIN, SPLIT, 4>, grid, 256, 0, J, c->d_primes, c->logn); break;
+        case 5: klaunch(c, k_base_convert<MAXIN, SPLIT, 5>, grid, 256, 0, J, c->d_primes, c->logn); break;
+        case 6: klaunch(c, k_base_convert<MAXIN, SPLIT, 6>, grid, 256, 0, J, c->d_primes, c->logn); break;
+        case 7: klaunch(c, k_base_convert<MAXIN, SPLIT, 7>, grid, 256, 0, J, c->d_primes, c->logn); break;
+        default: klaunch(c, k_base_convert<MAXIN, SPLIT, 8>, grid, 256, 0, J, c->d_primes, c->logn); break;
+    }
+}
+
+// Outputs per group MC in 4..8: the one with the fewest idle output slots over the launch's
+// jobs (sum of ceil(nout / MC) MC - nout), the larger MC on ties (fewer groups).
+void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
+    int best_mc = CONV_OUT, best_slots = -1;
+    for (int mc = CONV_OUT; mc >= 4; --mc) {
+        int slots = 0;
+        for (int i = 0; i < J0.n; ++i) slots += (J0.job[i].nout + mc - 1) / mc * mc;
+        if (best_slots < 0 || slots < best_slots) {
+            best_slots = slots;
+            best_mc = mc;
+        }
+    }
+    ConvJobs J = J0;
     int groups = 0;
     double bytes = 0;
     for (int i = 0; i < J.n; ++i) {
+        J.job[i].ngroups = (J.job[i].nout + best_mc - 1) / best_mc;
         groups += J.job[i].ngroups;
         bytes += (double)npoly * (J.job[i].nin + J.job[i].nout) * c->n * 8.0;
     }
@@ -1388,13 +1413,13 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly) {
     dim3 grid((c->n + 255) / 256, npoly, groups);
     { KTimer kt_(c, "base_convert", bytes);
     if (maxin <= 4)
-        klaunch(c, k_base_convert<4, false>, grid, 256, 0, J, c->d_primes, c->logn);
+        launch_base_convert<4, false>(c, J, grid, best_mc);
     else if (maxin <= 8 && c->mods_below_2_60)
-        klaunch(c, k_base_convert<8, true>, grid, 256, 0, J, c->d_primes, c->logn);
+        launch_base_convert<8, true>(c, J, grid, best_mc);
     else if (maxin <= 8)
-        klaunch(c, k_base_convert<8, false>, grid, 256, 0, J, c->d_primes, c->logn);
+        launch_base_convert<8, false>(c, J, grid, best_mc);
     else
-        klaunch(c, k_base_convert<MAX_CONV_IN, false>, grid, 256, 0, J, c->d_primes, c->logn);
+        launch_base_convert<MAX_CONV_IN, false>(c, J, grid, best_mc);
     }
     LAUNCH_CHECK();
 }
