@@ -1074,7 +1074,7 @@ int ckks_boot_set_bsgs_splits(ckks_ctx* ctx, ckks_boot* bt, const int32_t* B, in
         REQ(bt);
         CK_CHECK(n == (int)bt->levels.size() && (n == 0 || B), CKKS_EINVAL, "one baby-step count per BSGS level");
         for (int i = 0; i < n; ++i)
-            CK_CHECK(B[i] >= 1 && B[i] <= kern::BsgsTerms::MAX, CKKS_EINVAL, "baby-step count out of range");
+            CK_CHECK(B[i] >= 1 && B[i] <= kern::BsgsGiants::MAXB, CKKS_EINVAL, "baby-step count out of range");
         for (int i = 0; i < n; ++i) boot_level_slot(*bt, bt->levels[i]) = boot_level_plan(ctx, *bt, bt->levels[i], B[i]);
     });
 }
@@ -1096,7 +1096,7 @@ int ckks_boot_tune_bsgs(ckks_ctx* ctx, ckks_boot* bt, int reps, int32_t* B_out, 
         std::vector<int> chosen;
         for (const auto& lv : bt->levels) {
             std::vector<int> cand;
-            for (int b = 2; b <= std::min(lv.count, kern::BsgsTerms::MAX); b *= 2) cand.push_back(b);
+            for (int b = 2; b <= std::min(lv.count, kern::BsgsGiants::MAXB); b *= 2) cand.push_back(b);
             const int def = fp64::boot_bsgs_B(lv.count);
             if (std::find(cand.begin(), cand.end(), def) == cand.end()) cand.push_back(def);
             if (cand.size() < 2) {

@@ -217,15 +217,19 @@ namespace kern {
 void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
 // forward NTT of an arbitrary list of limbs: limb i at data + off[i] * N with prime ids[i] (N = 2^16)
 void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, const int* ids);
-// o[poly][limb] = sum_t a_t[poly][limb] * p_t[limb] (two polynomials of nl limbs, t < n <= 32)
-struct BsgsTerms {
-    static constexpr int MAX = 32;
-    const u64* a[MAX];
-    const u64* p[MAX];
-    int n;
+// The inner sums of up to MAXG giant steps in one pass over the baby rotations (two
+// polynomials of nl limbs each; limb r has prime ids[r]):
+// o[g] (+)= sum_b a[b] * p[g][b] (p[g][b] null: zero diagonal), accumulating into o[g] when
+// bit g of acc is set.  Every baby rotation is read once for all the giant steps.
+struct BsgsGiants {
+    static constexpr int MAXB = 32, MAXG = 8;
+    const u64* a[MAXB];
+    const u64* p[MAXG][MAXB];
+    u64* o[MAXG];
+    int nb, ng;
+    unsigned acc;
 };
-// limb r of a polynomial (nl limbs) has prime ids[r]
-void bsgs_inner(const ckks_ctx* c, const BsgsTerms& t, u64* o, int nl, const int* ids);
+void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids);
 void autotune_ntt(ckks_ctx* c, int reps);
 void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);

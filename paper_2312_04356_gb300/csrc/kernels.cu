@@ -814,37 +814,56 @@ __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const
 }
 
 // ------------------------------------------------- BSGS inner products ----
-// o[poly][limb] = sum_t a_t[poly][limb] * p_t[limb]: the products are summed exactly in
-// 128 bits (each < 2^122, at most 32 terms) and reduced once.
+// o[g][poly][limb] = sum_b a_b[poly][limb] * p_{g,b}[limb] for NG giant steps at once: each
+// baby value is loaded once and multiplied into every giant step's sum; the products are
+// summed exactly in 128 bits (each < 2^122, at most 32 terms) and reduced once.
 __device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P) {
     return add_mod(mul_shoup(hi, P.r64, P.r64p, P.m.q), reduce64(lo, P.m), P.m.q);
 }
-template <int V>
-__global__ void k_bsgs_inner(kern::BsgsTerms T, u64* __restrict__ o, const DevPrime* __restrict__ primes, int nl,
-                             const int* __restrict__ ids, int logn) {
+template <int V, int NG>
+__global__ void k_bsgs_inner_giants(kern::BsgsGiants T, const DevPrime* __restrict__ primes, int nl,
+                                    const int* __restrict__ ids, int logn) {
     griddep_entry();
     const int limb = blockIdx.y;           // 0 .. 2 nl - 1, polynomial-major
     const int r = limb % nl;
     const DevPrime P = primes[ids[r]];
     const size_t offa = (size_t)limb << logn, offp = (size_t)r << logn;
     EWV_BEGIN(1 << logn)
-    u64 lo[V], hi[V];
+    u64 lo[NG][V], hi[NG][V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) lo[v] = hi[v] = 0;
-    for (int t = 0; t < T.n; ++t) {
-        u64 x[V], y[V];
-        ldv<V>(T.a[t] + offa + j, x);
-        ldv<V>(T.p[t] + offp + j, y);
+    for (int g = 0; g < NG; ++g)
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const u64 pl = x[v] * y[v], ph = __umul64hi(x[v], y[v]);
-            lo[v] += pl;
-            hi[v] += ph + (lo[v] < pl ? 1ull : 0ull);
+        for (int v = 0; v < V; ++v) lo[g][v] = hi[g][v] = 0;
+    for (int b = 0; b < T.nb; ++b) {
+        u64 x[V];
+        ldv<V>(T.a[b] + offa + j, x);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const u64* pg = T.p[g][b];
+            if (!pg) continue;
+            u64 y[V];
+            ldv<V>(pg + offp + j, y);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const u64 pl = x[v] * y[v], ph = __umul64hi(x[v], y[v]);
+                lo[g][v] += pl;
+                hi[g][v] += ph + (lo[g][v] < pl ? 1ull : 0ull);
+            }
         }
     }
 #pragma unroll
-    for (int v = 0; v < V; ++v) lo[v] = reduce128_lazy(hi[v], lo[v], P);
-    stv<V>(o + offa + j, lo);
+    for (int g = 0; g < NG; ++g) {
+        u64 res[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) res[v] = reduce128_lazy(hi[g][v], lo[g][v], P);
+        if ((T.acc >> g) & 1u) {
+            u64 prev[V];
+            ldv<V>(T.o[g] + offa + j, prev);
+#pragma unroll
+            for (int v = 0; v < V; ++v) res[v] = add_mod(res[v], prev[v], P.m.q);
+        }
+        stv<V>(T.o[g] + offa + j, res);
+    }
 }
 
 // ------------------------------------------------------- base conversion ----
@@ -1211,12 +1230,45 @@ void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, 
     LAUNCH_CHECK();
 }
 
-void bsgs_inner(const ckks_ctx* c, const BsgsTerms& t, u64* o, int nl, const int* ids) {
-    CK_CHECK(t.n >= 1 && t.n <= BsgsTerms::MAX, CKKS_EINVAL, "1..32 BSGS terms per kernel");
-    { KTimer kt_(c, "bsgs_inner", (2.0 * t.n + t.n + 2.0) * nl * c->n * 8.0);
-    bool vec = al16(o);
-    for (int i = 0; i < t.n; ++i) vec = vec && al16(t.a[i]) && al16(t.p[i]);
-    EWV_LAUNCH(k_bsgs_inner, vec, 2 * nl, t, o, c->d_primes, nl, ids, c->logn);
+template <int V>
+static void launch_bsgs_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids) {
+    const dim3 grid = ewv_grid(c->n, 2 * nl, V);
+    switch (t.ng) {
+        case 1: klaunch(c, k_bsgs_inner_giants<V, 1>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
+        case 2: klaunch(c, k_bsgs_inner_giants<V, 2>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
+        case 3: klaunch(c, k_bsgs_inner_giants<V, 3>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
+        case 4: klaunch(c, k_bsgs_inner_giants<V, 4>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
+        case 5: klaunch(c, k_bsgs_inner_giants<V, 5>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
+        case 6: klaunch(c, k_bsgs_inner_giants<V, 6>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
+        case 7: klaunch(c, k_bsgs_inner_giants<V, 7>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
+        default: klaunch(c, k_bsgs_inner_giants<V, 8>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
+    }
+}
+
+void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids) {
+    CK_CHECK(t.nb >= 1 && t.nb <= BsgsGiants::MAXB && t.ng >= 1 && t.ng <= BsgsGiants::MAXG, CKKS_EINVAL,
+             "1..32 baby steps and 1..8 giant steps per inner-sum launch");
+    int terms = 0;
+    bool vec = true;
+    for (int b = 0; b < t.nb; ++b) vec = vec && al16(t.a[b]);
+    for (int g = 0; g < t.ng; ++g) {
+        vec = vec && al16(t.o[g]);
+        for (int b = 0; b < t.nb; ++b)
+            if (t.p[g][b]) {
+                ++terms;
+                vec = vec && al16(t.p[g][b]);
+            }
+    }
+    {
+        // algorithmic bytes: every baby (2 polynomials) once, every diagonal once, each giant's
+        // output written (and read when accumulating)
+        int accs = 0;
+        for (int g = 0; g < t.ng; ++g) accs += (t.acc >> g) & 1u;
+        KTimer kt_(c, "bsgs_inner", (2.0 * t.nb + terms + 2.0 * t.ng + 2.0 * accs) * nl * c->n * 8.0);
+        if (vec)
+            launch_bsgs_giants<2>(c, t, nl, ids);
+        else
+            launch_bsgs_giants<1>(c, t, nl, ids);
     }
     LAUNCH_CHECK();
 }

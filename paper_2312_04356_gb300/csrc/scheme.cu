@@ -768,33 +768,41 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
         std::vector<long long> steps;
         for (int b : used_b) steps.push_back(((long long)ps.step * b) % m);
         std::vector<DevBuf> baby = rotate_hoisted_ext(keys, a, steps);
-        std::map<int, int> bidx;
-        for (size_t i = 0; i < used_b.size(); ++i) bidx[used_b[i]] = (int)i;
-        for (int g = 0; g < ps.G(); ++g) {
-            kern::BsgsTerms terms;
-            terms.n = 0;
-            for (int b = 0; b < ps.B; ++b) {
-                auto it = ps.pts.find(std::make_pair(g, b));
-                if (it == ps.pts.end()) continue;
-                CK_CHECK(it->second->ext, CKKS_EINVAL, "BSGS diagonals must be over Q_l u P");
-                CK_CHECK(terms.n < kern::BsgsTerms::MAX, CKKS_EINVAL, "more than 32 baby steps per giant step");
-                terms.a[terms.n] = baby[bidx[b]].ptr;
-                terms.p[terms.n] = it->second->buf.ptr;
-                scale = a.scale * it->second->scale;
-                ++terms.n;
-                c->ops["pmult"]++;
+        // giant steps with at least one non-zero diagonal for this input, in chunks of up to
+        // MAXG: one pass over the baby rotations computes all their inner sums
+        std::vector<int> gs;
+        for (int g = 0; g < ps.G(); ++g)
+            for (int b = 0; b < ps.B; ++b)
+                if (ps.pts.count(std::make_pair(g, b))) {
+                    gs.push_back(g);
+                    break;
+                }
+        for (size_t k0 = 0; k0 < gs.size(); k0 += kern::BsgsGiants::MAXG) {
+            kern::BsgsGiants T;
+            T.nb = (int)used_b.size();
+            T.ng = (int)std::min(gs.size() - k0, (size_t)kern::BsgsGiants::MAXG);
+            T.acc = 0;
+            CK_CHECK(T.nb <= kern::BsgsGiants::MAXB, CKKS_EINVAL, "more than 32 baby steps per giant step");
+            for (int i = 0; i < T.nb; ++i) T.a[i] = baby[i].ptr;
+            for (int q = 0; q < T.ng; ++q) {
+                const int g = gs[k0 + q];
+                for (int i = 0; i < T.nb; ++i) {
+                    auto it = ps.pts.find(std::make_pair(g, used_b[i]));
+                    if (it == ps.pts.end()) {
+                        T.p[q][i] = nullptr;
+                        continue;
+                    }
+                    CK_CHECK(it->second->ext, CKKS_EINVAL, "BSGS diagonals must be over Q_l u P");
+                    T.p[q][i] = it->second->buf.ptr;
+                    scale = a.scale * it->second->scale;
+                    c->ops["pmult"]++;
+                }
+                auto it = inner.find(g);
+                if (it == inner.end()) it = inner.emplace(g, DevBuf(2 * next * n, c->stream)).first;
+                else T.acc |= 1u << q;
+                T.o[q] = it->second.ptr;
             }
-            if (!terms.n) continue;
-            auto it = inner.find(g);
-            if (it == inner.end()) {
-                DevBuf s(2 * next * n, c->stream);
-                kern::bsgs_inner(c, terms, s.ptr, (int)next, ext);
-                inner.emplace(g, std::move(s));
-            } else {
-                DevBuf s(2 * next * n, c->stream);
-                kern::bsgs_inner(c, terms, s.ptr, (int)next, ext);
-                kern::add(c, it->second.ptr, s.ptr, it->second.ptr, 2 * (int)next, ext, (int)next);
-            }
+            kern::bsgs_inner_giants(c, T, (int)next, ext);
         }
     }
     CK_CHECK(!inner.empty(), CKKS_EINVAL, "empty plaintext set");
