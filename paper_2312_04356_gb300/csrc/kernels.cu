@@ -582,6 +582,18 @@ __device__ __forceinline__ void ldv(const u64* p, u64 (&r)[V]) {
         r[0] = p[0];
     }
 }
+// streaming load (evict-first in L1 and L2): for data read once, so that it does not push
+// reused data out of L2
+template <int V>
+__device__ __forceinline__ void ldv_cs(const u64* p, u64 (&r)[V]) {
+    if constexpr (V == 2) {
+        const ulonglong2 t = __ldcs(reinterpret_cast<const ulonglong2*>(p));
+        r[0] = t.x;
+        r[1] = t.y;
+    } else {
+        r[0] = __ldcs(p);
+    }
+}
 template <int V>
 __device__ __forceinline__ void stv(u64* p, const u64 (&r)[V]) {
     if constexpr (V == 2)
@@ -1065,8 +1077,8 @@ __global__ void k_ks_inner_d(const u64* __restrict__ D, int next, const int* __r
     for (int d = 0; d < NDIG; ++d) {
         const u64* Dd = D + ((size_t)d * next + e) * n;
         const size_t kk = d * kstride + (size_t)id * n + j;
-        ldv<V>(kb + kk, yb[d]);
-        ldv<V>(ka + kk, ya[d]);
+        ldv_cs<V>(kb + kk, yb[d]);   // each key word is read once per key switch: keep the
+        ldv_cs<V>(ka + kk, ya[d]);   // raised digits, which every rotation re-reads, in L2
 #pragma unroll
         for (int v = 0; v < V; ++v) x[d][v] = Dd[src[v]];
     }
