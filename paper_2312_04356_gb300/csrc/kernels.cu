@@ -1062,7 +1062,9 @@ __global__ void k_ks_inner(const u64* __restrict__ D, int ndig, int next, const 
 template <bool ACC, int V, int NDIG>
 __global__ void k_ks_inner_d(const u64* __restrict__ D, int next, const int* __restrict__ ext_ids,
                              const u64* __restrict__ kb, const u64* __restrict__ ka, u64* __restrict__ ob,
-                             u64* __restrict__ oa, const DevPrime* __restrict__ P, int logn, u64 g, size_t kstride) {
+                             u64* __restrict__ oa, const DevPrime* __restrict__ P, int logn, u64 g, size_t kstride,
+                             const u64* __restrict__ x0, int x0rows, const u64* __restrict__ s0,
+                             const u64* __restrict__ s0p) {
     griddep_entry();
     const int e = blockIdx.y;
     const int id = ext_ids[e];
@@ -1107,6 +1109,15 @@ __global__ void k_ks_inner_d(const u64* __restrict__ D, int next, const int* __r
         for (int v = 0; v < V; ++v) {
             rb[v] = add_mod(rb[v], pb[v], pr.m.q);
             ra[v] = add_mod(ra[v], pa[v], pr.m.q);
+        }
+    }
+    if (x0 && e < x0rows) {
+        const u64* xr = x0 + (size_t)e * n;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            u64 t = xr[src[v]];
+            if (s0) t = mul_shoup(t, s0[e], s0p[e], pr.m.q);
+            rb[v] = add_mod(rb[v], t, pr.m.q);
         }
     }
     stv<V>(ob + (size_t)e * n + j, rb);
@@ -1490,25 +1501,26 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
 
 template <bool ACC, int V>
 static void launch_ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
-                            const u64* ka, u64* ob, u64* oa, u64 g) {
+                            const u64* ka, u64* ob, u64* oa, u64 g, const u64* x0, int x0rows, const u64* s0,
+                            const u64* s0p) {
     const dim3 grid = ewv_grid(c->n, next, V);
     const size_t ks = (size_t)c->nall << c->logn;
     switch (ndig) {
         case 1:
             klaunch(c, k_ks_inner_d<ACC, V, 1>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks);
+                    c->logn, g, ks, x0, x0rows, s0, s0p);
             break;
         case 2:
             klaunch(c, k_ks_inner_d<ACC, V, 2>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks);
+                    c->logn, g, ks, x0, x0rows, s0, s0p);
             break;
         case 3:
             klaunch(c, k_ks_inner_d<ACC, V, 3>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks);
+                    c->logn, g, ks, x0, x0rows, s0, s0p);
             break;
         case 4:
             klaunch(c, k_ks_inner_d<ACC, V, 4>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks);
+                    c->logn, g, ks, x0, x0rows, s0, s0p);
             break;
         default:
             klaunch(c, k_ks_inner<ACC, V>, grid, EW_THREADS, 0, D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes,
@@ -1518,23 +1530,28 @@ static void launch_ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next,
 }
 
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
-              const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate) {
+              const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate, const u64* x0, int x0rows, const u64* s,
+              const u64* sp) {
     const bool vec = al16(kb) && al16(ka) && al16(ob) && al16(oa);
+    const bool fuse = x0 && x0rows > 0 && ndig <= 4;   // the generic kernel adds x0 in a second pass
     {
-        KTimer kt_(c, "ks_inner", (3.0 * ndig + (accumulate ? 4.0 : 2.0)) * next * c->n * 8.0);
+        KTimer kt_(c, "ks_inner",
+                   (3.0 * ndig + (accumulate ? 4.0 : 2.0) + (fuse ? (double)x0rows / next : 0.0)) * next * c->n * 8.0);
+        const u64* fx = fuse ? x0 : nullptr;
         if (accumulate) {
             if (vec)
-                launch_ks_inner<true, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g);
+                launch_ks_inner<true, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, x0rows, s, sp);
             else
-                launch_ks_inner<true, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g);
+                launch_ks_inner<true, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, x0rows, s, sp);
         } else {
             if (vec)
-                launch_ks_inner<false, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g);
+                launch_ks_inner<false, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, x0rows, s, sp);
             else
-                launch_ks_inner<false, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g);
+                launch_ks_inner<false, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, x0rows, s, sp);
         }
     }
     LAUNCH_CHECK();
+    if (x0 && x0rows > 0 && !fuse) automorph_acc(c, x0, ob, x0rows, g, s, sp, ext_ids, x0rows);
 }
 void mul_scalar_acc(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nl, const int* ids,
                     int lpp) {

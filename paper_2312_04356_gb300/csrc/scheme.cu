@@ -523,16 +523,19 @@ DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out) {
 }
 
 // inner product with switching key `code` (automorphism g applied to D on the fly) over
-// Q_l u P: acc [2][next][N], NTT domain; `accumulate` adds to what acc holds
+// Q_l u P: acc [2][next][N], NTT domain; `accumulate` adds to what acc holds.  With x0, the
+// first x0rows rows of acc's first half also receive s x0(sigma_g) (s null: x0(sigma_g)), the
+// automorphed c0 term of a rotation, in the same kernel.
 void key_switch_inner(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
-                      u64* acc, bool accumulate) {
+                      u64* acc, bool accumulate, const u64* x0 = nullptr, int x0rows = 0, const u64* s = nullptr,
+                      const u64* sp = nullptr) {
     auto it = keys.swk.find(code);
     CK_CHECK(it != keys.swk.end(), CKKS_ENOKEY, "missing switching key (code " + std::to_string(code) + ")");
     const SwitchKey& k = *it->second;
     c->ops["keyswitch"]++;
     const size_t next = (size_t)level + 1 + c->np;
     kern::ks_inner(c, D, ndig, (int)next, c->d_ext_ids[level], k.b.ptr, k.a.ptr, acc, acc + next * c->n, g,
-                   accumulate);
+                   accumulate, x0, x0rows, s, sp);
 }
 
 // ModDown fused with the rescale after it: both halves of acc (Q_l u P, NTT domain) divided
@@ -730,8 +733,7 @@ static std::vector<DevBuf> rotate_hoisted_ext(const ckks_keys& keys, const ckks_
         } else {
             if (!D.ptr) D = mod_up(c, a.c1(), l, &ndig);
             c->ops["hrot"]++;
-            key_switch_inner(c, keys, D.ptr, ndig, l, g, g, o.ptr, false);
-            kern::automorph_acc(c, a.c0(), o.ptr, nl, g, c->d_pmod, c->d_pmod + c->nq, c->d_iota, nl);
+            key_switch_inner(c, keys, D.ptr, ndig, l, g, g, o.ptr, false, a.c0(), nl, c->d_pmod, c->d_pmod + c->nq);
         }
         outs.push_back(std::move(o));
     }
@@ -828,9 +830,8 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
         int ndig = 0;
         DevBuf D = mod_up(c, c1q.ptr, l, &ndig);
         if (!have_acc) acc = DevBuf(2 * next * n, c->stream);
-        key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, acc.ptr, have_acc);
+        key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, acc.ptr, have_acc, x, (int)next);
         have_acc = true;
-        kern::automorph_acc(c, x, acc.ptr, (int)next, gal, nullptr, nullptr, ext, (int)next);
     }
     if (rescale_out) {
         ckks_ct o = new_ct(c, l - 1, scale / (double)c->q[l]);
