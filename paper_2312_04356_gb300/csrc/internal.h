@@ -230,6 +230,16 @@ struct BsgsGiants {
     unsigned acc;
 };
 void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids);
+// o = sum_t w_t a_t (mod q per limb) for up to MAX terms with signed integer weights: the
+// integer-weighted sum of a Chebyshev leaf in one pass.  Arrays of nl limbs, limb k with
+// prime ids[k % lpp].
+struct LinComb {
+    static constexpr int MAX = 16;
+    const u64* a[MAX];
+    long long w[MAX];
+    int n;
+};
+void lincomb(const ckks_ctx* c, const LinComb& t, u64* o, int nl, const int* ids, int lpp);
 void autotune_ntt(ckks_ctx* c, int reps);
 void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);

@@ -915,20 +915,18 @@ static PolyVal cheb_leaf(ChebPowers& pw, const std::vector<double>& c) {
     int lev = 1 << 30;
     for (int k : ks) lev = std::min(lev, pw.T.at(k).level);
     const int target = lev - 1;
-    ckks_ct acc;
-    bool have = false;
+    CK_CHECK((int)ks.size() <= kern::LinComb::MAX, CKKS_EINVAL, "Chebyshev leaf with more than 16 terms");
+    kern::LinComb L;
+    L.n = 0;
     for (int k : ks) {
         const ckks_ct& t = pw.at(k, lev);
         const double s_c = (ctx->delta[target] * (double)ctx->q[lev]) / t.scale;
-        const int64_t w = llround_away(c[k] * s_c);
-        if (!have) {
-            acc = mul_int(t, w);
-            have = true;
-        } else {
-            ckks_ct term = mul_int(t, w);
-            kern::add(ctx, acc.buf.ptr, term.buf.ptr, acc.buf.ptr, 2 * (lev + 1), ctx->d_iota, lev + 1);
-        }
+        L.a[L.n] = t.buf.ptr;
+        L.w[L.n] = llround_away(c[k] * s_c);
+        ++L.n;
     }
+    ckks_ct acc = new_ct(ctx, lev, 0.0);
+    kern::lincomb(ctx, L, acc.buf.ptr, 2 * (lev + 1), ctx->d_iota, lev + 1);
     acc = rescale(acc);
     acc.scale = ctx->delta[target];
     out.ct = add_const(acc, c[0]);
