@@ -266,10 +266,13 @@ void automorph_acc(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, u64 g, c
 // X^{N/2} times a, NTT domain: pointwise by psi^((2 rev(i)+1) N/2)
 void imult(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, const int* ids, int lpp);
 // centred lift of one coefficient-domain limb with prime `src_id` into nlimbs limbs
-void lift_centred(const ckks_ctx* c, const u64* src, int src_id, u64* o, int nlimbs, const int* ids);
-// out_i = (a_i - b_i) * s_i  (s device residues per limb index % lpp, Shoup companions sp)
+// (lpp > 0: row k lifts the source row k / lpp, at src + (k / lpp) * src_pstride, to prime ids[k % lpp])
+void lift_centred(const ckks_ctx* c, const u64* src, int src_id, u64* o, int nlimbs, const int* ids, int lpp = 0,
+                  size_t src_pstride = 0);
+// out_i = (a_i - b_i) * s_i  (s device residues per limb index % lpp, Shoup companions sp); with
+// a_pstride, row k of a is at a + (k / lpp) * a_pstride + (k % lpp) * N (b and out contiguous)
 void sub_mul_scalar(const ckks_ctx* c, const u64* a, const u64* b, const u64* s, const u64* sp, u64* o,
-                    int nlimbs, const int* ids, int lpp);
+                    int nlimbs, const int* ids, int lpp, size_t a_pstride = 0);
 // fast base conversion, coefficient domain: in [nin][N] (limb stride in_stride words),
 // out rows written at out + out_row[m]*N
 void base_convert(const ckks_ctx* c, const ConvTab& t, const u64* in, size_t in_stride, u64* out,

@@ -821,30 +821,33 @@ __global__ void k_imult(const u64* a, u64* o, const DevPrime* P, const int* ids,
     }
 }
 template <int V>
-__global__ void k_lift_centred(const u64* src, u64 qs, u64* o, const DevPrime* P, const int* ids, int logn) {
+__global__ void k_lift_centred(const u64* src, u64 qs, u64* o, const DevPrime* P, const int* ids, int lpp,
+                               size_t src_pstride, int logn) {
     griddep_entry();
     const int limb = blockIdx.y;
-    const DevMod t = P[ids[limb]].m;
+    const DevMod t = P[ids[limb % lpp]].m;
     const size_t off = (size_t)limb << logn;
+    const u64* sr = src + (size_t)(limb / lpp) * src_pstride;
     EWV_BEGIN(1 << logn)
     u64 x[V];
-    ldv<V>(src + j, x);
+    ldv<V>(sr + j, x);
 #pragma unroll
     for (int v = 0; v < V; ++v) x[v] = centred_to(x[v], qs, t);
     stv<V>(o + off + j, x);
 }
 template <int V>
 __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const u64* sp, u64* o,
-                                 const DevPrime* P, const int* ids, int lpp, int logn) {
+                                 const DevPrime* P, const int* ids, int lpp, size_t a_pstride, int logn) {
     griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
     const u64 w = s[r], wp = sp[r];
     const size_t off = (size_t)limb << logn;
+    const size_t offa = a_pstride ? (size_t)(limb / lpp) * a_pstride + ((size_t)r << logn) : off;
     EWV_BEGIN(1 << logn)
     u64 x[V], y[V];
-    ldv<V>(a + off + j, x);
+    ldv<V>(a + offa + j, x);
     ldv<V>(b + off + j, y);
 #pragma unroll
     for (int v = 0; v < V; ++v) x[v] = mul_shoup(sub_mod(x[v], y[v], q), w, wp, q);
@@ -1443,18 +1446,22 @@ void imult(const ckks_ctx* c, const u64* a, u64* o, int nl, const int* ids, int 
     }
     LAUNCH_CHECK();
 }
-void lift_centred(const ckks_ctx* c, const u64* src, int src_id, u64* o, int nl, const int* ids) {
+void lift_centred(const ckks_ctx* c, const u64* src, int src_id, u64* o, int nl, const int* ids, int lpp,
+                  size_t src_pstride) {
     if (nl <= 0) return;
+    if (lpp <= 0) lpp = nl;
     { KTimer kt_(c, "lift_centred", (nl + 1.0) * c->n * 8.0);
-    EWV_LAUNCH(k_lift_centred, al16(src) && al16(o), nl, src, c->mod_of[src_id], o, c->d_primes, ids, c->logn);
+    EWV_LAUNCH(k_lift_centred, al16(src) && al16(o) && src_pstride % 2 == 0, nl, src, c->mod_of[src_id], o,
+               c->d_primes, ids, lpp, src_pstride, c->logn);
     }
     LAUNCH_CHECK();
 }
 void sub_mul_scalar(const ckks_ctx* c, const u64* a, const u64* b, const u64* s, const u64* sp, u64* o, int nl,
-                    const int* ids, int lpp) {
+                    const int* ids, int lpp, size_t a_pstride) {
     if (nl <= 0) return;
     { KTimer kt_(c, "sub_mul_scalar", 3.0 * (double)nl * c->n * 8.0);
-    EWV_LAUNCH(k_sub_mul_scalar, al16(a) && al16(b) && al16(o), nl, a, b, s, sp, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_sub_mul_scalar, al16(a) && al16(b) && al16(o) && a_pstride % 2 == 0, nl, a, b, s, sp, o, c->d_primes,
+               ids, lpp, a_pstride, c->logn);
     }
     LAUNCH_CHECK();
 }

@@ -63,14 +63,11 @@ extern "C" int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, int lev
         CUDA_CHECK(cudaMemcpyAsync(last, in0 + (size_t)level * n, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
         CUDA_CHECK(cudaMemcpyAsync(last + n, in1 + (size_t)level * n, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
         kern::ntt_inverse(ctx, last, 2, ctx->d_iota + level, 1);
-        kern::lift_centred(ctx, last, level, lift, level, ctx->d_iota);
-        kern::lift_centred(ctx, last + n, level, lift + (size_t)level * n, level, ctx->d_iota);
+        kern::lift_centred(ctx, last, level, lift, 2 * level, ctx->d_iota, level, n);   // both polynomials
         kern::ntt_forward(ctx, lift, 2 * level, ctx->d_iota, level);
         const u64* s = ctx->d_qlinv + (size_t)level * ctx->nq;
         const u64* sp = ctx->d_qlinv + (size_t)ctx->nq * ctx->nq + (size_t)level * ctx->nq;
-        kern::sub_mul_scalar(ctx, in0, lift, s, sp, out0, level, ctx->d_iota, level);
-        kern::sub_mul_scalar(ctx, in1, lift + (size_t)level * n, s, sp, out0 + (size_t)level * n, level, ctx->d_iota,
-                             level);
+        kern::sub_mul_scalar(ctx, in0, lift, s, sp, out0, 2 * level, ctx->d_iota, level, (size_t)nl * n);
         ctx->ops["rescale"]++;
     } catch (const CkksError& e) {
         ctx->err = e.msg;

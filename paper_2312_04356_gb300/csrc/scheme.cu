@@ -434,14 +434,12 @@ ckks_ct rescale(const ckks_ct& a) {
     CUDA_CHECK(cudaMemcpyAsync(last.ptr + n, a.c1() + (size_t)l * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
     kern::ntt_inverse(c, last.ptr, 2, c->d_iota + l, 1);
     DevBuf lift(2 * (size_t)l * n, c->stream);
-    kern::lift_centred(c, last.ptr, l, lift.ptr, l, c->d_iota);
-    kern::lift_centred(c, last.ptr + n, l, lift.ptr + (size_t)l * n, l, c->d_iota);
+    kern::lift_centred(c, last.ptr, l, lift.ptr, 2 * l, c->d_iota, l, n);     // both polynomials
     kern::ntt_forward(c, lift.ptr, 2 * l, c->d_iota, l);
     ckks_ct o = new_ct(c, l - 1, a.scale / (double)c->q[l]);
     const u64* s = c->d_qlinv + (size_t)l * c->nq;
     const u64* sp = c->d_qlinv + (size_t)c->nq * c->nq + (size_t)l * c->nq;
-    kern::sub_mul_scalar(c, a.c0(), lift.ptr, s, sp, o.c0(), l, c->d_iota, l);
-    kern::sub_mul_scalar(c, a.c1(), lift.ptr + (size_t)l * n, s, sp, o.c1(), l, c->d_iota, l);
+    kern::sub_mul_scalar(c, a.c0(), lift.ptr, s, sp, o.c0(), 2 * l, c->d_iota, l, (size_t)(l + 1) * n);
     return o;
 }
 
@@ -560,8 +558,7 @@ void mod_down_rescale(ckks_ctx* c, u64* acc, int level, u64* out) {
     kern::ntt_forward(c, conv.ptr, 2 * l, c->d_iota, l);
     const u64* s = c->d_pqlinv + (size_t)l * c->nq;
     const u64* sp = c->d_pqlinv + (size_t)c->nq * c->nq + (size_t)l * c->nq;
-    kern::sub_mul_scalar(c, ab, conv.ptr, s, sp, out, l, c->d_iota, l);
-    kern::sub_mul_scalar(c, aa, conv.ptr + (size_t)l * n, s, sp, out + (size_t)l * n, l, c->d_iota, l);
+    kern::sub_mul_scalar(c, ab, conv.ptr, s, sp, out, 2 * l, c->d_iota, l, next * n);    // aa = ab + next N
 }
 
 // acc (Q_l u P) += P x on the Q rows, x [2][l+1][N]
@@ -591,8 +588,13 @@ static void mod_down(ckks_ctx* c, u64* acc, int level, u64* out0, u64* out1) {
     kern::base_convert(c, c->moddown_tab(level), ab + (size_t)nl * n, n, conv.ptr, n, 2, (size_t)next * n,
                        (size_t)nl * n);
     kern::ntt_forward(c, conv.ptr, 2 * nl, c->d_iota, nl);
-    kern::sub_mul_scalar(c, ab, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out0, nl, c->d_iota, nl);
-    kern::sub_mul_scalar(c, aa, conv.ptr + (size_t)nl * n, c->d_pinv, c->d_pinv + c->nq, out1, nl, c->d_iota, nl);
+    if (out1 == out0 + (size_t)nl * n && aa == ab + next * n) {
+        kern::sub_mul_scalar(c, ab, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out0, 2 * nl, c->d_iota, nl, next * n);
+    } else {
+        kern::sub_mul_scalar(c, ab, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out0, nl, c->d_iota, nl);
+        kern::sub_mul_scalar(c, aa, conv.ptr + (size_t)nl * n, c->d_pinv, c->d_pinv + c->nq, out1, nl, c->d_iota,
+                             nl);
+    }
 }
 
 // inner product with switching key `code` (automorphism g applied to D on the fly), ModDown
