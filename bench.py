@@ -34,6 +34,16 @@ METRIC = "ms per conv2d+bootstrap block at N=2^16"
 # launch scales with its limbs, so the in-block traffic per launch is this ratio times the
 # launch's algorithmic bytes.
 NTT_FWD_DRAM_PER_ALGO_BYTE = (134.4 + 81.0 + 186.5 + 89.4) / (2 * 268.4)
+# The same ratio for the key-switch inner product, from the ncu capture of `--kernel ks`
+# (profiles/keyswitch_kernels_full.md): one launch at the top level, 3 digits x 31 extended
+# limbs with the automorphed c0 term on 24 rows = (3*3 + 2) * 31 + 24 = 365 limbs of
+# algorithmic traffic (191.4 MB); DRAM read 146.3 MB + write 3.6 MB (cold caches under ncu).
+KS_DRAM_PER_ALGO_BYTE = (146.3 + 3.6) / (365 * 65536 * 8 / 1e6)
+ROOF_NOTES = {
+    "ntt_fwd": "integer-multiply-pipe bound (fmaheavy 67-73% busy, DRAM 24-35% under ncu); see roofline_ntt_alu",
+    "ks_inner": "HBM bound: switching keys streamed once (evict-first), raised digits gathered through the Galois "
+                "permutation; DRAM 55% of peak under ncu with cold caches",
+}
 CONFIG = "cfg2"
 
 
@@ -430,11 +440,14 @@ def run_ours(args):
     pk = peaks()
     achieved = top[1]["bytes"] / (top[1]["ms"] * 1e-3) / 1e9
     per_launch = top[1]["bytes"] / top[1]["launches"]
-    traffic = round(NTT_FWD_DRAM_PER_ALGO_BYTE * per_launch) if top[0] == "ntt_fwd" else None
+    ratio = {"ntt_fwd": NTT_FWD_DRAM_PER_ALGO_BYTE, "ks_inner": KS_DRAM_PER_ALGO_BYTE}.get(top[0])
+    traffic = round(ratio * per_launch) if ratio else None
     roof = {"kernel": top[0], "bound": "hbm", "achieved": round(achieved, 1), "peak": pk.get("hbm_gbs"),
             "unit": "GB/s", "frac": round(achieved / pk.get("hbm_gbs"), 4), "traffic": traffic,
             "algorithmic_bytes_per_launch": round(per_launch),
-            "note": "the NTT passes are integer-pipe bound (ALU pipe ~51%, DRAM ~31% under ncu)",
+            "traffic_source": "DRAM bytes per algorithmic byte of the kernel's ncu capture x this launch's "
+                              "algorithmic bytes" if ratio else None,
+            "note": ROOF_NOTES.get(top[0]),
             "share": round(top[1]["ms"] / total, 4),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if not pk.get("fallback") else "fallback",
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),

@@ -230,13 +230,15 @@ struct BsgsGiants {
     unsigned acc;
 };
 void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids);
-// o = sum_t w_t a_t (mod q per limb) for up to MAX terms with signed integer weights: the
-// integer-weighted sum of a Chebyshev leaf in one pass.  Arrays of nl limbs, limb k with
-// prime ids[k % lpp].
+// o = sum_t w_t a_t (mod q per limb) for up to MAX terms: the integer-weighted sum of a
+// Chebyshev leaf in one pass.  Arrays of nl limbs, limb k with prime ids[k % lpp]; w[t][r]
+// is the weight's residue for limb index r < lpp, wp[t][r] its Shoup companion (passed by
+// value: about 10 KB of kernel parameters).
 struct LinComb {
-    static constexpr int MAX = 16;
+    static constexpr int MAX = 16, MAXL = 40;
     const u64* a[MAX];
-    long long w[MAX];
+    u64 w[MAX][MAXL];
+    u64 wp[MAX][MAXL];
     int n;
 };
 void lincomb(const ckks_ctx* c, const LinComb& t, u64* o, int nl, const int* ids, int lpp);

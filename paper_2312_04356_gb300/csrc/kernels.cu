@@ -708,29 +708,24 @@ __global__ void k_mul_scalar_v(const u64* a, ScalarVec sv, u64* o, const DevPrim
     for (int v = 0; v < V; ++v) x[v] = mul_shoup(x[v], w, wp, q);
     stv<V>(o + off + j, x);
 }
-// v mod q for a signed 64-bit v
-__device__ __forceinline__ u64 signed_residue(long long v, const DevMod& m) {
-    const u64 a = v < 0 ? (u64)(-(v + 1)) + 1ull : (u64)v;
-    const u64 r = reduce64(a, m);
-    return (v < 0 && r) ? m.q - r : r;
-}
 template <int V>
-__global__ void k_lincomb(kern::LinComb T, u64* __restrict__ o, const DevPrime* __restrict__ P,
-                          const int* __restrict__ ids, int lpp, int logn) {
+__global__ void k_lincomb(const __grid_constant__ kern::LinComb T, u64* __restrict__ o,
+                          const DevPrime* __restrict__ P, const int* __restrict__ ids, int lpp, int logn) {
     griddep_entry();
     const int limb = blockIdx.y;
-    const DevMod m = P[ids[limb % lpp]].m;
+    const int r = limb % lpp;
+    const u64 q = P[ids[r]].m.q;
     const size_t off = (size_t)limb << logn;
     EWV_BEGIN(1 << logn)
     u64 acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = 0;
     for (int t = 0; t < T.n; ++t) {
-        const u64 w = signed_residue(T.w[t], m);
+        const u64 w = T.w[t][r], wp = T.wp[t][r];
         u64 x[V];
         ldv<V>(T.a[t] + off + j, x);
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = add_mod(acc[v], mul_mod(x[v], w, m), m.q);
+        for (int v = 0; v < V; ++v) acc[v] = add_mod(acc[v], mul_shoup(x[v], w, wp, q), q);
     }
     stv<V>(o + off + j, acc);
 }
@@ -1394,7 +1389,8 @@ void mul_scalar_v(const ckks_ctx* c, const u64* a, const ScalarVec& sv, u64* o, 
 }
 void lincomb(const ckks_ctx* c, const LinComb& t, u64* o, int nl, const int* ids, int lpp) {
     if (nl <= 0) return;
-    CK_CHECK(t.n >= 1 && t.n <= LinComb::MAX, CKKS_EINVAL, "1..16 terms per linear combination");
+    CK_CHECK(t.n >= 1 && t.n <= LinComb::MAX && lpp <= LinComb::MAXL, CKKS_EINVAL,
+             "1..16 terms over at most 40 limbs per linear combination");
     bool vec = al16(o);
     for (int i = 0; i < t.n; ++i) vec = vec && al16(t.a[i]);
     { KTimer kt_(c, "lincomb", (t.n + 1.0) * (double)nl * c->n * 8.0);

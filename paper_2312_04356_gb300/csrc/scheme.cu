@@ -923,8 +923,12 @@ static PolyVal cheb_leaf(ChebPowers& pw, const std::vector<double>& c) {
     for (int k : ks) {
         const ckks_ct& t = pw.at(k, lev);
         const double s_c = (ctx->delta[target] * (double)ctx->q[lev]) / t.scale;
+        const long long w = llround_away(c[k] * s_c);
         L.a[L.n] = t.buf.ptr;
-        L.w[L.n] = llround_away(c[k] * s_c);
+        for (int i = 0; i <= lev; ++i) {
+            L.w[L.n][i] = from_signed(w, ctx->q[i]);
+            L.wp[L.n][i] = shoup(L.w[L.n][i], ctx->q[i]);
+        }
         ++L.n;
     }
     ckks_ct acc = new_ct(ctx, lev, 0.0);
