@@ -301,10 +301,14 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly);
 // ob/oa [next][N] = sum_d D_d(sigma_g) * key_d ; g = 1 means no automorphism
 // x0 (optional, rows [x0rows][N] with the primes of the first x0rows extended limbs): ob row e
 // += s[e] * x0[e](sigma_g) for e < x0rows (s null: unscaled), the automorphed c0 term of a
-// rotation, gathered with the same permutation as D
+// rotation, gathered with the same permutation as D; x1 (optional) likewise into oa (the
+// P-lifted d0, d1 of a relinearisation, g = 1)
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
               const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate = false, const u64* x0 = nullptr,
-              int x0rows = 0, const u64* s = nullptr, const u64* sp = nullptr);
+              int x0rows = 0, const u64* s = nullptr, const u64* sp = nullptr, const u64* x1 = nullptr);
+// d0 = a0 b0, d1 = a0 b1 + a1 b0 (d [2][nl][N]), d2 = a1 b1 (e [nl][N]) over nl limbs with
+// primes ids[0..nl); a, b [2][nl][N]
+void tensor(const ckks_ctx* c, const u64* a, const u64* b, u64* d, u64* e, int nl, const int* ids);
 // o += a * s[limb % lpp] (s residues, sp their Shoup companions; device arrays)
 void mul_scalar_acc(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nlimbs, const int* ids,
                     int lpp);

@@ -660,6 +660,31 @@ __global__ void k_mul(const u64* a, const u64* b, u64* o, const DevPrime* P, con
     for (int v = 0; v < V; ++v) x[v] = mul_mod(x[v], y[v], m);
     stv<V>(o + off + j, x);
 }
+// tensor product of two ciphertexts: d0 = a0 b0, d1 = a0 b1 + a1 b0 (d [2][nl][N]), d2 = a1 b1
+// (e [nl][N]); a, b [2][nl][N]; one pass over the nl limbs
+template <int V>
+__global__ void k_tensor(const u64* a, const u64* b, u64* d, u64* e, const DevPrime* P, const int* ids, int nl,
+                         int logn) {
+    griddep_entry();
+    const int limb = blockIdx.y;
+    const DevMod m = P[ids[limb]].m;
+    const size_t off = (size_t)limb << logn, ps = (size_t)nl << logn;
+    EWV_BEGIN(1 << logn)
+    u64 a0[V], a1[V], b0[V], b1[V], d0[V], d1[V], d2[V];
+    ldv<V>(a + off + j, a0);
+    ldv<V>(a + ps + off + j, a1);
+    ldv<V>(b + off + j, b0);
+    ldv<V>(b + ps + off + j, b1);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        d0[v] = mul_mod(a0[v], b0[v], m);
+        d1[v] = add_mod(mul_mod(a0[v], b1[v], m), mul_mod(a1[v], b0[v], m), m.q);
+        d2[v] = mul_mod(a1[v], b1[v], m);
+    }
+    stv<V>(d + off + j, d0);
+    stv<V>(d + ps + off + j, d1);
+    stv<V>(e + off + j, d2);
+}
 template <int V>
 __global__ void k_mul_acc(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
     griddep_entry();
@@ -1087,8 +1112,8 @@ template <bool ACC, int V, int NDIG>
 __global__ void k_ks_inner_d(const u64* __restrict__ D, int next, const int* __restrict__ ext_ids,
                              const u64* __restrict__ kb, const u64* __restrict__ ka, u64* __restrict__ ob,
                              u64* __restrict__ oa, const DevPrime* __restrict__ P, int logn, u64 g, size_t kstride,
-                             const u64* __restrict__ x0, int x0rows, const u64* __restrict__ s0,
-                             const u64* __restrict__ s0p) {
+                             const u64* __restrict__ x0, const u64* __restrict__ x1, int x0rows,
+                             const u64* __restrict__ s0, const u64* __restrict__ s0p) {
     griddep_entry();
     const int e = blockIdx.y;
     const int id = ext_ids[e];
@@ -1142,6 +1167,15 @@ __global__ void k_ks_inner_d(const u64* __restrict__ D, int next, const int* __r
             u64 t = xr[src[v]];
             if (s0) t = mul_shoup(t, s0[e], s0p[e], pr.m.q);
             rb[v] = add_mod(rb[v], t, pr.m.q);
+        }
+        if (x1) {
+            const u64* yr = x1 + (size_t)e * n;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                u64 t = yr[src[v]];
+                if (s0) t = mul_shoup(t, s0[e], s0p[e], pr.m.q);
+                ra[v] = add_mod(ra[v], t, pr.m.q);
+            }
         }
     }
     stv<V>(ob + (size_t)e * n + j, rb);
@@ -1364,6 +1398,13 @@ void mul(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const in
     }
     LAUNCH_CHECK();
 }
+void tensor(const ckks_ctx* c, const u64* a, const u64* b, u64* d, u64* e, int nl, const int* ids) {
+    if (nl <= 0) return;
+    { KTimer kt_(c, "tensor", 7.0 * (double)nl * c->n * 8.0);
+    EWV_LAUNCH(k_tensor, al16(a) && al16(b) && al16(d) && al16(e), nl, a, b, d, e, c->d_primes, ids, nl, c->logn);
+    }
+    LAUNCH_CHECK();
+}
 void mul_acc(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
     if (nl <= 0) return;
     { KTimer kt_(c, "mul_acc", 4.0 * (double)nl * c->n * 8.0);
@@ -1540,26 +1581,26 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
 
 template <bool ACC, int V>
 static void launch_ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
-                            const u64* ka, u64* ob, u64* oa, u64 g, const u64* x0, int x0rows, const u64* s0,
-                            const u64* s0p) {
+                            const u64* ka, u64* ob, u64* oa, u64 g, const u64* x0, const u64* x1, int x0rows,
+                            const u64* s0, const u64* s0p) {
     const dim3 grid = ewv_grid(c->n, next, V);
     const size_t ks = (size_t)c->nall << c->logn;
     switch (ndig) {
         case 1:
             klaunch(c, k_ks_inner_d<ACC, V, 1>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks, x0, x0rows, s0, s0p);
+                    c->logn, g, ks, x0, x1, x0rows, s0, s0p);
             break;
         case 2:
             klaunch(c, k_ks_inner_d<ACC, V, 2>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks, x0, x0rows, s0, s0p);
+                    c->logn, g, ks, x0, x1, x0rows, s0, s0p);
             break;
         case 3:
             klaunch(c, k_ks_inner_d<ACC, V, 3>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks, x0, x0rows, s0, s0p);
+                    c->logn, g, ks, x0, x1, x0rows, s0, s0p);
             break;
         case 4:
             klaunch(c, k_ks_inner_d<ACC, V, 4>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks, x0, x0rows, s0, s0p);
+                    c->logn, g, ks, x0, x1, x0rows, s0, s0p);
             break;
         default:
             klaunch(c, k_ks_inner<ACC, V>, grid, EW_THREADS, 0, D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes,
@@ -1570,27 +1611,31 @@ static void launch_ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next,
 
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
               const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate, const u64* x0, int x0rows, const u64* s,
-              const u64* sp) {
+              const u64* sp, const u64* x1) {
     const bool vec = al16(kb) && al16(ka) && al16(ob) && al16(oa);
-    const bool fuse = x0 && x0rows > 0 && ndig <= 4;   // the generic kernel adds x0 in a second pass
+    const bool fuse = x0 && x0rows > 0 && ndig <= 4;   // the generic kernel adds x0, x1 in further passes
     {
-        KTimer kt_(c, "ks_inner",
-                   (3.0 * ndig + (accumulate ? 4.0 : 2.0) + (fuse ? (double)x0rows / next : 0.0)) * next * c->n * 8.0);
+        const double extra = fuse ? (double)x0rows * (x1 ? 2.0 : 1.0) / next : 0.0;
+        KTimer kt_(c, "ks_inner", (3.0 * ndig + (accumulate ? 4.0 : 2.0) + extra) * next * c->n * 8.0);
         const u64* fx = fuse ? x0 : nullptr;
+        const u64* fy = fuse ? x1 : nullptr;
         if (accumulate) {
             if (vec)
-                launch_ks_inner<true, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, x0rows, s, sp);
+                launch_ks_inner<true, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp);
             else
-                launch_ks_inner<true, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, x0rows, s, sp);
+                launch_ks_inner<true, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp);
         } else {
             if (vec)
-                launch_ks_inner<false, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, x0rows, s, sp);
+                launch_ks_inner<false, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp);
             else
-                launch_ks_inner<false, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, x0rows, s, sp);
+                launch_ks_inner<false, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp);
         }
     }
     LAUNCH_CHECK();
-    if (x0 && x0rows > 0 && !fuse) automorph_acc(c, x0, ob, x0rows, g, s, sp, ext_ids, x0rows);
+    if (x0 && x0rows > 0 && !fuse) {
+        automorph_acc(c, x0, ob, x0rows, g, s, sp, ext_ids, x0rows);
+        if (x1) automorph_acc(c, x1, oa, x0rows, g, s, sp, ext_ids, x0rows);
+    }
 }
 void mul_scalar_acc(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nl, const int* ids,
                     int lpp) {

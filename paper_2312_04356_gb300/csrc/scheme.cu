@@ -526,14 +526,14 @@ DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out) {
 // automorphed c0 term of a rotation, in the same kernel.
 void key_switch_inner(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
                       u64* acc, bool accumulate, const u64* x0 = nullptr, int x0rows = 0, const u64* s = nullptr,
-                      const u64* sp = nullptr) {
+                      const u64* sp = nullptr, const u64* x1 = nullptr) {
     auto it = keys.swk.find(code);
     CK_CHECK(it != keys.swk.end(), CKKS_ENOKEY, "missing switching key (code " + std::to_string(code) + ")");
     const SwitchKey& k = *it->second;
     c->ops["keyswitch"]++;
     const size_t next = (size_t)level + 1 + c->np;
     kern::ks_inner(c, D, ndig, (int)next, c->d_ext_ids[level], k.b.ptr, k.a.ptr, acc, acc + next * c->n, g,
-                   accumulate, x0, x0rows, s, sp);
+                   accumulate, x0, x0rows, s, sp, x1);
 }
 
 // ModDown fused with the rescale after it: both halves of acc (Q_l u P, NTT domain) divided
@@ -664,10 +664,7 @@ ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
     const size_t n = c->n;
     ckks_ct o = new_ct(c, l, a.scale * b.scale);
     DevBuf d2(nl * n, c->stream);
-    kern::mul(c, a.c0(), b.c0(), o.c0(), nl, c->d_iota, nl);
-    kern::mul(c, a.c0(), b.c1(), o.c1(), nl, c->d_iota, nl);
-    kern::mul_acc(c, a.c1(), b.c0(), o.c1(), nl, c->d_iota, nl);
-    kern::mul(c, a.c1(), b.c1(), d2.ptr, nl, c->d_iota, nl);
+    kern::tensor(c, a.buf.ptr, b.buf.ptr, o.buf.ptr, d2.ptr, nl, c->d_iota);
     int ndig = 0;
     DevBuf D = mod_up(c, d2.ptr, l, &ndig);
     DevBuf k(2 * nl * n, c->stream);
@@ -689,15 +686,12 @@ ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct
     u64* d0 = d.ptr;
     u64* d1 = d.ptr + (size_t)nl * n;
     u64* d2 = d.ptr + 2 * (size_t)nl * n;
-    kern::mul(c, a.c0(), b.c0(), d0, nl, c->d_iota, nl);
-    kern::mul(c, a.c0(), b.c1(), d1, nl, c->d_iota, nl);
-    kern::mul_acc(c, a.c1(), b.c0(), d1, nl, c->d_iota, nl);
-    kern::mul(c, a.c1(), b.c1(), d2, nl, c->d_iota, nl);
+    kern::tensor(c, a.buf.ptr, b.buf.ptr, d0, d2, nl, c->d_iota);
     int ndig = 0;
     DevBuf D = mod_up(c, d2, l, &ndig);
     DevBuf acc(2 * ((size_t)nl + c->np) * n, c->stream);
-    key_switch_inner(c, keys, D.ptr, ndig, l, 0, 1, acc.ptr, false);
-    lift_p(c, d0, acc.ptr, l);
+    // relinearisation key switch with P d0, P d1 added on the Q rows in the same kernel
+    key_switch_inner(c, keys, D.ptr, ndig, l, 0, 1, acc.ptr, false, d0, nl, c->d_pmod, c->d_pmod + c->nq, d1);
     ckks_ct o = new_ct(c, l - 1, a.scale * b.scale / (double)c->q[l]);
     mod_down_rescale(c, acc.ptr, l, o.buf.ptr);
     return o;
