@@ -88,6 +88,7 @@ struct ckks_ctx {
     int* d_iota = nullptr;                   // 0..nall-1
     u64* d_pinv = nullptr;                   // P^{-1} mod q_i [nq], Shoup [nq]
     u64* d_qlinv = nullptr;                  // q_l^{-1} mod q_i [nq][nq], Shoup [nq][nq]
+    std::vector<u64> h_qlinv;                // host copy of the residues [nq][nq]
     u64* d_pqlinv = nullptr;                 // (P q_l)^{-1} mod q_i [nq][nq], Shoup [nq][nq]
     u64* d_pmod = nullptr;                   // P mod q_i [nq], Shoup [nq]
     std::vector<int*> d_ext_ids;             // per level: [0..l] + specials
@@ -254,7 +255,13 @@ void mul_acc(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, 
 void mul_scalar(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nlimbs, const int* ids,
                 int lpp);
 // by-value variants (no upload; usable inside stream capture)
-void mul_scalar_v(const ckks_ctx* c, const u64* a, const ScalarVec& sv, u64* o, int nlimbs, const int* ids, int lpp);
+// (a_pstride: row k of a at a + (k / lpp) * a_pstride + (k % lpp) * N; o contiguous)
+void mul_scalar_v(const ckks_ctx* c, const u64* a, const ScalarVec& sv, u64* o, int nlimbs, const int* ids, int lpp,
+                  size_t a_pstride = 0);
+// out_k = a_k s1[r] - b_k s2[r] (r = k % lpp; s1 by value, s2/s2p device residues and Shoup
+// companions; a rows as in mul_scalar_v, b and out contiguous)
+void sub_mul2_scalar(const ckks_ctx* c, const u64* a, const u64* b, const ScalarVec& s1, const u64* s2,
+                     const u64* s2p, u64* o, int nlimbs, const int* ids, int lpp, size_t a_pstride);
 void add_scalar_v(const ckks_ctx* c, u64* a, const ScalarVec& sv, int nlimbs, const int* ids, int lpp);
 // a[limb][*] += v[limb]: adds the constant polynomial v in the NTT domain (device array v)
 void add_const_term(const ckks_ctx* c, u64* a, const u64* v, int nlimbs, const int* ids);

@@ -719,16 +719,17 @@ __global__ void k_mul_scalar(const u64* a, const u64* s, const u64* sp, u64* o, 
 // per-limb scalars passed by value (no host-to-device copy, so the launch can be captured)
 template <int V>
 __global__ void k_mul_scalar_v(const u64* a, ScalarVec sv, u64* o, const DevPrime* P, const int* ids, int lpp,
-                               int logn) {
+                               size_t a_pstride, int logn) {
     griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
     const u64 w = sv.v[r], wp = sv.vp[r];
     const size_t off = (size_t)limb << logn;
+    const size_t offa = a_pstride ? (size_t)(limb / lpp) * a_pstride + ((size_t)r << logn) : off;
     EWV_BEGIN(1 << logn)
     u64 x[V];
-    ldv<V>(a + off + j, x);
+    ldv<V>(a + offa + j, x);
 #pragma unroll
     for (int v = 0; v < V; ++v) x[v] = mul_shoup(x[v], w, wp, q);
     stv<V>(o + off + j, x);
@@ -853,6 +854,24 @@ __global__ void k_lift_centred(const u64* src, u64 qs, u64* o, const DevPrime* P
     ldv<V>(sr + j, x);
 #pragma unroll
     for (int v = 0; v < V; ++v) x[v] = centred_to(x[v], qs, t);
+    stv<V>(o + off + j, x);
+}
+template <int V>
+__global__ void k_sub_mul2_scalar(const u64* a, const u64* b, ScalarVec s1, const u64* s2, const u64* s2p, u64* o,
+                                  const DevPrime* P, const int* ids, int lpp, size_t a_pstride, int logn) {
+    griddep_entry();
+    const int limb = blockIdx.y;
+    const int r = limb % lpp;
+    const u64 q = P[ids[r]].m.q;
+    const u64 w1 = s1.v[r], w1p = s1.vp[r], w2 = s2[r], w2p = s2p[r];
+    const size_t off = (size_t)limb << logn;
+    const size_t offa = a_pstride ? (size_t)(limb / lpp) * a_pstride + ((size_t)r << logn) : off;
+    EWV_BEGIN(1 << logn)
+    u64 x[V], y[V];
+    ldv<V>(a + offa + j, x);
+    ldv<V>(b + off + j, y);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = sub_mod(mul_shoup(x[v], w1, w1p, q), mul_shoup(y[v], w2, w2p, q), q);
     stv<V>(o + off + j, x);
 }
 template <int V>
@@ -1420,11 +1439,23 @@ void mul_scalar(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u6
     }
     LAUNCH_CHECK();
 }
-void mul_scalar_v(const ckks_ctx* c, const u64* a, const ScalarVec& sv, u64* o, int nl, const int* ids, int lpp) {
+void mul_scalar_v(const ckks_ctx* c, const u64* a, const ScalarVec& sv, u64* o, int nl, const int* ids, int lpp,
+                  size_t a_pstride) {
     if (nl <= 0) return;
     CK_CHECK(lpp <= ScalarVec::MAX, CKKS_EINVAL, "too many limbs for a by-value scalar vector");
     { KTimer kt_(c, "mul_scalar", 2.0 * (double)nl * c->n * 8.0);
-    EWV_LAUNCH(k_mul_scalar_v, al16(a) && al16(o), nl, a, sv, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_mul_scalar_v, al16(a) && al16(o) && a_pstride % 2 == 0, nl, a, sv, o, c->d_primes, ids, lpp,
+               a_pstride, c->logn);
+    }
+    LAUNCH_CHECK();
+}
+void sub_mul2_scalar(const ckks_ctx* c, const u64* a, const u64* b, const ScalarVec& s1, const u64* s2,
+                     const u64* s2p, u64* o, int nl, const int* ids, int lpp, size_t a_pstride) {
+    if (nl <= 0) return;
+    CK_CHECK(lpp <= ScalarVec::MAX, CKKS_EINVAL, "too many limbs for a by-value scalar vector");
+    { KTimer kt_(c, "sub_mul_scalar", 3.0 * (double)nl * c->n * 8.0);
+    EWV_LAUNCH(k_sub_mul2_scalar, al16(a) && al16(b) && al16(o) && a_pstride % 2 == 0, nl, a, b, s1, s2, s2p, o,
+               c->d_primes, ids, lpp, a_pstride, c->logn);
     }
     LAUNCH_CHECK();
 }

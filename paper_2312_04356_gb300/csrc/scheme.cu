@@ -295,6 +295,7 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
         }
     c->d_pinv = dev_upload_persistent(pinv);
     c->d_qlinv = dev_upload_persistent(qlinv);
+    c->h_qlinv.assign(qlinv.begin(), qlinv.begin() + (size_t)c->nq * c->nq);
     c->d_pqlinv = dev_upload_persistent(pqlinv);
     c->d_pmod = dev_upload_persistent(pmod);
     // every base-conversion table up front (no allocation later, e.g. inside stream capture)
@@ -423,25 +424,39 @@ ckks_ct imult(const ckks_ct& a) {
     return o;
 }
 
-ckks_ct rescale(const ckks_ct& a) {
+// rescale(mul_int(a, k)) without materialising a k: the dropped limbs are scaled by k while
+// they are copied out, and the tail computes a_i (k q_l^{-1}) - lift_i q_l^{-1} (the same
+// residues as (k a_i - lift_i) q_l^{-1}); like rescale(mul_int(a, k)) the scale becomes
+// a.scale / q_l (callers track the integer factor themselves).
+ckks_ct rescale_mul(const ckks_ct& a, long long k) {
     ckks_ctx* c = a.ctx;
     const int l = a.level;
     CK_CHECK(l >= 1, CKKS_ELEVEL, "cannot rescale a level-0 ciphertext");
+    CK_CHECK(l <= ScalarVec::MAX, CKKS_EINVAL, "too many limbs for a by-value scalar vector");
     c->ops["rescale"]++;
     const size_t n = c->n;
+    ScalarVec top;
+    top.v[0] = from_signed(k, c->q[l]);
+    top.vp[0] = shoup(top.v[0], c->q[l]);
     DevBuf last(2 * n, c->stream);
-    CUDA_CHECK(cudaMemcpyAsync(last.ptr, a.c0() + (size_t)l * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_CHECK(cudaMemcpyAsync(last.ptr + n, a.c1() + (size_t)l * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    kern::mul_scalar_v(c, a.c0() + (size_t)l * n, top, last.ptr, 2, c->d_iota + l, 1, (size_t)(l + 1) * n);
     kern::ntt_inverse(c, last.ptr, 2, c->d_iota + l, 1);
     DevBuf lift(2 * (size_t)l * n, c->stream);
     kern::lift_centred(c, last.ptr, l, lift.ptr, 2 * l, c->d_iota, l, n);     // both polynomials
     kern::ntt_forward(c, lift.ptr, 2 * l, c->d_iota, l);
     ckks_ct o = new_ct(c, l - 1, a.scale / (double)c->q[l]);
-    const u64* s = c->d_qlinv + (size_t)l * c->nq;
-    const u64* sp = c->d_qlinv + (size_t)c->nq * c->nq + (size_t)l * c->nq;
-    kern::sub_mul_scalar(c, a.c0(), lift.ptr, s, sp, o.c0(), 2 * l, c->d_iota, l, (size_t)(l + 1) * n);
+    ScalarVec s1;
+    for (int i = 0; i < l; ++i) {
+        s1.v[i] = mulmod(from_signed(k, c->q[i]), c->h_qlinv[(size_t)l * c->nq + i], c->q[i]);
+        s1.vp[i] = shoup(s1.v[i], c->q[i]);
+    }
+    const u64* s2 = c->d_qlinv + (size_t)l * c->nq;
+    const u64* s2p = c->d_qlinv + (size_t)c->nq * c->nq + (size_t)l * c->nq;
+    kern::sub_mul2_scalar(c, a.c0(), lift.ptr, s1, s2, s2p, o.c0(), 2 * l, c->d_iota, l, (size_t)(l + 1) * n);
     return o;
 }
+
+ckks_ct rescale(const ckks_ct& a) { return rescale_mul(a, 1); }
 
 ckks_ct mod_drop(const ckks_ct& a, int level) {
     CK_CHECK(level >= 0 && level <= a.level, CKKS_EINVAL, "mod_drop to a higher level");
@@ -462,7 +477,7 @@ ckks_ct level_down(const ckks_ct& a, int level) {
     while (cur->level > level) {
         const int l = cur->level;
         long long k = llround_away((c->delta[l - 1] * (double)c->q[l]) / cur->scale);
-        ckks_ct t = rescale(mul_int(*cur, k));
+        ckks_ct t = rescale_mul(*cur, k);
         t.scale = c->delta[l - 1];
         x = std::move(t);
         cur = &x;
@@ -977,7 +992,7 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
             if (Q.cst != 0.0) {
                 const int lk = Tn.level;
                 const double s_c = (ctx->delta[lk - 1] * (double)ctx->q[lk]) / Tn.scale;
-                prod = rescale(mul_int(Tn, llround_away(Q.cst * s_c)));
+                prod = rescale_mul(Tn, llround_away(Q.cst * s_c));
                 prod.scale = (Tn.scale * s_c) / (double)ctx->q[lk];
                 hp = true;
             }
@@ -1032,8 +1047,8 @@ void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, c
     ckks_ct cj = conjugate(keys, x);
     ckks_ct re = add(x, cj);
     ckks_ct im = imult(sub(cj, x));
-    re = rescale(mul_int(re, bt.c_drop));
-    im = rescale(mul_int(im, bt.c_drop));
+    re = rescale_mul(re, bt.c_drop);
+    im = rescale_mul(im, bt.c_drop);
     re.scale = c->delta[re.level];
     im.scale = c->delta[im.level];
     re_out = eval_mod(keys, re, bt.coeffs, bt.bp.r);
@@ -1089,7 +1104,7 @@ static ckks_ct boot_tail(const ckks_keys& keys, const ckks_boot& bt, const ckks_
     x.scale = bt.s_raise;
     for (const auto& ps : bt.ctos) x = bsgs(keys, x, *ps, true);
     ckks_ct re = add(x, conjugate(keys, x));
-    re = rescale(mul_int(re, bt.c_drop));
+    re = rescale_mul(re, bt.c_drop);
     re.scale = c->delta[re.level];
     re = eval_mod(keys, re, bt.coeffs, bt.bp.r);
     return tail(keys, bt, rescale(mul_plain(re, *bt.mask_re)));

@@ -15,6 +15,8 @@ ckks_ct mul_int(const ckks_ct& a, long long v);
 ckks_ct add_const(const ckks_ct& a, double cst);
 ckks_ct imult(const ckks_ct& a);
 ckks_ct rescale(const ckks_ct& a);
+// rescale(mul_int(a, k)) in one pass over the limbs (identical residues)
+ckks_ct rescale_mul(const ckks_ct& a, long long k);
 ckks_ct mod_drop(const ckks_ct& a, int level);
 ckks_ct level_down(const ckks_ct& a, int level);
 ckks_ct mod_raise(const ckks_ct& a);
