@@ -29,11 +29,12 @@ import numpy as np  # noqa: E402
 import workloads as WL  # noqa: E402
 
 METRIC = "ms per conv2d+bootstrap block at N=2^16"
-# DRAM bytes (read + write) per algorithmic byte of a forward NTT (two k_ntt16 passes), from the
-# ncu capture of the current kernel on 256 limbs (profiles/ntt16_256limbs_full.md): traffic of a
+# DRAM bytes (read + write) per algorithmic byte of a forward NTT done as two k_ntt16 passes
+# (one read and one write of the limbs per transform are the algorithmic bytes, 268.4 MB for 256
+# limbs), from the ncu capture on 256 limbs (profiles/ntt16_256limbs_full.md): traffic of a
 # launch scales with its limbs, so the in-block traffic per launch is this ratio times the
 # launch's algorithmic bytes.
-NTT_FWD_DRAM_PER_ALGO_BYTE = (134.4 + 81.0 + 186.5 + 89.4) / (2 * 268.4)
+NTT_FWD_DRAM_PER_ALGO_BYTE = (134.4 + 81.0 + 186.5 + 89.4) / 268.4
 # The same ratio for the key-switch inner product, from the ncu capture of `--kernel ks`
 # (profiles/keyswitch_kernels_full.md): one launch at the top level, 3 digits x 31 extended
 # limbs with the automorphed c0 term on 24 rows = (3*3 + 2) * 31 + 24 = 365 limbs of
@@ -151,9 +152,9 @@ def peaks():
 # product (four 32x32 -> 64 partial products) and two 64x64 low products (one 32x32 -> 64 and
 # two 32x32 -> 32 each): 6 wide + 4 narrow 32-bit multiplies, 16 lane-cycles of the integer
 # multiply (fmaheavy) pipe counting a wide product as two.  That pipe retires 16 lanes per
-# SM sub-partition per clock, 64 per SM: peak butterflies/s = 64 * SMs * clock / 16.  Each
-# k_ntt16 pass of one limb does 8 stages of N/2 butterflies and moves 2 N 8 algorithmic bytes,
-# so a pass's butterflies are its algorithmic bytes / 4.
+# SM sub-partition per clock, 64 per SM: peak butterflies/s = 64 * SMs * clock / 16.  A
+# transform of one limb does 16 stages of N/2 butterflies and has 2 N 8 algorithmic bytes (one
+# read, one write), so the butterflies are the algorithmic bytes / 2 (per pass or per launch).
 NTT_MUL_LANE_CYCLES_PER_BUTTERFLY = 16
 GB300_SMS = 152
 
@@ -167,7 +168,7 @@ def ntt_alu_roofline(kst, pk):
     for k in ("ntt_fwd", "ntt_inv"):
         v = kst.get(k)
         if v:
-            ach = v["bytes"] / 4.0 / (v["ms"] * 1e-3) / 1e9
+            ach = v["bytes"] / 2.0 / (v["ms"] * 1e-3) / 1e9
             out[k] = {"achieved": round(ach, 1), "frac": round(ach / peak, 4)}
     return out
 
@@ -787,7 +788,7 @@ def run_kernel_ntt(args):
     dev = torch.from_numpy(x.view(np.int64)).cuda()
     res = {}
     ok = True
-    for variant in ((0, 1, 2, 3, 4) if args.variant < 0 else (args.variant,)):
+    for variant in ((0, 1, 2, 3, 4, 5) if args.variant < 0 else (args.variant,)):
         K.ckks_ctx_set_ntt_variant(ctx, variant)
         for _ in range(args.warmup):
             K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)

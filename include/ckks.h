@@ -110,15 +110,17 @@ int ckks_ctx_reset_counters(ckks_ctx* ctx);
  * to cap bytes); *len receives the full length.  Synchronises the stream. */
 int ckks_ctx_kernel_stats(ckks_ctx* ctx, char* buf, int cap, int* len);
 
-/* Autotuner: times each NTT launch variant (16 values per thread with 16 or 4 sub-problems
- * per CTA and 3 or 4 resident CTAs per SM, or 4 values per thread) for limb counts 1, 2, 7,
- * 14, 24, 48, 96, 192 (forward + inverse, `reps` repetitions, 0 = 3) and keeps the fastest
- * per size class for this context.  All variants compute the same residues.  choice8 (may
- * be NULL) receives the chosen variant per class (0: 16 sub-problems / 80 registers,
- * 1: 16 / 64, 2: 4 / 80, 3: 4 / 64, 4: 4 values per thread; -1: default).  Only N = 2^16
- * has variants.  Synchronises the stream. */
+/* Autotuner: times each NTT launch variant (two passes of 8 stages with 16 values per thread,
+ * 16 or 4 sub-problems per CTA and 3 or 4 resident CTAs per SM, or 4 values per thread; or
+ * the whole transform in one launch by a cluster of 8 CTAs that exchange the half-transformed
+ * data through distributed shared memory) for limb counts 1, 2, 7, 14, 24, 48, 96, 192
+ * (forward + inverse, `reps` repetitions, 0 = 3) and keeps the fastest per size class for
+ * this context.  All variants compute the same residues.  choice8 (may be NULL) receives the
+ * chosen variant per class (0: 16 sub-problems / 80 registers, 1: 16 / 64, 2: 4 / 80,
+ * 3: 4 / 64, 4: 4 values per thread, 5: one-launch cluster; -1: default).  Only N = 2^16 has
+ * variants.  Synchronises the stream. */
 int ckks_autotune(ckks_ctx* ctx, int reps, int32_t* choice8);
-/* Use one NTT variant (0..4 as above) for every size, or -1 for the default rule. */
+/* Use one NTT variant (0..5 as above) for every size, or -1 for the default rule. */
 int ckks_ctx_set_ntt_variant(ckks_ctx* ctx, int variant);
 /* Launch mode of the context's kernels.  on != 0 (the default): kernels launched outside a
  * CUDA graph capture use programmatic stream serialization, so the next kernel is set up

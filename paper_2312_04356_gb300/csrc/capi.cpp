@@ -280,7 +280,7 @@ int ckks_autotune(ckks_ctx* ctx, int reps, int32_t* choice8) {
 int ckks_ctx_set_ntt_variant(ckks_ctx* ctx, int variant) {
     return guard(ctx, [&] {
         REQ(ctx);
-        CK_CHECK(variant >= -1 && variant <= 4, CKKS_EINVAL, "variant must be -1..4");
+        CK_CHECK(variant >= -1 && variant <= 5, CKKS_EINVAL, "variant must be -1..5");
         for (int i = 0; i < 8; ++i) ctx->ntt_choice[i] = variant;
     });
 }

@@ -5,6 +5,9 @@
 // grid (blockIdx.y) is one limb, so the modulus is uniform inside a CTA.
 #include "internal.h"
 
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
 // ------------------------------------------------- dependent launches ----
 // Every kernel of this file begins with griddep_entry(): it waits until the grids it depends
 // on have completed and their writes are visible (griddepcontrol.wait; a no-op for a plain
@@ -494,11 +497,121 @@ __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const De
     }
 }
 
+// ---- the whole N = 2^16 transform in one launch: a cluster of 8 CTAs per limb (512 threads
+// each, 16 values per thread).  Forward: CTA r runs stages 0-7 on columns 32r .. 32r+31 (the
+// COL pass of k_ntt16 with 32 sub-problems), writes them to its shared memory as [row][32],
+// and after a cluster barrier reads rows 32r .. 32r+31 from all eight CTAs through
+// distributed shared memory for stages 8-15 (the ROW pass).  Inverse: the same in reverse
+// order.  Butterflies, twiddles and lazy bounds are those of k_ntt16, so the residues are
+// identical; the data makes one trip through HBM instead of two.  Every thread of every CTA
+// reaches both cluster barriers (no early exit), and the second barrier keeps each CTA's
+// shared memory alive until the other CTAs have read it.
+constexpr int CL_SUBS = 32, CL_THREADS = 512, CL_SMEM_WORDS = CL_SUBS * F_STRIDE;
+
+template <bool INV>
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(CL_THREADS, 2)
+    k_ntt_cl(u64* __restrict__ data, const DevPrime* __restrict__ primes, const int* __restrict__ ids, int lpp,
+             size_t pstride, const int* __restrict__ loff) {
+    griddep_entry();
+    extern __shared__ u64 sm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int limb = blockIdx.y;
+    const int r = loff ? limb : limb % lpp;
+    const DevPrime* P = primes + ids[r];
+    const u64 q = P->m.q, q2 = 2 * q;
+    u64* a = loff ? data + ((size_t)loff[limb] << 16) : data + (size_t)(limb / lpp) * pstride + ((size_t)r << 16);
+    const int tid = threadIdx.x;
+    // COL mapping: column 32 rank + spc, elements (rows) t + 16 i / 16 t + i
+    const int spc = tid % CL_SUBS, tc = tid / CL_SUBS, col = CL_SUBS * rank + spc;
+    // ROW mapping: row 32 rank + spr, elements (columns) t + 16 i / 16 t + i
+    const int spr = tid >> 4, tr = tid & 15, row = CL_SUBS * rank + spr;
+    u64 x[16];
+    if (!INV) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = a[((size_t)(tc + 16 * i) << 8) + col];
+        fwd_round<false>(x, tc, 0, 0, P, q, q2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[f_slot(spc, tc + 16 * i)] = x[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(spc, 16 * tc + i)];
+        fwd_round<true>(x, tc, 0, 0, P, q, q2);                      // column col, rows 16 tc + i
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[(16 * tc + i) * CL_SUBS + spc] = x[i];
+        cl.sync();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {                               // column tr + 16 i of row `row`
+            const u64* src = cl.map_shared_rank(sm, i >> 1);
+            x[i] = src[row * CL_SUBS + tr + 16 * (i & 1)];
+        }
+        cl.sync();
+        fwd_round<false>(x, tr, row, 8, P, q, q2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[f_slot(spr, tr + 16 * i)] = x[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(spr, 16 * tr + i)];
+        fwd_round<true>(x, tr, row, 8, P, q, q2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            u64 v = x[i];
+            if (v >= 2 * q2) v -= 2 * q2;
+            if (v >= q2) v -= q2;
+            if (v >= q) v -= q;
+            x[i] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[f_slot(spr, 16 * tr + i)] = x[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) a[((size_t)row << 8) + tr + 16 * i] = sm[f_slot(spr, tr + 16 * i)];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[f_slot(spr, tr + 16 * i)] = a[((size_t)row << 8) + tr + 16 * i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(spr, 16 * tr + i)];
+        __syncthreads();
+        inv_round<true>(x, tr, row, 8, P, q, q2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[f_slot(spr, 16 * tr + i)] = x[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(spr, tr + 16 * i)];
+        inv_round<false>(x, tr, row, 8, P, q, q2);                   // row `row`, columns tr + 16 i
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[spr * 256 + tr + 16 * i] = x[i];
+        cl.sync();
+        {
+            const u64* src = cl.map_shared_rank(sm, tc >> 1);          // rows 16 tc + i live there
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = src[(16 * (tc & 1) + i) * 256 + col];
+        }
+        cl.sync();
+        inv_round<true>(x, tc, 0, 0, P, q, q2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[f_slot(spc, 16 * tc + i)] = x[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(spc, tc + 16 * i)];
+        inv_round<false>(x, tc, 0, 0, P, q, q2);
+        const u64 ni = P->n_inv, nip = P->n_inv_p;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) a[((size_t)(tc + 16 * i) << 8) + col] = mul_shoup(x[i], ni, nip, q);
+    }
+}
+
 // few limbs: 64-thread CTAs (4 sub-problems) so that the grid still covers the SMs
 // Variants (identical results): CTA of 16 or 4 sub-problems, register budget for 3 or 4
 // resident 256-thread CTAs per SM.  ckks_autotune times them per limb-count class; the
 // default (no tuning) is 16 sub-problems at >= 16 limbs, else 4, 80 registers.
-enum NttVariant { NTT_V16_R80 = 0, NTT_V16_R64 = 1, NTT_V4_R80 = 2, NTT_V4_R64 = 3, NTT_X4 = 4, NTT_NVARIANTS = 5 };
+enum NttVariant {
+    NTT_V16_R80 = 0, NTT_V16_R64 = 1, NTT_V4_R80 = 2, NTT_V4_R64 = 3, NTT_X4 = 4, NTT_CL = 5, NTT_NVARIANTS = 6
+};
 
 template <bool COL, bool INV>
 void launch_ntt16_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp,
@@ -533,13 +646,48 @@ inline int ntt_class(int nlimbs) {
     return c;
 }
 
-template <bool COL, bool INV>
-void launch_ntt16(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
-                  const int* loff = nullptr) {
-    KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0);
+template <bool INV>
+void launch_ntt_cl(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
+                   const int* loff) {
+    static bool smem_set = false;     // one opt-in per instantiation (the same on every device)
+    if (!smem_set) {
+        CUDA_CHECK(cudaFuncSetAttribute(k_ntt_cl<INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        CL_SMEM_WORDS * (int)sizeof(u64)));
+        smem_set = true;
+    }
+    klaunch(cx, k_ntt_cl<INV>, dim3(8, nlimbs), CL_THREADS, CL_SMEM_WORDS * sizeof(u64),
+            data, cx->d_primes, ids, lpp, pstride, loff);
+}
+
+// One whole N = 2^16 transform with variant v: the cluster kernel, or the two passes (forward:
+// COL then ROW; inverse: ROW then COL).  Algorithmic bytes: one read and one write of the
+// limbs per transform, split evenly over the two passes.
+template <bool INV>
+void launch_ntt_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
+                        const int* loff) {
+    const char* nm = INV ? "ntt_inv" : "ntt_fwd";
+    const double bytes = 2.0 * nlimbs * cx->n * 8.0;
+    if (v == NTT_CL) {
+        KTimer kt_(cx, nm, bytes);
+        launch_ntt_cl<INV>(cx, data, nlimbs, ids, lpp, pstride, loff);
+        return;
+    }
+    {
+        KTimer kt_(cx, nm, bytes / 2);
+        launch_ntt16_variant<!INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff);
+    }
+    {
+        KTimer kt_(cx, nm, bytes / 2);
+        launch_ntt16_variant<INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff);
+    }
+}
+
+template <bool INV>
+void launch_ntt_transform(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
+                          const int* loff = nullptr) {
     int v = cx->ntt_choice[ntt_class(nlimbs)];
     if (v < 0) v = nlimbs >= 16 ? NTT_V16_R80 : NTT_V4_R80;
-    launch_ntt16_variant<COL, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff);
+    launch_ntt_variant<INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff);
 }
 
 struct PassPlan {
@@ -562,7 +710,7 @@ void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int 
     const int stride = SUB > 1 ? SUB + 1 : 1;
     const size_t smem = (size_t)stride * (1 << p.c) * sizeof(u64);
     dim3 grid(tiles, nlimbs);
-    { KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0);
+    { KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0 * p.c / logn);
     klaunch(cx, k_ntt_pass<INV>, grid, NTT_THREADS, smem, data, cx->d_primes, ids, lpp, logn, p.s0, p.c, logsub,
             scale_out);
     }
@@ -1267,8 +1415,7 @@ void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
     if (nlimbs <= 0) return;
     if (pstride == 0) pstride = (size_t)lpp * c->n;
     if (c->logn == 16) {
-        launch_ntt16<true, false>(c, data, nlimbs, ids, lpp, pstride);
-        launch_ntt16<false, false>(c, data, nlimbs, ids, lpp, pstride);
+        launch_ntt_transform<false>(c, data, nlimbs, ids, lpp, pstride);
         LAUNCH_CHECK();
         return;
     }
@@ -1300,10 +1447,8 @@ void autotune_ntt(ckks_ctx* c, int reps) {
                 cudaEventRecord(e0, c->stream);
                 for (int r = 0; r < reps; ++r) {
                     const int* d = (const int*)dids.ptr;
-                    launch_ntt16_variant<true, false>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
-                    launch_ntt16_variant<false, false>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
-                    launch_ntt16_variant<false, true>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
-                    launch_ntt16_variant<true, true>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
+                    launch_ntt_variant<false>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
+                    launch_ntt_variant<true>(c, v, buf.ptr, nl, d, nl, (size_t)nl << 16, nullptr);
                 }
                 cudaEventRecord(e1, c->stream);
                 CUDA_CHECK(cudaEventSynchronize(e1));
@@ -1325,8 +1470,7 @@ void autotune_ntt(ckks_ctx* c, int reps) {
 void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, const int* ids) {
     if (nlimbs <= 0) return;
     CK_CHECK(c->logn == 16, CKKS_EINVAL, "limb-list NTT needs N = 2^16");
-    launch_ntt16<true, false>(c, data, nlimbs, ids, nlimbs, 0, off);
-    launch_ntt16<false, false>(c, data, nlimbs, ids, nlimbs, 0, off);
+    launch_ntt_transform<false>(c, data, nlimbs, ids, nlimbs, 0, off);
     LAUNCH_CHECK();
 }
 
@@ -1377,8 +1521,7 @@ void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
     if (nlimbs <= 0) return;
     if (pstride == 0) pstride = (size_t)lpp * c->n;
     if (c->logn == 16) {
-        launch_ntt16<false, true>(c, data, nlimbs, ids, lpp, pstride);
-        launch_ntt16<true, true>(c, data, nlimbs, ids, lpp, pstride);
+        launch_ntt_transform<true>(c, data, nlimbs, ids, lpp, pstride);
         LAUNCH_CHECK();
         return;
     }

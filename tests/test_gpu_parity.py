@@ -51,7 +51,7 @@ def test_ntt_bitexact(name):
     psis = [(list(P.psi_q) + list(P.psi_p))[i] for i in ids]
     x = WL.residues(3, mods, P.n)
     want = C.ntt_forward(x, mods, psis, P.logn)
-    for variant in (-1, 0, 1, 2, 3, 4):       # every launch variant the autotuner may pick
+    for variant in (-1, 0, 1, 2, 3, 4, 5):    # every launch variant the autotuner may pick
         K.ckks_ctx_set_ntt_variant(ctx, variant)
         dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
         K.ckks_ntt_forward(ctx, dev.data_ptr(), len(ids), ids)
@@ -63,7 +63,7 @@ def test_ntt_bitexact(name):
         assert (dev.cpu().numpy().view(np.uint64) == x).all(), variant
     K.ckks_ctx_set_ntt_variant(ctx, -1)
     if P.logn == 16:
-        assert all(c in (0, 1, 2, 3, 4) for c in K.ckks_autotune(ctx, 1))
+        assert all(c in (0, 1, 2, 3, 4, 5) for c in K.ckks_autotune(ctx, 1))
     # edge values: all zeros, all q-1
     e = np.stack([np.full(P.n, q - 1, dtype=np.uint64) for q in mods])
     e[0] = 0
@@ -71,6 +71,32 @@ def test_ntt_bitexact(name):
     K.ckks_ntt_forward(ctx, dev.data_ptr(), len(ids), ids)
     torch.cuda.synchronize()
     assert (dev.cpu().numpy().view(np.uint64) == C.ntt_forward(e, mods, psis, P.logn)).all()
+
+
+def test_cluster_ntt_in_key_switching():
+    """the one-launch cluster NTT forced for every size (1- and 3-limb transforms round-trip;
+    the limb-list transforms of ModUp, ModDown and the key switch): hoisted rotations at
+    N = 2^16 stay bit-exact against the oracle"""
+    K, o, ctx, keys = make_pair("cfg2", 7, rotations=[1, 5], conj=False)
+    P = o.P
+    K.ckks_ctx_set_ntt_variant(ctx, 5)
+    for nl in (1, 3):
+        ids = list(range(nl))
+        mods = [int(P.q[i]) for i in ids]
+        x = WL.residues(11 + nl, mods, P.n)
+        dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
+        K.ckks_ntt_forward(ctx, dev.data_ptr(), nl, ids)
+        K.ckks_ntt_inverse(ctx, dev.data_ptr(), nl, ids)
+        torch.cuda.synchronize()
+        assert (dev.cpu().numpy().view(np.uint64) == x).all(), nl
+    lev = 20
+    z = WL.slots(12, P.n // 2, 0.3)
+    ct = o.encrypt(o.encode_pt(z, lev, P.delta[lev]), 4)
+    g = import_ct(K, ctx, ct)
+    rots = K.ckks_rotate_hoisted(ctx, keys, g, [1, 5])
+    for r, gr in zip((1, 5), rots):
+        assert_ct_equal(K, ctx, gr, o.rotate(ct, r), "rotation %d" % r)
+    K.ckks_ctx_set_ntt_variant(ctx, -1)
 
 
 def test_keys_encrypt_decrypt_bitexact():
