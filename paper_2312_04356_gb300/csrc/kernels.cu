@@ -1114,7 +1114,7 @@ constexpr int CONV_OUT = 8;
 // then reduced as in the general path.
 // MC: outputs per CTA group (4..8), chosen per launch to leave the fewest idle output slots.
 template <int MAXIN, bool SPLIT, int MC>
-__global__ void __launch_bounds__(256, 3) k_base_convert(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn) {
+__global__ void __launch_bounds__(256, (MC <= 6 ? 4 : 3)) k_base_convert(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn) {
     griddep_entry();
     __shared__ u64 s_qi[MAX_CONV_IN], s_qinv[MAX_CONV_IN], s_qinvp[MAX_CONV_IN];
     __shared__ u64 s_c[CONV_OUT][MAX_CONV_IN];
