@@ -1717,10 +1717,11 @@ static void launch_base_convert(const ckks_ctx* c, const ConvJobs& J, dim3 grid,
 }
 
 // Outputs per group MC in 4..8: the one with the fewest idle output slots over the launch's
-// jobs (sum of ceil(nout / MC) MC - nout), the larger MC on ties (fewer groups).
+// jobs (sum of ceil(nout / MC) MC - nout); on ties 6, 5, 4 (4 resident CTAs per SM) before
+// 8, 7 (3 per SM).
 void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
     int best_mc = CONV_OUT, best_slots = -1;
-    for (int mc = CONV_OUT; mc >= 4; --mc) {
+    for (int mc : {6, 5, 4, 8, 7}) {
         int slots = 0;
         for (int i = 0; i < J0.n; ++i) slots += (J0.job[i].nout + mc - 1) / mc * mc;
         if (best_slots < 0 || slots < best_slots) {
