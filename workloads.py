@@ -9,7 +9,7 @@ or Gaussian (config 2: sigma 0.1).
 """
 import numpy as np
 
-# ring / chain shapes, one dict per named configuration (see DESIGN.md)
+# ring / chain shapes, one dict per named configuration
 PARAMS = {
     # N = 2^12, 6 primes: q0 60-bit, 3 x 40-bit scaling, 2 x 60-bit special, dnum = 2, scale 2^40
     "cfg1": dict(log_n=12, n_q=4, dnum=2, n_p=0, q0_bits=60, scale_bits=40, p_bits=60, boot_bits=0, n_boot=0,
