@@ -65,6 +65,11 @@ def parse_args():
     ap.add_argument("--batch-size", type=int, default=64, help="batch: number of seeded inputs")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--variant", type=int, default=-1, help="--kernel ntt: time one launch variant only")
+    ap.add_argument("--ntt-choice", default=None,
+                    help="comma list of 8 NTT variants per size class (as 'autotune' reports them): used "
+                         "instead of timing the variants, e.g. to profile the configuration of a plain run")
+    ap.add_argument("--bsgs-splits", default=None,
+                    help="comma list of baby-step counts per bootstrapping level, used instead of tuning")
     ap.add_argument("--kernel", default=None, choices=["ntt", "ks"],
                     help="time one kernel family alone on a buffer larger than L2 (for profiling)")
     return ap.parse_args()
@@ -174,10 +179,11 @@ def ntt_alu_roofline(kst, pk):
 
 
 # ------------------------------------------------------------- workload -----
-def block_setup(K, torch, seed=1, tune=False):
+def block_setup(K, torch, seed=1, tune=False, ntt_choice=None, bsgs_splits=None):
     """context, conv plan, bootstrapping configuration, keys and one encrypted input of the
     config-2 block; with tune, the NTT launch variants and then the BSGS split of every
-    bootstrapping level are autotuned before the keys are generated"""
+    bootstrapping level are autotuned before the keys are generated (or set from ntt_choice /
+    bsgs_splits, comma lists, when given)"""
     d = WL.PARAMS[CONFIG]
     spec = WL.CONV[CONFIG]
     w = 1
@@ -188,9 +194,19 @@ def block_setup(K, torch, seed=1, tune=False):
     bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
     tuned = {}
     if tune:
-        tuned["ntt_variant_per_size_class"] = K.ckks_autotune(ctx, 3)
+        if ntt_choice:
+            K.ckks_ctx_set_ntt_choices(ctx, [int(v) for v in ntt_choice.split(",")])
+            tuned["ntt_variant_per_size_class"] = [int(v) for v in ntt_choice.split(",")]
+            tuned["ntt_source"] = "given"
+        else:
+            tuned["ntt_variant_per_size_class"] = K.ckks_autotune(ctx, 3)
         tuned["bsgs_B_default"] = K.ckks_boot_bsgs_splits(bt)
-        tuned["bsgs_B"] = K.ckks_boot_tune_bsgs(ctx, bt, 3)
+        if bsgs_splits:
+            K.ckks_boot_set_bsgs_splits(ctx, bt, [int(v) for v in bsgs_splits.split(",")])
+            tuned["bsgs_B"] = K.ckks_boot_bsgs_splits(bt)
+            tuned["bsgs_source"] = "given"
+        else:
+            tuned["bsgs_B"] = K.ckks_boot_tune_bsgs(ctx, bt, 3)
     delta0 = 2.0 ** 49
     x = WL.image(seed, spec["cin"], spec["w0"])
     W = WL.weights(seed, spec["cout"], spec["cin"], spec["f"], spec["weight"])
@@ -322,7 +338,7 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()          # graphs cannot be captured on the legacy default stream
     torch.cuda.set_stream(stream)
-    s = block_setup(K, torch, seed=1 + rank, tune=True)
+    s = block_setup(K, torch, seed=1 + rank, tune=True, ntt_choice=args.ntt_choice, bsgs_splits=args.bsgs_splits)
     ctx = s["ctx"]
     tuned = s["tuned"]
     out = K.ckks_ct_create(ctx)

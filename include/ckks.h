@@ -122,6 +122,9 @@ int ckks_ctx_kernel_stats(ckks_ctx* ctx, char* buf, int cap, int* len);
 int ckks_autotune(ckks_ctx* ctx, int reps, int32_t* choice8);
 /* Use one NTT variant (0..5 as above) for every size, or -1 for the default rule. */
 int ckks_ctx_set_ntt_variant(ckks_ctx* ctx, int variant);
+/* Set the variant of each size class (choice8 as ckks_autotune returns it, -1..5 each), e.g.
+ * to replay an earlier tuning without timing again. */
+int ckks_ctx_set_ntt_choices(ckks_ctx* ctx, const int32_t* choice8);
 /* Launch mode of the context's kernels.  on != 0 (the default): kernels launched outside a
  * CUDA graph capture use programmatic stream serialization, so the next kernel is set up
  * while the previous one drains; each kernel waits for its predecessors to complete before

@@ -66,6 +66,7 @@ _SIGS = {
     "ckks_ctx_kernel_stats": [VP, VP, I, VP],
     "ckks_autotune": [VP, I, VP],
     "ckks_ctx_set_ntt_variant": [VP, I],
+    "ckks_ctx_set_ntt_choices": [VP, VP],
     "ckks_keygen": [VP, VP, I, I, PVP],
     "ckks_keys_add_rotations": [VP, VP, VP, I],
     "ckks_keys_destroy": [VP],
@@ -307,6 +308,12 @@ def ckks_ctx_gauss_table(ctx):
 
 def ckks_ctx_set_timing(ctx, on):
     ctx.check(lib().ckks_ctx_set_timing(ctx, int(on)))
+
+
+def ckks_ctx_set_ntt_choices(ctx, choice8):
+    a = np.ascontiguousarray(choice8, dtype=np.int32)
+    assert a.size == 8
+    ctx.check(lib().ckks_ctx_set_ntt_choices(ctx, _ptr(a)))
 
 
 def ckks_ctx_set_pdl(ctx, on):

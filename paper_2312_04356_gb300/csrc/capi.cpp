@@ -285,6 +285,15 @@ int ckks_ctx_set_ntt_variant(ckks_ctx* ctx, int variant) {
     });
 }
 
+int ckks_ctx_set_ntt_choices(ckks_ctx* ctx, const int32_t* choice8) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(choice8);
+        for (int i = 0; i < 8; ++i) CK_CHECK(choice8[i] >= -1 && choice8[i] <= 5, CKKS_EINVAL, "variant must be -1..5");
+        for (int i = 0; i < 8; ++i) ctx->ntt_choice[i] = choice8[i];
+    });
+}
+
 // ---------------------------------------------------------------- keys ------
 int ckks_keygen(ckks_ctx* ctx, const int32_t* steps, int n, int want_conj, ckks_keys** out) {
     return guard(ctx, [&] {
