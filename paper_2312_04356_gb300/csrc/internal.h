@@ -231,6 +231,23 @@ struct BsgsGiants {
     unsigned acc;
 };
 void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids);
+// Baby rotations and giant-step inner sums in one pass, the babies never stored: for every
+// extended limb e and word j, baby b = (sum_d D_d(sigma_b) kb_b,d, sum_d D_d(sigma_b) ka_b,d)
+// + (P c0(sigma_b), 0) on the Q rows (b with kb null: the identity, (P c0, P c1) on the Q rows,
+// 0 on the P rows), then o[g] (+)= sum_b baby_b p[g][b] as in bsgs_inner_giants.
+struct BsgsFused {
+    static constexpr int MAXB = 32, MAXG = 4;
+    const u64* kb[MAXB];
+    const u64* ka[MAXB];
+    u64 gal[MAXB];
+    const u64* p[MAXG][MAXB];
+    u64* o[MAXG];
+    int nb, ng, ndig;
+    unsigned acc;
+};
+// D [ndig][next][N] raised digits of c1; c0, c1 [nl][N]; s, sp: P mod q_i and Shoup
+void bsgs_fused(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1, int nl,
+                int next, const int* ext_ids, const u64* s, const u64* sp);
 // o = sum_t w_t a_t (mod q per limb) for up to MAX terms: the integer-weighted sum of a
 // Chebyshev leaf in one pass.  Arrays of nl limbs, limb k with prime ids[k % lpp]; w[t][r]
 // is the weight's residue for limb index r < lpp, wp[t][r] its Shoup companion (passed by

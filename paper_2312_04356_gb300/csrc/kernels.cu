@@ -1094,6 +1094,119 @@ __global__ void k_bsgs_inner_giants(kern::BsgsGiants T, const DevPrime* __restri
     }
 }
 
+// Baby rotations fused with the giant-step inner sums (see kern::bsgs_fused): per baby the
+// key-switch product is summed in 128 bits and reduced, the automorphed c0 term added, and the
+// reduced baby multiplied into every giant step's 128-bit sum; the babies stay in registers.
+// Same arithmetic as k_ks_inner_d followed by k_bsgs_inner_giants, so the same residues.
+template <int V, int NDIG, int NG>
+__global__ void k_bsgs_fused(const __grid_constant__ kern::BsgsFused T, const u64* __restrict__ D,
+                             const u64* __restrict__ c0, const u64* __restrict__ c1, int nl, int next,
+                             const int* __restrict__ ext_ids, const u64* __restrict__ s0,
+                             const u64* __restrict__ s0p, const DevPrime* __restrict__ P, int logn,
+                             size_t kstride) {
+    griddep_entry();
+    const int e = blockIdx.y;
+    const int id = ext_ids[e];
+    const DevPrime pr = P[id];
+    const u64 q = pr.m.q;
+    const size_t n = (size_t)1 << logn;
+    const bool qrow = e < nl;
+    const u64 w = qrow ? s0[e] : 0, wp = qrow ? s0p[e] : 0;
+    EWV_BEGIN(1 << logn)
+    u64 lob[NG][V], hib[NG][V], loa[NG][V], hia[NG][V];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int v = 0; v < V; ++v) lob[g][v] = hib[g][v] = loa[g][v] = hia[g][v] = 0;
+    for (int b = 0; b < T.nb; ++b) {
+        u64 rb[V], ra[V];
+        if (!T.kb[b]) {                                    // identity: (P c0, P c1) on the Q rows
+            u64 x0[V], x1[V];
+            if (qrow) {
+                ldv<V>(c0 + (size_t)e * n + j, x0);
+                ldv<V>(c1 + (size_t)e * n + j, x1);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                rb[v] = qrow ? mul_shoup(x0[v], w, wp, q) : 0;
+                ra[v] = qrow ? mul_shoup(x1[v], w, wp, q) : 0;
+            }
+        } else {
+            const u64 g = T.gal[b];
+            unsigned src[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) src[v] = galois_src(j + v, g, logn);
+            u64 x[NDIG][V], yb[NDIG][V], ya[NDIG][V];
+#pragma unroll
+            for (int d = 0; d < NDIG; ++d) {
+                const u64* Dd = D + ((size_t)d * next + e) * n;
+                const size_t kk = d * kstride + (size_t)id * n + j;
+                ldv_cs<V>(T.kb[b] + kk, yb[d]);
+                ldv_cs<V>(T.ka[b] + kk, ya[d]);
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[d][v] = Dd[src[v]];
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                u64 bl = 0, bh = 0, al = 0, ah = 0;
+#pragma unroll
+                for (int d = 0; d < NDIG; ++d) {
+                    const u64 pbl = x[d][v] * yb[d][v], pal = x[d][v] * ya[d][v];
+                    bh += __umul64hi(x[d][v], yb[d][v]);
+                    ah += __umul64hi(x[d][v], ya[d][v]);
+                    bl += pbl;
+                    bh += bl < pbl ? 1ull : 0ull;
+                    al += pal;
+                    ah += al < pal ? 1ull : 0ull;
+                }
+                rb[v] = reduce128_lazy(bh, bl, pr);
+                ra[v] = reduce128_lazy(ah, al, pr);
+                if (qrow) rb[v] = add_mod(rb[v], mul_shoup(c0[(size_t)e * n + src[v]], w, wp, q), q);
+            }
+        }
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg) {
+            const u64* pg = T.p[gg][b];
+            if (!pg) continue;
+            u64 y[V];
+            ldv_cs<V>(pg + (size_t)e * n + j, y);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const u64 pl = rb[v] * y[v], pa = ra[v] * y[v];
+                hib[gg][v] += __umul64hi(rb[v], y[v]);
+                hia[gg][v] += __umul64hi(ra[v], y[v]);
+                lob[gg][v] += pl;
+                hib[gg][v] += lob[gg][v] < pl ? 1ull : 0ull;
+                loa[gg][v] += pa;
+                hia[gg][v] += loa[gg][v] < pa ? 1ull : 0ull;
+            }
+        }
+    }
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg) {
+        u64 vb[V], va[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            vb[v] = reduce128_lazy(hib[gg][v], lob[gg][v], pr);
+            va[v] = reduce128_lazy(hia[gg][v], loa[gg][v], pr);
+        }
+        u64* ob = T.o[gg] + (size_t)e * n + j;
+        u64* oa = T.o[gg] + ((size_t)next + e) * n + j;
+        if ((T.acc >> gg) & 1u) {
+            u64 pb[V], pa[V];
+            ldv<V>(ob, pb);
+            ldv<V>(oa, pa);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                vb[v] = add_mod(vb[v], pb[v], q);
+                va[v] = add_mod(va[v], pa[v], q);
+            }
+        }
+        stv<V>(ob, vb);
+        stv<V>(oa, va);
+    }
+}
+
 // ------------------------------------------------------- base conversion ----
 // y_m = sum_i [x_i * qhat_i^{-1}]_{q_i} * (qhat_i mod p_m)  (no correction term), or, for an
 // exact table, minus v (Q mod p_m) with v = round(sum_i xhat_i / q_i) evaluated in FP64
@@ -1513,6 +1626,62 @@ void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int
             launch_bsgs_giants<2>(c, t, nl, ids);
         else
             launch_bsgs_giants<1>(c, t, nl, ids);
+    }
+    LAUNCH_CHECK();
+}
+
+template <int V, int NDIG>
+static void launch_bsgs_fused_g(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1,
+                                int nl, int next, const int* ext, const u64* s, const u64* sp) {
+    const dim3 grid = ewv_grid(c->n, next, V);
+    const size_t ks = (size_t)c->nall << c->logn;
+#define BF_CASE(NGV)                                                                                   \
+    case NGV:                                                                                          \
+        klaunch(c, k_bsgs_fused<V, NDIG, NGV>, grid, EW_THREADS, 0, t, D, c0, c1, nl, next, ext, s, sp, \
+                c->d_primes, c->logn, ks);                                                              \
+        break;
+    switch (t.ng) {
+        BF_CASE(1)
+        BF_CASE(2)
+        BF_CASE(3)
+        default:
+        BF_CASE(4)
+    }
+#undef BF_CASE
+}
+
+template <int V>
+static void launch_bsgs_fused(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1,
+                              int nl, int next, const int* ext, const u64* s, const u64* sp) {
+    switch (t.ndig) {
+        case 1: launch_bsgs_fused_g<V, 1>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        case 2: launch_bsgs_fused_g<V, 2>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        case 3: launch_bsgs_fused_g<V, 3>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        default: launch_bsgs_fused_g<V, 4>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+    }
+}
+
+void bsgs_fused(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1, int nl,
+                int next, const int* ext_ids, const u64* s, const u64* sp) {
+    CK_CHECK(t.nb >= 1 && t.nb <= BsgsFused::MAXB && t.ng >= 1 && t.ng <= BsgsFused::MAXG && t.ndig >= 1 &&
+                 t.ndig <= 4, CKKS_EINVAL, "fused BSGS: 1..32 babies, 1..4 giant steps, 1..4 digits");
+    int terms = 0, rots = 0;
+    for (int b = 0; b < t.nb; ++b) {
+        if (t.kb[b]) ++rots;
+        for (int g = 0; g < t.ng; ++g)
+            if (t.p[g][b]) ++terms;
+    }
+    int accs = 0;
+    for (int g = 0; g < t.ng; ++g) accs += (t.acc >> g) & 1u;
+    {
+        // algorithmic bytes: per rotation the digits, both key halves and c0 on the Q rows; the
+        // identity's c0 and c1; every diagonal once; each giant's output (read when accumulating)
+        const double limbs = (double)rots * (3.0 * t.ndig * next + nl) / next + (t.nb - rots) * 2.0 * nl / next +
+                             terms + 2.0 * t.ng + 2.0 * accs;
+        KTimer kt_(c, "bsgs_fused", limbs * next * c->n * 8.0);
+        // one word per thread: with two, the per-giant 128-bit sums of both words need ~100
+        // registers and the kernel ran slower (14.27 vs 14.00 ms per block)
+        launch_bsgs_fused<1>(c, t, D, c0, c1, nl, next, ext_ids, s, sp);
     }
     LAUNCH_CHECK();
 }

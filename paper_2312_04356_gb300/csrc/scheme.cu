@@ -780,9 +780,7 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
         std::vector<int> used_b(used.begin(), used.end());
         std::vector<long long> steps;
         for (int b : used_b) steps.push_back(((long long)ps.step * b) % m);
-        std::vector<DevBuf> baby = rotate_hoisted_ext(keys, a, steps);
-        // giant steps with at least one non-zero diagonal for this input, in chunks of up to
-        // MAXG: one pass over the baby rotations computes all their inner sums
+        // giant steps with at least one non-zero diagonal for this input
         std::vector<int> gs;
         for (int g = 0; g < ps.G(); ++g)
             for (int b = 0; b < ps.B; ++b)
@@ -790,6 +788,58 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
                     gs.push_back(g);
                     break;
                 }
+        if ((int)used_b.size() <= kern::BsgsFused::MAXB && (int)gs.size() <= kern::BsgsFused::MAXG &&
+            c->digits(l).size() <= 4) {
+            // babies and inner sums in one kernel: the baby rotations are never stored
+            DevBuf D;
+            int ndig = 1;
+            bool any_rot = false;
+            for (long long r : steps) any_rot = any_rot || r != 0;
+            if (any_rot) D = mod_up(c, a.c1(), l, &ndig);
+            kern::BsgsFused T;
+            T.nb = (int)used_b.size();
+            T.ng = (int)gs.size();
+            T.ndig = ndig;
+            T.acc = 0;
+            for (int i = 0; i < T.nb; ++i) {
+                if (steps[i] == 0) {
+                    T.kb[i] = T.ka[i] = nullptr;
+                    T.gal[i] = 1;
+                    continue;
+                }
+                const u64 gal = galois_of_step(c, steps[i]);
+                auto kt = keys.swk.find(gal);
+                CK_CHECK(kt != keys.swk.end(), CKKS_ENOKEY, "missing switching key (code " + std::to_string(gal) + ")");
+                T.kb[i] = kt->second->b.ptr;
+                T.ka[i] = kt->second->a.ptr;
+                T.gal[i] = gal;
+                c->ops["hrot"]++;
+                c->ops["keyswitch"]++;
+            }
+            for (int q = 0; q < T.ng; ++q) {
+                const int g = gs[q];
+                for (int i = 0; i < T.nb; ++i) {
+                    auto it = ps.pts.find(std::make_pair(g, used_b[i]));
+                    if (it == ps.pts.end()) {
+                        T.p[q][i] = nullptr;
+                        continue;
+                    }
+                    CK_CHECK(it->second->ext, CKKS_EINVAL, "BSGS diagonals must be over Q_l u P");
+                    T.p[q][i] = it->second->buf.ptr;
+                    scale = a.scale * it->second->scale;
+                    c->ops["pmult"]++;
+                }
+                auto it = inner.find(g);
+                if (it == inner.end()) it = inner.emplace(g, DevBuf(2 * next * n, c->stream)).first;
+                else T.acc |= 1u << q;
+                T.o[q] = it->second.ptr;
+            }
+            kern::bsgs_fused(c, T, D.ptr, a.c0(), a.c1(), nl, (int)next, ext, c->d_pmod, c->d_pmod + c->nq);
+            continue;
+        }
+        std::vector<DevBuf> baby = rotate_hoisted_ext(keys, a, steps);
+        // otherwise: the babies stored, then the inner sums in chunks of up to MAXG giant steps
+        // (one pass over the babies per chunk)
         for (size_t k0 = 0; k0 < gs.size(); k0 += kern::BsgsGiants::MAXG) {
             kern::BsgsGiants T;
             T.nb = (int)used_b.size();
