@@ -70,7 +70,7 @@ def parse_args():
                          "instead of timing the variants, e.g. to profile the configuration of a plain run")
     ap.add_argument("--bsgs-splits", default=None,
                     help="comma list of baby-step counts per bootstrapping level, used instead of tuning")
-    ap.add_argument("--kernel", default=None, choices=["ntt", "ks"],
+    ap.add_argument("--kernel", default=None, choices=["ntt", "ks", "bsgs"],
                     help="time one kernel family alone on a buffer larger than L2 (for profiling)")
     return ap.parse_args()
 
@@ -829,6 +829,40 @@ def run_kernel_ntt(args):
     print(json.dumps({"kernel": "ntt", "limbs": nl, "N": ctx.n, "roundtrip_exact": ok, "per_variant": res}))
 
 
+def run_kernel_bsgs(args):
+    """one top-level HMatmul shaped like a CtoS level of the config-2 bootstrap (63 diagonals
+    at stride 1024, B = 16, level 23, diagonals over Q_23 u P with random residues): the fused
+    baby-rotation / inner-sum kernel plus its giant steps; about 3 GB on the device"""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    d = WL.PARAMS[CONFIG]
+    ctx = K.ckks_ctx_create(d, 1, torch.cuda.current_stream().cuda_stream)
+    q, p, _, delta = K.ckks_ctx_info(ctx)
+    L = len(q) - 1
+    count, B, step = 63, 16, 1024
+    ps = K.ckks_ptset_create(ctx, -31 * step, step, count, B, L, float(q[L]))
+    mods = q + p
+    rows = [mods[i] for i in range(L + 1)] + list(p)
+    for i in range(count):
+        K.ckks_ptset_set_rns(ctx, ps, i // B, i % B, WL.residues(100 + i, rows, ctx.n))
+    keys = K.ckks_keygen(ctx, K.ckks_ptset_rotations(ps), False)
+    ct = K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, WL.slots(1, ctx.n // 2, 0.5), L, delta[L]), 1)
+    for _ in range(args.warmup):
+        K.ckks_bsgs(ctx, keys, ct, ps)
+    K.ckks_sync(ctx)
+    K.ckks_ctx_reset_counters(ctx)
+    K.ckks_ctx_set_timing(ctx, 1)
+    for _ in range(args.steps):
+        K.ckks_bsgs(ctx, keys, ct, ps)
+    K.ckks_ctx_set_timing(ctx, 0)
+    st = K.ckks_ctx_kernel_stats(ctx)
+    res = {k: {"launches": v["launches"], "us_per_launch": round(1e3 * v["ms"] / v["launches"], 2),
+               "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)} for k, v in st.items()}
+    print(json.dumps({"kernel": "bsgs", "level": L, "count": count, "B": B, "N": ctx.n, "per_kernel": res}))
+
+
 def run_kernel_ks(args):
     """hoisted rotations of one config-2 ciphertext at the top level (ModUp, key-switch inner
     product, ModDown): per-kernel times of the key switch alone, a few hundred MB on the device"""
@@ -864,6 +898,8 @@ if __name__ == "__main__":
         run_kernel_ntt(a)
     elif a.kernel == "ks":
         run_kernel_ks(a)
+    elif a.kernel == "bsgs":
+        run_kernel_bsgs(a)
     elif a.workload == "ds" and a.impl == "ours":
         run_ds(a)
     elif a.workload == "serve" and a.impl == "ours":

@@ -1098,13 +1098,28 @@ __global__ void k_bsgs_inner_giants(kern::BsgsGiants T, const DevPrime* __restri
 // key-switch product is summed in 128 bits and reduced, the automorphed c0 term added, and the
 // reduced baby multiplied into every giant step's 128-bit sum; the babies stay in registers.
 // Same arithmetic as k_ks_inner_d followed by k_bsgs_inner_giants, so the same residues.
-template <int V, int NDIG, int NG>
-__global__ void k_bsgs_fused(const __grid_constant__ kern::BsgsFused T, const u64* __restrict__ D,
-                             const u64* __restrict__ c0, const u64* __restrict__ c1, int nl, int next,
-                             const int* __restrict__ ext_ids, const u64* __restrict__ s0,
-                             const u64* __restrict__ s0p, const DevPrime* __restrict__ P, int logn,
-                             size_t kstride) {
+// The next baby's operands (key words, gathered digit words, c0, diagonal words) are copied
+// into shared memory by per-thread asynchronous copies while the current baby is computed:
+// two stages of NS words per thread, so the memory latency of a baby overlaps the arithmetic
+// of the previous one without holding the words in registers (a version loading them into
+// registers ran 1.7x slower on a top-level CtoS level, latency bound at 36% warp occupancy).
+__device__ __forceinline__ void cp_async8(u64* dst_smem, const u64* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int NDIG, int NG>
+__global__ void __launch_bounds__(256, 3)
+    k_bsgs_fused_async(const __grid_constant__ kern::BsgsFused T, const u64* __restrict__ D,
+                       const u64* __restrict__ c0, const u64* __restrict__ c1, int nl, int next,
+                       const int* __restrict__ ext_ids, const u64* __restrict__ s0, const u64* __restrict__ s0p,
+                       const DevPrime* __restrict__ P, int logn, size_t kstride) {
     griddep_entry();
+    constexpr int NS = 3 * NDIG + 2 + NG;       // kb, ka, D per digit; c0 (gathered or row); c1 row; diagonals
+    extern __shared__ u64 sbuf[];               // [2][NS][256]
     const int e = blockIdx.y;
     const int id = ext_ids[e];
     const DevPrime pr = P[id];
@@ -1112,98 +1127,88 @@ __global__ void k_bsgs_fused(const __grid_constant__ kern::BsgsFused T, const u6
     const size_t n = (size_t)1 << logn;
     const bool qrow = e < nl;
     const u64 w = qrow ? s0[e] : 0, wp = qrow ? s0p[e] : 0;
-    EWV_BEGIN(1 << logn)
-    u64 lob[NG][V], hib[NG][V], loa[NG][V], hia[NG][V];
-#pragma unroll
-    for (int g = 0; g < NG; ++g)
-#pragma unroll
-        for (int v = 0; v < V; ++v) lob[g][v] = hib[g][v] = loa[g][v] = hia[g][v] = 0;
-    for (int b = 0; b < T.nb; ++b) {
-        u64 rb[V], ra[V];
-        if (!T.kb[b]) {                                    // identity: (P c0, P c1) on the Q rows
-            u64 x0[V], x1[V];
+    const int tid = threadIdx.x;
+    const int j = blockIdx.x * 256 + tid;
+    if (j >= (int)n) return;
+    auto slot = [&](int st, int k) -> u64* { return sbuf + ((size_t)(st * NS + k) << 8) + tid; };
+    auto issue = [&](int b, int st) {
+        if (!T.kb[b]) {
             if (qrow) {
-                ldv<V>(c0 + (size_t)e * n + j, x0);
-                ldv<V>(c1 + (size_t)e * n + j, x1);
-            }
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                rb[v] = qrow ? mul_shoup(x0[v], w, wp, q) : 0;
-                ra[v] = qrow ? mul_shoup(x1[v], w, wp, q) : 0;
+                cp_async8(slot(st, 3 * NDIG), c0 + (size_t)e * n + j);
+                cp_async8(slot(st, 3 * NDIG + 1), c1 + (size_t)e * n + j);
             }
         } else {
-            const u64 g = T.gal[b];
-            unsigned src[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) src[v] = galois_src(j + v, g, logn);
-            u64 x[NDIG][V], yb[NDIG][V], ya[NDIG][V];
+            const unsigned src = galois_src(j, T.gal[b], logn);
 #pragma unroll
             for (int d = 0; d < NDIG; ++d) {
-                const u64* Dd = D + ((size_t)d * next + e) * n;
                 const size_t kk = d * kstride + (size_t)id * n + j;
-                ldv_cs<V>(T.kb[b] + kk, yb[d]);
-                ldv_cs<V>(T.ka[b] + kk, ya[d]);
-#pragma unroll
-                for (int v = 0; v < V; ++v) x[d][v] = Dd[src[v]];
+                cp_async8(slot(st, d), T.kb[b] + kk);
+                cp_async8(slot(st, NDIG + d), T.ka[b] + kk);
+                cp_async8(slot(st, 2 * NDIG + d), D + ((size_t)d * next + e) * n + src);
             }
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                u64 bl = 0, bh = 0, al = 0, ah = 0;
-#pragma unroll
-                for (int d = 0; d < NDIG; ++d) {
-                    const u64 pbl = x[d][v] * yb[d][v], pal = x[d][v] * ya[d][v];
-                    bh += __umul64hi(x[d][v], yb[d][v]);
-                    ah += __umul64hi(x[d][v], ya[d][v]);
-                    bl += pbl;
-                    bh += bl < pbl ? 1ull : 0ull;
-                    al += pal;
-                    ah += al < pal ? 1ull : 0ull;
-                }
-                rb[v] = reduce128_lazy(bh, bl, pr);
-                ra[v] = reduce128_lazy(ah, al, pr);
-                if (qrow) rb[v] = add_mod(rb[v], mul_shoup(c0[(size_t)e * n + src[v]], w, wp, q), q);
-            }
+            if (qrow) cp_async8(slot(st, 3 * NDIG), c0 + (size_t)e * n + src);
         }
 #pragma unroll
-        for (int gg = 0; gg < NG; ++gg) {
-            const u64* pg = T.p[gg][b];
-            if (!pg) continue;
-            u64 y[V];
-            ldv_cs<V>(pg + (size_t)e * n + j, y);
+        for (int g = 0; g < NG; ++g)
+            if (T.p[g][b]) cp_async8(slot(st, 3 * NDIG + 2 + g), T.p[g][b] + (size_t)e * n + j);
+        cp_async_commit();
+    };
+    u64 lob[NG], hib[NG], loa[NG], hia[NG];
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const u64 pl = rb[v] * y[v], pa = ra[v] * y[v];
-                hib[gg][v] += __umul64hi(rb[v], y[v]);
-                hia[gg][v] += __umul64hi(ra[v], y[v]);
-                lob[gg][v] += pl;
-                hib[gg][v] += lob[gg][v] < pl ? 1ull : 0ull;
-                loa[gg][v] += pa;
-                hia[gg][v] += loa[gg][v] < pa ? 1ull : 0ull;
+    for (int g = 0; g < NG; ++g) lob[g] = hib[g] = loa[g] = hia[g] = 0;
+    issue(0, 0);
+    if (T.nb > 1) issue(1, 1);
+    else cp_async_commit();
+    for (int b = 0; b < T.nb; ++b) {
+        const int st = b & 1;
+        cp_async_wait<1>();                          // the group of baby b has landed
+        u64 rb, ra;
+        if (!T.kb[b]) {
+            rb = qrow ? mul_shoup(*slot(st, 3 * NDIG), w, wp, q) : 0;
+            ra = qrow ? mul_shoup(*slot(st, 3 * NDIG + 1), w, wp, q) : 0;
+        } else {
+            u64 bl = 0, bh = 0, al = 0, ah = 0;
+#pragma unroll
+            for (int d = 0; d < NDIG; ++d) {
+                const u64 x = *slot(st, 2 * NDIG + d), yb = *slot(st, d), ya = *slot(st, NDIG + d);
+                const u64 pbl = x * yb, pal = x * ya;
+                bh += __umul64hi(x, yb);
+                ah += __umul64hi(x, ya);
+                bl += pbl;
+                bh += bl < pbl ? 1ull : 0ull;
+                al += pal;
+                ah += al < pal ? 1ull : 0ull;
             }
+            rb = reduce128_lazy(bh, bl, pr);
+            ra = reduce128_lazy(ah, al, pr);
+            if (qrow) rb = add_mod(rb, mul_shoup(*slot(st, 3 * NDIG), w, wp, q), q);
         }
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            if (!T.p[g][b]) continue;
+            const u64 y = *slot(st, 3 * NDIG + 2 + g);
+            const u64 pl = rb * y, pa = ra * y;
+            hib[g] += __umul64hi(rb, y);
+            hia[g] += __umul64hi(ra, y);
+            lob[g] += pl;
+            hib[g] += lob[g] < pl ? 1ull : 0ull;
+            loa[g] += pa;
+            hia[g] += loa[g] < pa ? 1ull : 0ull;
+        }
+        if (b + 2 < T.nb) issue(b + 2, st);          // this stage has been read
+        else cp_async_commit();                      // keep one group per iteration
     }
 #pragma unroll
-    for (int gg = 0; gg < NG; ++gg) {
-        u64 vb[V], va[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            vb[v] = reduce128_lazy(hib[gg][v], lob[gg][v], pr);
-            va[v] = reduce128_lazy(hia[gg][v], loa[gg][v], pr);
+    for (int g = 0; g < NG; ++g) {
+        u64 vb = reduce128_lazy(hib[g], lob[g], pr), va = reduce128_lazy(hia[g], loa[g], pr);
+        u64* ob = T.o[g] + (size_t)e * n + j;
+        u64* oa = T.o[g] + ((size_t)next + e) * n + j;
+        if ((T.acc >> g) & 1u) {
+            vb = add_mod(vb, *ob, q);
+            va = add_mod(va, *oa, q);
         }
-        u64* ob = T.o[gg] + (size_t)e * n + j;
-        u64* oa = T.o[gg] + ((size_t)next + e) * n + j;
-        if ((T.acc >> gg) & 1u) {
-            u64 pb[V], pa[V];
-            ldv<V>(ob, pb);
-            ldv<V>(oa, pa);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                vb[v] = add_mod(vb[v], pb[v], q);
-                va[v] = add_mod(va[v], pa[v], q);
-            }
-        }
-        stv<V>(ob, vb);
-        stv<V>(oa, va);
+        *ob = vb;
+        *oa = va;
     }
 }
 
@@ -1630,34 +1635,40 @@ void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int
     LAUNCH_CHECK();
 }
 
-template <int V, int NDIG>
-static void launch_bsgs_fused_g(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1,
-                                int nl, int next, const int* ext, const u64* s, const u64* sp) {
-    const dim3 grid = ewv_grid(c->n, next, V);
-    const size_t ks = (size_t)c->nall << c->logn;
-#define BF_CASE(NGV)                                                                                   \
-    case NGV:                                                                                          \
-        klaunch(c, k_bsgs_fused<V, NDIG, NGV>, grid, EW_THREADS, 0, t, D, c0, c1, nl, next, ext, s, sp, \
-                c->d_primes, c->logn, ks);                                                              \
-        break;
-    switch (t.ng) {
-        BF_CASE(1)
-        BF_CASE(2)
-        BF_CASE(3)
-        default:
-        BF_CASE(4)
+template <int NDIG, int NG>
+static void launch_bsgs_async_one(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0,
+                                  const u64* c1, int nl, int next, const int* ext, const u64* s, const u64* sp) {
+    constexpr int NS = 3 * NDIG + 2 + NG;
+    const size_t smem = 2 * (size_t)NS * 256 * sizeof(u64);
+    static bool attr = false;
+    if (!attr) {
+        CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_fused_async<NDIG, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+        attr = true;
     }
-#undef BF_CASE
+    const dim3 grid((c->n + 255) / 256, next);
+    klaunch(c, k_bsgs_fused_async<NDIG, NG>, grid, 256, smem, t, D, c0, c1, nl, next, ext, s, sp, c->d_primes,
+            c->logn, (size_t)c->nall << c->logn);
 }
 
-template <int V>
-static void launch_bsgs_fused(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1,
+template <int NDIG>
+static void launch_bsgs_async_g(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1,
+                                int nl, int next, const int* ext, const u64* s, const u64* sp) {
+    switch (t.ng) {
+        case 1: launch_bsgs_async_one<NDIG, 1>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        case 2: launch_bsgs_async_one<NDIG, 2>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        case 3: launch_bsgs_async_one<NDIG, 3>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        default: launch_bsgs_async_one<NDIG, 4>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+    }
+}
+
+static void launch_bsgs_async(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1,
                               int nl, int next, const int* ext, const u64* s, const u64* sp) {
     switch (t.ndig) {
-        case 1: launch_bsgs_fused_g<V, 1>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
-        case 2: launch_bsgs_fused_g<V, 2>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
-        case 3: launch_bsgs_fused_g<V, 3>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
-        default: launch_bsgs_fused_g<V, 4>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        case 1: launch_bsgs_async_g<1>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        case 2: launch_bsgs_async_g<2>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        case 3: launch_bsgs_async_g<3>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        default: launch_bsgs_async_g<4>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
     }
 }
 
@@ -1679,9 +1690,7 @@ void bsgs_fused(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* 
         const double limbs = (double)rots * (3.0 * t.ndig * next + nl) / next + (t.nb - rots) * 2.0 * nl / next +
                              terms + 2.0 * t.ng + 2.0 * accs;
         KTimer kt_(c, "bsgs_fused", limbs * next * c->n * 8.0);
-        // one word per thread: with two, the per-giant 128-bit sums of both words need ~100
-        // registers and the kernel ran slower (14.27 vs 14.00 ms per block)
-        launch_bsgs_fused<1>(c, t, D, c0, c1, nl, next, ext_ids, s, sp);
+        launch_bsgs_async(c, t, D, c0, c1, nl, next, ext_ids, s, sp);
     }
     LAUNCH_CHECK();
 }
