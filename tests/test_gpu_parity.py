@@ -61,9 +61,16 @@ def test_ntt_bitexact(name):
         K.ckks_ntt_inverse(ctx, dev.data_ptr(), len(ids), ids)
         torch.cuda.synchronize()
         assert (dev.cpu().numpy().view(np.uint64) == x).all(), variant
+    K.ckks_ctx_set_ntt_choices(ctx, [5, 4, 3, 2, 1, 0, 5, 4])   # one variant per size class
+    dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
+    K.ckks_ntt_forward(ctx, dev.data_ptr(), len(ids), ids)
+    torch.cuda.synchronize()
+    assert (dev.cpu().numpy().view(np.uint64) == want).all()
     K.ckks_ctx_set_ntt_variant(ctx, -1)
     if P.logn == 16:
-        assert all(c in (0, 1, 2, 3, 4, 5) for c in K.ckks_autotune(ctx, 1))
+        choice = K.ckks_autotune(ctx, 1)
+        assert all(c in (0, 1, 2, 3, 4, 5) for c in choice)
+        K.ckks_ctx_set_ntt_choices(ctx, choice)
     # edge values: all zeros, all q-1
     e = np.stack([np.full(P.n, q - 1, dtype=np.uint64) for q in mods])
     e[0] = 0
