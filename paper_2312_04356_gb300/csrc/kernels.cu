@@ -5,6 +5,8 @@
 // grid (blockIdx.y) is one limb, so the modulus is uniform inside a CTA.
 #include "internal.h"
 
+#include <atomic>
+
 #include <cooperative_groups.h>
 namespace cg = cooperative_groups;
 
@@ -17,6 +19,17 @@ namespace cg = cooperative_groups;
 // capture the launches stay plain: a graph already removes that latency, and programmatic
 // edges measured slightly slower there.
 __device__ __forceinline__ void griddep_entry() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Opt a kernel in to more than 48 KB of dynamic shared memory, once per device (bit d of
+// `done` records device d; concurrent first calls only repeat the same setting).
+static void allow_dynamic_smem(const void* func, int bytes, std::atomic<unsigned>& done) {
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    const unsigned bit = 1u << (dev & 31);
+    if (done.load() & bit) return;
+    CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.fetch_or(bit);
+}
 
 template <typename... P, typename... A>
 static inline void klaunch(const ckks_ctx* c, void (*k)(P...), dim3 grid, dim3 block, size_t smem, A... args) {
@@ -649,12 +662,8 @@ inline int ntt_class(int nlimbs) {
 template <bool INV>
 void launch_ntt_cl(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
                    const int* loff) {
-    static bool smem_set = false;     // one opt-in per instantiation (the same on every device)
-    if (!smem_set) {
-        CUDA_CHECK(cudaFuncSetAttribute(k_ntt_cl<INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        CL_SMEM_WORDS * (int)sizeof(u64)));
-        smem_set = true;
-    }
+    static std::atomic<unsigned> done{0};
+    allow_dynamic_smem((const void*)k_ntt_cl<INV>, CL_SMEM_WORDS * (int)sizeof(u64), done);
     klaunch(cx, k_ntt_cl<INV>, dim3(8, nlimbs), CL_THREADS, CL_SMEM_WORDS * sizeof(u64),
             data, cx->d_primes, ids, lpp, pstride, loff);
 }
@@ -1640,12 +1649,8 @@ static void launch_bsgs_async_one(const ckks_ctx* c, const BsgsFused& t, const u
                                   const u64* c1, int nl, int next, const int* ext, const u64* s, const u64* sp) {
     constexpr int NS = 3 * NDIG + 2 + NG;
     const size_t smem = 2 * (size_t)NS * 256 * sizeof(u64);
-    static bool attr = false;
-    if (!attr) {
-        CUDA_CHECK(cudaFuncSetAttribute(k_bsgs_fused_async<NDIG, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-        attr = true;
-    }
+    static std::atomic<unsigned> done{0};
+    allow_dynamic_smem((const void*)k_bsgs_fused_async<NDIG, NG>, (int)smem, done);
     const dim3 grid((c->n + 255) / 256, next);
     klaunch(c, k_bsgs_fused_async<NDIG, NG>, grid, 256, smem, t, D, c0, c1, nl, next, ext, s, sp, c->d_primes,
             c->logn, (size_t)c->nall << c->logn);
