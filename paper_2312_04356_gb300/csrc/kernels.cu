@@ -153,7 +153,6 @@ inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 // (T0 = N >> (s0+1), T1 = N >> (s0+c)), so the limb splits into independent
 // sub-problems of 2^c elements j = hi*2T0 + k*T1 + lo.  A CTA stages SUB of them
 // (4096 elements) in shared memory, runs the c stages, and writes them back.
-constexpr int NTT_TILE = 4096;
 constexpr int NTT_THREADS = 256;
 
 template <bool INV>
