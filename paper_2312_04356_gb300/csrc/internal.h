@@ -82,6 +82,11 @@ struct ckks_ctx {
     uint64_t seed = 0;
     u64 gauss[39];
     cudaStream_t stream = 0;
+    // side streams for independent giant steps of one HMatmul (created on first use)
+    static constexpr int NSIDE = 3;
+    cudaStream_t side[NSIDE] = {};
+    cudaEvent_t fork_ev = nullptr, side_ev[NSIDE] = {};
+    bool giant_streams = true;
     DevPrime* d_primes = nullptr;
     u64* d_tables = nullptr;
     u64* d_gauss = nullptr;

@@ -172,6 +172,11 @@ static void free_tab(ConvTab* t) {
 }
 
 ckks_ctx::~ckks_ctx() {
+    for (int k = 0; k < NSIDE; ++k) {
+        if (side_ev[k]) cudaEventDestroy(side_ev[k]);
+        if (side[k]) cudaStreamDestroy(side[k]);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
     cudaStreamSynchronize(stream);
     for (auto& kv : modup_tabs) free_tab(kv.second.get());
     for (auto& kv : moddown_tabs) free_tab(kv.second.get());
@@ -871,6 +876,65 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
     CK_CHECK(!inner.empty(), CKKS_EINVAL, "empty plaintext set");
     DevBuf acc;
     bool have_acc = false;
+    // giant steps with R != 0 are independent key switches: with two or more, each runs on a
+    // side stream into its own sum (its temporaries live on that stream), and the sums are
+    // added on the context's stream after it has waited for all of them
+    std::vector<std::pair<long long, u64*>> rot_giants;
+    for (auto& kv : inner) {
+        const long long R = (((long long)p0.a0 + (long long)p0.step * kv.first * p0.B) % m + m) % m;
+        if (R) rot_giants.emplace_back(R, kv.second.ptr);
+    }
+    if (c->giant_streams && rot_giants.size() >= 2) {
+        if (!c->fork_ev) {
+            CUDA_CHECK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+            for (int k = 0; k < ckks_ctx::NSIDE; ++k) {
+                CUDA_CHECK(cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking));
+                CUDA_CHECK(cudaEventCreateWithFlags(&c->side_ev[k], cudaEventDisableTiming));
+            }
+        }
+        std::vector<DevBuf> sums;
+        for (size_t k = 0; k < rot_giants.size(); ++k) sums.emplace_back(2 * next * n, c->stream);
+        const cudaStream_t main_stream = c->stream;
+        struct Restore {
+            ckks_ctx* c;
+            cudaStream_t s;
+            ~Restore() { c->stream = s; }
+        } restore{c, main_stream};
+        CUDA_CHECK(cudaEventRecord(c->fork_ev, main_stream));
+        const int nside = std::min((int)rot_giants.size(), ckks_ctx::NSIDE);
+        for (int k = 0; k < nside; ++k) CUDA_CHECK(cudaStreamWaitEvent(c->side[k], c->fork_ev, 0));
+        for (size_t k = 0; k < rot_giants.size(); ++k) {
+            c->stream = c->side[k % ckks_ctx::NSIDE];
+            const u64 gal = galois_of_step(c, rot_giants[k].first);
+            u64* x = rot_giants[k].second;
+            c->ops["hrot"]++;
+            DevBuf c1q((size_t)nl * n, c->stream);
+            mod_down_poly(c, x + next * n, l, c1q.ptr);
+            int ndig = 0;
+            DevBuf D = mod_up(c, c1q.ptr, l, &ndig);
+            key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, sums[k].ptr, false, x, (int)next);
+        }
+        for (int k = 0; k < nside; ++k) {
+            CUDA_CHECK(cudaEventRecord(c->side_ev[k], c->side[k]));
+            CUDA_CHECK(cudaStreamWaitEvent(main_stream, c->side_ev[k], 0));
+        }
+        c->stream = main_stream;
+        for (auto& kv : inner) {
+            const long long R = (((long long)p0.a0 + (long long)p0.step * kv.first * p0.B) % m + m) % m;
+            if (R) continue;
+            acc = std::move(kv.second);
+            have_acc = true;
+        }
+        for (size_t k = 0; k < sums.size(); ++k) {
+            if (!have_acc) {
+                acc = std::move(sums[k]);
+                have_acc = true;
+            } else {
+                kern::add(c, acc.ptr, sums[k].ptr, acc.ptr, 2 * (int)next, ext, (int)next);
+            }
+        }
+        inner.clear();
+    }
     for (auto& kv : inner) {
         const int g = kv.first;
         u64* x = kv.second.ptr;
