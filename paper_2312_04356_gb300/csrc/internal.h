@@ -82,7 +82,8 @@ struct ckks_ctx {
     uint64_t seed = 0;
     u64 gauss[39];
     cudaStream_t stream = 0;
-    // side streams for independent giant steps of one HMatmul (created on first use)
+    // side streams for independent work inside one operation (the giant steps of an HMatmul,
+    // the leaves of a Chebyshev evaluation); created on first use
     static constexpr int NSIDE = 3;
     cudaStream_t side[NSIDE] = {};
     cudaEvent_t fork_ev = nullptr, side_ev[NSIDE] = {};

@@ -756,6 +756,22 @@ static std::vector<DevBuf> rotate_hoisted_ext(const ckks_keys& keys, const ckks_
     return outs;
 }
 
+// side streams for independent work inside one operation (created on first use)
+static void ensure_side_streams(ckks_ctx* c) {
+    if (c->fork_ev) return;
+    CUDA_CHECK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    for (int k = 0; k < ckks_ctx::NSIDE; ++k) {
+        CUDA_CHECK(cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking));
+        CUDA_CHECK(cudaEventCreateWithFlags(&c->side_ev[k], cudaEventDisableTiming));
+    }
+}
+// puts the context's stream back when a forked section ends (also on an exception)
+struct StreamRestore {
+    ckks_ctx* c;
+    cudaStream_t s;
+    ~StreamRestore() { c->stream = s; }
+};
+
 // sum over inputs t and giant steps g of rot_{R_g}(sum_b pt_{g,b} (*) rot_{step b}(in_t)),
 // double hoisted: baby steps stay over Q_l u P (one ModUp per input, no ModDown), the
 // diagonals are over Q_l u P, and the inner sums of all inputs with the same giant step are
@@ -885,21 +901,11 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
         if (R) rot_giants.emplace_back(R, kv.second.ptr);
     }
     if (c->giant_streams && rot_giants.size() >= 2) {
-        if (!c->fork_ev) {
-            CUDA_CHECK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
-            for (int k = 0; k < ckks_ctx::NSIDE; ++k) {
-                CUDA_CHECK(cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking));
-                CUDA_CHECK(cudaEventCreateWithFlags(&c->side_ev[k], cudaEventDisableTiming));
-            }
-        }
+        ensure_side_streams(c);
         std::vector<DevBuf> sums;
         for (size_t k = 0; k < rot_giants.size(); ++k) sums.emplace_back(2 * next * n, c->stream);
         const cudaStream_t main_stream = c->stream;
-        struct Restore {
-            ckks_ctx* c;
-            cudaStream_t s;
-            ~Restore() { c->stream = s; }
-        } restore{c, main_stream};
+        StreamRestore restore{c, main_stream};
         CUDA_CHECK(cudaEventRecord(c->fork_ev, main_stream));
         const int nside = std::min((int)rot_giants.size(), ckks_ctx::NSIDE);
         for (int k = 0; k < nside; ++k) CUDA_CHECK(cudaStreamWaitEvent(c->side[k], c->fork_ev, 0));
@@ -1083,21 +1089,83 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
     pw.T[1] = copy_ct(x);
     for (int k = 1; k < std::min(b, d + 1); ++k) pw.need(k);
     for (int g : giants) pw.need(g);
-    std::function<PolyVal(std::vector<double>)> rec = [&](std::vector<double> c) -> PolyVal {
+    // The leaves (pieces of degree < b) depend only on the powers: collect them in the order
+    // the division below visits them, bring every T_k they use to its leaf level first (on
+    // the context's stream, so the cache is complete), then evaluate them, two or more on the
+    // side streams in parallel, and hand them to the division in that order.
+    auto trim = [](std::vector<double>& c) {
         int deg = (int)c.size() - 1;
         while (deg > 0 && c[deg] == 0.0) --deg;
         c.resize(deg + 1);
-        if (deg < b) return cheb_leaf(pw, c);
+    };
+    auto split = [&](const std::vector<double>& c, int* n_out, std::vector<double>* q, std::vector<double>* r) {
+        const int deg = (int)c.size() - 1;
         int n = 0;
         for (int g : giants)
             if (g <= deg) n = g;
-        std::vector<double> q(deg - n + 1), r(c.begin(), c.begin() + n);
-        q[0] = c[n];
+        q->assign(deg - n + 1, 0.0);
+        r->assign(c.begin(), c.begin() + n);
+        (*q)[0] = c[n];
         for (int j = 1; j <= deg - n; ++j) {
-            q[j] = 2.0 * c[n + j];
-            r[n - j] -= c[n + j];
+            (*q)[j] = 2.0 * c[n + j];
+            (*r)[n - j] -= c[n + j];
         }
-        PolyVal Q = rec(q), R = rec(r);
+        *n_out = n;
+    };
+    std::vector<std::vector<double>> leaves;
+    std::function<void(std::vector<double>)> collect = [&](std::vector<double> c) {
+        trim(c);
+        if ((int)c.size() - 1 < b) {
+            leaves.push_back(c);
+            return;
+        }
+        int n = 0;
+        std::vector<double> q, r;
+        split(c, &n, &q, &r);
+        collect(q);
+        collect(r);
+    };
+    collect(coeffs);
+    for (const auto& c : leaves) {
+        int lev = 1 << 30;
+        for (int k = 1; k < (int)c.size(); ++k)
+            if (c[k] != 0.0) lev = std::min(lev, pw.T.at(k).level);
+        for (int k = 1; k < (int)c.size(); ++k)
+            if (c[k] != 0.0) pw.at(k, lev);
+    }
+    ckks_ctx* cx = x.ctx;
+    std::vector<PolyVal> leaf_vals(leaves.size());
+    if (cx->giant_streams && leaves.size() >= 2) {
+        ensure_side_streams(cx);
+        const cudaStream_t main_stream = cx->stream;
+        StreamRestore restore{cx, main_stream};
+        CUDA_CHECK(cudaEventRecord(cx->fork_ev, main_stream));
+        const int nside = std::min((int)leaves.size(), ckks_ctx::NSIDE);
+        for (int k = 0; k < nside; ++k) CUDA_CHECK(cudaStreamWaitEvent(cx->side[k], cx->fork_ev, 0));
+        for (size_t i = 0; i < leaves.size(); ++i) {
+            cx->stream = cx->side[i % ckks_ctx::NSIDE];
+            leaf_vals[i] = cheb_leaf(pw, leaves[i]);
+        }
+        for (int k = 0; k < nside; ++k) {
+            CUDA_CHECK(cudaEventRecord(cx->side_ev[k], cx->side[k]));
+            CUDA_CHECK(cudaStreamWaitEvent(main_stream, cx->side_ev[k], 0));
+        }
+        cx->stream = main_stream;
+        for (auto& v : leaf_vals)       // freed later on the context's stream, after its uses there
+            if (!v.is_const) v.ct.buf.stream = main_stream;
+    } else {
+        for (size_t i = 0; i < leaves.size(); ++i) leaf_vals[i] = cheb_leaf(pw, leaves[i]);
+    }
+    size_t next_leaf = 0;
+    std::function<PolyVal(std::vector<double>)> rec = [&](std::vector<double> c) -> PolyVal {
+        trim(c);
+        const int deg = (int)c.size() - 1;
+        if (deg < b) return std::move(leaf_vals[next_leaf++]);
+        int n = 0;
+        std::vector<double> q, r;
+        split(c, &n, &q, &r);
+        PolyVal Q = rec(q);
+        PolyVal R = rec(r);
         const ckks_ct& Tn = pw.T.at(n);
         ckks_ctx* ctx = Tn.ctx;
         ckks_ct prod;
