@@ -1013,11 +1013,23 @@ struct ChebPowers {
         need(a);
         need(b);
         if (a != b) need(b - a);
+        T[k] = product(k);
+    }
+    // T_k from T_a, T_b (and T_(b-a)), which must exist
+    ckks_ct product(int k) {
+        const int a = k / 2, b = k - k / 2;
         const int m = prod_level(T.at(a).ctx, std::min(T.at(a).level, T.at(b).level));
         ckks_ct t = mul_relin_rescale(*keys, at(a, m), at(b, m));
         t = add(t, t);
-        t = (a == b) ? add_const(t, -1.0) : sub(t, at(b - a, m - 1));
-        T[k] = std::move(t);
+        return (a == b) ? add_const(t, -1.0) : sub(t, at(b - a, m - 1));
+    }
+    // the level_downs product(k) reads, made ahead (so that products can run side by side)
+    void warm(int k) {
+        const int a = k / 2, b = k - k / 2;
+        const int m = prod_level(T.at(a).ctx, std::min(T.at(a).level, T.at(b).level));
+        at(a, m);
+        at(b, m);
+        if (a != b) at(b - a, m - 1);
     }
 };
 
@@ -1087,8 +1099,54 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
     ChebPowers pw;
     pw.keys = &keys;
     pw.T[1] = copy_ct(x);
-    for (int k = 1; k < std::min(b, d + 1); ++k) pw.need(k);
-    for (int g : giants) pw.need(g);
+    // the powers by generations (a generation needs only earlier ones); within a generation the
+    // products are independent and, two or more, run on the side streams
+    {
+        std::vector<int> want;
+        for (int k = 2; k < std::min(b, d + 1); ++k) want.push_back(k);
+        for (int g : giants) want.push_back(g);
+        std::map<int, int> gen{{1, 0}};
+        std::function<int(int)> generation = [&](int k) -> int {
+            auto it = gen.find(k);
+            if (it != gen.end()) return it->second;
+            const int a = k / 2, bb = k - k / 2;
+            int g = std::max(generation(a), generation(bb));
+            if (a != bb) g = std::max(g, generation(bb - a));
+            gen[k] = g + 1;
+            return g + 1;
+        };
+        for (int k : want) generation(k);
+        int maxgen = 0;
+        for (const auto& kv : gen) maxgen = std::max(maxgen, kv.second);
+        ckks_ctx* cx = x.ctx;
+        for (int g = 1; g <= maxgen; ++g) {
+            std::vector<int> ks;
+            for (const auto& kv : gen)
+                if (kv.second == g && !pw.T.count(kv.first)) ks.push_back(kv.first);
+            if (ks.empty()) continue;
+            for (int k : ks) pw.warm(k);
+            if (!cx->giant_streams || ks.size() < 2) {
+                for (int k : ks) pw.T[k] = pw.product(k);
+                continue;
+            }
+            ensure_side_streams(cx);
+            const cudaStream_t main_stream = cx->stream;
+            StreamRestore restore{cx, main_stream};
+            CUDA_CHECK(cudaEventRecord(cx->fork_ev, main_stream));
+            const int nside = std::min((int)ks.size(), ckks_ctx::NSIDE);
+            for (int k = 0; k < nside; ++k) CUDA_CHECK(cudaStreamWaitEvent(cx->side[k], cx->fork_ev, 0));
+            for (size_t i = 0; i < ks.size(); ++i) {
+                cx->stream = cx->side[i % ckks_ctx::NSIDE];
+                pw.T[ks[i]] = pw.product(ks[i]);
+            }
+            for (int k = 0; k < nside; ++k) {
+                CUDA_CHECK(cudaEventRecord(cx->side_ev[k], cx->side[k]));
+                CUDA_CHECK(cudaStreamWaitEvent(main_stream, cx->side_ev[k], 0));
+            }
+            cx->stream = main_stream;
+            for (int k : ks) pw.T[k].buf.stream = main_stream;
+        }
+    }
     // The leaves (pieces of degree < b) depend only on the powers: collect them in the order
     // the division below visits them, bring every T_k they use to its leaf level first (on
     // the context's stream, so the cache is complete), then evaluate them, two or more on the
