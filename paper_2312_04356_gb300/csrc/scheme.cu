@@ -1214,17 +1214,45 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
     } else {
         for (size_t i = 0; i < leaves.size(); ++i) leaf_vals[i] = cheb_leaf(pw, leaves[i]);
     }
-    size_t next_leaf = 0;
-    std::function<PolyVal(std::vector<double>)> rec = [&](std::vector<double> c) -> PolyVal {
+    // The division as a tree (children visited Q before R, leaves in the same order as above);
+    // internal nodes are combined by height: nodes of one height are independent and, two or
+    // more, run on the side streams (the level_downs of T_n they read are made first).
+    struct Node {
+        int n = 0, q = -1, r = -1, leaf = -1, height = 0;
+        PolyVal val;
+    };
+    std::vector<Node> nodes;
+    int leaf_counter = 0;
+    std::function<int(std::vector<double>)> build = [&](std::vector<double> c) -> int {
         trim(c);
-        const int deg = (int)c.size() - 1;
-        if (deg < b) return std::move(leaf_vals[next_leaf++]);
+        const int id = (int)nodes.size();
+        nodes.emplace_back();
+        if ((int)c.size() - 1 < b) {
+            nodes[id].leaf = leaf_counter++;
+            return id;
+        }
         int n = 0;
         std::vector<double> q, r;
         split(c, &n, &q, &r);
-        PolyVal Q = rec(q);
-        PolyVal R = rec(r);
-        const ckks_ct& Tn = pw.T.at(n);
+        const int qi = build(q);
+        const int ri = build(r);
+        nodes[id].n = n;
+        nodes[id].q = qi;
+        nodes[id].r = ri;
+        nodes[id].height = 1 + std::max(nodes[qi].height, nodes[ri].height);
+        return id;
+    };
+    const int root = build(coeffs);
+    for (auto& nd : nodes)
+        if (nd.leaf >= 0) nd.val = std::move(leaf_vals[nd.leaf]);
+    auto prod_lev = [&](const Node& nd) {
+        const ckks_ct& Tn = pw.T.at(nd.n);
+        return prod_level(Tn.ctx, std::min(nodes[nd.q].val.ct.level, Tn.level));
+    };
+    auto combine = [&](Node& nd) -> PolyVal {
+        PolyVal& Q = nodes[nd.q].val;
+        PolyVal& R = nodes[nd.r].val;
+        const ckks_ct& Tn = pw.T.at(nd.n);
         ckks_ctx* ctx = Tn.ctx;
         ckks_ct prod;
         bool hp = false;
@@ -1237,22 +1265,54 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
                 hp = true;
             }
         } else {
-            const int lev = prod_level(ctx, std::min(Q.ct.level, Tn.level));
-            prod = mul_relin_rescale(keys, level_down(Q.ct, lev), pw.at(n, lev));
+            const int lev = prod_lev(nd);
+            prod = mul_relin_rescale(keys, level_down(Q.ct, lev), pw.at(nd.n, lev));
             hp = true;
         }
         PolyVal out;
         if (R.is_const) {
-            if (!hp) return R;
+            if (!hp) return std::move(R);
             out.ct = add_const(prod, R.cst);
             return out;
         }
-        if (!hp) return R;
+        if (!hp) return std::move(R);
         const int lev = std::min(prod.level, R.ct.level);
         out.ct = add(level_down(prod, lev), level_down(R.ct, lev));
         return out;
     };
-    PolyVal res = rec(coeffs);
+    for (int h = 1; h <= nodes[root].height; ++h) {
+        std::vector<int> ids;
+        for (int i = 0; i < (int)nodes.size(); ++i)
+            if (nodes[i].leaf < 0 && nodes[i].height == h) ids.push_back(i);
+        for (int i : ids)
+            if (!nodes[nodes[i].q].val.is_const) pw.at(nodes[i].n, prod_lev(nodes[i]));
+        if (!cx->giant_streams || ids.size() < 2) {
+            for (int i : ids) nodes[i].val = combine(nodes[i]);
+        } else {
+            ensure_side_streams(cx);
+            const cudaStream_t main_stream = cx->stream;
+            StreamRestore restore{cx, main_stream};
+            CUDA_CHECK(cudaEventRecord(cx->fork_ev, main_stream));
+            const int nside = std::min((int)ids.size(), ckks_ctx::NSIDE);
+            for (int k = 0; k < nside; ++k) CUDA_CHECK(cudaStreamWaitEvent(cx->side[k], cx->fork_ev, 0));
+            for (size_t k = 0; k < ids.size(); ++k) {
+                cx->stream = cx->side[k % ckks_ctx::NSIDE];
+                nodes[ids[k]].val = combine(nodes[ids[k]]);
+            }
+            for (int k = 0; k < nside; ++k) {
+                CUDA_CHECK(cudaEventRecord(cx->side_ev[k], cx->side[k]));
+                CUDA_CHECK(cudaStreamWaitEvent(main_stream, cx->side_ev[k], 0));
+            }
+            cx->stream = main_stream;
+            for (int i : ids)
+                if (!nodes[i].val.is_const) nodes[i].val.ct.buf.stream = main_stream;
+        }
+        for (int i : ids) {          // the children are consumed (after the join)
+            nodes[nodes[i].q].val = PolyVal();
+            nodes[nodes[i].r].val = PolyVal();
+        }
+    }
+    PolyVal res = std::move(nodes[root].val);
     CK_CHECK(!res.is_const, CKKS_EINVAL, "polynomial evaluates to a constant");
     CK_CHECK(res.ct.level >= want, CKKS_ELEVEL, "polynomial evaluation ended below its level budget");
     return level_down(res.ct, want);
