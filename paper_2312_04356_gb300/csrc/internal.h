@@ -84,7 +84,7 @@ struct ckks_ctx {
     cudaStream_t stream = 0;
     // side streams for independent work inside one operation (the giant steps of an HMatmul,
     // the leaves of a Chebyshev evaluation); created on first use
-    static constexpr int NSIDE = 3;
+    static constexpr int NSIDE = 4;
     cudaStream_t side[NSIDE] = {};
     cudaEvent_t fork_ev = nullptr, side_ev[NSIDE] = {};
     bool giant_streams = true;
