@@ -1099,58 +1099,8 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
     ChebPowers pw;
     pw.keys = &keys;
     pw.T[1] = copy_ct(x);
-    // the powers by generations (a generation needs only earlier ones); within a generation the
-    // products are independent and, two or more, run on the side streams
-    {
-        std::vector<int> want;
-        for (int k = 2; k < std::min(b, d + 1); ++k) want.push_back(k);
-        for (int g : giants) want.push_back(g);
-        std::map<int, int> gen{{1, 0}};
-        std::function<int(int)> generation = [&](int k) -> int {
-            auto it = gen.find(k);
-            if (it != gen.end()) return it->second;
-            const int a = k / 2, bb = k - k / 2;
-            int g = std::max(generation(a), generation(bb));
-            if (a != bb) g = std::max(g, generation(bb - a));
-            gen[k] = g + 1;
-            return g + 1;
-        };
-        for (int k : want) generation(k);
-        int maxgen = 0;
-        for (const auto& kv : gen) maxgen = std::max(maxgen, kv.second);
-        ckks_ctx* cx = x.ctx;
-        for (int g = 1; g <= maxgen; ++g) {
-            std::vector<int> ks;
-            for (const auto& kv : gen)
-                if (kv.second == g && !pw.T.count(kv.first)) ks.push_back(kv.first);
-            if (ks.empty()) continue;
-            for (int k : ks) pw.warm(k);
-            if (!cx->giant_streams || ks.size() < 2) {
-                for (int k : ks) pw.T[k] = pw.product(k);
-                continue;
-            }
-            ensure_side_streams(cx);
-            const cudaStream_t main_stream = cx->stream;
-            StreamRestore restore{cx, main_stream};
-            CUDA_CHECK(cudaEventRecord(cx->fork_ev, main_stream));
-            const int nside = std::min((int)ks.size(), ckks_ctx::NSIDE);
-            for (int k = 0; k < nside; ++k) CUDA_CHECK(cudaStreamWaitEvent(cx->side[k], cx->fork_ev, 0));
-            for (size_t i = 0; i < ks.size(); ++i) {
-                cx->stream = cx->side[i % ckks_ctx::NSIDE];
-                pw.T[ks[i]] = pw.product(ks[i]);
-            }
-            for (int k = 0; k < nside; ++k) {
-                CUDA_CHECK(cudaEventRecord(cx->side_ev[k], cx->side[k]));
-                CUDA_CHECK(cudaStreamWaitEvent(main_stream, cx->side_ev[k], 0));
-            }
-            cx->stream = main_stream;
-            for (int k : ks) pw.T[k].buf.stream = main_stream;
-        }
-    }
-    // The leaves (pieces of degree < b) depend only on the powers: collect them in the order
-    // the division below visits them, bring every T_k they use to its leaf level first (on
-    // the context's stream, so the cache is complete), then evaluate them, two or more on the
-    // side streams in parallel, and hand them to the division in that order.
+    // The leaves (pieces of degree < b) depend only on the baby steps T_1..T_(b-1): collect them
+    // in the order the Chebyshev division below visits them.
     auto trim = [](std::vector<double>& c) {
         int deg = (int)c.size() - 1;
         while (deg > 0 && c[deg] == 0.0) --deg;
@@ -1184,6 +1134,63 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
         collect(r);
     };
     collect(coeffs);
+    ckks_ctx* cx = x.ctx;
+    // Powers by generations (a generation needs only earlier ones); within a generation the
+    // products are independent and, two or more, run on the side streams.  The generations
+    // that hold baby steps come first; then the leaves are started on the side streams
+    // (every T_k they use brought to its leaf level beforehand, so the shared cache is
+    // complete), and the remaining giant steps are built on the context's stream meanwhile.
+    std::map<int, int> gen{{1, 0}};
+    std::function<int(int)> generation = [&](int k) -> int {
+        auto it = gen.find(k);
+        if (it != gen.end()) return it->second;
+        const int a = k / 2, bb = k - k / 2;
+        int g = std::max(generation(a), generation(bb));
+        if (a != bb) g = std::max(g, generation(bb - a));
+        gen[k] = g + 1;
+        return g + 1;
+    };
+    int baby_gen = 0, maxgen = 0;
+    for (int k = 2; k < std::min(b, d + 1); ++k) baby_gen = std::max(baby_gen, generation(k));
+    for (int g : giants) generation(g);
+    for (const auto& kv : gen) maxgen = std::max(maxgen, kv.second);
+    auto fork = [&](int nwork) -> int {
+        ensure_side_streams(cx);
+        CUDA_CHECK(cudaEventRecord(cx->fork_ev, cx->stream));
+        const int nside = std::min(nwork, ckks_ctx::NSIDE);
+        for (int k = 0; k < nside; ++k) CUDA_CHECK(cudaStreamWaitEvent(cx->side[k], cx->fork_ev, 0));
+        return nside;
+    };
+    auto join = [&](int nside, cudaStream_t main_stream) {
+        for (int k = 0; k < nside; ++k) {
+            CUDA_CHECK(cudaEventRecord(cx->side_ev[k], cx->side[k]));
+            CUDA_CHECK(cudaStreamWaitEvent(main_stream, cx->side_ev[k], 0));
+        }
+    };
+    auto run_generations = [&](int g0, int g1) {
+        for (int g = g0; g <= g1; ++g) {
+            std::vector<int> ks;
+            for (const auto& kv : gen)
+                if (kv.second == g && !pw.T.count(kv.first)) ks.push_back(kv.first);
+            if (ks.empty()) continue;
+            for (int k : ks) pw.warm(k);
+            if (!cx->giant_streams || ks.size() < 2) {
+                for (int k : ks) pw.T[k] = pw.product(k);
+                continue;
+            }
+            const cudaStream_t main_stream = cx->stream;
+            StreamRestore restore{cx, main_stream};
+            const int nside = fork((int)ks.size());
+            for (size_t i = 0; i < ks.size(); ++i) {
+                cx->stream = cx->side[i % ckks_ctx::NSIDE];
+                pw.T[ks[i]] = pw.product(ks[i]);
+            }
+            join(nside, main_stream);
+            cx->stream = main_stream;
+            for (int k : ks) pw.T[k].buf.stream = main_stream;
+        }
+    };
+    run_generations(1, baby_gen);
     for (const auto& c : leaves) {
         int lev = 1 << 30;
         for (int k = 1; k < (int)c.size(); ++k)
@@ -1191,28 +1198,25 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
         for (int k = 1; k < (int)c.size(); ++k)
             if (c[k] != 0.0) pw.at(k, lev);
     }
-    ckks_ctx* cx = x.ctx;
     std::vector<PolyVal> leaf_vals(leaves.size());
     if (cx->giant_streams && leaves.size() >= 2) {
-        ensure_side_streams(cx);
         const cudaStream_t main_stream = cx->stream;
-        StreamRestore restore{cx, main_stream};
-        CUDA_CHECK(cudaEventRecord(cx->fork_ev, main_stream));
-        const int nside = std::min((int)leaves.size(), ckks_ctx::NSIDE);
-        for (int k = 0; k < nside; ++k) CUDA_CHECK(cudaStreamWaitEvent(cx->side[k], cx->fork_ev, 0));
-        for (size_t i = 0; i < leaves.size(); ++i) {
-            cx->stream = cx->side[i % ckks_ctx::NSIDE];
-            leaf_vals[i] = cheb_leaf(pw, leaves[i]);
+        int nside = 0;
+        {
+            StreamRestore restore{cx, main_stream};
+            nside = fork((int)leaves.size());
+            for (size_t i = 0; i < leaves.size(); ++i) {
+                cx->stream = cx->side[i % ckks_ctx::NSIDE];
+                leaf_vals[i] = cheb_leaf(pw, leaves[i]);
+            }
         }
-        for (int k = 0; k < nside; ++k) {
-            CUDA_CHECK(cudaEventRecord(cx->side_ev[k], cx->side[k]));
-            CUDA_CHECK(cudaStreamWaitEvent(main_stream, cx->side_ev[k], 0));
-        }
-        cx->stream = main_stream;
+        run_generations(baby_gen + 1, maxgen);       // on the context's stream, beside the leaves
+        join(nside, main_stream);
         for (auto& v : leaf_vals)       // freed later on the context's stream, after its uses there
             if (!v.is_const) v.ct.buf.stream = main_stream;
     } else {
         for (size_t i = 0; i < leaves.size(); ++i) leaf_vals[i] = cheb_leaf(pw, leaves[i]);
+        run_generations(baby_gen + 1, maxgen);
     }
     // The division as a tree (children visited Q before R, leaves in the same order as above);
     // internal nodes are combined by height: nodes of one height are independent and, two or
