@@ -449,11 +449,14 @@ def run_ours(args):
         K.lib().ckks_ct_export_rns(ctx, gout, host_out.ctypes.data_as(K.ctypes.c_void_p))
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
 
-    # per-kernel CUDA-event timing of one more (eager) block: roofline of the dominant kernel
+    # per-kernel CUDA-event timing of one more (eager) block: roofline of the dominant kernel;
+    # side streams off so that each kernel is timed alone, not while sharing the GPU
+    K.ckks_ctx_set_side_streams(ctx, 0)
     K.ckks_ctx_reset_counters(ctx)
     K.ckks_ctx_set_timing(ctx, 1)
     K.ckks_block(ctx, s["keys"], s["ct"], s["conv"], s["bt"], out)
     K.ckks_ctx_set_timing(ctx, 0)
+    K.ckks_ctx_set_side_streams(ctx, 1)
     kst = K.ckks_ctx_kernel_stats(ctx)
     total = sum(v["ms"] for v in kst.values())
     top = max(kst.items(), key=lambda kv: kv[1]["ms"])

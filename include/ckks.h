@@ -131,6 +131,13 @@ int ckks_ctx_set_ntt_choices(ckks_ctx* ctx, const int32_t* choice8);
  * its first memory access, so results are identical either way.  Captured launches are
  * always plain.  on == 0: plain launches everywhere. */
 int ckks_ctx_set_pdl(ckks_ctx* ctx, int on);
+/* Independent work inside one operation (the giant steps of an HMatmul, the Chebyshev
+ * leaves, the products of one generation of the Chebyshev power ladder, the division nodes
+ * of one height) runs on up to four side streams joined back by events (parallel branches of
+ * a captured graph) when on != 0 (the default); on == 0 keeps everything on the context's
+ * stream, e.g. so that per-kernel event timing measures each kernel alone.  Results are
+ * identical either way. */
+int ckks_ctx_set_side_streams(ckks_ctx* ctx, int on);
 
 /* ---- keys (Sec. 2.1 KeyGen) ----------------------------------------------- */
 /* Secret key s (h-sparse or uniform ternary), public key (-a s + e, a) over Q_L,

@@ -61,6 +61,7 @@ _SIGS = {
     "ckks_ctx_gauss_table": [VP, VP],
     "ckks_ctx_set_timing": [VP, I],
     "ckks_ctx_set_pdl": [VP, I],
+    "ckks_ctx_set_side_streams": [VP, I],
     "ckks_ctx_counters": [VP, VP],
     "ckks_ctx_reset_counters": [VP],
     "ckks_ctx_kernel_stats": [VP, VP, I, VP],
@@ -314,6 +315,10 @@ def ckks_ctx_set_ntt_choices(ctx, choice8):
     a = np.ascontiguousarray(choice8, dtype=np.int32)
     assert a.size == 8
     ctx.check(lib().ckks_ctx_set_ntt_choices(ctx, _ptr(a)))
+
+
+def ckks_ctx_set_side_streams(ctx, on):
+    ctx.check(lib().ckks_ctx_set_side_streams(ctx, int(on)))
 
 
 def ckks_ctx_set_pdl(ctx, on):

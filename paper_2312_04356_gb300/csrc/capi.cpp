@@ -218,6 +218,13 @@ int ckks_ctx_set_pdl(ckks_ctx* ctx, int on) {
     });
 }
 
+int ckks_ctx_set_side_streams(ckks_ctx* ctx, int on) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        ctx->giant_streams = on != 0;
+    });
+}
+
 int ckks_ctx_counters(const ckks_ctx* ctx, int64_t* out) {
     return guard(ctx, [&] {
         REQ(ctx);

@@ -278,7 +278,7 @@ def _pixels(d, slots):
 def test_block_small_bitexact():
     """the whole Alg. 1 block (conv -> ModRaise -> CtoS -> EvalMod x2 -> mask -> StoC1) on the
     config-2 chain at N = 2^10: bit-exact ciphertext and decoded error <= 2^-12, with
-    dependent (default) and plain kernel launches"""
+    dependent (default) and plain kernel launches, with and without side streams"""
     d = _block_pair("cfg2_small", 31)
     K, o, ctx, keys = d["K"], d["o"], d["ctx"], d["keys"]
     ct = o.encrypt(d["pt"], 2)
@@ -300,6 +300,10 @@ def test_block_small_bitexact():
     gblk0 = K.ckks_block(ctx, keys, gct, gplan, d["bt"])
     K.ckks_ctx_set_pdl(ctx, 1)
     assert (K.ckks_ct_export_rns(ctx, gblk0) == K.ckks_ct_export_rns(ctx, gblk)).all()
+    K.ckks_ctx_set_side_streams(ctx, 0)            # everything on one stream: the same residues
+    gblk1 = K.ckks_block(ctx, keys, gct, gplan, d["bt"])
+    K.ckks_ctx_set_side_streams(ctx, 1)
+    assert (K.ckks_ct_export_rns(ctx, gblk1) == K.ckks_ct_export_rns(ctx, gblk)).all()
     zexp, _ = _expected_slots(d)
     got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gblk))
     assert np.abs(_pixels(d, got) - _pixels(d, zexp)).max() < 2.0 ** -12
