@@ -221,7 +221,7 @@ int ckks_ctx_set_pdl(ckks_ctx* ctx, int on) {
 int ckks_ctx_set_side_streams(ckks_ctx* ctx, int on) {
     return guard(ctx, [&] {
         REQ(ctx);
-        ctx->giant_streams = on != 0;
+        ctx->side_streams_on = on != 0;
     });
 }
 

@@ -87,7 +87,7 @@ struct ckks_ctx {
     static constexpr int NSIDE = 4;
     cudaStream_t side[NSIDE] = {};
     cudaEvent_t fork_ev = nullptr, side_ev[NSIDE] = {};
-    bool giant_streams = true;
+    bool side_streams_on = true;
     DevPrime* d_primes = nullptr;
     u64* d_tables = nullptr;
     u64* d_gauss = nullptr;
