@@ -23,10 +23,13 @@
  *    no call takes ownership of its arguments.  Inputs are const; output
  *    handles are overwritten (their device storage is resized as needed).
  *    Output handles may alias inputs unless stated otherwise.
- *  - All device work is enqueued on the stream given to ckks_ctx_create; calls
- *    return once the work is enqueued unless stated otherwise.  ckks_sync waits
- *    and reports deferred device errors.  A handle may only be used with the
- *    context that created it.
+ *  - All device work is enqueued on the stream given to ckks_ctx_create (and, for
+ *    independent work inside one call, on side streams that the call joins back to
+ *    it before returning; see ckks_ctx_set_side_streams); calls return once the
+ *    work is enqueued unless stated otherwise.  ckks_sync waits and reports
+ *    deferred device errors.  A handle may only be used with the context that
+ *    created it, and a context by one host thread at a time (the serving runtime's
+ *    worker replays recorded graphs and does not touch the context's state).
  *  - Return value: CKKS_OK (0) or one of the CKKS_E* codes; no exceptions cross
  *    the ABI.  ckks_last_error(ctx) describes the last failure on that context.
  *  - Randomness: SplitMix64 used as a counter generator; stream key
