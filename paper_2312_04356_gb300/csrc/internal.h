@@ -96,6 +96,7 @@ struct ckks_ctx {
     u64* d_qlinv = nullptr;                  // q_l^{-1} mod q_i [nq][nq], Shoup [nq][nq]
     std::vector<u64> h_qlinv;                // host copy of the residues [nq][nq]
     u64* d_pqlinv = nullptr;                 // (P q_l)^{-1} mod q_i [nq][nq], Shoup [nq][nq]
+    u64* d_pqlinv2 = nullptr;                // the same times 2 (products doubled in the tail)
     u64* d_pmod = nullptr;                   // P mod q_i [nq], Shoup [nq]
     std::vector<int*> d_ext_ids;             // per level: [0..l] + specials
     // per level: the rows of the raised digits that ModUp converts (offsets in limbs

@@ -191,6 +191,7 @@ ckks_ctx::~ckks_ctx() {
     cudaFree(d_pinv);
     cudaFree(d_qlinv);
     cudaFree(d_pqlinv);
+    cudaFree(d_pqlinv2);
     cudaFree(d_pmod);
 }
 
@@ -292,16 +293,21 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
         pmod[i] = pr;
         pmod[c->nq + i] = shoup(pr, c->q[i]);
     }
+    std::vector<u64> pqlinv2(2 * (size_t)c->nq * c->nq, 0);
     for (int l = 1; l < c->nq; ++l)
         for (int i = 0; i < l; ++i) {
             u64 v = invmod(mulmod(pmod[i], c->q[l] % c->q[i], c->q[i]), c->q[i]);
             pqlinv[(size_t)l * c->nq + i] = v;
             pqlinv[(size_t)c->nq * c->nq + (size_t)l * c->nq + i] = shoup(v, c->q[i]);
+            const u64 v2 = mulmod(v, 2, c->q[i]);
+            pqlinv2[(size_t)l * c->nq + i] = v2;
+            pqlinv2[(size_t)c->nq * c->nq + (size_t)l * c->nq + i] = shoup(v2, c->q[i]);
         }
     c->d_pinv = dev_upload_persistent(pinv);
     c->d_qlinv = dev_upload_persistent(qlinv);
     c->h_qlinv.assign(qlinv.begin(), qlinv.begin() + (size_t)c->nq * c->nq);
     c->d_pqlinv = dev_upload_persistent(pqlinv);
+    c->d_pqlinv2 = dev_upload_persistent(pqlinv2);
     c->d_pmod = dev_upload_persistent(pmod);
     // every base-conversion table up front (no allocation later, e.g. inside stream capture)
     for (int l = 0; l <= c->L; ++l) {
@@ -558,7 +564,7 @@ void key_switch_inner(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig
 
 // ModDown fused with the rescale after it: both halves of acc (Q_l u P, NTT domain) divided
 // by P q_l, (acc - Conv_{q_l, P -> Q_{l-1}}(acc)) (P q_l)^{-1}; out [2][l][N]
-void mod_down_rescale(ckks_ctx* c, u64* acc, int level, u64* out) {
+void mod_down_rescale(ckks_ctx* c, u64* acc, int level, u64* out, bool twice) {
     CK_CHECK(level >= 1, CKKS_ELEVEL, "cannot rescale a level-0 ciphertext");
     c->ops["rescale"]++;
     const size_t n = c->n;
@@ -576,8 +582,9 @@ void mod_down_rescale(ckks_ctx* c, u64* acc, int level, u64* out) {
     DevBuf conv(2 * (size_t)l * n, c->stream);
     kern::base_convert(c, c->mdrs_tab(l), ab + (size_t)l * n, n, conv.ptr, n, 2, next * n, (size_t)l * n);
     kern::ntt_forward(c, conv.ptr, 2 * l, c->d_iota, l);
-    const u64* s = c->d_pqlinv + (size_t)l * c->nq;
-    const u64* sp = c->d_pqlinv + (size_t)c->nq * c->nq + (size_t)l * c->nq;
+    const u64* tab = twice ? c->d_pqlinv2 : c->d_pqlinv;     // twice: 2 x the result, same pass
+    const u64* s = tab + (size_t)l * c->nq;
+    const u64* sp = tab + (size_t)c->nq * c->nq + (size_t)l * c->nq;
     kern::sub_mul_scalar(c, ab, conv.ptr, s, sp, out, 2 * l, c->d_iota, l, next * n);    // aa = ab + next N
 }
 
@@ -695,7 +702,7 @@ ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
 
 // HMult, relinearisation and rescale: (d0, d1) + keyswitch(d2) kept over Q_l u P and
 // divided by P q_l at once (the relinearisation's ModDown fused with the rescale)
-ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
+ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b, bool twice) {
     ckks_ctx* c = a.ctx;
     CK_CHECK(a.level == b.level, CKKS_EINVAL, "HMult operands at different levels");
     CK_CHECK(a.level >= 1, CKKS_ELEVEL, "cannot rescale a level-0 ciphertext");
@@ -713,7 +720,7 @@ ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct
     // relinearisation key switch with P d0, P d1 added on the Q rows in the same kernel
     key_switch_inner(c, keys, D.ptr, ndig, l, 0, 1, acc.ptr, false, d0, nl, c->d_pmod, c->d_pmod + c->nq, d1);
     ckks_ct o = new_ct(c, l - 1, a.scale * b.scale / (double)c->q[l]);
-    mod_down_rescale(c, acc.ptr, l, o.buf.ptr);
+    mod_down_rescale(c, acc.ptr, l, o.buf.ptr, twice);
     return o;
 }
 
@@ -966,7 +973,7 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
     }
     if (rescale_out) {
         ckks_ct o = new_ct(c, l - 1, scale / (double)c->q[l]);
-        mod_down_rescale(c, acc.ptr, l, o.buf.ptr);
+        mod_down_rescale(c, acc.ptr, l, o.buf.ptr, false);
         return o;
     }
     ckks_ct o = new_ct(c, l, scale);
@@ -1019,8 +1026,7 @@ struct ChebPowers {
     ckks_ct product(int k) {
         const int a = k / 2, b = k - k / 2;
         const int m = prod_level(T.at(a).ctx, std::min(T.at(a).level, T.at(b).level));
-        ckks_ct t = mul_relin_rescale(*keys, at(a, m), at(b, m));
-        t = add(t, t);
+        ckks_ct t = mul_relin_rescale(*keys, at(a, m), at(b, m), true);     // 2 T_a T_b
         return (a == b) ? add_const(t, -1.0) : sub(t, at(b - a, m - 1));
     }
     // the level_downs product(k) reads, made ahead (so that products can run side by side)
@@ -1336,8 +1342,7 @@ ckks_ct eval_relu(const ckks_keys& keys, const ckks_ct& x, const std::vector<std
 ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r) {
     ckks_ct y = cheb_eval(keys, x, coeffs);
     for (int i = 0; i < r; ++i) {
-        y = mul_relin_rescale(keys, y, y);
-        y = add(y, y);
+        y = mul_relin_rescale(keys, y, y, true);     // 2 y^2
         y = add_const(y, -1.0);
     }
     return y;

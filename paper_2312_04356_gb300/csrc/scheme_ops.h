@@ -28,7 +28,8 @@ std::vector<ckks_ct> rotate_hoisted(const ckks_keys& keys, const ckks_ct& a, con
 ckks_ct rotate(const ckks_keys& keys, const ckks_ct& a, long long r);
 ckks_ct conjugate(const ckks_keys& keys, const ckks_ct& a);
 ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b);
-ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b);
+// twice: 2 a b (the doubling folded into the rescale's tail; same residues as add(t, t))
+ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b, bool twice = false);
 ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps, bool rescale_out = false);
 ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins,
                    const std::vector<const ckks_ptset*>& pss, bool rescale_out);
