@@ -275,6 +275,15 @@ int ckks_conv2d_cins(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, co
  * the sets' BSGS over t = 0, 1, ... gives the stride-2 conv (ckks_block_multi). */
 int ckks_ptset_conv_fused_s2(ckks_ctx* ctx, const double* weights, int cin, int cout, int f, int w_in, int t,
                              int level, double pt_scale, int bsgs_B, ckks_ptset** out);
+/* Downsampling depthwise conv2d (Sec. 3.3.4): K[c][f][f] (host, row-major, read during the
+ * call) are the stride-2 kernels of channels 0 .. c - 1, output channel o = input channel o;
+ * the set is ckks_ptset_conv_fused_s2 with the diagonal weights W[o][o] = K[o] (cin = cout =
+ * c <= 4C: the channels of up to four input ciphertexts, which fill one output ciphertext;
+ * larger layers split their channels into such groups).  Average pooling with stride 2 is
+ * the case of equal kernels 1 / f^2 (zero padding f/2 counted in the mean).  CKKS_EINVAL for
+ * c < 1, f < 1, c^2 f^2 > 2^28, and whatever ckks_ptset_conv_fused_s2 refuses. */
+int ckks_ptset_dwconv_fused_s2(ckks_ctx* ctx, const double* K, int c, int f, int w_in, int t, int level,
+                               double pt_scale, int bsgs_B, ckks_ptset** out);
 /* The Alg. 2 decomposition (lines 1-8) as one plaintext set: diagonals at offsets b w/4,
  * |b| < w (0/1 masks), encoded at (level, scale); the slot permutation described at
  * ckks_boot_create.  Apply with ckks_bsgs + ckks_rescale. */
@@ -298,7 +307,8 @@ int ckks_fc_stoc(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const 
  * K[c][f][f] (cross-correlation, 'same' padding, kernel vectors of Fig. 1) packed in one
  * real-CinS plaintext <k_1 | ... | k_C>, so that one PMult gives k_i * i_i in every slice
  * (Eq. 6).  ckks_dwconv_cins = PMult + rescale; the output stays real-CinS.  Average
- * pooling with stride 1 is the case of equal kernels 1 / f^2. */
+ * pooling with stride 1 is the case of equal kernels 1 / f^2; with stride 2 it is
+ * ckks_ptset_dwconv_fused_s2 (a downsampling conv). */
 int ckks_encode_dwconv_kernel(ckks_ctx* ctx, const double* K, int c, int f, int w, int level, double scale,
                               ckks_pt* out);
 int ckks_dwconv_cins(ckks_ctx* ctx, const ckks_ct* in, const ckks_pt* kernel, ckks_ct* out);

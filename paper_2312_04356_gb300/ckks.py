@@ -114,6 +114,7 @@ _SIGS = {
     "ckks_conv2d_cins": [VP, VP, VP, VP, VP],
     "ckks_encode_dwconv_kernel": [VP, VP, I, I, I, I, D, VP],
     "ckks_ptset_conv_fused_s2": [VP, VP, I, I, I, I, I, I, D, I, PVP],
+    "ckks_ptset_dwconv_fused_s2": [VP, VP, I, I, I, I, I, D, I, PVP],
     "ckks_ptset_decompose": [VP, I, I, D, I, PVP],
     "ckks_ptset_fc_stoc": [VP, VP, I, I, I, D, I, PVP],
     "ckks_fc_stoc": [VP, VP, VP, VP, I, VP],
@@ -613,6 +614,16 @@ def ckks_ptset_conv_fused_s2(ctx, weights, cin, cout, f, w_in, t, level, pt_scal
     out = ctypes.c_void_p()
     ctx.check(lib().ckks_ptset_conv_fused_s2(ctx, _ptr(W), cin, cout, f, w_in, t, level, pt_scale, bsgs_B,
                                              ctypes.byref(out)))
+    return PtSet(out.value, ctx)
+
+
+def ckks_ptset_dwconv_fused_s2(ctx, K, w_in, t, level, pt_scale, bsgs_B=0) -> PtSet:
+    """K: (c, f, f) stride-2 depthwise kernels -> the decomposed conv set of input ciphertext t"""
+    a = _f64(K)
+    assert a.ndim == 3 and a.shape[1] == a.shape[2]
+    out = ctypes.c_void_p()
+    ctx.check(lib().ckks_ptset_dwconv_fused_s2(ctx, _ptr(a), a.shape[0], a.shape[1], w_in, t, level, pt_scale,
+                                               bsgs_B, ctypes.byref(out)))
     return PtSet(out.value, ctx)
 
 

@@ -835,6 +835,24 @@ int ckks_ptset_conv_fused_s2(ckks_ctx* ctx, const double* W, int cin, int cout, 
     });
 }
 
+// Downsampling depthwise conv (Sec. 3.3.4): output channel o reads input channel o only, so
+// the kernels form a diagonal W[o][o] = K[o] of the stride-2 conv above.
+int ckks_ptset_dwconv_fused_s2(ckks_ctx* ctx, const double* K, int c, int f, int w_in, int t, int level,
+                               double pt_scale, int B, ckks_ptset** out) {
+    std::vector<double> W;
+    const int st = guard(ctx, [&] {
+        REQ(ctx);
+        REQ(K);
+        CK_CHECK(c >= 1 && f >= 1 && (long long)c * c * f * f <= (1LL << 28), CKKS_EINVAL,
+                 "channel count or kernel size out of range");
+        W.assign((size_t)c * c * f * f, 0.0);
+        for (int o = 0; o < c; ++o)
+            std::copy(K + (size_t)o * f * f, K + (size_t)(o + 1) * f * f, W.begin() + ((size_t)o * c + o) * f * f);
+    });
+    if (st != CKKS_OK) return st;
+    return ckks_ptset_conv_fused_s2(ctx, W.data(), c, c, f, w_in, t, level, pt_scale, B, out);
+}
+
 int ckks_ptset_fc_stoc(ckks_ctx* ctx, const double* M, int n_out, int n_in, int level, double pt_scale, int B,
                        ckks_ptset** out) {
     return guard(ctx, [&] {

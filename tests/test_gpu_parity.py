@@ -599,6 +599,65 @@ def _downsample_own_plans():
     assert np.abs(pix - want).max() < 2.0 ** -12
 
 
+def test_downsample_dwconv_and_avgpool():
+    """downsampling depthwise conv and stride-2 average pooling (Sec. 3.3.4) through Alg. 2:
+    the library's depthwise sets (ckks_ptset_dwconv_fused_s2) give the same ciphertext as the
+    general stride-2 sets with the diagonal weights, and decode within 2^-12 of the FP64
+    strided depthwise conv / average pooling; channels without a kernel decode to zero"""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        _downsample_dwconv_avgpool()
+
+
+def _downsample_dwconv_avgpool():
+    from oracle.scheme import Oracle
+    from paper_2312_04356_gb300 import ckks as K
+    seed = 63
+    P, w0, w, f, C, x, _ = _ds_case(seed)
+    ctx = gpu_ctx("cfg2_small", seed)
+    m = P.n // 2
+    bt_in = K.ckks_boot_create(ctx, w, w0, C, stride=2)
+    bt_out = K.ckks_boot_create(ctx, w // 2, w0 // 2, 4 * C)
+    conv_rots = {(d * (w * w // 8)) % m for d in range(1, 4 * C)}
+    keys = K.ckks_keygen(ctx, sorted(set(K.ckks_boot_rotations(bt_in)) | set(K.ckks_boot_rotations(bt_out))
+                                     | conv_rots), True)
+    cfg_in = BT.BootConfig(Oracle(P, seed), w, w0, C, stride=2)      # layout only
+    gins = []
+    for t in range(2):
+        re, im = _ds_tail_slots(P, cfg_in, x[t * C:(t + 1) * C], seed + t)
+        gre = K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, re, cfg_in.l_em, cfg_in.s_em), 2 * t + 1)
+        gim = K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, im, cfg_in.l_em, cfg_in.s_em), 2 * t + 2)
+        gins.append(K.ckks_level_down(ctx, K.ckks_stoc1(ctx, keys, gre, gim, bt_in), 1))
+    lev, sc = K.ckks_ct_info(gins[0])
+    s_pt = (2.0 ** 49 * float(P.q[1])) / sc
+    c = 2 * C
+    Kd = np.random.default_rng(seed).normal(0.0, 0.3, (c, f, f))
+    Ka = np.full((c, f, f), 1.0 / (f * f))
+    w2 = w // 2
+    ell2 = w2 * w2 // 2
+
+    def run(plans):
+        return K.ckks_block_multi(ctx, keys, gins, plans, bt_out)
+
+    def decoded_pixels(ct):
+        got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, ct))
+        return np.stack([E.encode(got[i * ell2:(i + 1) * ell2], w2 * w2) for i in range(4 * C)])
+
+    def diag_weights(k):
+        Wd = np.zeros((c, c, f, f))
+        Wd[np.arange(c), np.arange(c)] = k
+        return Wd
+
+    gdw = run([K.ckks_ptset_dwconv_fused_s2(ctx, Kd, w, t, 1, s_pt) for t in range(2)])
+    gfull = run([K.ckks_ptset_conv_fused_s2(ctx, diag_weights(Kd), c, c, f, w, t, 1, s_pt) for t in range(2)])
+    assert (K.ckks_ct_export_rns(ctx, gdw) == K.ckks_ct_export_rns(ctx, gfull)).all()
+    for ct, k in ((gdw, Kd), (run([K.ckks_ptset_dwconv_fused_s2(ctx, Ka, w, t, 1, s_pt) for t in range(2)]), Ka)):
+        pix = decoded_pixels(ct)
+        want = np.stack([E.flatten_padded(v, w2) for v in E.conv2d_stride2(x, diag_weights(k))])
+        assert np.abs(pix[:c] - want).max() < 2.0 ** -12
+        assert np.abs(pix[c:]).max() < 2.0 ** -12
+
+
 def test_fc_stoc_bitexact_and_fp64():
     """FC fused with the whole StoC (Sec. 4.3): replication rotations + BSGS over the n_in
     diagonals of V M, bit-exact against the oracle; the library's own set decodes (coefficient

@@ -110,6 +110,58 @@ def test_decomposed_kernels_give_the_stride2_conv(f):
     assert np.abs(acc - ref).max() < 1e-12
 
 
+def _dwconv_stride2_loops(x, Kd):
+    c_, h, _ = x.shape
+    f = Kd.shape[1]
+    c = f // 2
+    out = np.zeros((c_, h // 2, h // 2))
+    for i in range(c_):
+        for y in range(h // 2):
+            for xx in range(h // 2):
+                for a in range(f):
+                    for b in range(f):
+                        r, col = 2 * y + a - c, 2 * xx + b - c
+                        if 0 <= r < h and 0 <= col < h:
+                            out[i, y, xx] += Kd[i, a, b] * x[i, r, col]
+    return out
+
+
+def _avgpool_stride2(x, f):
+    """mean over the f x f windows at stride 2 of the zero-padded image (padding counted)"""
+    c = f // 2
+    h = x.shape[1]
+    xp = np.pad(x, ((0, 0), (c, c), (c, c)))
+    s = sum(xp[:, a:a + h:2, b:b + h:2] for a in range(f) for b in range(f))
+    return s / (f * f)
+
+
+@pytest.mark.parametrize("f", [3, 5])
+def test_downsampling_dwconv_and_avgpool_through_the_decomposition(f):
+    """Sec. 3.3.4: a downsampling depthwise conv is the stride-2 conv whose weights are
+    diagonal (output channel i reads input channel i); through the decomposed kernels of the
+    polyphase images it gives the strided depthwise conv (brute force), and with equal
+    kernels 1/f^2 the stride-2 average pooling (window sums of the padded image)"""
+    C, h = 3, 8
+    x = rng.random((4 * C, h, h))
+    Kd = rng.normal(size=(4 * C, f, f))
+    W = np.zeros((4 * C, 4 * C, f, f))
+    W[np.arange(4 * C), np.arange(4 * C)] = Kd
+    pp = E.decompose_images(x)
+
+    def through_decomposition(W):
+        return sum(E.conv2d_same(pp[4 * C * t:4 * C * (t + 1)], E.decompose_kernels(W, C, t)) for t in range(4))
+
+    assert np.abs(through_decomposition(W) - _dwconv_stride2_loops(x, Kd)).max() < 1e-12
+    Wa = np.zeros_like(W)
+    Wa[np.arange(4 * C), np.arange(4 * C)] = 1.0 / (f * f)
+    assert np.abs(through_decomposition(Wa) - _avgpool_stride2(x, f)).max() < 1e-12
+    # the decomposed kernels of input ciphertext t touch only output channels tC .. tC + C - 1
+    for t in range(4):
+        Wt = E.decompose_kernels(W, C, t)
+        rows = np.flatnonzero(np.abs(Wt).reshape(4 * C, -1).sum(axis=1))
+        assert set(rows.tolist()) <= set(range(t * C, (t + 1) * C))
+
+
 def _tail_inputs(o, cfg, x, nonce):
     """Re / Im ciphertexts as the bootstrap hands them to the tail: slot i l + u holds pixel
     rev_l(u) (Re) or rev_l(u) + l (Im) of channel i, divided by the mask value; pixels outside
