@@ -83,7 +83,9 @@ def test_ntt_bitexact(name):
 def test_cluster_ntt_in_key_switching():
     """the one-launch cluster NTT forced for every size (1- and 3-limb transforms round-trip;
     the limb-list transforms of ModUp, ModDown and the key switch): hoisted rotations at
-    N = 2^16 stay bit-exact against the oracle"""
+    N = 2^16 stay bit-exact against the oracle.  Then every two-pass variant forced in turn,
+    and the default: hoisted rotations, HMult + relinearisation (ModDown) and rescale
+    bit-exact at N = 2^16"""
     K, o, ctx, keys = make_pair("cfg2", 7, rotations=[1, 5], conj=False)
     P = o.P
     K.ckks_ctx_set_ntt_variant(ctx, 5)
@@ -101,8 +103,17 @@ def test_cluster_ntt_in_key_switching():
     ct = o.encrypt(o.encode_pt(z, lev, P.delta[lev]), 4)
     g = import_ct(K, ctx, ct)
     rots = K.ckks_rotate_hoisted(ctx, keys, g, [1, 5])
-    for r, gr in zip((1, 5), rots):
-        assert_ct_equal(K, ctx, gr, o.rotate(ct, r), "rotation %d" % r)
+    want_rot = [o.rotate(ct, r) for r in (1, 5)]
+    for r, gr, w in zip((1, 5), rots, want_rot):
+        assert_ct_equal(K, ctx, gr, w, "rotation %d" % r)
+    want_rs = o.rescale(ct)
+    want_hm = o.mul_relin(ct, ct)
+    for v in (0, 1, 2, 3, 4, -1):
+        K.ckks_ctx_set_ntt_variant(ctx, v)
+        for r, gr, w in zip((1, 5), K.ckks_rotate_hoisted(ctx, keys, g, [1, 5]), want_rot):
+            assert_ct_equal(K, ctx, gr, w, "rotation %d, variant %d" % (r, v))
+        assert_ct_equal(K, ctx, K.ckks_rescale(ctx, g), want_rs, "rescale, variant %d" % v)
+        assert_ct_equal(K, ctx, K.ckks_mul_relin(ctx, keys, g, g), want_hm, "HMult, variant %d" % v)
     K.ckks_ctx_set_ntt_variant(ctx, -1)
 
 
