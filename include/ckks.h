@@ -260,12 +260,12 @@ int ckks_bsgs(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* ct, const ckk
  * BSGS over offsets d*l, d < C; bsgs_B = 0 picks 2^ceil(log2(C)/2). */
 int ckks_ptset_conv_fused(ckks_ctx* ctx, const double* weights, int cin, int cout, int f, int w, int level,
                           double pt_scale, int bsgs_B, ckks_ptset** out);
-/* Alg. 1 line 1: BSGS with the fused diagonals, then rescale.  The output is
+/* Alg. 1, conv step: BSGS with the fused diagonals, then rescale.  The output is
  * coefficient-encoded: coefficient k*C + rev_C(i) holds Delta * o_i[k] (Thm. 2, Y = X^C). */
 int ckks_conv2d_cins(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ckks_ptset* conv,
                      ckks_ct* out);
 
-/* Decomposed downsampling conv2d (Alg. 2 lines 10-11).  W[cout][cin][f][f] is a stride-2
+/* Decomposed downsampling conv2d (Alg. 2's decomposed conv).  W[cout][cin][f][f] is a stride-2
  * cross-correlation with zero padding f/2 (PyTorch semantics, even image width).  Input
  * ciphertext t holds channels tC .. tC + C - 1 (C = N / w_in^2) as the stride-2 tail of
  * ckks_boot_create leaves them: 4C polyphase slices of width w_in/2.  The set rewrites the
@@ -284,7 +284,7 @@ int ckks_ptset_conv_fused_s2(ckks_ctx* ctx, const double* weights, int cin, int 
  * c < 1, f < 1, c^2 f^2 > 2^28, and whatever ckks_ptset_conv_fused_s2 refuses. */
 int ckks_ptset_dwconv_fused_s2(ckks_ctx* ctx, const double* K, int c, int f, int w_in, int t, int level,
                                double pt_scale, int bsgs_B, ckks_ptset** out);
-/* The Alg. 2 decomposition (lines 1-8) as one plaintext set: diagonals at offsets b w/4,
+/* The Alg. 2 decomposition as one plaintext set: diagonals at offsets b w/4,
  * |b| < w (0/1 masks), encoded at (level, scale); the slot permutation described at
  * ckks_boot_create.  Apply with ckks_bsgs + ckks_rescale. */
 int ckks_ptset_decompose(ckks_ctx* ctx, int w, int level, double scale, int bsgs_B, ckks_ptset** out);
@@ -328,9 +328,9 @@ typedef struct ckks_boot_params {
  * T_{N/2}^{-1} in ctos_levels BSGS levels (largest stride first, plaintext scale q_l,
  * last level times 1/2); Chebyshev coefficients of cos(2 pi (K_eff y - 1/4) / 2^r);
  * padding masks times q0 / (2 pi delta0); StoC1 = S_{l <- 1} in stoc_levels levels.
- * stride = 2 (Alg. 2 lines 1-9): after Re + i Im the tail applies the decomposition (one
- * HMatmul by the slot permutation sum_j (>> j l/4) calG_l (<< r_j), r = (0, l/2, w/4,
- * l/2 + w/4), calG_l of Appendix B, plaintexts at canonical scale; see
+ * stride = 2 (Alg. 2's decomposition and S_{l/4<-1}): after Re + i Im the tail applies
+ * the decomposition (one HMatmul by the slot permutation sum_j (>> j l/4) calG_l (<< r_j),
+ * r = (0, l/2, w/4, l/2 + w/4), calG_l of Appendix B, plaintexts at canonical scale; see
  * ckks_ptset_decompose) and StoC1 becomes S_{l/4 <- 1}: the output holds, in slice
  * 4i + q + 2p, the polyphase image x_i[p::2][q::2] of channel i as real CinS of width w/2.
  * Needs w >= 4 and an even w0; l_out is one level lower than with stride 1. */
@@ -366,10 +366,11 @@ int ckks_boot_set_decomp(ckks_ctx* ctx, ckks_boot* bt, const ckks_ptset* ps);
 int ckks_boot_set_coeffs(ckks_ctx* ctx, ckks_boot* bt, const double* coeffs, int deg);
 int ckks_boot_set_masks(ckks_ctx* ctx, ckks_boot* bt, const ckks_pt* re, const ckks_pt* im);
 /* ModRaise -> CtoS -> conjugate split (Re = ct + conj, Im = i (conj - ct)) -> scale drop
- * -> EvalMod(Re), EvalMod(Im) (Alg. 1 line 2). */
+ * -> EvalMod(Re), EvalMod(Im) (Alg. 1, bootstrapping step). */
 int ckks_bootstrap(ckks_ctx* ctx, const ckks_keys* keys, const ckks_boot* bt, const ckks_ct* ct0,
                    ckks_ct* out_re, ckks_ct* out_im);
-/* mask PMults, Re + i Im, HMatmul(S_{l<-1}) (Alg. 1 lines 3-6 without HActivation) */
+/* mask PMults, Re + i Im, HMatmul(S_{l<-1}) (Alg. 1, activation and StoC1 steps, without
+ * HActivation) */
 int ckks_stoc1(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* re, const ckks_ct* im, const ckks_boot* bt,
                ckks_ct* out);
 /* one conv2d + bootstrap block: conv2d_cins -> bootstrap -> stoc1 */
@@ -377,8 +378,8 @@ int ckks_block(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const ck
                const ckks_boot* bt, ckks_ct* out);
 /* The same block over n_in input ciphertexts: sum_t BSGS(in[t], conv[t]) (HAdd, one
  * rescale) -> bootstrap -> stoc1.  With the plaintext sets of ckks_ptset_conv_fused_s2 this
- * is Alg. 2 lines 10-17 (the downsampling conv bootstraps one ciphertext where a stride-1
- * conv followed by densify bootstraps s^2 = 4); with ckks_ptset_conv_fused sets over
+ * is Alg. 2 from the decomposed convs to the end (the downsampling conv bootstraps one
+ * ciphertext where a stride-1 conv followed by densify bootstraps s^2 = 4); with ckks_ptset_conv_fused sets over
  * different input channels it is the C_in > C block matrix-vector product (Sec. 3.3.3).
  * All inputs share level and scale, all sets share level and scale; 1 <= n_in <= 64. */
 int ckks_block_multi(ckks_ctx* ctx, const ckks_keys* keys, int n_in, const ckks_ct* const* in,
@@ -499,7 +500,7 @@ int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, cons
  * device) race on it. */
 int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, int level, uint64_t* d_out);
 
-/* HActivation (Sec. 2.4.2; Alg. 1 lines 3-4) as a composite polynomial ReLU:
+/* HActivation (Sec. 2.4.2; Alg. 1, activation step) as a composite polynomial ReLU:
  * y = s_k(...s_1(x)) with each stage a Chebyshev series (coefficients concatenated in
  * `coeffs`, degrees in degs[n_stages], evaluated as by ckks_eval_poly), then x * y with x
  * brought down to y's level.  With s_1..s_{k-1} normalised odd sign approximations and

@@ -14,21 +14,21 @@ defers them to the CKKS bootstrapping papers it cites in Sec. 2.4):
 * CtoS = T_{N/2}^{-1} (Sec. 2.4) in `ctos_levels` BSGS levels, largest stride first;
   every level's plaintexts are encoded at scale q_l, so the rescale keeps the
   scale; the 1/2 of the conjugate split is folded into the last level.
-* Re = ct + conj(ct), Im = i (conj(ct) - ct) (Alg. 1 line 2), taken while the
+* Re = ct + conj(ct), Im = i (conj(ct) - ct) (Alg. 1, bootstrapping step), taken while the
   scale is still q0 K_eff so that the conjugation's key-switch noise is negligible.
 * One integer multiply + rescale per part drops the scale to the canonical Delta
   of the next level (K_eff absorbs the rounding of that integer).
 * EvalMod: Chebyshev interpolant of cos(2 pi (K_eff y - 1/4) / 2^r) of degree `deg`
   on [-1, 1], then r double-angle steps c <- 2c^2 - 1, giving sin(2 pi t / q0).
-* Mask (Alg. 1 lines 3-4): PMult by the 0/1 padding masks times q0 / (2 pi Delta_0),
+* Mask (Alg. 1, activation step): PMult by the 0/1 padding masks times q0 / (2 pi Delta_0),
   which also turns sin(2 pi t / q0) back into the conv output o.
 * HActivation is not part of this block (it is evaluated by cheb_eval/eval_poly
   on its own).  Recombine Re + i Im, then HMatmul(S_{l<-1}) (StoC1) in
-  `stoc_levels` BSGS levels at canonical scales (Alg. 1 lines 5-6).
+  `stoc_levels` BSGS levels at canonical scales (Alg. 1, StoC1 step).
 * stride = 2 (the next conv downsamples, Alg. 2): between the recombination and the
-  StoC1 the tail applies the decomposition of Alg. 2 lines 1-8 (one HMatmul by the
+  StoC1 the tail applies Alg. 2's decomposition (one HMatmul by the
   permutation sum_j (>> j l/4) calG_l (<< r_j), at canonical scale), and the StoC1 becomes
-  S_{l/4<-1} (line 9): the output holds 4C polyphase slices of (w/2)^2 reals.
+  S_{l/4<-1}: the output holds 4C polyphase slices of (w/2)^2 reals.
 """
 import math
 
@@ -166,8 +166,8 @@ def block(orc: Oracle, ct_in, conv_plan, cfg: BootConfig):
 
 def block_multi(orc: Oracle, cts, conv_plans, cfg: BootConfig):
     """conv2d over several input ciphertexts, then bootstrap + StoC1 tail.  With the
-    decomposed kernels of a stride-2 conv this is Alg. 2 lines 10-17 (BSGS per input
-    ciphertext, HAdd, one rescale; the giant steps of both share one ModDown fused with the
+    decomposed kernels of a stride-2 conv this is Alg. 2 from the decomposed convs to the end
+    (BSGS per input ciphertext, HAdd, one rescale; the giant steps of both share one ModDown fused with the
     rescale); with plain kernels it is the C_in > C generalisation
     (Sec. 3.3.3: the block matrix-vector product, one output ciphertext)."""
     x = orc.bsgs_multi(cts, conv_plans, rescale=True)

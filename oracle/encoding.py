@@ -443,7 +443,7 @@ def rotation_diag(r, m):
 
 
 def decompose_diag(w, n_ring):
-    """Alg. 2 lines 1-8 as one linear map on the slots:
+    """Alg. 2's decomposition as one linear map on the slots:
     D = sum_{j<4} (>> j l/4) calG_l (<< r_j),  r = (0, l/2, w/4, l/2 + w/4)"""
     m = n_ring // 2
     ell = w * w // 2

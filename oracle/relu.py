@@ -1,4 +1,4 @@
-"""Composite polynomial ReLU (HActivation, Sec. 2.4.2 / Alg. 1 lines 3-4) for the oracle.
+"""Composite polynomial ReLU (HActivation, Sec. 2.4.2 / Alg. 1, activation step) for the oracle.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 

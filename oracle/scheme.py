@@ -558,7 +558,7 @@ class Oracle:
 
     # --------------------------------------------------- fused CinS conv ----
     def conv_plan(self, W, cin, cout, f, w, level, pt_scale, B=None):
-        """Alg. 1 line 1: diagonals of S'K^ as a BSGS plan over offsets d*l, d < C"""
+        """Alg. 1, conv step: diagonals of S'K^ as a BSGS plan over offsets d*l, d < C"""
         n = self.P.n
         ell = w * w // 2
         C_ = n // (w * w)

@@ -271,7 +271,7 @@ static int bit_reverse(int x, int bits) {
     return r;
 }
 
-// The decomposition of Alg. 2 lines 1-8 is a permutation of the slots.  Before it, slot
+// Alg. 2's decomposition is a permutation of the slots.  Before it, slot
 // i l + rev_l(k) holds pixels k and k + l of channel i (k = r w + c with r < w/2).  The
 // polyphase image (p, q) of channel i, x[2u + p][2v + q] of size (w/2)^2, goes to slice
 // 4i + q + 2p of length l/4, whose slot rev_{l/4}(u w/2 + v) holds its pixels (u, v) and

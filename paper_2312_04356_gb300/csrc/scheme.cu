@@ -1381,8 +1381,8 @@ ckks_ct block(const ckks_keys& keys, const ckks_boot& bt, const ckks_ptset& conv
 }
 
 // conv over several input ciphertexts (BSGS each, HAdd, one rescale), then the block's
-// bootstrap and tail: Alg. 2 lines 10-17 with the decomposed stride-2 kernels, or the
-// C_in > C block matrix-vector product (Sec. 3.3.3).
+// bootstrap and tail: with the decomposed stride-2 kernels, Alg. 2 from the decomposed convs
+// to the end; otherwise the C_in > C block matrix-vector product (Sec. 3.3.3).
 ckks_ct block_multi(const ckks_keys& keys, const ckks_boot& bt, const std::vector<const ckks_ptset*>& convs,
                     const std::vector<const ckks_ct*>& ins) {
     return boot_tail(keys, bt, bsgs_multi(keys, ins, convs, true));

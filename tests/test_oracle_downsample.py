@@ -19,7 +19,7 @@ def _perm_matrix(src):
 
 @pytest.mark.parametrize("w", [8, 16])
 def test_decomposition_is_the_polyphase_permutation(w):
-    """Alg. 2 lines 1-8 (calG_l with the rotations r and the shifts j l/4) equal the slot
+    """Alg. 2's decomposition (calG_l with the rotations r and the shifts j l/4) equals the slot
     permutation derived from the layouts alone; every slot is moved exactly once; the offsets
     form the arithmetic progression the BSGS plan uses"""
     n = 4 * w * w
@@ -223,7 +223,7 @@ def _conv_plans(o, d, scale_in):
 def test_downsample_tail_and_decomposed_conv(ds_setup):
     """stride-2 tail (mask, Re + i Im, decomposition, S_{l/4<-1}) decodes to the real CinS of
     the polyphase images; the two decomposed BSGS convs + HAdd + rescale decode to the stride-2
-    conv2d (Alg. 2 lines 1-12)"""
+    conv2d (Alg. 2 up to the sum of the decomposed convs)"""
     d = ds_setup
     o, P, w, w0, C, x = d["o"], d["P"], d["w"], d["w0"], d["C"], d["x"]
     cfg = d["cfg_in"]
