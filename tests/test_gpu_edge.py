@@ -41,6 +41,12 @@ def test_error_returns_leave_the_context_usable():
     assert _code(K, lambda: K.ckks_bsgs(ctx, keys, hi, empty)) == K.CKKS_EINVAL
     assert _code(K, lambda: K.ckks_ct_import_rns(ctx, np.zeros((2, P.L + 2, P.n), dtype=np.uint64), P.L + 1, 1.0)
                  ) == K.CKKS_EINVAL
+    # downsampling depthwise sets (w_in = 8: C = N / 64 channels per input ciphertext)
+    C = P.n // 64
+    dw = K.ckks_ptset_dwconv_fused_s2
+    assert _code(K, lambda: dw(ctx, np.ones((4, 2, 2)), 8, 0, 1, 1.0)) == K.CKKS_EINVAL           # even kernel
+    assert _code(K, lambda: dw(ctx, np.ones((4, 3, 3)), 8, 1, 1, 1.0)) == K.CKKS_EINVAL           # no channel in t = 1
+    assert _code(K, lambda: dw(ctx, np.ones((4 * C + 1, 3, 3)), 8, 0, 1, 1.0)) == K.CKKS_EINVAL   # > 4C outputs
     # still usable: a rotation that has its key is bit-exact against the oracle
     oct_ = o.encrypt(o.encode_pt(z, P.L, P.delta[P.L]), 3)
     assert_ct_equal(K, ctx, K.ckks_rotate_hoisted(ctx, keys, import_ct(K, ctx, oct_), [1])[0], o.rotate(oct_, 1),
