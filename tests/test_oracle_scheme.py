@@ -155,6 +155,35 @@ def test_chebyshev_and_evalmod(small):
     assert np.abs(slots(o, out).real - np.polynomial.chebyshev.chebval(y, coeffs)).max() < 1e-5
 
 
+def test_evalmod_function_is_the_scaled_sine():
+    """EvalMod in FP64 with the bootstrapping configuration's own coefficients (Chebyshev
+    interpolant of cos(2 pi (K_eff y - 1/4) / 2^r), then r double angles c <- 2 c^2 - 1)
+    against sin(2 pi K_eff y) on the intervals where ModRaise puts t / (q0 K_eff): y = (k + u)
+    / K_eff, |k| < K, |u| <= 2^-9 (a message ratio Delta0 / q0 = 2^-11 with |o| up to 4).
+    Then the masks' factor q0 / (2 pi Delta0) returns o up to the sine's cubic term, whose
+    closed form |o| (2 pi u)^2 / 6 bounds the error for |o| <= 1."""
+    from tests.pairs import oracle_params
+    P = oracle_params("cfg2_small")              # the config-2 chain at N = 2^10
+    cfg = BT.BootConfig(Oracle(P, 5), 8, 4, 4)
+    c = np.array(cfg.coeffs)
+    assert len(c) == cfg.deg + 1 and cfg.r == 3 and abs(cfg.K_eff - cfg.K) < 1e-6
+    u = np.linspace(-2.0 ** -9, 2.0 ** -9, 1025)
+    ratio = cfg.delta0 / float(P.q[0])
+    worst = worst_o = 0.0
+    for k in range(-cfg.K + 1, cfg.K):
+        y = (k + u) / cfg.K_eff
+        v = np.polynomial.chebyshev.chebval(y, c)
+        for _ in range(cfg.r):
+            v = 2.0 * v * v - 1.0
+        worst = max(worst, np.abs(v - np.sin(2.0 * np.pi * cfg.K_eff * y)).max())
+        small_o = np.abs(u) <= ratio                      # |o| <= 1
+        o_rec = v[small_o] / (2.0 * np.pi * ratio)        # masks: q0 / (2 pi Delta0)
+        worst_o = max(worst_o, np.abs(o_rec - u[small_o] / ratio).max())
+    assert worst < 1e-11, worst
+    assert worst_o <= (2.0 * np.pi * ratio) ** 2 / 6.0 * 1.01 + 1e-12, worst_o
+    assert worst_o < 2.0 ** -12 / 100
+
+
 @pytest.mark.slow
 def test_block_matches_fp64_conv():
     """Alg. 1 block (no activation) at N = 2^10 with the config-2 prime chain: decoded output
