@@ -238,6 +238,33 @@ def check_accuracy(K, s, out):
 
 
 # ------------------------------------------------------------ oracle arm -----
+_ORACLE_SETUP = {}
+
+
+def _oracle_setup():
+    """The oracle, its keys and the sample's inputs, made once per process: keys and
+    plaintexts are resident in the timed GPU block too, so only the operations are timed."""
+    if "s" not in _ORACLE_SETUP:
+        from oracle import encoding as E
+        from oracle import params as PP
+        from oracle.scheme import Oracle
+        d = WL.PARAMS[CONFIG]
+        spec = WL.CONV[CONFIG]
+        P = PP.Params(d["log_n"], d["n_q"], d["dnum"], d["q0_bits"], d["scale_bits"], d["p_bits"], h=d["h"],
+                      sigma=d["sigma"], n_p=d["n_p"], boot_bits=d["boot_bits"], n_boot=d["n_boot"])
+        o = Oracle(P, 1)
+        w = E.pad_width(spec["w0"], spec["f"])
+        x = WL.image(1, spec["cin"], spec["w0"])
+        W = WL.weights(1, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+        plan = o.conv_plan(W, spec["cin"], spec["cout"], spec["f"], w, 1, (2.0 ** 49 * float(P.q[1])) / P.delta[1])
+        o.gen_rotation_keys(plan.rotations(P.n // 2) + [1])
+        ct = o.encrypt(o.encode_pt(E.cins_input_slots(x, w, P.n), 1, P.delta[1]), 1)
+        hi = o.encrypt(o.encode_pt(WL.slots(2, P.n // 2, 0.5), 19, P.delta[19]), 2)
+        pt = o.encode_pt(WL.slots(3, P.n // 2), 19, P.delta[19])
+        _ORACLE_SETUP["s"] = (o, plan, ct, hi, pt)
+    return _ORACLE_SETUP["s"]
+
+
 def oracle_sample(seconds_budget, counts=None):
     """Time the CPU oracle on a bounded sample of the block and scale it to ms per block.
 
@@ -246,28 +273,12 @@ def oracle_sample(seconds_budget, counts=None):
     estimate is conv + n_keyswitch * t_ks + n_rescale * t_rs + n_pmult * t_pm, with the
     counts of one block (taken from the block's structure: they are properties of the
     algorithm, identical on both implementations)."""
-    from oracle import boot as BT
-    from oracle import encoding as E
-    from oracle import params as PP
-    from oracle.scheme import Oracle
-    d = WL.PARAMS[CONFIG]
-    spec = WL.CONV[CONFIG]
-    P = PP.Params(d["log_n"], d["n_q"], d["dnum"], d["q0_bits"], d["scale_bits"], d["p_bits"], h=d["h"],
-                  sigma=d["sigma"], n_p=d["n_p"], boot_bits=d["boot_bits"], n_boot=d["n_boot"])
-    o = Oracle(P, 1)
-    w = E.pad_width(spec["w0"], spec["f"])
-    x = WL.image(1, spec["cin"], spec["w0"])
-    W = WL.weights(1, spec["cout"], spec["cin"], spec["f"], spec["weight"])
-    plan = o.conv_plan(W, spec["cin"], spec["cout"], spec["f"], w, 1, (2.0 ** 49 * float(P.q[1])) / P.delta[1])
-    o.gen_rotation_keys(plan.rotations(P.n // 2) + [1])
-    ct = o.encrypt(o.encode_pt(E.cins_input_slots(x, w, P.n), 1, P.delta[1]), 1)
+    o, plan, ct, hi, pt = _oracle_setup()
     t0 = time.perf_counter()
     o.conv2d_cins(ct, plan)
     t_conv = time.perf_counter() - t0
-    hi = o.encrypt(o.encode_pt(WL.slots(2, P.n // 2, 0.5), 19, P.delta[19]), 2)
     reps = 0
     t_ks = t_rs = t_pm = 0.0
-    pt = o.encode_pt(WL.slots(3, P.n // 2), 19, P.delta[19])
     start = time.perf_counter()
     while True:
         t0 = time.perf_counter()
