@@ -403,6 +403,25 @@ int ckks_graph_launch(ckks_graph* graph, void* stream);
 int ckks_graph_info(const ckks_graph* graph, int64_t* kernel_launches);
 int ckks_graph_destroy(ckks_graph* graph);
 
+/* ---- batched blocks ------------------------------------------------------------ */
+/* B independent ciphertexts through the same block (conv set, bootstrap configuration):
+ * one ckks_block graph per input (in[i] -> out[i], recorded as ckks_block_graph_create
+ * does, so each input runs once eagerly first), spread round-robin over min(n_streams, B)
+ * CUDA streams the batch owns, so that the small launches of different ciphertexts overlap.
+ * The inputs and outputs must stay alive while the batch exists; each launch re-reads in[]
+ * and overwrites out[].  CKKS_EINVAL for B outside 1..1024, n_streams outside 1..32, an
+ * output that aliases an input or another output; otherwise what ckks_block_graph_create
+ * returns. */
+typedef struct ckks_batch ckks_batch;
+int ckks_block_batch_create(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                            const ckks_ptset* conv, const ckks_boot* bt, ckks_ct* const* out, int n_streams,
+                            ckks_batch** batch);
+/* Launches the B graphs after the work already enqueued on the context's stream; the
+ * context's stream then waits for all of them (so ckks_sync covers the batch).  Asynchronous. */
+int ckks_batch_launch(ckks_batch* batch);
+/* Waits for the context's stream, then frees the graphs, streams and events. */
+int ckks_batch_destroy(ckks_batch* batch);
+
 /* ---- serving loop ----------------------------------------------------------------
  * Continuous batching of inference requests (no counterpart in the paper, whose
  * measurements are one image at a time; a server needs batched throughput).

@@ -155,6 +155,9 @@ _SIGS = {
     "ckks_graph_launch": [VP, VP],
     "ckks_graph_info": [VP, VP],
     "ckks_graph_destroy": [VP],
+    "ckks_block_batch_create": [VP, VP, I, PVP, VP, VP, PVP, I, PVP],
+    "ckks_batch_launch": [VP],
+    "ckks_batch_destroy": [VP],
     "ckks_eval_relu": [VP, VP, VP, VP, VP, I, VP],
     "ckks_rescale_noalloc": [VP, VP, I, VP],
     "ckks_ntt_forward": [VP, VP, I, VP],
@@ -259,6 +262,10 @@ class Boot(_Handle):
 
 class Graph(_Handle):
     _destroy = "ckks_graph_destroy"
+
+
+class Batch(_Handle):
+    _destroy = "ckks_batch_destroy"
 
 
 class Server(_Handle):
@@ -791,6 +798,22 @@ def ckks_block_graph_create(ctx, keys, ct, conv, bt, out) -> Graph:
     gr = Graph(g.value, ctx)
     gr.refs = (keys, ct, conv, bt, out)     # the graph reads and writes these buffers
     return gr
+
+
+def ckks_block_batch_create(ctx, keys, ins, conv, bt, outs, n_streams=8) -> Batch:
+    """one block graph per input (ins[i] -> outs[i]) over n_streams streams of the batch's own"""
+    n = len(ins)
+    assert n == len(outs)
+    b = ctypes.c_void_p()
+    ctx.check(lib().ckks_block_batch_create(ctx, keys, n, _ptrs(ins), conv, bt, _ptrs(outs), n_streams,
+                                            ctypes.byref(b)))
+    bh = Batch(b.value, ctx)
+    bh.refs = (keys, list(ins), conv, bt, list(outs))     # the graphs read and write these buffers
+    return bh
+
+
+def ckks_batch_launch(batch):
+    batch.ctx.check(lib().ckks_batch_launch(batch))
 
 
 def ckks_graph_launch(graph, stream=0):

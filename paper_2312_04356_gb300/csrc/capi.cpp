@@ -1451,6 +1451,89 @@ int ckks_graph_destroy(ckks_graph* g) {
     return CKKS_OK;
 }
 
+// Batched blocks: one recorded block per input, the graphs spread over streams of their own
+// so that independent ciphertexts overlap on the device; fork and join through events on
+// the context's stream.
+struct ckks_batch {
+    ckks_ctx* ctx = nullptr;
+    std::vector<ckks_graph*> graphs;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;      // one per stream
+    cudaEvent_t fork = nullptr;
+    ~ckks_batch() {
+        for (ckks_graph* g : graphs) delete g;
+        for (cudaEvent_t e : done) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        for (cudaStream_t s : streams) cudaStreamDestroy(s);
+    }
+};
+
+int ckks_block_batch_create(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                            const ckks_ptset* conv, const ckks_boot* bt, ckks_ct* const* out, int n_streams,
+                            ckks_batch** batch) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(in);
+        REQ(out);
+        REQ(batch);
+        CK_CHECK(B >= 1 && B <= 1024, CKKS_EINVAL, "batch size must be 1..1024");
+        CK_CHECK(n_streams >= 1 && n_streams <= 32, CKKS_EINVAL, "stream count must be 1..32");
+        for (int i = 0; i < B; ++i) {
+            CT_OK(in[i]);
+            REQ(out[i]);
+            for (int j = 0; j < B; ++j) {
+                CK_CHECK(out[i] != in[j], CKKS_EINVAL, "an output aliases an input of the batch");
+                CK_CHECK(j == i || out[i] != out[j], CKKS_EINVAL, "outputs of the batch must be distinct");
+            }
+        }
+        std::unique_ptr<ckks_batch> b(new ckks_batch);
+        b->ctx = ctx;
+        for (int i = 0; i < B; ++i) {
+            ckks_graph* g = nullptr;
+            const int st = ckks_block_graph_create(ctx, keys, in[i], conv, bt, out[i], &g);
+            if (st != CKKS_OK) CK_THROW(st, ctx->err);
+            b->graphs.push_back(g);
+        }
+        const int S = std::min(n_streams, B);
+        for (int k = 0; k < S; ++k) {
+            cudaStream_t s = nullptr;
+            CUDA_CHECK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            b->streams.push_back(s);
+            cudaEvent_t e = nullptr;
+            CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            b->done.push_back(e);
+        }
+        CUDA_CHECK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        *batch = b.release();
+    });
+}
+
+int ckks_batch_launch(ckks_batch* b) {
+    if (!b) return CKKS_EINVAL;
+    return guard(b->ctx, [&] {
+        ckks_ctx* c = b->ctx;
+        const size_t S = b->streams.size();
+        CUDA_CHECK(cudaEventRecord(b->fork, c->stream));
+        for (cudaStream_t s : b->streams) CUDA_CHECK(cudaStreamWaitEvent(s, b->fork, 0));
+        for (size_t i = 0; i < b->graphs.size(); ++i) {
+            CUDA_CHECK(cudaGraphLaunch(b->graphs[i]->exec, b->streams[i % S]));
+            c->launches += b->graphs[i]->launches;
+        }
+        for (size_t k = 0; k < S; ++k) {
+            CUDA_CHECK(cudaEventRecord(b->done[k], b->streams[k]));
+            CUDA_CHECK(cudaStreamWaitEvent(c->stream, b->done[k], 0));
+        }
+    });
+}
+
+int ckks_batch_destroy(ckks_batch* b) {
+    if (b) {
+        cudaStreamSynchronize(b->ctx->stream);     // the graphs may still run
+        delete b;
+    }
+    return CKKS_OK;
+}
+
 int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, int deg, int basis,
                    double a, double b, ckks_ct* out) {
     return guard(ctx, [&] {

@@ -165,3 +165,26 @@ def test_faults_leave_the_loop_serving(env):
         K.ckks_server_add_model(tiny, [env["conv"]], [env["bt"]])
     assert ei.value.code == K.CKKS_ENOMEM
     tiny.close()
+
+
+def test_block_batch_equals_blocks_alone(env):
+    """ckks_block_batch_create / ckks_batch_launch: 5 inputs round-robin over 2 streams,
+    launched twice; every output equals the eager block of its input; an output that aliases
+    an input is refused before anything is recorded"""
+    K, ctx = env["K"], env["ctx"]
+    ins, want = [], []
+    for i in range(5):
+        _, limbs = env["make_input"](300 + i)
+        ins.append(K.ckks_ct_import_rns(ctx, limbs, 1, env["delta"][1]))
+        want.append(env["eager"](limbs, 1))
+    outs = [K.ckks_ct_create(ctx) for _ in ins]
+    with pytest.raises(K.CkksError) as ei:
+        K.ckks_block_batch_create(ctx, env["keys"], ins, env["conv"], env["bt"], [ins[0]] + outs[1:], 2)
+    assert ei.value.code == K.CKKS_EINVAL
+    batch = K.ckks_block_batch_create(ctx, env["keys"], ins, env["conv"], env["bt"], outs, 2)
+    for _ in range(2):
+        K.ckks_batch_launch(batch)
+        K.ckks_sync(ctx)
+        for o, w in zip(outs, want):
+            assert (K.ckks_ct_export_rns(ctx, o) == w).all()
+    batch.close()
