@@ -45,3 +45,13 @@ def test_oracle_and_library_share_no_code():
             text = open(f).read()
             assert not re.search(r"^\s*(import|from)\s+paper_2312_04356_gb300", text, flags=re.M), f
             assert "libckks_gb300" not in text and "#include" not in text.replace("#include <", ""), f
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_is_plain_c(lang, std):
+    """include/ckks.h compiles on its own as pedantic C99 and as C++17 (no torch or CUDA
+    types in the signatures; checked for syntax only, nothing is written)"""
+    cc = "gcc" if lang == "c" else "g++"
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang,
+                        os.path.join(ROOT, "include", "ckks.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
