@@ -32,3 +32,23 @@ def test_dram_ratios_from_captures():
     assert math.isclose(bench.NTT_FWD_DRAM_PER_ALGO_BYTE, 491.3 / 268.4, rel_tol=1e-3)
     assert math.isclose(bench.KS_DRAM_PER_ALGO_BYTE, 149.9 / (365 * 0.524288), rel_tol=1e-3)
     assert 1.0 < bench.NTT_FWD_DRAM_PER_ALGO_BYTE < 2.0 and 0.5 < bench.KS_DRAM_PER_ALGO_BYTE < 1.0
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the oracle on the host, no GPU needed) prints one JSON
+    line with the keys the bench contract asks of that arm"""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["higher_is_better"] is False and line["unit"] == "ms"
+    assert line["value"] > 0 and line["metric"] == bench.METRIC
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
