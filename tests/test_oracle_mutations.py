@@ -1,0 +1,73 @@
+"""Mistakes planted in the oracle, on the CPU: each is a plausible slip in one step, and the
+pin of that step must fail on it (while the same pin passes on a correct restatement), so
+the pins would notice such a slip in the oracle itself."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import _clib as C
+from oracle import params as PP
+from oracle.scheme import Oracle
+from tests import test_oracle_arith as A
+from tests import test_oracle_scheme as S
+
+
+def _rescale_py(c, q, centred):
+    """(c_i - r) q_l^{-1} mod q_i, r the remainder of the top limb, centred or in [0, q_l)"""
+    c = np.asarray(c, dtype=np.uint64)
+    l = c.shape[0] - 1
+    ql = int(q[l])
+    out = np.empty((l, c.shape[1]), dtype=np.uint64)
+    for i in range(l):
+        qi = int(q[i])
+        inv = pow(ql, -1, qi)
+        row = []
+        for a, t in zip(c[i], c[l]):
+            r = int(t) - ql if centred and int(t) > ql // 2 else int(t)
+            row.append(((int(a) - r) * inv) % qi)
+        out[i] = row
+    return out
+
+
+def _base_convert_py(x, qin, qout, terms):
+    """sum over the first `terms` inputs of [x_i qhat_i^{-1}]_{q_i} qhat_i, mod each output"""
+    x = np.asarray(x, dtype=np.uint64)
+    Q = math.prod(int(v) for v in qin)
+    out = np.zeros((len(qout), x.shape[1]), dtype=np.uint64)
+    for m, p in enumerate(qout):
+        for j in range(x.shape[1]):
+            s = 0
+            for i in range(terms):
+                qh = Q // int(qin[i])
+                s += (int(x[i, j]) * pow(qh, -1, int(qin[i])) % int(qin[i])) * qh
+            out[m, j] = s % int(p)
+    return out
+
+
+def test_uncentred_rescale_fails_its_pin(monkeypatch):
+    monkeypatch.setattr(C, "rescale", lambda c, q: _rescale_py(c, q, centred=True))
+    A.test_rescale_is_rounded_division()                         # correct restatement passes
+    monkeypatch.setattr(C, "rescale", lambda c, q: _rescale_py(c, q, centred=False))
+    with pytest.raises(AssertionError):
+        A.test_rescale_is_rounded_division()
+
+
+def test_base_conversion_with_a_dropped_term_fails_its_pin(monkeypatch):
+    monkeypatch.setattr(C, "base_convert", lambda x, qi, qo: _base_convert_py(x, qi, qo, len(qi)))
+    A.test_base_convert_is_crt_plus_small_multiple()             # correct restatement passes
+    monkeypatch.setattr(C, "base_convert", lambda x, qi, qo: _base_convert_py(x, qi, qo, len(qi) - 1))
+    with pytest.raises(AssertionError):
+        A.test_base_convert_is_crt_plus_small_multiple()
+
+
+def test_rotation_in_the_wrong_direction_fails_its_pin(monkeypatch):
+    """Galois element 5^{-r} instead of 5^r (keys generated for the same wrong elements, so
+    everything decrypts): the slot-roll pin sees the wrong direction"""
+    monkeypatch.setattr(Oracle, "galois", lambda self, r: pow(5, (-r) % (self.P.n // 2), 2 * self.P.n))
+    o = Oracle(PP.Params(9, 6, 3, 60, 40, 60, h=32), 42)
+    o.gen_relin_key()
+    o.gen_conj_key()
+    o.gen_rotation_keys([1, 3, 7, 100])
+    with pytest.raises(AssertionError):
+        S.test_rotation_conjugation_product(o)
