@@ -71,3 +71,21 @@ def test_rotation_in_the_wrong_direction_fails_its_pin(monkeypatch):
     o.gen_rotation_keys([1, 3, 7, 100])
     with pytest.raises(AssertionError):
         S.test_rotation_conjugation_product(o)
+
+
+def test_ntt_with_the_inverse_root_or_natural_order_fails_its_pin(monkeypatch):
+    """psi^{-1} for psi evaluates at the same set of odd powers, only permuted; an output in
+    natural instead of bit-reversed order is the same values permuted too: the pin checks
+    each output position"""
+    real = C.ntt_forward
+    logn = 5
+    rev = np.array([int(format(i, "05b")[::-1], 2) for i in range(1 << logn)])
+    monkeypatch.setattr(C, "ntt_forward", lambda a, q, psi, lg: real(
+        a, q, [pow(int(p), -1, int(m)) for p, m in zip(psi, q)], lg))
+    with pytest.raises(AssertionError):
+        A.test_ntt_is_evaluation_at_odd_roots(logn)
+    monkeypatch.setattr(C, "ntt_forward", lambda a, q, psi, lg: real(a, q, psi, lg)[:, rev])
+    with pytest.raises(AssertionError):
+        A.test_ntt_is_evaluation_at_odd_roots(logn)
+    monkeypatch.setattr(C, "ntt_forward", real)
+    A.test_ntt_is_evaluation_at_odd_roots(logn)
