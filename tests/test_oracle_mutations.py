@@ -89,3 +89,33 @@ def test_ntt_with_the_inverse_root_or_natural_order_fails_its_pin(monkeypatch):
         A.test_ntt_is_evaluation_at_odd_roots(logn)
     monkeypatch.setattr(C, "ntt_forward", real)
     A.test_ntt_is_evaluation_at_odd_roots(logn)
+
+
+def _kernel_vector_py(K, w, flip_offsets=False, wrap_sign=-1.0):
+    """Fig. 1 kernel vector; flip_offsets turns the cross-correlation into a convolution,
+    wrap_sign = +1 forgets the sign of a tap that wraps around Y^{w^2} + 1"""
+    f = K.shape[0]
+    c = f // 2
+    n = w * w
+    v = np.zeros(n)
+    for a in range(f):
+        for b in range(f):
+            q = -((a - c) * w + (b - c))
+            if flip_offsets:
+                q = -q
+            if q >= 0:
+                v[q] += K[a, b]
+            else:
+                v[n + q] += wrap_sign * K[a, b]
+    return v
+
+
+def test_conv_kernel_vector_slips_fail_their_pin(monkeypatch):
+    from oracle import encoding as E
+    from tests import test_oracle_encoding as EN
+    monkeypatch.setattr(E, "kernel_vector", lambda K, w: _kernel_vector_py(K, w))
+    EN.test_conv2d_as_negacyclic_convolution()                   # correct restatement passes
+    for slip in (dict(flip_offsets=True), dict(wrap_sign=1.0)):
+        monkeypatch.setattr(E, "kernel_vector", lambda K, w, s=slip: _kernel_vector_py(K, w, **s))
+        with pytest.raises(AssertionError):
+            EN.test_conv2d_as_negacyclic_convolution()
