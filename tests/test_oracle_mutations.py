@@ -119,3 +119,13 @@ def test_conv_kernel_vector_slips_fail_their_pin(monkeypatch):
         monkeypatch.setattr(E, "kernel_vector", lambda K, w, s=slip: _kernel_vector_py(K, w, **s))
         with pytest.raises(AssertionError):
             EN.test_conv2d_as_negacyclic_convolution()
+
+
+def test_dft_twiddle_root_slip_fails_its_pin(monkeypatch):
+    """W_k of the block B_k with omega_{4k} (Eq. 2's subscript copied to the block size) in
+    place of omega_{8k}: the recursive factorisation no longer rebuilds T = V P"""
+    from oracle import encoding as E
+    from tests import test_oracle_encoding as EN
+    monkeypatch.setattr(E, "W_diag", lambda k: np.array([E.omega(4 * k, pow(5, i, 4 * k)) for i in range(k)]))
+    with pytest.raises(AssertionError):
+        EN.test_special_dft_factorisation(16)
