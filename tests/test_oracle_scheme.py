@@ -69,6 +69,30 @@ def test_rotation_conjugation_product(small):
     assert np.abs(slots(o, c) - (z + 0.75)).max() < 1e-6
 
 
+def test_theorem1_under_encryption(small):
+    """Theorem 1 / Eq. 5 homomorphically: the folded slices P_l m_i in slot encoding, taken
+    through S_{l<-1} as the StoC1 BSGS levels under encryption, decrypt to the direct
+    real-CinS encoding of the slices (the partial DFT of slot encoding is CinS)"""
+    o = small
+    P = o.P
+    n, m = P.n, P.n // 2
+    ell = 8
+    C = m // ell
+    sl = 0.5 * rng.normal(size=(C, 2 * ell))
+    z = np.kron(np.eye(C), E.P_matrix(ell)) @ np.concatenate([E.fold(v) for v in sl])
+    assert np.abs(z - E.real_cins_slots(sl)).max() > 0.1              # the map is not trivial
+    lev = P.L
+    ct = o.encrypt(o.encode_pt(z, lev, P.delta[lev]), 8)
+    for D, strides in E.stoc1_groups(n, ell, 2):
+        a0, step, count = E.ap_of_group(strides, m)
+        plan = o.make_plan(D, a0, step, count, lev, float(P.q[lev]))
+        o.gen_rotation_keys(plan.rotations(m))
+        ct = o.rescale(o.bsgs(ct, plan))
+        lev -= 1
+    assert ct.level == P.L - 2
+    assert np.abs(slots(o, ct) - E.real_cins_slots(sl)).max() < 1e-5
+
+
 def test_mod_raise_overflow_is_small_multiple_of_q0(small):
     o = small
     m = o.P.n // 2
