@@ -297,7 +297,8 @@ def oracle_sample(seconds_budget, counts=None):
     t_ks, t_rs, t_pm = t_ks / reps, t_rs / reps, t_pm / reps
     counts = counts or block_op_counts()
     est = t_conv + counts["keyswitch"] * t_ks + counts["rescale"] * t_rs + counts["pmult"] * t_pm
-    cores = os.cpu_count()
+    from oracle import _clib
+    cores = _clib.max_threads()            # threads of the oracle's OpenMP loops over limbs
     sample = ("oracle at N=2^16, config-2 chain: fused conv at level 1 (%.2f s) + %d x [1 key switch, 1 rescale, "
               "1 PMult] at level 19 (%.2f / %.3f / %.3f s each); ms per block = conv + %d keyswitch + %d rescale + "
               "%d PMult" % (t_conv, reps, t_ks, t_rs, t_pm, counts["keyswitch"], counts["rescale"], counts["pmult"]))

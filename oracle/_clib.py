@@ -53,6 +53,7 @@ def lib():
         sig = {
             "orc_pow_mod": (u64, [u64, u64, u64]),
             "orc_mul_mod": (u64, [u64, u64, u64]),
+            "orc_max_threads": (c_int, []),
             "orc_ntt_naive": (None, [U64P, U64P, c_int, u64, u64]),
             "orc_ntt_forward": (None, [U64P, c_int, c_int, U64P, U64P]),
             "orc_ntt_inverse": (None, [U64P, c_int, c_int, U64P, U64P]),
@@ -237,6 +238,11 @@ def sample_gauss(n, sigma, seed, tag):
     out = np.empty(n, dtype=np.int64)
     lib().orc_sample_gauss(out, n, sigma, seed, tag)
     return out
+
+
+def max_threads():
+    """threads of the oracle's OpenMP loops"""
+    return int(lib().orc_max_threads())
 
 
 def splitmix_mix(z):

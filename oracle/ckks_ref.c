@@ -19,10 +19,22 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef uint64_t u64;
 typedef int64_t i64;
 typedef unsigned __int128 u128;
+
+/* threads the OpenMP loops over limbs use (1 without OpenMP) */
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ */
 /* scalar modular arithmetic (q < 2^62)                                */
