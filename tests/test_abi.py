@@ -55,3 +55,19 @@ def test_header_is_plain_c(lang, std):
     r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang,
                         os.path.join(ROOT, "include", "ckks.h")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_binding_argument_counts_match_the_header():
+    """every ctypes signature of the binding has as many arguments as the C declaration"""
+    from paper_2312_04356_gb300 import ckks
+    src = open(os.path.join(ROOT, "include", "ckks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = re.findall(r"^\s*(?:int|const char\*)\s+(ckks_\w+)\s*\(([^;]*?)\)\s*;", src, flags=re.M | re.S)
+    assert len(decls) == len(declared())
+    bad = []
+    for name, params in decls:
+        params = " ".join(params.split())
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        if name in ckks._SIGS and len(ckks._SIGS[name]) != n:
+            bad.append((name, n, len(ckks._SIGS[name])))
+    assert not bad, bad
