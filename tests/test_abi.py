@@ -71,3 +71,34 @@ def test_binding_argument_counts_match_the_header():
         if name in ckks._SIGS and len(ckks._SIGS[name]) != n:
             bad.append((name, n, len(ckks._SIGS[name])))
     assert not bad, bad
+
+
+def _kind_c(param):
+    if "*" in param:
+        return "ptr"
+    t = param.strip().rsplit(" ", 1)[0].replace("const ", "").strip()
+    return {"int": "i32", "int32_t": "i32", "double": "f64", "uint64_t": "u64", "int64_t": "i64"}.get(t, t)
+
+
+def _kind_py(t):
+    import ctypes
+    if t is ctypes.c_void_p or t is ctypes.c_char_p or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int: "i32", ctypes.c_double: "f64", ctypes.c_uint64: "u64", ctypes.c_int64: "i64"}.get(t, str(t))
+
+
+def test_binding_argument_types_match_the_header():
+    """pointer, int, double and 64-bit integer positions agree between each C declaration
+    and its ctypes signature (a swapped int / double would pass garbage, not fail)"""
+    from paper_2312_04356_gb300 import ckks
+    src = open(os.path.join(ROOT, "include", "ckks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = re.findall(r"^\s*(?:int|const char\*)\s+(ckks_\w+)\s*\(([^;]*?)\)\s*;", src, flags=re.M | re.S)
+    bad = []
+    for name, params in decls:
+        params = " ".join(params.split())
+        ps = [] if params in ("", "void") else params.split(",")
+        for i, (p, t) in enumerate(zip(ps, ckks._SIGS.get(name, []))):
+            if _kind_c(p) != _kind_py(t):
+                bad.append((name, i, p.strip(), _kind_c(p), _kind_py(t)))
+    assert not bad, bad
