@@ -13,6 +13,8 @@ Modules
   encoding.py  FP64 encodings, special DFT factors, real CinS, conv kernels
   scheme.py    keys, encryption, key switching, rotations, BSGS, Chebyshev evaluation
   boot.py      Alg. 1 block: fused conv, ModRaise, CtoS, EvalMod, mask, StoC1
+  plain.py     the same steps without the key-switch restructurings (a ModDown per
+               rotation, separate rescales, term-by-term Chebyshev series), to pin them
 
 Parity status: every function is pinned by tests/test_oracle_*.py against a
 value or identity the paper or the mathematics fixes (see the test docstrings).

@@ -129,3 +129,73 @@ def test_dft_twiddle_root_slip_fails_its_pin(monkeypatch):
     monkeypatch.setattr(E, "W_diag", lambda k: np.array([E.omega(4 * k, pow(5, i, 4 * k)) for i in range(k)]))
     with pytest.raises(AssertionError):
         EN.test_special_dft_factorisation(16)
+
+
+def _div_round_py(self, acc, level, S, mode="centred"):
+    """(a - r) M^{-1} mod q_i over the first `level` Q rows, M = prod S, r the remainder of a
+    mod M by exact CRT: centred (the rounding), in [0, M) (a floor), or centred plus one unit"""
+    M = math.prod(int(m) for m in S)
+    out = np.empty((level, acc.shape[1]), dtype=np.uint64)
+    for j in range(acc.shape[1]):
+        r = 0
+        for k, mk in enumerate(S):
+            mk = int(mk)
+            r += int(acc[level + k, j]) * pow((M // mk) % mk, -1, mk) * (M // mk)
+        r %= M
+        if mode != "floor" and r > M // 2:
+            r -= M
+        for i in range(level):
+            qi = int(self.P.q[i])
+            v = (int(acc[i, j]) - r) * pow(M % qi, -1, qi)
+            if mode == "plus_one":
+                v += 1
+            out[i, j] = v % qi
+    return out
+
+
+def test_fused_rescale_slips_fail_their_pin(monkeypatch):
+    """ModDown fused with the rescale taking the floor (remainder in [0, q_l P)) instead of the
+    rounding, or landing one unit off: the rounded-division pin fails on both"""
+    from tests import test_oracle_plain as PLT
+    monkeypatch.setattr(Oracle, "_div_round", lambda self, a, l, S: _div_round_py(self, a, l, S))
+    PLT.test_mod_down_rescale_is_rounded_division(2)             # correct restatement passes
+    for mode in ("floor", "plus_one"):
+        monkeypatch.setattr(Oracle, "_div_round", lambda self, a, l, S, m=mode: _div_round_py(self, a, l, S, m))
+        with pytest.raises(AssertionError):
+            PLT.test_mod_down_rescale_is_rounded_division(2)
+
+
+def test_chebyshev_leaf_with_a_dropped_term_fails_its_pin(monkeypatch):
+    """a Chebyshev leaf that forgets its highest term: the series pin against the plain
+    term-by-term evaluation fails"""
+    from tests import test_oracle_plain as PLT
+    real = Oracle.cheb_leaf
+
+    def dropped(self, T, at, coeffs):
+        c = list(coeffs)
+        for k in range(len(c) - 1, 0, -1):
+            if c[k] != 0.0:
+                c[k] = 0.0
+                break
+        return real(self, T, at, c)
+    monkeypatch.setattr(Oracle, "cheb_leaf", dropped)
+    with pytest.raises(AssertionError):
+        PLT.test_cheb_eval_matches_plain()
+
+
+def test_baby_rotation_without_the_p_lift_fails_its_pin(monkeypatch):
+    """the double-hoisted baby rotation adding automorph(c0) without the factor P: the BSGS
+    pin against the plain HMatmul fails"""
+    from tests import test_oracle_plain as PLT
+    monkeypatch.setattr(Oracle, "lift_p", lambda self, acc, x, level: _lift_unscaled(self, acc, x, level))
+    o = Oracle(PP.Params(9, 6, 3, 60, 40, 60, h=32), 77)
+    o.gen_relin_key()
+    with pytest.raises(AssertionError):
+        PLT.test_bsgs_double_hoisted_matches_plain(o)
+
+
+def _lift_unscaled(self, acc, x, level):
+    q = self.P.moduli(level)
+    out = acc.copy()
+    out[: level + 1] = C.add(acc[: level + 1], x, q)
+    return out
