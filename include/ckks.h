@@ -40,6 +40,7 @@
 #ifndef CKKS_GB300_H
 #define CKKS_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -98,6 +99,33 @@ int ckks_sync(ckks_ctx* ctx);
 int ckks_ctx_info(const ckks_ctx* ctx, uint64_t* q, uint64_t* p, uint64_t* psi, double* delta);
 /* The 39-entry cumulative table of the Gaussian sampler (entry k: values <= k - 19). */
 int ckks_ctx_gauss_table(const ckks_ctx* ctx, uint64_t* table39);
+
+/* ---- device memory -------------------------------------------------------- */
+/* A caller-provided device allocator: alloc(user, bytes, cuda_stream) returns device memory
+ * (16-byte aligned; NULL = out of memory) for work enqueued on cuda_stream;
+ * free(user, ptr, bytes, cuda_stream) gives it back when the library has enqueued its last
+ * use on that stream, so the allocator may hand it out again for later work on the same
+ * stream without waiting (the contract of a stream-ordered caching allocator such as
+ * PyTorch's).  The callbacks run on the calling host thread and must not call this library. */
+typedef void* (*ckks_alloc_fn)(void* user, size_t bytes, void* cuda_stream);
+typedef void (*ckks_free_fn)(void* user, void* ptr, size_t bytes, void* cuda_stream);
+/* Device memory of this context's later calls (ciphertexts, plaintexts, keys, temporaries)
+ * comes from alloc / free_fn (both NULL: the library's default, stream-ordered cudaMallocAsync
+ * on the device's default memory pool, whose release threshold it raises so the pool
+ * caches).  With a caller allocator every call keeps all of its work on the context's stream
+ * (no side streams, see ckks_ctx_set_side_streams).  Memory of work recorded into a CUDA
+ * graph (ckks_*_graph_create, ckks_block_batch_create, the serving runtime) still comes from
+ * the stream-ordered pool: it must live as long as the graph.  The constant tables built by
+ * ckks_ctx_create come from cudaMalloc.  A buffer is freed through the allocator that
+ * provided it, so the allocator may be changed at any time; `user` is passed back unchanged
+ * and must stay valid while buffers from it are alive.
+ * Errors: CKKS_EINVAL (only one of alloc / free_fn given). */
+int ckks_ctx_set_allocator(ckks_ctx* ctx, ckks_alloc_fn alloc, ckks_free_fn free_fn, void* user);
+/* Usage of the device's default memory pool (the library's default allocator): stats4 =
+ * bytes in use now, the most in use since the last reset, bytes reserved now, the most
+ * reserved since the last reset.  reset_high != 0 first resets both high-water marks to the
+ * current values.  Synchronises the context's stream. */
+int ckks_ctx_pool_stats(ckks_ctx* ctx, int reset_high, uint64_t* stats4);
 
 /* ---- measurement (the paper's per-phase breakdown, Table 2) ---------------- */
 /* Switch per-kernel CUDA-event timing on or off (off by default).  While on, every
@@ -513,7 +541,8 @@ int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, cons
  * rejected with CKKS_EINVAL.  No cudaMalloc / cudaFree (or any allocating routine) is
  * called; per-kernel timing is suspended during the call.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device current: make that
- * first call before any stream capture.  Every call shares the array and leaves its
+ * first call before any stream capture (a first call on a capturing stream returns
+ * CKKS_EINVAL).  Every call shares the array and leaves its
  * contents behind; nothing in it needs to start at zero (each word is written before it is
  * read), but calls that overlap on the GPU (other streams, other contexts on the same
  * device) race on it. */

@@ -56,6 +56,8 @@ I64 = ctypes.c_int64
 _SIGS = {
     "ckks_ctx_create": [ctypes.POINTER(ckks_params), U64, VP, PVP],
     "ckks_ctx_destroy": [VP],
+    "ckks_ctx_set_allocator": [VP, VP, VP, VP],
+    "ckks_ctx_pool_stats": [VP, I, VP],
     "ckks_sync": [VP],
     "ckks_ctx_info": [VP, VP, VP, VP, VP],
     "ckks_ctx_gauss_table": [VP, VP],
@@ -323,6 +325,48 @@ def ckks_ctx_set_ntt_choices(ctx, choice8):
     a = np.ascontiguousarray(choice8, dtype=np.int32)
     assert a.size == 8
     ctx.check(lib().ckks_ctx_set_ntt_choices(ctx, _ptr(a)))
+
+
+# caller allocator callbacks: alloc(user, bytes, stream) -> device pointer; free(user, ptr, bytes, stream)
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+def ckks_ctx_set_allocator(ctx, alloc=None, free=None):
+    """alloc(nbytes, stream) -> int device pointer (0 = out of memory), free(ptr, nbytes, stream);
+    both None restores the library's stream-ordered pool.  The callback objects stay referenced
+    by the context for its lifetime (buffers free through the allocator that made them)."""
+    if (alloc is None) != (free is None):
+        raise ValueError("give both alloc and free, or neither")
+    if alloc is None:
+        ctx.check(lib().ckks_ctx_set_allocator(ctx, None, None, None))
+        return
+    a = _ALLOC_FN(lambda user, nbytes, stream: alloc(nbytes, stream or 0) or None)
+    f = _FREE_FN(lambda user, ptr, nbytes, stream: free(ptr, nbytes, stream or 0))
+    if not hasattr(ctx, "_allocators"):
+        ctx._allocators = []
+    ctx._allocators.append((a, f))
+    ctx.check(lib().ckks_ctx_set_allocator(ctx, ctypes.cast(a, VP), ctypes.cast(f, VP), None))
+
+
+def torch_allocator(device=None):
+    """(alloc, free) callbacks for ckks_ctx_set_allocator that serve the library from PyTorch's
+    caching allocator on the stream the library names"""
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, dev, stream)
+
+    def free(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+    return alloc, free
+
+
+def ckks_ctx_pool_stats(ctx, reset_high=False):
+    a = np.zeros(4, dtype=np.uint64)
+    ctx.check(lib().ckks_ctx_pool_stats(ctx, int(reset_high), _ptr(a)))
+    return dict(zip(["used", "used_high", "reserved", "reserved_high"], [int(x) for x in a]))
 
 
 def ckks_ctx_set_side_streams(ctx, on):

@@ -14,9 +14,18 @@ using namespace hostmath;
 
 namespace {
 
+// Puts the calling context's allocator in place for the call (DevBufs made during it take
+// their memory from it) and restores the previous one afterwards, also on an exception.
+struct AllocScope {
+    const DevAlloc* prev;
+    explicit AllocScope(const ckks_ctx* c) : prev(tl_alloc) { tl_alloc = c && c->alloc.alloc ? &c->alloc : nullptr; }
+    ~AllocScope() { tl_alloc = prev; }
+};
+
 template <class F>
 int guard(const ckks_ctx* c, F&& f) {
     try {
+        AllocScope scope(c);
         f();
         return CKKS_OK;
     } catch (const CkksError& e) {
@@ -215,6 +224,40 @@ int ckks_ctx_set_pdl(ckks_ctx* ctx, int on) {
     return guard(ctx, [&] {
         REQ(ctx);
         ctx->pdl = on != 0;
+    });
+}
+
+int ckks_ctx_set_allocator(ckks_ctx* ctx, ckks_alloc_fn alloc, ckks_free_fn free_fn, void* user) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        CK_CHECK((alloc == nullptr) == (free_fn == nullptr), CKKS_EINVAL, "give both alloc and free_fn, or neither");
+        ctx->alloc.alloc = alloc;
+        ctx->alloc.free = free_fn;
+        ctx->alloc.user = alloc ? user : nullptr;
+    });
+}
+
+int ckks_ctx_pool_stats(ckks_ctx* ctx, int reset_high, uint64_t* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(out);
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        int dev = 0;
+        CUDA_CHECK(cudaGetDevice(&dev));
+        cudaMemPool_t pool;
+        CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, dev));
+        if (reset_high) {
+            uint64_t zero = 0;
+            CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+            CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &zero));
+        }
+        const cudaMemPoolAttr attrs[4] = {cudaMemPoolAttrUsedMemCurrent, cudaMemPoolAttrUsedMemHigh,
+                                          cudaMemPoolAttrReservedMemCurrent, cudaMemPoolAttrReservedMemHigh};
+        for (int k = 0; k < 4; ++k) {
+            uint64_t v = 0;
+            CUDA_CHECK(cudaMemPoolGetAttribute(pool, attrs[k], &v));
+            out[k] = v;
+        }
     });
 }
 

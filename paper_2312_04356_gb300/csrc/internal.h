@@ -56,11 +56,26 @@ struct ConvTab {
     u64* d_corr = nullptr;
 };
 
-// Device buffer owned by RAII (stream-ordered allocation on the context's stream).
+// A caller-provided device allocator (ckks_ctx_set_allocator); both null = the library's own
+// stream-ordered pool (cudaMallocAsync on the device's default memory pool).
+struct DevAlloc {
+    ckks_alloc_fn alloc = nullptr;
+    ckks_free_fn free = nullptr;
+    void* user = nullptr;
+};
+// The allocator of the context whose C-ABI call is running on this thread (set by that call's
+// guard, null outside calls).  DevBufs made during the call take their memory from it, except
+// while their stream is being captured into a CUDA graph (graph memory must live as long as
+// the graph, so it comes from the stream-ordered pool).
+extern thread_local const DevAlloc* tl_alloc;
+
+// Device buffer owned by RAII: stream-ordered allocation on the context's stream, from the
+// caller's allocator when one is set (the buffer remembers which, and frees through it).
 struct DevBuf {
     u64* ptr = nullptr;
     size_t words = 0;
     cudaStream_t stream = 0;
+    DevAlloc al;          // non-null alloc: allocated by this caller allocator
     DevBuf() {}
     DevBuf(size_t w, cudaStream_t s);
     ~DevBuf();
@@ -88,6 +103,11 @@ struct ckks_ctx {
     cudaStream_t side[NSIDE] = {};
     cudaEvent_t fork_ev = nullptr, side_ev[NSIDE] = {};
     bool side_streams_on = true;
+    DevAlloc alloc;       // caller allocator for the buffers of this context's calls
+    // side streams are used only without a caller allocator: a stream-ordered caching
+    // allocator (PyTorch's) reuses a freed block on the stream it was allocated on, so every
+    // buffer must be used on that one stream
+    bool use_side_streams() const { return side_streams_on && alloc.alloc == nullptr; }
     DevPrime* d_primes = nullptr;
     u64* d_tables = nullptr;
     u64* d_gauss = nullptr;

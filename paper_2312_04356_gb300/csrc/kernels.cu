@@ -49,7 +49,22 @@ static inline void klaunch(const ckks_ctx* c, void (*k)(P...), dim3 grid, dim3 b
 }
 
 // ------------------------------------------------------------ DevBuf -------
+thread_local const DevAlloc* tl_alloc = nullptr;
+
 DevBuf::DevBuf(size_t w, cudaStream_t s) : words(w), stream(s) {
+    if (w && tl_alloc && tl_alloc->alloc) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CUDA_CHECK(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            void* p = tl_alloc->alloc(tl_alloc->user, w * sizeof(u64), (void*)s);
+            CK_CHECK(p != nullptr, CKKS_ENOMEM, "the caller's device allocator returned NULL");
+            CK_CHECK(((uintptr_t)p & 15) == 0, CKKS_EINVAL, "the caller's device allocator returned a pointer "
+                                                            "that is not 16-byte aligned");
+            ptr = (u64*)p;
+            al = *tl_alloc;
+            return;
+        }
+    }
     if (w) {
         cudaError_t e = cudaMallocAsync((void**)&ptr, w * sizeof(u64), s);
         if (e != cudaSuccess) {
@@ -65,15 +80,23 @@ DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
         ptr = o.ptr;
         words = o.words;
         stream = o.stream;
+        al = o.al;
         o.ptr = nullptr;
         o.words = 0;
+        o.al = DevAlloc();
     }
     return *this;
 }
 void DevBuf::reset() {
-    if (ptr) cudaFreeAsync(ptr, stream);
+    if (ptr) {
+        if (al.free)
+            al.free(al.user, ptr, words * sizeof(u64), (void*)stream);
+        else if (!al.alloc)
+            cudaFreeAsync(ptr, stream);
+    }
     ptr = nullptr;
     words = 0;
+    al = DevAlloc();
 }
 
 static cudaEvent_t take_event(const ckks_ctx* c) {

@@ -907,7 +907,7 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
         const long long R = (((long long)p0.a0 + (long long)p0.step * kv.first * p0.B) % m + m) % m;
         if (R) rot_giants.emplace_back(R, kv.second.ptr);
     }
-    if (c->side_streams_on && rot_giants.size() >= 2) {
+    if (c->use_side_streams() && rot_giants.size() >= 2) {
         ensure_side_streams(c);
         std::vector<DevBuf> sums;
         for (size_t k = 0; k < rot_giants.size(); ++k) sums.emplace_back(2 * next * n, c->stream);
@@ -1180,7 +1180,7 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
                 if (kv.second == g && !pw.T.count(kv.first)) ks.push_back(kv.first);
             if (ks.empty()) continue;
             for (int k : ks) pw.warm(k);
-            if (!cx->side_streams_on || ks.size() < 2) {
+            if (!cx->use_side_streams() || ks.size() < 2) {
                 for (int k : ks) pw.T[k] = pw.product(k);
                 continue;
             }
@@ -1205,7 +1205,7 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
             if (c[k] != 0.0) pw.at(k, lev);
     }
     std::vector<PolyVal> leaf_vals(leaves.size());
-    if (cx->side_streams_on && leaves.size() >= 2) {
+    if (cx->use_side_streams() && leaves.size() >= 2) {
         const cudaStream_t main_stream = cx->stream;
         int nside = 0;
         {
@@ -1296,7 +1296,7 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
             if (nodes[i].leaf < 0 && nodes[i].height == h) ids.push_back(i);
         for (int i : ids)
             if (!nodes[nodes[i].q].val.is_const) pw.at(nodes[i].n, prod_lev(nodes[i]));
-        if (!cx->side_streams_on || ids.size() < 2) {
+        if (!cx->use_side_streams() || ids.size() < 2) {
             for (int i : ids) nodes[i].val = combine(nodes[i]);
         } else {
             ensure_side_streams(cx);

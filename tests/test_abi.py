@@ -77,7 +77,8 @@ def _kind_c(param):
     if "*" in param:
         return "ptr"
     t = param.strip().rsplit(" ", 1)[0].replace("const ", "").strip()
-    return {"int": "i32", "int32_t": "i32", "double": "f64", "uint64_t": "u64", "int64_t": "i64"}.get(t, t)
+    return {"int": "i32", "int32_t": "i32", "double": "f64", "uint64_t": "u64", "int64_t": "i64",
+            "ckks_alloc_fn": "ptr", "ckks_free_fn": "ptr"}.get(t, t)
 
 
 def _kind_py(t):
