@@ -21,13 +21,19 @@ std::mutex g_scratch_mu;
 std::unordered_map<int, u64*> g_scratch_addr;   // device ordinal -> device address of the array
 
 // The array's name is only a host-side handle; the address a kernel may use is looked
-// up once per device, with that device current.
-u64* scratch_for_current_device() {
+// up once per device, with that device current.  The look-up is not allowed while `stream`
+// is being captured into a CUDA graph: such a first call is refused with a clear error.
+u64* scratch_for_current_device(cudaStream_t stream) {
     int dev = 0;
     CUDA_CHECK(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_scratch_mu);
     auto it = g_scratch_addr.find(dev);
     if (it != g_scratch_addr.end()) return it->second;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_CHECK(cudaStreamIsCapturing(stream, &cs));
+    CK_CHECK(cs == cudaStreamCaptureStatusNone, CKKS_EINVAL,
+             "ckks_rescale_noalloc: the first call on a device looks up the scratch array's address and "
+             "cannot run inside a stream capture; call it once before capturing");
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_rescale_scratch);
     if (e != cudaSuccess)
@@ -57,7 +63,7 @@ extern "C" int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, int lev
         u64* out0 = reinterpret_cast<u64*>(d_out);
         CK_CHECK(out0 + 2 * level * n <= in0 || in0 + 2 * nl * n <= out0, CKKS_EINVAL,
                  "d_out must not overlap d_in");
-        u64* scratch = scratch_for_current_device();
+        u64* scratch = scratch_for_current_device(ctx->stream);
         u64* last = scratch;            // [2][N]: the dropped limb of c0 and c1
         u64* lift = scratch + 2 * n;    // [2][level][N]
         CUDA_CHECK(cudaMemcpyAsync(last, in0 + (size_t)level * n, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
