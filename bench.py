@@ -31,14 +31,15 @@ import workloads as WL  # noqa: E402
 METRIC = "ms per conv2d+bootstrap block at N=2^16"
 # DRAM bytes (read + write) per algorithmic byte of a forward NTT done as two k_ntt16 passes
 # (one read and one write of the limbs per transform are the algorithmic bytes, 268.4 MB for 256
-# limbs), from the ncu capture on 256 limbs (profiles/ntt16_256limbs_full.md): traffic of a
-# launch scales with its limbs, so the in-block traffic per launch is this ratio times the
-# launch's algorithmic bytes.
+# limbs): ncu (--set full, one forward transform of 256 limbs at N = 2^16, cold caches) counted
+# 134.4 + 81.0 MB for the first pass and 186.5 + 89.4 MB for the second; traffic of a launch
+# scales with its limbs, so the in-block traffic per launch is this ratio times the launch's
+# algorithmic bytes.
 NTT_FWD_DRAM_PER_ALGO_BYTE = (134.4 + 81.0 + 186.5 + 89.4) / 268.4
-# The same ratio for the key-switch inner product, from the ncu capture of `--kernel ks`
-# (profiles/keyswitch_kernels_full.md): one launch at the top level, 3 digits x 31 extended
-# limbs with the automorphed c0 term on 24 rows = (3*3 + 2) * 31 + 24 = 365 limbs of
-# algorithmic traffic (191.4 MB); DRAM read 146.3 MB + write 3.6 MB (cold caches under ncu).
+# The same ratio for the key-switch inner product, from an ncu capture (cold caches) of one
+# launch at the top level (`--kernel ks`): 3 digits x 31 extended limbs with the automorphed c0
+# term on 24 rows = (3*3 + 2) * 31 + 24 = 365 limbs of algorithmic traffic (191.4 MB); DRAM
+# read 146.3 MB + write 3.6 MB.
 KS_DRAM_PER_ALGO_BYTE = (146.3 + 3.6) / (365 * 65536 * 8 / 1e6)
 ROOF_NOTES = {
     "ntt_fwd": "integer-multiply-pipe bound (fmaheavy 67-74% busy, DRAM 24-35% under ncu): the roofline is that "
