@@ -69,6 +69,7 @@ def lib():
             "orc_base_convert": (None, [U64P, c_int, U64P, U64P, c_int, U64P, c_int]),
             "orc_rescale": (None, [U64P, U64P, c_int, c_int, U64P]),
             "orc_mod_down": (None, [U64P, U64P, c_int, c_int, c_int, U64P, U64P]),
+            "orc_div_round": (None, [U64P, U64P, c_int, c_int, c_int, U64P, U64P]),
             "orc_mod_raise": (None, [U64P, U64P, c_int, c_int, U64P]),
             "orc_splitmix_mix": (u64, [u64]),
             "orc_stream_key": (u64, [u64, u64]),
@@ -199,6 +200,15 @@ def mod_down(c, q, p):
     nq, np_ = len(q), len(p)
     out = np.empty((nq, c.shape[1]), dtype=np.uint64)
     lib().orc_mod_down(c, out, nq, np_, c.shape[1], _mods(q), _mods(p))
+    return out
+
+
+def div_round(x, level, q, S):
+    """x: rows q_0..q_{level-1} then one row per modulus of S ([level + len(S)][n]) ->
+    round(x / prod S) over q_0..q_{level-1} ([level][n]), exact"""
+    x = _u(x)
+    out = np.empty((level, x.shape[1]), dtype=np.uint64)
+    lib().orc_div_round(x, out, level, len(S), x.shape[1], _mods(q[:level]), _mods(S))
     return out
 
 

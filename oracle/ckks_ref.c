@@ -306,6 +306,96 @@ void orc_mod_down(const u64 *in, u64 *out, int nq, int np, int n, const u64 *q, 
     free(conv);
 }
 
+/* Exact rounded division by M = prod S_k (a ModDown by P fused with the rescale by q_l,
+   Sec. 2.4): in rows 0..l-1 hold x mod q_i, rows l..l+nS-1 hold x mod S_k; out_i =
+   round(x / M) mod q_i = (x_i - r) M^{-1} mod q_i with r the centred remainder of x mod M.
+   r comes from the CRT written out in multi-precision integers: X = sum_k xhat_k (M / S_k),
+   xhat_k = x_k (M / S_k)^{-1} mod S_k, is x mod M plus a multiple of M below nS M; subtract
+   M until X < M, then r = X or X - M (whichever lies in (-M/2, M/2]). */
+#define BIG_WORDS 10                      /* 640 bits: M up to 8 primes of 61 bits, X < 9 M */
+typedef struct { u64 w[BIG_WORDS]; } big_t;
+
+static void big_set(big_t *a, u64 v) { memset(a, 0, sizeof(*a)); a->w[0] = v; }
+static void big_mul_word(big_t *a, u64 m) {          /* a *= m */
+    u128 carry = 0;
+    for (int i = 0; i < BIG_WORDS; i++) {
+        u128 t = (u128)a->w[i] * m + carry;
+        a->w[i] = (u64)t;
+        carry = t >> 64;
+    }
+}
+static void big_add_mul_word(big_t *a, const big_t *b, u64 m) {   /* a += b * m */
+    u128 carry = 0;
+    for (int i = 0; i < BIG_WORDS; i++) {
+        u128 t = (u128)b->w[i] * m + a->w[i] + carry;
+        a->w[i] = (u64)t;
+        carry = t >> 64;
+    }
+}
+static int big_cmp(const big_t *a, const big_t *b) {
+    for (int i = BIG_WORDS - 1; i >= 0; i--)
+        if (a->w[i] != b->w[i]) return a->w[i] > b->w[i] ? 1 : -1;
+    return 0;
+}
+static void big_sub(big_t *a, const big_t *b) {      /* a -= b, a >= b */
+    u64 borrow = 0;
+    for (int i = 0; i < BIG_WORDS; i++) {
+        u64 bi = b->w[i] + borrow;
+        u64 nb = (bi < borrow) || (a->w[i] < bi);
+        a->w[i] -= bi;
+        borrow = nb;
+    }
+}
+static u64 big_mod_word(const big_t *a, u64 q) {      /* a mod q, Horner over the words */
+    u64 r = 0;
+    for (int i = BIG_WORDS - 1; i >= 0; i--) r = (u64)((((u128)r << 64) | a->w[i]) % q);
+    return r;
+}
+
+void orc_div_round(const u64 *in, u64 *out, int l, int nS, int n, const u64 *q, const u64 *S) {
+    big_t M, Mk[16], Mhalf;
+    u64 Mk_inv[16];
+    big_set(&M, 1);
+    for (int k = 0; k < nS; k++) big_mul_word(&M, S[k]);
+    for (int k = 0; k < nS; k++) {
+        u64 prod = 1;
+        big_set(&Mk[k], 1);
+        for (int t = 0; t < nS; t++)
+            if (t != k) {
+                big_mul_word(&Mk[k], S[t]);
+                prod = mul_mod(prod, S[t] % S[k], S[k]);
+            }
+        Mk_inv[k] = inv_mod(prod, S[k]);
+    }
+    Mhalf = M;                                           /* floor(M / 2) */
+    for (int i = 0; i < BIG_WORDS; i++)
+        Mhalf.w[i] = (M.w[i] >> 1) | (i + 1 < BIG_WORDS ? M.w[i + 1] << 63 : 0);
+    u64 *Mmod = (u64 *)malloc(sizeof(u64) * (size_t)(l + 1));
+    u64 *Minv = (u64 *)malloc(sizeof(u64) * (size_t)(l + 1));
+    for (int i = 0; i < l; i++) {
+        Mmod[i] = big_mod_word(&M, q[i]);
+        Minv[i] = inv_mod(Mmod[i], q[i]);
+    }
+#pragma omp parallel for
+    for (int j = 0; j < n; j++) {
+        big_t X;
+        big_set(&X, 0);
+        for (int k = 0; k < nS; k++) {
+            u64 xk = in[(size_t)(l + k) * n + j];
+            big_add_mul_word(&X, &Mk[k], mul_mod(xk, Mk_inv[k], S[k]));
+        }
+        while (big_cmp(&X, &M) >= 0) big_sub(&X, &M);
+        int neg = big_cmp(&X, &Mhalf) > 0;               /* r = X - M */
+        for (int i = 0; i < l; i++) {
+            u64 rm = big_mod_word(&X, q[i]);
+            if (neg) rm = sub_mod(rm, Mmod[i], q[i]);
+            out[(size_t)i * n + j] = mul_mod(sub_mod(in[(size_t)i * n + j], rm, q[i]), Minv[i], q[i]);
+        }
+    }
+    free(Mmod);
+    free(Minv);
+}
+
 /* ModRaise (Sec. 2.4): the centred residue mod q0 lifted to every limb */
 void orc_mod_raise(const u64 *in, u64 *out, int nq, int n, const u64 *q) {
 #pragma omp parallel for

@@ -374,29 +374,15 @@ class Oracle:
     def mod_down_rescale(self, acc_b, acc_a, level):
         """ModDown fused with the rescale after it: the Q_l u P polynomials divided by M = q_l P
         with rounding, out_i = (a_i - r) M^{-1} mod q_i (i < l), r the centred remainder of a
-        mod M.  Exact: r by CRT in Python integers."""
+        mod M.  Exact: r by the CRT written out in multi-precision integers."""
         P = self.P
         self.ops["rescale"] += 1
         S = [int(P.q[level])] + [int(x) for x in P.p]
         return self._div_round(acc_b, level, S), self._div_round(acc_a, level, S)
 
     def _div_round(self, acc, level, S):
-        M = 1
-        for m in S:
-            M *= m
-        r = np.zeros(acc.shape[1], dtype=object)
-        for k, mk in enumerate(S):
-            Mk = M // mk
-            r = r + (acc[level + k].astype(object) * pow(Mk % mk, -1, mk)) % mk * Mk
-        r = r % M
-        r = np.where(r > M // 2, r - M, r)
-        q = self.P.moduli(level - 1)
-        out = np.empty((len(q), acc.shape[1]), dtype=np.uint64)
-        for i, qi in enumerate(q):
-            qi = int(qi)
-            inv = pow(M % qi, -1, qi)
-            out[i] = ((acc[i].astype(object) - r) % qi * inv % qi).astype(np.uint64)
-        return out
+        """acc rows q_0..q_l then the special primes (S = [q_l] + P) -> round(acc / prod S)"""
+        return C.div_round(acc, level, self.P.moduli(level - 1), S)
 
     def rotate_hoisted(self, ct, steps):
         """HRot(ct, r) for every r in steps, sharing one ModUp of c1"""
