@@ -459,6 +459,49 @@ def test_cfg2_block_full_size():
     assert err < 2.0 ** -12, err
 
 
+@pytest.mark.slow
+def test_cfg2_block_full_size_bitexact():
+    """config 2 at full size (N = 2^16, 24 limbs, dnum 3, 16 channels of 32 x 32) with the BSGS
+    splits the tuner picks on GB300 (CtoS 16 / 16 / 32, StoC1 16 / 16 / 8: the fused baby-step
+    kernel with 4 and with 2 giant steps): every limb of the encryption, the fused conv, the
+    bootstrap's EvalMod outputs (Re and Im: ModRaise, three CtoS HMatmuls, the conjugate split,
+    the scale drop, the degree-59 Chebyshev series and three double angles, across the
+    segment boundary), StoC1, the block as called (which skips the Im branch its zero mask
+    removes) and the block replayed as the CUDA graph the bench times, against the oracle's
+    block; decoded within 2^-12 of the masked FP64 conv2d"""
+    s = torch.cuda.Stream()          # the graph needs a context on a non-default stream
+    with torch.cuda.stream(s):
+        _full_size_block(s)
+
+
+def _full_size_block(s):
+    d = _block_pair("cfg2", 7, splits=([16, 16, 32], [16, 16, 8]))
+    K, o, ctx, keys = d["K"], d["o"], d["ctx"], d["keys"]
+    ct = o.encrypt(d["pt"], 2)
+    gct = K.ckks_encrypt(ctx, keys, import_pt(K, ctx, d["pt"]), 2)
+    assert_ct_equal(K, ctx, gct, ct, "encryption")
+    gplan = import_plan(K, ctx, d["plan"])
+    x0 = o.conv2d_cins(ct, d["plan"])
+    gx0 = K.ckks_conv2d_cins(ctx, keys, gct, gplan)
+    assert_ct_equal(K, ctx, gx0, x0, "conv")
+    re, im = BT.bootstrap(o, x0, d["cfg"])
+    gre, gim = K.ckks_bootstrap(ctx, keys, d["bt"], gx0)
+    assert_ct_equal(K, ctx, gre, re, "EvalMod Re")
+    assert_ct_equal(K, ctx, gim, im, "EvalMod Im")
+    out = BT.stoc1(o, re, im, d["cfg"])
+    assert_ct_equal(K, ctx, K.ckks_stoc1(ctx, keys, gre, gim, d["bt"]), out, "StoC1")
+    assert_ct_equal(K, ctx, K.ckks_block(ctx, keys, gct, gplan, d["bt"]), out, "block")
+    gout = K.ckks_ct_create(ctx)
+    g = K.ckks_block_graph_create(ctx, keys, gct, gplan, d["bt"], gout)
+    K.ckks_graph_launch(g)
+    K.ckks_sync(ctx)
+    assert_ct_equal(K, ctx, gout, out, "block graph replay")
+    zexp, _ = _expected_slots(d)
+    got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gout))
+    err = np.abs(_pixels(d, got) - _pixels(d, zexp)).max()
+    assert err < 2.0 ** -12, err
+
+
 # ------------------------------------------------- downsampling conv (Alg. 2) ----
 def _ds_tail_slots(P, cfg, x, seed):
     """Re / Im slot vectors as the bootstrap hands them to the tail (slot i l + u: pixel
