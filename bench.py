@@ -59,7 +59,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
+    ap.add_argument("--oracle-small", action="store_true",
+                    help="--impl reference: the config-2 chain at N=2^10 (checks the arm quickly; not a measurement)")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
     ap.add_argument("--batch", type=int, default=8, help="ciphertexts run concurrently for the batched figure")
     ap.add_argument("--workload", default="block", choices=["block", "ds", "serve", "batch"],
@@ -239,104 +240,183 @@ def check_accuracy(K, s, out):
 
 
 # ------------------------------------------------------------ oracle arm -----
-_ORACLE_SETUP = {}
+# BSGS splits of the oracle's block (CtoS levels, StoC1 levels): the splits the GPU tuner picks
+# on GB300 for config 2.
+ORACLE_SPLITS = ([16, 16, 32], [16, 16, 8])
+# Share of the whole oracle block taken by its first two steps (the fused conv; ModRaise and
+# the first CtoS HMatmul), from a full block timed step by step with `--impl reference` on the
+# GB300 machine's host (16 cores); the CPU baseline of the GPU arm times those two steps and
+# divides by this share.
+ORACLE_SAMPLE_SHARE = 0.145       # (1329.6 + 7203.6) / 58763.6 ms, Neoverse-V2 x 16
+_ORACLE = {}
 
 
-def _oracle_setup():
-    """The oracle, its keys and the sample's inputs, made once per process: keys and
-    plaintexts are resident in the timed GPU block too, so only the operations are timed."""
-    if "s" not in _ORACLE_SETUP:
+def _oracle_block(full, name=CONFIG):
+    """The oracle on the config-2 chain with the block's plans, keys and input, made once per
+    process (keys and plaintexts are resident in the GPU arm's timed block too).  full: keys
+    for every step of the block; else only for its first two steps.  name = "cfg2_small" runs
+    the same chain at N = 2^10 (a quick check of the reference arm, not a measurement)."""
+    key = (full, name)
+    if key not in _ORACLE:
+        from oracle import boot as BT
         from oracle import encoding as E
         from oracle import params as PP
         from oracle.scheme import Oracle
-        d = WL.PARAMS[CONFIG]
-        spec = WL.CONV[CONFIG]
+        d = WL.PARAMS[name]
+        spec = WL.CONV[name]
         P = PP.Params(d["log_n"], d["n_q"], d["dnum"], d["q0_bits"], d["scale_bits"], d["p_bits"], h=d["h"],
                       sigma=d["sigma"], n_p=d["n_p"], boot_bits=d["boot_bits"], n_boot=d["n_boot"])
         o = Oracle(P, 1)
         w = E.pad_width(spec["w0"], spec["f"])
         x = WL.image(1, spec["cin"], spec["w0"])
         W = WL.weights(1, spec["cout"], spec["cin"], spec["f"], spec["weight"])
-        plan = o.conv_plan(W, spec["cin"], spec["cout"], spec["f"], w, 1, (2.0 ** 49 * float(P.q[1])) / P.delta[1])
-        o.gen_rotation_keys(plan.rotations(P.n // 2) + [1])
+        splits = ORACLE_SPLITS if name == CONFIG else (None, None)
+        cfg = BT.BootConfig(o, w, spec["w0"], spec["cout"], ctos_B=splits[0], stoc_B=splits[1])
+        plan = o.conv_plan(W, spec["cin"], spec["cout"], spec["f"], w, 1, (cfg.delta0 * float(P.q[1])) / P.delta[1])
+        m = P.n // 2
+        if full:
+            o.gen_relin_key()
+            o.gen_conj_key()
+            o.gen_rotation_keys(BT.block_rotations(o, plan, cfg))
+        else:
+            o.gen_rotation_keys(sorted(set(plan.rotations(m)) | set(cfg.ctos[0].rotations(m))))
         ct = o.encrypt(o.encode_pt(E.cins_input_slots(x, w, P.n), 1, P.delta[1]), 1)
-        hi = o.encrypt(o.encode_pt(WL.slots(2, P.n // 2, 0.5), 19, P.delta[19]), 2)
-        pt = o.encode_pt(WL.slots(3, P.n // 2), 19, P.delta[19])
-        _ORACLE_SETUP["s"] = (o, plan, ct, hi, pt)
-    return _ORACLE_SETUP["s"]
+        _ORACLE[key] = (o, BT.block_stages(o, plan, cfg), ct)
+    return _ORACLE[key]
 
 
-def oracle_sample(seconds_budget, counts=None):
-    """Time the CPU oracle on a bounded sample of the block and scale it to ms per block.
-
-    Sample: the fused conv at level 1, then at level 19 one hoisted rotation (one key
-    switch), one rescale and one PMult, all at N = 2^16 on the config-2 chain.  The block
-    estimate is conv + n_keyswitch * t_ks + n_rescale * t_rs + n_pmult * t_pm, with the
-    counts of one block (taken from the block's structure: they are properties of the
-    algorithm, identical on both implementations)."""
-    o, plan, ct, hi, pt = _oracle_setup()
-    t0 = time.perf_counter()
-    o.conv2d_cins(ct, plan)
-    t_conv = time.perf_counter() - t0
-    reps = 0
-    t_ks = t_rs = t_pm = 0.0
-    start = time.perf_counter()
-    while True:
-        t0 = time.perf_counter()
-        o.rotate(hi, 1)
-        t1 = time.perf_counter()
-        o.rescale(hi)
-        t2 = time.perf_counter()
-        o.mul_plain(hi, pt)
-        t3 = time.perf_counter()
-        t_ks += t1 - t0
-        t_rs += t2 - t1
-        t_pm += t3 - t2
-        reps += 1
-        if time.perf_counter() - start > seconds_budget * 0.5 or reps >= 8:
-            break
-    t_ks, t_rs, t_pm = t_ks / reps, t_rs / reps, t_pm / reps
-    counts = counts or block_op_counts()
-    est = t_conv + counts["keyswitch"] * t_ks + counts["rescale"] * t_rs + counts["pmult"] * t_pm
+def _cores():
     from oracle import _clib
-    cores = _clib.max_threads()            # threads of the oracle's OpenMP loops over limbs
-    sample = ("oracle at N=2^16, config-2 chain: fused conv at level 1 (%.2f s) + %d x [1 key switch, 1 rescale, "
-              "1 PMult] at level 19 (%.2f / %.3f / %.3f s each); ms per block = conv + %d keyswitch + %d rescale + "
-              "%d PMult" % (t_conv, reps, t_ks, t_rs, t_pm, counts["keyswitch"], counts["rescale"], counts["pmult"]))
-    return est * 1e3, cores, sample
+    return _clib.max_threads()            # threads of the oracle's OpenMP loops
 
 
-# Operation counts of one config-2 block as the oracle runs it (EvalMod on both the Re and
-# the Im part, double-hoisted HMatmuls, BSGS splits 16/16/32/16/16/8): 156 key switches
-# (117 rotations, 38 relinearisations, 1 conjugation), 253 PMults, 101 rescales, as the
-# library's counters report them for the same steps with the zero-mask skip off.  The GPU
-# arm passes its live counts instead (they follow the splits its tuner picked).
-BLOCK_OP_COUNTS = {"keyswitch": 156, "pmult": 253, "hrot": 117, "hmult": 38, "rescale": 101}
+def _host_model():
+    """the host CPU's model name (lscpu), e.g. to state which cores timed the oracle"""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
 
 
-def block_op_counts():
-    return dict(BLOCK_OP_COUNTS)
+def oracle_cfg1_e2e():
+    """config 1 end to end on the oracle: encode -> encrypt -> fused CinS conv -> decrypt ->
+    decode, ms (keys made beforehand)"""
+    from oracle import encoding as E
+    from oracle import params as PP
+    from oracle.scheme import Oracle
+    d = WL.PARAMS["cfg1"]
+    spec = WL.CONV["cfg1"]
+    P = PP.Params(d["log_n"], d["n_q"], d["dnum"], d["q0_bits"], d["scale_bits"], d["p_bits"], h=d["h"],
+                  sigma=d["sigma"])
+    x = WL.image(0, spec["cin"], spec["w0"])
+    W = WL.weights(0, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+    w = E.pad_width(spec["w0"], spec["f"])
+    o = Oracle(P, 3)
+    plan = o.conv_plan(W, 1, 1, spec["f"], w, P.L, (P.delta[P.L - 1] * float(P.q[P.L])) / P.delta[P.L])
+    o.gen_rotation_keys(plan.rotations(P.n // 2))
+    t0 = time.perf_counter()
+    ct = o.encrypt(o.encode_pt(E.cins_input_slots(x, w, P.n), P.L, P.delta[P.L]), 1)
+    out = o.conv2d_cins(ct, plan)
+    E.conv_output_from_coeffs(o.decode_coeffs(o.decrypt(out)), P.n // (w * w), w * w, 1, w, spec["w0"])
+    return (time.perf_counter() - t0) * 1e3
+
+
+def oracle_sample():
+    """CPU baseline of the GPU arm: the first two steps of the oracle's config-2 block (the fused
+    conv; ModRaise and the first CtoS HMatmul) timed at the oracle's thread count and scaled by
+    their measured share of a whole block; the fused conv also on one thread; config 1 end to
+    end."""
+    from oracle import _clib
+    o, stages, ct = _oracle_block(full=False)
+    times = {}
+    v = [ct]
+    for name, step in stages[:2]:
+        t0 = time.perf_counter()
+        v = step(v)
+        times[name] = time.perf_counter() - t0
+    cores = _cores()
+    _clib.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        stages[0][1]([ct])
+        conv_1t = time.perf_counter() - t0
+    finally:
+        _clib.set_threads(cores)
+    e2e1 = oracle_cfg1_e2e()
+    sample_s = sum(times.values())
+    value = sample_s / ORACLE_SAMPLE_SHARE * 1e3
+    return {"value": round(value, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": "oracle at N=2^16 on the config-2 chain: the block's first two steps measured (fused conv "
+                      "%.2f s, ModRaise + first CtoS HMatmul %.2f s), divided by their share %.3f of a whole "
+                      "oracle block timed step by step (--impl reference)" % (
+                          times["conv"], times["modraise_ctos0"], ORACLE_SAMPLE_SHARE),
+            "one_thread": {"step": "fused conv", "s": round(conv_1t, 3), "speedup": round(conv_1t / times["conv"], 2)},
+            "cfg1_e2e_ms": round(e2e1, 1), "host": _host_model()}
 
 
 def run_reference(args):
+    """The oracle's whole config-2 block, measured: its steps (fused conv; ModRaise + CtoS
+    HMatmul; two more CtoS HMatmuls; conjugate split; EvalMod Re; EvalMod Im; masks + Re + i Im;
+    three StoC1 HMatmuls) run one per bench step, in order, the block starting over after its
+    last step; `value` = the sum over the steps of each step's mean measured time, i.e. ms per
+    block, every step measured (warm-up steps fill in a step the timed ones did not reach)."""
     rank, _, _ = rank_info()
     if rank != 0:      # under torchrun rank 0 alone times the oracle; the others exit without work
         return
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    vals = []
-    cores = sample = None
-    for i in range(args.warmup + args.steps):
-        v, cores, sample = oracle_sample(per_step)
-        if i >= args.warmup:
-            vals.append(v)
-    value = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+    small = getattr(args, "oracle_small", False)
+    t_setup = time.perf_counter()
+    o, stages, ct = _oracle_block(full=True, name="cfg2_small" if small else CONFIG)
+    t_setup = time.perf_counter() - t_setup
+    S = len(stages)
+    per = {name: [] for name, _ in stages}
+    warm = {name: [] for name, _ in stages}
+    v = [ct]
+    timed_s = 0.0
+    n_run = max(args.warmup + args.steps, S)       # at least one whole block
+    for i in range(n_run):
+        name, step = stages[i % S]
+        if i % S == 0:
+            v = [ct]
+        t0 = time.perf_counter()
+        v = step(v)
+        dt = time.perf_counter() - t0
+        if i < args.warmup:
+            warm[name].append(dt)
+        elif i < args.warmup + args.steps:
+            per[name].append(dt)
+            timed_s += dt
+        else:
+            warm[name].append(dt)
+    stage_ms = {}
+    for name, _ in stages:
+        xs = per[name] or warm[name]
+        stage_ms[name] = 1e3 * sum(xs) / len(xs) if xs else None
+    measured = all(x is not None for x in stage_ms.values())
+    value = sum(stage_ms.values()) if measured else None
+    cores = _cores()
+    sample = ("the oracle's whole config-2 block (N=2^16, 24 limbs, BSGS splits %s / %s) measured step by step: "
+              "%d steps per block, one per bench step, block restarted after its last step; value = sum of each "
+              "step's mean time%s" % (ORACLE_SPLITS[0], ORACLE_SPLITS[1], S,
+                                      "" if all(per[n] for n, _ in stages) else
+                                      " (steps outside the timed region measured in the warm-up or after it)"))
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1) if value else None, "unit": "ms",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(timed_s * 1e3 / max(1, args.steps), 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "config-2 block: 16x32x32 -> 16, 3x3 conv fused with StoC2, full bootstrap, "
-                                   "N=2^16, 24 limbs", "l2": "working set > L2"},
-            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": ("config-2 block: 16x32x32 -> 16, 3x3 conv fused with StoC2, full bootstrap, "
+                                    "N=2^16, 24 limbs") if not small else
+                                   "config-2 chain at N=2^10 (check of the arm only, not a measurement)",
+                       "l2": "working set > L2", "steps_per_block": S,
+                       "setup_s": round(t_setup, 1)},
+            "stage_ms": {k: round(x, 1) for k, x in stage_ms.items() if x is not None},
+            "cpu_baseline": {"value": round(value, 1) if value else None, "unit": "ms", "cores": cores,
+                             "kind": "oracle", "sample": sample, "host": _host_model()},
+            "e2e": {"value": round(value, 1) if value else None, "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -523,8 +603,7 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         try:
-            v, cores, sample = oracle_sample(args.cpu_sample_seconds, counts_full)
-            cpu = {"value": round(v, 1), "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
+            cpu = oracle_sample()
         except Exception as e:  # the baseline is reported, never required
             cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": "failed: %s" % e}
     line = {"metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,

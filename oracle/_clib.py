@@ -54,6 +54,7 @@ def lib():
             "orc_pow_mod": (u64, [u64, u64, u64]),
             "orc_mul_mod": (u64, [u64, u64, u64]),
             "orc_max_threads": (c_int, []),
+            "orc_set_threads": (None, [c_int]),
             "orc_ntt_naive": (None, [U64P, U64P, c_int, u64, u64]),
             "orc_ntt_forward": (None, [U64P, c_int, c_int, U64P, U64P]),
             "orc_ntt_inverse": (None, [U64P, c_int, c_int, U64P, U64P]),
@@ -253,6 +254,11 @@ def sample_gauss(n, sigma, seed, tag):
 def max_threads():
     """threads of the oracle's OpenMP loops"""
     return int(lib().orc_max_threads())
+
+
+def set_threads(n):
+    """use n threads in the oracle's OpenMP loops from now on"""
+    lib().orc_set_threads(int(n))
 
 
 def splitmix_mix(z):

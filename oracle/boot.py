@@ -125,13 +125,17 @@ class BootConfig:
         return re, im
 
 
-def bootstrap(orc: Oracle, ct0, cfg: BootConfig):
-    """ModRaise -> CtoS -> scale drop -> conjugate split -> EvalMod (Re), EvalMod (Im)"""
-    P = orc.P
+def mod_raise(orc: Oracle, ct0, cfg: BootConfig):
+    """ModRaise, the result declared at scale q0 K_eff"""
     x = orc.mod_raise(ct0)
     x.scale = cfg.s_raise
-    for plan in cfg.ctos:
-        x = orc.bsgs(x, plan, rescale=True)
+    return x
+
+
+def conj_split(orc: Oracle, x, cfg: BootConfig):
+    """Re = x + conj(x), Im = i (conj(x) - x), each brought to the canonical scale by one
+    integer multiply and rescale"""
+    P = orc.P
     cj = orc.conjugate(x)
     re = orc.add(x, cj)
     im = orc.imult(orc.sub(cj, x))
@@ -139,6 +143,25 @@ def bootstrap(orc: Oracle, ct0, cfg: BootConfig):
     im = orc.rescale(orc.mul_int(im, cfg.c_drop))
     re.scale = P.delta[re.level]
     im.scale = P.delta[im.level]
+    return re, im
+
+
+def mask_recombine(orc: Oracle, re, im, cfg: BootConfig):
+    """mask both parts, Re + i Im, and the Alg. 2 decomposition of a stride-2 block"""
+    a = orc.rescale(orc.mul_plain(re, cfg.pt_mask_re))
+    b = orc.rescale(orc.mul_plain(im, cfg.pt_mask_im))
+    y = orc.add(a, orc.imult(b))
+    if cfg.decomp is not None:
+        y = orc.bsgs(y, cfg.decomp, rescale=True)
+    return y
+
+
+def bootstrap(orc: Oracle, ct0, cfg: BootConfig):
+    """ModRaise -> CtoS -> scale drop -> conjugate split -> EvalMod (Re), EvalMod (Im)"""
+    x = mod_raise(orc, ct0, cfg)
+    for plan in cfg.ctos:
+        x = orc.bsgs(x, plan, rescale=True)
+    re, im = conj_split(orc, x, cfg)
     re = orc.eval_mod(re, cfg.coeffs, cfg.r)
     im = orc.eval_mod(im, cfg.coeffs, cfg.r)
     return re, im
@@ -146,11 +169,7 @@ def bootstrap(orc: Oracle, ct0, cfg: BootConfig):
 
 def stoc1(orc: Oracle, re, im, cfg: BootConfig):
     """mask, Re + i Im, HMatmul(S_{l<-1})"""
-    a = orc.rescale(orc.mul_plain(re, cfg.pt_mask_re))
-    b = orc.rescale(orc.mul_plain(im, cfg.pt_mask_im))
-    y = orc.add(a, orc.imult(b))
-    if cfg.decomp is not None:
-        y = orc.bsgs(y, cfg.decomp, rescale=True)
+    y = mask_recombine(orc, re, im, cfg)
     for plan in cfg.stoc:
         y = orc.bsgs(y, plan, rescale=True)
     return y
@@ -162,6 +181,27 @@ def block(orc: Oracle, ct_in, conv_plan, cfg: BootConfig):
     assert abs(x.scale - cfg.delta0) <= 1e-9 * cfg.delta0
     re, im = bootstrap(orc, x, cfg)
     return stoc1(orc, re, im, cfg)
+
+
+def block_stages(orc: Oracle, conv_plan, cfg: BootConfig):
+    """The block's steps in order, as (name, step) pairs: each step takes the list of
+    ciphertexts the previous one returned (first [ct_in]) and returns the next list; chained
+    they compute block().  Used to time a block one step at a time."""
+    def conv(v):
+        x = orc.conv2d_cins(v[0], conv_plan)
+        assert abs(x.scale - cfg.delta0) <= 1e-9 * cfg.delta0
+        return [x]
+    stages = [("conv", conv),
+              ("modraise_ctos0", lambda v: [orc.bsgs(mod_raise(orc, v[0], cfg), cfg.ctos[0], rescale=True)])]
+    for i, plan in enumerate(cfg.ctos[1:], 1):
+        stages.append(("ctos%d" % i, lambda v, p=plan: [orc.bsgs(v[0], p, rescale=True)]))
+    stages.append(("conj_split", lambda v: list(conj_split(orc, v[0], cfg))))
+    stages.append(("evalmod_re", lambda v: [orc.eval_mod(v[0], cfg.coeffs, cfg.r), v[1]]))
+    stages.append(("evalmod_im", lambda v: [v[0], orc.eval_mod(v[1], cfg.coeffs, cfg.r)]))
+    stages.append(("mask_recombine", lambda v: [mask_recombine(orc, v[0], v[1], cfg)]))
+    for i, plan in enumerate(cfg.stoc):
+        stages.append(("stoc%d" % i, lambda v, p=plan: [orc.bsgs(v[0], p, rescale=True)]))
+    return stages
 
 
 def block_multi(orc: Oracle, cts, conv_plans, cfg: BootConfig):

@@ -27,6 +27,15 @@ typedef uint64_t u64;
 typedef int64_t i64;
 typedef unsigned __int128 u128;
 
+/* threads of the OpenMP loops from now on (n >= 1) */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* threads the OpenMP loops over limbs use (1 without OpenMP) */
 int orc_max_threads(void) {
 #ifdef _OPENMP

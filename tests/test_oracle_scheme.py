@@ -228,6 +228,11 @@ def test_block_matches_fp64_conv():
     o.gen_relin_key()
     out = BT.block(o, ct, plan, cfg)
     assert out.level == cfg.l_out
+    # the block one step at a time (how the CPU baseline times it) is the same ciphertext
+    v = [ct]
+    for _, step in BT.block_stages(o, plan, cfg):
+        v = step(v)
+    assert len(v) == 1 and (v[0].c0 == out.c0).all() and (v[0].c1 == out.c1).all()
     got = slots(o, out)
     ell = w * w // 2
     pix = np.stack([E.encode(got[i * ell:(i + 1) * ell], w * w) for i in range(C)])
