@@ -450,6 +450,25 @@ int ckks_batch_launch(ckks_batch* batch);
 /* Waits for the context's stream, then frees the graphs, streams and events. */
 int ckks_batch_destroy(ckks_batch* batch);
 
+/* Lockstep batch (the paper's amortisation of the BSGS plaintexts, Sec. 2.5, and of the
+ * key-switching keys, Sec. 2.1, over many ciphertexts): B ciphertexts of one shape (same level
+ * and scale) through the same block (Alg. 1 without HActivation, as ckks_block computes it)
+ * as ONE batch: every kernel of the block is launched once for all B ciphertexts, so each
+ * switching key and plaintext diagonal streams from HBM about once per batch (the CTAs of the
+ * B ciphertexts that read the same key words run side by side and share them through L2),
+ * and every NTT, base conversion and elementwise launch covers B times the limbs.  Each out[i]
+ * receives exactly the ciphertext ckks_block would give for in[i] (same residues).  Device
+ * memory: about B times that of one block.  CKKS_EINVAL for B outside 1..1024, inputs of
+ * different levels or scales, an output that aliases an input or another output. */
+int ckks_block_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                       const ckks_ptset* conv, const ckks_boot* bt, ckks_ct* const* out);
+/* The same lockstep batch recorded as one CUDA graph (gather of in[], batched block, scatter
+ * into out[]), after one eager run that sizes out[]; the rules of ckks_block_graph_create
+ * apply to every in[i] and out[i]. */
+int ckks_block_batched_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                                    const ckks_ptset* conv, const ckks_boot* bt, ckks_ct* const* out,
+                                    ckks_graph** graph);
+
 /* ---- serving loop ----------------------------------------------------------------
  * Continuous batching of inference requests (no counterpart in the paper, whose
  * measurements are one image at a time; a server needs batched throughput).

@@ -159,6 +159,8 @@ _SIGS = {
     "ckks_graph_destroy": [VP],
     "ckks_block_batch_create": [VP, VP, I, PVP, VP, VP, PVP, I, PVP],
     "ckks_batch_launch": [VP],
+    "ckks_block_batched": [VP, VP, I, PVP, VP, VP, PVP],
+    "ckks_block_batched_graph_create": [VP, VP, I, PVP, VP, VP, PVP, PVP],
     "ckks_batch_destroy": [VP],
     "ckks_eval_relu": [VP, VP, VP, VP, VP, I, VP],
     "ckks_rescale_noalloc": [VP, VP, I, VP],
@@ -854,6 +856,24 @@ def ckks_block_batch_create(ctx, keys, ins, conv, bt, outs, n_streams=8) -> Batc
     bh = Batch(b.value, ctx)
     bh.refs = (keys, list(ins), conv, bt, list(outs))     # the graphs read and write these buffers
     return bh
+
+
+def ckks_block_batched(ctx, keys, ins, conv, bt, outs=None):
+    """the lockstep batch: every input through one block, each kernel launched once for all"""
+    outs = outs or [ckks_ct_create(ctx) for _ in ins]
+    assert len(outs) == len(ins)
+    ctx.check(lib().ckks_block_batched(ctx, keys, len(ins), _ptrs(ins), conv, bt, _ptrs(outs)))
+    return outs
+
+
+def ckks_block_batched_graph_create(ctx, keys, ins, conv, bt, outs) -> Graph:
+    assert len(outs) == len(ins)
+    g = ctypes.c_void_p()
+    ctx.check(lib().ckks_block_batched_graph_create(ctx, keys, len(ins), _ptrs(ins), conv, bt, _ptrs(outs),
+                                                    ctypes.byref(g)))
+    gr = Graph(g.value, ctx)
+    gr.refs = (keys, list(ins), conv, bt, list(outs))     # the graph reads and writes these buffers
+    return gr
 
 
 def ckks_batch_launch(batch):

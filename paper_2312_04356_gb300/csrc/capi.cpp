@@ -1475,6 +1475,95 @@ int ckks_downsample_layer_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int
     });
 }
 
+// ---- lockstep batches: B ciphertexts of one shape through one block, every kernel launched once
+// for all of them (keys and plaintext diagonals read once per launch) ----
+namespace {
+// the inputs gathered into one batched ciphertext [B][2][l+1][N]
+ckks_ct gather_batch(ckks_ctx* ctx, int B, const ckks_ct* const* in) {
+    CK_CHECK(B >= 1 && B <= 1024, CKKS_EINVAL, "B must be in [1, 1024]");
+    REQ(in);
+    for (int t = 0; t < B; ++t) {
+        CT_OK(in[t]);
+        CK_CHECK(in[t]->nb == 1 && in[t]->level == in[0]->level, CKKS_EINVAL, "batch inputs differ in level");
+        CK_CHECK(fabs(in[t]->scale - in[0]->scale) <= ldexp(1.0, -30) * fabs(in[0]->scale), CKKS_EINVAL,
+                 "batch inputs differ in scale");
+    }
+    ckks_ct x = ops::new_ct(ctx, in[0]->level, in[0]->scale, B);
+    for (int t = 0; t < B; ++t)
+        CUDA_CHECK(cudaMemcpyAsync(x.c0(t), in[t]->buf.ptr, x.cstride() * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    return x;
+}
+// each ciphertext of a batch into its own handle (sized before, when `sized`)
+void scatter_batch(ckks_ctx* ctx, const ckks_ct& y, ckks_ct* const* out, bool sized) {
+    for (int t = 0; t < y.nb; ++t) {
+        if (!sized) ops::ensure_ct(*out[t], ctx, y.level);
+        CK_CHECK(out[t]->level == y.level && out[t]->nb == 1, CKKS_EINVAL, "output handle changed shape");
+        out[t]->scale = y.scale;
+        CUDA_CHECK(cudaMemcpyAsync(out[t]->buf.ptr, y.c0(t), y.cstride() * 8, cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+    }
+}
+void batch_args(int B, const ckks_ct* const* in, ckks_ct* const* out) {
+    REQ(in);
+    REQ(out);
+    for (int t = 0; t < B; ++t) {
+        REQ(out[t]);
+        for (int u = 0; u < B; ++u) CK_CHECK(out[t] != in[u], CKKS_EINVAL, "outputs must not alias inputs");
+        for (int u = 0; u < t; ++u) CK_CHECK(out[t] != out[u], CKKS_EINVAL, "outputs must be distinct");
+    }
+}
+}  // namespace
+
+int ckks_block_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                       const ckks_ptset* conv, const ckks_boot* bt, ckks_ct* const* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(keys);
+        REQ(conv);
+        REQ(bt);
+        batch_args(B, in, out);
+        ckks_ct x = gather_batch(ctx, B, in);
+        ckks_ct y = ops::block(*keys, *bt, *conv, x);
+        scatter_batch(ctx, y, out, false);
+    });
+}
+
+int ckks_block_batched_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                                    const ckks_ptset* conv, const ckks_boot* bt, ckks_ct* const* out,
+                                    ckks_graph** g) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(keys);
+        REQ(conv);
+        REQ(bt);
+        REQ(g);
+        batch_args(B, in, out);
+        CK_CHECK(ctx->stream != nullptr, CKKS_EINVAL, "graphs need a context created on a non-default stream");
+        {   // one eager run: sizes the outputs and builds any lazily created table
+            ckks_ct x = gather_batch(ctx, B, in);
+            scatter_batch(ctx, ops::block(*keys, *bt, *conv, x), out, false);
+        }
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        std::unique_ptr<ckks_graph> gr(new ckks_graph());
+        gr->ctx = ctx;
+        const long long l0 = ctx->launches;
+        CUDA_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            ckks_ct x = gather_batch(ctx, B, in);
+            scatter_batch(ctx, ops::block(*keys, *bt, *conv, x), out, true);
+        } catch (...) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(ctx->stream, &tmp);
+            if (tmp) cudaGraphDestroy(tmp);
+            throw;
+        }
+        CUDA_CHECK(cudaStreamEndCapture(ctx->stream, &gr->graph));
+        CUDA_CHECK(cudaGraphInstantiate(&gr->exec, gr->graph, 0));
+        gr->launches = ctx->launches - l0;
+        *g = gr.release();
+    });
+}
+
 int ckks_graph_launch(ckks_graph* g, void* stream) {
     if (!g) return CKKS_EINVAL;
     return guard(g->ctx, [&] {

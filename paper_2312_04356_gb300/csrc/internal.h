@@ -157,13 +157,18 @@ struct ckks_ctx {
     ~ckks_ctx();
 };
 
+// A ciphertext, or a batch of nb ciphertexts at the same level and scale that every operation
+// processes in lockstep (one launch per kernel for the whole batch, keys and plaintexts read
+// once per launch): [nb][2][level+1][N].
 struct ckks_ct {
     ckks_ctx* ctx = nullptr;
-    DevBuf buf;           // [2][level+1][N]
+    DevBuf buf;           // [nb][2][level+1][N]
     int level = -1;
     double scale = 1.0;
-    u64* c0() const { return buf.ptr; }
-    u64* c1() const { return buf.ptr + (size_t)(level + 1) * ctx->n; }
+    int nb = 1;
+    size_t cstride() const { return 2 * (size_t)(level + 1) * ctx->n; }   // words per ciphertext
+    u64* c0(int t = 0) const { return buf.ptr + t * cstride(); }
+    u64* c1(int t = 0) const { return c0(t) + (size_t)(level + 1) * ctx->n; }
 };
 
 struct ckks_pt {
@@ -243,8 +248,10 @@ struct ScalarVec {
 namespace kern {
 // pstride: words between consecutive polynomials of lpp limbs (0 = lpp * N, contiguous)
 void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
-// forward NTT of an arbitrary list of limbs: limb i at data + off[i] * N with prime ids[i] (N = 2^16)
-void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, const int* ids);
+// forward NTT of an arbitrary list of limbs: limb i at data + off[i] * N with prime ids[i] (N = 2^16);
+// for nb copies of the list, copy t at data + t * bstride
+void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, const int* ids, int nb = 1,
+                      size_t bstride = 0);
 // The inner sums of up to MAXG giant steps in one pass over the baby rotations (two
 // polynomials of nl limbs each; limb r has prime ids[r]):
 // o[g] (+)= sum_b a[b] * p[g][b] (p[g][b] null: zero diagonal), accumulating into o[g] when
@@ -257,7 +264,14 @@ struct BsgsGiants {
     int nb, ng;
     unsigned acc;
 };
-void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids);
+// A batch of nb ciphertexts sharing keys and plaintexts: ciphertext t's operands at + t dstr,
+// + t ostr and + t xstr words (which operand each stride moves is stated per call)
+struct KsBatch {
+    int nb = 1;
+    size_t dstr = 0, ostr = 0, xstr = 0;
+};
+// (bt: a batch of bt.nb ciphertexts, babies at a[b] + t dstr, outputs at o[g] + t ostr)
+void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids, const KsBatch& bt);
 // Baby rotations and giant-step inner sums in one pass, the babies never stored: for every
 // extended limb e and word j, baby b = (sum_d D_d(sigma_b) kb_b,d, sum_d D_d(sigma_b) ka_b,d)
 // + (P c0(sigma_b), 0) on the Q rows (b with kb null: the identity, (P c0, P c1) on the Q rows,
@@ -273,8 +287,9 @@ struct BsgsFused {
     unsigned acc;
 };
 // D [ndig][next][N] raised digits of c1; c0, c1 [nl][N]; s, sp: P mod q_i and Shoup
+// (bt: a batch of bt.nb ciphertexts, D at + t dstr, c0 and c1 at + t xstr, outputs at o[g] + t ostr)
 void bsgs_fused(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1, int nl,
-                int next, const int* ext_ids, const u64* s, const u64* sp);
+                int next, const int* ext_ids, const u64* s, const u64* sp, const KsBatch& bt);
 // o = sum_t w_t a_t (mod q per limb) for up to MAX terms: the integer-weighted sum of a
 // Chebyshev leaf in one pass.  Arrays of nl limbs, limb k with prime ids[k % lpp]; w[t][r]
 // is the weight's residue for limb index r < lpp, wp[t][r] its Shoup companion (passed by
@@ -292,7 +307,8 @@ void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void sub(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void neg(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, const int* ids, int lpp);
-void mul(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
+// bmod > 0: b broadcast, row k of a times row k % bmod of b (a plaintext times a batch)
+void mul(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp, int bmod = 0);
 // o += a * b
 void mul_acc(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 // o = a * s[limb % lpp] (s residues, sp their Shoup companions; device arrays)
@@ -306,7 +322,9 @@ void mul_scalar_v(const ckks_ctx* c, const u64* a, const ScalarVec& sv, u64* o, 
 // companions; a rows as in mul_scalar_v, b and out contiguous)
 void sub_mul2_scalar(const ckks_ctx* c, const u64* a, const u64* b, const ScalarVec& s1, const u64* s2,
                      const u64* s2p, u64* o, int nlimbs, const int* ids, int lpp, size_t a_pstride);
-void add_scalar_v(const ckks_ctx* c, u64* a, const ScalarVec& sv, int nlimbs, const int* ids, int lpp);
+// (a_pstride: row k of a at a + (k / lpp) * a_pstride + (k % lpp) * N)
+void add_scalar_v(const ckks_ctx* c, u64* a, const ScalarVec& sv, int nlimbs, const int* ids, int lpp,
+                  size_t a_pstride = 0);
 // a[limb][*] += v[limb]: adds the constant polynomial v in the NTT domain (device array v)
 void add_const_term(const ckks_ctx* c, u64* a, const u64* v, int nlimbs, const int* ids);
 // signed small ints (device int64 [N]) -> residues [nlimbs][N] (coefficient domain)
@@ -354,15 +372,21 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly);
 // += s[e] * x0[e](sigma_g) for e < x0rows (s null: unscaled), the automorphed c0 term of a
 // rotation, gathered with the same permutation as D; x1 (optional) likewise into oa (the
 // P-lifted d0, d1 of a relinearisation, g = 1)
+// (bt: a batch of bt.nb ciphertexts switched with the same key, D at + t dstr, ob / oa at + t ostr,
+// x0 / x1 at + t xstr; at most 4 digits)
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
               const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate = false, const u64* x0 = nullptr,
-              int x0rows = 0, const u64* s = nullptr, const u64* sp = nullptr, const u64* x1 = nullptr);
+              int x0rows = 0, const u64* s = nullptr, const u64* sp = nullptr, const u64* x1 = nullptr,
+              const KsBatch& bt = KsBatch());
 // d0 = a0 b0, d1 = a0 b1 + a1 b0 (d [2][nl][N]), d2 = a1 b1 (e [nl][N]) over nl limbs with
-// primes ids[0..nl); a, b [2][nl][N]
-void tensor(const ckks_ctx* c, const u64* a, const u64* b, u64* d, u64* e, int nl, const int* ids);
-// o += a * s[limb % lpp] (s residues, sp their Shoup companions; device arrays)
+// primes ids[0..nl); a, b [2][nl][N]; for a batch of nb ciphertexts, ciphertext t's operands at
+// a + t ab_bstride, b + t ab_bstride, d + t d_bstride, e + t e_bstride
+void tensor(const ckks_ctx* c, const u64* a, const u64* b, u64* d, u64* e, int nl, const int* ids, int nb = 1,
+            size_t ab_bstride = 0, size_t d_bstride = 0, size_t e_bstride = 0);
+// o += a * s[limb % lpp] (s residues, sp their Shoup companions; device arrays); o_pstride: row k
+// of o at o + (k / lpp) * o_pstride + (k % lpp) * N (a contiguous)
 void mul_scalar_acc(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nlimbs, const int* ids,
-                    int lpp);
+                    int lpp, size_t o_pstride = 0);
 // uniform residues in the NTT domain drawn from the counter stream (see ckks.h)
 void sample_uniform(const ckks_ctx* c, u64* o, int nlimbs, const int* ids, u64 key);
 void sample_small(const ckks_ctx* c, int64_t* o, u64 key, int kind /*0 ternary, 1 gauss*/);

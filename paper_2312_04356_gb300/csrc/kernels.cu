@@ -181,13 +181,13 @@ constexpr int NTT_THREADS = 256;
 template <bool INV>
 __global__ void __launch_bounds__(NTT_THREADS)
     k_ntt_pass(u64* __restrict__ data, const DevPrime* __restrict__ primes, const int* __restrict__ ids, int lpp,
-               int logn, int s0, int c, int logsub, int scale_out) {
+               size_t pstride, int logn, int s0, int c, int logsub, int scale_out) {
     griddep_entry();
     extern __shared__ u64 sm[];
     const int limb = blockIdx.y;
     const DevPrime* P = primes + ids[limb % lpp];
     const u64 q = P->m.q;
-    u64* a = data + ((size_t)limb << logn);
+    u64* a = data + (size_t)(limb / lpp) * pstride + ((size_t)(limb % lpp) << logn);
     const int span = 1 << c;
     const int SUB = 1 << logsub;
     const int stride = SUB > 1 ? SUB + 1 : 1;
@@ -341,11 +341,10 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
     griddep_entry();
     __shared__ u64 sm[SUBS * F_STRIDE];
     const int limb = blockIdx.y;
-    const int r = loff ? limb : limb % lpp;
+    const int r = limb % lpp;
     const DevPrime* P = primes + ids[r];
     const u64 q = P->m.q, q2 = 2 * q;
-    u64* a = loff ? data + ((size_t)loff[limb] << 16)
-                  : data + (size_t)(limb / lpp) * pstride + ((size_t)r << 16);
+    u64* a = data + (size_t)(limb / lpp) * pstride + ((size_t)(loff ? loff[r] : r) << 16);
     const int tid = threadIdx.x;
     const int sp = COL ? (tid % SUBS) : (tid >> 4);
     const int t = COL ? (tid / SUBS) : (tid & 15);
@@ -429,10 +428,10 @@ __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const De
     griddep_entry();
     __shared__ u64 sm[4 * F_STRIDE];
     const int limb = blockIdx.y;
-    const int r = loff ? limb : limb % lpp;
+    const int r = limb % lpp;
     const DevPrime* P = primes + ids[r];
     const u64 q = P->m.q, q2 = 2 * q;
-    u64* a = loff ? data + ((size_t)loff[limb] << 16) : data + (size_t)(limb / lpp) * pstride + ((size_t)r << 16);
+    u64* a = data + (size_t)(limb / lpp) * pstride + ((size_t)(loff ? loff[r] : r) << 16);
     const int tid = threadIdx.x;
     const int sp = COL ? (tid & 3) : (tid >> 6);
     const int t = COL ? (tid >> 2) : (tid & 63);
@@ -552,10 +551,10 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(CL_THREADS, 2)
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int limb = blockIdx.y;
-    const int r = loff ? limb : limb % lpp;
+    const int r = limb % lpp;
     const DevPrime* P = primes + ids[r];
     const u64 q = P->m.q, q2 = 2 * q;
-    u64* a = loff ? data + ((size_t)loff[limb] << 16) : data + (size_t)(limb / lpp) * pstride + ((size_t)r << 16);
+    u64* a = data + (size_t)(limb / lpp) * pstride + ((size_t)(loff ? loff[r] : r) << 16);
     const int tid = threadIdx.x;
     // COL mapping: column 32 rank + spc, elements (rows) t + 16 i / 16 t + i
     const int spc = tid % CL_SUBS, tc = tid / CL_SUBS, col = CL_SUBS * rank + spc;
@@ -731,7 +730,8 @@ inline std::vector<PassPlan> ntt_passes(int logn) {
 }
 
 template <bool INV>
-void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, PassPlan p, int scale_out) {
+void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride, PassPlan p,
+                 int scale_out) {
     const int logn = cx->logn;
     int logsub = 12 - p.c;
     if (logsub < 0) logsub = 0;
@@ -742,7 +742,8 @@ void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int 
     const size_t smem = (size_t)stride * (1 << p.c) * sizeof(u64);
     dim3 grid(tiles, nlimbs);
     { KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0 * p.c / logn);
-    klaunch(cx, k_ntt_pass<INV>, grid, NTT_THREADS, smem, data, cx->d_primes, ids, lpp, logn, p.s0, p.c, logsub,
+    klaunch(cx, k_ntt_pass<INV>, grid, NTT_THREADS, smem, data, cx->d_primes, ids, lpp, pstride, logn, p.s0, p.c,
+            logsub,
             scale_out);
     }
 }
@@ -825,29 +826,38 @@ __global__ void k_neg(const u64* a, u64* o, const DevPrime* P, const int* ids, i
     for (int v = 0; v < V; ++v) x[v] = neg_mod(x[v], q);
     stv<V>(o + off + j, x);
 }
+// bmod > 0: b is broadcast, row limb % bmod of b multiplies row limb of a (one plaintext times
+// every polynomial of a batch of ciphertexts)
 template <int V>
-__global__ void k_mul(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn) {
+__global__ void k_mul(const u64* a, const u64* b, u64* o, const DevPrime* P, const int* ids, int lpp, int logn,
+                      int bmod) {
     griddep_entry();
     const int limb = blockIdx.y;
     const DevMod m = P[ids[limb % lpp]].m;
     const size_t off = (size_t)limb << logn;
+    const size_t boff = (size_t)(bmod ? limb % bmod : limb) << logn;
     EWV_BEGIN(1 << logn)
     u64 x[V], y[V];
     ldv<V>(a + off + j, x);
-    ldv<V>(b + off + j, y);
+    ldv<V>(b + boff + j, y);
 #pragma unroll
     for (int v = 0; v < V; ++v) x[v] = mul_mod(x[v], y[v], m);
     stv<V>(o + off + j, x);
 }
 // tensor product of two ciphertexts: d0 = a0 b0, d1 = a0 b1 + a1 b0 (d [2][nl][N]), d2 = a1 b1
 // (e [nl][N]); a, b [2][nl][N]; one pass over the nl limbs
+// blockIdx.z: ciphertext t of a batch, its operands at a + t abs, b + t abs, d + t dbs, e + t ebs
 template <int V>
 __global__ void k_tensor(const u64* a, const u64* b, u64* d, u64* e, const DevPrime* P, const int* ids, int nl,
-                         int logn) {
+                         int logn, size_t abs, size_t dbs, size_t ebs) {
     griddep_entry();
     const int limb = blockIdx.y;
     const DevMod m = P[ids[limb]].m;
     const size_t off = (size_t)limb << logn, ps = (size_t)nl << logn;
+    a += blockIdx.z * abs;
+    b += blockIdx.z * abs;
+    d += blockIdx.z * dbs;
+    e += blockIdx.z * ebs;
     EWV_BEGIN(1 << logn)
     u64 a0[V], a1[V], b0[V], b1[V], d0[V], d1[V], d2[V];
     ldv<V>(a + off + j, a0);
@@ -934,14 +944,16 @@ __global__ void k_lincomb(const __grid_constant__ kern::LinComb T, u64* __restri
     }
     stv<V>(o + off + j, acc);
 }
+// ps > 0: row limb of a at (limb / lpp) ps + (limb % lpp) N (e.g. c0 of every ciphertext of a batch)
 template <int V>
-__global__ void k_add_scalar_v(u64* a, ScalarVec sv, const DevPrime* P, const int* ids, int lpp, int logn) {
+__global__ void k_add_scalar_v(u64* a, ScalarVec sv, const DevPrime* P, const int* ids, int lpp, int logn,
+                               size_t ps) {
     griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
     const u64 c = sv.v[r];
-    const size_t off = (size_t)limb << logn;
+    const size_t off = ps ? (size_t)(limb / lpp) * ps + ((size_t)r << logn) : (size_t)limb << logn;
     EWV_BEGIN(1 << logn)
     u64 x[V];
     ldv<V>(a + off + j, x);
@@ -1079,14 +1091,18 @@ __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const
 __device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P) {
     return add_mod(mul_shoup(hi, P.r64, P.r64p, P.m.q), reduce64(lo, P.m), P.m.q);
 }
+// blockIdx.y = row * nbt + t: ciphertext t of a batch (babies at T.a[b] + t astr, outputs at
+// T.o[g] + t ostr; the diagonals are shared and read by neighbouring CTAs)
 template <int V, int NG>
 __global__ void k_bsgs_inner_giants(kern::BsgsGiants T, const DevPrime* __restrict__ primes, int nl,
-                                    const int* __restrict__ ids, int logn) {
+                                    const int* __restrict__ ids, int logn, int nbt, size_t astr, size_t ostr) {
     griddep_entry();
-    const int limb = blockIdx.y;           // 0 .. 2 nl - 1, polynomial-major
+    const int t = blockIdx.y % nbt;
+    const int limb = blockIdx.y / nbt;     // 0 .. 2 nl - 1, polynomial-major
     const int r = limb % nl;
     const DevPrime P = primes[ids[r]];
-    const size_t offa = (size_t)limb << logn, offp = (size_t)r << logn;
+    const size_t offa = t * astr + ((size_t)limb << logn), offo = t * ostr + ((size_t)limb << logn);
+    const size_t offp = (size_t)r << logn;
     EWV_BEGIN(1 << logn)
     u64 lo[NG][V], hi[NG][V];
 #pragma unroll
@@ -1117,11 +1133,11 @@ __global__ void k_bsgs_inner_giants(kern::BsgsGiants T, const DevPrime* __restri
         for (int v = 0; v < V; ++v) res[v] = reduce128_lazy(hi[g][v], lo[g][v], P);
         if ((T.acc >> g) & 1u) {
             u64 prev[V];
-            ldv<V>(T.o[g] + offa + j, prev);
+            ldv<V>(T.o[g] + offo + j, prev);
 #pragma unroll
             for (int v = 0; v < V; ++v) res[v] = add_mod(res[v], prev[v], P.m.q);
         }
-        stv<V>(T.o[g] + offa + j, res);
+        stv<V>(T.o[g] + offo + j, res);
     }
 }
 
@@ -1147,7 +1163,7 @@ __global__ void __launch_bounds__(256, 3)
     k_bsgs_fused_async(const __grid_constant__ kern::BsgsFused T, const u64* __restrict__ D,
                        const u64* __restrict__ c0, const u64* __restrict__ c1, int nl, int next,
                        const int* __restrict__ ext_ids, const u64* __restrict__ s0, const u64* __restrict__ s0p,
-                       const DevPrime* __restrict__ P, int logn, size_t kstride) {
+                       const DevPrime* __restrict__ P, int logn, size_t kstride, kern::KsBatch bt) {
     griddep_entry();
     constexpr int NS = 3 * NDIG + 2 + NG;       // kb, ka, D per digit; c0 (gathered or row); c1 row; diagonals
     extern __shared__ u64 sbuf[];               // [2][NS][256]
@@ -1159,8 +1175,15 @@ __global__ void __launch_bounds__(256, 3)
     const bool qrow = e < nl;
     const u64 w = qrow ? s0[e] : 0, wp = qrow ? s0p[e] : 0;
     const int tid = threadIdx.x;
-    const int j = blockIdx.x * 256 + tid;
+    // ciphertext t of a batch (fastest varying, so that the CTAs reading the same key and diagonal
+    // words run side by side and share them through L2): D + t dstr, c0 / c1 + t xstr, outputs
+    // + t ostr
+    const int t = blockIdx.x % bt.nb;
+    const int j = (blockIdx.x / bt.nb) * 256 + tid;
     if (j >= (int)n) return;
+    D += t * bt.dstr;
+    c0 += t * bt.xstr;
+    c1 += t * bt.xstr;
     auto slot = [&](int st, int k) -> u64* { return sbuf + ((size_t)(st * NS + k) << 8) + tid; };
     auto issue = [&](int b, int st) {
         if (!T.kb[b]) {
@@ -1232,8 +1255,8 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
         u64 vb = reduce128_lazy(hib[g], lob[g], pr), va = reduce128_lazy(hia[g], loa[g], pr);
-        u64* ob = T.o[g] + (size_t)e * n + j;
-        u64* oa = T.o[g] + ((size_t)next + e) * n + j;
+        u64* ob = T.o[g] + t * bt.ostr + (size_t)e * n + j;
+        u64* oa = T.o[g] + t * bt.ostr + ((size_t)next + e) * n + j;
         if ((T.acc >> g) & 1u) {
             vb = add_mod(vb, *ob, q);
             va = add_mod(va, *oa, q);
@@ -1424,18 +1447,29 @@ __global__ void k_ks_inner(const u64* __restrict__ D, int ndig, int next, const 
 // The same product for a digit count fixed at compile time: every digit's key words and
 // gathered input are loaded before any arithmetic, the products are summed exactly in 128 bits
 // (each < 2^122, at most 4 terms) and reduced once per output word.
+// A batch of bt.nb key switches with the same key: ciphertext t's digits at D + t dstr, its
+// outputs at ob / oa + t ostr, its x0 / x1 at + t xstr.  The ciphertext index is the fastest
+// varying part of blockIdx.x, so the CTAs that read the same key words run side by side and
+// all but the first find them in L2: the key streams from HBM about once per batch.
 template <bool ACC, int V, int NDIG>
 __global__ void k_ks_inner_d(const u64* __restrict__ D, int next, const int* __restrict__ ext_ids,
                              const u64* __restrict__ kb, const u64* __restrict__ ka, u64* __restrict__ ob,
                              u64* __restrict__ oa, const DevPrime* __restrict__ P, int logn, u64 g, size_t kstride,
                              const u64* __restrict__ x0, const u64* __restrict__ x1, int x0rows,
-                             const u64* __restrict__ s0, const u64* __restrict__ s0p) {
+                             const u64* __restrict__ s0, const u64* __restrict__ s0p, kern::KsBatch bt) {
     griddep_entry();
     const int e = blockIdx.y;
     const int id = ext_ids[e];
     const DevPrime pr = P[id];
     const size_t n = (size_t)1 << logn;
-    EWV_BEGIN(1 << logn)
+    const int t = blockIdx.x % bt.nb;
+    const int j = V * ((blockIdx.x / bt.nb) * blockDim.x + threadIdx.x);
+    if (j >= (int)n) return;
+    D += t * bt.dstr;
+    ob += t * bt.ostr;
+    oa += t * bt.ostr;
+    if (x0) x0 += t * bt.xstr;
+    if (x1) x1 += t * bt.xstr;
     unsigned src[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) src[v] = g == 1 ? (unsigned)(j + v) : galois_src(j + v, g, logn);
@@ -1444,8 +1478,13 @@ __global__ void k_ks_inner_d(const u64* __restrict__ D, int next, const int* __r
     for (int d = 0; d < NDIG; ++d) {
         const u64* Dd = D + ((size_t)d * next + e) * n;
         const size_t kk = d * kstride + (size_t)id * n + j;
-        ldv_cs<V>(kb + kk, yb[d]);   // each key word is read once per key switch: keep the
-        ldv_cs<V>(ka + kk, ya[d]);   // raised digits, which every rotation re-reads, in L2
+        if (bt.nb == 1) {
+            ldv_cs<V>(kb + kk, yb[d]);   // each key word is read once per key switch: keep the
+            ldv_cs<V>(ka + kk, ya[d]);   // raised digits, which every rotation re-reads, in L2
+        } else {
+            ldv<V>(kb + kk, yb[d]);      // the other ciphertexts of the batch read them next
+            ldv<V>(ka + kk, ya[d]);
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) x[d][v] = Dd[src[v]];
     }
@@ -1500,21 +1539,23 @@ __global__ void k_ks_inner_d(const u64* __restrict__ D, int next, const int* __r
 
 // o += a * s[limb % lpp] (Shoup pairs s, sp)
 template <int V>
+// o_ps > 0: row limb of o at (limb / lpp) o_ps + (limb % lpp) N (a contiguous)
 __global__ void k_mul_scalar_acc(const u64* a, const u64* s, const u64* sp, u64* o, const DevPrime* P, const int* ids,
-                                 int lpp, int logn) {
+                                 int lpp, int logn, size_t o_ps) {
     griddep_entry();
     const int limb = blockIdx.y;
     const int r = limb % lpp;
     const u64 q = P[ids[r]].m.q;
     const u64 w = s[r], wp = sp[r];
     const size_t off = (size_t)limb << logn;
+    const size_t ooff = o_ps ? (size_t)(limb / lpp) * o_ps + ((size_t)r << logn) : off;
     EWV_BEGIN(1 << logn)
     u64 x[V], z[V];
     ldv<V>(a + off + j, x);
-    ldv<V>(o + off + j, z);
+    ldv<V>(o + ooff + j, z);
 #pragma unroll
     for (int v = 0; v < V; ++v) z[v] = add_mod(z[v], mul_shoup(x[v], w, wp, q), q);
-    stv<V>(o + off + j, z);
+    stv<V>(o + ooff + j, z);
 }
 
 // ------------------------------------------------------------ sampling ----
@@ -1568,8 +1609,7 @@ void ntt_forward(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
         LAUNCH_CHECK();
         return;
     }
-    CK_CHECK(pstride == (size_t)lpp * c->n, CKKS_EINVAL, "strided polynomials need N = 2^16");
-    for (const PassPlan& p : ntt_passes(c->logn)) launch_pass<false>(c, data, nlimbs, ids, lpp, p, 0);
+    for (const PassPlan& p : ntt_passes(c->logn)) launch_pass<false>(c, data, nlimbs, ids, lpp, pstride, p, 0);
     LAUNCH_CHECK();
 }
 
@@ -1616,29 +1656,34 @@ void autotune_ntt(ckks_ctx* c, int reps) {
     LAUNCH_CHECK();
 }
 
-void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, const int* ids) {
-    if (nlimbs <= 0) return;
+void ntt_forward_list(const ckks_ctx* c, u64* data, int nlimbs, const int* off, const int* ids, int nb,
+                      size_t bstride) {
+    if (nlimbs <= 0 || nb <= 0) return;
     CK_CHECK(c->logn == 16, CKKS_EINVAL, "limb-list NTT needs N = 2^16");
-    launch_ntt_transform<false>(c, data, nlimbs, ids, nlimbs, 0, off);
+    launch_ntt_transform<false>(c, data, nlimbs * nb, ids, nlimbs, bstride, off);
     LAUNCH_CHECK();
 }
 
 template <int V>
-static void launch_bsgs_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids) {
-    const dim3 grid = ewv_grid(c->n, 2 * nl, V);
+static void launch_bsgs_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids, const KsBatch& bt) {
+    const dim3 grid = ewv_grid(c->n, 2 * nl * bt.nb, V);
+#define GIANTS_CASE(NG)                                                                                         \
+    klaunch(c, k_bsgs_inner_giants<V, NG>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn, bt.nb, bt.dstr, \
+            bt.ostr)
     switch (t.ng) {
-        case 1: klaunch(c, k_bsgs_inner_giants<V, 1>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
-        case 2: klaunch(c, k_bsgs_inner_giants<V, 2>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
-        case 3: klaunch(c, k_bsgs_inner_giants<V, 3>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
-        case 4: klaunch(c, k_bsgs_inner_giants<V, 4>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
-        case 5: klaunch(c, k_bsgs_inner_giants<V, 5>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
-        case 6: klaunch(c, k_bsgs_inner_giants<V, 6>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
-        case 7: klaunch(c, k_bsgs_inner_giants<V, 7>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
-        default: klaunch(c, k_bsgs_inner_giants<V, 8>, grid, EW_THREADS, 0, t, c->d_primes, nl, ids, c->logn); break;
+        case 1: GIANTS_CASE(1); break;
+        case 2: GIANTS_CASE(2); break;
+        case 3: GIANTS_CASE(3); break;
+        case 4: GIANTS_CASE(4); break;
+        case 5: GIANTS_CASE(5); break;
+        case 6: GIANTS_CASE(6); break;
+        case 7: GIANTS_CASE(7); break;
+        default: GIANTS_CASE(8); break;
     }
+#undef GIANTS_CASE
 }
 
-void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids) {
+void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int* ids, const KsBatch& bt) {
     CK_CHECK(t.nb >= 1 && t.nb <= BsgsGiants::MAXB && t.ng >= 1 && t.ng <= BsgsGiants::MAXG, CKKS_EINVAL,
              "1..32 baby steps and 1..8 giant steps per inner-sum launch");
     int terms = 0;
@@ -1657,50 +1702,51 @@ void bsgs_inner_giants(const ckks_ctx* c, const BsgsGiants& t, int nl, const int
         // output written (and read when accumulating)
         int accs = 0;
         for (int g = 0; g < t.ng; ++g) accs += (t.acc >> g) & 1u;
-        KTimer kt_(c, "bsgs_inner", (2.0 * t.nb + terms + 2.0 * t.ng + 2.0 * accs) * nl * c->n * 8.0);
+        KTimer kt_(c, "bsgs_inner", (bt.nb * (2.0 * t.nb + 2.0 * t.ng + 2.0 * accs) + terms) * nl * c->n * 8.0);
         if (vec)
-            launch_bsgs_giants<2>(c, t, nl, ids);
+            launch_bsgs_giants<2>(c, t, nl, ids, bt);
         else
-            launch_bsgs_giants<1>(c, t, nl, ids);
+            launch_bsgs_giants<1>(c, t, nl, ids, bt);
     }
     LAUNCH_CHECK();
 }
 
 template <int NDIG, int NG>
 static void launch_bsgs_async_one(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0,
-                                  const u64* c1, int nl, int next, const int* ext, const u64* s, const u64* sp) {
+                                  const u64* c1, int nl, int next, const int* ext, const u64* s, const u64* sp,
+                                  const KsBatch& bt) {
     constexpr int NS = 3 * NDIG + 2 + NG;
     const size_t smem = 2 * (size_t)NS * 256 * sizeof(u64);
     static std::atomic<unsigned> done{0};
     allow_dynamic_smem((const void*)k_bsgs_fused_async<NDIG, NG>, (int)smem, done);
-    const dim3 grid((c->n + 255) / 256, next);
+    const dim3 grid((c->n + 255) / 256 * bt.nb, next);
     klaunch(c, k_bsgs_fused_async<NDIG, NG>, grid, 256, smem, t, D, c0, c1, nl, next, ext, s, sp, c->d_primes,
-            c->logn, (size_t)c->nall << c->logn);
+            c->logn, (size_t)c->nall << c->logn, bt);
 }
 
 template <int NDIG>
 static void launch_bsgs_async_g(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1,
-                                int nl, int next, const int* ext, const u64* s, const u64* sp) {
+                                int nl, int next, const int* ext, const u64* s, const u64* sp, const KsBatch& bt) {
     switch (t.ng) {
-        case 1: launch_bsgs_async_one<NDIG, 1>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
-        case 2: launch_bsgs_async_one<NDIG, 2>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
-        case 3: launch_bsgs_async_one<NDIG, 3>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
-        default: launch_bsgs_async_one<NDIG, 4>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        case 1: launch_bsgs_async_one<NDIG, 1>(c, t, D, c0, c1, nl, next, ext, s, sp, bt); break;
+        case 2: launch_bsgs_async_one<NDIG, 2>(c, t, D, c0, c1, nl, next, ext, s, sp, bt); break;
+        case 3: launch_bsgs_async_one<NDIG, 3>(c, t, D, c0, c1, nl, next, ext, s, sp, bt); break;
+        default: launch_bsgs_async_one<NDIG, 4>(c, t, D, c0, c1, nl, next, ext, s, sp, bt); break;
     }
 }
 
 static void launch_bsgs_async(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1,
-                              int nl, int next, const int* ext, const u64* s, const u64* sp) {
+                              int nl, int next, const int* ext, const u64* s, const u64* sp, const KsBatch& bt) {
     switch (t.ndig) {
-        case 1: launch_bsgs_async_g<1>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
-        case 2: launch_bsgs_async_g<2>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
-        case 3: launch_bsgs_async_g<3>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
-        default: launch_bsgs_async_g<4>(c, t, D, c0, c1, nl, next, ext, s, sp); break;
+        case 1: launch_bsgs_async_g<1>(c, t, D, c0, c1, nl, next, ext, s, sp, bt); break;
+        case 2: launch_bsgs_async_g<2>(c, t, D, c0, c1, nl, next, ext, s, sp, bt); break;
+        case 3: launch_bsgs_async_g<3>(c, t, D, c0, c1, nl, next, ext, s, sp, bt); break;
+        default: launch_bsgs_async_g<4>(c, t, D, c0, c1, nl, next, ext, s, sp, bt); break;
     }
 }
 
 void bsgs_fused(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* c0, const u64* c1, int nl,
-                int next, const int* ext_ids, const u64* s, const u64* sp) {
+                int next, const int* ext_ids, const u64* s, const u64* sp, const KsBatch& bt) {
     CK_CHECK(t.nb >= 1 && t.nb <= BsgsFused::MAXB && t.ng >= 1 && t.ng <= BsgsFused::MAXG && t.ndig >= 1 &&
                  t.ndig <= 4, CKKS_EINVAL, "fused BSGS: 1..32 babies, 1..4 giant steps, 1..4 digits");
     int terms = 0, rots = 0;
@@ -1714,10 +1760,12 @@ void bsgs_fused(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* 
     {
         // algorithmic bytes: per rotation the digits, both key halves and c0 on the Q rows; the
         // identity's c0 and c1; every diagonal once; each giant's output (read when accumulating)
-        const double limbs = (double)rots * (3.0 * t.ndig * next + nl) / next + (t.nb - rots) * 2.0 * nl / next +
-                             terms + 2.0 * t.ng + 2.0 * accs;
-        KTimer kt_(c, "bsgs_fused", limbs * next * c->n * 8.0);
-        launch_bsgs_async(c, t, D, c0, c1, nl, next, ext_ids, s, sp);
+        // (a batch reads the keys and diagonals once, and its ciphertexts' own words each)
+        const double shared = (double)rots * 2.0 * t.ndig + terms;
+        const double own = (double)rots * (t.ndig * next + nl) / next + (t.nb - rots) * 2.0 * nl / next +
+                           2.0 * t.ng + 2.0 * accs;
+        KTimer kt_(c, "bsgs_fused", (shared + bt.nb * own) * next * c->n * 8.0);
+        launch_bsgs_async(c, t, D, c0, c1, nl, next, ext_ids, s, sp, bt);
     }
     LAUNCH_CHECK();
 }
@@ -1730,10 +1778,9 @@ void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
         LAUNCH_CHECK();
         return;
     }
-    CK_CHECK(pstride == (size_t)lpp * c->n, CKKS_EINVAL, "strided polynomials need N = 2^16");
     std::vector<PassPlan> ps = ntt_passes(c->logn);
     for (int i = (int)ps.size() - 1; i >= 0; --i)
-        launch_pass<true>(c, data, nlimbs, ids, lpp, ps[i], ps[i].s0 == 0 ? 1 : 0);
+        launch_pass<true>(c, data, nlimbs, ids, lpp, pstride, ps[i], ps[i].s0 == 0 ? 1 : 0);
     LAUNCH_CHECK();
 }
 
@@ -1758,17 +1805,26 @@ void neg(const ckks_ctx* c, const u64* a, u64* o, int nl, const int* ids, int lp
     }
     LAUNCH_CHECK();
 }
-void mul(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {
+void mul(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp, int bmod) {
     if (nl <= 0) return;
-    { KTimer kt_(c, "mul", 3.0 * (double)nl * c->n * 8.0);
-    EWV_LAUNCH(k_mul, al16(a) && al16(b) && al16(o), nl, a, b, o, c->d_primes, ids, lpp, c->logn);
+    { KTimer kt_(c, "mul", (bmod ? 2.0 + (double)bmod / nl : 3.0) * (double)nl * c->n * 8.0);
+    EWV_LAUNCH(k_mul, al16(a) && al16(b) && al16(o), nl, a, b, o, c->d_primes, ids, lpp, c->logn, bmod);
     }
     LAUNCH_CHECK();
 }
-void tensor(const ckks_ctx* c, const u64* a, const u64* b, u64* d, u64* e, int nl, const int* ids) {
-    if (nl <= 0) return;
-    { KTimer kt_(c, "tensor", 7.0 * (double)nl * c->n * 8.0);
-    EWV_LAUNCH(k_tensor, al16(a) && al16(b) && al16(d) && al16(e), nl, a, b, d, e, c->d_primes, ids, nl, c->logn);
+void tensor(const ckks_ctx* c, const u64* a, const u64* b, u64* d, u64* e, int nl, const int* ids, int nb,
+            size_t ab_bstride, size_t d_bstride, size_t e_bstride) {
+    if (nl <= 0 || nb <= 0) return;
+    const bool vec = al16(a) && al16(b) && al16(d) && al16(e);
+    dim3 grid = ewv_grid(c->n, nl, vec ? 2 : 1);
+    grid.z = nb;
+    { KTimer kt_(c, "tensor", 7.0 * (double)nl * nb * c->n * 8.0);
+    if (vec)
+        klaunch(c, k_tensor<2>, grid, EW_THREADS, 0, a, b, d, e, c->d_primes, ids, nl, c->logn, ab_bstride, d_bstride,
+                e_bstride);
+    else
+        klaunch(c, k_tensor<1>, grid, EW_THREADS, 0, a, b, d, e, c->d_primes, ids, nl, c->logn, ab_bstride, d_bstride,
+                e_bstride);
     }
     LAUNCH_CHECK();
 }
@@ -1818,11 +1874,12 @@ void lincomb(const ckks_ctx* c, const LinComb& t, u64* o, int nl, const int* ids
     }
     LAUNCH_CHECK();
 }
-void add_scalar_v(const ckks_ctx* c, u64* a, const ScalarVec& sv, int nl, const int* ids, int lpp) {
+void add_scalar_v(const ckks_ctx* c, u64* a, const ScalarVec& sv, int nl, const int* ids, int lpp,
+                  size_t a_pstride) {
     if (nl <= 0) return;
     CK_CHECK(lpp <= ScalarVec::MAX, CKKS_EINVAL, "too many limbs for a by-value scalar vector");
     { KTimer kt_(c, "add_scalar", 2.0 * (double)nl * c->n * 8.0);
-    EWV_LAUNCH(k_add_scalar_v, al16(a), nl, a, sv, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_add_scalar_v, al16(a) && a_pstride % 2 == 0, nl, a, sv, c->d_primes, ids, lpp, c->logn, a_pstride);
     }
     LAUNCH_CHECK();
 }
@@ -1962,25 +2019,26 @@ void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
 template <bool ACC, int V>
 static void launch_ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
                             const u64* ka, u64* ob, u64* oa, u64 g, const u64* x0, const u64* x1, int x0rows,
-                            const u64* s0, const u64* s0p) {
-    const dim3 grid = ewv_grid(c->n, next, V);
+                            const u64* s0, const u64* s0p, const KsBatch& bt) {
+    dim3 grid = ewv_grid(c->n, next, V);
+    grid.x *= bt.nb;
     const size_t ks = (size_t)c->nall << c->logn;
     switch (ndig) {
         case 1:
             klaunch(c, k_ks_inner_d<ACC, V, 1>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks, x0, x1, x0rows, s0, s0p);
+                    c->logn, g, ks, x0, x1, x0rows, s0, s0p, bt);
             break;
         case 2:
             klaunch(c, k_ks_inner_d<ACC, V, 2>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks, x0, x1, x0rows, s0, s0p);
+                    c->logn, g, ks, x0, x1, x0rows, s0, s0p, bt);
             break;
         case 3:
             klaunch(c, k_ks_inner_d<ACC, V, 3>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks, x0, x1, x0rows, s0, s0p);
+                    c->logn, g, ks, x0, x1, x0rows, s0, s0p, bt);
             break;
         case 4:
             klaunch(c, k_ks_inner_d<ACC, V, 4>, grid, EW_THREADS, 0, D, next, ext_ids, kb, ka, ob, oa, c->d_primes,
-                    c->logn, g, ks, x0, x1, x0rows, s0, s0p);
+                    c->logn, g, ks, x0, x1, x0rows, s0, s0p, bt);
             break;
         default:
             klaunch(c, k_ks_inner<ACC, V>, grid, EW_THREADS, 0, D, ndig, next, ext_ids, kb, ka, ob, oa, c->d_primes,
@@ -1991,24 +2049,28 @@ static void launch_ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next,
 
 void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ext_ids, const u64* kb,
               const u64* ka, u64* ob, u64* oa, u64 g, bool accumulate, const u64* x0, int x0rows, const u64* s,
-              const u64* sp, const u64* x1) {
+              const u64* sp, const u64* x1, const KsBatch& bt) {
+    CK_CHECK(bt.nb >= 1 && (bt.nb == 1 || ndig <= 4), CKKS_EINVAL, "batched key switching needs at most 4 digits");
     const bool vec = al16(kb) && al16(ka) && al16(ob) && al16(oa);
     const bool fuse = x0 && x0rows > 0 && ndig <= 4;   // the generic kernel adds x0, x1 in further passes
     {
+        // algorithmic bytes: the key once for the whole batch, per ciphertext its digits, outputs
+        // (read too when accumulating) and the x0 / x1 rows
         const double extra = fuse ? (double)x0rows * (x1 ? 2.0 : 1.0) / next : 0.0;
-        KTimer kt_(c, "ks_inner", (3.0 * ndig + (accumulate ? 4.0 : 2.0) + extra) * next * c->n * 8.0);
+        KTimer kt_(c, "ks_inner",
+                   (2.0 * ndig + bt.nb * (ndig + (accumulate ? 4.0 : 2.0) + extra)) * next * c->n * 8.0);
         const u64* fx = fuse ? x0 : nullptr;
         const u64* fy = fuse ? x1 : nullptr;
         if (accumulate) {
             if (vec)
-                launch_ks_inner<true, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp);
+                launch_ks_inner<true, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp, bt);
             else
-                launch_ks_inner<true, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp);
+                launch_ks_inner<true, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp, bt);
         } else {
             if (vec)
-                launch_ks_inner<false, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp);
+                launch_ks_inner<false, 2>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp, bt);
             else
-                launch_ks_inner<false, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp);
+                launch_ks_inner<false, 1>(c, D, ndig, next, ext_ids, kb, ka, ob, oa, g, fx, fy, x0rows, s, sp, bt);
         }
     }
     LAUNCH_CHECK();
@@ -2018,10 +2080,11 @@ void ks_inner(const ckks_ctx* c, const u64* D, int ndig, int next, const int* ex
     }
 }
 void mul_scalar_acc(const ckks_ctx* c, const u64* a, const u64* s, const u64* sp, u64* o, int nl, const int* ids,
-                    int lpp) {
+                    int lpp, size_t o_pstride) {
     if (nl <= 0) return;
     { KTimer kt_(c, "mul_scalar_acc", 3.0 * (double)nl * c->n * 8.0);
-    EWV_LAUNCH(k_mul_scalar_acc, al16(a) && al16(o), nl, a, s, sp, o, c->d_primes, ids, lpp, c->logn);
+    EWV_LAUNCH(k_mul_scalar_acc, al16(a) && al16(o) && o_pstride % 2 == 0, nl, a, s, sp, o, c->d_primes, ids, lpp,
+               c->logn, o_pstride);
     }
     LAUNCH_CHECK();
 }

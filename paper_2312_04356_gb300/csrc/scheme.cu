@@ -341,28 +341,30 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
 // ============================================================ helpers ======
 namespace ops {
 
-void ensure_ct(ckks_ct& ct, ckks_ctx* c, int level) {
+void ensure_ct(ckks_ct& ct, ckks_ctx* c, int level, int nb) {
     ct.ctx = c;
-    size_t need = 2 * (size_t)(level + 1) * c->n;
+    size_t need = (size_t)nb * 2 * (size_t)(level + 1) * c->n;
     if (ct.buf.words < need || ct.buf.ptr == nullptr) ct.buf = DevBuf(need, c->stream);
     ct.level = level;
+    ct.nb = nb;
 }
 
-ckks_ct new_ct(ckks_ctx* c, int level, double scale) {
+ckks_ct new_ct(ckks_ctx* c, int level, double scale, int nb) {
     ckks_ct ct;
-    ensure_ct(ct, c, level);
+    ensure_ct(ct, c, level, nb);
     ct.scale = scale;
     return ct;
 }
 
 ckks_ct copy_ct(const ckks_ct& a) {
-    ckks_ct o = new_ct(a.ctx, a.level, a.scale);
-    CUDA_CHECK(cudaMemcpyAsync(o.buf.ptr, a.buf.ptr, 2 * (size_t)(a.level + 1) * a.ctx->n * 8,
-                               cudaMemcpyDeviceToDevice, a.ctx->stream));
+    ckks_ct o = new_ct(a.ctx, a.level, a.scale, a.nb);
+    CUDA_CHECK(cudaMemcpyAsync(o.buf.ptr, a.buf.ptr, a.nb * a.cstride() * 8, cudaMemcpyDeviceToDevice,
+                               a.ctx->stream));
     return o;
 }
 
 static void check_same(const ckks_ct& a, const ckks_ct& b) {
+    CK_CHECK(a.nb == b.nb, CKKS_EINVAL, "batch sizes differ");
     CK_CHECK(a.level == b.level, CKKS_EINVAL, "ciphertext levels differ");
     CK_CHECK(fabs(a.scale - b.scale) <= ldexp(1.0, -30) * fabs(a.scale), CKKS_EINVAL, "ciphertext scales differ");
 }
@@ -370,16 +372,16 @@ static void check_same(const ckks_ct& a, const ckks_ct& b) {
 ckks_ct add(const ckks_ct& a, const ckks_ct& b) {
     check_same(a, b);
     ckks_ctx* c = a.ctx;
-    ckks_ct o = new_ct(c, a.level, a.scale);
-    kern::add(c, a.buf.ptr, b.buf.ptr, o.buf.ptr, 2 * (a.level + 1), c->d_iota, a.level + 1);
+    ckks_ct o = new_ct(c, a.level, a.scale, a.nb);
+    kern::add(c, a.buf.ptr, b.buf.ptr, o.buf.ptr, 2 * (a.level + 1) * a.nb, c->d_iota, a.level + 1);
     return o;
 }
 
 ckks_ct sub(const ckks_ct& a, const ckks_ct& b) {
     check_same(a, b);
     ckks_ctx* c = a.ctx;
-    ckks_ct o = new_ct(c, a.level, a.scale);
-    kern::sub(c, a.buf.ptr, b.buf.ptr, o.buf.ptr, 2 * (a.level + 1), c->d_iota, a.level + 1);
+    ckks_ct o = new_ct(c, a.level, a.scale, a.nb);
+    kern::sub(c, a.buf.ptr, b.buf.ptr, o.buf.ptr, 2 * (a.level + 1) * a.nb, c->d_iota, a.level + 1);
     return o;
 }
 
@@ -387,16 +389,17 @@ ckks_ct mul_plain(const ckks_ct& a, const ckks_pt& p) {
     CK_CHECK(p.level == a.level, CKKS_EINVAL, "plaintext level differs from the ciphertext level");
     ckks_ctx* c = a.ctx;
     c->ops["pmult"]++;
-    ckks_ct o = new_ct(c, a.level, a.scale * p.scale);
+    ckks_ct o = new_ct(c, a.level, a.scale * p.scale, a.nb);
     const int nl = a.level + 1;
-    kern::mul(c, a.c0(), p.buf.ptr, o.c0(), nl, c->d_iota, nl);
-    kern::mul(c, a.c1(), p.buf.ptr, o.c1(), nl, c->d_iota, nl);
+    // c0 and c1 of every ciphertext of the batch times the one plaintext, one launch
+    kern::mul(c, a.buf.ptr, p.buf.ptr, o.buf.ptr, 2 * nl * a.nb, c->d_iota, nl, nl);
     return o;
 }
 
 // o += a * p (both polynomials)
 void mul_plain_acc(ckks_ct& o, const ckks_ct& a, const ckks_pt& p) {
     CK_CHECK(p.level == a.level && o.level == a.level, CKKS_EINVAL, "level mismatch in multiply-accumulate");
+    CK_CHECK(a.nb == 1 && o.nb == 1, CKKS_EINVAL, "multiply-accumulate takes single ciphertexts");
     ckks_ctx* c = a.ctx;
     c->ops["pmult"]++;
     const int nl = a.level + 1;
@@ -412,8 +415,8 @@ ckks_ct mul_int(const ckks_ct& a, long long v) {
         sv.v[i] = from_signed(v, c->q[i]);
         sv.vp[i] = shoup(sv.v[i], c->q[i]);
     }
-    ckks_ct o = new_ct(c, a.level, a.scale);
-    kern::mul_scalar_v(c, a.buf.ptr, sv, o.buf.ptr, 2 * nl, c->d_iota, nl);
+    ckks_ct o = new_ct(c, a.level, a.scale, a.nb);
+    kern::mul_scalar_v(c, a.buf.ptr, sv, o.buf.ptr, 2 * nl * a.nb, c->d_iota, nl);
     return o;
 }
 
@@ -424,14 +427,14 @@ ckks_ct add_const(const ckks_ct& a, double cst) {
     ScalarVec sv;
     for (int i = 0; i < nl; ++i) sv.v[i] = from_signed(v, c->q[i]);
     ckks_ct o = copy_ct(a);
-    kern::add_scalar_v(c, o.c0(), sv, nl, c->d_iota, nl);
+    kern::add_scalar_v(c, o.c0(), sv, nl * a.nb, c->d_iota, nl, a.cstride());    // c0 of each ciphertext
     return o;
 }
 
 ckks_ct imult(const ckks_ct& a) {
     ckks_ctx* c = a.ctx;
-    ckks_ct o = new_ct(c, a.level, a.scale);
-    kern::imult(c, a.buf.ptr, o.buf.ptr, 2 * (a.level + 1), c->d_iota, a.level + 1);
+    ckks_ct o = new_ct(c, a.level, a.scale, a.nb);
+    kern::imult(c, a.buf.ptr, o.buf.ptr, 2 * (a.level + 1) * a.nb, c->d_iota, a.level + 1);
     return o;
 }
 
@@ -449,13 +452,15 @@ ckks_ct rescale_mul(const ckks_ct& a, long long k) {
     ScalarVec top;
     top.v[0] = from_signed(k, c->q[l]);
     top.vp[0] = shoup(top.v[0], c->q[l]);
-    DevBuf last(2 * n, c->stream);
-    kern::mul_scalar_v(c, a.c0() + (size_t)l * n, top, last.ptr, 2, c->d_iota + l, 1, (size_t)(l + 1) * n);
-    kern::ntt_inverse(c, last.ptr, 2, c->d_iota + l, 1);
-    DevBuf lift(2 * (size_t)l * n, c->stream);
-    kern::lift_centred(c, last.ptr, l, lift.ptr, 2 * l, c->d_iota, l, n);     // both polynomials
-    kern::ntt_forward(c, lift.ptr, 2 * l, c->d_iota, l);
-    ckks_ct o = new_ct(c, l - 1, a.scale / (double)c->q[l]);
+    // the last limb of every polynomial (c0, c1 of each ciphertext: 2 nb rows (l + 1) N apart)
+    const int np_ = 2 * a.nb;
+    DevBuf last((size_t)np_ * n, c->stream);
+    kern::mul_scalar_v(c, a.c0() + (size_t)l * n, top, last.ptr, np_, c->d_iota + l, 1, (size_t)(l + 1) * n);
+    kern::ntt_inverse(c, last.ptr, np_, c->d_iota + l, 1);
+    DevBuf lift((size_t)np_ * l * n, c->stream);
+    kern::lift_centred(c, last.ptr, l, lift.ptr, np_ * l, c->d_iota, l, n);     // every polynomial
+    kern::ntt_forward(c, lift.ptr, np_ * l, c->d_iota, l);
+    ckks_ct o = new_ct(c, l - 1, a.scale / (double)c->q[l], a.nb);
     ScalarVec s1;
     for (int i = 0; i < l; ++i) {
         s1.v[i] = mulmod(from_signed(k, c->q[i]), c->h_qlinv[(size_t)l * c->nq + i], c->q[i]);
@@ -463,7 +468,7 @@ ckks_ct rescale_mul(const ckks_ct& a, long long k) {
     }
     const u64* s2 = c->d_qlinv + (size_t)l * c->nq;
     const u64* s2p = c->d_qlinv + (size_t)c->nq * c->nq + (size_t)l * c->nq;
-    kern::sub_mul2_scalar(c, a.c0(), lift.ptr, s1, s2, s2p, o.c0(), 2 * l, c->d_iota, l, (size_t)(l + 1) * n);
+    kern::sub_mul2_scalar(c, a.c0(), lift.ptr, s1, s2, s2p, o.c0(), np_ * l, c->d_iota, l, (size_t)(l + 1) * n);
     return o;
 }
 
@@ -472,10 +477,11 @@ ckks_ct rescale(const ckks_ct& a) { return rescale_mul(a, 1); }
 ckks_ct mod_drop(const ckks_ct& a, int level) {
     CK_CHECK(level >= 0 && level <= a.level, CKKS_EINVAL, "mod_drop to a higher level");
     ckks_ctx* c = a.ctx;
-    ckks_ct o = new_ct(c, level, a.scale);
+    ckks_ct o = new_ct(c, level, a.scale, a.nb);
     const size_t bytes = (size_t)(level + 1) * c->n * 8;
-    CUDA_CHECK(cudaMemcpyAsync(o.c0(), a.c0(), bytes, cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_CHECK(cudaMemcpyAsync(o.c1(), a.c1(), bytes, cudaMemcpyDeviceToDevice, c->stream));
+    // the first level + 1 limbs of every polynomial: 2 nb rows of `bytes`
+    CUDA_CHECK(cudaMemcpy2DAsync(o.c0(), bytes, a.c0(), (size_t)(a.level + 1) * c->n * 8, bytes, 2 * a.nb,
+                                 cudaMemcpyDeviceToDevice, c->stream));
     return o;
 }
 
@@ -500,48 +506,52 @@ ckks_ct mod_raise(const ckks_ct& a) {
     ckks_ctx* c = a.ctx;
     CK_CHECK(a.level == 0, CKKS_EINVAL, "ModRaise needs a level-0 ciphertext");
     const size_t n = c->n;
-    DevBuf coef(2 * n, c->stream);
-    CUDA_CHECK(cudaMemcpyAsync(coef.ptr, a.c0(), n * 8, cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_CHECK(cudaMemcpyAsync(coef.ptr + n, a.c1(), n * 8, cudaMemcpyDeviceToDevice, c->stream));
-    kern::ntt_inverse(c, coef.ptr, 2, c->d_iota, 1);
-    ckks_ct o = new_ct(c, c->L, a.scale);
-    kern::lift_centred(c, coef.ptr, 0, o.c0(), c->nq, c->d_iota);
-    kern::lift_centred(c, coef.ptr + n, 0, o.c1(), c->nq, c->d_iota);
-    kern::ntt_forward(c, o.buf.ptr, 2 * c->nq, c->d_iota, c->nq);
+    const int np_ = 2 * a.nb;                        // a level-0 batch is np_ consecutive limbs
+    DevBuf coef((size_t)np_ * n, c->stream);
+    CUDA_CHECK(cudaMemcpyAsync(coef.ptr, a.c0(), np_ * n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    kern::ntt_inverse(c, coef.ptr, np_, c->d_iota, 1);
+    ckks_ct o = new_ct(c, c->L, a.scale, a.nb);
+    kern::lift_centred(c, coef.ptr, 0, o.buf.ptr, np_ * c->nq, c->d_iota, c->nq, n);   // row k from source k / nq
+    kern::ntt_forward(c, o.buf.ptr, np_ * c->nq, c->d_iota, c->nq);
     return o;
 }
 
 // ------------------------------------------------------- key switching -----
-// D: [ndig][next][N], NTT domain
-DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out) {
+// D: [ndig][next][N], NTT domain; for a batch, x of ciphertext t at x + t xstride and D
+// [nb][ndig][next][N]
+DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out, int nb, size_t xstride) {
     const size_t n = c->n;
     const int nl = level + 1;
     const int next = nl + c->np;
     std::vector<std::vector<int>> dig = c->digits(level);
     const int ndig = (int)dig.size();
-    DevBuf coef(nl * n, c->stream);
-    CUDA_CHECK(cudaMemcpyAsync(coef.ptr, x, nl * n * 8, cudaMemcpyDeviceToDevice, c->stream));
-    kern::ntt_inverse(c, coef.ptr, nl, c->d_iota, nl);
-    DevBuf D((size_t)ndig * next * n, c->stream);
+    const size_t dstr = (size_t)ndig * next * n;     // words per ciphertext of D
+    if (xstride == 0) xstride = (size_t)nl * n;
+    DevBuf coef((size_t)nb * nl * n, c->stream);
+    CUDA_CHECK(cudaMemcpy2DAsync(coef.ptr, nl * n * 8, x, xstride * 8, nl * n * 8, nb, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    kern::ntt_inverse(c, coef.ptr, nb * nl, c->d_iota, nl);
+    DevBuf D((size_t)nb * dstr, c->stream);
     const int* ext = c->d_ext_ids[level];
     kern::ConvJobs jobs;
     jobs.n = 0;
     for (int d = 0; d < ndig; ++d)
         kern::add_conv_job(jobs, c->modup_tab(level, d), coef.ptr + (size_t)dig[d].front() * n,
-                           D.ptr + (size_t)d * next * n, 0, 0);
-    kern::base_convert_jobs(c, jobs, 1);
+                           D.ptr + (size_t)d * next * n, (size_t)nl * n, dstr);
+    kern::base_convert_jobs(c, jobs, nb);
     for (int d = 0; d < ndig; ++d) {
         u64* Dd = D.ptr + (size_t)d * next * n;
         const int lo = dig[d].front(), hi = dig[d].back() + 1;
-        CUDA_CHECK(cudaMemcpyAsync(Dd + (size_t)lo * n, x + (size_t)lo * n, (size_t)(hi - lo) * n * 8,
-                                   cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_CHECK(cudaMemcpy2DAsync(Dd + (size_t)lo * n, dstr * 8, x + (size_t)lo * n, xstride * 8,
+                                     (size_t)(hi - lo) * n * 8, nb, cudaMemcpyDeviceToDevice, c->stream));
         if (c->logn != 16) {
-            if (lo > 0) kern::ntt_forward(c, Dd, lo, ext, lo);
-            if (next > hi) kern::ntt_forward(c, Dd + (size_t)hi * n, next - hi, ext + hi, next - hi);
+            if (lo > 0) kern::ntt_forward(c, Dd, nb * lo, ext, lo, dstr);
+            if (next > hi) kern::ntt_forward(c, Dd + (size_t)hi * n, nb * (next - hi), ext + hi, next - hi, dstr);
         }
     }
-    if (c->logn == 16)   // every converted row of every digit in one launch
-        kern::ntt_forward_list(c, D.ptr, c->modup_nrows[level], c->d_modup_off[level], c->d_modup_pid[level]);
+    if (c->logn == 16)   // every converted row of every digit of every ciphertext in one launch
+        kern::ntt_forward_list(c, D.ptr, c->modup_nrows[level], c->d_modup_off[level], c->d_modup_pid[level], nb,
+                               dstr);
     *ndig_out = ndig;
     return D;
 }
@@ -550,86 +560,65 @@ DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out) {
 // Q_l u P: acc [2][next][N], NTT domain; `accumulate` adds to what acc holds.  With x0, the
 // first x0rows rows of acc's first half also receive s x0(sigma_g) (s null: x0(sigma_g)), the
 // automorphed c0 term of a rotation, in the same kernel.
+// For a batch of nb ciphertexts: D [nb][ndig][next][N], acc [nb][2][next][N], x0 / x1 of ciphertext t
+// at + t xstr; the key is read once for the batch.
 void key_switch_inner(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
                       u64* acc, bool accumulate, const u64* x0 = nullptr, int x0rows = 0, const u64* s = nullptr,
-                      const u64* sp = nullptr, const u64* x1 = nullptr) {
+                      const u64* sp = nullptr, const u64* x1 = nullptr, int nb = 1, size_t xstr = 0) {
     auto it = keys.swk.find(code);
     CK_CHECK(it != keys.swk.end(), CKKS_ENOKEY, "missing switching key (code " + std::to_string(code) + ")");
     const SwitchKey& k = *it->second;
     c->ops["keyswitch"]++;
     const size_t next = (size_t)level + 1 + c->np;
+    kern::KsBatch bt;
+    bt.nb = nb;
+    bt.dstr = (size_t)ndig * next * c->n;
+    bt.ostr = 2 * next * c->n;
+    bt.xstr = xstr;
     kern::ks_inner(c, D, ndig, (int)next, c->d_ext_ids[level], k.b.ptr, k.a.ptr, acc, acc + next * c->n, g,
-                   accumulate, x0, x0rows, s, sp, x1);
+                   accumulate, x0, x0rows, s, sp, x1, bt);
 }
 
 // ModDown fused with the rescale after it: both halves of acc (Q_l u P, NTT domain) divided
-// by P q_l, (acc - Conv_{q_l, P -> Q_{l-1}}(acc)) (P q_l)^{-1}; out [2][l][N]
-void mod_down_rescale(ckks_ctx* c, u64* acc, int level, u64* out, bool twice) {
+// by P q_l, (acc - Conv_{q_l, P -> Q_{l-1}}(acc)) (P q_l)^{-1}; out [2][l][N].  A batch: acc
+// [nb][2][next][N] -> out [nb][2][l][N] (every polynomial of the batch in each launch).
+void mod_down_rescale(ckks_ctx* c, u64* acc, int level, u64* out, bool twice, int nb = 1) {
     CK_CHECK(level >= 1, CKKS_ELEVEL, "cannot rescale a level-0 ciphertext");
     c->ops["rescale"]++;
     const size_t n = c->n;
-    const int l = level, np1 = c->np + 1;
+    const int l = level, np1 = c->np + 1, npoly = 2 * nb;
     const size_t next = (size_t)l + 1 + c->np;
-    u64* ab = acc;
-    u64* aa = acc + next * n;
     const int* pid = c->d_ext_ids[level] + l;      // q_l, then the special primes
-    if (c->logn == 16) {
-        kern::ntt_inverse(c, ab + (size_t)l * n, 2 * np1, pid, np1, next * n);
-    } else {
-        kern::ntt_inverse(c, ab + (size_t)l * n, np1, pid, np1);
-        kern::ntt_inverse(c, aa + (size_t)l * n, np1, pid, np1);
-    }
-    DevBuf conv(2 * (size_t)l * n, c->stream);
-    kern::base_convert(c, c->mdrs_tab(l), ab + (size_t)l * n, n, conv.ptr, n, 2, next * n, (size_t)l * n);
-    kern::ntt_forward(c, conv.ptr, 2 * l, c->d_iota, l);
+    kern::ntt_inverse(c, acc + (size_t)l * n, npoly * np1, pid, np1, next * n);
+    DevBuf conv((size_t)npoly * l * n, c->stream);
+    kern::base_convert(c, c->mdrs_tab(l), acc + (size_t)l * n, n, conv.ptr, n, npoly, next * n, (size_t)l * n);
+    kern::ntt_forward(c, conv.ptr, npoly * l, c->d_iota, l);
     const u64* tab = twice ? c->d_pqlinv2 : c->d_pqlinv;     // twice: 2 x the result, same pass
     const u64* s = tab + (size_t)l * c->nq;
     const u64* sp = tab + (size_t)c->nq * c->nq + (size_t)l * c->nq;
-    kern::sub_mul_scalar(c, ab, conv.ptr, s, sp, out, 2 * l, c->d_iota, l, next * n);    // aa = ab + next N
+    kern::sub_mul_scalar(c, acc, conv.ptr, s, sp, out, npoly * l, c->d_iota, l, next * n);
 }
 
-// acc (Q_l u P) += P x on the Q rows, x [2][l+1][N]
-static void lift_p(ckks_ctx* c, const u64* x, u64* acc, int level) {
+// acc (Q_l u P) += P x on the Q rows, x [nb][2][l+1][N], acc [nb][2][next][N]
+static void lift_p(ckks_ctx* c, const u64* x, u64* acc, int level, int nb = 1) {
     const int nl = level + 1;
     const size_t next = (size_t)nl + c->np;
-    kern::mul_scalar_acc(c, x, c->d_pmod, c->d_pmod + c->nq, acc, nl, c->d_iota, nl);
-    kern::mul_scalar_acc(c, x + (size_t)nl * c->n, c->d_pmod, c->d_pmod + c->nq, acc + next * c->n, nl, c->d_iota,
-                         nl);
+    kern::mul_scalar_acc(c, x, c->d_pmod, c->d_pmod + c->nq, acc, 2 * nl * nb, c->d_iota, nl, next * c->n);
 }
 
-// ModDown of both halves of acc: out0, out1 [l+1][N]
-static void mod_down(ckks_ctx* c, u64* acc, int level, u64* out0, u64* out1) {
+// ModDown of both halves of acc: [nb][2][next][N] -> out [nb][2][l+1][N]
+static void mod_down(ckks_ctx* c, u64* acc, int level, u64* out, int nb = 1) {
     const size_t n = c->n;
-    const int nl = level + 1;
+    const int nl = level + 1, npoly = 2 * nb;
     const int next = nl + c->np;
-    u64* ab = acc;
-    u64* aa = acc + (size_t)next * n;
     const int* pid = c->d_ext_ids[level] + nl;
-    if (c->logn == 16) {
-        kern::ntt_inverse(c, ab + (size_t)nl * n, 2 * c->np, pid, c->np, (size_t)next * n);
-    } else {
-        kern::ntt_inverse(c, ab + (size_t)nl * n, c->np, pid, c->np);
-        kern::ntt_inverse(c, aa + (size_t)nl * n, c->np, pid, c->np);
-    }
-    DevBuf conv(2 * (size_t)nl * n, c->stream);
-    kern::base_convert(c, c->moddown_tab(level), ab + (size_t)nl * n, n, conv.ptr, n, 2, (size_t)next * n,
+    kern::ntt_inverse(c, acc + (size_t)nl * n, npoly * c->np, pid, c->np, (size_t)next * n);
+    DevBuf conv((size_t)npoly * nl * n, c->stream);
+    kern::base_convert(c, c->moddown_tab(level), acc + (size_t)nl * n, n, conv.ptr, n, npoly, (size_t)next * n,
                        (size_t)nl * n);
-    kern::ntt_forward(c, conv.ptr, 2 * nl, c->d_iota, nl);
-    if (out1 == out0 + (size_t)nl * n && aa == ab + next * n) {
-        kern::sub_mul_scalar(c, ab, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out0, 2 * nl, c->d_iota, nl, next * n);
-    } else {
-        kern::sub_mul_scalar(c, ab, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out0, nl, c->d_iota, nl);
-        kern::sub_mul_scalar(c, aa, conv.ptr + (size_t)nl * n, c->d_pinv, c->d_pinv + c->nq, out1, nl, c->d_iota,
-                             nl);
-    }
-}
-
-// inner product with switching key `code` (automorphism g applied to D on the fly), ModDown
-void key_switch_raised(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
-                       u64* out0, u64* out1) {
-    DevBuf acc(2 * ((size_t)level + 1 + c->np) * c->n, c->stream);
-    key_switch_inner(c, keys, D, ndig, level, code, g, acc.ptr, false);
-    mod_down(c, acc.ptr, level, out0, out1);
+    kern::ntt_forward(c, conv.ptr, npoly * nl, c->d_iota, nl);
+    kern::sub_mul_scalar(c, acc, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out, npoly * nl, c->d_iota, nl,
+                         (size_t)next * n);
 }
 
 u64 galois_of_step(const ckks_ctx* c, long long r) {
@@ -639,10 +628,24 @@ u64 galois_of_step(const ckks_ctx* c, long long r) {
     return powmod(5, (u64)r, 2ULL * c->n);
 }
 
-std::vector<ckks_ct> rotate_hoisted(const ckks_keys& keys, const ckks_ct& a, const std::vector<long long>& steps) {
+// rot_g(a) for every ciphertext of a: the key switch of the automorphed raised digits D of c1 with
+// P c0(sigma_g) added on the Q rows in the same kernel, then ModDown: ModDown(P x + k) = x +
+// ModDown(k) exactly (P x vanishes on the P rows), so this is automorph(c0) + ModDown(k) in
+// fewer passes.
+static ckks_ct switch_galois(const ckks_keys& keys, const ckks_ct& a, const u64* D, int ndig, u64 g) {
     ckks_ctx* c = a.ctx;
     const int l = a.level, nl = l + 1;
-    const size_t n = c->n;
+    DevBuf acc((size_t)a.nb * 2 * ((size_t)nl + c->np) * c->n, c->stream);
+    key_switch_inner(c, keys, D, ndig, l, g, g, acc.ptr, false, a.c0(), nl, c->d_pmod, c->d_pmod + c->nq, nullptr,
+                     a.nb, a.cstride());
+    ckks_ct o = new_ct(c, l, a.scale, a.nb);
+    mod_down(c, acc.ptr, l, o.buf.ptr, a.nb);
+    return o;
+}
+
+std::vector<ckks_ct> rotate_hoisted(const ckks_keys& keys, const ckks_ct& a, const std::vector<long long>& steps) {
+    ckks_ctx* c = a.ctx;
+    const int l = a.level;
     std::vector<ckks_ct> outs;
     DevBuf D;
     int ndig = 0;
@@ -652,14 +655,9 @@ std::vector<ckks_ct> rotate_hoisted(const ckks_keys& keys, const ckks_ct& a, con
             outs.push_back(copy_ct(a));
             continue;
         }
-        if (!D.ptr) D = mod_up(c, a.c1(), l, &ndig);
+        if (!D.ptr) D = mod_up(c, a.c1(), l, &ndig, a.nb, a.cstride());
         c->ops["hrot"]++;
-        ckks_ct o = new_ct(c, l, a.scale);
-        DevBuf k0(nl * n, c->stream);
-        key_switch_raised(c, keys, D.ptr, ndig, l, g, g, k0.ptr, o.c1());
-        kern::automorph(c, a.c0(), o.c0(), nl, g);
-        kern::add(c, o.c0(), k0.ptr, o.c0(), nl, c->d_iota, nl);
-        outs.push_back(std::move(o));
+        outs.push_back(switch_galois(keys, a, D.ptr, ndig, g));
     }
     return outs;
 }
@@ -671,32 +669,37 @@ ckks_ct rotate(const ckks_keys& keys, const ckks_ct& a, long long r) {
 
 ckks_ct conjugate(const ckks_keys& keys, const ckks_ct& a) {
     ckks_ctx* c = a.ctx;
-    const int l = a.level, nl = l + 1;
-    const u64 g = 2ULL * c->n - 1;
     int ndig = 0;
-    DevBuf D = mod_up(c, a.c1(), l, &ndig);
-    ckks_ct o = new_ct(c, l, a.scale);
-    DevBuf k0(nl * (size_t)c->n, c->stream);
-    key_switch_raised(c, keys, D.ptr, ndig, l, g, g, k0.ptr, o.c1());
-    kern::automorph(c, a.c0(), o.c0(), nl, g);
-    kern::add(c, o.c0(), k0.ptr, o.c0(), nl, c->d_iota, nl);
-    return o;
+    DevBuf D = mod_up(c, a.c1(), a.level, &ndig, a.nb, a.cstride());
+    return switch_galois(keys, a, D.ptr, ndig, 2ULL * c->n - 1);
+}
+
+// tensor product of a batch: d [nb][3][l+1][N] (d0, d1, d2 of each ciphertext)
+static DevBuf tensor_batch(const ckks_ct& a, const ckks_ct& b) {
+    ckks_ctx* c = a.ctx;
+    const size_t nl = a.level + 1, n = c->n;
+    DevBuf d((size_t)a.nb * 3 * nl * n, c->stream);
+    kern::tensor(c, a.buf.ptr, b.buf.ptr, d.ptr, d.ptr + 2 * nl * n, (int)nl, c->d_iota, a.nb, a.cstride(),
+                 3 * nl * n, 3 * nl * n);
+    return d;
 }
 
 ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
     ckks_ctx* c = a.ctx;
-    CK_CHECK(a.level == b.level, CKKS_EINVAL, "HMult operands at different levels");
+    CK_CHECK(a.level == b.level && a.nb == b.nb, CKKS_EINVAL, "HMult operands at different levels");
     c->ops["hmult"]++;
     const int l = a.level, nl = l + 1;
-    const size_t n = c->n;
-    ckks_ct o = new_ct(c, l, a.scale * b.scale);
-    DevBuf d2(nl * n, c->stream);
-    kern::tensor(c, a.buf.ptr, b.buf.ptr, o.buf.ptr, d2.ptr, nl, c->d_iota);
+    const size_t n = c->n, ds = 3 * (size_t)nl * n;
+    DevBuf d = tensor_batch(a, b);
     int ndig = 0;
-    DevBuf D = mod_up(c, d2.ptr, l, &ndig);
-    DevBuf k(2 * nl * n, c->stream);
-    key_switch_raised(c, keys, D.ptr, ndig, l, 0, 1, k.ptr, k.ptr + nl * n);
-    kern::add(c, o.buf.ptr, k.ptr, o.buf.ptr, 2 * nl, c->d_iota, nl);
+    DevBuf D = mod_up(c, d.ptr + 2 * (size_t)nl * n, l, &ndig, a.nb, ds);
+    DevBuf acc((size_t)a.nb * 2 * ((size_t)nl + c->np) * n, c->stream);
+    // relinearisation key switch with P d0, P d1 added on the Q rows in the same kernel; then
+    // ModDown (= (d0, d1) + ModDown(k), see switch_galois)
+    key_switch_inner(c, keys, D.ptr, ndig, l, 0, 1, acc.ptr, false, d.ptr, nl, c->d_pmod, c->d_pmod + c->nq,
+                     d.ptr + (size_t)nl * n, a.nb, ds);
+    ckks_ct o = new_ct(c, l, a.scale * b.scale, a.nb);
+    mod_down(c, acc.ptr, l, o.buf.ptr, a.nb);
     return o;
 }
 
@@ -704,36 +707,35 @@ ckks_ct mul_relin(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b) {
 // divided by P q_l at once (the relinearisation's ModDown fused with the rescale)
 ckks_ct mul_relin_rescale(const ckks_keys& keys, const ckks_ct& a, const ckks_ct& b, bool twice) {
     ckks_ctx* c = a.ctx;
-    CK_CHECK(a.level == b.level, CKKS_EINVAL, "HMult operands at different levels");
+    CK_CHECK(a.level == b.level && a.nb == b.nb, CKKS_EINVAL, "HMult operands at different levels");
     CK_CHECK(a.level >= 1, CKKS_ELEVEL, "cannot rescale a level-0 ciphertext");
     c->ops["hmult"]++;
     const int l = a.level, nl = l + 1;
-    const size_t n = c->n;
-    DevBuf d(3 * (size_t)nl * n, c->stream);       // d0, d1, d2
-    u64* d0 = d.ptr;
-    u64* d1 = d.ptr + (size_t)nl * n;
-    u64* d2 = d.ptr + 2 * (size_t)nl * n;
-    kern::tensor(c, a.buf.ptr, b.buf.ptr, d0, d2, nl, c->d_iota);
+    const size_t n = c->n, ds = 3 * (size_t)nl * n;
+    DevBuf d = tensor_batch(a, b);                 // d0, d1, d2 of each ciphertext
     int ndig = 0;
-    DevBuf D = mod_up(c, d2, l, &ndig);
-    DevBuf acc(2 * ((size_t)nl + c->np) * n, c->stream);
+    DevBuf D = mod_up(c, d.ptr + 2 * (size_t)nl * n, l, &ndig, a.nb, ds);
+    DevBuf acc((size_t)a.nb * 2 * ((size_t)nl + c->np) * n, c->stream);
     // relinearisation key switch with P d0, P d1 added on the Q rows in the same kernel
-    key_switch_inner(c, keys, D.ptr, ndig, l, 0, 1, acc.ptr, false, d0, nl, c->d_pmod, c->d_pmod + c->nq, d1);
-    ckks_ct o = new_ct(c, l - 1, a.scale * b.scale / (double)c->q[l]);
-    mod_down_rescale(c, acc.ptr, l, o.buf.ptr, twice);
+    key_switch_inner(c, keys, D.ptr, ndig, l, 0, 1, acc.ptr, false, d.ptr, nl, c->d_pmod, c->d_pmod + c->nq,
+                     d.ptr + (size_t)nl * n, a.nb, ds);
+    ckks_ct o = new_ct(c, l - 1, a.scale * b.scale / (double)c->q[l], a.nb);
+    mod_down_rescale(c, acc.ptr, l, o.buf.ptr, twice, a.nb);
     return o;
 }
 
 // ---------------------------------------------------------------- BSGS -----
-// ModDown of one polynomial x over Q_l u P (NTT domain; its P rows are consumed): out [l+1][N]
-static void mod_down_poly(ckks_ctx* c, u64* x, int level, u64* out) {
+// ModDown of one polynomial x over Q_l u P (NTT domain; its P rows are consumed): out [l+1][N];
+// for a batch, nb polynomials at x + t xstride -> out [nb][l+1][N]
+static void mod_down_poly(ckks_ctx* c, u64* x, int level, u64* out, int nb = 1, size_t xstride = 0) {
     const size_t n = c->n;
     const int nl = level + 1;
-    kern::ntt_inverse(c, x + (size_t)nl * n, c->np, c->d_ext_ids[level] + nl, c->np);
-    DevBuf conv((size_t)nl * n, c->stream);
-    kern::base_convert(c, c->moddown_tab(level), x + (size_t)nl * n, n, conv.ptr, n, 1, 0, 0);
-    kern::ntt_forward(c, conv.ptr, nl, c->d_iota, nl);
-    kern::sub_mul_scalar(c, x, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out, nl, c->d_iota, nl);
+    if (xstride == 0) xstride = ((size_t)nl + c->np) * n;
+    kern::ntt_inverse(c, x + (size_t)nl * n, nb * c->np, c->d_ext_ids[level] + nl, c->np, xstride);
+    DevBuf conv((size_t)nb * nl * n, c->stream);
+    kern::base_convert(c, c->moddown_tab(level), x + (size_t)nl * n, n, conv.ptr, n, nb, xstride, (size_t)nl * n);
+    kern::ntt_forward(c, conv.ptr, nb * nl, c->d_iota, nl);
+    kern::sub_mul_scalar(c, x, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out, nb * nl, c->d_iota, nl, xstride);
 }
 
 // rot_r(a) for every r in steps kept over Q_l u P before ModDown (double hoisting), each
@@ -749,14 +751,15 @@ static std::vector<DevBuf> rotate_hoisted_ext(const ckks_keys& keys, const ckks_
     int ndig = 0;
     for (long long r : steps) {
         const u64 g = galois_of_step(c, r);
-        DevBuf o(2 * next * n, c->stream);
+        DevBuf o((size_t)a.nb * 2 * next * n, c->stream);      // [nb][2][next][N]
         if (g == 1) {
-            CUDA_CHECK(cudaMemsetAsync(o.ptr, 0, 2 * next * n * 8, c->stream));
-            lift_p(c, a.buf.ptr, o.ptr, l);
+            CUDA_CHECK(cudaMemsetAsync(o.ptr, 0, (size_t)a.nb * 2 * next * n * 8, c->stream));
+            lift_p(c, a.buf.ptr, o.ptr, l, a.nb);
         } else {
-            if (!D.ptr) D = mod_up(c, a.c1(), l, &ndig);
+            if (!D.ptr) D = mod_up(c, a.c1(), l, &ndig, a.nb, a.cstride());
             c->ops["hrot"]++;
-            key_switch_inner(c, keys, D.ptr, ndig, l, g, g, o.ptr, false, a.c0(), nl, c->d_pmod, c->d_pmod + c->nq);
+            key_switch_inner(c, keys, D.ptr, ndig, l, g, g, o.ptr, false, a.c0(), nl, c->d_pmod, c->d_pmod + c->nq,
+                             nullptr, a.nb, a.cstride());
         }
         outs.push_back(std::move(o));
     }
@@ -789,10 +792,12 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
                    const std::vector<const ckks_ptset*>& pss, bool rescale_out) {
     ckks_ctx* c = ins[0]->ctx;
     const int l = ins[0]->level, nl = l + 1;
-    const size_t n = c->n, next = (size_t)nl + c->np;
+    const int nb = ins[0]->nb;                       // a batch: every sum below is [nb][2][next][N]
+    const size_t n = c->n, next = (size_t)nl + c->np, es = 2 * next * n;
     const long long m = c->n / 2;
     const int* ext = c->d_ext_ids[l];
     const ckks_ptset& p0 = *pss[0];
+    for (const ckks_ct* a : ins) CK_CHECK(a->nb == nb, CKKS_EINVAL, "the inputs of one HMatmul differ in batch size");
     for (const ckks_ptset* ps : pss)
         CK_CHECK(ps->a0 == p0.a0 && ps->step == p0.step && ps->B == p0.B && ps->G() == p0.G(), CKKS_EINVAL,
                  "the plaintext sets of one HMatmul must share their BSGS geometry");
@@ -823,7 +828,7 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
             int ndig = 1;
             bool any_rot = false;
             for (long long r : steps) any_rot = any_rot || r != 0;
-            if (any_rot) D = mod_up(c, a.c1(), l, &ndig);
+            if (any_rot) D = mod_up(c, a.c1(), l, &ndig, nb, a.cstride());
             kern::BsgsFused T;
             T.nb = (int)used_b.size();
             T.ng = (int)gs.size();
@@ -858,11 +863,16 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
                     c->ops["pmult"]++;
                 }
                 auto it = inner.find(g);
-                if (it == inner.end()) it = inner.emplace(g, DevBuf(2 * next * n, c->stream)).first;
+                if (it == inner.end()) it = inner.emplace(g, DevBuf(nb * es, c->stream)).first;
                 else T.acc |= 1u << q;
                 T.o[q] = it->second.ptr;
             }
-            kern::bsgs_fused(c, T, D.ptr, a.c0(), a.c1(), nl, (int)next, ext, c->d_pmod, c->d_pmod + c->nq);
+            kern::KsBatch bt;
+            bt.nb = nb;
+            bt.dstr = (size_t)ndig * next * n;
+            bt.xstr = a.cstride();
+            bt.ostr = es;
+            kern::bsgs_fused(c, T, D.ptr, a.c0(), a.c1(), nl, (int)next, ext, c->d_pmod, c->d_pmod + c->nq, bt);
             continue;
         }
         std::vector<DevBuf> baby = rotate_hoisted_ext(keys, a, steps);
@@ -889,11 +899,15 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
                     c->ops["pmult"]++;
                 }
                 auto it = inner.find(g);
-                if (it == inner.end()) it = inner.emplace(g, DevBuf(2 * next * n, c->stream)).first;
+                if (it == inner.end()) it = inner.emplace(g, DevBuf(nb * es, c->stream)).first;
                 else T.acc |= 1u << q;
                 T.o[q] = it->second.ptr;
             }
-            kern::bsgs_inner_giants(c, T, (int)next, ext);
+            kern::KsBatch bt;
+            bt.nb = nb;
+            bt.dstr = es;
+            bt.ostr = es;
+            kern::bsgs_inner_giants(c, T, (int)next, ext, bt);
         }
     }
     CK_CHECK(!inner.empty(), CKKS_EINVAL, "empty plaintext set");
@@ -910,7 +924,7 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
     if (c->use_side_streams() && rot_giants.size() >= 2) {
         ensure_side_streams(c);
         std::vector<DevBuf> sums;
-        for (size_t k = 0; k < rot_giants.size(); ++k) sums.emplace_back(2 * next * n, c->stream);
+        for (size_t k = 0; k < rot_giants.size(); ++k) sums.emplace_back(nb * es, c->stream);
         const cudaStream_t main_stream = c->stream;
         StreamRestore restore{c, main_stream};
         CUDA_CHECK(cudaEventRecord(c->fork_ev, main_stream));
@@ -921,11 +935,12 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
             const u64 gal = galois_of_step(c, rot_giants[k].first);
             u64* x = rot_giants[k].second;
             c->ops["hrot"]++;
-            DevBuf c1q((size_t)nl * n, c->stream);
-            mod_down_poly(c, x + next * n, l, c1q.ptr);
+            DevBuf c1q((size_t)nb * nl * n, c->stream);
+            mod_down_poly(c, x + next * n, l, c1q.ptr, nb, es);
             int ndig = 0;
-            DevBuf D = mod_up(c, c1q.ptr, l, &ndig);
-            key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, sums[k].ptr, false, x, (int)next);
+            DevBuf D = mod_up(c, c1q.ptr, l, &ndig, nb, (size_t)nl * n);
+            key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, sums[k].ptr, false, x, (int)next, nullptr, nullptr,
+                             nullptr, nb, es);
         }
         for (int k = 0; k < nside; ++k) {
             CUDA_CHECK(cudaEventRecord(c->side_ev[k], c->side[k]));
@@ -943,7 +958,7 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
                 acc = std::move(sums[k]);
                 have_acc = true;
             } else {
-                kern::add(c, acc.ptr, sums[k].ptr, acc.ptr, 2 * (int)next, ext, (int)next);
+                kern::add(c, acc.ptr, sums[k].ptr, acc.ptr, 2 * (int)next * nb, ext, (int)next);
             }
         }
         inner.clear();
@@ -957,27 +972,28 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
                 acc = std::move(kv.second);
                 have_acc = true;
             } else {
-                kern::add(c, acc.ptr, x, acc.ptr, 2 * (int)next, ext, (int)next);
+                kern::add(c, acc.ptr, x, acc.ptr, 2 * (int)next * nb, ext, (int)next);
             }
             continue;
         }
         const u64 gal = galois_of_step(c, R);
         c->ops["hrot"]++;
-        DevBuf c1q((size_t)nl * n, c->stream);
-        mod_down_poly(c, x + next * n, l, c1q.ptr);
+        DevBuf c1q((size_t)nb * nl * n, c->stream);
+        mod_down_poly(c, x + next * n, l, c1q.ptr, nb, es);
         int ndig = 0;
-        DevBuf D = mod_up(c, c1q.ptr, l, &ndig);
-        if (!have_acc) acc = DevBuf(2 * next * n, c->stream);
-        key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, acc.ptr, have_acc, x, (int)next);
+        DevBuf D = mod_up(c, c1q.ptr, l, &ndig, nb, (size_t)nl * n);
+        if (!have_acc) acc = DevBuf(nb * es, c->stream);
+        key_switch_inner(c, keys, D.ptr, ndig, l, gal, gal, acc.ptr, have_acc, x, (int)next, nullptr, nullptr,
+                         nullptr, nb, es);
         have_acc = true;
     }
     if (rescale_out) {
-        ckks_ct o = new_ct(c, l - 1, scale / (double)c->q[l]);
-        mod_down_rescale(c, acc.ptr, l, o.buf.ptr, false);
+        ckks_ct o = new_ct(c, l - 1, scale / (double)c->q[l], nb);
+        mod_down_rescale(c, acc.ptr, l, o.buf.ptr, false, nb);
         return o;
     }
-    ckks_ct o = new_ct(c, l, scale);
-    mod_down(c, acc.ptr, l, o.c0(), o.c1());
+    ckks_ct o = new_ct(c, l, scale, nb);
+    mod_down(c, acc.ptr, l, o.buf.ptr, nb);
     return o;
 }
 
@@ -1078,8 +1094,9 @@ static PolyVal cheb_leaf(ChebPowers& pw, const std::vector<double>& c) {
         }
         ++L.n;
     }
-    ckks_ct acc = new_ct(ctx, lev, 0.0);
-    kern::lincomb(ctx, L, acc.buf.ptr, 2 * (lev + 1), ctx->d_iota, lev + 1);
+    const int nb = pw.T.at(1).nb;
+    ckks_ct acc = new_ct(ctx, lev, 0.0, nb);
+    kern::lincomb(ctx, L, acc.buf.ptr, 2 * (lev + 1) * nb, ctx->d_iota, lev + 1);
     acc = rescale(acc);
     acc.scale = ctx->delta[target];
     out.ct = add_const(acc, c[0]);
@@ -1561,6 +1578,7 @@ ckks_ct encrypt_sk(const ckks_keys& K, const ckks_pt& pt, u64 nonce) {
 
 void decrypt(const ckks_keys& K, const ckks_ct& ct, ckks_pt& out) {
     ckks_ctx* c = K.ctx;
+    CK_CHECK(ct.nb == 1, CKKS_EINVAL, "decrypt takes a single ciphertext");
     const int nl = ct.level + 1;
     DevBuf m((size_t)nl * c->n, c->stream);
     kern::mul(c, ct.c1(), K.s_ntt.ptr, m.ptr, nl, c->d_iota, nl);

@@ -4,8 +4,8 @@
 
 namespace ops {
 DevBuf upload(ckks_ctx* c, const std::vector<u64>& v);
-void ensure_ct(ckks_ct& ct, ckks_ctx* c, int level);
-ckks_ct new_ct(ckks_ctx* c, int level, double scale);
+void ensure_ct(ckks_ct& ct, ckks_ctx* c, int level, int nb = 1);
+ckks_ct new_ct(ckks_ctx* c, int level, double scale, int nb = 1);
 ckks_ct copy_ct(const ckks_ct& a);
 ckks_ct add(const ckks_ct& a, const ckks_ct& b);
 ckks_ct sub(const ckks_ct& a, const ckks_ct& b);
@@ -20,9 +20,10 @@ ckks_ct rescale_mul(const ckks_ct& a, long long k);
 ckks_ct mod_drop(const ckks_ct& a, int level);
 ckks_ct level_down(const ckks_ct& a, int level);
 ckks_ct mod_raise(const ckks_ct& a);
-DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out);
-void key_switch_raised(ckks_ctx* c, const ckks_keys& keys, const u64* D, int ndig, int level, u64 code, u64 g,
-                       u64* out0, u64* out1);
+// per digit, the polynomial x (NTT domain, [l+1][N]) raised to Q_l u P: [ndig][next][N]; for a
+// batch, nb polynomials at x + t xstride -> [nb][ndig][next][N]
+DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out, int nb = 1, size_t xstride = 0);
+
 u64 galois_of_step(const ckks_ctx* c, long long r);
 std::vector<ckks_ct> rotate_hoisted(const ckks_keys& keys, const ckks_ct& a, const std::vector<long long>& steps);
 ckks_ct rotate(const ckks_keys& keys, const ckks_ct& a, long long r);
