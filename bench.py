@@ -239,6 +239,102 @@ def check_accuracy(K, s, out):
     return float(np.abs(got - ref).max())
 
 
+def lockstep_batches(K, torch, s, B, rounds, timing_B=0):
+    """Config 3's batched figure: for each stride-1 block shape of the three stages of a
+    ResNet-20-shaped network (16 x 32 x 32, 32 x 16 x 16, 64 x 8 x 8 channels x pixels; the first
+    is the config-2 block), B seeded inputs run as ONE lockstep batch (ckks_block_batched,
+    recorded as one CUDA graph: every kernel launched once for the B ciphertexts, keys and
+    diagonals shared through L2), against the same block one ciphertext at a time (its own
+    graph, replayed B times).  Every batched output equals the one-at-a-time output of its
+    input; one output per shape is decoded against FP64 conv2d.  With timing_B, one eager batch
+    of timing_B config-2 ciphertexts is timed per kernel (the batched rooflines)."""
+    ctx, keys = s["ctx"], s["keys"]
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    stream = torch.cuda.current_stream()
+    out = {}
+    kst = None
+    for nm in ("cfg3_s1", "cfg3_s2", "cfg3_s3"):
+        spec = WL.CONV[nm]
+        w = 1
+        while w < spec["w0"] + spec["f"] // 2:
+            w *= 2
+        if nm == "cfg3_s1":
+            bt, conv, W = s["bt"], s["conv"], s["W"]
+        else:
+            bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
+            W = WL.weights(11, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+            conv = K.ckks_ptset_conv_fused(ctx, W, spec["cin"], spec["cout"], spec["f"], w, 1,
+                                           (2.0 ** 49 * q[1]) / delta[1])
+            K.ckks_keys_add_rotations(ctx, keys, sorted(set(K.ckks_ptset_rotations(conv)) |
+                                                        set(K.ckks_boot_rotations(bt))))
+        xs = [WL.image(2000 + b, spec["cin"], spec["w0"]) for b in range(B)]
+        ins = [K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, x, w, 1, delta[1]), 2000 + b)
+               for b, x in enumerate(xs)]
+        outs = [K.ckks_ct_create(ctx) for _ in range(B)]
+        g = K.ckks_block_batched_graph_create(ctx, keys, ins, conv, bt, outs)
+        one_out = K.ckks_ct_create(ctx)
+        g1 = K.ckks_block_graph_create(ctx, keys, ins[0], conv, bt, one_out)
+        K.ckks_graph_launch(g)
+        K.ckks_graph_launch(g1)
+        K.ckks_sync(ctx)
+
+        def timed(fn):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        t_batch = timed(lambda: [K.ckks_graph_launch(g) for _ in range(rounds)]) / rounds
+        t_one = timed(lambda: [K.ckks_graph_launch(g1) for _ in range(B)]) / B
+        # every batched output against its input's own block (checked on up to 4 inputs)
+        same = True
+        for b in range(min(B, 4)):
+            if b:
+                K.ckks_ct_copy_into(ctx, ins[b], ins[0])
+            K.ckks_graph_launch(g1)
+            K.ckks_sync(ctx)
+            same = same and bool((K.ckks_ct_export_rns(ctx, one_out) == K.ckks_ct_export_rns(ctx, outs[b])).all())
+        got = K.ckks_decode_image(ctx, K.ckks_decrypt(ctx, keys, outs[1]), spec["cout"], spec["w0"], w)
+        err = float(np.abs(got - conv2d_same(xs[1], W)).max())
+        out[nm] = {"shape": "%dx%dx%d" % (spec["cin"], spec["w0"], spec["w0"]), "B": B,
+                   "ct_per_s": round(B / (t_batch / 1e3), 2), "ms_per_ct": round(t_batch / B, 3),
+                   "one_at_a_time_ms": round(t_one, 3), "speedup": round(t_one / (t_batch / B), 3),
+                   "outputs_equal_one_at_a_time": same, "decoded_max_abs_err": err,
+                   "launches_per_batch": K.ckks_graph_info(g), "launches_per_block": K.ckks_graph_info(g1)}
+        del g, g1, outs, ins, one_out
+        K.ckks_sync(ctx)
+        if nm == "cfg3_s1" and timing_B:
+            ins = [K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, xs[b % B], w, 1, delta[1]), 3000 + b)
+                   for b in range(timing_B)]
+            K.ckks_ctx_set_side_streams(ctx, 0)
+            K.ckks_ctx_reset_counters(ctx)
+            K.ckks_ctx_set_timing(ctx, 1)
+            K.ckks_block_batched(ctx, keys, ins, conv, bt)
+            K.ckks_ctx_set_timing(ctx, 0)
+            K.ckks_ctx_set_side_streams(ctx, 1)
+            kst = K.ckks_ctx_kernel_stats(ctx)
+            del ins
+            K.ckks_sync(ctx)
+    return out, kst
+
+
+def conv2d_same(x, W):
+    """FP64 conv2d, stride 1, zero padding f // 2 (cross-correlation), x (cin, h, h), W (cout, cin, f, f)"""
+    f = W.shape[2]
+    c = f // 2
+    h = x.shape[1]
+    xp = np.zeros((x.shape[0], h + 2 * c, h + 2 * c))
+    xp[:, c:c + h, c:c + h] = x
+    ref = np.zeros((W.shape[0], h, h))
+    for a in range(f):
+        for b in range(f):
+            ref += np.einsum("oi,ihw->ohw", W[:, :, a, b], xp[:, a:a + h, b:b + h])
+    return ref
+
+
 # ------------------------------------------------------------ oracle arm -----
 # BSGS splits of the oracle's block (CtoS levels, StoC1 levels): the splits the GPU tuner picks
 # on GB300 for config 2.
@@ -598,6 +694,23 @@ def run_ours(args):
                    "unit": "GB/s", "frac": round(gbs / pk.get("hbm_gbs"), 4), "parts": parts,
                    "note": ROOF_NOTES.get("bsgs_fused")}
     roof_alu = ntt_alu_roofline(kst, pk)
+    # config 3's lockstep batches (B inputs per stride-1 stage shape, one graph each) and the
+    # per-kernel rooflines of one eager lockstep batch of config-2 blocks
+    lock, kst_b = lockstep_batches(K, torch, s, max(1, args.batch_size), max(1, min(args.steps, 2)),
+                                   timing_B=max(1, args.batch_size))
+    roof_b = {"B": max(1, args.batch_size), "ntt_alu": ntt_alu_roofline(kst_b, pk)}
+    parts_b = {}
+    for name in ("bsgs_fused", "ks_inner"):
+        v = kst_b.get(name)
+        if v:
+            gbs = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+            parts_b[name] = {"achieved": round(gbs, 1), "frac": round(gbs / pk.get("hbm_gbs"), 4),
+                             "launches": v["launches"], "ms": round(v["ms"], 3)}
+    roof_b["keyswitch_hbm"] = parts_b
+    roof_b["note"] = ("algorithmic bytes count each switching key and plaintext diagonal once per batch launch "
+                      "(the batch's CTAs share them through L2) and every ciphertext's own words")
+    roof_b["kernels"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
+                         for k, v in sorted(kst_b.items(), key=lambda kv: -kv[1]["ms"])[:8]}
     if rank != 0:
         return
     cpu = None
@@ -616,7 +729,7 @@ def run_ours(args):
                        "execution": "CUDA graph replay of the block",
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "gpu_launches": launches, "launches_per_block": per_graph,
-            "batched": batched, "autotune": tuned,
+            "batched": batched, "batched_lockstep": lock, "roofline_batched": roof_b, "autotune": tuned,
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(host_in.nbytes),
                     "d2h_bytes_per_step": int(host_out.nbytes)},
             "roofline": roof, "roofline_keyswitch": roof_ks, "roofline_ntt_alu": roof_alu, "op_counts": counts,
