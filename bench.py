@@ -63,7 +63,7 @@ def parse_args():
                     help="--impl reference: the config-2 chain at N=2^10 (checks the arm quickly; not a measurement)")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
     ap.add_argument("--batch", type=int, default=8, help="ciphertexts run concurrently for the batched figure")
-    ap.add_argument("--workload", default="block", choices=["block", "ds", "serve", "batch"],
+    ap.add_argument("--workload", default="block", choices=["block", "ds", "serve", "batch", "cfg4"],
                     help="block: the Alg. 1 block (default); ds: the downsampling layer of Alg. 2; "
                          "serve: the serving loop under Poisson arrivals; batch: 64 uneven-shape blocks "
                          "(ResNet-20 stage shapes) batched through the serving runtime")
@@ -75,7 +75,8 @@ def parse_args():
                          "instead of timing the variants, e.g. to profile the configuration of a plain run")
     ap.add_argument("--bsgs-splits", default=None,
                     help="comma list of baby-step counts per bootstrapping level, used instead of tuning")
-    ap.add_argument("--kernel", default=None, choices=["ntt", "ks", "bsgs"],
+    ap.add_argument("--limbs", type=int, default=256, help="--kernel ntt: limbs per launch")
+    ap.add_argument("--kernel", default=None, choices=["ntt", "ks", "bsgs", "bblock"],
                     help="time one kernel family alone on a buffer larger than L2 (for profiling)")
     return ap.parse_args()
 
@@ -839,6 +840,165 @@ def run_ds(args):
     print(json.dumps(line), flush=True)
 
 
+def polyphase(x):
+    """the four stride-2 phases of each channel of x (c, h, h), h even: image 4i + q + 2p is
+    x[i, p::2, q::2] (how a client lays out the input of a stride-2 first layer)"""
+    c, h, _ = x.shape
+    out = np.zeros((4 * c, h // 2, h // 2))
+    for i in range(c):
+        for p in range(2):
+            for q in range(2):
+                out[4 * i + q + 2 * p] = x[i, p::2, q::2]
+    return out
+
+
+def conv2d_stride2(x, W):
+    """FP64 cross-correlation, stride 2, zero padding f // 2"""
+    return conv2d_same(x, W)[:, ::2, ::2]
+
+
+def run_cfg4(args):
+    """ImageNet-shaped ResNet-18 layers at N = 2^16 (config 4: 224 x 224 x 3 input, He-normal
+    weights), each timed on the GPU and combined into seconds per inference:
+      stem       7x7 stride-2 conv 224^2 x 3 -> 112^2 x 64: the client encodes the polyphase images
+                 of each input channel (one channel per ciphertext at width 256), the decomposed
+                 5x5 kernels (Alg. 2) run as a unit-stride conv over 3 input ciphertexts; 16 output
+                 ciphertexts (4 channels each at w = 128), each conv + bootstrap (ckks_block_multi)
+      pool       3x3 stride-2 average pooling (the downsampling depthwise conv of Alg. 2) 112^2 x 64
+                 -> 56^2 x 64: 4 output ciphertexts, each from 4 stride-2 tails (ckks_downsample_layer)
+      stage k    3x3 convs at 56^2 x 64 (4 ciphertexts in and out), 28^2 x 128 (2), 14^2 x 256 (1) and
+                 7^2 x 512 (1), each output ciphertext a block matrix-vector product over the inputs
+                 (Sec. 3.3.3) with its bootstrap; the stride-2 3x3 entry conv of stages 2-4 and its
+                 1x1 stride-2 shortcut as Alg. 2 layers
+    per inference = stem + pool + 4 stage-1 convs + for stages 2-4 (entry + shortcut + 3 convs).
+    HActivation is excluded as in the config-2 block (each conv layer carries its bootstrap);
+    the residual additions are elementwise and not timed.  Layers are timed one at a time on
+    inputs of their own shape (encrypted seeded images; the Alg. 2 layers on EvalMod outputs of
+    a config-2 bootstrap, which have the same level and scale); the conv layers are decoded
+    against FP64 conv2d."""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = block_setup(K, torch, seed=1)
+    ctx, keys = s["ctx"], s["keys"]
+    tuned = K.ckks_autotune(ctx, 3)
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    s_pt = (2.0 ** 49 * q[1]) / delta[1]
+    rng = np.random.default_rng(44)
+    have = set(s["rots"])
+
+    def need(*objs):
+        r = set()
+        for o in objs:
+            r |= set(K.ckks_ptset_rotations(o) if isinstance(o, K.PtSet) else K.ckks_boot_rotations(o))
+        new = sorted(r - have)
+        if new:
+            K.ckks_keys_add_rotations(ctx, keys, new)
+            have.update(new)
+
+    def he(cout, cin, f):
+        return rng.normal(0.0, np.sqrt(2.0 / (cin * f * f)), (cout, cin, f, f))
+
+    def enc(imgs, w):
+        return K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, imgs, w, 1, delta[1]), int(rng.integers(1 << 30)))
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()                                             # warm-up (lazy tables, pool)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def err_of(out, ref, w, c):
+        got = K.ckks_decode_image(ctx, K.ckks_decrypt(ctx, keys, out), c, ref.shape[1], w)
+        return float(np.abs(got - ref[:c]).max())
+
+    layers = {}
+    # EvalMod outputs of a config-2 bootstrap: inputs of every Alg. 2 layer (same level and scale)
+    x0 = K.ckks_conv2d_cins(ctx, keys, s["ct"], s["conv"])
+    re, im = K.ckks_bootstrap(ctx, keys, s["bt"], x0)
+
+    # ---- stem
+    x = WL.image(7, 3, 224)
+    W = he(64, 3, 7)
+    pp = polyphase(x)
+    bt = K.ckks_boot_create(ctx, 128, 112, 4)
+    sets = [[K.ckks_ptset_conv_fused_s2(ctx, W[4 * j:4 * j + 4], 3, 4, 7, 256, t, 1, s_pt) for t in range(3)]
+            for j in range(16)]
+    need(bt, *sets[0])
+    ins = [enc(pp[4 * t:4 * t + 4], 128) for t in range(3)]
+    t_ms, outs = timed(lambda: [K.ckks_block_multi(ctx, keys, ins, sets[j], bt) for j in range(16)])
+    layers["stem"] = {"ms": round(t_ms, 2), "ciphertexts_out": 16, "inputs_per_output": 3,
+                      "decoded_max_abs_err": err_of(outs[0], conv2d_stride2(x, W[:4]), 128, 4)}
+    del sets, ins, outs
+
+    # ---- Alg. 2 layers: (name, n outputs, inputs per output, bt_in (w, w0, cout), bt_out (w, w0, cout), set maker)
+    def ds_layer(name, n_out, n_in, bin_, bout, make_set):
+        b_in = K.ckks_boot_create(ctx, bin_[0], bin_[1], bin_[2], stride=2)
+        b_out = K.ckks_boot_create(ctx, bout[0], bout[1], bout[2])
+        sets_ = [make_set(t) for t in range(n_in)]
+        need(b_in, b_out, *sets_)
+        t_ms_, _ = timed(lambda: [K.ckks_downsample_layer(ctx, keys, [re] * n_in, [im] * n_in, b_in, sets_, b_out)
+                                  for _ in range(n_out)])
+        layers[name] = {"ms": round(t_ms_, 2), "ciphertexts_out": n_out, "inputs_per_output": n_in}
+
+    ds_layer("pool", 4, 4, (128, 112, 4), (64, 56, 16),
+             lambda t: K.ckks_ptset_dwconv_fused_s2(ctx, np.full((16, 3, 3), 1.0 / 9.0), 128, t, 1, s_pt))
+
+    # ---- stride-1 stage convs: (name, channels, image width, ciphertexts)
+    def stage_conv(name, c, h, n):
+        w = 1
+        while w < h + 1:
+            w *= 2
+        C = c // n
+        b = K.ckks_boot_create(ctx, w, h, C)
+        Wc = he(c, c, 3)
+        sets_ = [[K.ckks_ptset_conv_fused(ctx, Wc[C * j:C * j + C, C * i:C * i + C], C, C, 3, w, 1, s_pt)
+                  for i in range(n)] for j in range(n)]
+        need(b, *sets_[0])
+        xs = rng.random((c, h, h))
+        ins_ = [enc(xs[C * i:C * i + C], w) for i in range(n)]
+        t_ms_, outs_ = timed(lambda: [K.ckks_block_multi(ctx, keys, ins_, sets_[j], b) for j in range(n)])
+        layers[name] = {"ms": round(t_ms_, 2), "ciphertexts_out": n, "inputs_per_output": n,
+                        "decoded_max_abs_err": err_of(outs_[0], conv2d_same(xs, Wc[:C]), w, C)}
+
+    stage_conv("stage1_conv_56x56x64", 64, 56, 4)
+    for (name, cin, cout, h_in, n_in, n_out) in (("stage2", 64, 128, 56, 4, 2), ("stage3", 128, 256, 28, 2, 1),
+                                                  ("stage4", 256, 512, 14, 1, 1)):
+        w_in = 1
+        while w_in < h_in + 1:
+            w_in *= 2
+        Cin = cin // n_in
+        cpo = cout // n_out
+        for f, tag in ((3, "entry"), (1, "shortcut_1x1")):
+            Wd = he(cout, cin, f)
+            ds_layer("%s_%s" % (name, tag), n_out, n_in, (w_in, h_in, Cin), (w_in // 2, h_in // 2, cpo),
+                     lambda t, Wd=Wd, f=f: K.ckks_ptset_conv_fused_s2(ctx, Wd[:cpo], cin, cpo, f, w_in, t, 1, s_pt))
+        stage_conv("%s_conv_%dx%dx%d" % (name, h_in // 2, h_in // 2, cout), cout, h_in // 2, n_out)
+    L = layers
+    total = (L["stem"]["ms"] + L["pool"]["ms"] + 4 * L["stage1_conv_56x56x64"]["ms"] +
+             sum(L["%s_entry" % k]["ms"] + L["%s_shortcut_1x1" % k]["ms"] + 3 * L[n]["ms"]
+                 for k, n in (("stage2", "stage2_conv_28x28x128"), ("stage3", "stage3_conv_14x14x256"),
+                              ("stage4", "stage4_conv_7x7x512"))))
+    line = {"metric": "seconds per ResNet-18-shaped inference at N=2^16 (projected from timed layers)",
+            "value": round(total / 1e3, 3), "unit": "s", "n_gpus": 1, "higher_is_better": False, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "config 4: 224x224x3 input, 7x7/2 stem, 3x3/2 avg pool, stages 56^2x64, "
+                                   "28^2x128, 14^2x256, 7^2x512 (4 convs each; stride-2 entries and 1x1 stride-2 "
+                                   "shortcuts as Alg. 2 layers); He-normal weights, inputs U[0,1)",
+                       "projection": "stem + pool + 4 x stage1 conv + sum over stages 2-4 of (entry + shortcut + "
+                                     "3 x conv); HActivation excluded; eager calls timed with CUDA events",
+                       "autotune_ntt_variant_per_size_class": tuned},
+            "layers": layers, "rotation_keys": len(have)}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """The serving loop at N = 2^16 under Poisson arrivals: 70% one-block requests (a config-2
     block) and 30% two-block chains, at three offered loads relative to the measured capacity;
@@ -1019,7 +1179,7 @@ def run_batch(args):
 
 
 def run_kernel_ntt(args):
-    """forward + inverse NTT of 256 limbs (256 MiB, > L2) cycling over the config-2 primes"""
+    """forward + inverse NTT of --limbs limbs (256: 128 MiB, > L2) cycling over the config-2 primes"""
     import torch
     from paper_2312_04356_gb300 import build
     build.build()
@@ -1028,7 +1188,7 @@ def run_kernel_ntt(args):
     ctx = K.ckks_ctx_create(d, 1, torch.cuda.current_stream().cuda_stream)
     q, p, _, _ = K.ckks_ctx_info(ctx)
     mods = q + p
-    nl = 256
+    nl = max(1, args.limbs)
     ids = [i % len(mods) for i in range(nl)]
     x = WL.residues(1, [mods[i] for i in ids], ctx.n)
     dev = torch.from_numpy(x.view(np.int64)).cuda()
@@ -1057,6 +1217,36 @@ def run_kernel_ntt(args):
                 res[variant][k]["Gbutterfly_s"] = alu[k]["achieved"]
                 res[variant][k]["alu_frac"] = alu[k]["frac"]
     print(json.dumps({"kernel": "ntt", "limbs": nl, "N": ctx.n, "roundtrip_exact": ok, "per_variant": res}))
+
+
+def run_kernel_bblock(args):
+    """one config-2 block as a lockstep batch of --batch-size ciphertexts, eager, side streams off,
+    per-kernel timing (a case small enough for ncu captures of the batched key-switch kernels)"""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    s = block_setup(K, torch, seed=1)
+    ctx = s["ctx"]
+    q, p, _, delta = K.ckks_ctx_info(ctx)
+    B = max(1, args.batch_size)
+    ins = [K.ckks_encrypt(ctx, s["keys"], K.ckks_encode_image(ctx, s["x"], s["w"], 1, delta[1]), 10 + b)
+           for b in range(B)]
+    K.ckks_ctx_set_side_streams(ctx, 0)
+    for _ in range(args.warmup):
+        K.ckks_block_batched(ctx, s["keys"], ins, s["conv"], s["bt"])
+    K.ckks_sync(ctx)
+    K.ckks_ctx_reset_counters(ctx)
+    K.ckks_ctx_set_timing(ctx, 1)
+    for _ in range(args.steps):
+        outs = K.ckks_block_batched(ctx, s["keys"], ins, s["conv"], s["bt"])
+    K.ckks_ctx_set_timing(ctx, 0)
+    st = K.ckks_ctx_kernel_stats(ctx)
+    err = check_accuracy(K, s, outs[0])
+    res = {k: {"launches": v["launches"], "ms_per_block": round(v["ms"] / args.steps, 3),
+               "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)}
+           for k, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])}
+    print(json.dumps({"kernel": "bblock", "B": B, "N": ctx.n, "decoded_max_abs_err": err, "per_kernel": res}))
 
 
 def run_kernel_bsgs(args):
@@ -1130,12 +1320,16 @@ if __name__ == "__main__":
         run_kernel_ks(a)
     elif a.kernel == "bsgs":
         run_kernel_bsgs(a)
+    elif a.kernel == "bblock":
+        run_kernel_bblock(a)
     elif a.workload == "ds" and a.impl == "ours":
         run_ds(a)
     elif a.workload == "serve" and a.impl == "ours":
         run_serve(a)
     elif a.workload == "batch" and a.impl == "ours":
         run_batch(a)
+    elif a.workload == "cfg4" and a.impl == "ours":
+        run_cfg4(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

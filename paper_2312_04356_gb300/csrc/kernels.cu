@@ -1225,13 +1225,8 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
             for (int d = 0; d < NDIG; ++d) {
                 const u64 x = *slot(st, 2 * NDIG + d), yb = *slot(st, d), ya = *slot(st, NDIG + d);
-                const u64 pbl = x * yb, pal = x * ya;
-                bh += __umul64hi(x, yb);
-                ah += __umul64hi(x, ya);
-                bl += pbl;
-                bh += bl < pbl ? 1ull : 0ull;
-                al += pal;
-                ah += al < pal ? 1ull : 0ull;
+                mac128(bl, bh, x, yb);
+                mac128(al, ah, x, ya);
             }
             rb = reduce128_lazy(bh, bl, pr);
             ra = reduce128_lazy(ah, al, pr);
@@ -1241,13 +1236,8 @@ __global__ void __launch_bounds__(256, 3)
         for (int g = 0; g < NG; ++g) {
             if (!T.p[g][b]) continue;
             const u64 y = *slot(st, 3 * NDIG + 2 + g);
-            const u64 pl = rb * y, pa = ra * y;
-            hib[g] += __umul64hi(rb, y);
-            hia[g] += __umul64hi(ra, y);
-            lob[g] += pl;
-            hib[g] += lob[g] < pl ? 1ull : 0ull;
-            loa[g] += pa;
-            hia[g] += loa[g] < pa ? 1ull : 0ull;
+            mac128(lob[g], hib[g], rb, y);
+            mac128(loa[g], hia[g], ra, y);
         }
         if (b + 2 < T.nb) issue(b + 2, st);          // this stage has been read
         else cp_async_commit();                      // keep one group per iteration

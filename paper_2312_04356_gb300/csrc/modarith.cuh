@@ -49,6 +49,34 @@ __device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wp, u64 q) {
     return r >= q ? r - q : r;
 }
 
+// (hi:lo) += x y, the 128-bit product formed from four 32 x 32 products in one carry chain of
+// 32-bit multiply-adds (the low and high halves of the 64-bit product share their partial
+// products)
+__device__ __forceinline__ void mac128(u64& lo, u64& hi, u64 x, u64 y) {
+    unsigned a0, a1, a2, a3;
+    asm("mov.b64 {%0, %1}, %4;\n\t"
+        "mov.b64 {%2, %3}, %5;"
+        : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
+        : "l"(lo), "l"(hi));
+    const unsigned x0 = (unsigned)x, x1 = (unsigned)(x >> 32), y0 = (unsigned)y, y1 = (unsigned)(y >> 32);
+    asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "madc.hi.u32    %3, %5, %7, %3;\n\t"
+        "mad.lo.cc.u32  %1, %4, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32       %3, %3, 0;\n\t"
+        "mad.lo.cc.u32  %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32       %3, %3, 0;"
+        : "+r"(a0), "+r"(a1), "+r"(a2), "+r"(a3)
+        : "r"(x0), "r"(x1), "r"(y0), "r"(y1));
+    asm("mov.b64 %0, {%2, %3};\n\t"
+        "mov.b64 %1, {%4, %5};"
+        : "=l"(lo), "=l"(hi)
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3));
+}
+
 // reduce an arbitrary 64-bit word mod q (q < 2^61): (0:x) < 2^64 <= 2^(2s) whenever s >= 32
 __device__ __forceinline__ u64 reduce64(u64 x, const DevMod& m) { return barrett_reduce128(0, x, m); }
 
