@@ -325,6 +325,42 @@ def lockstep_batches(K, torch, s, B, rounds, timing_B=0):
             kst = K.ckks_ctx_kernel_stats(ctx)
             del ins
             K.ckks_sync(ctx)
+    # the stride-2 entries of stages 2 and 3 (Alg. 2 layers, 16 x 32 x 32 -> 32 x 16 x 16 and
+    # 32 x 16 x 16 -> 64 x 8 x 8) as lockstep batches of B and one at a time; their inputs are
+    # EvalMod outputs of a config-2 bootstrap (the level and scale every such layer receives)
+    x0 = K.ckks_conv2d_cins(ctx, keys, s["ct"], s["conv"])
+    re, im = K.ckks_bootstrap(ctx, keys, s["bt"], x0)
+    for nm, (w_in, h_in, cin, cout) in (("entry_s1_s2", (64, 32, 16, 32)), ("entry_s2_s3", (32, 16, 32, 64))):
+        b_in = K.ckks_boot_create(ctx, w_in, h_in, cin, stride=2)
+        b_out = K.ckks_boot_create(ctx, w_in // 2, h_in // 2, cout)
+        Wd = WL.weights(12, cout, cin, 3, "gauss")
+        cs = [K.ckks_ptset_conv_fused_s2(ctx, Wd, cin, cout, 3, w_in, 0, 1, (2.0 ** 49 * q[1]) / delta[1])]
+        K.ckks_keys_add_rotations(ctx, keys, sorted(set(K.ckks_boot_rotations(b_in)) | set(K.ckks_boot_rotations(b_out))
+                                                    | set(K.ckks_ptset_rotations(cs[0]))))
+
+        def batch_call():
+            return K.ckks_downsample_layer_batched(ctx, keys, [[re]] * B, [[im]] * B, b_in, cs, b_out)
+
+        def one_call():
+            return K.ckks_downsample_layer(ctx, keys, [re], [im], b_in, cs, b_out)
+        batch_call()
+        one_call()
+        t_b = timed(lambda: batch_call())
+        t_1 = timed(lambda: one_call())
+        out[nm] = {"B": B, "ms_per_ct": round(t_b / B, 3), "one_at_a_time_ms": round(t_1, 3),
+                   "speedup": round(t_1 / (t_b / B), 3), "execution": "eager (not a graph)"}
+        K.ckks_sync(ctx)
+    # a ResNet-20-shaped inference: 9 blocks per stage, the first block of stages 2 and 3 the
+    # stride-2 entry (HActivation excluded as in the config-2 block)
+    per = {k: (out[k]["ms_per_ct"], out[k]["one_at_a_time_ms"]) for k in out}
+    inf_b = 9 * per["cfg3_s1"][0] + per["entry_s1_s2"][0] + 8 * per["cfg3_s2"][0] + per["entry_s2_s3"][0] + \
+        8 * per["cfg3_s3"][0]
+    inf_1 = 9 * per["cfg3_s1"][1] + per["entry_s1_s2"][1] + 8 * per["cfg3_s2"][1] + per["entry_s2_s3"][1] + \
+        8 * per["cfg3_s3"][1]
+    out["resnet20_inference"] = {"batched_ms_per_inference": round(inf_b, 1), "one_at_a_time_ms": round(inf_1, 1),
+                                 "batched_inferences_per_s": round(1e3 / inf_b, 3),
+                                 "how": "9 x 16x32x32 block + stride-2 entry + 8 x 32x16x16 + stride-2 entry + 8 x "
+                                        "64x8x8, per-ciphertext times of B-wide lockstep batches"}
     return out, kst
 
 
@@ -723,6 +759,11 @@ def run_ours(args):
                       "(the batch's CTAs share them through L2) and every ciphertext's own words")
     roof_b["kernels"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
                          for k, v in sorted(kst_b.items(), key=lambda kv: -kv[1]["ms"])[:8]}
+    # the serving loop (config 5's continuous batching, config-2 requests): capacity and one
+    # Poisson load at 0.8 of it with 8 slots, beside one slot (the unbatched plain path)
+    cap, loads, plain, _ = serve_figures(K, s, 8, 2.0, loads=(0.8,), with_plain=True)
+    serving = {"slots": 8, "mix": "70% one config-2 block, 30% two-block chains; host limbs in and out",
+               "capacity_closed_loop": cap, "poisson_0.8": loads[0], "plain_one_slot": plain}
     if rank != 0:
         return
     cpu = None
@@ -741,7 +782,8 @@ def run_ours(args):
                        "execution": "CUDA graph replay of the block",
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "gpu_launches": launches, "launches_per_block": per_graph,
-            "batched": batched, "batched_lockstep": lock, "roofline_batched": roof_b, "autotune": tuned,
+            "batched": batched, "batched_lockstep": lock, "roofline_batched": roof_b, "serving": serving,
+            "autotune": tuned,
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(host_in.nbytes),
                     "d2h_bytes_per_step": int(host_out.nbytes)},
             "roofline": roof, "roofline_keyswitch": roof_ks, "roofline_ntt_alu": roof_alu, "op_counts": counts,
@@ -1010,26 +1052,13 @@ def run_cfg4(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
-    """The serving loop at N = 2^16 under Poisson arrivals: 70% one-block requests (a config-2
-    block) and 30% two-block chains, at three offered loads relative to the measured capacity;
-    8 slots, no HBM budget.  Reports completed requests/s, p50/p99/mean latency per load."""
-    import torch
-    from paper_2312_04356_gb300 import build
-    build.build()
-    import paper_2312_04356_gb300.ckks as K
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    s = block_setup(K, torch, seed=1)
+def serve_figures(K, s, slots, seconds, loads=(0.5, 0.8, 0.95), with_plain=False):
+    """The serving loop at N = 2^16 (config-2 blocks): 70% one-block requests and 30% two-block
+    chains, inputs and outputs as host limbs; a saturating closed loop gives the capacity, then
+    Poisson arrivals at the given fractions of it; with_plain, the same closed loop with one slot
+    (the unbatched plain GPU path).  Returns (capacity, [per-load figures], plain, model info)."""
     ctx = s["ctx"]
-    K.ckks_autotune(ctx, 3)
     q, p, psi, delta = K.ckks_ctx_info(ctx)
-    slots = max(1, args.batch)
-    srv = K.ckks_server_create(ctx, s["keys"], slots, 0)
-    A = K.ckks_server_add_model(srv, [s["conv"]], [s["bt"]])
-    B = K.ckks_server_add_model(srv, [s["conv"], s["conv"]], [s["bt"], s["bt"]])
-    infoA, infoB = K.ckks_server_model_info(srv, A), K.ckks_server_model_info(srv, B)
-    K.ckks_server_start(srv)
     inputs = []
     for i in range(4):
         x = WL.image(200 + i, s["spec"]["cin"], s["spec"]["w0"])
@@ -1038,7 +1067,14 @@ def run_serve(args):
     K.ckks_sync(ctx)
     g = np.random.default_rng(17)
 
-    def run(rate, seconds, closed=False):
+    def make(n_slots):
+        srv = K.ckks_server_create(ctx, s["keys"], n_slots, 0)
+        A = K.ckks_server_add_model(srv, [s["conv"]], [s["bt"]])
+        B = K.ckks_server_add_model(srv, [s["conv"], s["conv"]], [s["bt"], s["bt"]])
+        K.ckks_server_start(srv)
+        return srv, A, B
+
+    def run(srv, A, B, n_slots, rate, secs, closed=False):
         K.ckks_server_reset_stats(srv)
         ids = []
         t0 = time.perf_counter()
@@ -1046,15 +1082,15 @@ def run_serve(args):
         n_req = 0
         while True:
             now = time.perf_counter()
-            if now - t0 > seconds:
+            if now - t0 > secs:
                 break
             if closed or now >= t_next:
                 model = A if g.random() < 0.7 else B
                 ids.append(K.ckks_server_submit(srv, model, inputs[n_req % len(inputs)], 1, delta[1]))
                 n_req += 1
                 t_next += float(g.exponential(1.0 / rate)) if not closed else 0.0
-                if closed and len(ids) >= 4 * slots:
-                    K.ckks_server_wait(srv, ids[-3 * slots], 120)
+                if closed and len(ids) >= 4 * n_slots:
+                    K.ckks_server_wait(srv, ids[-3 * n_slots], 120)
             else:
                 time.sleep(min(t_next - now, 0.001))
         for r in ids:
@@ -1063,27 +1099,53 @@ def run_serve(args):
         for r in ids:
             K.ckks_server_result(srv, r, ctx.n)
         st = K.ckks_server_stats(srv)
-        return {"offered_per_s": None if closed else rate, "requests": len(ids),
+        return {"offered_per_s": None if closed else round(rate, 2), "requests": len(ids),
                 "completed_per_s": round(st["completed"] / (t_end - t0), 2), "p50_ms": round(st["p50_ms"], 2),
                 "p99_ms": round(st["p99_ms"], 2), "mean_ms": round(st["mean_ms"], 2),
                 "max_in_flight": int(st["max_in_flight"]), "failed": int(st["failed"])}
 
-    run(10.0, 1.0)                                   # warm-up
+    srv, A, B = make(slots)
+    info = [K.ckks_server_model_info(srv, A), K.ckks_server_model_info(srv, B)]
+    run(srv, A, B, slots, 10.0, 1.0)                                   # warm-up
+    cap = run(srv, A, B, slots, None, seconds, closed=True)           # saturating closed loop
+    per_load = [run(srv, A, B, slots, f * cap["completed_per_s"], seconds) for f in loads]
+    srv.close()
+    plain = None
+    if with_plain:
+        srv, A, B = make(1)
+        run(srv, A, B, 1, 10.0, 0.5)
+        plain = run(srv, A, B, 1, None, seconds, closed=True)
+        srv.close()
+    return cap, per_load, plain, info
+
+
+def run_serve(args):
+    """The serving loop at N = 2^16 under Poisson arrivals: 70% one-block requests (a config-2
+    block) and 30% two-block chains, at three offered loads relative to the measured capacity;
+    --batch slots, no HBM budget.  Reports completed requests/s, p50/p99/mean latency per load,
+    beside the unbatched plain path (one slot)."""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = block_setup(K, torch, seed=1)
+    K.ckks_autotune(s["ctx"], 3)
+    slots = max(1, args.batch)
     sampler = ClockSampler(0)
     sampler.start()
-    cap = run(None, args.serve_seconds, closed=True)  # saturating closed loop: the capacity
-    loads = [run(f * cap["completed_per_s"], args.serve_seconds) for f in (0.5, 0.8, 0.95)]
+    cap, loads, plain, info = serve_figures(K, s, slots, args.serve_seconds, with_plain=True)
     clocks = sampler.stop()
     line = {"metric": "serving: completed requests/s and latency at N=2^16 (Poisson mix)",
             "value": cap["completed_per_s"], "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": "70% one config-2 block, 30% chains of two blocks; requests carry host "
                                    "coefficient limbs in and out (H2D, NTT, blocks, iNTT, D2H)",
-                       "slots": slots, "hbm_budget": 0, "footprint_bytes": [infoA["footprint"], infoB["footprint"]],
-                       "kernels_per_request": [infoA["kernels"], infoB["kernels"]]},
-            "capacity_closed_loop": cap, "poisson": loads, "clocks": clocks}
+                       "slots": slots, "hbm_budget": 0, "footprint_bytes": [i["footprint"] for i in info],
+                       "kernels_per_request": [i["kernels"] for i in info]},
+            "capacity_closed_loop": cap, "poisson": loads, "plain_one_slot": plain, "clocks": clocks}
     print(json.dumps(line), flush=True)
-    srv.close()
 
 
 def run_batch(args):

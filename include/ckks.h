@@ -468,6 +468,14 @@ int ckks_block_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_c
 int ckks_block_batched_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
                                     const ckks_ptset* conv, const ckks_boot* bt, ckks_ct* const* out,
                                     ckks_graph** graph);
+/* The Alg. 2 layer of ckks_downsample_layer for B independent inputs as one lockstep batch:
+ * input b is the n_in pairs re[b * n_in + t], im[b * n_in + t] (t < n_in; every pair at the
+ * level and scale of an EvalMod output), all inputs share bt_in, conv[n_in] and bt_out; out[b]
+ * receives exactly what ckks_downsample_layer gives for input b.  Errors as
+ * ckks_downsample_layer and ckks_block_batched. */
+int ckks_downsample_layer_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, int n_in, const ckks_ct* const* re,
+                                  const ckks_ct* const* im, const ckks_boot* bt_in, const ckks_ptset* const* conv,
+                                  const ckks_boot* bt_out, ckks_ct* const* out);
 
 /* ---- serving loop ----------------------------------------------------------------
  * Continuous batching of inference requests (no counterpart in the paper, whose

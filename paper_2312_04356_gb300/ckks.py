@@ -161,6 +161,7 @@ _SIGS = {
     "ckks_batch_launch": [VP],
     "ckks_block_batched": [VP, VP, I, PVP, VP, VP, PVP],
     "ckks_block_batched_graph_create": [VP, VP, I, PVP, VP, VP, PVP, PVP],
+    "ckks_downsample_layer_batched": [VP, VP, I, I, PVP, PVP, VP, PVP, VP, PVP],
     "ckks_batch_destroy": [VP],
     "ckks_eval_relu": [VP, VP, VP, VP, VP, I, VP],
     "ckks_rescale_noalloc": [VP, VP, I, VP],
@@ -863,6 +864,18 @@ def ckks_block_batched(ctx, keys, ins, conv, bt, outs=None):
     outs = outs or [ckks_ct_create(ctx) for _ in ins]
     assert len(outs) == len(ins)
     ctx.check(lib().ckks_block_batched(ctx, keys, len(ins), _ptrs(ins), conv, bt, _ptrs(outs)))
+    return outs
+
+
+def ckks_downsample_layer_batched(ctx, keys, res, ims, bt_in, convs, bt_out, outs=None):
+    """res[b][t], ims[b][t]: input b's n_in EvalMod output pairs; one lockstep batch over b"""
+    B, n_in = len(res), len(convs)
+    assert all(len(r) == n_in for r in res) and all(len(i) == n_in for i in ims) and len(ims) == B
+    outs = outs or [ckks_ct_create(ctx) for _ in range(B)]
+    flat_r = [c for r in res for c in r]
+    flat_i = [c for i in ims for c in i]
+    ctx.check(lib().ckks_downsample_layer_batched(ctx, keys, B, n_in, _ptrs(flat_r), _ptrs(flat_i), bt_in,
+                                                  _ptrs(convs), bt_out, _ptrs(outs)))
     return outs
 
 

@@ -1564,6 +1564,41 @@ int ckks_block_batched_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int B,
     });
 }
 
+int ckks_downsample_layer_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, int n_in, const ckks_ct* const* re,
+                                  const ckks_ct* const* im, const ckks_boot* bt_in, const ckks_ptset* const* conv,
+                                  const ckks_boot* bt_out, ckks_ct* const* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(keys);
+        REQ(re);
+        REQ(im);
+        REQ(out);
+        CK_CHECK(B >= 1 && B <= 1024, CKKS_EINVAL, "B must be in [1, 1024]");
+        std::vector<const ckks_ct*> vre, vim;
+        std::vector<const ckks_ptset*> vconv;
+        ds_args(n_in, re, im, conv, bt_in, bt_out, vre, vim, vconv);     // checks input 0's n_in pairs
+        std::vector<ckks_ct> R, I;
+        std::vector<const ckks_ct*> col(B);
+        for (int t = 0; t < n_in; ++t) {
+            for (int b = 0; b < B; ++b) col[b] = re[(size_t)b * n_in + t];
+            R.push_back(gather_batch(ctx, B, col.data()));
+            for (int b = 0; b < B; ++b) col[b] = im[(size_t)b * n_in + t];
+            I.push_back(gather_batch(ctx, B, col.data()));
+        }
+        for (int b = 0; b < B; ++b) {
+            REQ(out[b]);
+            for (int u = 0; u < B * n_in; ++u)
+                CK_CHECK(out[b] != re[u] && out[b] != im[u], CKKS_EINVAL, "outputs must not alias inputs");
+        }
+        std::vector<const ckks_ct*> pr, pi;
+        for (int t = 0; t < n_in; ++t) {
+            pr.push_back(&R[t]);
+            pi.push_back(&I[t]);
+        }
+        scatter_batch(ctx, ops::downsample_layer(*keys, *bt_in, *bt_out, pr, pi, vconv), out, false);
+    });
+}
+
 int ckks_graph_launch(ckks_graph* g, void* stream) {
     if (!g) return CKKS_EINVAL;
     return guard(g->ctx, [&] {

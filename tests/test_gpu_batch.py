@@ -135,3 +135,42 @@ def test_batched_block_arguments():
     low = K.ckks_rescale(ctx, K.ckks_mul_int(ctx, d["gcts"][1], 1))
     with pytest.raises(K.CkksError):                                    # inputs at different levels
         K.ckks_block_batched(ctx, keys, [d["gcts"][0], low], d["gplan"], d["bt"])
+
+
+def test_batched_downsample_layer_equals_one_at_a_time():
+    """Alg. 2 for B = 2 inputs (each two EvalMod output pairs of the config-2 chain at N = 2^10)
+    as one lockstep batch: each output equals ckks_downsample_layer on that input alone"""
+    from paper_2312_04356_gb300 import ckks as K
+    spec = WL.CONV["cfg2_small"]
+    w0, w, C = spec["w0"], E.pad_width(spec["w0"], spec["f"]), 16
+    ctx = gpu_ctx("cfg2_small", 56)
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    bt = K.ckks_boot_create(ctx, w, w0, spec["cout"])
+    bt_in = K.ckks_boot_create(ctx, w, w0, C, stride=2)
+    bt_out = K.ckks_boot_create(ctx, w // 2, w0 // 2, 4 * C)
+    W = WL.weights(56, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+    conv = K.ckks_ptset_conv_fused(ctx, W, spec["cin"], spec["cout"], spec["f"], w, 1, (2.0 ** 49 * q[1]) / delta[1])
+    W2 = WL.weights(57, 4 * C, 2 * C, 3, "normal")
+    convs = [K.ckks_ptset_conv_fused_s2(ctx, W2, 2 * C, 4 * C, 3, w, t, 1, (2.0 ** 49 * q[1]) / delta[1])
+             for t in range(2)]
+    rots = set(K.ckks_ptset_rotations(conv))
+    for o in (bt, bt_in, bt_out):
+        rots |= set(K.ckks_boot_rotations(o))
+    for o in convs:
+        rots |= set(K.ckks_ptset_rotations(o))
+    keys = K.ckks_keygen(ctx, sorted(rots), True)
+    res, ims = [], []
+    for b in range(2):
+        rb, ib = [], []
+        for t in range(2):
+            x = WL.image(60 + 2 * b + t, spec["cin"], w0)
+            ct = K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, x, w, 1, delta[1]), 60 + 2 * b + t)
+            r_, i_ = K.ckks_bootstrap(ctx, keys, bt, K.ckks_conv2d_cins(ctx, keys, ct, conv))
+            rb.append(r_)
+            ib.append(i_)
+        res.append(rb)
+        ims.append(ib)
+    outs = K.ckks_downsample_layer_batched(ctx, keys, res, ims, bt_in, convs, bt_out)
+    for b in range(2):
+        one = K.ckks_downsample_layer(ctx, keys, res[b], ims[b], bt_in, convs, bt_out)
+        assert (K.ckks_ct_export_rns(ctx, outs[b]) == K.ckks_ct_export_rns(ctx, one)).all()
