@@ -169,6 +169,11 @@ int ckks_ctx_set_pdl(ckks_ctx* ctx, int on);
  * stream, e.g. so that per-kernel event timing measures each kernel alone.  Results are
  * identical either way. */
 int ckks_ctx_set_side_streams(ckks_ctx* ctx, int on);
+/* on != 0: the independent products of one generation of a Chebyshev evaluation's power
+ * ladder (T_3 and T_4; T_5 .. T_8) that are taken at the same level run as one lockstep batch
+ * (one launch per kernel for all of them, the relinearisation key read once) instead of side
+ * by side on the side streams; results are identical either way.  Off by default. */
+int ckks_ctx_set_inner_batching(ckks_ctx* ctx, int on);
 
 /* ---- keys (Sec. 2.1 KeyGen) ----------------------------------------------- */
 /* Secret key s (h-sparse or uniform ternary), public key (-a s + e, a) over Q_L,
@@ -476,6 +481,15 @@ int ckks_block_batched_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int B,
 int ckks_downsample_layer_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, int n_in, const ckks_ct* const* re,
                                   const ckks_ct* const* im, const ckks_boot* bt_in, const ckks_ptset* const* conv,
                                   const ckks_boot* bt_out, ckks_ct* const* out);
+/* Lockstep batches of ckks_bootstrap (out_re[b], out_im[b] from in[b]), ckks_eval_poly and
+ * ckks_eval_relu (out[b] from in[b]): every input at the same level and scale, each output
+ * exactly what the single-ciphertext call gives; errors as those calls and ckks_block_batched. */
+int ckks_bootstrap_batched(ckks_ctx* ctx, const ckks_keys* keys, const ckks_boot* bt, int B, const ckks_ct* const* in,
+                           ckks_ct* const* out_re, ckks_ct* const* out_im);
+int ckks_eval_poly_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                           const double* coeffs, int deg, int basis, double a, double b, ckks_ct* const* out);
+int ckks_eval_relu_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                           const double* coeffs, const int* degs, int n_stages, ckks_ct* const* out);
 
 /* ---- serving loop ----------------------------------------------------------------
  * Continuous batching of inference requests (no counterpart in the paper, whose
@@ -549,9 +563,16 @@ int ckks_downsample_layer_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int
 
 /* ---- polynomial evaluation (HActivation) --------------------------------- */
 #define CKKS_BASIS_CHEB 0
-/* sum_k c_k T_k(y), y = (2x - a - b) / (b - a) (only a = -1, b = 1 supported); T_k from
- * T_{ceil(k/2)} T_{floor(k/2)}, each c_k T_k brought to the canonical scale of the
- * common target level after one rescale; levels used: ceil(log2 deg) + 1. */
+#define CKKS_BASIS_POWER 1
+/* p(x) for slots x in [a, b] (HActivation, Sec. 2.4.2).  CKKS_BASIS_CHEB: p = sum_k c_k T_k(y),
+ * y = (2x - a - b) / (b - a); CKKS_BASIS_POWER: p = sum_k c_k x^k, re-expressed on the host in
+ * FP64 as a Chebyshev series in y (well conditioned for moderate degrees only).  For [a, b] !=
+ * [-1, 1] the variable y costs one level: x times llround(alpha Delta_(l-1) q_l / scale), alpha =
+ * 2 / (b - a), rescaled onto the canonical scale, then -(a + b) / (b - a) added.  T_k from
+ * T_{ceil(k/2)} T_{floor(k/2)} (baby and giant steps, Chebyshev division), each piece brought to
+ * the canonical scale of its target level after one rescale; levels used: ceil(log2 deg) + 1
+ * (+ 1 for the change of variable).  Errors: CKKS_EINVAL (deg < 1, a >= b, unknown basis),
+ * CKKS_ELEVEL. */
 int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, int deg,
                    int basis, double a, double b, ckks_ct* out);
 

@@ -73,6 +73,15 @@ class BsgsPlan:
         return sorted({r for r in baby + giant if r})
 
 
+def power_in_y(c, alpha, beta):
+    """sum_k c_k x^k with x = (y - beta) / alpha, as power coefficients in y (binomial expansion)"""
+    out = [0.0] * len(c)
+    for k, ck in enumerate(c):
+        for j in range(k + 1):
+            out[j] += ck * math.comb(k, j) * (-beta) ** (k - j) / alpha ** k
+    return out
+
+
 def default_bsgs_B(count):
     """Baby-step count: 2^ceil(log2(count)/2)."""
     return 1 << math.ceil(math.log2(count) / 2) if count > 1 else 1
@@ -714,6 +723,28 @@ class Oracle:
         want = self.poly_out_level(x.level, depth + 1)
         assert out.level >= want, (out.level, want)
         return self.level_down(out, want)
+
+    def affine(self, x, alpha, beta):
+        """alpha x + beta: x times the integer llround(alpha Delta_(l-1) q_l / scale), rescaled onto
+        the canonical scale Delta_(l-1) (one level), then beta added"""
+        P = self.P
+        l = x.level
+        assert l >= 1
+        c = round_half_away(alpha * (P.delta[l - 1] * float(P.q[l])) / x.scale)
+        y = self.rescale(self.mul_int(x, c))
+        y.scale = P.delta[l - 1]
+        return self.add_const(y, beta)
+
+    def eval_poly(self, x, coeffs, a=-1.0, b=1.0, basis="cheb"):
+        """p(x) for x in [a, b]: the variable y = (2x - a - b) / (b - a) by `affine` (skipped for
+        [-1, 1]); a power-basis p is first re-expressed as a Chebyshev series in y (FP64: the
+        binomial change of variable, then numpy's poly2cheb); then cheb_eval"""
+        coeffs = [float(v) for v in coeffs]
+        alpha, beta = 2.0 / (b - a), -(a + b) / (b - a)
+        if basis == "power":
+            coeffs = list(np.polynomial.chebyshev.poly2cheb(power_in_y(coeffs, alpha, beta)))
+        y = x if (a == -1.0 and b == 1.0) else self.affine(x, alpha, beta)
+        return self.cheb_eval(y, coeffs)
 
     def eval_mod(self, x, coeffs, r):
         """cos(2 pi (K y - 1/4) / 2^r) by Chebyshev, then r double angles -> sin(2 pi K y)"""

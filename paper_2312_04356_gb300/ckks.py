@@ -18,7 +18,7 @@ SO_PATH = os.path.join(_HERE, "_build", "libckks_gb300.so")
 
 CKKS_OK, CKKS_EINVAL, CKKS_ENOKEY, CKKS_ELEVEL, CKKS_ENOMEM, CKKS_ETIMEOUT, CKKS_ECUDA = range(7)
 CKKS_SLOT, CKKS_COEFF, CKKS_CINS_REAL = 0, 1, 2
-CKKS_BASIS_CHEB = 0
+CKKS_BASIS_CHEB, CKKS_BASIS_POWER = 0, 1
 
 _lib = None
 
@@ -58,6 +58,7 @@ _SIGS = {
     "ckks_ctx_destroy": [VP],
     "ckks_ctx_set_allocator": [VP, VP, VP, VP],
     "ckks_ctx_pool_stats": [VP, I, VP],
+    "ckks_ctx_set_inner_batching": [VP, I],
     "ckks_sync": [VP],
     "ckks_ctx_info": [VP, VP, VP, VP, VP],
     "ckks_ctx_gauss_table": [VP, VP],
@@ -162,6 +163,9 @@ _SIGS = {
     "ckks_block_batched": [VP, VP, I, PVP, VP, VP, PVP],
     "ckks_block_batched_graph_create": [VP, VP, I, PVP, VP, VP, PVP, PVP],
     "ckks_downsample_layer_batched": [VP, VP, I, I, PVP, PVP, VP, PVP, VP, PVP],
+    "ckks_bootstrap_batched": [VP, VP, VP, I, PVP, PVP, PVP],
+    "ckks_eval_poly_batched": [VP, VP, I, PVP, VP, I, I, D, D, PVP],
+    "ckks_eval_relu_batched": [VP, VP, I, PVP, VP, VP, I, PVP],
     "ckks_batch_destroy": [VP],
     "ckks_eval_relu": [VP, VP, VP, VP, VP, I, VP],
     "ckks_rescale_noalloc": [VP, VP, I, VP],
@@ -370,6 +374,10 @@ def ckks_ctx_pool_stats(ctx, reset_high=False):
     a = np.zeros(4, dtype=np.uint64)
     ctx.check(lib().ckks_ctx_pool_stats(ctx, int(reset_high), _ptr(a)))
     return dict(zip(["used", "used_high", "reserved", "reserved_high"], [int(x) for x in a]))
+
+
+def ckks_ctx_set_inner_batching(ctx, on):
+    ctx.check(lib().ckks_ctx_set_inner_batching(ctx, int(on)))
 
 
 def ckks_ctx_set_side_streams(ctx, on):
@@ -876,6 +884,30 @@ def ckks_downsample_layer_batched(ctx, keys, res, ims, bt_in, convs, bt_out, out
     flat_i = [c for i in ims for c in i]
     ctx.check(lib().ckks_downsample_layer_batched(ctx, keys, B, n_in, _ptrs(flat_r), _ptrs(flat_i), bt_in,
                                                   _ptrs(convs), bt_out, _ptrs(outs)))
+    return outs
+
+
+def ckks_bootstrap_batched(ctx, keys, bt, ins):
+    re = [ckks_ct_create(ctx) for _ in ins]
+    im = [ckks_ct_create(ctx) for _ in ins]
+    ctx.check(lib().ckks_bootstrap_batched(ctx, keys, bt, len(ins), _ptrs(ins), _ptrs(re), _ptrs(im)))
+    return re, im
+
+
+def ckks_eval_poly_batched(ctx, keys, ins, coeffs, basis=CKKS_BASIS_CHEB, a=-1.0, b=1.0):
+    outs = [ckks_ct_create(ctx) for _ in ins]
+    c = _f64(coeffs)
+    ctx.check(lib().ckks_eval_poly_batched(ctx, keys, len(ins), _ptrs(ins), _ptr(c), len(c) - 1, basis, a, b,
+                                           _ptrs(outs)))
+    return outs
+
+
+def ckks_eval_relu_batched(ctx, keys, ins, stages):
+    outs = [ckks_ct_create(ctx) for _ in ins]
+    c = _f64(np.concatenate([np.asarray(st, dtype=np.float64) for st in stages]))
+    degs = np.ascontiguousarray([len(st) - 1 for st in stages], dtype=np.int32)
+    ctx.check(lib().ckks_eval_relu_batched(ctx, keys, len(ins), _ptrs(ins), _ptr(c), _ptr(degs), len(stages),
+                                           _ptrs(outs)))
     return outs
 
 

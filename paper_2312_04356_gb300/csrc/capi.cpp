@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <set>
 
@@ -258,6 +259,13 @@ int ckks_ctx_pool_stats(ckks_ctx* ctx, int reset_high, uint64_t* out) {
             CUDA_CHECK(cudaMemPoolGetAttribute(pool, attrs[k], &v));
             out[k] = v;
         }
+    });
+}
+
+int ckks_ctx_set_inner_batching(ckks_ctx* ctx, int on) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        ctx->inner_batching = on != 0;
     });
 }
 
@@ -1599,6 +1607,61 @@ int ckks_downsample_layer_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, i
     });
 }
 
+int ckks_bootstrap_batched(ckks_ctx* ctx, const ckks_keys* keys, const ckks_boot* bt, int B, const ckks_ct* const* in,
+                           ckks_ct* const* out_re, ckks_ct* const* out_im) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(keys);
+        REQ(bt);
+        batch_args(B, in, out_re);
+        batch_args(B, in, out_im);
+        for (int b = 0; b < B; ++b)
+            for (int u = 0; u < B; ++u) CK_CHECK(out_re[b] != out_im[u], CKKS_EINVAL, "outputs must be distinct");
+        ckks_ct x = gather_batch(ctx, B, in);
+        ckks_ct re, im;
+        ops::bootstrap(*keys, *bt, x, re, im);
+        scatter_batch(ctx, re, out_re, false);
+        scatter_batch(ctx, im, out_im, false);
+    });
+}
+
+int ckks_eval_poly_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                           const double* coeffs, int deg, int basis, double a, double b, ckks_ct* const* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(keys);
+        REQ(coeffs);
+        batch_args(B, in, out);
+        CK_CHECK(basis == CKKS_BASIS_CHEB || basis == CKKS_BASIS_POWER, CKKS_EINVAL, "unknown basis");
+        CK_CHECK(deg >= 1, CKKS_EINVAL, "polynomial degree must be >= 1");
+        CK_CHECK(std::isfinite(a) && std::isfinite(b) && b > a, CKKS_EINVAL, "the interval needs a < b");
+        ckks_ct x = gather_batch(ctx, B, in);
+        std::vector<double> c(coeffs, coeffs + deg + 1);
+        scatter_batch(ctx, ops::eval_poly(*keys, x, c, basis == CKKS_BASIS_POWER, a, b), out, false);
+    });
+}
+
+int ckks_eval_relu_batched(ckks_ctx* ctx, const ckks_keys* keys, int B, const ckks_ct* const* in,
+                           const double* coeffs, const int* degs, int n_stages, ckks_ct* const* out) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(keys);
+        REQ(coeffs);
+        REQ(degs);
+        batch_args(B, in, out);
+        CK_CHECK(n_stages >= 1, CKKS_EINVAL, "n_stages must be >= 1");
+        std::vector<std::vector<double>> st;
+        size_t off = 0;
+        for (int i = 0; i < n_stages; ++i) {
+            CK_CHECK(degs[i] >= 1, CKKS_EINVAL, "stage degree must be >= 1");
+            st.emplace_back(coeffs + off, coeffs + off + degs[i] + 1);
+            off += degs[i] + 1;
+        }
+        ckks_ct x = gather_batch(ctx, B, in);
+        scatter_batch(ctx, ops::eval_relu(*keys, x, st), out, false);
+    });
+}
+
 int ckks_graph_launch(ckks_graph* g, void* stream) {
     if (!g) return CKKS_EINVAL;
     return guard(g->ctx, [&] {
@@ -1708,10 +1771,11 @@ int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, cons
         CT_OK(in);
         REQ(coeffs);
         REQ(out);
-        CK_CHECK(basis == CKKS_BASIS_CHEB, CKKS_EINVAL, "only the Chebyshev basis is supported");
-        CK_CHECK(a == -1.0 && b == 1.0, CKKS_EINVAL, "only the interval [-1, 1] is supported");
+        CK_CHECK(basis == CKKS_BASIS_CHEB || basis == CKKS_BASIS_POWER, CKKS_EINVAL, "unknown basis");
+        CK_CHECK(deg >= 1, CKKS_EINVAL, "polynomial degree must be >= 1");
+        CK_CHECK(std::isfinite(a) && std::isfinite(b) && b > a, CKKS_EINVAL, "the interval needs a < b");
         std::vector<double> c(coeffs, coeffs + deg + 1);
-        assign(out, ops::cheb_eval(*keys, *in, c));
+        assign(out, ops::eval_poly(*keys, *in, c, basis == CKKS_BASIS_POWER, a, b));
     });
 }
 

@@ -393,4 +393,35 @@ std::vector<double> cheb_interp_cos(double K, int r, int deg) {
     return c;
 }
 
+// Power coefficients of p(x), x = (y - beta) / alpha, re-expressed as a Chebyshev series in y:
+// the binomial change of variable, then Horner's rule in the Chebyshev basis (y T_0 = T_1,
+// y T_j = (T_(j+1) + T_(j-1)) / 2).
+std::vector<double> power_to_cheb(const std::vector<double>& c, double alpha, double beta) {
+    const int n = (int)c.size();
+    std::vector<double> py(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        double binom = 1.0;                                  // C(k, j), j = 0 .. k
+        for (int j = 0; j <= k; ++j) {
+            py[j] += c[k] * binom * std::pow(-beta, k - j) / std::pow(alpha, k);
+            binom = binom * (k - j) / (j + 1);
+        }
+    }
+    std::vector<double> r(1, py[n - 1]);
+    for (int k = n - 2; k >= 0; --k) {
+        std::vector<double> t(r.size() + 1, 0.0);            // y * r
+        for (size_t j = 0; j < r.size(); ++j) {
+            if (j == 0) {
+                t[1] += r[0];
+            } else {
+                t[j + 1] += 0.5 * r[j];
+                t[j - 1] += 0.5 * r[j];
+            }
+        }
+        t[0] += py[k];
+        r.swap(t);
+    }
+    r.resize(n);
+    return r;
+}
+
 }  // namespace fp64

@@ -54,6 +54,9 @@ struct ConvTab {
     // exact (rounded) conversion only: 1/q_i as doubles [nin], p_m - (prod q_i mod p_m) [nout]
     double* d_inv_q = nullptr;
     u64* d_corr = nullptr;
+    // N^{-1} qhat_i^{-1} mod q_i and its Shoup companion, [nin][2]: the factor an inverse NTT
+    // ends with when its output feeds this conversion directly (prescaled inputs)
+    u64* d_iscale = nullptr;
 };
 
 // A caller-provided device allocator (ckks_ctx_set_allocator); both null = the library's own
@@ -103,6 +106,9 @@ struct ckks_ctx {
     cudaStream_t side[NSIDE] = {};
     cudaEvent_t fork_ev = nullptr, side_ev[NSIDE] = {};
     bool side_streams_on = true;
+    // independent products inside one operation (a generation of the Chebyshev power ladder)
+    // run as one lockstep batch instead of side by side on side streams
+    bool inner_batching = false;
     DevAlloc alloc;       // caller allocator for the buffers of this context's calls
     // side streams are used only without a caller allocator: a stream-ordered caching
     // allocator (PyTorch's) reuses a freed block on the stream it was allocated on, so every
@@ -123,6 +129,9 @@ struct ckks_ctx {
     // from the start of [ndig][next][N]) and their prime ids, for one NTT launch
     std::vector<int*> d_modup_off, d_modup_pid;
     std::vector<int> modup_nrows;
+    // per level: for each of the l + 1 rows of a ModUp input, N^{-1} qhat^{-1} of its digit's
+    // conversion (Shoup pairs, [l+1][2]), the inverse NTT's final factor for prescaled inputs
+    std::vector<u64*> d_modup_iscale;
     std::map<std::pair<int, int>, std::unique_ptr<ConvTab>> modup_tabs;  // (level, digit)
     std::map<int, std::unique_ptr<ConvTab>> moddown_tabs;               // level
     std::map<int, std::unique_ptr<ConvTab>> mdrs_tabs;                  // level: {q_l, P} -> Q_{l-1}
@@ -303,7 +312,10 @@ struct LinComb {
 };
 void lincomb(const ckks_ctx* c, const LinComb& t, u64* o, int nl, const int* ids, int lpp);
 void autotune_ntt(ckks_ctx* c, int reps);
-void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0);
+// (osc: per row r = k % lpp a Shoup pair (w, w') at osc[2r], osc[2r + 1] that replaces the final
+// factor N^{-1}, e.g. N^{-1} qhat^{-1} for a base conversion that reads the output prescaled)
+void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0,
+                 const u64* osc = nullptr);
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void sub(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void neg(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, const int* ids, int lpp);
@@ -346,8 +358,10 @@ void sub_mul_scalar(const ckks_ctx* c, const u64* a, const u64* b, const u64* s,
                     int nlimbs, const int* ids, int lpp, size_t a_pstride = 0);
 // fast base conversion, coefficient domain: in [nin][N] (limb stride in_stride words),
 // out rows written at out + out_row[m]*N
+// (prescaled: the inputs already carry the factor qhat_i^{-1}, see ConvTab::d_iscale)
 void base_convert(const ckks_ctx* c, const ConvTab& t, const u64* in, size_t in_stride, u64* out,
-                  size_t out_stride, int npoly, size_t in_poly_stride, size_t out_poly_stride);
+                  size_t out_stride, int npoly, size_t in_poly_stride, size_t out_poly_stride,
+                  bool prescaled = false);
 // several conversions in one launch (e.g. every digit of a ModUp)
 struct ConvJob {
     const u64* in;
@@ -358,13 +372,15 @@ struct ConvJob {
     const u64* corr;
     int nin, nout, ngroups;
     size_t in_pstride, out_pstride;
+    bool prescaled;        // inputs are x_i qhat_i^{-1} already (no product on load)
 };
 struct ConvJobs {
     static constexpr int MAX = 4;
     int n;
     ConvJob job[MAX];
 };
-void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t in_pstride, size_t out_pstride);
+void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t in_pstride, size_t out_pstride,
+                  bool prescaled = false);
 void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly);
 // key-switch inner product: D [ndig][next][N], key rows krow[e] of [ndig][nall][N];
 // ob/oa [next][N] = sum_d D_d(sigma_g) * key_d ; g = 1 means no automorphism
@@ -428,6 +444,7 @@ std::vector<double> decompose_kernels(const double* W, int cout, int cin, int f,
 std::vector<cplx> real_cins_slots(const double* m, int C, int two_l);
 std::vector<double> cins_to_reals(const std::vector<cplx>& z, int C, int two_l);
 std::vector<double> cheb_interp_cos(double K, int r, int deg);
+std::vector<double> power_to_cheb(const std::vector<double>& c, double alpha, double beta);
 int default_bsgs_B(int count);
 int boot_bsgs_B(int count);
 }  // namespace fp64

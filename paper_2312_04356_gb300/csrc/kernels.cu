@@ -181,7 +181,7 @@ constexpr int NTT_THREADS = 256;
 template <bool INV>
 __global__ void __launch_bounds__(NTT_THREADS)
     k_ntt_pass(u64* __restrict__ data, const DevPrime* __restrict__ primes, const int* __restrict__ ids, int lpp,
-               size_t pstride, int logn, int s0, int c, int logsub, int scale_out) {
+               size_t pstride, int logn, int s0, int c, int logsub, int scale_out, const u64* __restrict__ osc) {
     griddep_entry();
     extern __shared__ u64 sm[];
     const int limb = blockIdx.y;
@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(NTT_THREADS)
         __syncthreads();
     }
 
-    const u64 ninv = P->n_inv, ninvp = P->n_inv_p;
+    // the inverse transform's final factor: N^{-1}, or per row a caller-given (w, w') Shoup pair
+    const u64 ninv = osc ? osc[2 * (limb % lpp)] : P->n_inv, ninvp = osc ? osc[2 * (limb % lpp) + 1] : P->n_inv_p;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         int s, k;
         if (T1 == 1) {
@@ -337,7 +338,7 @@ __device__ __forceinline__ void inv_round(u64 (&x)[16], int t, int hi, int s0, c
 template <bool COL, bool INV, int SUBS, int MINB>
 __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ data, const DevPrime* __restrict__ primes,
                                                     const int* __restrict__ ids, int lpp, size_t pstride,
-                                                    const int* __restrict__ loff) {
+                                                    const int* __restrict__ loff, const u64* __restrict__ osc) {
     griddep_entry();
     __shared__ u64 sm[SUBS * F_STRIDE];
     const int limb = blockIdx.y;
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
         for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(sp, t + 16 * i)];
         inv_round<false>(x, t, hi, s0, P, q, q2);
         if (COL) {
-            const u64 ni = P->n_inv, nip = P->n_inv_p;
+            const u64 ni = osc ? osc[2 * r] : P->n_inv, nip = osc ? osc[2 * r + 1] : P->n_inv_p;
 #pragma unroll
             for (int i = 0; i < 16; ++i) a[gidx(t + 16 * i)] = mul_shoup(x[i], ni, nip, q);
         } else {
@@ -424,7 +425,7 @@ __device__ __forceinline__ int ins0(int t, int p) { return ((t >> p) << (p + 1))
 template <bool COL, bool INV>
 __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const DevPrime* __restrict__ primes,
                                                 const int* __restrict__ ids, int lpp, size_t pstride,
-                                                const int* __restrict__ loff) {
+                                                const int* __restrict__ loff, const u64* __restrict__ osc) {
     griddep_entry();
     __shared__ u64 sm[4 * F_STRIDE];
     const int limb = blockIdx.y;
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const De
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sm[f_slot(sp, ks[i])] = x[i];
             } else if (COL) {
-                const u64 ni = P->n_inv, nip = P->n_inv_p;
+                const u64 ni = osc ? osc[2 * r] : P->n_inv, nip = osc ? osc[2 * r + 1] : P->n_inv_p;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[gidx(ks[i])] = mul_shoup(x[i], ni, nip, q);
             } else {
@@ -545,7 +546,7 @@ constexpr int CL_SUBS = 32, CL_THREADS = 512, CL_SMEM_WORDS = CL_SUBS * F_STRIDE
 template <bool INV>
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(CL_THREADS, 2)
     k_ntt_cl(u64* __restrict__ data, const DevPrime* __restrict__ primes, const int* __restrict__ ids, int lpp,
-             size_t pstride, const int* __restrict__ loff) {
+             size_t pstride, const int* __restrict__ loff, const u64* __restrict__ osc) {
     griddep_entry();
     extern __shared__ u64 sm[];
     cg::cluster_group cl = cg::this_cluster();
@@ -633,7 +634,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(CL_THREADS, 2)
 #pragma unroll
         for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(spc, tc + 16 * i)];
         inv_round<false>(x, tc, 0, 0, P, q, q2);
-        const u64 ni = P->n_inv, nip = P->n_inv_p;
+        const u64 ni = osc ? osc[2 * r] : P->n_inv, nip = osc ? osc[2 * r + 1] : P->n_inv_p;
 #pragma unroll
         for (int i = 0; i < 16; ++i) a[((size_t)(tc + 16 * i) << 8) + col] = mul_shoup(x[i], ni, nip, q);
     }
@@ -649,27 +650,27 @@ enum NttVariant {
 
 template <bool COL, bool INV>
 void launch_ntt16_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp,
-                          size_t pstride, const int* loff) {
+                          size_t pstride, const int* loff, const u64* osc) {
     switch (v) {
         case NTT_V16_R80:
             klaunch(cx, k_ntt16<COL, INV, 16, 3>, dim3(256 / 16, nlimbs), 256, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff);
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
             break;
         case NTT_V16_R64:
             klaunch(cx, k_ntt16<COL, INV, 16, 4>, dim3(256 / 16, nlimbs), 256, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff);
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
             break;
         case NTT_V4_R80:
             klaunch(cx, k_ntt16<COL, INV, 4, 8>, dim3(256 / 4, nlimbs), 64, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff);
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
             break;
         case NTT_V4_R64:
             klaunch(cx, k_ntt16<COL, INV, 4, 12>, dim3(256 / 4, nlimbs), 64, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff);
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
             break;
         default:
             klaunch(cx, k_ntt16s<COL, INV>, dim3(256 / 4, nlimbs), 256, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff);
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
             break;
     }
 }
@@ -682,11 +683,11 @@ inline int ntt_class(int nlimbs) {
 
 template <bool INV>
 void launch_ntt_cl(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
-                   const int* loff) {
+                   const int* loff, const u64* osc) {
     static std::atomic<unsigned> done{0};
     allow_dynamic_smem((const void*)k_ntt_cl<INV>, CL_SMEM_WORDS * (int)sizeof(u64), done);
     klaunch(cx, k_ntt_cl<INV>, dim3(8, nlimbs), CL_THREADS, CL_SMEM_WORDS * sizeof(u64),
-            data, cx->d_primes, ids, lpp, pstride, loff);
+            data, cx->d_primes, ids, lpp, pstride, loff, osc);
 }
 
 // One whole N = 2^16 transform with variant v: the cluster kernel, or the two passes (forward:
@@ -694,30 +695,30 @@ void launch_ntt_cl(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, in
 // limbs per transform, split evenly over the two passes.
 template <bool INV>
 void launch_ntt_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
-                        const int* loff) {
+                        const int* loff, const u64* osc = nullptr) {
     const char* nm = INV ? "ntt_inv" : "ntt_fwd";
     const double bytes = 2.0 * nlimbs * cx->n * 8.0;
     if (v == NTT_CL) {
         KTimer kt_(cx, nm, bytes);
-        launch_ntt_cl<INV>(cx, data, nlimbs, ids, lpp, pstride, loff);
+        launch_ntt_cl<INV>(cx, data, nlimbs, ids, lpp, pstride, loff, osc);
         return;
     }
     {
         KTimer kt_(cx, nm, bytes / 2);
-        launch_ntt16_variant<!INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff);
+        launch_ntt16_variant<!INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc);
     }
     {
         KTimer kt_(cx, nm, bytes / 2);
-        launch_ntt16_variant<INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff);
+        launch_ntt16_variant<INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc);
     }
 }
 
 template <bool INV>
 void launch_ntt_transform(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
-                          const int* loff = nullptr) {
+                          const int* loff = nullptr, const u64* osc = nullptr) {
     int v = cx->ntt_choice[ntt_class(nlimbs)];
     if (v < 0) v = nlimbs >= 16 ? NTT_V16_R80 : NTT_V4_R80;
-    launch_ntt_variant<INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff);
+    launch_ntt_variant<INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc);
 }
 
 struct PassPlan {
@@ -731,7 +732,7 @@ inline std::vector<PassPlan> ntt_passes(int logn) {
 
 template <bool INV>
 void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride, PassPlan p,
-                 int scale_out) {
+                 int scale_out, const u64* osc = nullptr) {
     const int logn = cx->logn;
     int logsub = 12 - p.c;
     if (logsub < 0) logsub = 0;
@@ -743,8 +744,7 @@ void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int 
     dim3 grid(tiles, nlimbs);
     { KTimer kt_(cx, INV ? "ntt_inv" : "ntt_fwd", 2.0 * nlimbs * cx->n * 8.0 * p.c / logn);
     klaunch(cx, k_ntt_pass<INV>, grid, NTT_THREADS, smem, data, cx->d_primes, ids, lpp, pstride, logn, p.s0, p.c,
-            logsub,
-            scale_out);
+            logsub, scale_out, osc);
     }
 }
 
@@ -1323,7 +1323,7 @@ __global__ void __launch_bounds__(256, (MC <= 6 ? 4 : 3)) k_base_convert(kern::C
     u64 xh[MAXIN];
 #pragma unroll
     for (int i = 0; i < MAXIN; ++i)
-        if (i < nin) xh[i] = mul_shoup(in[i * n + j], s_qinv[i], s_qinvp[i], s_qi[i]);
+        if (i < nin) xh[i] = job.prescaled ? in[i * n + j] : mul_shoup(in[i * n + j], s_qinv[i], s_qinvp[i], s_qi[i]);
     u64 lo[MC], hi[MC];
     if (SPLIT) {
         constexpr u64 M30 = (1ull << 30) - 1;
@@ -1760,17 +1760,18 @@ void bsgs_fused(const ckks_ctx* c, const BsgsFused& t, const u64* D, const u64* 
     LAUNCH_CHECK();
 }
 
-void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride) {
+void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride, const u64* osc) {
     if (nlimbs <= 0) return;
     if (pstride == 0) pstride = (size_t)lpp * c->n;
     if (c->logn == 16) {
-        launch_ntt_transform<true>(c, data, nlimbs, ids, lpp, pstride);
+        launch_ntt_transform<true>(c, data, nlimbs, ids, lpp, pstride, nullptr, osc);
         LAUNCH_CHECK();
         return;
     }
     std::vector<PassPlan> ps = ntt_passes(c->logn);
     for (int i = (int)ps.size() - 1; i >= 0; --i)
-        launch_pass<true>(c, data, nlimbs, ids, lpp, pstride, ps[i], ps[i].s0 == 0 ? 1 : 0);
+        launch_pass<true>(c, data, nlimbs, ids, lpp, pstride, ps[i], ps[i].s0 == 0 ? 1 : 0,
+                          ps[i].s0 == 0 ? osc : nullptr);
     LAUNCH_CHECK();
 }
 
@@ -1929,15 +1930,16 @@ void sub_mul_scalar(const ckks_ctx* c, const u64* a, const u64* b, const u64* s,
     LAUNCH_CHECK();
 }
 void base_convert(const ckks_ctx* c, const ConvTab& t, const u64* in, size_t in_stride, u64* out,
-                  size_t out_stride, int npoly, size_t in_pstride, size_t out_pstride) {
+                  size_t out_stride, int npoly, size_t in_pstride, size_t out_pstride, bool prescaled) {
     CK_CHECK(in_stride == (size_t)c->n && out_stride == (size_t)c->n, CKKS_EINVAL, "limbs must be contiguous");
     ConvJobs J;
     J.n = 0;
-    add_conv_job(J, t, in, out, in_pstride, out_pstride);
+    add_conv_job(J, t, in, out, in_pstride, out_pstride, prescaled);
     base_convert_jobs(c, J, npoly);
 }
 
-void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t in_pstride, size_t out_pstride) {
+void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t in_pstride, size_t out_pstride,
+                  bool prescaled) {
     CK_CHECK(J.n < ConvJobs::MAX, CKKS_EINVAL, "too many base-conversion jobs");
     CK_CHECK(t.nin <= MAX_CONV_IN, CKKS_EINVAL, "base conversion with more than 16 input limbs");
     ConvJob& j = J.job[J.n++];
@@ -1955,6 +1957,7 @@ void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t
     j.ngroups = (t.nout + CONV_OUT - 1) / CONV_OUT;
     j.in_pstride = in_pstride;
     j.out_pstride = out_pstride;
+    j.prescaled = prescaled;
 }
 
 template <int MAXIN, bool SPLIT>

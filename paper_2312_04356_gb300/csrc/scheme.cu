@@ -95,6 +95,14 @@ static std::unique_ptr<ConvTab> make_conv_tab(ckks_ctx* c, const std::vector<int
             qmod[(size_t)t->nout * t->nin + (size_t)m * t->nin + i] = shoup(v, pm);
         }
     }
+    // N^{-1} qhat_i^{-1}: the inverse NTT that produces this conversion's inputs ends with it
+    std::vector<u64> isc(2 * t->nin);
+    for (int i = 0; i < t->nin; ++i) {
+        const u64 qi = c->mod_of[in_ids[i]];
+        isc[2 * i] = mulmod(invmod((u64)c->n % qi, qi), qinv[i], qi);
+        isc[2 * i + 1] = shoup(isc[2 * i], qi);
+    }
+    t->d_iscale = dev_upload_persistent(isc);
     std::vector<int> ids_rows = out_ids;
     ids_rows.insert(ids_rows.end(), out_rows.begin(), out_rows.end());
     t->d_in_ids = dev_upload_persistent(in_ids);
@@ -169,6 +177,7 @@ static void free_tab(ConvTab* t) {
     cudaFree(t->d_qhat_mod);
     if (t->d_inv_q) cudaFree(t->d_inv_q);
     if (t->d_corr) cudaFree(t->d_corr);
+    cudaFree(t->d_iscale);
 }
 
 ckks_ctx::~ckks_ctx() {
@@ -184,6 +193,7 @@ ckks_ctx::~ckks_ctx() {
     for (int* p : d_ext_ids) cudaFree(p);
     for (int* p : d_modup_off) cudaFree(p);
     for (int* p : d_modup_pid) cudaFree(p);
+    for (u64* p : d_modup_iscale) cudaFree(p);
     cudaFree(d_iota);
     cudaFree(d_primes);
     cudaFree(d_tables);
@@ -327,6 +337,15 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
         c->d_modup_off.push_back(dev_upload_persistent(off));
         c->d_modup_pid.push_back(dev_upload_persistent(pid));
         c->modup_nrows.push_back((int)off.size());
+        // the final factor of the inverse NTT of a ModUp input: row r of digit d gets that
+        // digit's N^{-1} qhat^{-1}
+        std::vector<u64> isc;
+        for (int d = 0; d < (int)dig.size(); ++d) {
+            std::vector<u64> h(2 * dig[d].size());
+            CUDA_CHECK(cudaMemcpy(h.data(), c->modup_tab(l, d).d_iscale, h.size() * 8, cudaMemcpyDeviceToHost));
+            isc.insert(isc.end(), h.begin(), h.end());
+        }
+        c->d_modup_iscale.push_back(dev_upload_persistent(isc));
     }
     cudaMemPool_t pool;
     int dev = 0;
@@ -530,14 +549,14 @@ DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out, int nb, size_
     DevBuf coef((size_t)nb * nl * n, c->stream);
     CUDA_CHECK(cudaMemcpy2DAsync(coef.ptr, nl * n * 8, x, xstride * 8, nl * n * 8, nb, cudaMemcpyDeviceToDevice,
                                  c->stream));
-    kern::ntt_inverse(c, coef.ptr, nb * nl, c->d_iota, nl);
+    kern::ntt_inverse(c, coef.ptr, nb * nl, c->d_iota, nl, 0, c->d_modup_iscale[level]);   // prescaled
     DevBuf D((size_t)nb * dstr, c->stream);
     const int* ext = c->d_ext_ids[level];
     kern::ConvJobs jobs;
     jobs.n = 0;
     for (int d = 0; d < ndig; ++d)
         kern::add_conv_job(jobs, c->modup_tab(level, d), coef.ptr + (size_t)dig[d].front() * n,
-                           D.ptr + (size_t)d * next * n, (size_t)nl * n, dstr);
+                           D.ptr + (size_t)d * next * n, (size_t)nl * n, dstr, true);
     kern::base_convert_jobs(c, jobs, nb);
     for (int d = 0; d < ndig; ++d) {
         u64* Dd = D.ptr + (size_t)d * next * n;
@@ -589,9 +608,10 @@ void mod_down_rescale(ckks_ctx* c, u64* acc, int level, u64* out, bool twice, in
     const int l = level, np1 = c->np + 1, npoly = 2 * nb;
     const size_t next = (size_t)l + 1 + c->np;
     const int* pid = c->d_ext_ids[level] + l;      // q_l, then the special primes
-    kern::ntt_inverse(c, acc + (size_t)l * n, npoly * np1, pid, np1, next * n);
+    const ConvTab& tab_c = c->mdrs_tab(l);
+    kern::ntt_inverse(c, acc + (size_t)l * n, npoly * np1, pid, np1, next * n, tab_c.d_iscale);
     DevBuf conv((size_t)npoly * l * n, c->stream);
-    kern::base_convert(c, c->mdrs_tab(l), acc + (size_t)l * n, n, conv.ptr, n, npoly, next * n, (size_t)l * n);
+    kern::base_convert(c, tab_c, acc + (size_t)l * n, n, conv.ptr, n, npoly, next * n, (size_t)l * n, true);
     kern::ntt_forward(c, conv.ptr, npoly * l, c->d_iota, l);
     const u64* tab = twice ? c->d_pqlinv2 : c->d_pqlinv;     // twice: 2 x the result, same pass
     const u64* s = tab + (size_t)l * c->nq;
@@ -612,10 +632,11 @@ static void mod_down(ckks_ctx* c, u64* acc, int level, u64* out, int nb = 1) {
     const int nl = level + 1, npoly = 2 * nb;
     const int next = nl + c->np;
     const int* pid = c->d_ext_ids[level] + nl;
-    kern::ntt_inverse(c, acc + (size_t)nl * n, npoly * c->np, pid, c->np, (size_t)next * n);
+    const ConvTab& tab_c = c->moddown_tab(level);
+    kern::ntt_inverse(c, acc + (size_t)nl * n, npoly * c->np, pid, c->np, (size_t)next * n, tab_c.d_iscale);
     DevBuf conv((size_t)npoly * nl * n, c->stream);
-    kern::base_convert(c, c->moddown_tab(level), acc + (size_t)nl * n, n, conv.ptr, n, npoly, (size_t)next * n,
-                       (size_t)nl * n);
+    kern::base_convert(c, tab_c, acc + (size_t)nl * n, n, conv.ptr, n, npoly, (size_t)next * n, (size_t)nl * n,
+                       true);
     kern::ntt_forward(c, conv.ptr, npoly * nl, c->d_iota, nl);
     kern::sub_mul_scalar(c, acc, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out, npoly * nl, c->d_iota, nl,
                          (size_t)next * n);
@@ -731,9 +752,10 @@ static void mod_down_poly(ckks_ctx* c, u64* x, int level, u64* out, int nb = 1, 
     const size_t n = c->n;
     const int nl = level + 1;
     if (xstride == 0) xstride = ((size_t)nl + c->np) * n;
-    kern::ntt_inverse(c, x + (size_t)nl * n, nb * c->np, c->d_ext_ids[level] + nl, c->np, xstride);
+    const ConvTab& tab_c = c->moddown_tab(level);
+    kern::ntt_inverse(c, x + (size_t)nl * n, nb * c->np, c->d_ext_ids[level] + nl, c->np, xstride, tab_c.d_iscale);
     DevBuf conv((size_t)nb * nl * n, c->stream);
-    kern::base_convert(c, c->moddown_tab(level), x + (size_t)nl * n, n, conv.ptr, n, nb, xstride, (size_t)nl * n);
+    kern::base_convert(c, tab_c, x + (size_t)nl * n, n, conv.ptr, n, nb, xstride, (size_t)nl * n, true);
     kern::ntt_forward(c, conv.ptr, nb * nl, c->d_iota, nl);
     kern::sub_mul_scalar(c, x, conv.ptr, c->d_pinv, c->d_pinv + c->nq, out, nb * nl, c->d_iota, nl, xstride);
 }
@@ -1002,6 +1024,24 @@ ckks_ct bsgs(const ckks_keys& keys, const ckks_ct& a, const ckks_ptset& ps, bool
 }
 
 // ------------------------------------------------ Chebyshev / EvalMod -----
+// Ciphertexts of one level and scale gathered into one lockstep batch, and ciphertext t of a batch
+// copied out (so that independent products inside one operation share their launches and keys)
+static ckks_ct gather_cts(const std::vector<const ckks_ct*>& v) {
+    ckks_ctx* c = v[0]->ctx;
+    ckks_ct x = new_ct(c, v[0]->level, v[0]->scale, (int)v.size());
+    for (size_t t = 0; t < v.size(); ++t) {
+        CK_CHECK(v[t]->nb == 1 && v[t]->level == x.level, CKKS_EINVAL, "gathered ciphertexts differ in level");
+        CUDA_CHECK(cudaMemcpyAsync(x.c0((int)t), v[t]->buf.ptr, x.cstride() * 8, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return x;
+}
+static ckks_ct take_ct(const ckks_ct& batch, int t) {
+    ckks_ctx* c = batch.ctx;
+    ckks_ct o = new_ct(c, batch.level, batch.scale);
+    CUDA_CHECK(cudaMemcpyAsync(o.buf.ptr, batch.c0(t), batch.cstride() * 8, cudaMemcpyDeviceToDevice, c->stream));
+    return o;
+}
+
 // Level at which to multiply two ciphertexts available at level m: a product at the
 // bottom level of the bootstrapping segment would not rescale onto the circuit segment's
 // canonical scale, so it is taken one level lower.
@@ -1044,6 +1084,34 @@ struct ChebPowers {
         const int m = prod_level(T.at(a).ctx, std::min(T.at(a).level, T.at(b).level));
         ckks_ct t = mul_relin_rescale(*keys, at(a, m), at(b, m), true);     // 2 T_a T_b
         return (a == b) ? add_const(t, -1.0) : sub(t, at(b - a, m - 1));
+    }
+    // several T_k at once: the products taken at the same level run as one lockstep batch
+    // (one relinearisation key read, every launch over all of them); same residues as product(k)
+    void products_batched(const std::vector<int>& ks) {
+        std::map<int, std::vector<int>> by_level;
+        for (int k : ks) {
+            const int a = k / 2, b = k - k / 2;
+            by_level[prod_level(T.at(a).ctx, std::min(T.at(a).level, T.at(b).level))].push_back(k);
+        }
+        for (auto& kv : by_level) {
+            const int m = kv.first;
+            const std::vector<int>& g = kv.second;
+            if (g.size() == 1) {
+                T[g[0]] = product(g[0]);
+                continue;
+            }
+            std::vector<const ckks_ct*> xa, xb;
+            for (int k : g) {
+                xa.push_back(&at(k / 2, m));
+                xb.push_back(&at(k - k / 2, m));
+            }
+            ckks_ct prod = mul_relin_rescale(*keys, gather_cts(xa), gather_cts(xb), true);     // 2 T_a T_b
+            for (size_t i = 0; i < g.size(); ++i) {
+                const int k = g[i], a = k / 2, b = k - k / 2;
+                ckks_ct t = take_ct(prod, (int)i);
+                T[k] = (a == b) ? add_const(t, -1.0) : sub(t, at(b - a, m - 1));
+            }
+        }
     }
     // the level_downs product(k) reads, made ahead (so that products can run side by side)
     void warm(int k) {
@@ -1197,6 +1265,10 @@ ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<dou
                 if (kv.second == g && !pw.T.count(kv.first)) ks.push_back(kv.first);
             if (ks.empty()) continue;
             for (int k : ks) pw.warm(k);
+            if (cx->inner_batching && ks.size() >= 2) {
+                pw.products_batched(ks);
+                continue;
+            }
             if (!cx->use_side_streams() || ks.size() < 2) {
                 for (int k : ks) pw.T[k] = pw.product(k);
                 continue;
@@ -1354,6 +1426,28 @@ ckks_ct eval_relu(const ckks_keys& keys, const ckks_ct& x, const std::vector<std
     const int lev = prod_level(x.ctx, y.level);
     CK_CHECK(lev >= 1, CKKS_ELEVEL, "not enough levels for the final product");
     return mul_relin_rescale(keys, level_down(x, lev), level_down(y, lev));
+}
+
+// alpha x + beta: x times llround(alpha Delta_(l-1) q_l / scale), rescaled onto the canonical
+// scale Delta_(l-1) (one level), then beta added
+ckks_ct affine(const ckks_ct& x, double alpha, double beta) {
+    ckks_ctx* c = x.ctx;
+    const int l = x.level;
+    CK_CHECK(l >= 1, CKKS_ELEVEL, "not enough levels for the change of variable");
+    ckks_ct y = rescale_mul(x, llround_away(alpha * (c->delta[l - 1] * (double)c->q[l]) / x.scale));
+    y.scale = c->delta[l - 1];
+    return add_const(y, beta);
+}
+
+// p(x) on [a, b]: y = (2x - a - b) / (b - a) (no level for [-1, 1]), a power-basis p re-expressed
+// as a Chebyshev series in y on the host, then cheb_eval
+ckks_ct eval_poly(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, bool power, double a,
+                  double b) {
+    CK_CHECK(b > a, CKKS_EINVAL, "the interval needs a < b");
+    const double alpha = 2.0 / (b - a), beta = -(a + b) / (b - a);
+    std::vector<double> ch = power ? fp64::power_to_cheb(coeffs, alpha, beta) : coeffs;
+    if (a == -1.0 && b == 1.0) return cheb_eval(keys, x, ch);
+    return cheb_eval(keys, affine(x, alpha, beta), ch);
 }
 
 ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r) {

@@ -36,6 +36,9 @@ ckks_ct bsgs_multi(const ckks_keys& keys, const std::vector<const ckks_ct*>& ins
                    const std::vector<const ckks_ptset*>& pss, bool rescale_out);
 ckks_ct cheb_eval(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs);
 ckks_ct eval_mod(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, int r);
+ckks_ct affine(const ckks_ct& x, double alpha, double beta);
+ckks_ct eval_poly(const ckks_keys& keys, const ckks_ct& x, const std::vector<double>& coeffs, bool power, double a,
+                  double b);
 ckks_ct eval_relu(const ckks_keys& keys, const ckks_ct& x, const std::vector<std::vector<double>>& stages);
 void bootstrap(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& ct0, ckks_ct& re_out, ckks_ct& im_out);
 ckks_ct stoc1(const ckks_keys& keys, const ckks_boot& bt, const ckks_ct& re, const ckks_ct& im);

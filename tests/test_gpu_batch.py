@@ -174,3 +174,30 @@ def test_batched_downsample_layer_equals_one_at_a_time():
     for b in range(2):
         one = K.ckks_downsample_layer(ctx, keys, res[b], ims[b], bt_in, convs, bt_out)
         assert (K.ckks_ct_export_rns(ctx, outs[b]) == K.ckks_ct_export_rns(ctx, one)).all()
+
+
+def test_batched_bootstrap_and_activation_equal_one_at_a_time():
+    """ckks_bootstrap_batched, ckks_eval_poly_batched (on [0, 2]) and ckks_eval_relu_batched (the
+    fitted composite (15, 15, 27)) for B = 3 inputs give each input's single-ciphertext result"""
+    from oracle import relu as R
+    d = _setup("cfg2_small", 58, WL.CONV["cfg2_small"], 3, oracle_keys=False)
+    K, ctx, keys = d["K"], d["ctx"], d["keys"]
+    x0s = [K.ckks_conv2d_cins(ctx, keys, c, d["gplan"]) for c in d["gcts"]]
+    res, ims = K.ckks_bootstrap_batched(ctx, keys, d["bt"], x0s)
+    for x0, r, i in zip(x0s, res, ims):
+        r1, i1 = K.ckks_bootstrap(ctx, keys, d["bt"], x0)
+        assert (K.ckks_ct_export_rns(ctx, r) == K.ckks_ct_export_rns(ctx, r1)).all()
+        assert (K.ckks_ct_export_rns(ctx, i) == K.ckks_ct_export_rns(ctx, i1)).all()
+    P = d["o"].P
+    rng = np.random.default_rng(58)
+    ins = [K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, rng.uniform(-1, 1, P.n // 2), P.L, P.delta[P.L]), 20 + b)
+           for b in range(3)]
+    c = list(rng.normal(0, 0.3, 8))
+    polys = K.ckks_eval_poly_batched(ctx, keys, ins, c, K.CKKS_BASIS_CHEB, 0.0, 2.0)
+    stages, _ = R.composite_relu_stages()
+    relus = K.ckks_eval_relu_batched(ctx, keys, ins, stages)
+    for x, po, re_ in zip(ins, polys, relus):
+        p1 = K.ckks_eval_poly(ctx, keys, x, c, K.CKKS_BASIS_CHEB, 0.0, 2.0)
+        assert (K.ckks_ct_export_rns(ctx, po) == K.ckks_ct_export_rns(ctx, p1)).all()
+        q1 = K.ckks_eval_relu(ctx, keys, x, stages)
+        assert (K.ckks_ct_export_rns(ctx, re_) == K.ckks_ct_export_rns(ctx, q1)).all()

@@ -315,6 +315,10 @@ def test_block_small_bitexact():
     gblk1 = K.ckks_block(ctx, keys, gct, gplan, d["bt"])
     K.ckks_ctx_set_side_streams(ctx, 1)
     assert (K.ckks_ct_export_rns(ctx, gblk1) == K.ckks_ct_export_rns(ctx, gblk)).all()
+    K.ckks_ctx_set_inner_batching(ctx, 1)          # Chebyshev generations as lockstep batches
+    gblk2 = K.ckks_block(ctx, keys, gct, gplan, d["bt"])
+    K.ckks_ctx_set_inner_batching(ctx, 0)
+    assert (K.ckks_ct_export_rns(ctx, gblk2) == K.ckks_ct_export_rns(ctx, gblk)).all()
     zexp, _ = _expected_slots(d)
     got = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, gblk))
     assert np.abs(_pixels(d, got) - _pixels(d, zexp)).max() < 2.0 ** -12
@@ -739,3 +743,27 @@ def test_fc_stoc_bitexact_and_fp64():
     y = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, K.ckks_fc_stoc(ctx, keys, gct, own, n_in)), K.CKKS_COEFF)
     assert np.abs(y[:n_out] - M @ x[:n_in]).max() < 2.0 ** -12
     assert np.abs(y[n_out:]).max() < 2.0 ** -12
+
+
+def test_eval_poly_interval_and_power_basis():
+    """ckks_eval_poly on [0, 4] in the Chebyshev basis of the interval: bit-exact against the
+    oracle (the change of variable y = (2x - a - b) / (b - a) costs one level); in the power
+    basis on [-3, 1]: decoded against numpy's polynomial (the FP64 re-expression in the
+    Chebyshev basis differs in its last bits between the two sides)"""
+    K, o, ctx, keys = make_pair("cfg2_small", 45)
+    P = o.P
+    rng = np.random.default_rng(45)
+    c = list(rng.normal(0, 0.3, 8))
+    x = rng.uniform(0.0, 4.0, P.n // 2)
+    ct = o.encrypt(o.encode_pt(x, P.L, P.delta[P.L]), 2)
+    want = o.eval_poly(ct, c, 0.0, 4.0, "cheb")
+    got = K.ckks_eval_poly(ctx, keys, import_ct(K, ctx, ct), c, K.CKKS_BASIS_CHEB, 0.0, 4.0)
+    assert_ct_equal(K, ctx, got, want, "eval_poly on [0, 4]")
+    x2 = rng.uniform(-3.0, 1.0, P.n // 2)
+    ct2 = import_ct(K, ctx, o.encrypt(o.encode_pt(x2, P.L, P.delta[P.L]), 3))
+    out = K.ckks_eval_poly(ctx, keys, ct2, c, K.CKKS_BASIS_POWER, -3.0, 1.0)
+    dec = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, out)).real
+    ref = np.polynomial.polynomial.polyval(x2, c)
+    assert np.abs(dec - ref).max() < 1e-6 * max(1.0, np.abs(ref).max())
+    with pytest.raises(K.CkksError):
+        K.ckks_eval_poly(ctx, keys, ct2, c, K.CKKS_BASIS_POWER, 1.0, -3.0)      # a >= b

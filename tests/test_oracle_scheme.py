@@ -337,3 +337,24 @@ def test_fc_fused_with_stoc():
     y = o.decode_coeffs(o.decrypt(out))
     assert np.abs(y[:n_out] - M @ x[:n_in]).max() < 1e-6
     assert np.abs(y[n_out:]).max() < 1e-6
+
+
+@pytest.mark.parametrize("a,b,basis", [(0.0, 4.0, "cheb"), (-3.0, 1.0, "power"), (-1.0, 1.0, "power")])
+def test_eval_poly_intervals_and_bases(small, a, b, basis):
+    """p on [a, b] in the Chebyshev basis of the interval (sum c_k T_k((2x - a - b) / (b - a))) or
+    in the power basis (sum c_k x^k), decoded against numpy's evaluation of the same p"""
+    o = small
+    P = o.P
+    m = P.n // 2
+    x = rng.uniform(a, b, m)
+    L = P.L
+    ct = o.encrypt(o.encode_pt(x, L, P.delta[L]), 9)
+    c = list(rng.normal(0, 0.3, 6))
+    out = o.eval_poly(ct, c, a, b, basis)
+    if basis == "cheb":
+        want = np.polynomial.chebyshev.chebval((2 * x - a - b) / (b - a), c)
+    else:
+        want = np.polynomial.polynomial.polyval(x, c)
+    extra = 0 if (a, b) == (-1.0, 1.0) else 1
+    assert out.level == L - extra - math.ceil(math.log2(5)) - 1
+    assert np.abs(slots(o, out).real - want).max() < 1e-4 * max(1.0, np.abs(want).max())
