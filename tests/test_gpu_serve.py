@@ -188,3 +188,56 @@ def test_block_batch_equals_blocks_alone(env):
         for o, w in zip(outs, want):
             assert (K.ckks_ct_export_rns(ctx, o) == w).all()
     batch.close()
+
+
+@pytest.mark.slow
+def test_full_size_results_identical_alone_and_in_mix():
+    """config 2 at full size (N = 2^16, 24 limbs): one request alone, then the same input among
+    ten 1- and 2-block requests arriving together on 4 slots: bit-identical results, equal to
+    the eager C-ABI path, the one-block output within 2^-12 of FP64 conv2d"""
+    from paper_2312_04356_gb300 import ckks as K
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = gpu_ctx("cfg2", 72)
+    spec = WL.CONV["cfg2"]
+    w = E.pad_width(spec["w0"], spec["f"])
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    bt = K.ckks_boot_create(ctx, w, spec["w0"], spec["cout"])
+    W = WL.weights(72, spec["cout"], spec["cin"], spec["f"], spec["weight"])
+    conv = K.ckks_ptset_conv_fused(ctx, W, spec["cin"], spec["cout"], spec["f"], w, 1, (2.0 ** 49 * q[1]) / delta[1])
+    keys = K.ckks_keygen(ctx, sorted(set(K.ckks_ptset_rotations(conv)) | set(K.ckks_boot_rotations(bt))), True)
+    xs = {s: WL.image(s, spec["cin"], spec["w0"]) for s in range(1, 5)}
+    limbs = {s: K.ckks_ct_export_rns(ctx, K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, x, w, 1, delta[1]), s))
+             for s, x in xs.items()}
+
+    def eager(lim, n_blocks):
+        ct = K.ckks_ct_import_rns(ctx, lim, 1, delta[1])
+        for b in range(n_blocks):
+            if b:
+                ct = K.ckks_level_down(ctx, ct, 1)
+            ct = K.ckks_block(ctx, keys, ct, conv, bt)
+        return K.ckks_ct_export_rns(ctx, ct)
+
+    srv = K.ckks_server_create(ctx, keys, 4, 0)
+    A = K.ckks_server_add_model(srv, [conv], [bt])
+    B = K.ckks_server_add_model(srv, [conv, conv], [bt, bt])
+    K.ckks_server_start(srv)
+    rid = K.ckks_server_submit(srv, A, limbs[1], 1, delta[1])
+    assert K.ckks_server_wait(srv, rid, 120) == K.CKKS_REQ_DONE
+    alone, lev, sc = K.ckks_server_result(srv, rid, ctx.n)
+    assert (alone == eager(limbs[1], 1)).all()
+    got = K.ckks_decode_image(ctx, K.ckks_decrypt(ctx, keys, K.ckks_ct_import_rns(ctx, alone, lev, sc)),
+                              spec["cout"], spec["w0"], w)
+    assert np.abs(got - E.conv2d_same(xs[1], W)[: spec["cout"]]).max() < 2.0 ** -12
+    plan = [(A, 2), (B, 3), (A, 1), (A, 4), (B, 1), (A, 3), (A, 2), (B, 4), (A, 1), (A, 4)]
+    ids = [(K.ckks_server_submit(srv, m, limbs[s], 1, delta[1]), m, s) for m, s in plan]
+    refs = {}
+    for r, m, s in ids:
+        assert K.ckks_server_wait(srv, r, 300) == K.CKKS_REQ_DONE
+        out, _, _ = K.ckks_server_result(srv, r, ctx.n)
+        if (m, s) not in refs:
+            refs[(m, s)] = alone if (m, s) == (A, 1) else eager(limbs[s], 1 if m == A else 2)
+        assert (out == refs[(m, s)]).all()
+    st = K.ckks_server_stats(srv)
+    assert st["completed"] == 11 and st["failed"] == 0 and st["max_in_flight"] >= 2
+    srv.close()
