@@ -82,7 +82,7 @@ def parse_args():
     ap.add_argument("--bsgs-splits", default=None,
                     help="comma list of baby-step counts per bootstrapping level, used instead of tuning")
     ap.add_argument("--limbs", type=int, default=256, help="--kernel ntt: limbs per launch")
-    ap.add_argument("--kernel", default=None, choices=["ntt", "ks", "bsgs", "bblock"],
+    ap.add_argument("--kernel", default=None, choices=["ntt", "ks", "bsgs", "bblock", "conv"],
                     help="time one kernel family alone on a buffer larger than L2 (for profiling)")
     return ap.parse_args()
 
@@ -1385,9 +1385,45 @@ def run_kernel_ks(args):
                       "per_kernel": res}))
 
 
+def run_kernel_conv(args):
+    """base conversion alone, on the tensor cores and on the integer pipe: the ModUp of one
+    config-2 ciphertext at the top level (three digits of 8 limbs, 23 outputs each) and the
+    ModDowns of four hoisted rotations (two polynomials, 7 -> 24 limbs), timed per kernel"""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    d = WL.PARAMS[CONFIG]
+    ctx = K.ckks_ctx_create(d, 1, torch.cuda.current_stream().cuda_stream)
+    q, p, _, delta = K.ckks_ctx_info(ctx)
+    L = len(q) - 1
+    steps = [1, 2, 3, 4]
+    keys = K.ckks_keygen(ctx, steps, False)
+    ct = K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, WL.slots(1, ctx.n // 2, 0.5), L, delta[L]), 1)
+    out = {}
+    for name, tc in (("tensor", 1), ("integer", 0)):
+        K.ckks_ctx_set_tensor_conversion(ctx, tc)
+        for _ in range(args.warmup):
+            K.ckks_rotate_hoisted(ctx, keys, ct, steps)
+        K.ckks_sync(ctx)
+        K.ckks_ctx_reset_counters(ctx)
+        K.ckks_ctx_set_timing(ctx, 1)
+        for _ in range(args.steps):
+            K.ckks_rotate_hoisted(ctx, keys, ct, steps)
+        K.ckks_ctx_set_timing(ctx, 0)
+        v = K.ckks_ctx_kernel_stats(ctx)["base_convert"]
+        out[name] = {"launches": v["launches"], "us_per_launch": round(1e3 * v["ms"] / v["launches"], 2),
+                     "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)}
+    K.ckks_ctx_set_tensor_conversion(ctx, 1)
+    print(json.dumps({"kernel": "base_convert", "level": L, "N": ctx.n, "rotations_per_step": len(steps),
+                      "device_faults": K.ckks_ctx_take_device_faults(ctx), "per_kernel": out}))
+
+
 if __name__ == "__main__":
     a = parse_args()
-    if a.kernel == "ntt":
+    if a.kernel == "conv":
+        run_kernel_conv(a)
+    elif a.kernel == "ntt":
         run_kernel_ntt(a)
     elif a.kernel == "ks":
         run_kernel_ks(a)

@@ -59,6 +59,8 @@ _SIGS = {
     "ckks_ctx_set_allocator": [VP, VP, VP, VP],
     "ckks_ctx_pool_stats": [VP, I, VP],
     "ckks_ctx_set_inner_batching": [VP, I],
+    "ckks_ctx_set_tensor_conversion": [VP, I],
+    "ckks_ctx_take_device_faults": [VP, VP],
     "ckks_sync": [VP],
     "ckks_ctx_info": [VP, VP, VP, VP, VP],
     "ckks_ctx_gauss_table": [VP, VP],
@@ -378,6 +380,16 @@ def ckks_ctx_pool_stats(ctx, reset_high=False):
 
 def ckks_ctx_set_inner_batching(ctx, on):
     ctx.check(lib().ckks_ctx_set_inner_batching(ctx, int(on)))
+
+
+def ckks_ctx_set_tensor_conversion(ctx, on):
+    ctx.check(lib().ckks_ctx_set_tensor_conversion(ctx, int(on)))
+
+
+def ckks_ctx_take_device_faults(ctx):
+    a = np.zeros(1, dtype=np.uint32)
+    ctx.check(lib().ckks_ctx_take_device_faults(ctx, _ptr(a)))
+    return int(a[0])
 
 
 def ckks_ctx_set_side_streams(ctx, on):

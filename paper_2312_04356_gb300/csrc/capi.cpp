@@ -269,6 +269,22 @@ int ckks_ctx_set_inner_batching(ckks_ctx* ctx, int on) {
     });
 }
 
+int ckks_ctx_set_tensor_conversion(ckks_ctx* ctx, int on) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        ctx->conv_tc = on != 0;
+    });
+}
+
+int ckks_ctx_take_device_faults(ckks_ctx* ctx, uint32_t* count) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        REQ(count);
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        *count = kern::take_device_faults();
+    });
+}
+
 int ckks_ctx_set_side_streams(ckks_ctx* ctx, int on) {
     return guard(ctx, [&] {
         REQ(ctx);

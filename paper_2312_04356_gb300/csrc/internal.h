@@ -52,11 +52,20 @@ struct ConvTab {
     u64* d_qhat_inv = nullptr;   // [nin] and Shoup [nin]
     u64* d_qhat_mod = nullptr;   // [nout][nin] and Shoup [nout][nin]
     // exact (rounded) conversion only: 1/q_i as doubles [nin], p_m - (prod q_i mod p_m) [nout]
+    // followed by its Shoup companions [nout]
     double* d_inv_q = nullptr;
     u64* d_corr = nullptr;
     // N^{-1} qhat_i^{-1} mod q_i and its Shoup companion, [nin][2]: the factor an inverse NTT
     // ends with when its output feeds this conversion directly (prescaled inputs)
     u64* d_iscale = nullptr;
+    // tensor-core form (kern::base_convert_jobs with ctx->conv_tc): the table split into 8-bit
+    // chunks as FP16 operands in the shared-memory image of the MMA's B operand,
+    // [outputs padded to tc_S tc_groups][tc_nin2][8 chunks b of the entry][8 chunks a of the
+    // input word] = chunk b of (qhat_mod[m][i] 2^(8a) mod p_m); inputs padded to an even count
+    // tc_nin2, outputs to tc_groups groups of tc_S (even, <= 16)
+    unsigned short* d_tcb = nullptr;
+    u64* d_tcr = nullptr;        // floor(2^88 / p_m) [nout]: Shoup companion of 2^24 mod p_m
+    int tc_nin2 = 0, tc_S = 0, tc_groups = 0;
 };
 
 // A caller-provided device allocator (ckks_ctx_set_allocator); both null = the library's own
@@ -109,6 +118,9 @@ struct ckks_ctx {
     // independent products inside one operation (a generation of the Chebyshev power ladder)
     // run as one lockstep batch instead of side by side on side streams
     bool inner_batching = false;
+    // base conversions on the tensor cores (tcgen05 MMA of 8-bit chunks, exact FP32 sums)
+    // instead of 64-bit multiply-adds on the integer pipe; results are identical either way
+    bool conv_tc = true;
     DevAlloc alloc;       // caller allocator for the buffers of this context's calls
     // side streams are used only without a caller allocator: a stream-ordered caching
     // allocator (PyTorch's) reuses a freed block on the stream it was allocated on, so every
@@ -373,6 +385,9 @@ struct ConvJob {
     int nin, nout, ngroups;
     size_t in_pstride, out_pstride;
     bool prescaled;        // inputs are x_i qhat_i^{-1} already (no product on load)
+    const unsigned short* tcb;   // tensor-core form of the table (ConvTab::d_tcb, d_tcr)
+    const u64* tcr;
+    int tc_nin2, tc_S;
 };
 struct ConvJobs {
     static constexpr int MAX = 4;
@@ -382,6 +397,16 @@ struct ConvJobs {
 void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t in_pstride, size_t out_pstride,
                   bool prescaled = false);
 void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly);
+// tensor-core form of a conversion table (qmod [nout][nin], output moduli pm): the B image
+// described at ConvTab::d_tcb, with its padded input count, group size and group count, and
+// floor(2^88 / p_m) per output; empty when an output modulus is outside (2^39, 2^62)
+std::vector<unsigned short> conv_tc_image(const std::vector<u64>& qmod, const std::vector<u64>& pm, int nin, int nout,
+                                          int& nin2, int& S, int& groups, std::vector<u64>& r24p);
+// the launch can run on the tensor cores (ctx->conv_tc, N >= 128, every job has its image)
+bool conv_tc_eligible(const ckks_ctx* c, const ConvJobs& J);
+void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly);
+// bounded device waits that ran out since the last call (the count is cleared); synchronous
+unsigned take_device_faults();
 // key-switch inner product: D [ndig][next][N], key rows krow[e] of [ndig][nall][N];
 // ob/oa [next][N] = sum_d D_d(sigma_g) * key_d ; g = 1 means no automorphism
 // x0 (optional, rows [x0rows][N] with the primes of the first x0rows extended limbs): ob row e

@@ -3,50 +3,12 @@
 // Layout: a polynomial is [limb][N] uint64, limb k of an array of several
 // polynomials uses the prime with global id ids[k % lpp].  One CTA row of the
 // grid (blockIdx.y) is one limb, so the modulus is uniform inside a CTA.
-#include "internal.h"
+#include "launch.cuh"
 
 #include <atomic>
 
 #include <cooperative_groups.h>
 namespace cg = cooperative_groups;
-
-// ------------------------------------------------- dependent launches ----
-// Every kernel of this file begins with griddep_entry(): it waits until the grids it depends
-// on have completed and their writes are visible (griddepcontrol.wait; a no-op for a plain
-// launch).  With that wait ahead of every memory access, a launch with programmatic stream
-// serialization keeps stream order while the next grid is set up as the previous one
-// drains, which hides most of the launch latency of eager calls.  Inside a CUDA graph
-// capture the launches stay plain: a graph already removes that latency, and programmatic
-// edges measured slightly slower there.
-__device__ __forceinline__ void griddep_entry() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-// Opt a kernel in to more than 48 KB of dynamic shared memory, once per device (bit d of
-// `done` records device d; concurrent first calls only repeat the same setting).
-static void allow_dynamic_smem(const void* func, int bytes, std::atomic<unsigned>& done) {
-    int dev = 0;
-    CUDA_CHECK(cudaGetDevice(&dev));
-    const unsigned bit = 1u << (dev & 31);
-    if (done.load() & bit) return;
-    CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    done.fetch_or(bit);
-}
-
-template <typename... P, typename... A>
-static inline void klaunch(const ckks_ctx* c, void (*k)(P...), dim3 grid, dim3 block, size_t smem, A... args) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (c->pdl) cudaStreamIsCapturing(c->stream, &cs);
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = (c->pdl && cs == cudaStreamCaptureStatusNone) ? 1 : 0;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = c->stream;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k, args...);
-}
 
 // ------------------------------------------------------------ DevBuf -------
 thread_local const DevAlloc* tl_alloc = nullptr;
@@ -1088,9 +1050,6 @@ __global__ void k_sub_mul_scalar(const u64* a, const u64* b, const u64* s, const
 // o[g][poly][limb] = sum_b a_b[poly][limb] * p_{g,b}[limb] for NG giant steps at once: each
 // baby value is loaded once and multiplied into every giant step's sum; the products are
 // summed exactly in 128 bits (each < 2^122, at most 32 terms) and reduced once.
-__device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P) {
-    return add_mod(mul_shoup(hi, P.r64, P.r64p, P.m.q), reduce64(lo, P.m), P.m.q);
-}
 // blockIdx.y = row * nbt + t: ciphertext t of a batch (babies at T.a[b] + t astr, outputs at
 // T.o[g] + t ostr; the diagonals are shared and read by neighbouring CTAs)
 template <int V, int NG>
@@ -1958,6 +1917,10 @@ void add_conv_job(ConvJobs& J, const ConvTab& t, const u64* in, u64* out, size_t
     j.in_pstride = in_pstride;
     j.out_pstride = out_pstride;
     j.prescaled = prescaled;
+    j.tcb = t.d_tcb;
+    j.tcr = t.d_tcr;
+    j.tc_nin2 = t.tc_nin2;
+    j.tc_S = t.tc_S;
 }
 
 template <int MAXIN, bool SPLIT>
@@ -1975,6 +1938,11 @@ static void launch_base_convert(const ckks_ctx* c, const ConvJobs& J, dim3 grid,
 // jobs (sum of ceil(nout / MC) MC - nout); on ties 6, 5, 4 (4 resident CTAs per SM) before
 // 8, 7 (3 per SM).
 void base_convert_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
+    if (conv_tc_eligible(c, J0)) {
+        base_convert_tc_jobs(c, J0, npoly);
+        LAUNCH_CHECK();
+        return;
+    }
     int best_mc = CONV_OUT, best_slots = -1;
     for (int mc : {6, 5, 4, 8, 7}) {
         int slots = 0;

@@ -1,0 +1,48 @@
+// Launch helpers and device routines shared by the kernel translation units.
+#pragma once
+#include "internal.h"
+
+#include <atomic>
+
+// ------------------------------------------------- dependent launches ----
+// Every kernel of the library begins with griddep_entry(): it waits until the grids it depends
+// on have completed and their writes are visible (griddepcontrol.wait; a no-op for a plain
+// launch).  With that wait ahead of every memory access, a launch with programmatic stream
+// serialization keeps stream order while the next grid is set up as the previous one
+// drains, which hides most of the launch latency of eager calls.  Inside a CUDA graph
+// capture the launches stay plain: a graph already removes that latency, and programmatic
+// edges measured slightly slower there.
+__device__ __forceinline__ void griddep_entry() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Opt a kernel in to more than 48 KB of dynamic shared memory, once per device (bit d of
+// `done` records device d; concurrent first calls only repeat the same setting).
+static inline void allow_dynamic_smem(const void* func, int bytes, std::atomic<unsigned>& done) {
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    const unsigned bit = 1u << (dev & 31);
+    if (done.load() & bit) return;
+    CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.fetch_or(bit);
+}
+
+template <typename... P, typename... A>
+static inline void klaunch(const ckks_ctx* c, void (*k)(P...), dim3 grid, dim3 block, size_t smem, A... args) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (c->pdl) cudaStreamIsCapturing(c->stream, &cs);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = (c->pdl && cs == cudaStreamCaptureStatusNone) ? 1 : 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// (hi:lo) mod q for any 128-bit value: hi (2^64 mod q) + lo mod q, canonical
+__device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P) {
+    return add_mod(mul_shoup(hi, P.r64, P.r64p, P.m.q), reduce64(lo, P.m), P.m.q);
+}

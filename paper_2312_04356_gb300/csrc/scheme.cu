@@ -109,15 +109,23 @@ static std::unique_ptr<ConvTab> make_conv_tab(ckks_ctx* c, const std::vector<int
     t->d_out_ids = dev_upload_persistent(ids_rows);
     t->d_qhat_inv = dev_upload_persistent(qinv);
     t->d_qhat_mod = dev_upload_persistent(qmod);
+    {
+        std::vector<u64> pm(t->nout), r24p;
+        for (int m = 0; m < t->nout; ++m) pm[m] = c->mod_of[out_ids[m]];
+        t->d_tcb = dev_upload_persistent(kern::conv_tc_image(qmod, pm, t->nin, t->nout, t->tc_nin2, t->tc_S,
+                                                             t->tc_groups, r24p));
+        if (t->d_tcb) t->d_tcr = dev_upload_persistent(r24p);
+    }
     if (exact) {
         std::vector<double> invq(t->nin);
         for (int i = 0; i < t->nin; ++i) invq[i] = 1.0 / (double)c->mod_of[in_ids[i]];
-        std::vector<u64> corr(t->nout);
+        std::vector<u64> corr(2 * t->nout);
         for (int m = 0; m < t->nout; ++m) {
             const u64 pm = c->mod_of[out_ids[m]];
             u64 v = 1;
             for (int k = 0; k < t->nin; ++k) v = mulmod(v, c->mod_of[in_ids[k]] % pm, pm);
             corr[m] = v ? pm - v : 0;
+            corr[t->nout + m] = shoup(corr[m], pm);
         }
         t->d_inv_q = dev_upload_persistent(invq);
         t->d_corr = dev_upload_persistent(corr);

@@ -1,0 +1,52 @@
+"""The arithmetic behind base conversion on the tensor cores, checked on the CPU: cutting the
+input words and the pre-shifted table entries into 8-bit chunks turns sum_i x_i c_i mod p into
+eight FP32 matrix-product columns whose values are exact integers below 2^23 (so adding 2^23
+exposes them in the low mantissa bits), from which the 128-bit sum is reassembled."""
+import numpy as np
+
+rng = np.random.default_rng(23)
+
+
+def _chunks(v):
+    return [(v >> (8 * a)) & 0xFF for a in range(8)]
+
+
+def _convert_by_chunks(x, c, p):
+    """x: nin words, c: nin table entries (mod p); returns y = sum_i x_i c_i mod p through the
+    chunked FP16 x FP16 -> FP32 product"""
+    nin = len(x)
+    A = np.array([ch for xi in x for ch in _chunks(xi)], dtype=np.float16)          # K = 8 nin
+    B = np.zeros((8, 8 * nin), dtype=np.float16)
+    for i, ci in enumerate(c):
+        for a in range(8):
+            e = (ci << (8 * a)) % p
+            for b, ch in enumerate(_chunks(e)):
+                B[b, 8 * i + a] = ch
+    D = np.zeros(8, dtype=np.float32)
+    for k in range(8 * nin):                       # FP32 accumulation, one product at a time
+        D = (D + A[k].astype(np.float32) * B[:, k].astype(np.float32)).astype(np.float32)
+    assert (D < 2.0 ** 23).all()
+    w = [int(np.float32(d + np.float32(2.0 ** 23)).view(np.uint32)) for d in D]
+    assert all(v >> 23 == 0x4B000000 >> 23 for v in w)
+    s = sum((v - 0x4B000000) << (8 * b) for b, v in enumerate(w))
+    return s % p
+
+
+def test_chunked_conversion_equals_the_sum():
+    for nin, bits in ((8, 60), (7, 60), (16, 60), (3, 42), (1, 48)):
+        p = int(rng.integers(2 ** (bits - 1), 2 ** bits)) | 1
+        x = [int(v) for v in rng.integers(0, 2 ** 61, nin, dtype=np.uint64)]
+        c = [int(v) % p for v in rng.integers(0, 2 ** 62, nin, dtype=np.uint64)]
+        assert _convert_by_chunks(x, c, p) == sum(a * b for a, b in zip(x, c)) % p
+
+
+def test_largest_chunk_sums_stay_exact():
+    """every chunk 255 on both sides with 16 inputs (K = 128): each column sum is 128 * 255^2,
+    still below 2^23"""
+    assert 128 * 255 * 255 < 2 ** 23
+    p = (1 << 61) - 1
+    x = [2 ** 64 - 1] * 16
+    A = np.full(128, 255, dtype=np.float32)
+    assert float(np.sum(A * A, dtype=np.float32)) == 128 * 255 * 255
+    c = [p - 1] * 16
+    assert _convert_by_chunks(x, c, p) == sum(a * b for a, b in zip(x, c)) % p
