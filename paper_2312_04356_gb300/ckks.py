@@ -382,8 +382,8 @@ def ckks_ctx_set_inner_batching(ctx, on):
     ctx.check(lib().ckks_ctx_set_inner_batching(ctx, int(on)))
 
 
-def ckks_ctx_set_tensor_conversion(ctx, on):
-    ctx.check(lib().ckks_ctx_set_tensor_conversion(ctx, int(on)))
+def ckks_ctx_set_tensor_conversion(ctx, mode):
+    ctx.check(lib().ckks_ctx_set_tensor_conversion(ctx, int(mode)))
 
 
 def ckks_ctx_take_device_faults(ctx):

@@ -269,10 +269,12 @@ int ckks_ctx_set_inner_batching(ckks_ctx* ctx, int on) {
     });
 }
 
-int ckks_ctx_set_tensor_conversion(ckks_ctx* ctx, int on) {
+int ckks_ctx_set_tensor_conversion(ckks_ctx* ctx, int mode) {
     return guard(ctx, [&] {
         REQ(ctx);
-        ctx->conv_tc = on != 0;
+        CK_CHECK(mode >= 0 && mode <= 2, CKKS_EINVAL, "tensor conversion mode must be 0, 1 or 2");
+        ctx->conv_tc = mode != 0;
+        if (mode) ctx->conv_tc_tpr = mode;
     });
 }
 

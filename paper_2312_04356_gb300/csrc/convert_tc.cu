@@ -172,8 +172,13 @@ __device__ __forceinline__ u64 chunk_reduce(const unsigned* w, u64 p, u64 r24p) 
     return y;
 }
 
-template <int MAXIN>
-__global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM)
+// TPR threads per coefficient row (CTA = 128 TPR threads): thread (r, h) writes the chunks of
+// the inputs i = h (mod TPR) of row r and finishes the output pairs p = h (mod TPR) of row r;
+// warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31, the rows of its threads.  With
+// TPR > 1 an exact table's rounding term needs all of a row's xh_i: they go through shared
+// memory ([nin][128] words after the B image) and every thread of the row sums them in order.
+template <int MAXIN, int TPR>
+__global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
     k_base_convert_tc(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn, int tiles) {
     griddep_entry();
     extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -195,11 +200,13 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM)
     const int mcount = min(S, job.nout - m0);
     const bool exact = job.inv_q != nullptr;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (TC_M - 1), h = tid / TC_M;
     unsigned ncols = 32;
     while (ncols < 8u * S) ncols <<= 1;
     const unsigned sbo = (unsigned)nin2 * 128u;   // bytes per 8-row group of A and of B
     unsigned char* sA = tc_smem;
     unsigned char* sB = tc_smem + TC_M * nin2 * 16;
+    u64* xs = reinterpret_cast<u64*>(sB + S * sbo);
     const unsigned bytesB = (unsigned)S * sbo;
 
     if (tid < nin) {
@@ -242,28 +249,32 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM)
     const int t0 = blockIdx.x * tiles, t1 = min(ntiles, t0 + tiles);
     const unsigned idesc = idesc_f16_f32(TC_M, 8 * S);
     const unsigned aaddr = smem_u32(sA), baddr = smem_u32(sB);
-    const unsigned tlane = taddr + ((unsigned)(warp * 32) << 16);
-    unsigned char* arow = sA + (tid >> 3) * sbo + (tid & 7) * 16;
+    const unsigned tlane = taddr + ((unsigned)((warp & 3) * 32) << 16);
+    unsigned char* arow = sA + (row >> 3) * sbo + (row & 7) * 16;
     bool ok = true, b_ready = false;
     unsigned phase = 0;
 
-    u64 x[MAXIN];
+    constexpr int NX = MAXIN / TPR;   // this thread's inputs: i = k TPR + h
+    u64 x[NX];
 #pragma unroll
-    for (int i = 0; i < MAXIN; ++i)
-        if (i < nin && t0 < t1) x[i] = in[(size_t)i * n + (size_t)t0 * TC_M + tid];
+    for (int k = 0; k < NX; ++k)
+        if (k * TPR + h < nin && t0 < t1) x[k] = in[(size_t)(k * TPR + h) * n + (size_t)t0 * TC_M + row];
     for (int t = t0; t < t1; ++t) {
-        const size_t j = (size_t)t * TC_M + tid;
+        const size_t j = (size_t)t * TC_M + row;
         double f = 0.0;
 #pragma unroll
-        for (int i = 0; i < MAXIN; ++i) {
+        for (int k = 0; k < NX; ++k) {
+            const int i = k * TPR + h;
             if (i < nin) {
-                const u64 xh = job.prescaled ? x[i] : mul_shoup(x[i], s_qinv[i], s_qinvp[i], s_qi[i]);
-                if (exact) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xh), s_invq[i]));
+                const u64 xh = job.prescaled ? x[k] : mul_shoup(x[k], s_qinv[i], s_qinvp[i], s_qi[i]);
+                if (exact) {
+                    if (TPR == 1) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xh), s_invq[i]));
+                    else xs[i * TC_M + row] = xh;
+                }
                 *reinterpret_cast<uint4*>(arow + i * 128) = chunks_f16(xh);
             }
         }
-        if (nin < nin2) *reinterpret_cast<uint4*>(arow + nin * 128) = make_uint4(0u, 0u, 0u, 0u);
-        const u64 v = exact ? (u64)__double2ll_rn(f) : 0;
+        if (nin < nin2 && nin % TPR == h) *reinterpret_cast<uint4*>(arow + nin * 128) = make_uint4(0u, 0u, 0u, 0u);
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -280,26 +291,30 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM)
             }
         }
         __syncwarp();
+        if (TPR > 1 && exact) {
+            for (int i = 0; i < nin; ++i) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xs[i * TC_M + row]), s_invq[i]));
+        }
+        const u64 v = exact ? (u64)__double2ll_rn(f) : 0;
         // the next tile's inputs are in flight while the MMAs and this tile's epilogue run
         if (t + 1 < t1) {
 #pragma unroll
-            for (int i = 0; i < MAXIN; ++i)
-                if (i < nin) x[i] = in[(size_t)i * n + j + TC_M];
+            for (int k = 0; k < NX; ++k)
+                if (k * TPR + h < nin) x[k] = in[(size_t)(k * TPR + h) * n + j + TC_M];
         }
         if (!mbar_wait(barM, phase)) ok = false;
         phase ^= 1u;
         tc_fence_after();
         __syncwarp();
-        for (int p = 0; p < S / 2; ++p) {
+        for (int p = h; p < S / 2; p += TPR) {
             unsigned r[16];
             tmem_ld16(tlane + 16u * p, r);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = 2 * p + h;
+            for (int e = 0; e < 2; ++e) {
+                const int m = 2 * p + e;
                 if (m >= mcount) continue;
                 unsigned w[8];
 #pragma unroll
-                for (int b = 0; b < 8; ++b) w[b] = __float_as_uint(__fadd_rn(__uint_as_float(r[8 * h + b]), 8388608.0f));
+                for (int b = 0; b < 8; ++b) w[b] = __float_as_uint(__fadd_rn(__uint_as_float(r[8 * e + b]), 8388608.0f));
                 const u64 pm = s_p[m];
                 u64 y = chunk_reduce(w, pm, s_r24p[m]);
                 if (exact) y = add_mod(y, mul_shoup(v, s_corr[m], s_corrp[m], pm), pm);
@@ -365,6 +380,15 @@ bool conv_tc_eligible(const ckks_ctx* c, const ConvJobs& J) {
     return J.n > 0;
 }
 
+template <int MAXIN, int TPR>
+static void launch_tc(const ckks_ctx* c, const ConvJobs& J, dim3 grid, unsigned smem, int per) {
+    // the attribute is set once per device for the largest operand tiles (K = 128, S = 16)
+    constexpr int SMEM_MAX = TC_M * TC_MAXIN * 16 + TC_MAXS * TC_MAXIN * 128 + TC_M * TC_MAXIN * 8;
+    static std::atomic<unsigned> done{0};
+    allow_dynamic_smem((const void*)k_base_convert_tc<MAXIN, TPR>, SMEM_MAX, done);
+    klaunch(c, k_base_convert_tc<MAXIN, TPR>, grid, TC_M * TPR, smem, J, c->d_primes, c->logn, per);
+}
+
 void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
     ConvJobs J = J0;
     int groups = 0, maxin = 0;
@@ -375,13 +399,10 @@ void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
         jb.ngroups = (jb.nout + jb.tc_S - 1) / jb.tc_S;
         groups += jb.ngroups;
         maxin = std::max(maxin, jb.nin);
-        smem = std::max(smem, (unsigned)(TC_M * jb.tc_nin2 * 16 + jb.tc_S * jb.tc_nin2 * 128));
+        smem = std::max(smem, (unsigned)(TC_M * jb.tc_nin2 * 16 + jb.tc_S * jb.tc_nin2 * 128 + TC_M * jb.tc_nin2 * 8));
         bytes += (double)npoly * (jb.nin + jb.nout) * c->n * 8.0;
     }
     if (groups == 0) return;
-    // the attribute is set once per device for the largest operand tiles (K = 128, S = 16)
-    constexpr int SMEM_MAX = TC_M * TC_MAXIN * 8 * 2 + TC_MAXS * TC_MAXIN * 128;
-    static std::atomic<unsigned> done8{0}, done16{0};
     int dev = 0, nsm = 0;
     CUDA_CHECK(cudaGetDevice(&dev));
     CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -393,12 +414,13 @@ void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
     per = std::min(per, ntiles);
     const dim3 grid((ntiles + per - 1) / per, npoly, groups);
     KTimer kt_(c, "base_convert", bytes);
+    const bool two = c->conv_tc_tpr == 2;
     if (maxin <= 8) {
-        allow_dynamic_smem((const void*)k_base_convert_tc<8>, SMEM_MAX, done8);
-        klaunch(c, k_base_convert_tc<8>, grid, TC_M, smem, J, c->d_primes, c->logn, per);
+        if (two) launch_tc<8, 2>(c, J, grid, smem, per);
+        else launch_tc<8, 1>(c, J, grid, smem, per);
     } else {
-        allow_dynamic_smem((const void*)k_base_convert_tc<16>, SMEM_MAX, done16);
-        klaunch(c, k_base_convert_tc<16>, grid, TC_M, smem, J, c->d_primes, c->logn, per);
+        if (two) launch_tc<16, 2>(c, J, grid, smem, per);
+        else launch_tc<16, 1>(c, J, grid, smem, per);
     }
 }
 
