@@ -1401,7 +1401,7 @@ def run_kernel_conv(args):
     keys = K.ckks_keygen(ctx, steps, False)
     ct = K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, WL.slots(1, ctx.n // 2, 0.5), L, delta[L]), 1)
     out = {}
-    for name, tc in (("tensor_2_threads_per_row", 2), ("tensor_1_thread_per_row", 1), ("integer", 0)):
+    for name, tc in (("tensor_1_thread_per_row", 1), ("tensor_2_threads_per_row", 2), ("integer", 0)):
         K.ckks_ctx_set_tensor_conversion(ctx, tc)
         for _ in range(args.warmup):
             K.ckks_rotate_hoisted(ctx, keys, ct, steps)
@@ -1414,7 +1414,7 @@ def run_kernel_conv(args):
         v = K.ckks_ctx_kernel_stats(ctx)["base_convert"]
         out[name] = {"launches": v["launches"], "us_per_launch": round(1e3 * v["ms"] / v["launches"], 2),
                      "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)}
-    K.ckks_ctx_set_tensor_conversion(ctx, 2)
+    K.ckks_ctx_set_tensor_conversion(ctx, 1)
     print(json.dumps({"kernel": "base_convert", "level": L, "N": ctx.n, "rotations_per_step": len(steps),
                       "device_faults": K.ckks_ctx_take_device_faults(ctx), "per_kernel": out}))
 

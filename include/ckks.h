@@ -174,11 +174,11 @@ int ckks_ctx_set_side_streams(ckks_ctx* ctx, int on);
  * (one launch per kernel for all of them, the relinearisation key read once) instead of side
  * by side on the side streams; results are identical either way.  Off by default. */
 int ckks_ctx_set_inner_batching(ckks_ctx* ctx, int on);
-/* mode 2 (the default) or 1: base conversions (ModUp, ModDown, ModDown fused with the
+/* mode 1 (the default) or 2: base conversions (ModUp, ModDown, ModDown fused with the
  * rescale; Sec. 2's hybrid key switching) run on the tensor cores: the 64-bit words and the
  * table are cut into 8-bit chunks, the chunk products are summed by FP16 x FP16 -> FP32 MMAs
  * (every sum an integer below 2^23, so exact) and reassembled and reduced mod p on the
- * integer pipe, by two (mode 2) or one (mode 1) threads per coefficient.  mode 0: 64-bit
+ * integer pipe, by one (mode 1) or two (mode 2) threads per coefficient.  mode 0: 64-bit
  * multiply-adds on the integer pipe.  Results are identical in every mode.  Errors:
  * CKKS_EINVAL (mode outside 0..2). */
 int ckks_ctx_set_tensor_conversion(ckks_ctx* ctx, int mode);

@@ -11,9 +11,10 @@
 //     y_m = sum_b 2^(8b) D_{m,b}  (mod p_m),    D_{m,b} = sum_{i,a} x_{i,a} e_{m,i,a,b}.
 // D is an ordinary matrix product with K = 8 nin and 8 columns per output.  Every operand is
 // an integer in [0, 255] (exact in FP16) and every D is a sum of at most 8 * 16 products
-// below 2^16, so it stays below 2^23: its FP32 accumulation is exact.  Adding 2^23 to D puts
-// its integer value in the low 23 bits of the FP32 word, from which the 128-bit value of
-// sum_b 2^(8b) D_{m,b} is assembled and reduced mod p_m (with, for an exact table, the
+// below 2^16, so it stays below 2^23.  The accumulators start at 2^23 instead of 0: every
+// partial sum is then an integer in [2^23, 2^24), exact in FP32 with a fixed exponent, and
+// the final word's low 23 bits are D itself, from which the value of sum_b 2^(8b) D_{m,b} is
+// assembled and reduced mod p_m (with, for an exact table, the
 // rounded correction v (Q mod p_m) of the integer-pipe kernel, Halevi-Polyakov-Shoup 2019).
 // The result is the canonical residue, so it equals the integer-pipe kernel's word for word.
 //
@@ -139,6 +140,16 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, unsigned (&r)[16]) {
                  : "memory");
 }
 
+// 16 consecutive 32-bit columns of this thread's TMEM lane set to v
+__device__ __forceinline__ void tmem_st16(unsigned taddr, unsigned v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1};" ::"r"(taddr),
+        "r"(v)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // the 8 bytes of x as FP16 values, byte a in half a: each half is first 0x64bb (the FP16
 // number 1024 + bb), then 1024 is subtracted exactly
 __device__ __forceinline__ uint4 chunks_f16(u64 x) {
@@ -157,8 +168,8 @@ __device__ __forceinline__ uint4 chunks_f16(u64 x) {
     return h;
 }
 
-// y = sum_b 2^(8b) D_b mod p from the FP32 words w_b of D_b + 2^23 (bit patterns
-// 0x4B000000 + D_b, D_b < 2^23): lo = D_0 + 2^8 D_1 + 2^16 D_2 < 2^39 < p and
+// y = sum_b 2^(8b) D_b mod p from the FP32 words w_b = 2^23 + D_b (bit patterns
+// 0x4B000000 + D_b, D_b < 2^23; the accumulators start at 2^23): lo = D_0 + 2^8 D_1 + 2^16 D_2 < 2^39 < p and
 // hi = D_3 + ... + 2^32 D_7 < 2^56, y = lo + hi 2^24 mod p with one lazy Shoup product by
 // 2^24 (< p; companion r24p = floor(2^88 / p)), result canonical
 __device__ __forceinline__ u64 chunk_reduce(const unsigned* w, u64 p, u64 r24p) {
@@ -177,7 +188,10 @@ __device__ __forceinline__ u64 chunk_reduce(const unsigned* w, u64 p, u64 r24p) 
 // warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31, the rows of its threads.  With
 // TPR > 1 an exact table's rounding term needs all of a row's xh_i: they go through shared
 // memory ([nin][128] words after the B image) and every thread of the row sums them in order.
-template <int MAXIN, int TPR>
+// EXACT / PRE: every job of the launch has an exact table / prescaled inputs.  The
+// accumulators of a tile are set to 2^23 before its first MMA, so that each holds 2^23 + D
+// (exact: below 2^24) and its bit pattern exposes D directly.
+template <int MAXIN, int TPR, bool EXACT, bool PRE>
 __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
     k_base_convert_tc(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn, int tiles) {
     griddep_entry();
@@ -198,7 +212,7 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
     const int nin = job.nin, nin2 = job.tc_nin2, S = job.tc_S;
     const int m0 = z * S;
     const int mcount = min(S, job.nout - m0);
-    const bool exact = job.inv_q != nullptr;
+    constexpr bool exact = EXACT;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int row = tid & (TC_M - 1), h = tid / TC_M;
     unsigned ncols = 32;
@@ -266,7 +280,7 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
         for (int k = 0; k < NX; ++k) {
             const int i = k * TPR + h;
             if (i < nin) {
-                const u64 xh = job.prescaled ? x[k] : mul_shoup(x[k], s_qinv[i], s_qinvp[i], s_qi[i]);
+                const u64 xh = PRE ? x[k] : mul_shoup(x[k], s_qinv[i], s_qinvp[i], s_qi[i]);
                 if (exact) {
                     if (TPR == 1) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xh), s_invq[i]));
                     else xs[i * TC_M + row] = xh;
@@ -275,6 +289,14 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
             }
         }
         if (nin < nin2 && nin % TPR == h) *reinterpret_cast<uint4*>(arow + nin * 128) = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int k = 0; k < 8 / TPR; ++k) {
+            const int p = h + k * TPR;
+            if (p >= S / 2) break;
+            tmem_st16(tlane + 16u * p, 0x4B000000u);
+        }
+        tmem_wait_st();
+        tc_fence_before();
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -286,7 +308,7 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
             if (ok) {
                 for (int s = 0; s < nin2 / 2; ++s)
                     mma_f16(taddr, smem_desc(aaddr + 256u * s, 128u, sbo), smem_desc(baddr + 256u * s, 128u, sbo),
-                            idesc, s);
+                            idesc, 1);
                 mma_commit(barM);
             }
         }
@@ -305,18 +327,18 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
         phase ^= 1u;
         tc_fence_after();
         __syncwarp();
-        for (int p = h; p < S / 2; p += TPR) {
+#pragma unroll
+        for (int k = 0; k < 8 / TPR; ++k) {
+            const int p = h + k * TPR;
+            if (p >= S / 2) break;
             unsigned r[16];
             tmem_ld16(tlane + 16u * p, r);
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int m = 2 * p + e;
                 if (m >= mcount) continue;
-                unsigned w[8];
-#pragma unroll
-                for (int b = 0; b < 8; ++b) w[b] = __float_as_uint(__fadd_rn(__uint_as_float(r[8 * e + b]), 8388608.0f));
                 const u64 pm = s_p[m];
-                u64 y = chunk_reduce(w, pm, s_r24p[m]);
+                u64 y = chunk_reduce(r + 8 * e, pm, s_r24p[m]);
                 if (exact) y = add_mod(y, mul_shoup(v, s_corr[m], s_corrp[m], pm), pm);
                 out[(size_t)s_row[m] * n + j] = y;
             }
@@ -380,16 +402,41 @@ bool conv_tc_eligible(const ckks_ctx* c, const ConvJobs& J) {
     return J.n > 0;
 }
 
-template <int MAXIN, int TPR>
+template <int MAXIN, int TPR, bool EXACT, bool PRE>
 static void launch_tc(const ckks_ctx* c, const ConvJobs& J, dim3 grid, unsigned smem, int per) {
     // the attribute is set once per device for the largest operand tiles (K = 128, S = 16)
     constexpr int SMEM_MAX = TC_M * TC_MAXIN * 16 + TC_MAXS * TC_MAXIN * 128 + TC_M * TC_MAXIN * 8;
     static std::atomic<unsigned> done{0};
-    allow_dynamic_smem((const void*)k_base_convert_tc<MAXIN, TPR>, SMEM_MAX, done);
-    klaunch(c, k_base_convert_tc<MAXIN, TPR>, grid, TC_M * TPR, smem, J, c->d_primes, c->logn, per);
+    allow_dynamic_smem((const void*)k_base_convert_tc<MAXIN, TPR, EXACT, PRE>, SMEM_MAX, done);
+    klaunch(c, k_base_convert_tc<MAXIN, TPR, EXACT, PRE>, grid, TC_M * TPR, smem, J, c->d_primes, c->logn, per);
+}
+
+template <int MAXIN, int TPR>
+static void launch_tc_flags(const ckks_ctx* c, const ConvJobs& J, dim3 grid, unsigned smem, int per, bool exact,
+                            bool pre) {
+    if (exact) {
+        if (pre) launch_tc<MAXIN, TPR, true, true>(c, J, grid, smem, per);
+        else launch_tc<MAXIN, TPR, true, false>(c, J, grid, smem, per);
+    } else {
+        if (pre) launch_tc<MAXIN, TPR, false, true>(c, J, grid, smem, per);
+        else launch_tc<MAXIN, TPR, false, false>(c, J, grid, smem, per);
+    }
 }
 
 void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
+    // one launch per run of jobs that agree on the table kind and the input scaling
+    for (int i = 1; i < J0.n; ++i) {
+        if ((J0.job[i].inv_q != nullptr) != (J0.job[0].inv_q != nullptr) || J0.job[i].prescaled != J0.job[0].prescaled) {
+            for (int k = 0; k < J0.n; ++k) {
+                ConvJobs one;
+                one.n = 1;
+                one.job[0] = J0.job[k];
+                base_convert_tc_jobs(c, one, npoly);
+            }
+            return;
+        }
+    }
+    const bool exact = J0.n > 0 && J0.job[0].inv_q != nullptr, pre = J0.n > 0 && J0.job[0].prescaled;
     ConvJobs J = J0;
     int groups = 0, maxin = 0;
     unsigned smem = TC_SMEM_FLOOR;
@@ -416,11 +463,11 @@ void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
     KTimer kt_(c, "base_convert", bytes);
     const bool two = c->conv_tc_tpr == 2;
     if (maxin <= 8) {
-        if (two) launch_tc<8, 2>(c, J, grid, smem, per);
-        else launch_tc<8, 1>(c, J, grid, smem, per);
+        if (two) launch_tc_flags<8, 2>(c, J, grid, smem, per, exact, pre);
+        else launch_tc_flags<8, 1>(c, J, grid, smem, per, exact, pre);
     } else {
-        if (two) launch_tc<16, 2>(c, J, grid, smem, per);
-        else launch_tc<16, 1>(c, J, grid, smem, per);
+        if (two) launch_tc_flags<16, 2>(c, J, grid, smem, per, exact, pre);
+        else launch_tc_flags<16, 1>(c, J, grid, smem, per, exact, pre);
     }
 }
 

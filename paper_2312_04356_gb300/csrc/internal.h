@@ -121,7 +121,7 @@ struct ckks_ctx {
     // base conversions on the tensor cores (tcgen05 MMA of 8-bit chunks, exact FP32 sums)
     // instead of 64-bit multiply-adds on the integer pipe; results are identical either way
     bool conv_tc = true;
-    int conv_tc_tpr = 2;    // threads per coefficient row of the tensor-core conversion (1 or 2)
+    int conv_tc_tpr = 1;    // threads per coefficient row of the tensor-core conversion (1 or 2)
     DevAlloc alloc;       // caller allocator for the buffers of this context's calls
     // side streams are used only without a caller allocator: a stream-ordered caching
     // allocator (PyTorch's) reuses a freed block on the stream it was allocated on, so every

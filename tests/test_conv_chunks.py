@@ -1,7 +1,9 @@
 """The arithmetic behind base conversion on the tensor cores, checked on the CPU: cutting the
 input words and the pre-shifted table entries into 8-bit chunks turns sum_i x_i c_i mod p into
-eight FP32 matrix-product columns whose values are exact integers below 2^23 (so adding 2^23
-exposes them in the low mantissa bits), from which the 128-bit sum is reassembled."""
+eight FP32 matrix-product columns whose values are exact integers below 2^23; accumulating them
+from a start value of 2^23 keeps every partial sum an exact integer in [2^23, 2^24), so the final
+word's low 23 bits are the column sum, from which the sum is reassembled mod p as
+lo + 2^24 hi (lo = D_0 + 2^8 D_1 + 2^16 D_2 < 2^39)."""
 import numpy as np
 
 rng = np.random.default_rng(23)
@@ -22,14 +24,17 @@ def _convert_by_chunks(x, c, p):
             e = (ci << (8 * a)) % p
             for b, ch in enumerate(_chunks(e)):
                 B[b, 8 * i + a] = ch
-    D = np.zeros(8, dtype=np.float32)
-    for k in range(8 * nin):                       # FP32 accumulation, one product at a time
+    D = np.full(8, 2.0 ** 23, dtype=np.float32)   # FP32 accumulation from 2^23, one product at a time
+    for k in range(8 * nin):
         D = (D + A[k].astype(np.float32) * B[:, k].astype(np.float32)).astype(np.float32)
-    assert (D < 2.0 ** 23).all()
-    w = [int(np.float32(d + np.float32(2.0 ** 23)).view(np.uint32)) for d in D]
+    assert (D < 2.0 ** 24).all()
+    w = [int(v) for v in D.view(np.uint32)]
     assert all(v >> 23 == 0x4B000000 >> 23 for v in w)
-    s = sum((v - 0x4B000000) << (8 * b) for b, v in enumerate(w))
-    return s % p
+    d = [v - 0x4B000000 for v in w]
+    lo = d[0] + (d[1] << 8) + (d[2] << 16)
+    hi = d[3] + (d[4] << 8) + (d[5] << 16) + (d[6] << 24) + (d[7] << 32)
+    assert lo < 2 ** 39 and hi < 2 ** 56
+    return (lo + (hi << 24)) % p
 
 
 def test_chunked_conversion_equals_the_sum():
