@@ -40,6 +40,7 @@ struct DevPrime {
     const ulonglong2* itw;   // (psi^-rev(k), Shoup companion)          (inverse, Gentleman-Sande)
     u64 n_inv, n_inv_p;
     u64 r64, r64p;           // 2^64 mod q and its Shoup companion (128-bit lazy sums)
+    u64 inv64;               // floor(2^64 / q): Shoup companion of 1, reduces any 64-bit word
 };
 
 // Base-conversion table: inputs (prime ids in_ids, count nin) -> outputs (out_ids, nout).

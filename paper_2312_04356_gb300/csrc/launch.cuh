@@ -42,7 +42,11 @@ static inline void klaunch(const ckks_ctx* c, void (*k)(P...), dim3 grid, dim3 b
     cudaLaunchKernelEx(&cfg, k, args...);
 }
 
-// (hi:lo) mod q for any 128-bit value: hi (2^64 mod q) + lo mod q, canonical
+// (hi:lo) mod q for any 128-bit value: hi (2^64 mod q) + lo mod q, canonical; lo is reduced
+// as the Shoup product lo * 1 (companion floor(2^64 / q)), one high product instead of Barrett's
 __device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P) {
-    return add_mod(mul_shoup(hi, P.r64, P.r64p, P.m.q), reduce64(lo, P.m), P.m.q);
+    const u64 q = P.m.q;
+    u64 l = lo - __umul64hi(lo, P.inv64) * q;      // [0, 2q)
+    if (l >= q) l -= q;
+    return add_mod(mul_shoup(hi, P.r64, P.r64p, q), l, q);
 }

@@ -280,6 +280,7 @@ ckks_ctx* ctx_create(const ckks_params* P, uint64_t seed, cudaStream_t stream) {
         dp.n_inv_p = shoup(dp.n_inv, qq);
         dp.r64 = (u64)(((unsigned __int128)1 << 64) % qq);
         dp.r64p = shoup(dp.r64, qq);
+        dp.inv64 = (u64)((((unsigned __int128)1) << 64) / qq);
     }
     CUDA_CHECK(cudaMemcpy(c->d_tables, tables.data(), tables.size() * sizeof(u64), cudaMemcpyHostToDevice));
     c->d_primes = dev_upload_persistent(primes);
