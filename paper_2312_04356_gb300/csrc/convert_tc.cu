@@ -16,7 +16,10 @@
 // the final word's low 23 bits are D itself, from which the value of sum_b 2^(8b) D_{m,b} is
 // assembled and reduced mod p_m (with, for an exact table, the
 // rounded correction v (Q mod p_m) of the integer-pipe kernel, Halevi-Polyakov-Shoup 2019).
-// The result is the canonical residue, so it equals the integer-pipe kernel's word for word.
+// Every output goes to a forward NTT.  For N = 2^16 the words are left congruent but below 4p
+// (the radix-16 transform's lazy butterflies take such inputs and end canonical); otherwise they
+// are the canonical residues.  Either way the transformed words equal the integer-pipe
+// kernel's.
 //
 // A CTA takes 128 coefficients per tile (MMA M = 128, one TMEM lane per coefficient) for one
 // output group of S <= 16 outputs (N = 8 S <= 128 TMEM columns, four CTAs per SM fill the
@@ -171,16 +174,13 @@ __device__ __forceinline__ uint4 chunks_f16(u64 x) {
 // y = sum_b 2^(8b) D_b mod p from the FP32 words w_b = 2^23 + D_b (bit patterns
 // 0x4B000000 + D_b, D_b < 2^23; the accumulators start at 2^23): lo = D_0 + 2^8 D_1 + 2^16 D_2 < 2^39 < p and
 // hi = D_3 + ... + 2^32 D_7 < 2^56, y = lo + hi 2^24 mod p with one lazy Shoup product by
-// 2^24 (< p; companion r24p = floor(2^88 / p)), result canonical
-__device__ __forceinline__ u64 chunk_reduce(const unsigned* w, u64 p, u64 r24p) {
+// 2^24 (< p; companion r24p = floor(2^88 / p)); the result lies in [0, 3p), not reduced
+__device__ __forceinline__ u64 chunk_reduce_lazy(const unsigned* w, u64 p, u64 r24p) {
     constexpr u64 OFF_LO = 0x4B000000ull * 0x010101ull, OFF_HI = 0x4B000000ull * 0x0101010101ull;
     const u64 lo = (u64)w[0] + (u64)w[1] * 256u + (u64)w[2] * 65536u - OFF_LO;
     const u64 hi = (u64)w[3] + (u64)w[4] * 256u + (u64)w[5] * 65536u + (u64)w[6] * 16777216u +
                    ((u64)w[7] << 32) - OFF_HI;
-    u64 y = lo + ((hi << 24) - __umul64hi(hi, r24p) * p);   // lo + [0, 2p) < 3p
-    if (y >= 2 * p) y -= 2 * p;
-    if (y >= p) y -= p;
-    return y;
+    return lo + ((hi << 24) - __umul64hi(hi, r24p) * p);   // lo + [0, 2p) < 3p
 }
 
 // TPR threads per coefficient row (CTA = 128 TPR threads): thread (r, h) writes the chunks of
@@ -193,7 +193,7 @@ __device__ __forceinline__ u64 chunk_reduce(const unsigned* w, u64 p, u64 r24p) 
 // (exact: below 2^24) and its bit pattern exposes D directly.
 template <int MAXIN, int TPR, bool EXACT, bool PRE>
 __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
-    k_base_convert_tc(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn, int tiles) {
+    k_base_convert_tc(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn, int tiles, int lazy) {
     griddep_entry();
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) u64 s_bar[2];   // [0]: B image landed, [1]: MMAs of the tile done
@@ -338,8 +338,15 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
                 const int m = 2 * p + e;
                 if (m >= mcount) continue;
                 const u64 pm = s_p[m];
-                u64 y = chunk_reduce(r + 8 * e, pm, s_r24p[m]);
-                if (exact) y = add_mod(y, mul_shoup(v, s_corr[m], s_corrp[m], pm), pm);
+                u64 y = chunk_reduce_lazy(r + 8 * e, pm, s_r24p[m]);
+                if (lazy) {
+                    // the forward NTT of N = 2^16 takes inputs below 4p
+                    if (exact) y += mul_shoup(v, s_corr[m], s_corrp[m], pm);
+                } else {
+                    if (y >= 2 * pm) y -= 2 * pm;
+                    if (y >= pm) y -= pm;
+                    if (exact) y = add_mod(y, mul_shoup(v, s_corr[m], s_corrp[m], pm), pm);
+                }
                 out[(size_t)s_row[m] * n + j] = y;
             }
         }
@@ -408,7 +415,10 @@ static void launch_tc(const ckks_ctx* c, const ConvJobs& J, dim3 grid, unsigned 
     constexpr int SMEM_MAX = TC_M * TC_MAXIN * 16 + TC_MAXS * TC_MAXIN * 128 + TC_M * TC_MAXIN * 8;
     static std::atomic<unsigned> done{0};
     allow_dynamic_smem((const void*)k_base_convert_tc<MAXIN, TPR, EXACT, PRE>, SMEM_MAX, done);
-    klaunch(c, k_base_convert_tc<MAXIN, TPR, EXACT, PRE>, grid, TC_M * TPR, smem, J, c->d_primes, c->logn, per);
+    // every conversion output goes to a forward NTT; for N = 2^16 its lazy butterflies take
+    // inputs below 4p, so the words are left in [0, 4p) there (canonical for the generic NTT)
+    klaunch(c, k_base_convert_tc<MAXIN, TPR, EXACT, PRE>, grid, TC_M * TPR, smem, J, c->d_primes, c->logn, per,
+            c->logn == 16 ? 1 : 0);
 }
 
 template <int MAXIN, int TPR>
