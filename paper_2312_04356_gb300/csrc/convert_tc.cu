@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
     __shared__ __align__(8) u64 s_bar[2];   // [0]: B image landed, [1]: MMAs of the tile done
     __shared__ unsigned s_taddr;
     __shared__ u64 s_qi[TC_MAXIN], s_qinv[TC_MAXIN], s_qinvp[TC_MAXIN];
-    __shared__ double s_invq[TC_MAXIN];
+    __shared__ u64 s_invm[TC_MAXIN];
+    __shared__ int s_invs[TC_MAXIN];
     __shared__ u64 s_p[TC_MAXS], s_r24p[TC_MAXS], s_corr[TC_MAXS], s_corrp[TC_MAXS];
     __shared__ int s_row[TC_MAXS];
 
@@ -227,7 +228,8 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
         s_qi[tid] = P[job.in_ids[tid]].m.q;
         s_qinv[tid] = job.qinv[tid];
         s_qinvp[tid] = job.qinv[nin + tid];
-        s_invq[tid] = exact ? job.inv_q[tid] : 0.0;
+        s_invm[tid] = exact ? job.inv_q[tid] : 0;
+        s_invs[tid] = exact ? (int)job.inv_q[nin + tid] : 64;
     }
     if (tid < mcount) {
         s_p[tid] = P[job.out_ids[m0 + tid]].m.q;
@@ -275,14 +277,14 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
         if (k * TPR + h < nin && t0 < t1) x[k] = in[(size_t)(k * TPR + h) * n + (size_t)t0 * TC_M + row];
     for (int t = t0; t < t1; ++t) {
         const size_t j = (size_t)t * TC_M + row;
-        double f = 0.0;
+        u64 f = 0;
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
             const int i = k * TPR + h;
             if (i < nin) {
                 const u64 xh = PRE ? x[k] : mul_shoup(x[k], s_qinv[i], s_qinvp[i], s_qi[i]);
                 if (exact) {
-                    if (TPR == 1) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xh), s_invq[i]));
+                    if (TPR == 1) f += conv_round_term(xh, s_invm[i], s_invs[i]);
                     else xs[i * TC_M + row] = xh;
                 }
                 *reinterpret_cast<uint4*>(arow + i * 128) = chunks_f16(xh);
@@ -314,9 +316,9 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
         }
         __syncwarp();
         if (TPR > 1 && exact) {
-            for (int i = 0; i < nin; ++i) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xs[i * TC_M + row]), s_invq[i]));
+            for (int i = 0; i < nin; ++i) f += conv_round_term(xs[i * TC_M + row], s_invm[i], s_invs[i]);
         }
-        const u64 v = exact ? (u64)__double2ll_rn(f) : 0;
+        const u64 v = exact ? conv_round_finish(f) : 0;
         // the next tile's inputs are in flight while the MMAs and this tile's epilogue run
         if (t + 1 < t1) {
 #pragma unroll

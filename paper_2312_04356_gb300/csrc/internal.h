@@ -52,9 +52,10 @@ struct ConvTab {
     int* d_out_ids = nullptr;
     u64* d_qhat_inv = nullptr;   // [nin] and Shoup [nin]
     u64* d_qhat_mod = nullptr;   // [nout][nin] and Shoup [nout][nin]
-    // exact (rounded) conversion only: 1/q_i as doubles [nin], p_m - (prod q_i mod p_m) [nout]
-    // followed by its Shoup companions [nout]
-    double* d_inv_q = nullptr;
+    // exact (rounded) conversion only: the reciprocals 1/q_i = M_i 2^-(64 + b_i) (b_i = bitlen(q_i)
+    // - 1, M_i = floor(2^(64 + b_i) / q_i) in [2^63, 2^64)) as [nin] M_i then [nin] shifts b_i + 6;
+    // p_m - (prod q_i mod p_m) [nout] followed by its Shoup companions [nout]
+    u64* d_inv_q = nullptr;
     u64* d_corr = nullptr;
     // N^{-1} qhat_i^{-1} mod q_i and its Shoup companion, [nin][2]: the factor an inverse NTT
     // ends with when its output feeds this conversion directly (prescaled inputs)
@@ -382,7 +383,7 @@ struct ConvJob {
     u64* out;
     const int *in_ids, *out_ids, *out_rows;
     const u64 *qinv, *qmod;
-    const double* inv_q;   // non-null: subtract v Q, v = round(sum_i xhat_i / q_i) (centred remainder)
+    const u64* inv_q;      // non-null: subtract v Q, v = round(sum_i xhat_i / q_i) (centred remainder)
     const u64* corr;
     int nin, nout, ngroups;
     size_t in_pstride, out_pstride;

@@ -1217,9 +1217,10 @@ __global__ void __launch_bounds__(256, 3)
 
 // ------------------------------------------------------- base conversion ----
 // y_m = sum_i [x_i * qhat_i^{-1}]_{q_i} * (qhat_i mod p_m)  (no correction term), or, for an
-// exact table, minus v (Q mod p_m) with v = round(sum_i xhat_i / q_i) evaluated in FP64
-// (Halevi, Polyakov, Shoup 2019): y then represents the centred remainder of x mod Q, up
-// to an FP64 error that matters only within ~1e-15 of a half-integer.
+// exact table, minus v (Q mod p_m) with v = round(sum_i xhat_i / q_i) (Halevi, Polyakov,
+// Shoup 2019), evaluated in 58-bit fixed point (conv_round_term): y then represents the
+// centred remainder of x mod Q, up to a rounding error that matters only within 2^-53 of a
+// half-integer.
 // One thread per coefficient; grid.z walks over (job, group of MC <= CONV_OUT outputs), so
 // the digits of one ModUp (or the two halves of one ModDown) share a launch.  The products
 // are summed exactly in 128 bits (each < 2^122, at most 16 terms) and reduced once:
@@ -1241,7 +1242,8 @@ __global__ void __launch_bounds__(256, (MC <= 6 ? 4 : 3)) k_base_convert(kern::C
     __shared__ u64 s_c[CONV_OUT][MAX_CONV_IN];
     __shared__ DevPrime s_pm[CONV_OUT];
     __shared__ int s_row[CONV_OUT];
-    __shared__ double s_invq[MAX_CONV_IN];
+    __shared__ u64 s_invm[MAX_CONV_IN];
+    __shared__ int s_invs[MAX_CONV_IN];
     __shared__ u64 s_corr[CONV_OUT];
     __shared__ uint2 s_c2[CONV_OUT][MAXIN];     // SPLIT: (c mod 2^30, c >> 30)
     // which job and output group this CTA serves
@@ -1260,7 +1262,8 @@ __global__ void __launch_bounds__(256, (MC <= 6 ? 4 : 3)) k_base_convert(kern::C
         s_qi[tid] = P[job.in_ids[tid]].m.q;
         s_qinv[tid] = job.qinv[tid];
         s_qinvp[tid] = job.qinv[nin + tid];
-        s_invq[tid] = exact ? job.inv_q[tid] : 0.0;
+        s_invm[tid] = exact ? job.inv_q[tid] : 0;
+        s_invs[tid] = exact ? (int)job.inv_q[nin + tid] : 64;
     }
     if (tid < CONV_OUT * MAX_CONV_IN) {
         const int m = tid / MAX_CONV_IN, i = tid % MAX_CONV_IN;
@@ -1332,11 +1335,11 @@ __global__ void __launch_bounds__(256, (MC <= 6 ? 4 : 3)) k_base_convert(kern::C
         }
     }
     if (exact) {
-        double f = 0.0;
+        u64 f = 0;
 #pragma unroll
         for (int i = 0; i < MAXIN; ++i)
-            if (i < nin) f = __dadd_rn(f, __dmul_rn(__ull2double_rn(xh[i]), s_invq[i]));
-        const u64 v = (u64)__double2ll_rn(f);
+            if (i < nin) f += conv_round_term(xh[i], s_invm[i], s_invs[i]);
+        const u64 v = conv_round_finish(f);
 #pragma unroll
         for (int m = 0; m < MC; ++m) {
             const u64 pl = v * s_corr[m], ph = __umul64hi(v, s_corr[m]);

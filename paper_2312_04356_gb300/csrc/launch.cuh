@@ -50,3 +50,15 @@ __device__ __forceinline__ u64 reduce128_lazy(u64 hi, u64 lo, const DevPrime& P)
     if (l >= q) l -= q;
     return add_mod(mul_shoup(hi, P.r64, P.r64p, q), l, q);
 }
+
+// The rounding term of an exact base conversion, v = round(sum_i xh_i / q_i) (xh_i < q_i, at
+// most 16 terms), in fixed point with 58 fractional bits: with 1/q_i = M_i 2^-(64 + b_i)
+// (M_i = floor(2^(64 + b_i) / q_i), b_i = bitlen(q_i) - 1), term i is the 128-bit product
+// xh_i M_i shifted right by sh_i = b_i + 6.  Each term is truncated by less than 2^-57 and the
+// sum (< 16) by less than 2^-53 in all, against ~2^-49 for the same sum in FP64; the sum is
+// never exactly a half-integer (Q is odd), so round-half-up is round-to-nearest.
+__device__ __forceinline__ u64 conv_round_term(u64 xh, u64 m, int sh) {
+    const u64 lo = xh * m, hi = __umul64hi(xh, m);
+    return sh >= 64 ? hi >> (sh - 64) : (hi << (64 - sh)) | (lo >> sh);
+}
+__device__ __forceinline__ u64 conv_round_finish(u64 s) { return (s + (1ull << 57)) >> 58; }

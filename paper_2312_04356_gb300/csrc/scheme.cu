@@ -117,8 +117,15 @@ static std::unique_ptr<ConvTab> make_conv_tab(ckks_ctx* c, const std::vector<int
         if (t->d_tcb) t->d_tcr = dev_upload_persistent(r24p);
     }
     if (exact) {
-        std::vector<double> invq(t->nin);
-        for (int i = 0; i < t->nin; ++i) invq[i] = 1.0 / (double)c->mod_of[in_ids[i]];
+        // 1/q_i = M_i 2^-(64 + b_i): the rounding term in fixed point (kern: conv_round)
+        std::vector<u64> invq(2 * t->nin);
+        for (int i = 0; i < t->nin; ++i) {
+            const u64 qi = c->mod_of[in_ids[i]];
+            int b = 63;
+            while (!((qi >> b) & 1)) --b;
+            invq[i] = (u64)((((unsigned __int128)1) << (64 + b)) / qi);
+            invq[t->nin + i] = (u64)(b + 6);
+        }
         std::vector<u64> corr(2 * t->nout);
         for (int m = 0; m < t->nout; ++m) {
             const u64 pm = c->mod_of[out_ids[m]];

@@ -55,3 +55,33 @@ def test_largest_chunk_sums_stay_exact():
     assert float(np.sum(A * A, dtype=np.float32)) == 128 * 255 * 255
     c = [p - 1] * 16
     assert _convert_by_chunks(x, c, p) == sum(a * b for a, b in zip(x, c)) % p
+
+
+def _round_term(xh, q):
+    """one term of the exact conversion's rounding sum in 58-bit fixed point: 1/q = M 2^-(64+b),
+    b = bitlen(q) - 1, M = floor(2^(64+b) / q); the 128-bit product xh M shifted right by b + 6"""
+    b = q.bit_length() - 1
+    m = (1 << (64 + b)) // q
+    assert 2 ** 63 <= m < 2 ** 64
+    return (xh * m) >> (b + 6)
+
+
+def test_fixed_point_rounding_term_within_bound():
+    """the fixed-point sum of up to 16 terms xh_i / q_i stays within 2^-53 of the exact sum and
+    rounds to the same integer away from half-integers (the exact value is never a half-integer
+    for odd moduli)"""
+    from fractions import Fraction
+    for trial in range(200):
+        nin = int(rng.integers(1, 17))
+        qs = [int(rng.integers(2 ** (int(rng.integers(40, 62)) - 1), 2 ** 61)) | 1 for _ in range(nin)]
+        xs = [int(rng.integers(0, q)) for q in qs]
+        if trial % 10 == 0:
+            xs = [q - 1 for q in qs]                 # largest terms
+        s = sum(_round_term(x, q) for x, q in zip(xs, qs))
+        assert s < 2 ** 62
+        exact = sum(Fraction(x, q) for x, q in zip(xs, qs))
+        err = exact - Fraction(s, 2 ** 58)
+        assert 0 <= err < Fraction(1, 2 ** 53)
+        v = (s + 2 ** 57) >> 58
+        if abs(exact - int(exact) - Fraction(1, 2)) > Fraction(1, 2 ** 52):
+            assert v == int(exact + Fraction(1, 2))
