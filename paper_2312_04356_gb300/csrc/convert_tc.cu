@@ -191,9 +191,10 @@ __device__ __forceinline__ u64 chunk_reduce_lazy(const unsigned* w, u64 p, u64 r
 // EXACT / PRE: every job of the launch has an exact table / prescaled inputs.  The
 // accumulators of a tile are set to 2^23 before its first MMA, so that each holds 2^23 + D
 // (exact: below 2^24) and its bit pattern exposes D directly.
-template <int MAXIN, int TPR, bool EXACT, bool PRE>
+template <int MAXIN, int TPR, bool EXACT, bool PRE, bool LAZY>
 __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
-    k_base_convert_tc(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn, int tiles, int lazy) {
+    k_base_convert_tc(kern::ConvJobs J, const DevPrime* __restrict__ P, int logn, int tiles) {
+    constexpr bool lazy = LAZY;
     griddep_entry();
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) u64 s_bar[2];   // [0]: B image landed, [1]: MMAs of the tile done
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int m = 2 * p + e;
-                if (m >= mcount) continue;
+                if (m >= mcount) continue;   // only the last group of a table can be short
                 const u64 pm = s_p[m];
                 u64 y = chunk_reduce_lazy(r + 8 * e, pm, s_r24p[m]);
                 if (lazy) {
@@ -411,28 +412,33 @@ bool conv_tc_eligible(const ckks_ctx* c, const ConvJobs& J) {
     return J.n > 0;
 }
 
-template <int MAXIN, int TPR, bool EXACT, bool PRE>
+template <int MAXIN, int TPR, bool EXACT, bool PRE, bool LAZY>
 static void launch_tc(const ckks_ctx* c, const ConvJobs& J, dim3 grid, unsigned smem, int per) {
     // the attribute is set once per device for the largest operand tiles (K = 128, S = 16)
     constexpr int SMEM_MAX = TC_M * TC_MAXIN * 16 + TC_MAXS * TC_MAXIN * 128 + TC_M * TC_MAXIN * 8;
     static std::atomic<unsigned> done{0};
-    allow_dynamic_smem((const void*)k_base_convert_tc<MAXIN, TPR, EXACT, PRE>, SMEM_MAX, done);
-    // every conversion output goes to a forward NTT; for N = 2^16 its lazy butterflies take
-    // inputs below 4p, so the words are left in [0, 4p) there (canonical for the generic NTT)
-    klaunch(c, k_base_convert_tc<MAXIN, TPR, EXACT, PRE>, grid, TC_M * TPR, smem, J, c->d_primes, c->logn, per,
-            c->logn == 16 ? 1 : 0);
+    allow_dynamic_smem((const void*)k_base_convert_tc<MAXIN, TPR, EXACT, PRE, LAZY>, SMEM_MAX, done);
+    klaunch(c, k_base_convert_tc<MAXIN, TPR, EXACT, PRE, LAZY>, grid, TC_M * TPR, smem, J, c->d_primes, c->logn, per);
 }
 
-template <int MAXIN, int TPR>
+template <int MAXIN, int TPR, bool LAZY>
 static void launch_tc_flags(const ckks_ctx* c, const ConvJobs& J, dim3 grid, unsigned smem, int per, bool exact,
                             bool pre) {
     if (exact) {
-        if (pre) launch_tc<MAXIN, TPR, true, true>(c, J, grid, smem, per);
-        else launch_tc<MAXIN, TPR, true, false>(c, J, grid, smem, per);
+        if (pre) launch_tc<MAXIN, TPR, true, true, LAZY>(c, J, grid, smem, per);
+        else launch_tc<MAXIN, TPR, true, false, LAZY>(c, J, grid, smem, per);
     } else {
-        if (pre) launch_tc<MAXIN, TPR, false, true>(c, J, grid, smem, per);
-        else launch_tc<MAXIN, TPR, false, false>(c, J, grid, smem, per);
+        if (pre) launch_tc<MAXIN, TPR, false, true, LAZY>(c, J, grid, smem, per);
+        else launch_tc<MAXIN, TPR, false, false, LAZY>(c, J, grid, smem, per);
     }
+}
+// every conversion output goes to a forward NTT; for N = 2^16 its lazy butterflies take inputs
+// below 4p, so the words are left in [0, 4p) there (canonical for the generic NTT)
+template <int MAXIN, int TPR>
+static void launch_tc_lazy(const ckks_ctx* c, const ConvJobs& J, dim3 grid, unsigned smem, int per, bool exact,
+                           bool pre) {
+    if (c->logn == 16) launch_tc_flags<MAXIN, TPR, true>(c, J, grid, smem, per, exact, pre);
+    else launch_tc_flags<MAXIN, TPR, false>(c, J, grid, smem, per, exact, pre);
 }
 
 void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
@@ -475,11 +481,11 @@ void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
     KTimer kt_(c, "base_convert", bytes);
     const bool two = c->conv_tc_tpr == 2;
     if (maxin <= 8) {
-        if (two) launch_tc_flags<8, 2>(c, J, grid, smem, per, exact, pre);
-        else launch_tc_flags<8, 1>(c, J, grid, smem, per, exact, pre);
+        if (two) launch_tc_lazy<8, 2>(c, J, grid, smem, per, exact, pre);
+        else launch_tc_lazy<8, 1>(c, J, grid, smem, per, exact, pre);
     } else {
-        if (two) launch_tc_flags<16, 2>(c, J, grid, smem, per, exact, pre);
-        else launch_tc_flags<16, 1>(c, J, grid, smem, per, exact, pre);
+        if (two) launch_tc_lazy<16, 2>(c, J, grid, smem, per, exact, pre);
+        else launch_tc_lazy<16, 1>(c, J, grid, smem, per, exact, pre);
     }
 }
 
