@@ -92,7 +92,9 @@ typedef struct ckks_params {
 int ckks_ctx_create(const ckks_params* params, uint64_t seed, void* cuda_stream, ckks_ctx** out);
 int ckks_ctx_destroy(ckks_ctx* ctx);
 const char* ckks_last_error(const ckks_ctx* ctx);
-/* Waits for the context's stream; returns CKKS_ECUDA on a deferred device error. */
+/* Waits for the context's stream; returns CKKS_ECUDA on a deferred device error and
+ * CKKS_ETIMEOUT while bounded device waits that ran out are on record for the device (see
+ * ckks_ctx_take_device_faults). */
 int ckks_sync(ckks_ctx* ctx);
 /* Host copies of the chain: q[n_q], p[n_p], psi[n_q + n_p] (q's then p's), delta[n_q].
  * Any pointer may be NULL. */
@@ -188,6 +190,12 @@ int ckks_ctx_set_tensor_conversion(ckks_ctx* ctx, int mode);
  * records it here, releases its tensor memory and returns; its outputs are then undefined.
  * Zero in normal operation.  Synchronises the context's stream. */
 int ckks_ctx_take_device_faults(ckks_ctx* ctx, uint32_t* count);
+/* Test hook for the bounded waits (no counterpart in the paper): on != 0 makes the
+ * tensor-core base conversion on the context's device withhold its MMAs and their completion
+ * signal, so that each of its CTAs gives up waiting after ~1 s, records the timeout, releases
+ * its tensor memory and returns (outputs undefined); on == 0 restores normal operation.  The
+ * device and the context stay usable.  Synchronises the context's stream.  For tests only. */
+int ckks_debug_withhold_tensor_commit(ckks_ctx* ctx, int on);
 
 /* ---- keys (Sec. 2.1 KeyGen) ----------------------------------------------- */
 /* Secret key s (h-sparse or uniform ternary), public key (-a s + e, a) over Q_L,

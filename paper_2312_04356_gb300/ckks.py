@@ -61,6 +61,7 @@ _SIGS = {
     "ckks_ctx_set_inner_batching": [VP, I],
     "ckks_ctx_set_tensor_conversion": [VP, I],
     "ckks_ctx_take_device_faults": [VP, VP],
+    "ckks_debug_withhold_tensor_commit": [VP, I],
     "ckks_sync": [VP],
     "ckks_ctx_info": [VP, VP, VP, VP, VP],
     "ckks_ctx_gauss_table": [VP, VP],
@@ -390,6 +391,10 @@ def ckks_ctx_take_device_faults(ctx):
     a = np.zeros(1, dtype=np.uint32)
     ctx.check(lib().ckks_ctx_take_device_faults(ctx, _ptr(a)))
     return int(a[0])
+
+
+def ckks_debug_withhold_tensor_commit(ctx, on):
+    ctx.check(lib().ckks_debug_withhold_tensor_commit(ctx, int(on)))
 
 
 def ckks_ctx_set_side_streams(ctx, on):

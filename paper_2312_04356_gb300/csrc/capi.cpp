@@ -191,6 +191,8 @@ int ckks_sync(ckks_ctx* ctx) {
         REQ(ctx);
         CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
         CUDA_CHECK(cudaGetLastError());
+        CK_CHECK(kern::peek_device_faults() == 0, CKKS_ETIMEOUT,
+                 "a bounded device wait gave up (ckks_ctx_take_device_faults reads and clears the count)");
     });
 }
 
@@ -275,6 +277,14 @@ int ckks_ctx_set_tensor_conversion(ckks_ctx* ctx, int mode) {
         CK_CHECK(mode >= 0 && mode <= 2, CKKS_EINVAL, "tensor conversion mode must be 0, 1 or 2");
         ctx->conv_tc = mode != 0;
         if (mode) ctx->conv_tc_tpr = mode;
+    });
+}
+
+int ckks_debug_withhold_tensor_commit(ckks_ctx* ctx, int on) {
+    return guard(ctx, [&] {
+        REQ(ctx);
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        kern::set_tc_withhold(on != 0);
     });
 }
 

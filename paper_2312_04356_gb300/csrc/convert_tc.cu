@@ -39,6 +39,9 @@
 namespace {
 
 __device__ unsigned g_tc_faults;   // bounded waits that ran out (read and cleared by the host)
+// test hook: nonzero withholds the MMAs and their commit, so that every tile's bounded wait on
+// the MMA barrier runs out (the path a lost completion would take); set only by tests
+__device__ unsigned g_tc_withhold;
 
 constexpr int TC_M = 128;               // coefficients per tile: MMA M, TMEM lanes
 constexpr int TC_MAXIN = 16;
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(TC_M * TPR, TC_CTAS_PER_SM)
                 if (!mbar_wait(barB, 0)) ok = false;
             }
             tc_fence_after();
-            if (ok) {
+            if (ok && !*(volatile unsigned*)&g_tc_withhold) {
                 for (int s = 0; s < nin2 / 2; ++s)
                     mma_f16(taddr, smem_desc(aaddr + 256u * s, 128u, sbo), smem_desc(baddr + 256u * s, 128u, sbo),
                             idesc, 1);
@@ -487,6 +490,17 @@ void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J0, int npoly) {
         if (two) launch_tc_lazy<16, 2>(c, J, grid, smem, per, exact, pre);
         else launch_tc_lazy<16, 1>(c, J, grid, smem, per, exact, pre);
     }
+}
+
+void set_tc_withhold(bool on) {
+    const unsigned v = on ? 1u : 0u;
+    CUDA_CHECK(cudaMemcpyToSymbol(g_tc_withhold, &v, sizeof(v)));
+}
+
+unsigned peek_device_faults() {
+    unsigned v = 0;
+    CUDA_CHECK(cudaMemcpyFromSymbol(&v, g_tc_faults, sizeof(v)));
+    return v;
 }
 
 unsigned take_device_faults() {

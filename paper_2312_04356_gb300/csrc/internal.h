@@ -410,6 +410,9 @@ bool conv_tc_eligible(const ckks_ctx* c, const ConvJobs& J);
 void base_convert_tc_jobs(const ckks_ctx* c, const ConvJobs& J, int npoly);
 // bounded device waits that ran out since the last call (the count is cleared); synchronous
 unsigned take_device_faults();
+unsigned peek_device_faults();   // the same count, not cleared
+// test hook: withhold the tensor-core conversion's MMAs so that its bounded waits run out
+void set_tc_withhold(bool on);
 // key-switch inner product: D [ndig][next][N], key rows krow[e] of [ndig][nall][N];
 // ob/oa [next][N] = sum_d D_d(sigma_g) * key_d ; g = 1 means no automorphism
 // x0 (optional, rows [x0rows][N] with the primes of the first x0rows extended limbs): ob row e
