@@ -546,6 +546,33 @@ typedef struct ckks_server_params {
 int ckks_server_create(ckks_ctx* ctx, const ckks_keys* keys, const ckks_server_params* sp, ckks_server** out);
 int ckks_server_add_model(ckks_server* s, int n_blocks, const ckks_ptset* const* convs, const ckks_boot* const* boots,
                           int* model_id);
+/* A model as a chain of layers over several ciphertexts (a ResNet-shaped network of Alg. 1
+ * blocks and Alg. 2 downsampling layers).  Layer k maps its n_in ciphertexts (the previous
+ * layer's n_out) to n_out ciphertexts:
+ *   CKKS_LAYER_BLOCK: output j is the Alg. 1 block over all inputs with the sets
+ *     convs[j n_in .. j n_in + n_in - 1] and configuration boot (ckks_block for one input,
+ *     the Sec. 3.3.3 block matrix-vector product of ckks_block_multi for several), each input
+ *     first brought down to the sets' level;
+ *   CKKS_LAYER_DOWNSAMPLE: output j is ckks_downsample_layer(bt_in = boot_in, bt_out = boot,
+ *     convs[j n_in ..]) over the EvalMod outputs of the previous layer, which must be a block
+ *     layer and then stops after its bootstrap (Alg. 2 consumes the Re / Im halves; no StoC1).
+ * Requests carry [n_in][2][level + 1][N] limbs of the first layer's inputs and return
+ * [n_out][2][l_out + 1][N] of the last layer's outputs (ckks_server_model_shape).  Recording,
+ * footprint and errors as ckks_server_add_model, plus CKKS_EINVAL for a layer whose input
+ * count differs from the previous layer's output count, a downsampling layer first or after
+ * another downsampling layer, or a missing configuration. */
+#define CKKS_LAYER_BLOCK 0
+#define CKKS_LAYER_DOWNSAMPLE 1
+typedef struct ckks_server_layer {
+    int kind;                          /* CKKS_LAYER_BLOCK or CKKS_LAYER_DOWNSAMPLE */
+    int n_in, n_out;                   /* ciphertexts into and out of the layer, 1..64 */
+    const ckks_ptset* const* convs;    /* n_out * n_in conv sets, output-major */
+    const ckks_boot* boot;             /* block: its configuration; downsampling: bt_out */
+    const ckks_boot* boot_in;          /* downsampling: bt_in; block: ignored */
+} ckks_server_layer;
+int ckks_server_add_model_layers(ckks_server* s, int n_layers, const ckks_server_layer* layers, int* model_id);
+/* shape2[0..1] = ciphertexts into and out of a request of the model */
+int ckks_server_model_shape(const ckks_server* s, int model_id, int* shape2);
 /* info[0..5] = input level, input scale, output level, output scale, footprint bytes, kernels per request */
 int ckks_server_model_info(const ckks_server* s, int model_id, double* info6);
 int ckks_server_start(ckks_server* s);

@@ -19,6 +19,7 @@ SO_PATH = os.path.join(_HERE, "_build", "libckks_gb300.so")
 CKKS_OK, CKKS_EINVAL, CKKS_ENOKEY, CKKS_ELEVEL, CKKS_ENOMEM, CKKS_ETIMEOUT, CKKS_ECUDA = range(7)
 CKKS_SLOT, CKKS_COEFF, CKKS_CINS_REAL = 0, 1, 2
 CKKS_BASIS_CHEB, CKKS_BASIS_POWER = 0, 1
+CKKS_LAYER_BLOCK, CKKS_LAYER_DOWNSAMPLE = 0, 1
 
 _lib = None
 
@@ -38,6 +39,11 @@ class ckks_params(ctypes.Structure):
 
 class ckks_server_params(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_longlong)]
+
+
+class ckks_server_layer(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_in", ctypes.c_int), ("n_out", ctypes.c_int),
+                ("convs", ctypes.POINTER(ctypes.c_void_p)), ("boot", ctypes.c_void_p), ("boot_in", ctypes.c_void_p)]
 
 
 class ckks_boot_params(ctypes.Structure):
@@ -129,6 +135,8 @@ _SIGS = {
     "ckks_downsample_layer": [VP, VP, I, PVP, PVP, VP, PVP, VP, VP],
     "ckks_server_create": [VP, VP, ctypes.POINTER(ckks_server_params), PVP],
     "ckks_server_add_model": [VP, I, PVP, PVP, ctypes.POINTER(I)],
+    "ckks_server_add_model_layers": [VP, I, ctypes.POINTER(ckks_server_layer), ctypes.POINTER(I)],
+    "ckks_server_model_shape": [VP, I, VP],
     "ckks_server_model_info": [VP, I, VP],
     "ckks_server_start": [VP],
     "ckks_server_submit": [VP, I, VP, I, D, ctypes.POINTER(U64)],
@@ -1008,6 +1016,34 @@ def ckks_server_add_model(srv, convs, boots):
     return mid.value
 
 
+def ckks_server_add_model_layers(srv, layers):
+    """layers: dicts with kind (CKKS_LAYER_BLOCK / CKKS_LAYER_DOWNSAMPLE), convs (n_out lists of
+    n_in sets, output-major), boot and, for a downsampling layer, boot_in"""
+    arr = (ckks_server_layer * len(layers))()
+    keep = []
+    for k, L in enumerate(layers):
+        rows = L["convs"]
+        flat = [p for row in rows for p in row]
+        cv = _ptrs(flat)
+        keep.append(cv)
+        arr[k].kind = L["kind"]
+        arr[k].n_in = len(rows[0])
+        arr[k].n_out = len(rows)
+        arr[k].convs = ctypes.cast(cv, ctypes.POINTER(ctypes.c_void_p))
+        arr[k].boot = L["boot"].ptr
+        arr[k].boot_in = L["boot_in"].ptr if L.get("boot_in") is not None else None
+        srv.refs += flat + [L["boot"]] + ([L["boot_in"]] if L.get("boot_in") is not None else [])
+    mid = ctypes.c_int()
+    srv.check(lib().ckks_server_add_model_layers(srv, len(layers), arr, ctypes.byref(mid)))
+    return mid.value
+
+
+def ckks_server_model_shape(srv, model_id):
+    a = np.zeros(2, dtype=np.int32)
+    srv.check(lib().ckks_server_model_shape(srv, model_id, _ptr(a)))
+    return int(a[0]), int(a[1])
+
+
 def ckks_server_model_info(srv, model_id):
     a = np.zeros(6, dtype=np.float64)
     srv.check(lib().ckks_server_model_info(srv, model_id, _ptr(a)))
@@ -1040,10 +1076,11 @@ def ckks_server_wait(srv, rid, timeout_s=60.0):
     return st.value
 
 
-def ckks_server_result(srv, rid, n):
+def ckks_server_result(srv, rid, n, n_out=1):
+    """limbs [2][level + 1][N] of a one-output model, [n_out][2][level + 1][N] otherwise"""
     lev, sc = ctypes.c_int(), ctypes.c_double()
     srv.check(lib().ckks_server_result(srv, rid, None, ctypes.byref(lev), ctypes.byref(sc)))
-    out = np.zeros((2, lev.value + 1, n), dtype=np.uint64)
+    out = np.zeros((2, lev.value + 1, n) if n_out == 1 else (n_out, 2, lev.value + 1, n), dtype=np.uint64)
     srv.check(lib().ckks_server_result(srv, rid, _ptr(out), ctypes.byref(lev), ctypes.byref(sc)))
     return out, lev.value, sc.value
 

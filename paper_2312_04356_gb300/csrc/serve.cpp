@@ -29,13 +29,27 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// One layer of a model: n_out output ciphertexts from n_in inputs.  A block layer computes each
+// output as an Alg. 1 block over all inputs (ckks_block, or the Sec. 3.3.3 block matrix-vector
+// product when n_in > 1); a downsampling layer (Alg. 2) computes each output from the EvalMod
+// outputs of the layer before it, which then stops after its bootstrap (no StoC1).
+struct Layer {
+    int kind = CKKS_LAYER_BLOCK;
+    int n_in = 1, n_out = 1;
+    std::vector<const ckks_ptset*> convs;   // [n_out][n_in]
+    const ckks_boot* boot = nullptr;        // block: its configuration; downsampling: bt_out
+    const ckks_boot* boot_in = nullptr;     // downsampling: bt_in (stride-2 tail of the inputs)
+};
+
 struct Model {
-    std::vector<const ckks_ptset*> convs;
-    std::vector<const ckks_boot*> boots;
+    std::vector<Layer> layers;
     int in_level = 0, out_level = 0;
     double in_scale = 0, out_scale = 0;
+    int n_in = 1, n_out = 1;      // ciphertexts into and out of a request
     long long footprint = 0;      // peak bytes of temporaries of one request
     long long kernels = 0;        // kernel launches of one request's graph
+    size_t in_words(size_t n) const { return (size_t)n_in * 2 * (size_t)(in_level + 1) * n; }
+    size_t out_words(size_t n) const { return (size_t)n_out * 2 * (size_t)(out_level + 1) * n; }
 };
 
 struct Request {
@@ -104,21 +118,68 @@ int sguard(ckks_server* s, F&& f) {
     }
 }
 
-// One request of model m, reading d_in and writing d_out (both coefficient domain).
+// One request of model m, reading d_in and writing d_out (both coefficient domain,
+// [ciphertexts][2][level + 1][N]).
 void run_model(ckks_server* s, const Model& m, const u64* d_in, u64* d_out) {
     ckks_ctx* c = s->ctx;
-    ckks_ct x = ops::new_ct(c, m.in_level, m.in_scale);
-    const size_t win = 2 * (size_t)(m.in_level + 1) * c->n;
-    CUDA_CHECK(cudaMemcpyAsync(x.buf.ptr, d_in, win * 8, cudaMemcpyDeviceToDevice, c->stream));
-    kern::ntt_forward(c, x.buf.ptr, 2 * (m.in_level + 1), c->d_iota, m.in_level + 1);
-    for (size_t b = 0; b < m.convs.size(); ++b) {
-        if (x.level != m.convs[b]->level) x = ops::level_down(x, m.convs[b]->level);
-        x = ops::block(*s->keys, *m.boots[b], *m.convs[b], x);
+    const ckks_keys& keys = *s->keys;
+    const size_t per_in = 2 * (size_t)(m.in_level + 1) * c->n;
+    std::vector<ckks_ct> xs;
+    for (int i = 0; i < m.n_in; ++i) {
+        ckks_ct x = ops::new_ct(c, m.in_level, m.in_scale);
+        CUDA_CHECK(cudaMemcpyAsync(x.buf.ptr, d_in + i * per_in, per_in * 8, cudaMemcpyDeviceToDevice, c->stream));
+        kern::ntt_forward(c, x.buf.ptr, 2 * (m.in_level + 1), c->d_iota, m.in_level + 1);
+        xs.push_back(std::move(x));
     }
-    CK_CHECK(x.level == m.out_level, CKKS_EINVAL, "model output level changed");
-    const size_t wout = 2 * (size_t)(x.level + 1) * c->n;
-    CUDA_CHECK(cudaMemcpyAsync(d_out, x.buf.ptr, wout * 8, cudaMemcpyDeviceToDevice, c->stream));
-    kern::ntt_inverse(c, d_out, 2 * (x.level + 1), c->d_iota, x.level + 1);
+    std::vector<ckks_ct> res, ims;    // EvalMod outputs handed to a downsampling layer
+    for (size_t k = 0; k < m.layers.size(); ++k) {
+        const Layer& L = m.layers[k];
+        const bool to_ds = k + 1 < m.layers.size() && m.layers[k + 1].kind == CKKS_LAYER_DOWNSAMPLE;
+        std::vector<ckks_ct> ys, nre, nim;
+        if (L.kind == CKKS_LAYER_BLOCK) {
+            const int lev = L.convs[0]->level;
+            for (ckks_ct& x : xs)
+                if (x.level != lev) x = ops::level_down(x, lev);
+            std::vector<const ckks_ct*> ins;
+            for (const ckks_ct& x : xs) ins.push_back(&x);
+            for (int j = 0; j < L.n_out; ++j) {
+                const std::vector<const ckks_ptset*> cs(L.convs.begin() + (size_t)j * L.n_in,
+                                                        L.convs.begin() + (size_t)(j + 1) * L.n_in);
+                if (!to_ds) {
+                    ys.push_back(L.n_in == 1 ? ops::block(keys, *L.boot, *cs[0], *ins[0])
+                                             : ops::block_multi(keys, *L.boot, cs, ins));
+                } else {
+                    const ckks_ct x0 = L.n_in == 1 ? ops::bsgs(keys, *ins[0], *cs[0], true)
+                                                   : ops::bsgs_multi(keys, ins, cs, true);
+                    ckks_ct re, im;
+                    ops::bootstrap(keys, *L.boot, x0, re, im);
+                    nre.push_back(std::move(re));
+                    nim.push_back(std::move(im));
+                }
+            }
+        } else {
+            std::vector<const ckks_ct*> rp, ip;
+            for (size_t i = 0; i < res.size(); ++i) {
+                rp.push_back(&res[i]);
+                ip.push_back(&ims[i]);
+            }
+            for (int j = 0; j < L.n_out; ++j) {
+                const std::vector<const ckks_ptset*> cs(L.convs.begin() + (size_t)j * L.n_in,
+                                                        L.convs.begin() + (size_t)(j + 1) * L.n_in);
+                ys.push_back(ops::downsample_layer(keys, *L.boot_in, *L.boot, rp, ip, cs));
+            }
+        }
+        xs = std::move(ys);
+        res = std::move(nre);
+        ims = std::move(nim);
+    }
+    const size_t per_out = 2 * (size_t)(m.out_level + 1) * c->n;
+    for (int j = 0; j < m.n_out; ++j) {
+        CK_CHECK(xs[j].level == m.out_level, CKKS_EINVAL, "model output level changed");
+        CUDA_CHECK(cudaMemcpyAsync(d_out + j * per_out, xs[j].buf.ptr, per_out * 8, cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        kern::ntt_inverse(c, d_out + j * per_out, 2 * (m.out_level + 1), c->d_iota, m.out_level + 1);
+    }
 }
 
 double percentile(std::vector<double> v, double p) {
@@ -151,7 +212,7 @@ bool step(ckks_server* s) {
             r.state = CKKS_REQ_CANCELLED;
             ++s->cancelled;
         } else {
-            r.out.assign(sl.h_out, sl.h_out + 2 * (size_t)(s->models[r.model].out_level + 1) * s->ctx->n);
+            r.out.assign(sl.h_out, sl.h_out + s->models[r.model].out_words(s->ctx->n));
             r.state = CKKS_REQ_DONE;
             ++s->completed;
             s->lat_ms.push_back(std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count());
@@ -188,8 +249,7 @@ bool step(ckks_server* s) {
         cudaError_t e = cudaMemcpyAsync(sl.d_in, sl.h_in, r.in.size() * 8, cudaMemcpyHostToDevice, sl.stream);
         if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec[r.model], sl.stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sl.h_out, sl.d_out, 2 * (size_t)(m.out_level + 1) * s->ctx->n * 8,
-                                cudaMemcpyDeviceToHost, sl.stream);
+            e = cudaMemcpyAsync(sl.h_out, sl.d_out, m.out_words(s->ctx->n) * 8, cudaMemcpyDeviceToHost, sl.stream);
         if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
         if (e != cudaSuccess) {
             r.state = CKKS_REQ_FAILED;
@@ -267,6 +327,109 @@ int ckks_server_create(ckks_ctx* ctx, const ckks_keys* keys, const ckks_server_p
     });
 }
 
+}  // extern "C"
+
+namespace {
+
+// checks a model's layers, sizes the slots' buffers, runs one request eagerly (checking keys and
+// levels, measuring the footprint) and records the request's graph for every slot
+void add_model_impl(ckks_server* s, Model m, int* model_id) {
+    CK_CHECK(!s->started, CKKS_EINVAL, "models are added before ckks_server_start");
+    CK_CHECK(!s->ctx->timing, CKKS_EINVAL, "switch kernel timing off before recording graphs");
+    ckks_ctx* c = s->ctx;
+    const int nl = (int)m.layers.size();
+    CK_CHECK(nl >= 1 && nl <= 64, CKKS_EINVAL, "a model has 1 to 64 layers");
+    for (int k = 0; k < nl; ++k) {
+        const Layer& L = m.layers[k];
+        CK_CHECK(L.kind == CKKS_LAYER_BLOCK || L.kind == CKKS_LAYER_DOWNSAMPLE, CKKS_EINVAL, "unknown layer kind");
+        CK_CHECK(L.n_in >= 1 && L.n_in <= 64 && L.n_out >= 1 && L.n_out <= 64, CKKS_EINVAL,
+                 "a layer has 1 to 64 ciphertexts in and out");
+        CK_CHECK(L.boot != nullptr, CKKS_EINVAL, "a layer needs its bootstrapping configuration");
+        CK_CHECK((int)L.convs.size() == L.n_in * L.n_out, CKKS_EINVAL, "a layer needs n_out x n_in conv sets");
+        for (const ckks_ptset* p : L.convs) CK_CHECK(p != nullptr, CKKS_EINVAL, "a conv set is NULL");
+        if (k > 0) CK_CHECK(L.n_in == m.layers[k - 1].n_out, CKKS_EINVAL, "a layer's inputs are the previous outputs");
+        if (L.kind == CKKS_LAYER_DOWNSAMPLE) {
+            CK_CHECK(k > 0 && m.layers[k - 1].kind == CKKS_LAYER_BLOCK, CKKS_EINVAL,
+                     "a downsampling layer follows a block layer (it takes that layer's EvalMod outputs)");
+            CK_CHECK(L.boot_in != nullptr, CKKS_EINVAL, "a downsampling layer needs bt_in");
+        }
+    }
+    m.n_in = m.layers.front().n_in;
+    m.n_out = m.layers.back().n_out;
+    m.in_level = m.layers.front().convs[0]->level;
+    m.in_scale = c->delta[m.in_level];
+    m.out_level = m.layers.back().boot->l_out;
+    m.out_scale = c->delta[m.out_level];
+    const size_t win = m.in_words(c->n), wout = m.out_words(c->n);
+    // slot buffers sized for every model
+    for (Slot& sl : s->slots) {
+        if (sl.in_words < win) {
+            if (sl.d_in) cudaFree(sl.d_in);
+            if (sl.h_in) cudaFreeHost(sl.h_in);
+            sl.d_in = nullptr;
+            sl.h_in = nullptr;
+            CUDA_CHECK(cudaMalloc((void**)&sl.d_in, win * 8));
+            CUDA_CHECK(cudaMallocHost((void**)&sl.h_in, win * 8));
+            CUDA_CHECK(cudaMemset(sl.d_in, 0, win * 8));
+            sl.in_words = win;
+        }
+        if (sl.out_words < wout) {
+            if (sl.d_out) cudaFree(sl.d_out);
+            if (sl.h_out) cudaFreeHost(sl.h_out);
+            sl.d_out = nullptr;
+            sl.h_out = nullptr;
+            CUDA_CHECK(cudaMalloc((void**)&sl.d_out, wout * 8));
+            CUDA_CHECK(cudaMallocHost((void**)&sl.h_out, wout * 8));
+            sl.out_words = wout;
+        }
+    }
+    // one eager request: builds lazily created tables, checks keys and levels, and
+    // measures the temporaries' peak in the context's memory pool
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    cudaMemPool_t pool;
+    CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, s->device));
+    unsigned long long zero = 0, base = 0, high = 0;   // the pool attributes are 64-bit
+    CUDA_CHECK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &base));
+    CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    const long long l0 = c->launches;
+    run_model(s, m, s->slots[0].d_in, s->slots[0].d_out);
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    m.kernels = c->launches - l0;
+    CUDA_CHECK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+    m.footprint = high > base ? (long long)(high - base) : 0;
+    if (s->sp.hbm_budget > 0)
+        CK_CHECK(m.footprint <= s->sp.hbm_budget, CKKS_ENOMEM, "one request of this model exceeds the HBM budget");
+    const int id = (int)s->models.size();
+    for (Slot& sl : s->slots) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        CUDA_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            run_model(s, m, sl.d_in, sl.d_out);
+        } catch (...) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(c->stream, &tmp);
+            if (tmp) cudaGraphDestroy(tmp);
+            throw;
+        }
+        CUDA_CHECK(cudaStreamEndCapture(c->stream, &g));
+        const cudaError_t ie = cudaGraphInstantiate(&e, g, 0);
+        if (ie != cudaSuccess) {
+            cudaGraphDestroy(g);
+            CUDA_CHECK(ie);
+        }
+        sl.graph.push_back(g);
+        sl.exec.push_back(e);
+    }
+    c->launches = l0 + m.kernels;
+    s->models.push_back(std::move(m));
+    *model_id = id;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ckks_server_add_model(ckks_server* s, int n_blocks, const ckks_ptset* const* convs, const ckks_boot* const* boots,
                           int* model_id) {
     if (!s) return CKKS_EINVAL;
@@ -274,86 +437,50 @@ int ckks_server_add_model(ckks_server* s, int n_blocks, const ckks_ptset* const*
         REQ(convs);
         REQ(boots);
         REQ(model_id);
-        CK_CHECK(!s->started, CKKS_EINVAL, "models are added before ckks_server_start");
         CK_CHECK(n_blocks >= 1 && n_blocks <= 64, CKKS_EINVAL, "n_blocks must be in [1, 64]");
-        CK_CHECK(!s->ctx->timing, CKKS_EINVAL, "switch kernel timing off before recording graphs");
-        ckks_ctx* c = s->ctx;
         Model m;
         for (int b = 0; b < n_blocks; ++b) {
             REQ(convs[b]);
             REQ(boots[b]);
-            m.convs.push_back(convs[b]);
-            m.boots.push_back(boots[b]);
+            Layer L;
+            L.convs.push_back(convs[b]);
+            L.boot = boots[b];
+            m.layers.push_back(std::move(L));
         }
-        m.in_level = convs[0]->level;
-        m.in_scale = c->delta[m.in_level];
-        m.out_level = boots[n_blocks - 1]->l_out;
-        m.out_scale = c->delta[m.out_level];
-        const size_t win = 2 * (size_t)(m.in_level + 1) * c->n, wout = 2 * (size_t)(m.out_level + 1) * c->n;
-        // slot buffers sized for every model
-        for (Slot& sl : s->slots) {
-            if (sl.in_words < win) {
-                if (sl.d_in) cudaFree(sl.d_in);
-                if (sl.h_in) cudaFreeHost(sl.h_in);
-                sl.d_in = nullptr;
-                sl.h_in = nullptr;
-                CUDA_CHECK(cudaMalloc((void**)&sl.d_in, win * 8));
-                CUDA_CHECK(cudaMallocHost((void**)&sl.h_in, win * 8));
-                CUDA_CHECK(cudaMemset(sl.d_in, 0, win * 8));
-                sl.in_words = win;
-            }
-            if (sl.out_words < wout) {
-                if (sl.d_out) cudaFree(sl.d_out);
-                if (sl.h_out) cudaFreeHost(sl.h_out);
-                sl.d_out = nullptr;
-                sl.h_out = nullptr;
-                CUDA_CHECK(cudaMalloc((void**)&sl.d_out, wout * 8));
-                CUDA_CHECK(cudaMallocHost((void**)&sl.h_out, wout * 8));
-                sl.out_words = wout;
-            }
-        }
-        // one eager request: builds lazily created tables, checks keys and levels, and
-        // measures the temporaries' peak in the context's memory pool
-        CUDA_CHECK(cudaStreamSynchronize(c->stream));
-        cudaMemPool_t pool;
-        CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, s->device));
-        unsigned long long zero = 0, base = 0, high = 0;   // the pool attributes are 64-bit
-        CUDA_CHECK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &base));
-        CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
-        const long long l0 = c->launches;
-        run_model(s, m, s->slots[0].d_in, s->slots[0].d_out);
-        CUDA_CHECK(cudaStreamSynchronize(c->stream));
-        m.kernels = c->launches - l0;
-        CUDA_CHECK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
-        m.footprint = high > base ? (long long)(high - base) : 0;
-        if (s->sp.hbm_budget > 0)
-            CK_CHECK(m.footprint <= s->sp.hbm_budget, CKKS_ENOMEM, "one request of this model exceeds the HBM budget");
-        const int id = (int)s->models.size();
-        for (Slot& sl : s->slots) {
-            cudaGraph_t g = nullptr;
-            cudaGraphExec_t e = nullptr;
-            CUDA_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-            try {
-                run_model(s, m, sl.d_in, sl.d_out);
-            } catch (...) {
-                cudaGraph_t tmp = nullptr;
-                cudaStreamEndCapture(c->stream, &tmp);
-                if (tmp) cudaGraphDestroy(tmp);
-                throw;
-            }
-            CUDA_CHECK(cudaStreamEndCapture(c->stream, &g));
-            const cudaError_t ie = cudaGraphInstantiate(&e, g, 0);
-            if (ie != cudaSuccess) {
-                cudaGraphDestroy(g);
-                CUDA_CHECK(ie);
-            }
-            sl.graph.push_back(g);
-            sl.exec.push_back(e);
-        }
-        c->launches = l0 + m.kernels;
-        s->models.push_back(std::move(m));
-        *model_id = id;
+        add_model_impl(s, std::move(m), model_id);
     });
+}
+
+int ckks_server_add_model_layers(ckks_server* s, int n_layers, const ckks_server_layer* layers, int* model_id) {
+    if (!s) return CKKS_EINVAL;
+    return sguard(s, [&] {
+        REQ(layers);
+        REQ(model_id);
+        CK_CHECK(n_layers >= 1 && n_layers <= 64, CKKS_EINVAL, "n_layers must be in [1, 64]");
+        Model m;
+        for (int k = 0; k < n_layers; ++k) {
+            const ckks_server_layer& d = layers[k];
+            CK_CHECK(d.n_in >= 1 && d.n_in <= 64 && d.n_out >= 1 && d.n_out <= 64, CKKS_EINVAL,
+                     "a layer has 1 to 64 ciphertexts in and out");
+            REQ(d.convs);
+            Layer L;
+            L.kind = d.kind;
+            L.n_in = d.n_in;
+            L.n_out = d.n_out;
+            L.convs.assign(d.convs, d.convs + (size_t)d.n_in * d.n_out);
+            L.boot = d.boot;
+            L.boot_in = d.boot_in;
+            m.layers.push_back(std::move(L));
+        }
+        add_model_impl(s, std::move(m), model_id);
+    });
+}
+
+int ckks_server_model_shape(const ckks_server* s, int model_id, int* shape2) {
+    if (!s || !shape2 || model_id < 0 || model_id >= (int)s->models.size()) return CKKS_EINVAL;
+    shape2[0] = s->models[model_id].n_in;
+    shape2[1] = s->models[model_id].n_out;
+    return CKKS_OK;
 }
 
 int ckks_server_start(ckks_server* s) {
@@ -380,7 +507,7 @@ int ckks_server_submit(ckks_server* s, int model_id, const uint64_t* host_in, in
         CK_CHECK(s->sp.hbm_budget == 0 || m.footprint <= s->sp.hbm_budget, CKKS_ENOMEM, "request exceeds the budget");
         Request r;
         r.model = model_id;
-        r.in.assign(host_in, host_in + 2 * (size_t)(level + 1) * s->ctx->n);
+        r.in.assign(host_in, host_in + m.in_words(s->ctx->n));
         r.t_submit = Clock::now();
         {
             std::lock_guard<std::mutex> lk(s->mu);
