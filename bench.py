@@ -69,10 +69,11 @@ def parse_args():
                     help="--impl reference: the config-2 chain at N=2^10 (checks the arm quickly; not a measurement)")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
     ap.add_argument("--batch", type=int, default=8, help="ciphertexts run concurrently for the batched figure")
-    ap.add_argument("--workload", default="block", choices=["block", "ds", "serve", "batch", "cfg4"],
+    ap.add_argument("--workload", default="block", choices=["block", "ds", "serve", "batch", "cfg4", "serve5"],
                     help="block: the Alg. 1 block (default); ds: the downsampling layer of Alg. 2; "
                          "serve: the serving loop under Poisson arrivals; batch: 64 uneven-shape blocks "
-                         "(ResNet-20 stage shapes) batched through the serving runtime")
+                         "(ResNet-20 stage shapes) batched through the serving runtime; cfg4: ResNet-18-shaped "
+                         "layers; serve5: whole ResNet-20 / ResNet-18-shaped requests through the serving loop")
     ap.add_argument("--batch-size", type=int, default=64, help="batch: number of seeded inputs")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--variant", type=int, default=-1, help="--kernel ntt: time one launch variant only")
@@ -1417,6 +1418,175 @@ def run_kernel_ks(args):
                       "per_kernel": res}))
 
 
+def run_serve5(args):
+    """Config 5: the serving loop at N = 2^16 with whole-network requests, 70% ResNet-20-shaped
+    stacks on CIFAR-shaped input (27 conv-bootstrap layers: 9 per stage at 16x32x32, 32x16x16 and
+    64x8x8, the first of stages 2 and 3 an Alg. 2 stride-2 entry fed by the EvalMod outputs of the
+    layer before it) and 30% ResNet-18-shaped stacks on ImageNet-shaped input (the 7x7 stride-2
+    stem over three client-encoded polyphase ciphertexts into 16, the 3x3 stride-2 average pool
+    into 4, stage convs whose channels span 4 / 2 / 1 / 1 ciphertexts, stride-2 entries; the 1x1
+    shortcut branches and the residual additions are not part of the chained model), each as one
+    recorded request graph per slot.  A saturating closed loop gives the capacity, then Poisson
+    arrivals at 0.5 / 0.8 / 0.95 of it, beside the same closed loop on one slot (the unbatched
+    plain path).  HActivation excluded as in the config-2 block; synthetic weights and inputs."""
+    import torch
+    from paper_2312_04356_gb300 import build
+    build.build()
+    import paper_2312_04356_gb300.ckks as K
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = K.ckks_ctx_create(WL.PARAMS[CONFIG], 1, stream.cuda_stream)
+    tuned = K.ckks_autotune(ctx, 3)
+    q, p, psi, delta = K.ckks_ctx_info(ctx)
+    s_pt = (2.0 ** 49 * q[1]) / delta[1]
+    rng = np.random.default_rng(55)
+    t_setup = time.perf_counter()
+
+    def he(cout, cin, f):
+        return rng.normal(0.0, np.sqrt(2.0 / (cin * f * f)), (cout, cin, f, f))
+
+    def conv_sets(c, n, w):                   # [n][n] sets of a stage conv over n ciphertexts
+        C = c // n
+        Wc = he(c, c, 3)
+        return [[K.ckks_ptset_conv_fused(ctx, Wc[C * j:C * j + C, C * i:C * i + C], C, C, 3, w, 1, s_pt)
+                 for i in range(n)] for j in range(n)]
+
+    def entry_sets(cin, cout, n_in, n_out, w_in, f=3):
+        cpo = cout // n_out
+        Wd = he(cout, cin, f)
+        return [[K.ckks_ptset_conv_fused_s2(ctx, Wd[cpo * j:cpo * j + cpo], cin, cpo, f, w_in, t, 1, s_pt)
+                 for t in range(n_in)] for j in range(n_out)]
+
+    B, D = K.CKKS_LAYER_BLOCK, K.CKKS_LAYER_DOWNSAMPLE
+    boots, sets = [], []
+
+    def boot(*a, **kw):
+        b = K.ckks_boot_create(ctx, *a, **kw)
+        boots.append(b)
+        return b
+
+    # ---- ResNet-20-shaped stack (27 layers)
+    r20 = []
+    stages = ((16, 32, 64), (32, 16, 32), (64, 8, 16))    # channels, image width, slice width
+    for si, (c, h, w) in enumerate(stages):
+        bt = boot(w, h, c)
+        cs = conv_sets(c, 1, w)
+        sets.extend(p for row in cs for p in row)
+        n_blocks = 9 if si == 0 else 8
+        last = si == len(stages) - 1
+        for b in range(n_blocks):
+            pre_ds = not last and b == n_blocks - 1
+            bt_b = boot(w, h, c, stride=2) if pre_ds else bt
+            r20.append(dict(kind=B, convs=cs, boot=bt_b))
+        if not last:
+            c2, h2, w2 = stages[si + 1]
+            es = entry_sets(c, c2, 1, 1, w)
+            sets.extend(p for row in es for p in row)
+            r20.append(dict(kind=D, convs=es, boot=boot(w2, h2, c2), boot_in=r20[-1]["boot"]))
+    # ---- ResNet-18-shaped stack (18 layers)
+    r18 = []
+    W = he(64, 3, 7)
+    stem = [[K.ckks_ptset_conv_fused_s2(ctx, W[4 * j:4 * j + 4], 3, 4, 7, 256, t, 1, s_pt) for t in range(3)]
+            for j in range(16)]
+    sets.extend(p for row in stem for p in row)
+    bt_in = boot(128, 112, 4, stride=2)
+    r18.append(dict(kind=B, convs=stem, boot=bt_in))
+    pool = [K.ckks_ptset_dwconv_fused_s2(ctx, np.full((16, 3, 3), 1.0 / 9.0), 128, t, 1, s_pt) for t in range(4)]
+    sets.extend(pool)
+    r18.append(dict(kind=D, convs=[pool] * 4, boot=boot(64, 56, 16), boot_in=bt_in, n_in=16,
+                    inputs=[[4 * j + t for t in range(4)] for j in range(4)]))
+    shapes = ((64, 56, 64, 4), (128, 28, 32, 2), (256, 14, 16, 1), (512, 7, 8, 1))   # c, h, w, ciphertexts
+    for si, (c, h, w, n) in enumerate(shapes):
+        cs = conv_sets(c, n, w)
+        sets.extend(p for row in cs for p in row)
+        bt = boot(w, h, c // n)
+        n_conv = 4 if si == 0 else 3
+        last = si == len(shapes) - 1
+        for b in range(n_conv):
+            pre_ds = not last and b == n_conv - 1
+            r18.append(dict(kind=B, convs=cs, boot=boot(w, h, c // n, stride=2) if pre_ds else bt))
+        if not last:
+            c2, h2, w2, n2 = shapes[si + 1]
+            es = entry_sets(c, c2, n, n2, w)
+            sets.extend(p for row in es for p in row)
+            r18.append(dict(kind=D, convs=es, boot=boot(w2, h2, c2 // n2), boot_in=r18[-1]["boot"]))
+    rots = set()
+    for x in sets:
+        rots |= set(K.ckks_ptset_rotations(x))
+    for b in boots:
+        rots |= set(K.ckks_boot_rotations(b))
+    keys = K.ckks_keygen(ctx, sorted(rots), True)
+    # inputs: one 16 x 32 x 32 ciphertext; three polyphase ciphertexts of a 3 x 224 x 224 image
+    x20 = K.ckks_ct_export_rns(ctx, K.ckks_encrypt(ctx, keys, K.ckks_encode_image(
+        ctx, WL.image(301, 16, 32), 64, 1, delta[1]), 301))
+    pp = polyphase(WL.image(302, 3, 224))
+    x18 = np.stack([K.ckks_ct_export_rns(ctx, K.ckks_encrypt(ctx, keys, K.ckks_encode_image(
+        ctx, pp[4 * t:4 * t + 4], 128, 1, delta[1]), 303 + t)) for t in range(3)])
+    K.ckks_sync(ctx)
+    setup_s = time.perf_counter() - t_setup
+    g = np.random.default_rng(19)
+
+    def make(n_slots):
+        t0 = time.perf_counter()
+        srv = K.ckks_server_create(ctx, keys, n_slots, 0)
+        a = K.ckks_server_add_model_layers(srv, r20)
+        b = K.ckks_server_add_model_layers(srv, r18)
+        K.ckks_server_start(srv)
+        return srv, a, b, time.perf_counter() - t0
+
+    def run(srv, a, b, rate, secs, closed=False, n_slots=1):
+        K.ckks_server_reset_stats(srv)
+        ids = []
+        t0 = time.perf_counter()
+        t_next = t0
+        while time.perf_counter() - t0 <= secs:
+            now = time.perf_counter()
+            if closed or now >= t_next:
+                if g.random() < 0.7:
+                    ids.append((K.ckks_server_submit(srv, a, x20, 1, delta[1]), 1))
+                else:
+                    ids.append((K.ckks_server_submit(srv, b, x18, 1, delta[1]), 4))
+                t_next += 0.0 if closed else float(g.exponential(1.0 / rate))
+                if closed and len(ids) >= 2 * n_slots:
+                    K.ckks_server_wait(srv, ids[-2 * n_slots + 1][0], 600)
+            else:
+                time.sleep(min(t_next - now, 0.005))
+        for r, _ in ids:
+            K.ckks_server_wait(srv, r, 600)
+        t_end = time.perf_counter()
+        for r, n_out in ids:
+            K.ckks_server_result(srv, r, ctx.n, n_out)
+        st = K.ckks_server_stats(srv)
+        return {"offered_per_s": None if closed else round(rate, 3), "requests": len(ids),
+                "completed_per_s": round(st["completed"] / (t_end - t0), 3), "p50_ms": round(st["p50_ms"], 1),
+                "p99_ms": round(st["p99_ms"], 1), "mean_ms": round(st["mean_ms"], 1),
+                "max_in_flight": int(st["max_in_flight"]), "failed": int(st["failed"])}
+
+    slots = max(1, args.batch)
+    secs = max(4.0, float(args.serve_seconds))
+    srv, a, b, rec_s = make(slots)
+    info = {"resnet20": K.ckks_server_model_info(srv, a), "resnet18": K.ckks_server_model_info(srv, b),
+            "resnet18_shape": K.ckks_server_model_shape(srv, b)}
+    run(srv, a, b, 1.0, 2.0)                                               # warm-up
+    cap = run(srv, a, b, None, secs, closed=True, n_slots=slots)
+    loads = [run(srv, a, b, f * cap["completed_per_s"], secs) for f in (0.5, 0.8, 0.95)]
+    srv.close()
+    srv, a, b, _ = make(1)
+    run(srv, a, b, 1.0, 1.0)
+    plain = run(srv, a, b, None, secs, closed=True, n_slots=1)
+    srv.close()
+    line = {"metric": "requests/s of whole-network inference requests at N=2^16 (config 5 mix)",
+            "value": cap["completed_per_s"], "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "config 5: 70% ResNet-20-shaped stacks (27 layers), 30% ResNet-18-shaped stacks "
+                                   "(18 layers, shortcut branches not chained); Poisson arrivals",
+                       "slots": slots, "seconds_per_load": secs, "rotation_keys": len(rots),
+                       "autotune_ntt_variant_per_size_class": tuned},
+            "capacity_closed_loop": cap, "poisson": dict(zip(("0.5", "0.8", "0.95"), loads)),
+            "plain_one_slot": plain, "models": info, "setup_s": round(setup_s, 1), "record_s": round(rec_s, 1)}
+    print(json.dumps(line), flush=True)
+
+
 def run_kernel_conv(args):
     """base conversion alone, on the tensor cores and on the integer pipe: the ModUp of one
     config-2 ciphertext at the top level (three digits of 8 limbs, 23 outputs each) and the
@@ -1471,6 +1641,8 @@ if __name__ == "__main__":
         run_batch(a)
     elif a.workload == "cfg4" and a.impl == "ours":
         run_cfg4(a)
+    elif a.workload == "serve5" and a.impl == "ours":
+        run_serve5(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -548,25 +548,27 @@ int ckks_server_add_model(ckks_server* s, int n_blocks, const ckks_ptset* const*
                           int* model_id);
 /* A model as a chain of layers over several ciphertexts (a ResNet-shaped network of Alg. 1
  * blocks and Alg. 2 downsampling layers).  Layer k maps its n_in ciphertexts (the previous
- * layer's n_out) to n_out ciphertexts:
- *   CKKS_LAYER_BLOCK: output j is the Alg. 1 block over all inputs with the sets
- *     convs[j n_in .. j n_in + n_in - 1] and configuration boot (ckks_block for one input,
- *     the Sec. 3.3.3 block matrix-vector product of ckks_block_multi for several), each input
- *     first brought down to the sets' level;
- *   CKKS_LAYER_DOWNSAMPLE: output j is ckks_downsample_layer(bt_in = boot_in, bt_out = boot,
- *     convs[j n_in ..]) over the EvalMod outputs of the previous layer, which must be a block
- *     layer and then stops after its bootstrap (Alg. 2 consumes the Re / Im halves; no StoC1).
+ * layer's n_out) to n_out ciphertexts; output j reads k of them, in_index[j k .. j k + k - 1]
+ * (in_index NULL: all n_in in order, k = n_in), with the sets convs[j k .. j k + k - 1]:
+ *   CKKS_LAYER_BLOCK: output j is the Alg. 1 block over its inputs with configuration boot
+ *     (ckks_block for one input, the Sec. 3.3.3 block matrix-vector product of
+ *     ckks_block_multi for several), each input first brought down to the sets' level;
+ *   CKKS_LAYER_DOWNSAMPLE: output j is ckks_downsample_layer(bt_in = boot_in, bt_out = boot)
+ *     over the EvalMod outputs of its inputs: the previous layer must be a block layer, and
+ *     it then stops after its bootstrap (Alg. 2 consumes the Re / Im halves; no StoC1).
  * Requests carry [n_in][2][level + 1][N] limbs of the first layer's inputs and return
  * [n_out][2][l_out + 1][N] of the last layer's outputs (ckks_server_model_shape).  Recording,
  * footprint and errors as ckks_server_add_model, plus CKKS_EINVAL for a layer whose input
- * count differs from the previous layer's output count, a downsampling layer first or after
- * another downsampling layer, or a missing configuration. */
+ * count differs from the previous layer's output count, an input index out of range, a
+ * downsampling layer first or after another downsampling layer, or a missing configuration. */
 #define CKKS_LAYER_BLOCK 0
 #define CKKS_LAYER_DOWNSAMPLE 1
 typedef struct ckks_server_layer {
     int kind;                          /* CKKS_LAYER_BLOCK or CKKS_LAYER_DOWNSAMPLE */
     int n_in, n_out;                   /* ciphertexts into and out of the layer, 1..64 */
-    const ckks_ptset* const* convs;    /* n_out * n_in conv sets, output-major */
+    int k;                             /* inputs per output, 1..n_in (n_in when in_index is NULL) */
+    const int* in_index;               /* [n_out][k] input indices, or NULL: every output reads all */
+    const ckks_ptset* const* convs;    /* n_out * k conv sets, output-major */
     const ckks_boot* boot;             /* block: its configuration; downsampling: bt_out */
     const ckks_boot* boot_in;          /* downsampling: bt_in; block: ignored */
 } ckks_server_layer;

@@ -42,8 +42,9 @@ class ckks_server_params(ctypes.Structure):
 
 
 class ckks_server_layer(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("n_in", ctypes.c_int), ("n_out", ctypes.c_int),
-                ("convs", ctypes.POINTER(ctypes.c_void_p)), ("boot", ctypes.c_void_p), ("boot_in", ctypes.c_void_p)]
+    _fields_ = [("kind", ctypes.c_int), ("n_in", ctypes.c_int), ("n_out", ctypes.c_int), ("k", ctypes.c_int),
+                ("in_index", ctypes.POINTER(ctypes.c_int)), ("convs", ctypes.POINTER(ctypes.c_void_p)),
+                ("boot", ctypes.c_void_p), ("boot_in", ctypes.c_void_p)]
 
 
 class ckks_boot_params(ctypes.Structure):
@@ -1018,7 +1019,8 @@ def ckks_server_add_model(srv, convs, boots):
 
 def ckks_server_add_model_layers(srv, layers):
     """layers: dicts with kind (CKKS_LAYER_BLOCK / CKKS_LAYER_DOWNSAMPLE), convs (n_out lists of
-    n_in sets, output-major), boot and, for a downsampling layer, boot_in"""
+    k sets, output-major), boot, for a downsampling layer boot_in, and optionally inputs (n_out
+    lists of k input indices, with n_in the number of inputs; default: every output reads all)"""
     arr = (ckks_server_layer * len(layers))()
     keep = []
     for k, L in enumerate(layers):
@@ -1027,8 +1029,15 @@ def ckks_server_add_model_layers(srv, layers):
         cv = _ptrs(flat)
         keep.append(cv)
         arr[k].kind = L["kind"]
-        arr[k].n_in = len(rows[0])
+        arr[k].k = len(rows[0])
         arr[k].n_out = len(rows)
+        if L.get("inputs") is not None:
+            idx = (ctypes.c_int * (len(rows) * len(rows[0])))(*[i for row in L["inputs"] for i in row])
+            keep.append(idx)
+            arr[k].in_index = ctypes.cast(idx, ctypes.POINTER(ctypes.c_int))
+            arr[k].n_in = L["n_in"]
+        else:
+            arr[k].n_in = len(rows[0])
         arr[k].convs = ctypes.cast(cv, ctypes.POINTER(ctypes.c_void_p))
         arr[k].boot = L["boot"].ptr
         arr[k].boot_in = L["boot_in"].ptr if L.get("boot_in") is not None else None

@@ -29,14 +29,15 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// One layer of a model: n_out output ciphertexts from n_in inputs.  A block layer computes each
-// output as an Alg. 1 block over all inputs (ckks_block, or the Sec. 3.3.3 block matrix-vector
+// One layer of a model: n_out output ciphertexts from n_in inputs, output j from k of them
+// (in_index).  A block layer computes each output as an Alg. 1 block over its inputs (ckks_block, or the Sec. 3.3.3 block matrix-vector
 // product when n_in > 1); a downsampling layer (Alg. 2) computes each output from the EvalMod
 // outputs of the layer before it, which then stops after its bootstrap (no StoC1).
 struct Layer {
     int kind = CKKS_LAYER_BLOCK;
-    int n_in = 1, n_out = 1;
-    std::vector<const ckks_ptset*> convs;   // [n_out][n_in]
+    int n_in = 1, n_out = 1, k = 1;
+    std::vector<int> in_index;              // [n_out][k] (every output reads inputs 0..n_in-1 if empty)
+    std::vector<const ckks_ptset*> convs;   // [n_out][k]
     const ckks_boot* boot = nullptr;        // block: its configuration; downsampling: bt_out
     const ckks_boot* boot_in = nullptr;     // downsampling: bt_in (stride-2 tail of the inputs)
 };
@@ -140,11 +141,11 @@ void run_model(ckks_server* s, const Model& m, const u64* d_in, u64* d_out) {
             const int lev = L.convs[0]->level;
             for (ckks_ct& x : xs)
                 if (x.level != lev) x = ops::level_down(x, lev);
-            std::vector<const ckks_ct*> ins;
-            for (const ckks_ct& x : xs) ins.push_back(&x);
             for (int j = 0; j < L.n_out; ++j) {
-                const std::vector<const ckks_ptset*> cs(L.convs.begin() + (size_t)j * L.n_in,
-                                                        L.convs.begin() + (size_t)(j + 1) * L.n_in);
+                const std::vector<const ckks_ptset*> cs(L.convs.begin() + (size_t)j * L.k,
+                                                        L.convs.begin() + (size_t)(j + 1) * L.k);
+                std::vector<const ckks_ct*> ins;
+                for (int t = 0; t < L.k; ++t) ins.push_back(&xs[L.in_index.empty() ? t : L.in_index[j * L.k + t]]);
                 if (!to_ds) {
                     ys.push_back(L.n_in == 1 ? ops::block(keys, *L.boot, *cs[0], *ins[0])
                                              : ops::block_multi(keys, *L.boot, cs, ins));
@@ -158,14 +159,15 @@ void run_model(ckks_server* s, const Model& m, const u64* d_in, u64* d_out) {
                 }
             }
         } else {
-            std::vector<const ckks_ct*> rp, ip;
-            for (size_t i = 0; i < res.size(); ++i) {
-                rp.push_back(&res[i]);
-                ip.push_back(&ims[i]);
-            }
             for (int j = 0; j < L.n_out; ++j) {
-                const std::vector<const ckks_ptset*> cs(L.convs.begin() + (size_t)j * L.n_in,
-                                                        L.convs.begin() + (size_t)(j + 1) * L.n_in);
+                const std::vector<const ckks_ptset*> cs(L.convs.begin() + (size_t)j * L.k,
+                                                        L.convs.begin() + (size_t)(j + 1) * L.k);
+                std::vector<const ckks_ct*> rp, ip;
+                for (int t = 0; t < L.k; ++t) {
+                    const int i = L.in_index.empty() ? t : L.in_index[j * L.k + t];
+                    rp.push_back(&res[i]);
+                    ip.push_back(&ims[i]);
+                }
                 ys.push_back(ops::downsample_layer(keys, *L.boot_in, *L.boot, rp, ip, cs));
             }
         }
@@ -345,7 +347,12 @@ void add_model_impl(ckks_server* s, Model m, int* model_id) {
         CK_CHECK(L.n_in >= 1 && L.n_in <= 64 && L.n_out >= 1 && L.n_out <= 64, CKKS_EINVAL,
                  "a layer has 1 to 64 ciphertexts in and out");
         CK_CHECK(L.boot != nullptr, CKKS_EINVAL, "a layer needs its bootstrapping configuration");
-        CK_CHECK((int)L.convs.size() == L.n_in * L.n_out, CKKS_EINVAL, "a layer needs n_out x n_in conv sets");
+        CK_CHECK(L.k >= 1 && L.k <= L.n_in, CKKS_EINVAL, "a layer's outputs read 1 to n_in inputs each");
+        CK_CHECK(!L.in_index.empty() || L.k == L.n_in, CKKS_EINVAL, "without input indices every output reads all");
+        CK_CHECK(L.in_index.empty() || (int)L.in_index.size() == L.n_out * L.k, CKKS_EINVAL,
+                 "a layer needs n_out x k input indices");
+        for (int i : L.in_index) CK_CHECK(i >= 0 && i < L.n_in, CKKS_EINVAL, "an input index is out of range");
+        CK_CHECK((int)L.convs.size() == L.k * L.n_out, CKKS_EINVAL, "a layer needs n_out x k conv sets");
         for (const ckks_ptset* p : L.convs) CK_CHECK(p != nullptr, CKKS_EINVAL, "a conv set is NULL");
         if (k > 0) CK_CHECK(L.n_in == m.layers[k - 1].n_out, CKKS_EINVAL, "a layer's inputs are the previous outputs");
         if (L.kind == CKKS_LAYER_DOWNSAMPLE) {
@@ -445,6 +452,7 @@ int ckks_server_add_model(ckks_server* s, int n_blocks, const ckks_ptset* const*
             Layer L;
             L.convs.push_back(convs[b]);
             L.boot = boots[b];
+            L.k = 1;
             m.layers.push_back(std::move(L));
         }
         add_model_impl(s, std::move(m), model_id);
@@ -463,11 +471,14 @@ int ckks_server_add_model_layers(ckks_server* s, int n_layers, const ckks_server
             CK_CHECK(d.n_in >= 1 && d.n_in <= 64 && d.n_out >= 1 && d.n_out <= 64, CKKS_EINVAL,
                      "a layer has 1 to 64 ciphertexts in and out");
             REQ(d.convs);
+            CK_CHECK(d.k >= 1 && d.k <= d.n_in, CKKS_EINVAL, "a layer's outputs read 1 to n_in inputs each");
             Layer L;
             L.kind = d.kind;
             L.n_in = d.n_in;
             L.n_out = d.n_out;
-            L.convs.assign(d.convs, d.convs + (size_t)d.n_in * d.n_out);
+            L.k = d.k;
+            if (d.in_index) L.in_index.assign(d.in_index, d.in_index + (size_t)d.n_out * d.k);
+            L.convs.assign(d.convs, d.convs + (size_t)d.k * d.n_out);
             L.boot = d.boot;
             L.boot_in = d.boot_in;
             m.layers.push_back(std::move(L));

@@ -1,7 +1,7 @@
 """Serving models made of layers over several ciphertexts (config-2 chain at N = 2^10): a block
-layer with one input and two outputs followed by a Sec. 3.3.3 block over both, and a
-ResNet-stage pattern of a block whose EvalMod outputs feed an Alg. 2 downsampling layer and
-then a block of the new shape.  Each request's result equals the same layers called eagerly
+layer with one input and two outputs followed by a Sec. 3.3.3 block over both, a ResNet-stage
+pattern of a block whose EvalMod outputs feed an Alg. 2 downsampling layer and then a block of
+the new shape, and layers whose outputs read chosen inputs.  Each request's result equals the same layers called eagerly
 through the C ABI, limb for limb, alone and while the other model's requests run beside it."""
 import numpy as np
 import pytest
@@ -44,7 +44,17 @@ def env():
     m2_l1 = [[K.ckks_ptset_conv_fused(ctx, wts(C, C), C, C, 3, w, 1, s_pt)]]
     m2_l2 = [[K.ckks_ptset_conv_fused_s2(ctx, wts(4 * C, C), C, 4 * C, 3, w, 0, 1, s_pt)]]
     m2_l3 = [[K.ckks_ptset_conv_fused(ctx, wts(4 * C, 4 * C), 4 * C, 4 * C, 3, w // 2, 1, s_pt)]]
-    sets = [p for L in (m1_l1, m1_l2, m2_l1, m2_l2, m2_l3) for row in L for p in row]
+    # model M3: outputs reading chosen inputs (the two ciphertexts swapped, one input each)
+    m3_l1 = [[K.ckks_ptset_conv_fused(ctx, wts(C, C), C, C, 3, w, 1, s_pt)] for _ in range(2)]
+    m3_l2 = [[K.ckks_ptset_conv_fused(ctx, wts(C, C), C, C, 3, w, 1, s_pt)] for _ in range(2)]
+    m3_l3 = [[K.ckks_ptset_conv_fused(ctx, wts(C, C), C, C, 3, w, 1, s_pt) for _ in range(2)]]
+    # model M4: two blocks' EvalMod outputs -> one Alg. 2 output from each -> one block over both
+    m4_l1 = [[K.ckks_ptset_conv_fused(ctx, wts(C, C), C, C, 3, w, 1, s_pt)] for _ in range(2)]
+    m4_l2 = [[K.ckks_ptset_conv_fused_s2(ctx, wts(4 * C, C), C, 4 * C, 3, w, 0, 1, s_pt)] for _ in range(2)]
+    m4_l3 = [[K.ckks_ptset_conv_fused(ctx, wts(4 * C, 4 * C), 4 * C, 4 * C, 3, w // 2, 1, s_pt)
+              for _ in range(2)]]
+    sets = [p for L in (m1_l1, m1_l2, m2_l1, m2_l2, m2_l3, m3_l1, m3_l2, m3_l3, m4_l1, m4_l2, m4_l3)
+            for row in L for p in row]
     rots = set()
     for p in sets:
         rots |= set(K.ckks_ptset_rotations(p))
@@ -55,6 +65,12 @@ def env():
     m2 = [dict(kind=K.CKKS_LAYER_BLOCK, convs=m2_l1, boot=bt_in),
           dict(kind=K.CKKS_LAYER_DOWNSAMPLE, convs=m2_l2, boot=bt_out, boot_in=bt_in),
           dict(kind=K.CKKS_LAYER_BLOCK, convs=m2_l3, boot=bt_out)]
+    m3 = [dict(kind=K.CKKS_LAYER_BLOCK, convs=m3_l1, boot=b1),
+          dict(kind=K.CKKS_LAYER_BLOCK, convs=m3_l2, boot=b1, inputs=[[1], [0]], n_in=2),
+          dict(kind=K.CKKS_LAYER_BLOCK, convs=m3_l3, boot=b1)]
+    m4 = [dict(kind=K.CKKS_LAYER_BLOCK, convs=m4_l1, boot=bt_in),
+          dict(kind=K.CKKS_LAYER_DOWNSAMPLE, convs=m4_l2, boot=bt_out, boot_in=bt_in, inputs=[[0], [1]], n_in=2),
+          dict(kind=K.CKKS_LAYER_BLOCK, convs=m4_l3, boot=bt_out)]
 
     def make_input(seed):
         x = WL.image(seed, C, w0)
@@ -73,8 +89,23 @@ def env():
         y = K.ckks_level_down(ctx, y, 1)
         return K.ckks_ct_export_rns(ctx, K.ckks_block(ctx, keys, y, m2_l3[0][0], bt_out))
 
-    return dict(K=K, ctx=ctx, keys=keys, m1=m1, m2=m2, make_input=make_input, eager_m1=eager_m1,
-                eager_m2=eager_m2, delta=delta)
+    def eager_m3(limbs):
+        x = K.ckks_ct_import_rns(ctx, limbs, 1, delta[1])
+        ys = [K.ckks_level_down(ctx, K.ckks_block(ctx, keys, x, m3_l1[j][0], b1), 1) for j in range(2)]
+        zs = [K.ckks_level_down(ctx, K.ckks_block(ctx, keys, ys[1 - j], m3_l2[j][0], b1), 1) for j in range(2)]
+        return K.ckks_ct_export_rns(ctx, K.ckks_block_multi(ctx, keys, zs, m3_l3[0], b1))
+
+    def eager_m4(limbs):
+        x = K.ckks_ct_import_rns(ctx, limbs, 1, delta[1])
+        ds = []
+        for j in range(2):
+            re, im = K.ckks_bootstrap(ctx, keys, bt_in, K.ckks_conv2d_cins(ctx, keys, x, m4_l1[j][0]))
+            d = K.ckks_downsample_layer(ctx, keys, [re], [im], bt_in, m4_l2[j], bt_out)
+            ds.append(K.ckks_level_down(ctx, d, 1))
+        return K.ckks_ct_export_rns(ctx, K.ckks_block_multi(ctx, keys, ds, m4_l3[0], bt_out))
+
+    return dict(K=K, ctx=ctx, keys=keys, m1=m1, m2=m2, m3=m3, m4=m4, make_input=make_input, eager_m1=eager_m1,
+                eager_m2=eager_m2, eager_m3=eager_m3, eager_m4=eager_m4, delta=delta)
 
 
 def _server(env, slots):
@@ -126,5 +157,31 @@ def test_layer_model_checks(env):
         bad["boot_in"] = None
         with pytest.raises(K.CkksError):        # a downsampling layer needs bt_in
             K.ckks_server_add_model_layers(srv, [m2[0], bad, m2[2]])
+        bad = dict(env["m3"][1])
+        bad["inputs"] = [[2], [0]]
+        with pytest.raises(K.CkksError):        # an input index out of range
+            K.ckks_server_add_model_layers(srv, [env["m3"][0], bad, env["m3"][2]])
+    finally:
+        srv.close()
+
+
+def test_outputs_reading_chosen_inputs(env):
+    """block and downsampling layers whose outputs each read one chosen input ciphertext (the
+    ResNet-18 pooling and stage-entry pattern), against the same layers called eagerly"""
+    K, ctx = env["K"], env["ctx"]
+    n = ctx.n
+    ins = {s: env["make_input"](s) for s in (11, 12)}
+    want = {11: env["eager_m3"](ins[11]), 12: env["eager_m4"](ins[12])}
+    srv = K.ckks_server_create(ctx, env["keys"], 2, 0)
+    try:
+        a = K.ckks_server_add_model_layers(srv, env["m3"])
+        b = K.ckks_server_add_model_layers(srv, env["m4"])
+        K.ckks_server_start(srv)
+        rids = {11: K.ckks_server_submit(srv, a, ins[11], 1, env["delta"][1]),
+                12: K.ckks_server_submit(srv, b, ins[12], 1, env["delta"][1])}
+        for s, rid in rids.items():
+            assert K.ckks_server_wait(srv, rid, 120.0) == K.CKKS_REQ_DONE
+            out, _, _ = K.ckks_server_result(srv, rid, n)
+            assert (out == want[s]).all(), s
     finally:
         srv.close()
