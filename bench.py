@@ -1535,6 +1535,7 @@ def run_serve5(args):
         return srv, a, b, time.perf_counter() - t0
 
     def run(srv, a, b, rate, secs, closed=False, n_slots=1):
+        out_a, out_b = K.ckks_server_model_shape(srv, a)[1], K.ckks_server_model_shape(srv, b)[1]
         K.ckks_server_reset_stats(srv)
         ids = []
         t0 = time.perf_counter()
@@ -1543,9 +1544,9 @@ def run_serve5(args):
             now = time.perf_counter()
             if closed or now >= t_next:
                 if g.random() < 0.7:
-                    ids.append((K.ckks_server_submit(srv, a, x20, 1, delta[1]), 1))
+                    ids.append((K.ckks_server_submit(srv, a, x20, 1, delta[1]), out_a))
                 else:
-                    ids.append((K.ckks_server_submit(srv, b, x18, 1, delta[1]), 4))
+                    ids.append((K.ckks_server_submit(srv, b, x18, 1, delta[1]), out_b))
                 t_next += 0.0 if closed else float(g.exponential(1.0 / rate))
                 if closed and len(ids) >= 2 * n_slots:
                     K.ckks_server_wait(srv, ids[-2 * n_slots + 1][0], 600)

@@ -66,11 +66,9 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    u64* d_in = nullptr;          // coefficient-domain input limbs
-    u64* d_out = nullptr;         // coefficient-domain output limbs
-    u64* h_in = nullptr;          // pinned staging
-    u64* h_out = nullptr;
-    size_t in_words = 0, out_words = 0;
+    // by model: coefficient-domain input and output limbs and their pinned staging; each model's
+    // recorded graphs read and write its own buffers, which live as long as the server
+    std::vector<u64*> d_in, d_out, h_in, h_out;
     std::vector<cudaGraphExec_t> exec;   // by model
     std::vector<cudaGraph_t> graph;
     uint64_t req = 0;             // 0: free
@@ -214,7 +212,7 @@ bool step(ckks_server* s) {
             r.state = CKKS_REQ_CANCELLED;
             ++s->cancelled;
         } else {
-            r.out.assign(sl.h_out, sl.h_out + s->models[r.model].out_words(s->ctx->n));
+            r.out.assign(sl.h_out[r.model], sl.h_out[r.model] + s->models[r.model].out_words(s->ctx->n));
             r.state = CKKS_REQ_DONE;
             ++s->completed;
             s->lat_ms.push_back(std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count());
@@ -247,11 +245,13 @@ bool step(ckks_server* s) {
         if (!free_slot) break;
         s->queue.pop_front();
         Slot& sl = *free_slot;
-        std::copy(r.in.begin(), r.in.end(), sl.h_in);
-        cudaError_t e = cudaMemcpyAsync(sl.d_in, sl.h_in, r.in.size() * 8, cudaMemcpyHostToDevice, sl.stream);
+        std::copy(r.in.begin(), r.in.end(), sl.h_in[r.model]);
+        cudaError_t e = cudaMemcpyAsync(sl.d_in[r.model], sl.h_in[r.model], r.in.size() * 8, cudaMemcpyHostToDevice,
+                                        sl.stream);
         if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec[r.model], sl.stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sl.h_out, sl.d_out, m.out_words(s->ctx->n) * 8, cudaMemcpyDeviceToHost, sl.stream);
+            e = cudaMemcpyAsync(sl.h_out[r.model], sl.d_out[r.model], m.out_words(s->ctx->n) * 8,
+                                cudaMemcpyDeviceToHost, sl.stream);
         if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
         if (e != cudaSuccess) {
             r.state = CKKS_REQ_FAILED;
@@ -301,10 +301,10 @@ ckks_server::~ckks_server() {
             if (g) cudaGraphDestroy(g);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
-        if (sl.d_in) cudaFree(sl.d_in);
-        if (sl.d_out) cudaFree(sl.d_out);
-        if (sl.h_in) cudaFreeHost(sl.h_in);
-        if (sl.h_out) cudaFreeHost(sl.h_out);
+        for (u64* p : sl.d_in) cudaFree(p);
+        for (u64* p : sl.d_out) cudaFree(p);
+        for (u64* p : sl.h_in) cudaFreeHost(p);
+        for (u64* p : sl.h_out) cudaFreeHost(p);
     }
 }
 
@@ -368,65 +368,76 @@ void add_model_impl(ckks_server* s, Model m, int* model_id) {
     m.out_level = m.layers.back().boot->l_out;
     m.out_scale = c->delta[m.out_level];
     const size_t win = m.in_words(c->n), wout = m.out_words(c->n);
-    // slot buffers sized for every model
-    for (Slot& sl : s->slots) {
-        if (sl.in_words < win) {
-            if (sl.d_in) cudaFree(sl.d_in);
-            if (sl.h_in) cudaFreeHost(sl.h_in);
-            sl.d_in = nullptr;
-            sl.h_in = nullptr;
-            CUDA_CHECK(cudaMalloc((void**)&sl.d_in, win * 8));
-            CUDA_CHECK(cudaMallocHost((void**)&sl.h_in, win * 8));
-            CUDA_CHECK(cudaMemset(sl.d_in, 0, win * 8));
-            sl.in_words = win;
+    // this model's staging buffers and graphs in every slot, kept until the server is destroyed
+    // (the graphs refer to the buffers); they join the slots only once the whole model is
+    // recorded, so that a failure leaves the slots' per-model vectors aligned with the models
+    struct Staged {
+        u64 *d_in = nullptr, *d_out = nullptr, *h_in = nullptr, *h_out = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<Staged> st(s->slots.size());
+    auto release = [&] {
+        for (Staged& x : st) {
+            if (x.exec) cudaGraphExecDestroy(x.exec);
+            if (x.graph) cudaGraphDestroy(x.graph);
+            if (x.d_in) cudaFree(x.d_in);
+            if (x.d_out) cudaFree(x.d_out);
+            if (x.h_in) cudaFreeHost(x.h_in);
+            if (x.h_out) cudaFreeHost(x.h_out);
         }
-        if (sl.out_words < wout) {
-            if (sl.d_out) cudaFree(sl.d_out);
-            if (sl.h_out) cudaFreeHost(sl.h_out);
-            sl.d_out = nullptr;
-            sl.h_out = nullptr;
-            CUDA_CHECK(cudaMalloc((void**)&sl.d_out, wout * 8));
-            CUDA_CHECK(cudaMallocHost((void**)&sl.h_out, wout * 8));
-            sl.out_words = wout;
+    };
+    long long l0 = 0;
+    try {
+        for (Staged& x : st) {
+            CUDA_CHECK(cudaMalloc((void**)&x.d_in, win * 8));
+            CUDA_CHECK(cudaMalloc((void**)&x.d_out, wout * 8));
+            CUDA_CHECK(cudaMallocHost((void**)&x.h_in, win * 8));
+            CUDA_CHECK(cudaMallocHost((void**)&x.h_out, wout * 8));
+            CUDA_CHECK(cudaMemset(x.d_in, 0, win * 8));
         }
+        // one eager request: builds lazily created tables, checks keys and levels, and
+        // measures the temporaries' peak in the context's memory pool
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        cudaMemPool_t pool;
+        CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, s->device));
+        unsigned long long zero = 0, base = 0, high = 0;   // the pool attributes are 64-bit
+        CUDA_CHECK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &base));
+        CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+        l0 = c->launches;
+        run_model(s, m, st[0].d_in, st[0].d_out);
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        m.kernels = c->launches - l0;
+        CUDA_CHECK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+        m.footprint = high > base ? (long long)(high - base) : 0;
+        if (s->sp.hbm_budget > 0)
+            CK_CHECK(m.footprint <= s->sp.hbm_budget, CKKS_ENOMEM, "one request of this model exceeds the HBM budget");
+        for (Staged& x : st) {
+            CUDA_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                run_model(s, m, x.d_in, x.d_out);
+            } catch (...) {
+                cudaGraph_t tmp = nullptr;
+                cudaStreamEndCapture(c->stream, &tmp);
+                if (tmp) cudaGraphDestroy(tmp);
+                throw;
+            }
+            CUDA_CHECK(cudaStreamEndCapture(c->stream, &x.graph));
+            CUDA_CHECK(cudaGraphInstantiate(&x.exec, x.graph, 0));
+        }
+    } catch (...) {
+        release();
+        throw;
     }
-    // one eager request: builds lazily created tables, checks keys and levels, and
-    // measures the temporaries' peak in the context's memory pool
-    CUDA_CHECK(cudaStreamSynchronize(c->stream));
-    cudaMemPool_t pool;
-    CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, s->device));
-    unsigned long long zero = 0, base = 0, high = 0;   // the pool attributes are 64-bit
-    CUDA_CHECK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &base));
-    CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
-    const long long l0 = c->launches;
-    run_model(s, m, s->slots[0].d_in, s->slots[0].d_out);
-    CUDA_CHECK(cudaStreamSynchronize(c->stream));
-    m.kernels = c->launches - l0;
-    CUDA_CHECK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
-    m.footprint = high > base ? (long long)(high - base) : 0;
-    if (s->sp.hbm_budget > 0)
-        CK_CHECK(m.footprint <= s->sp.hbm_budget, CKKS_ENOMEM, "one request of this model exceeds the HBM budget");
     const int id = (int)s->models.size();
-    for (Slot& sl : s->slots) {
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t e = nullptr;
-        CUDA_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        try {
-            run_model(s, m, sl.d_in, sl.d_out);
-        } catch (...) {
-            cudaGraph_t tmp = nullptr;
-            cudaStreamEndCapture(c->stream, &tmp);
-            if (tmp) cudaGraphDestroy(tmp);
-            throw;
-        }
-        CUDA_CHECK(cudaStreamEndCapture(c->stream, &g));
-        const cudaError_t ie = cudaGraphInstantiate(&e, g, 0);
-        if (ie != cudaSuccess) {
-            cudaGraphDestroy(g);
-            CUDA_CHECK(ie);
-        }
-        sl.graph.push_back(g);
-        sl.exec.push_back(e);
+    for (size_t k = 0; k < s->slots.size(); ++k) {
+        Slot& sl = s->slots[k];
+        sl.d_in.push_back(st[k].d_in);
+        sl.d_out.push_back(st[k].d_out);
+        sl.h_in.push_back(st[k].h_in);
+        sl.h_out.push_back(st[k].h_out);
+        sl.graph.push_back(st[k].graph);
+        sl.exec.push_back(st[k].exec);
     }
     c->launches = l0 + m.kernels;
     s->models.push_back(std::move(m));
