@@ -331,6 +331,20 @@ void autotune_ntt(ckks_ctx* c, int reps);
 // factor N^{-1}, e.g. N^{-1} qhat^{-1} for a base conversion that reads the output prescaled)
 void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride = 0,
                  const u64* osc = nullptr);
+// Inverse transform read out of place: row k of the input at src + (k / lpp) * src_pstride +
+// (k % lpp) N, row k of the output at data + (k / lpp) * pstride + (k % lpp) N (pstride 0: lpp N);
+// src is left unchanged; osc as in ntt_inverse.  k_id >= 0: one contiguous row per polynomial
+// (lpp = 1, pstride N), all with the prime k_id, and the result is multiplied by kres (a residue
+// mod that prime).  At N = 2^16 the first pass reads src and the last applies the factor; the
+// cluster variant and smaller rings copy (and scale) first.
+void ntt_inverse_from(const ckks_ctx* c, const u64* src, size_t src_pstride, u64* data, int nlimbs, const int* ids,
+                      int lpp, size_t pstride, const u64* osc, u64 kres = 1, int k_id = -1);
+// Forward transform of a centred lift: row k of o (lpp rows per polynomial, contiguous) is the
+// NTT of the coefficient-domain source row k / lpp (at src + (k / lpp) * src_pstride, residues
+// mod the prime src_id) lifted to the prime ids[k % lpp]; lift_centred then ntt_forward in one
+// pass over the data at N = 2^16 (the lift happens as the first pass loads its input).
+void ntt_forward_lift(const ckks_ctx* c, const u64* src, int src_id, size_t src_pstride, u64* o, int nlimbs,
+                      const int* ids, int lpp);
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void sub(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void neg(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, const int* ids, int lpp);

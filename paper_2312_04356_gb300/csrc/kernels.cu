@@ -294,13 +294,40 @@ __device__ __forceinline__ void inv_round(u64 (&x)[16], int t, int hi, int s0, c
     }
 }
 
+// Input of the first pass of a transform when it is not the data array itself (SRC kernels).
+// Forward: row k reads the coefficient-domain source row k / lpp at src + (k / lpp) *
+// src_pstride, residues mod qs, and transforms their centred lift to the row's prime (the
+// rescale's and ModRaise's lift, done while loading).  Inverse: row k reads src + (k / lpp) *
+// src_pstride + (k % lpp) N (an out-of-place transform; the input is left as it is).  In both
+// cases the result goes to the data array.  ow != 0 replaces the inverse's final factor N^{-1}
+// by the Shoup pair (ow, owp), e.g. k N^{-1} to multiply the result by the integer k.
+struct NttSrc {
+    const u64* src;
+    size_t src_pstride;
+    u64 qs;
+    u64 ow, owp;
+};
+
+// Centred lift of v (a residue mod qs) to a value congruent mod q that the forward transform's
+// first stage accepts: below 6q suffices (the uncorrected first stage takes it below 8q, the
+// corrected second one back below 6q, as between the two passes), and the transform ends in
+// [0, q) whatever representative it starts from, so the residues equal those of the exact
+// lift.  For qs < 4q the lift needs no reduction: v for v <= qs/2 (below 2q), else
+// v - qs + 2q (in (0, 2q)); otherwise the exact centred lift.
+__device__ __forceinline__ u64 lift_lazy(u64 v, u64 qs, bool small, const DevMod& t) {
+    if (small) return v > (qs >> 1) ? v + 2 * t.q - qs : v;
+    return centred_to(v, qs, t);
+}
+
 // COL: sub-problems are columns (s0 = 0, T1 = 256, element j = k*256 + lo), threads with
 //      consecutive tid take consecutive columns.  ROW: sub-problems are contiguous rows
 //      (s0 = 8, T1 = 1, j = hi*256 + k), consecutive tid take consecutive k.
-template <bool COL, bool INV, int SUBS, int MINB>
+template <bool COL, bool INV, int SUBS, int MINB, bool SRC = false>
 __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ data, const DevPrime* __restrict__ primes,
                                                     const int* __restrict__ ids, int lpp, size_t pstride,
-                                                    const int* __restrict__ loff, const u64* __restrict__ osc) {
+                                                    const int* __restrict__ loff, const u64* __restrict__ osc,
+                                                    NttSrc io) {
+    static_assert(!SRC || COL != INV, "only the first pass of a transform reads a separate source");
     griddep_entry();
     __shared__ u64 sm[SUBS * F_STRIDE];
     const int limb = blockIdx.y;
@@ -318,8 +345,15 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
     auto gidx = [&](int k) -> size_t { return COL ? ((size_t)k << 8) + sub : ((size_t)sub << 8) + k; };
 
     if (!INV) {
+        if (SRC) {
+            const u64* sr = io.src + (size_t)(limb / lpp) * io.src_pstride;
+            const bool small = io.qs < 4 * q;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) x[i] = a[gidx(t + 16 * i)];
+            for (int i = 0; i < 16; ++i) x[i] = lift_lazy(sr[gidx(t + 16 * i)], io.qs, small, P->m);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = a[gidx(t + 16 * i)];
+        }
         fwd_round<false>(x, t, hi, s0, P, q, q2);
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[f_slot(sp, t + 16 * i)] = x[i];
@@ -351,8 +385,9 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
 #pragma unroll
             for (int i = 0; i < 16; ++i) x[i] = a[gidx(16 * t + i)];
         } else {
+            const u64* sr = SRC ? io.src + (size_t)(limb / lpp) * io.src_pstride + ((size_t)r << 16) : a;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) sm[f_slot(sp, t + 16 * i)] = a[gidx(t + 16 * i)];
+            for (int i = 0; i < 16; ++i) sm[f_slot(sp, t + 16 * i)] = sr[gidx(t + 16 * i)];
             __syncthreads();
 #pragma unroll
             for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(sp, 16 * t + i)];
@@ -366,7 +401,8 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
         for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(sp, t + 16 * i)];
         inv_round<false>(x, t, hi, s0, P, q, q2);
         if (COL) {
-            const u64 ni = osc ? osc[2 * r] : P->n_inv, nip = osc ? osc[2 * r + 1] : P->n_inv_p;
+            const u64 ni = io.ow ? io.ow : osc ? osc[2 * r] : P->n_inv;
+            const u64 nip = io.ow ? io.owp : osc ? osc[2 * r + 1] : P->n_inv_p;
 #pragma unroll
             for (int i = 0; i < 16; ++i) a[gidx(t + 16 * i)] = mul_shoup(x[i], ni, nip, q);
         } else {
@@ -384,10 +420,12 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
 // lazy bounds are those of k_ntt16, so both kernels return the same residues.
 __device__ __forceinline__ int ins0(int t, int p) { return ((t >> p) << (p + 1)) | (t & ((1 << p) - 1)); }
 
-template <bool COL, bool INV>
+template <bool COL, bool INV, bool SRC = false>
 __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const DevPrime* __restrict__ primes,
                                                 const int* __restrict__ ids, int lpp, size_t pstride,
-                                                const int* __restrict__ loff, const u64* __restrict__ osc) {
+                                                const int* __restrict__ loff, const u64* __restrict__ osc,
+                                                NttSrc io) {
+    static_assert(!SRC || COL != INV, "only the first pass of a transform reads a separate source");
     griddep_entry();
     __shared__ u64 sm[4 * F_STRIDE];
     const int limb = blockIdx.y;
@@ -411,8 +449,15 @@ __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const De
             k0 = ins0(ins0(t, 6 - u), 7 - u);
             const int ks[4] = {k0, k0 + e, k0 + d, k0 + d + e};
             if (rr == 0) {
+                if (SRC) {
+                    const u64* sr = io.src + (size_t)(limb / lpp) * io.src_pstride;
+                    const bool small = io.qs < 4 * q;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) x[i] = a[gidx(ks[i])];
+                    for (int i = 0; i < 4; ++i) x[i] = lift_lazy(sr[gidx(ks[i])], io.qs, small, P->m);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) x[i] = a[gidx(ks[i])];
+                }
             } else {
                 __syncthreads();
 #pragma unroll
@@ -457,8 +502,9 @@ __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const De
             k0 = ins0(ins0(t, 6 - u), 7 - u);
             const int ks[4] = {k0, k0 + e, k0 + d, k0 + d + e};
             if (rr == 3) {
+                const u64* sr = SRC ? io.src + (size_t)(limb / lpp) * io.src_pstride + ((size_t)r << 16) : a;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) x[i] = a[gidx(ks[i])];
+                for (int i = 0; i < 4; ++i) x[i] = sr[gidx(ks[i])];
             } else {
                 __syncthreads();
 #pragma unroll
@@ -483,7 +529,8 @@ __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const De
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sm[f_slot(sp, ks[i])] = x[i];
             } else if (COL) {
-                const u64 ni = osc ? osc[2 * r] : P->n_inv, nip = osc ? osc[2 * r + 1] : P->n_inv_p;
+                const u64 ni = io.ow ? io.ow : osc ? osc[2 * r] : P->n_inv;
+                const u64 nip = io.ow ? io.owp : osc ? osc[2 * r + 1] : P->n_inv_p;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[gidx(ks[i])] = mul_shoup(x[i], ni, nip, q);
             } else {
@@ -610,29 +657,29 @@ enum NttVariant {
     NTT_V16_R80 = 0, NTT_V16_R64 = 1, NTT_V4_R80 = 2, NTT_V4_R64 = 3, NTT_X4 = 4, NTT_CL = 5, NTT_NVARIANTS = 6
 };
 
-template <bool COL, bool INV>
+template <bool COL, bool INV, bool SRC = false>
 void launch_ntt16_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp,
-                          size_t pstride, const int* loff, const u64* osc) {
+                          size_t pstride, const int* loff, const u64* osc, const NttSrc& io) {
     switch (v) {
         case NTT_V16_R80:
-            klaunch(cx, k_ntt16<COL, INV, 16, 3>, dim3(256 / 16, nlimbs), 256, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
+            klaunch(cx, k_ntt16<COL, INV, 16, 3, SRC>, dim3(256 / 16, nlimbs), 256, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc, io);
             break;
         case NTT_V16_R64:
-            klaunch(cx, k_ntt16<COL, INV, 16, 4>, dim3(256 / 16, nlimbs), 256, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
+            klaunch(cx, k_ntt16<COL, INV, 16, 4, SRC>, dim3(256 / 16, nlimbs), 256, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc, io);
             break;
         case NTT_V4_R80:
-            klaunch(cx, k_ntt16<COL, INV, 4, 8>, dim3(256 / 4, nlimbs), 64, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
+            klaunch(cx, k_ntt16<COL, INV, 4, 8, SRC>, dim3(256 / 4, nlimbs), 64, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc, io);
             break;
         case NTT_V4_R64:
-            klaunch(cx, k_ntt16<COL, INV, 4, 12>, dim3(256 / 4, nlimbs), 64, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
+            klaunch(cx, k_ntt16<COL, INV, 4, 12, SRC>, dim3(256 / 4, nlimbs), 64, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc, io);
             break;
         default:
-            klaunch(cx, k_ntt16s<COL, INV>, dim3(256 / 4, nlimbs), 256, 0,
-                    data, cx->d_primes, ids, lpp, pstride, loff, osc);
+            klaunch(cx, k_ntt16s<COL, INV, SRC>, dim3(256 / 4, nlimbs), 256, 0,
+                    data, cx->d_primes, ids, lpp, pstride, loff, osc, io);
             break;
     }
 }
@@ -655,32 +702,43 @@ void launch_ntt_cl(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, in
 // One whole N = 2^16 transform with variant v: the cluster kernel, or the two passes (forward:
 // COL then ROW; inverse: ROW then COL).  Algorithmic bytes: one read and one write of the
 // limbs per transform, split evenly over the two passes.
+// (io: a separate source of the first pass and an output factor, as NttSrc describes; the
+// cluster variant takes neither, its callers read in place)
 template <bool INV>
 void launch_ntt_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
-                        const int* loff, const u64* osc = nullptr) {
+                        const int* loff, const u64* osc = nullptr, const NttSrc& io = NttSrc{}) {
     const char* nm = INV ? "ntt_inv" : "ntt_fwd";
     const double bytes = 2.0 * nlimbs * cx->n * 8.0;
     if (v == NTT_CL) {
+        CK_CHECK(!io.src && !io.ow, CKKS_EINVAL, "the cluster NTT reads its input in place");
         KTimer kt_(cx, nm, bytes);
         launch_ntt_cl<INV>(cx, data, nlimbs, ids, lpp, pstride, loff, osc);
         return;
     }
     {
         KTimer kt_(cx, nm, bytes / 2);
-        launch_ntt16_variant<!INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc);
+        if (io.src)
+            launch_ntt16_variant<!INV, INV, true>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc, io);
+        else
+            launch_ntt16_variant<!INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc, io);
     }
     {
         KTimer kt_(cx, nm, bytes / 2);
-        launch_ntt16_variant<INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc);
+        launch_ntt16_variant<INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc, io);
     }
+}
+
+// the variant that transforms of nlimbs limbs use: the tuned one of their size class, else
+// 16 sub-problems per CTA from 16 limbs on and 4 below
+inline int ntt_pick(const ckks_ctx* cx, int nlimbs) {
+    const int v = cx->ntt_choice[ntt_class(nlimbs)];
+    return v >= 0 ? v : nlimbs >= 16 ? NTT_V16_R80 : NTT_V4_R80;
 }
 
 template <bool INV>
 void launch_ntt_transform(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
-                          const int* loff = nullptr, const u64* osc = nullptr) {
-    int v = cx->ntt_choice[ntt_class(nlimbs)];
-    if (v < 0) v = nlimbs >= 16 ? NTT_V16_R80 : NTT_V4_R80;
-    launch_ntt_variant<INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc);
+                          const int* loff = nullptr, const u64* osc = nullptr, const NttSrc& io = NttSrc{}) {
+    launch_ntt_variant<INV>(cx, ntt_pick(cx, nlimbs), data, nlimbs, ids, lpp, pstride, loff, osc, io);
 }
 
 struct PassPlan {
@@ -1735,6 +1793,51 @@ void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
         launch_pass<true>(c, data, nlimbs, ids, lpp, pstride, ps[i], ps[i].s0 == 0 ? 1 : 0,
                           ps[i].s0 == 0 ? osc : nullptr);
     LAUNCH_CHECK();
+}
+
+void ntt_inverse_from(const ckks_ctx* c, const u64* src, size_t src_pstride, u64* data, int nlimbs, const int* ids,
+                      int lpp, size_t pstride, const u64* osc, u64 kres, int k_id) {
+    if (nlimbs <= 0) return;
+    if (pstride == 0) pstride = (size_t)lpp * c->n;
+    const bool scaled = k_id >= 0 && kres != 1;
+    CK_CHECK(nlimbs % lpp == 0, CKKS_EINVAL, "whole polynomials only");
+    CK_CHECK(!scaled || (lpp == 1 && osc == nullptr && pstride == c->n), CKKS_EINVAL,
+             "an integer factor needs one contiguous row per polynomial and no output scale table");
+    if (c->logn == 16 && ntt_pick(c, nlimbs) != NTT_CL) {
+        NttSrc io{src, src_pstride, 0, 0, 0};
+        if (scaled) {
+            const u64 q = c->mod_of[k_id];
+            io.ow = hostmath::mulmod(kres, hostmath::invmod((u64)c->n % q, q), q);
+            io.owp = hostmath::shoup(io.ow, q);
+        }
+        launch_ntt_transform<true>(c, data, nlimbs, ids, lpp, pstride, nullptr, osc, io);
+        LAUNCH_CHECK();
+        return;
+    }
+    // the cluster variant and the small rings: copy (and scale), then transform in place
+    if (scaled) {
+        ScalarVec sv;
+        sv.v[0] = kres;
+        sv.vp[0] = hostmath::shoup(kres, c->mod_of[k_id]);
+        mul_scalar_v(c, src, sv, data, nlimbs, ids, 1, src_pstride);
+    } else {
+        CUDA_CHECK(cudaMemcpy2DAsync(data, pstride * 8, src, src_pstride * 8, (size_t)lpp * c->n * 8, nlimbs / lpp,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+    }
+    ntt_inverse(c, data, nlimbs, ids, lpp, pstride, osc);
+}
+
+void ntt_forward_lift(const ckks_ctx* c, const u64* src, int src_id, size_t src_pstride, u64* o, int nlimbs,
+                      const int* ids, int lpp) {
+    if (nlimbs <= 0) return;
+    if (c->logn == 16 && ntt_pick(c, nlimbs) != NTT_CL) {
+        const NttSrc io{src, src_pstride, c->mod_of[src_id], 0, 0};
+        launch_ntt_transform<false>(c, o, nlimbs, ids, lpp, (size_t)lpp * c->n, nullptr, nullptr, io);
+        LAUNCH_CHECK();
+        return;
+    }
+    lift_centred(c, src, src_id, o, nlimbs, ids, lpp, src_pstride);
+    ntt_forward(c, o, nlimbs, ids, lpp);
 }
 
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {

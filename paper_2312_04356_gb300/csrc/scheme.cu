@@ -484,17 +484,15 @@ ckks_ct rescale_mul(const ckks_ct& a, long long k) {
     CK_CHECK(l <= ScalarVec::MAX, CKKS_EINVAL, "too many limbs for a by-value scalar vector");
     c->ops["rescale"]++;
     const size_t n = c->n;
-    ScalarVec top;
-    top.v[0] = from_signed(k, c->q[l]);
-    top.vp[0] = shoup(top.v[0], c->q[l]);
-    // the last limb of every polynomial (c0, c1 of each ciphertext: 2 nb rows (l + 1) N apart)
+    // k times the last limb of every polynomial (c0, c1 of each ciphertext: 2 nb rows (l + 1) N
+    // apart), to the coefficient domain; then its centred lift to the other l primes, back to
+    // the NTT domain
     const int np_ = 2 * a.nb;
     DevBuf last((size_t)np_ * n, c->stream);
-    kern::mul_scalar_v(c, a.c0() + (size_t)l * n, top, last.ptr, np_, c->d_iota + l, 1, (size_t)(l + 1) * n);
-    kern::ntt_inverse(c, last.ptr, np_, c->d_iota + l, 1);
+    kern::ntt_inverse_from(c, a.c0() + (size_t)l * n, (size_t)(l + 1) * n, last.ptr, np_, c->d_iota + l, 1, n,
+                           nullptr, from_signed(k, c->q[l]), l);
     DevBuf lift((size_t)np_ * l * n, c->stream);
-    kern::lift_centred(c, last.ptr, l, lift.ptr, np_ * l, c->d_iota, l, n);     // every polynomial
-    kern::ntt_forward(c, lift.ptr, np_ * l, c->d_iota, l);
+    kern::ntt_forward_lift(c, last.ptr, l, n, lift.ptr, np_ * l, c->d_iota, l);     // every polynomial
     ckks_ct o = new_ct(c, l - 1, a.scale / (double)c->q[l], a.nb);
     ScalarVec s1;
     for (int i = 0; i < l; ++i) {
@@ -543,11 +541,9 @@ ckks_ct mod_raise(const ckks_ct& a) {
     const size_t n = c->n;
     const int np_ = 2 * a.nb;                        // a level-0 batch is np_ consecutive limbs
     DevBuf coef((size_t)np_ * n, c->stream);
-    CUDA_CHECK(cudaMemcpyAsync(coef.ptr, a.c0(), np_ * n * 8, cudaMemcpyDeviceToDevice, c->stream));
-    kern::ntt_inverse(c, coef.ptr, np_, c->d_iota, 1);
+    kern::ntt_inverse_from(c, a.c0(), n, coef.ptr, np_, c->d_iota, 1, n, nullptr);
     ckks_ct o = new_ct(c, c->L, a.scale, a.nb);
-    kern::lift_centred(c, coef.ptr, 0, o.buf.ptr, np_ * c->nq, c->d_iota, c->nq, n);   // row k from source k / nq
-    kern::ntt_forward(c, o.buf.ptr, np_ * c->nq, c->d_iota, c->nq);
+    kern::ntt_forward_lift(c, coef.ptr, 0, n, o.buf.ptr, np_ * c->nq, c->d_iota, c->nq);   // row k from source k / nq
     return o;
 }
 
@@ -563,9 +559,8 @@ DevBuf mod_up(ckks_ctx* c, const u64* x, int level, int* ndig_out, int nb, size_
     const size_t dstr = (size_t)ndig * next * n;     // words per ciphertext of D
     if (xstride == 0) xstride = (size_t)nl * n;
     DevBuf coef((size_t)nb * nl * n, c->stream);
-    CUDA_CHECK(cudaMemcpy2DAsync(coef.ptr, nl * n * 8, x, xstride * 8, nl * n * 8, nb, cudaMemcpyDeviceToDevice,
-                                 c->stream));
-    kern::ntt_inverse(c, coef.ptr, nb * nl, c->d_iota, nl, 0, c->d_modup_iscale[level]);   // prescaled
+    kern::ntt_inverse_from(c, x, xstride, coef.ptr, nb * nl, c->d_iota, nl, (size_t)nl * n,
+                           c->d_modup_iscale[level]);   // prescaled
     DevBuf D((size_t)nb * dstr, c->stream);
     const int* ext = c->d_ext_ids[level];
     kern::ConvJobs jobs;

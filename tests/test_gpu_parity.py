@@ -85,7 +85,10 @@ def test_cluster_ntt_in_key_switching():
     the limb-list transforms of ModUp, ModDown and the key switch): hoisted rotations at
     N = 2^16 stay bit-exact against the oracle.  Then every two-pass variant forced in turn,
     and the default: hoisted rotations, HMult + relinearisation (ModDown) and rescale
-    bit-exact at N = 2^16"""
+    bit-exact at N = 2^16.  Every variant, the cluster one included: the level drop by
+    rescales with integer factors (the inverse transform that reads the top limbs in place
+    and applies the factor with N^-1, the forward transform that lifts while it loads) and
+    ModRaise"""
     K, o, ctx, keys = make_pair("cfg2", 7, rotations=[1, 5], conj=False)
     P = o.P
     K.ckks_ctx_set_ntt_variant(ctx, 5)
@@ -114,6 +117,14 @@ def test_cluster_ntt_in_key_switching():
             assert_ct_equal(K, ctx, gr, w, "rotation %d, variant %d" % (r, v))
         assert_ct_equal(K, ctx, K.ckks_rescale(ctx, g), want_rs, "rescale, variant %d" % v)
         assert_ct_equal(K, ctx, K.ckks_mul_relin(ctx, keys, g, g), want_hm, "HMult, variant %d" % v)
+    want_ld = o.level_down(ct, lev - 2)
+    x0 = o.mod_drop(ct, 0)
+    g0 = import_ct(K, ctx, x0)
+    want_mr = o.mod_raise(x0)
+    for v in (5, 0, 1, 2, 3, 4, -1):
+        K.ckks_ctx_set_ntt_variant(ctx, v)
+        assert_ct_equal(K, ctx, K.ckks_level_down(ctx, g, lev - 2), want_ld, "level drop, variant %d" % v)
+        assert_ct_equal(K, ctx, K.ckks_mod_raise(ctx, g0), want_mr, "ModRaise, variant %d" % v)
     K.ckks_ctx_set_ntt_variant(ctx, -1)
 
 
