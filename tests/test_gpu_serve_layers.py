@@ -77,7 +77,7 @@ def env():
         ct = K.ckks_encrypt(ctx, keys, K.ckks_encode_image(ctx, x, w, 1, delta[1]), seed)
         return K.ckks_ct_export_rns(ctx, ct)
 
-    def eager_m1(limbs):
+    def eager_m1(limbs, keys=keys):
         x = K.ckks_ct_import_rns(ctx, limbs, 1, delta[1])
         ys = [K.ckks_level_down(ctx, K.ckks_block(ctx, keys, x, m1_l1[j][0], b1), 1) for j in range(2)]
         return K.ckks_ct_export_rns(ctx, K.ckks_block_multi(ctx, keys, ys, m1_l2[0], b1))
@@ -104,8 +104,27 @@ def env():
             ds.append(K.ckks_level_down(ctx, d, 1))
         return K.ckks_ct_export_rns(ctx, K.ckks_block_multi(ctx, keys, ds, m4_l3[0], bt_out))
 
-    return dict(K=K, ctx=ctx, keys=keys, m1=m1, m2=m2, m3=m3, m4=m4, make_input=make_input, eager_m1=eager_m1,
-                eager_m2=eager_m2, eager_m3=eager_m3, eager_m4=eager_m4, delta=delta)
+    # model M5: the second layer of M1 alone (two input ciphertexts: larger requests than M1's)
+    m5 = [dict(kind=K.CKKS_LAYER_BLOCK, convs=m1_l2, boot=b1)]
+
+    def eager_m5(limbs2, keys=keys):
+        xs = [K.ckks_ct_import_rns(ctx, limbs2[t], 1, delta[1]) for t in range(2)]
+        return K.ckks_ct_export_rns(ctx, K.ckks_block_multi(ctx, keys, xs, m1_l2[0], b1))
+
+    def model_rotations(layers):
+        r = set()
+        for L in layers:
+            for row in L["convs"]:
+                for p in row:
+                    r |= set(K.ckks_ptset_rotations(p))
+            for b in (L["boot"], L.get("boot_in")):
+                if b is not None:
+                    r |= set(K.ckks_boot_rotations(b))
+        return r
+
+    return dict(K=K, ctx=ctx, keys=keys, rots=rots, m1=m1, m2=m2, m3=m3, m4=m4, m5=m5, make_input=make_input,
+                eager_m1=eager_m1, eager_m2=eager_m2, eager_m3=eager_m3, eager_m4=eager_m4, eager_m5=eager_m5,
+                model_rotations=model_rotations, delta=delta)
 
 
 def _server(env, slots):
@@ -183,5 +202,45 @@ def test_outputs_reading_chosen_inputs(env):
             assert K.ckks_server_wait(srv, rid, 120.0) == K.CKKS_REQ_DONE
             out, _, _ = K.ckks_server_result(srv, rid, n)
             assert (out == want[s]).all(), s
+    finally:
+        srv.close()
+
+
+def test_failed_model_between_models_of_different_request_sizes(env):
+    """one server, three models added in turn: M1 (one input ciphertext); M2, refused while it
+    is recorded because the server's keys lack one of its rotations (CKKS_ENOKEY from its eager
+    run, after its staging buffers were made); M5 (two input ciphertexts, larger requests than
+    M1's).  Each model keeps its own staging buffers, so M1's recorded graphs stay valid after
+    the larger model is added, and the refused model leaves no trace: requests of M1 and M5,
+    alone and mixed, equal the same layers called eagerly with the same keys"""
+    K, ctx = env["K"], env["ctx"]
+    n = ctx.n
+    keep = env["model_rotations"](env["m1"]) | env["model_rotations"](env["m5"])
+    only_m2 = sorted(env["model_rotations"](env["m2"]) - keep)
+    if not only_m2:
+        pytest.skip("every rotation of M2 is also one of M1's or M5's")
+    short = K.ckks_keygen(ctx, sorted(set(env["rots"]) - {only_m2[0]}), True)
+    x1 = env["make_input"](21)
+    x5 = np.stack([env["make_input"](22), env["make_input"](23)])
+    want1 = env["eager_m1"](x1, short)
+    want5 = env["eager_m5"](x5, short)
+    srv = K.ckks_server_create(ctx, short, 2, 0)
+    try:
+        a = K.ckks_server_add_model_layers(srv, env["m1"])
+        with pytest.raises(K.CkksError) as ei:
+            K.ckks_server_add_model_layers(srv, env["m2"])
+        assert ei.value.code == K.CKKS_ENOKEY
+        b = K.ckks_server_add_model_layers(srv, env["m5"])
+        assert b == a + 1
+        assert K.ckks_server_model_shape(srv, a) == (1, 1) and K.ckks_server_model_shape(srv, b) == (2, 1)
+        K.ckks_server_start(srv)
+        for _ in range(2):
+            rids = [(K.ckks_server_submit(srv, a, x1, 1, env["delta"][1]), want1),
+                    (K.ckks_server_submit(srv, b, x5, 1, env["delta"][1]), want5),
+                    (K.ckks_server_submit(srv, a, x1, 1, env["delta"][1]), want1)]
+            for rid, want in rids:
+                assert K.ckks_server_wait(srv, rid, 120.0) == K.CKKS_REQ_DONE
+                out, _, _ = K.ckks_server_result(srv, rid, n)
+                assert (out == want).all()
     finally:
         srv.close()
