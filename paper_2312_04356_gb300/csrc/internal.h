@@ -339,12 +339,6 @@ void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
 // cluster variant and smaller rings copy (and scale) first.
 void ntt_inverse_from(const ckks_ctx* c, const u64* src, size_t src_pstride, u64* data, int nlimbs, const int* ids,
                       int lpp, size_t pstride, const u64* osc, u64 kres = 1, int k_id = -1);
-// Forward transform of a centred lift: row k of o (lpp rows per polynomial, contiguous) is the
-// NTT of the coefficient-domain source row k / lpp (at src + (k / lpp) * src_pstride, residues
-// mod the prime src_id) lifted to the prime ids[k % lpp]; lift_centred then ntt_forward in one
-// pass over the data at N = 2^16 (the lift happens as the first pass loads its input).
-void ntt_forward_lift(const ckks_ctx* c, const u64* src, int src_id, size_t src_pstride, u64* o, int nlimbs,
-                      const int* ids, int lpp);
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void sub(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);
 void neg(const ckks_ctx* c, const u64* a, u64* o, int nlimbs, const int* ids, int lpp);

@@ -294,30 +294,16 @@ __device__ __forceinline__ void inv_round(u64 (&x)[16], int t, int hi, int s0, c
     }
 }
 
-// Input of the first pass of a transform when it is not the data array itself (SRC kernels).
-// Forward: row k reads the coefficient-domain source row k / lpp at src + (k / lpp) *
-// src_pstride, residues mod qs, and transforms their centred lift to the row's prime (the
-// rescale's and ModRaise's lift, done while loading).  Inverse: row k reads src + (k / lpp) *
-// src_pstride + (k % lpp) N (an out-of-place transform; the input is left as it is).  In both
-// cases the result goes to the data array.  ow != 0 replaces the inverse's final factor N^{-1}
-// by the Shoup pair (ow, owp), e.g. k N^{-1} to multiply the result by the integer k.
+// Input of the inverse transform's first pass when it is not the data array itself (SRC
+// kernels): row k reads src + (k / lpp) * src_pstride + (k % lpp) N and the result goes to the
+// data array, so the input is left as it is (no copy before an out-of-place transform).
+// ow != 0 replaces the final factor N^{-1} by the Shoup pair (ow, owp), e.g. k N^{-1} to
+// multiply the result by the integer k.
 struct NttSrc {
     const u64* src;
     size_t src_pstride;
-    u64 qs;
     u64 ow, owp;
 };
-
-// Centred lift of v (a residue mod qs) to a value congruent mod q that the forward transform's
-// first stage accepts: below 6q suffices (the uncorrected first stage takes it below 8q, the
-// corrected second one back below 6q, as between the two passes), and the transform ends in
-// [0, q) whatever representative it starts from, so the residues equal those of the exact
-// lift.  For qs < 4q the lift needs no reduction: v for v <= qs/2 (below 2q), else
-// v - qs + 2q (in (0, 2q)); otherwise the exact centred lift.
-__device__ __forceinline__ u64 lift_lazy(u64 v, u64 qs, bool small, const DevMod& t) {
-    if (small) return v > (qs >> 1) ? v + 2 * t.q - qs : v;
-    return centred_to(v, qs, t);
-}
 
 // COL: sub-problems are columns (s0 = 0, T1 = 256, element j = k*256 + lo), threads with
 //      consecutive tid take consecutive columns.  ROW: sub-problems are contiguous rows
@@ -327,7 +313,7 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
                                                     const int* __restrict__ ids, int lpp, size_t pstride,
                                                     const int* __restrict__ loff, const u64* __restrict__ osc,
                                                     NttSrc io) {
-    static_assert(!SRC || COL != INV, "only the first pass of a transform reads a separate source");
+    static_assert(!SRC || (INV && !COL), "only the inverse transform's first pass reads a separate source");
     griddep_entry();
     __shared__ u64 sm[SUBS * F_STRIDE];
     const int limb = blockIdx.y;
@@ -345,15 +331,8 @@ __global__ void __launch_bounds__(16 * SUBS, MINB) k_ntt16(u64* __restrict__ dat
     auto gidx = [&](int k) -> size_t { return COL ? ((size_t)k << 8) + sub : ((size_t)sub << 8) + k; };
 
     if (!INV) {
-        if (SRC) {
-            const u64* sr = io.src + (size_t)(limb / lpp) * io.src_pstride;
-            const bool small = io.qs < 4 * q;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) x[i] = lift_lazy(sr[gidx(t + 16 * i)], io.qs, small, P->m);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) x[i] = a[gidx(t + 16 * i)];
-        }
+        for (int i = 0; i < 16; ++i) x[i] = a[gidx(t + 16 * i)];
         fwd_round<false>(x, t, hi, s0, P, q, q2);
 #pragma unroll
         for (int i = 0; i < 16; ++i) sm[f_slot(sp, t + 16 * i)] = x[i];
@@ -425,7 +404,7 @@ __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const De
                                                 const int* __restrict__ ids, int lpp, size_t pstride,
                                                 const int* __restrict__ loff, const u64* __restrict__ osc,
                                                 NttSrc io) {
-    static_assert(!SRC || COL != INV, "only the first pass of a transform reads a separate source");
+    static_assert(!SRC || (INV && !COL), "only the inverse transform's first pass reads a separate source");
     griddep_entry();
     __shared__ u64 sm[4 * F_STRIDE];
     const int limb = blockIdx.y;
@@ -449,15 +428,8 @@ __global__ void __launch_bounds__(256) k_ntt16s(u64* __restrict__ data, const De
             k0 = ins0(ins0(t, 6 - u), 7 - u);
             const int ks[4] = {k0, k0 + e, k0 + d, k0 + d + e};
             if (rr == 0) {
-                if (SRC) {
-                    const u64* sr = io.src + (size_t)(limb / lpp) * io.src_pstride;
-                    const bool small = io.qs < 4 * q;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) x[i] = lift_lazy(sr[gidx(ks[i])], io.qs, small, P->m);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) x[i] = a[gidx(ks[i])];
-                }
+                for (int i = 0; i < 4; ++i) x[i] = a[gidx(ks[i])];
             } else {
                 __syncthreads();
 #pragma unroll
@@ -702,8 +674,8 @@ void launch_ntt_cl(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, in
 // One whole N = 2^16 transform with variant v: the cluster kernel, or the two passes (forward:
 // COL then ROW; inverse: ROW then COL).  Algorithmic bytes: one read and one write of the
 // limbs per transform, split evenly over the two passes.
-// (io: a separate source of the first pass and an output factor, as NttSrc describes; the
-// cluster variant takes neither, its callers read in place)
+// (io: a separate source of the inverse's first pass and an output factor, as NttSrc
+// describes; the cluster variant takes neither, its callers copy first)
 template <bool INV>
 void launch_ntt_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
                         const int* loff, const u64* osc = nullptr, const NttSrc& io = NttSrc{}) {
@@ -715,10 +687,11 @@ void launch_ntt_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const 
         launch_ntt_cl<INV>(cx, data, nlimbs, ids, lpp, pstride, loff, osc);
         return;
     }
+    CK_CHECK(INV || !io.src, CKKS_EINVAL, "only the inverse transform reads a separate source");
     {
         KTimer kt_(cx, nm, bytes / 2);
-        if (io.src)
-            launch_ntt16_variant<!INV, INV, true>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc, io);
+        if (INV && io.src)     // the inverse's first pass is the ROW pass
+            launch_ntt16_variant<false, true, true>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc, io);
         else
             launch_ntt16_variant<!INV, INV>(cx, v, data, nlimbs, ids, lpp, pstride, loff, osc, io);
     }
@@ -1804,7 +1777,7 @@ void ntt_inverse_from(const ckks_ctx* c, const u64* src, size_t src_pstride, u64
     CK_CHECK(!scaled || (lpp == 1 && osc == nullptr && pstride == c->n), CKKS_EINVAL,
              "an integer factor needs one contiguous row per polynomial and no output scale table");
     if (c->logn == 16 && ntt_pick(c, nlimbs) != NTT_CL) {
-        NttSrc io{src, src_pstride, 0, 0, 0};
+        NttSrc io{src, src_pstride, 0, 0};
         if (scaled) {
             const u64 q = c->mod_of[k_id];
             io.ow = hostmath::mulmod(kres, hostmath::invmod((u64)c->n % q, q), q);
@@ -1825,19 +1798,6 @@ void ntt_inverse_from(const ckks_ctx* c, const u64* src, size_t src_pstride, u64
                                      cudaMemcpyDeviceToDevice, c->stream));
     }
     ntt_inverse(c, data, nlimbs, ids, lpp, pstride, osc);
-}
-
-void ntt_forward_lift(const ckks_ctx* c, const u64* src, int src_id, size_t src_pstride, u64* o, int nlimbs,
-                      const int* ids, int lpp) {
-    if (nlimbs <= 0) return;
-    if (c->logn == 16 && ntt_pick(c, nlimbs) != NTT_CL) {
-        const NttSrc io{src, src_pstride, c->mod_of[src_id], 0, 0};
-        launch_ntt_transform<false>(c, o, nlimbs, ids, lpp, (size_t)lpp * c->n, nullptr, nullptr, io);
-        LAUNCH_CHECK();
-        return;
-    }
-    lift_centred(c, src, src_id, o, nlimbs, ids, lpp, src_pstride);
-    ntt_forward(c, o, nlimbs, ids, lpp);
 }
 
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nl, const int* ids, int lpp) {

@@ -492,7 +492,8 @@ ckks_ct rescale_mul(const ckks_ct& a, long long k) {
     kern::ntt_inverse_from(c, a.c0() + (size_t)l * n, (size_t)(l + 1) * n, last.ptr, np_, c->d_iota + l, 1, n,
                            nullptr, from_signed(k, c->q[l]), l);
     DevBuf lift((size_t)np_ * l * n, c->stream);
-    kern::ntt_forward_lift(c, last.ptr, l, n, lift.ptr, np_ * l, c->d_iota, l);     // every polynomial
+    kern::lift_centred(c, last.ptr, l, lift.ptr, np_ * l, c->d_iota, l, n);     // every polynomial
+    kern::ntt_forward(c, lift.ptr, np_ * l, c->d_iota, l);
     ckks_ct o = new_ct(c, l - 1, a.scale / (double)c->q[l], a.nb);
     ScalarVec s1;
     for (int i = 0; i < l; ++i) {
@@ -543,7 +544,8 @@ ckks_ct mod_raise(const ckks_ct& a) {
     DevBuf coef((size_t)np_ * n, c->stream);
     kern::ntt_inverse_from(c, a.c0(), n, coef.ptr, np_, c->d_iota, 1, n, nullptr);
     ckks_ct o = new_ct(c, c->L, a.scale, a.nb);
-    kern::ntt_forward_lift(c, coef.ptr, 0, n, o.buf.ptr, np_ * c->nq, c->d_iota, c->nq);   // row k from source k / nq
+    kern::lift_centred(c, coef.ptr, 0, o.buf.ptr, np_ * c->nq, c->d_iota, c->nq, n);   // row k from source k / nq
+    kern::ntt_forward(c, o.buf.ptr, np_ * c->nq, c->d_iota, c->nq);
     return o;
 }
 

@@ -86,9 +86,8 @@ def test_cluster_ntt_in_key_switching():
     N = 2^16 stay bit-exact against the oracle.  Then every two-pass variant forced in turn,
     and the default: hoisted rotations, HMult + relinearisation (ModDown) and rescale
     bit-exact at N = 2^16.  Every variant, the cluster one included: the level drop by
-    rescales with integer factors (the inverse transform that reads the top limbs in place
-    and applies the factor with N^-1, the forward transform that lifts while it loads) and
-    ModRaise"""
+    rescales with integer factors (the inverse transform that reads the top limbs where they
+    lie and applies the factor with N^-1) and ModRaise"""
     K, o, ctx, keys = make_pair("cfg2", 7, rotations=[1, 5], conj=False)
     P = o.P
     K.ckks_ctx_set_ntt_variant(ctx, 5)
