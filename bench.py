@@ -38,9 +38,9 @@ METRIC = "ms per conv2d+bootstrap block at N=2^16"
 NTT_FWD_DRAM_PER_ALGO_BYTE = (134.4 + 81.0 + 186.5 + 89.4) / 268.4
 # The same ratio at the block's own launch sizes (at most ~70 limbs, so the whole transform
 # fits in the 129 MB L2): ncu with warm caches (no flush, as in the block) on a 24-limb forward
-# transform counted 0.012 + 0.021 MB (first pass) and 0.143 + 0.030 MB (second pass) of DRAM
+# transform counted 0.005 + 0.050 MB (first pass) and 0.082 + 0.025 MB (second pass) of DRAM
 # traffic for 25.2 MB of algorithmic bytes.
-NTT_FWD_DRAM_PER_ALGO_BYTE_IN_L2 = (0.012544 + 0.020736 + 0.142848 + 0.029696) / (2 * 24 * 0.524288)
+NTT_FWD_DRAM_PER_ALGO_BYTE_IN_L2 = (0.005120 + 0.049920 + 0.082432 + 0.025088) / (2 * 24 * 0.524288)
 L2_BYTES = 129e6
 # The same ratio for the key-switch inner product, from an ncu capture (cold caches) of one
 # launch at the top level (`--kernel ks`): 3 digits x 31 extended limbs with the automorphed c0
