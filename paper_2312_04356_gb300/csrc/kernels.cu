@@ -124,10 +124,12 @@ inline dim3 ewv_grid(int n, int nlimbs, int v) {
     return dim3(x, nlimbs);
 }
 inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+// words per thread of the elementwise kernels when every pointer is 16-byte aligned
+constexpr int EWV_VEC = 4;
 #define EWV_LAUNCH(K, vec, nl, ...)                                                          \
     do {                                                                                     \
         if (vec)                                                                             \
-            klaunch(c, K<2>, ewv_grid(c->n, (nl), 2), EW_THREADS, 0, __VA_ARGS__);        \
+            klaunch(c, K<EWV_VEC>, ewv_grid(c->n, (nl), EWV_VEC), EW_THREADS, 0, __VA_ARGS__); \
         else                                                                                 \
             klaunch(c, K<1>, ewv_grid(c->n, (nl), 1), EW_THREADS, 0, __VA_ARGS__);        \
     } while (0)
@@ -742,37 +744,45 @@ void launch_pass(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int 
 }
 
 // ----------------------------------------------------------- elementwise ----
-// One thread per V consecutive words of a limb (V = 2: 16-byte loads and stores, used when
-// every pointer of the launch is 16-byte aligned); all operands are loaded before any
+// One thread per V consecutive words of a limb (V = 2 or 4: 16-byte loads and stores, used
+// when every pointer of the launch is 16-byte aligned); all operands are loaded before any
 // store, so in-place calls (o == a) are safe.
 template <int V>
 __device__ __forceinline__ void ldv(const u64* p, u64 (&r)[V]) {
-    if constexpr (V == 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p);
-        r[0] = t.x;
-        r[1] = t.y;
-    } else {
+    if constexpr (V == 1) {
         r[0] = p[0];
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k += 2) {
+            const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p + k);
+            r[k] = t.x;
+            r[k + 1] = t.y;
+        }
     }
 }
 // streaming load (evict-first in L1 and L2): for data read once, so that it does not push
 // reused data out of L2
 template <int V>
 __device__ __forceinline__ void ldv_cs(const u64* p, u64 (&r)[V]) {
-    if constexpr (V == 2) {
-        const ulonglong2 t = __ldcs(reinterpret_cast<const ulonglong2*>(p));
-        r[0] = t.x;
-        r[1] = t.y;
-    } else {
+    if constexpr (V == 1) {
         r[0] = __ldcs(p);
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k += 2) {
+            const ulonglong2 t = __ldcs(reinterpret_cast<const ulonglong2*>(p + k));
+            r[k] = t.x;
+            r[k + 1] = t.y;
+        }
     }
 }
 template <int V>
 __device__ __forceinline__ void stv(u64* p, const u64 (&r)[V]) {
-    if constexpr (V == 2)
-        *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(r[0], r[1]);
-    else
+    if constexpr (V == 1) {
         p[0] = r[0];
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k += 2) *reinterpret_cast<ulonglong2*>(p + k) = make_ulonglong2(r[k], r[k + 1]);
+    }
 }
 #define EWV_BEGIN(n)                                                \
     const int j = V * (blockIdx.x * blockDim.x + threadIdx.x);      \
