@@ -466,10 +466,10 @@ int ckks_ct_export_rns(ckks_ctx* ctx, const ckks_ct* ct, uint64_t* host) {
         REQ(ct);
         REQ(host);
         CK_CHECK(ct->level >= 0, CKKS_EINVAL, "empty ciphertext");
-        const size_t words = 2 * (size_t)(ct->level + 1) * ctx->n;
+        const int nl = ct->level + 1;
+        const size_t words = 2 * (size_t)nl * ctx->n;
         DevBuf t(words, ctx->stream);
-        CUDA_CHECK(cudaMemcpyAsync(t.ptr, ct->buf.ptr, words * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-        kern::ntt_inverse(ctx, t.ptr, 2 * (ct->level + 1), ctx->d_iota, ct->level + 1);
+        kern::ntt_inverse_from(ctx, ct->buf.ptr, (size_t)nl * ctx->n, t.ptr, 2 * nl, ctx->d_iota, nl, 0, nullptr);
         CUDA_CHECK(cudaMemcpyAsync(host, t.ptr, words * 8, cudaMemcpyDeviceToHost, ctx->stream));
         CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     });

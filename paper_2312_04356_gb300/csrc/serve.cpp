@@ -176,9 +176,9 @@ void run_model(ckks_server* s, const Model& m, const u64* d_in, u64* d_out) {
     const size_t per_out = 2 * (size_t)(m.out_level + 1) * c->n;
     for (int j = 0; j < m.n_out; ++j) {
         CK_CHECK(xs[j].level == m.out_level, CKKS_EINVAL, "model output level changed");
-        CUDA_CHECK(cudaMemcpyAsync(d_out + j * per_out, xs[j].buf.ptr, per_out * 8, cudaMemcpyDeviceToDevice,
-                                   c->stream));
-        kern::ntt_inverse(c, d_out + j * per_out, 2 * (m.out_level + 1), c->d_iota, m.out_level + 1);
+        const int nl = m.out_level + 1;
+        kern::ntt_inverse_from(c, xs[j].buf.ptr, (size_t)nl * c->n, d_out + j * per_out, 2 * nl, c->d_iota, nl, 0,
+                               nullptr);
     }
 }
 
