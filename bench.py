@@ -797,6 +797,10 @@ def run_ours(args):
     cap, loads, plain, _ = serve_figures(K, s, 8, 2.0, loads=(0.8,), with_plain=True)
     serving = {"slots": 8, "mix": "70% one config-2 block, 30% two-block chains; host limbs in and out",
                "capacity_closed_loop": cap, "poisson_0.8": loads[0], "plain_one_slot": plain}
+    try:
+        activation = activation_figures(K, torch, ctx, s["keys"], stream, value)
+    except Exception as e:  # reported beside the block, never required
+        activation = {"failed": str(e)}
     if rank != 0:
         return
     cpu = None
@@ -816,6 +820,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clocks, "gpu_launches": launches, "launches_per_block": per_graph,
             "batched": batched, "batched_lockstep": lock, "roofline_batched": roof_b, "serving": serving,
+            "activation": activation,
             "autotune": tuned,
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(host_in.nbytes),
                     "d2h_bytes_per_step": int(host_out.nbytes)},
@@ -825,6 +830,48 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def activation_figures(K, torch, ctx, keys, stream, block_ms, reps=5):
+    """HActivation (Alg. 1's activation step) at N = 2^16 as the composite polynomial ReLU
+    x (1 + s3(s2(s1(x)))) / 2 of degrees (15, 15, 27), timed with CUDA events on its own: its
+    levels do not fit after the block's, so in a network it runs after a bootstrap of its own.
+    The stages are Chebyshev least-squares fits (numpy) of tanh(5x), tanh(5x) and
+    (1 + tanh(8x)) / 2: the time depends on the degrees only, and the decoded output is compared
+    with the same composite evaluated in FP64."""
+    from numpy.polynomial import chebyshev as CH
+    nodes = np.cos(np.pi * (np.arange(4096) + 0.5) / 4096)
+
+    def fit(f, deg, odd):
+        c = CH.chebfit(nodes, f(nodes), deg)
+        if odd:
+            c[0::2] = 0.0
+        return c
+    stages = [fit(lambda x: np.tanh(5 * x), 15, True), fit(lambda x: np.tanh(5 * x), 15, True),
+              fit(lambda x: (1 + np.tanh(8 * x)) / 2, 27, False)]
+    q, _, _, delta = K.ckks_ctx_info(ctx)
+    lev = len(q) - 1
+    v = np.random.default_rng(77).uniform(-1.0, 1.0, ctx.n // 2)
+    ct = K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, v, lev, delta[lev]), 77)
+    out = K.ckks_eval_relu(ctx, keys, ct, stages)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        K.ckks_eval_relu(ctx, keys, ct, stages, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    y = v
+    for c in stages:
+        y = CH.chebval(y, c)
+    dec = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, out)).real
+    lev_out, _ = K.ckks_ct_info(out)
+    return {"relu_ms": round(ms, 3), "degrees": [15, 15, 27], "from_level": lev, "to_level": lev_out,
+            "decoded_max_abs_err_vs_fp64_composite": float(np.abs(dec - v * y).max()),
+            "block_plus_activation_ms": round(block_ms + ms, 3),
+            "how": "eager calls (no graph) on a fresh encryption at the top level, mean of %d" % reps,
+            "note": "in a network the activation needs one more bootstrap (about one block) before it"}
 
 
 def run_ds(args):

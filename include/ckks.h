@@ -622,7 +622,8 @@ int ckks_downsample_layer_graph_create(ckks_ctx* ctx, const ckks_keys* keys, int
  * 2 / (b - a), rescaled onto the canonical scale, then -(a + b) / (b - a) added.  T_k from
  * T_{ceil(k/2)} T_{floor(k/2)} (baby and giant steps, Chebyshev division), each piece brought to
  * the canonical scale of its target level after one rescale; levels used: ceil(log2 deg) + 1
- * (+ 1 for the change of variable).  Errors: CKKS_EINVAL (deg < 1, a >= b, unknown basis),
+ * (+ 1 for the change of variable, + 1 when the evaluation crosses from the bootstrapping
+ * segment of the chain into the circuit segment).  Errors: CKKS_EINVAL (deg < 1, a >= b, unknown basis),
  * CKKS_ELEVEL. */
 int ckks_eval_poly(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, int deg,
                    int basis, double a, double b, ckks_ct* out);
@@ -652,7 +653,8 @@ int ckks_rescale_noalloc(ckks_ctx* ctx, const uint64_t* d_in, int level, uint64_
  * `coeffs`, degrees in degs[n_stages], evaluated as by ckks_eval_poly), then x * y with x
  * brought down to y's level.  With s_1..s_{k-1} normalised odd sign approximations and
  * s_k = (1 + sign approximation) / 2 this is x (1 + sign(x)) / 2.  Levels used:
- * sum_i (ceil(log2 deg_i) + 1) + 1. */
+ * sum_i (ceil(log2 deg_i) + 1) + 1, and one more when the stages cross from the bootstrapping
+ * segment of the chain into the circuit segment (18 for degrees (15, 15, 27) from level 23). */
 int ckks_eval_relu(ckks_ctx* ctx, const ckks_keys* keys, const ckks_ct* in, const double* coeffs, const int* degs,
                    int n_stages, ckks_ct* out);
 
