@@ -451,6 +451,25 @@ def test_eval_relu_bitexact():
     assert np.abs(dec - R.relu_poly_fp64(v, stages)).max() < 2.0 ** -12
 
 
+def test_eval_relu_full_size_across_the_segment_boundary():
+    """HActivation at N = 2^16 (config-2 chain) from the top level: the (15, 15, 27) composite
+    crosses from the 48-bit bootstrapping segment into the 42-bit circuit segment, uses 18
+    levels (one more than the stages' depth, as the header states) and decodes within 2^-12 of
+    the FP64 polynomial ReLU"""
+    from oracle import relu as R
+    from paper_2312_04356_gb300 import ckks as K
+    stages, _ = R.composite_relu_stages()
+    P = oracle_params("cfg2")
+    ctx = gpu_ctx("cfg2", 47)
+    keys = K.ckks_keygen(ctx, [], False)
+    v = np.random.default_rng(6).uniform(-1, 1, P.n // 2)
+    ct = K.ckks_encrypt(ctx, keys, K.ckks_encode(ctx, v, P.L, P.delta[P.L]), 3)
+    got = K.ckks_eval_relu(ctx, keys, ct, stages)
+    assert K.ckks_ct_info(got)[0] == P.L - 18
+    dec = K.ckks_decode(ctx, K.ckks_decrypt(ctx, keys, got)).real
+    assert np.abs(dec - R.relu_poly_fp64(v, stages)).max() < 2.0 ** -12
+
+
 @pytest.mark.slow
 def test_cfg2_block_full_size():
     """config 2 at full size (N = 2^16, 24 limbs, 16 channels of 32x32, Gaussian weights):
