@@ -798,7 +798,7 @@ def run_ours(args):
     serving = {"slots": 8, "mix": "70% one config-2 block, 30% two-block chains; host limbs in and out",
                "capacity_closed_loop": cap, "poisson_0.8": loads[0], "plain_one_slot": plain}
     try:
-        activation = activation_figures(K, torch, ctx, s["keys"], stream, value)
+        activation = activation_figures(K, torch, ctx, s["keys"], stream, ms_per_step)
     except Exception as e:  # reported beside the block, never required
         activation = {"failed": str(e)}
     if rank != 0:
@@ -838,7 +838,8 @@ def activation_figures(K, torch, ctx, keys, stream, block_ms, reps=5):
     levels do not fit after the block's, so in a network it runs after a bootstrap of its own.
     The stages are Chebyshev least-squares fits (numpy) of tanh(5x), tanh(5x) and
     (1 + tanh(8x)) / 2: the time depends on the degrees only, and the decoded output is compared
-    with the same composite evaluated in FP64."""
+    with the same composite evaluated in FP64.  block_ms is one GPU's time per block, so that
+    block_plus_activation_ms is one ciphertext's latency through both."""
     from numpy.polynomial import chebyshev as CH
     nodes = np.cos(np.pi * (np.arange(4096) + 0.5) / 4096)
 
