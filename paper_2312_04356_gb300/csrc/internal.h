@@ -335,8 +335,8 @@ void ntt_inverse(const ckks_ctx* c, u64* data, int nlimbs, const int* ids, int l
 // (k % lpp) N, row k of the output at data + (k / lpp) * pstride + (k % lpp) N (pstride 0: lpp N);
 // src is left unchanged; osc as in ntt_inverse.  k_id >= 0: one contiguous row per polynomial
 // (lpp = 1, pstride N), all with the prime k_id, and the result is multiplied by kres (a residue
-// mod that prime).  At N = 2^16 the first pass reads src and the last applies the factor; the
-// cluster variant and smaller rings copy (and scale) first.
+// mod that prime).  At N = 2^16 the first pass reads src and the last applies the factor;
+// smaller rings copy (and scale) first.
 void ntt_inverse_from(const ckks_ctx* c, const u64* src, size_t src_pstride, u64* data, int nlimbs, const int* ids,
                       int lpp, size_t pstride, const u64* osc, u64 kres = 1, int k_id = -1);
 void add(const ckks_ctx* c, const u64* a, const u64* b, u64* o, int nlimbs, const int* ids, int lpp);

@@ -529,7 +529,7 @@ constexpr int CL_SUBS = 32, CL_THREADS = 512, CL_SMEM_WORDS = CL_SUBS * F_STRIDE
 template <bool INV>
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(CL_THREADS, 2)
     k_ntt_cl(u64* __restrict__ data, const DevPrime* __restrict__ primes, const int* __restrict__ ids, int lpp,
-             size_t pstride, const int* __restrict__ loff, const u64* __restrict__ osc) {
+             size_t pstride, const int* __restrict__ loff, const u64* __restrict__ osc, NttSrc io) {
     griddep_entry();
     extern __shared__ u64 sm[];
     cg::cluster_group cl = cg::this_cluster();
@@ -587,8 +587,9 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(CL_THREADS, 2)
 #pragma unroll
         for (int i = 0; i < 16; ++i) a[((size_t)row << 8) + tr + 16 * i] = sm[f_slot(spr, tr + 16 * i)];
     } else {
+        const u64* sr = io.src ? io.src + (size_t)(limb / lpp) * io.src_pstride + ((size_t)r << 16) : a;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) sm[f_slot(spr, tr + 16 * i)] = a[((size_t)row << 8) + tr + 16 * i];
+        for (int i = 0; i < 16; ++i) sm[f_slot(spr, tr + 16 * i)] = sr[((size_t)row << 8) + tr + 16 * i];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(spr, 16 * tr + i)];
@@ -617,7 +618,8 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(CL_THREADS, 2)
 #pragma unroll
         for (int i = 0; i < 16; ++i) x[i] = sm[f_slot(spc, tc + 16 * i)];
         inv_round<false>(x, tc, 0, 0, P, q, q2);
-        const u64 ni = osc ? osc[2 * r] : P->n_inv, nip = osc ? osc[2 * r + 1] : P->n_inv_p;
+        const u64 ni = io.ow ? io.ow : osc ? osc[2 * r] : P->n_inv;
+        const u64 nip = io.ow ? io.owp : osc ? osc[2 * r + 1] : P->n_inv_p;
 #pragma unroll
         for (int i = 0; i < 16; ++i) a[((size_t)(tc + 16 * i) << 8) + col] = mul_shoup(x[i], ni, nip, q);
     }
@@ -666,30 +668,29 @@ inline int ntt_class(int nlimbs) {
 
 template <bool INV>
 void launch_ntt_cl(const ckks_ctx* cx, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
-                   const int* loff, const u64* osc) {
+                   const int* loff, const u64* osc, const NttSrc& io) {
     static std::atomic<unsigned> done{0};
     allow_dynamic_smem((const void*)k_ntt_cl<INV>, CL_SMEM_WORDS * (int)sizeof(u64), done);
     klaunch(cx, k_ntt_cl<INV>, dim3(8, nlimbs), CL_THREADS, CL_SMEM_WORDS * sizeof(u64),
-            data, cx->d_primes, ids, lpp, pstride, loff, osc);
+            data, cx->d_primes, ids, lpp, pstride, loff, osc, io);
 }
 
 // One whole N = 2^16 transform with variant v: the cluster kernel, or the two passes (forward:
 // COL then ROW; inverse: ROW then COL).  Algorithmic bytes: one read and one write of the
 // limbs per transform, split evenly over the two passes.
 // (io: a separate source of the inverse's first pass and an output factor, as NttSrc
-// describes; the cluster variant takes neither, its callers copy first)
+// describes)
 template <bool INV>
 void launch_ntt_variant(const ckks_ctx* cx, int v, u64* data, int nlimbs, const int* ids, int lpp, size_t pstride,
                         const int* loff, const u64* osc = nullptr, const NttSrc& io = NttSrc{}) {
     const char* nm = INV ? "ntt_inv" : "ntt_fwd";
     const double bytes = 2.0 * nlimbs * cx->n * 8.0;
+    CK_CHECK(INV || !io.src, CKKS_EINVAL, "only the inverse transform reads a separate source");
     if (v == NTT_CL) {
-        CK_CHECK(!io.src && !io.ow, CKKS_EINVAL, "the cluster NTT reads its input in place");
         KTimer kt_(cx, nm, bytes);
-        launch_ntt_cl<INV>(cx, data, nlimbs, ids, lpp, pstride, loff, osc);
+        launch_ntt_cl<INV>(cx, data, nlimbs, ids, lpp, pstride, loff, osc, io);
         return;
     }
-    CK_CHECK(INV || !io.src, CKKS_EINVAL, "only the inverse transform reads a separate source");
     {
         KTimer kt_(cx, nm, bytes / 2);
         if (INV && io.src)     // the inverse's first pass is the ROW pass
@@ -1786,7 +1787,7 @@ void ntt_inverse_from(const ckks_ctx* c, const u64* src, size_t src_pstride, u64
     CK_CHECK(nlimbs % lpp == 0, CKKS_EINVAL, "whole polynomials only");
     CK_CHECK(!scaled || (lpp == 1 && osc == nullptr && pstride == c->n), CKKS_EINVAL,
              "an integer factor needs one contiguous row per polynomial and no output scale table");
-    if (c->logn == 16 && ntt_pick(c, nlimbs) != NTT_CL) {
+    if (c->logn == 16) {
         NttSrc io{src, src_pstride, 0, 0};
         if (scaled) {
             const u64 q = c->mod_of[k_id];
@@ -1797,7 +1798,7 @@ void ntt_inverse_from(const ckks_ctx* c, const u64* src, size_t src_pstride, u64
         LAUNCH_CHECK();
         return;
     }
-    // the cluster variant and the small rings: copy (and scale), then transform in place
+    // the smaller rings: copy (and scale), then transform in place
     if (scaled) {
         ScalarVec sv;
         sv.v[0] = kres;
